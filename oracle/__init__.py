@@ -1,0 +1,208 @@
+"""ctypes binding of the plain FP64 CPU oracle (mhd_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by the test suite, the package's smoke check and the
+benchmark's CPU-baseline leg. The CUDA library never imports or links it.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mhd_oracle.c")
+_SO = os.path.join(_HERE, "_build", "libmhd_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, ERR_ARG, ERR_NOCONV = 0, 1, 3
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C11, -O2, no fused multiply-add)."""
+    os.makedirs(os.path.dirname(_SO), exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "mhd_oracle.h"))):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-D_DEFAULT_SOURCE", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = C.CDLL(build())
+            _declare(_lib)
+    return _lib
+
+
+_dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+
+
+def _declare(L):
+    vp, i, d = C.c_void_p, C.c_int, C.c_double
+    L.og_create.restype = vp
+    L.og_create.argtypes = [i, i, i, d, d, d]
+    L.og_destroy.argtypes = [vp]
+    for name in ("og_radial_nodes", "og_volumes", "og_ktilde2"):
+        getattr(L, name).argtypes = [vp, _dp]
+    L.og_apply_M.argtypes = [vp, d, i, _dp, _dp]
+    L.og_apply_K_neumann.argtypes = [vp, i, _dp, _dp]
+    L.og_diag.argtypes = [vp, d, _dp]
+    L.og_pcg.restype = i
+    L.og_pcg.argtypes = [vp, d, i, _dp, _dp, d, i, i, C.POINTER(C.c_int), C.POINTER(C.c_double)]
+    L.og_coeffs.restype = i
+    L.og_coeffs.argtypes = [vp, d, d, d, d, d, _dp, _dp, _dp, _dp, _dp]
+    L.og_bcentre.argtypes = [vp, _dp, _dp, _dp, _dp]
+    L.og_current_edges.argtypes = [vp, _dp, _dp, _dp, _dp, _dp, _dp]
+    L.og_current_centre.argtypes = [vp, _dp, _dp, _dp, _dp]
+    L.og_force.argtypes = [vp, _dp, _dp, _dp, _dp, d, _dp]
+    L.og_efield_edges.argtypes = [vp, _dp, _dp, _dp, _dp, d, _dp, _dp, _dp]
+    L.og_ct.argtypes = [vp, _dp, _dp, _dp, d, _dp, _dp, _dp]
+    L.og_divb.argtypes = [vp, _dp, _dp, _dp, _dp]
+    L.og_step.restype = i
+    L.og_step.argtypes = [vp, d, d, d, d, d, d, d, i, _dp, _dp, _dp, _dp, _dp]
+    if hasattr(L, "og_adjoint_step"):
+        L.og_adjoint_step.restype = i
+        L.og_adjoint_step.argtypes = [vp, d, d, d, d, d, i] + [_dp] * 12
+
+
+def _c(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Grid:
+    """Oracle grid: nr x nt x np cells, r in [r0, r1] with geometric stretch."""
+
+    def __init__(self, nr, nt, np_, r0, r1, stretch):
+        self.L = lib()
+        self.h = self.L.og_create(nr, nt, np_, r0, r1, stretch)
+        if not self.h:
+            raise ValueError("bad grid")
+        self.nr, self.nt, self.np = nr, nt, np_
+        self.N = nr * nt * np_
+        self.r0, self.r1, self.stretch = r0, r1, stretch
+
+    @classmethod
+    def from_desc(cls, d):
+        return cls(d.nr, d.nt, d.np, d.r0, d.r1, d.stretch)
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            self.L.og_destroy(h)
+            self.h = None
+
+    # shapes
+    @property
+    def shapes(self):
+        nr, nt, n = self.nr, self.nt, self.np
+        return dict(br=(nr + 1, nt, n), bt=(nr, nt + 1, n), bp=(nr, nt, n),
+                    er=(nr, nt + 1, n), et=(nr + 1, nt, n), ep=(nr + 1, nt + 1, n))
+
+    def radial_nodes(self):
+        o = np.empty(self.nr + 1)
+        self.L.og_radial_nodes(self.h, o)
+        return o
+
+    def volumes(self):
+        o = np.empty((self.nr, self.nt))
+        self.L.og_volumes(self.h, o)
+        return o
+
+    def ktilde2(self):
+        o = np.empty((self.nr, self.nt))
+        self.L.og_ktilde2(self.h, o)
+        return o
+
+    def apply_M(self, alpha, p):
+        p = _c(p)
+        nc = p.size // self.N
+        q = np.empty_like(p)
+        self.L.og_apply_M(self.h, alpha, nc, p, q)
+        return q
+
+    def apply_K_neumann(self, p):
+        p = _c(p)
+        q = np.empty_like(p)
+        self.L.og_apply_K_neumann(self.h, p.size // self.N, p, q)
+        return q
+
+    def diag(self, alpha):
+        o = np.empty((self.nr, self.nt))
+        self.L.og_diag(self.h, alpha, o)
+        return o
+
+    def pcg(self, alpha, b, x0=None, tol=1e-9, max_iter=100000, fixed_iters=0):
+        b = _c(b)
+        x = np.zeros_like(b) if x0 is None else _c(x0).copy()
+        it = C.c_int(0)
+        rr = C.c_double(0)
+        st = self.L.og_pcg(self.h, alpha, b.size // self.N, b, x, tol, max_iter, fixed_iters,
+                           C.byref(it), C.byref(rr))
+        return x, it.value, rr.value, st
+
+    def coeffs(self, v, br, bt, bp, nu=1e-3, cfl=0.4, dt_fixed=0.0, dt_max=0.0, asi_fixed=-1.0):
+        o = np.empty(5)
+        st = self.L.og_coeffs(self.h, nu, cfl, dt_fixed, dt_max, asi_fixed, _c(v), _c(br), _c(bt),
+                              _c(bp), o)
+        if st != OK:
+            raise ValueError(f"og_coeffs status {st}")
+        return dict(dt=o[0], cf=o[1], cw=o[2], alpha_si=o[3], alpha_nu=o[4])
+
+    def bcentre(self, br, bt, bp):
+        o = np.empty((3, self.nr, self.nt, self.np))
+        self.L.og_bcentre(self.h, _c(br), _c(bt), _c(bp), o)
+        return o
+
+    def current_edges(self, br, bt, bp):
+        s = self.shapes
+        jr, jt, jp = np.empty(s["er"]), np.empty(s["et"]), np.empty(s["ep"])
+        self.L.og_current_edges(self.h, _c(br), _c(bt), _c(bp), jr, jt, jp)
+        return jr, jt, jp
+
+    def current_centre(self, br, bt, bp):
+        o = np.empty((3, self.nr, self.nt, self.np))
+        self.L.og_current_centre(self.h, _c(br), _c(bt), _c(bp), o)
+        return o
+
+    def force(self, v, br, bt, bp, dt):
+        o = np.empty((3, self.nr, self.nt, self.np))
+        self.L.og_force(self.h, _c(v), _c(br), _c(bt), _c(bp), dt, o)
+        return o
+
+    def efield_edges(self, vbar, br, bt, bp, eta=0.0):
+        s = self.shapes
+        er, et, ep = np.empty(s["er"]), np.empty(s["et"]), np.empty(s["ep"])
+        self.L.og_efield_edges(self.h, _c(vbar), _c(br), _c(bt), _c(bp), eta, er, et, ep)
+        return er, et, ep
+
+    def ct(self, er, et, ep, dt, br, bt, bp):
+        br, bt, bp = _c(br).copy(), _c(bt).copy(), _c(bp).copy()
+        self.L.og_ct(self.h, _c(er), _c(et), _c(ep), dt, br, bt, bp)
+        return br, bt, bp
+
+    def divb(self, br, bt, bp):
+        o = np.empty((self.nr, self.nt, self.np))
+        self.L.og_divb(self.h, _c(br), _c(bt), _c(bp), o)
+        return o
+
+    def step(self, state, nu=1e-3, eta=0.0, cfl=0.4, dt_fixed=0.0, dt_max=0.0, asi_fixed=-1.0,
+             tol=1e-9, max_iter=100000):
+        """One step on a copy of `state` (dict br, bt, bp, vr, vt, vp). Returns (new, info)."""
+        v = np.ascontiguousarray(np.stack([state["vr"], state["vt"], state["vp"]]), dtype=np.float64)
+        br, bt, bp = _c(state["br"]).copy(), _c(state["bt"]).copy(), _c(state["bp"]).copy()
+        info = np.zeros(11)
+        st = self.L.og_step(self.h, nu, eta, cfl, dt_fixed, dt_max, asi_fixed, tol, max_iter, v, br,
+                            bt, bp, info)
+        out = dict(br=br, bt=bt, bp=bp, vr=v[0].copy(), vt=v[1].copy(), vp=v[2].copy())
+        inf = dict(status=st, dt=info[0], cf=info[1], cw=info[2], alpha_si=info[3],
+                   alpha_nu=info[4], iters=[int(info[5]), int(info[6]), int(info[7])],
+                   relres=list(info[8:11]))
+        return out, inf

@@ -1,0 +1,691 @@
+/*
+ * Plain FP64 CPU oracle for the zero-beta MHD step (arXiv 1811.02605). TEST INFRASTRUCTURE:
+ * only tests, the smoke check and the benchmark's CPU baseline use it. See mhd_oracle.h for
+ * layouts. Each function cites the passage of the paper it restates; where the paper is silent
+ * the comment states the reading taken.
+ */
+#include "mhd_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+struct og_grid {
+    int nr, nt, np;
+    long long N;
+    double r0, r1, stretch;
+    double dth, dph;
+    double *r;        /* nr+1 radial nodes */
+    double *rc;       /* nr   radial centres */
+    double *sn, *cn;  /* nt+1 sin/cos of theta nodes (exact 0, +-1 at the poles) */
+    double *sc, *cc;  /* nt   sin/cos of theta centres */
+    /* per (i,j) tables, nr*nt: cell volume, rho at the centre, k~^2 */
+    double *vol, *rho, *kt2;
+    /* stiffness weights of the symmetric operator K (reading R3):
+     *   wr[i*nt+j], i = 0..nr  : radial face i (between cells i-1 and i); wr[0] is the
+     *                            Dirichlet weight at r0 (one-sided), wr[nr] = 0 (Neumann)
+     *   wt[i*(nt+1)+j], j = 0..nt : theta face j; 0 at the poles (zero face area)
+     *   wp[i*nt+j]              : each of the two phi faces of the cell */
+    double *wr, *wt, *wp;
+};
+
+#define IDX(g, i, j, k) ((((long long)(i)) * (g)->nt + (j)) * (g)->np + (k))
+#define IDXT(g, i, j, k) ((((long long)(i)) * ((g)->nt + 1) + (j)) * (g)->np + (k))
+#define KP(g, k) (((k) + 1) % (g)->np)
+#define KM(g, k) (((k) + (g)->np - 1) % (g)->np)
+
+static double rho0(const og_grid* g, double r) { return (g->r0 / r) * (g->r0 / r); }
+
+/* ---------------------------------------------------------------------------------------------
+ * Grid (reading R2: geometric radial stretch, uniform theta in [0,pi], periodic phi; exact
+ * finite-volume geometry of spherical cells).
+ * ------------------------------------------------------------------------------------------- */
+og_grid* og_create(int nr, int nt, int np, double r0, double r1, double stretch) {
+    if (nr < 2 || nt < 2 || np < 1 || !(r1 > r0) || !(r0 > 0) || !(stretch > 0)) return NULL;
+    og_grid* g = (og_grid*)calloc(1, sizeof(og_grid));
+    g->nr = nr; g->nt = nt; g->np = np;
+    g->N = (long long)nr * nt * np;
+    g->r0 = r0; g->r1 = r1; g->stretch = stretch;
+    g->dth = M_PI / nt;
+    g->dph = 2.0 * M_PI / np;
+    g->r = (double*)malloc(sizeof(double) * (nr + 1));
+    g->rc = (double*)malloc(sizeof(double) * nr);
+    g->sn = (double*)malloc(sizeof(double) * (nt + 1));
+    g->cn = (double*)malloc(sizeof(double) * (nt + 1));
+    g->sc = (double*)malloc(sizeof(double) * nt);
+    g->cc = (double*)malloc(sizeof(double) * nt);
+    g->vol = (double*)malloc(sizeof(double) * nr * nt);
+    g->rho = (double*)malloc(sizeof(double) * nr * nt);
+    g->kt2 = (double*)malloc(sizeof(double) * nr * nt);
+    g->wr = (double*)calloc((size_t)(nr + 1) * nt, sizeof(double));
+    g->wt = (double*)calloc((size_t)nr * (nt + 1), sizeof(double));
+    g->wp = (double*)calloc((size_t)nr * nt, sizeof(double));
+
+    /* r_{i+1} = r_i + h0 s^i, h0 = (r1-r0)(s-1)/(s^nr-1) */
+    double h0;
+    if (stretch == 1.0) {
+        h0 = (r1 - r0) / nr;
+    } else {
+        double snr = 1.0;
+        for (int i = 0; i < nr; i++) snr *= stretch;
+        h0 = (r1 - r0) * (stretch - 1.0) / (snr - 1.0);
+    }
+    g->r[0] = r0;
+    double dr = h0;
+    for (int i = 0; i < nr; i++) { g->r[i + 1] = g->r[i] + dr; dr *= stretch; }
+    for (int i = 0; i < nr; i++) g->rc[i] = 0.5 * (g->r[i] + g->r[i + 1]);
+    for (int j = 0; j <= nt; j++) { g->sn[j] = sin(j * g->dth); g->cn[j] = cos(j * g->dth); }
+    g->sn[0] = 0.0; g->sn[nt] = 0.0; g->cn[0] = 1.0; g->cn[nt] = -1.0;
+    for (int j = 0; j < nt; j++) { g->sc[j] = sin((j + 0.5) * g->dth); g->cc[j] = cos((j + 0.5) * g->dth); }
+
+    for (int i = 0; i < nr; i++) {
+        double ri = g->r[i], ro = g->r[i + 1];
+        double ring = 0.5 * (ro * ro - ri * ri);       /* int r dr over the shell */
+        for (int j = 0; j < nt; j++) {
+            double band = g->cn[j] - g->cn[j + 1];      /* int sin(theta) dtheta over the band */
+            g->vol[i * nt + j] = (ro * ro * ro - ri * ri * ri) / 3.0 * band * g->dph;
+            g->rho[i * nt + j] = rho0(g, g->rc[i]);
+            double a = ro - ri;
+            double b = g->rc[i] * g->dth;
+            double c = g->rc[i] * g->sc[j] * g->dph;
+            g->kt2[i * nt + j] = 1.0 / (a * a) + 1.0 / (b * b) + 1.0 / (c * c);
+            /* phi face: area ring*dth, centre distance rc sin(theta_c) dphi, rho at rc */
+            g->wp[i * nt + j] = g->rho[i * nt + j] * (ring * g->dth) / c;
+        }
+        /* theta faces j = 1..nt-1: area sin(theta_j) ring dphi, distance rc dth */
+        for (int j = 1; j < nt; j++)
+            g->wt[i * (nt + 1) + j] = rho0(g, g->rc[i]) * (g->sn[j] * ring * g->dph) / (g->rc[i] * g->dth);
+    }
+    for (int j = 0; j < nt; j++) {
+        double band = g->cn[j] - g->cn[j + 1];
+        /* Dirichlet face at r0: rho0(r0) A / (rc_0 - r0) */
+        g->wr[0 * nt + j] = rho0(g, r0) * (r0 * r0 * band * g->dph) / (g->rc[0] - r0);
+        /* interior radial faces: rho0(r_i) A / (rc_i - rc_{i-1}) */
+        for (int i = 1; i < nr; i++)
+            g->wr[i * nt + j] = rho0(g, g->r[i]) * (g->r[i] * g->r[i] * band * g->dph) / (g->rc[i] - g->rc[i - 1]);
+        g->wr[nr * nt + j] = 0.0; /* Neumann at r1 */
+    }
+    return g;
+}
+
+void og_destroy(og_grid* g) {
+    if (!g) return;
+    free(g->r); free(g->rc); free(g->sn); free(g->cn); free(g->sc); free(g->cc);
+    free(g->vol); free(g->rho); free(g->kt2); free(g->wr); free(g->wt); free(g->wp);
+    free(g);
+}
+
+void og_radial_nodes(const og_grid* g, double* r) { memcpy(r, g->r, sizeof(double) * (g->nr + 1)); }
+void og_volumes(const og_grid* g, double* v) { memcpy(v, g->vol, sizeof(double) * g->nr * g->nt); }
+void og_ktilde2(const og_grid* g, double* k) { memcpy(k, g->kt2, sizeof(double) * g->nr * g->nt); }
+
+/* ---------------------------------------------------------------------------------------------
+ * Implicit operator (Eq. 1, viscous and semi-implicit terms; Sec. 4.1 "sparse matrix-vector
+ * products (essentially stencil operations)"). Reading R3: the operator (1/rho) div(rho grad u)
+ * acts on each spherical component separately; multiplied by the cell volume it becomes the
+ * symmetric finite-volume form M_alpha = D + alpha K with D = rho_c V_c and
+ * (K u)_c = sum over faces w_f (u_c - u_nb), Dirichlet u = 0 at r0, Neumann at r1.
+ * ------------------------------------------------------------------------------------------- */
+static void apply_op(const og_grid* g, double alpha, int with_d, int with_dirichlet, int ncomp,
+                     const double* p, double* q) {
+    int nr = g->nr, nt = g->nt, np = g->np;
+    for (int c = 0; c < ncomp; c++) {
+        const double* u = p + c * g->N;
+        double* o = q + c * g->N;
+        for (int i = 0; i < nr; i++)
+            for (int j = 0; j < nt; j++)
+                for (int k = 0; k < np; k++) {
+                    double uc = u[IDX(g, i, j, k)];
+                    double s = 0.0;
+                    if (i > 0) s += g->wr[i * nt + j] * (uc - u[IDX(g, i - 1, j, k)]);
+                    else if (with_dirichlet) s += g->wr[0 * nt + j] * uc;
+                    if (i < nr - 1) s += g->wr[(i + 1) * nt + j] * (uc - u[IDX(g, i + 1, j, k)]);
+                    if (j > 0) s += g->wt[i * (nt + 1) + j] * (uc - u[IDX(g, i, j - 1, k)]);
+                    if (j < nt - 1) s += g->wt[i * (nt + 1) + j + 1] * (uc - u[IDX(g, i, j + 1, k)]);
+                    s += g->wp[i * nt + j] * (uc - u[IDX(g, i, j, KM(g, k))]);
+                    s += g->wp[i * nt + j] * (uc - u[IDX(g, i, j, KP(g, k))]);
+                    double d = with_d ? g->rho[i * nt + j] * g->vol[i * nt + j] * uc : 0.0;
+                    o[IDX(g, i, j, k)] = d + alpha * s;
+                }
+    }
+}
+
+void og_apply_M(const og_grid* g, double alpha, int ncomp, const double* p, double* q) {
+    apply_op(g, alpha, 1, 1, ncomp, p, q);
+}
+
+void og_apply_K_neumann(const og_grid* g, int ncomp, const double* p, double* q) {
+    apply_op(g, 1.0, 0, 0, ncomp, p, q);
+}
+
+void og_diag(const og_grid* g, double alpha, double* d) {
+    int nr = g->nr, nt = g->nt;
+    for (int i = 0; i < nr; i++)
+        for (int j = 0; j < nt; j++) {
+            double s = g->wr[i * nt + j] + g->wr[(i + 1) * nt + j] + g->wt[i * (nt + 1) + j] +
+                       g->wt[i * (nt + 1) + j + 1] + 2.0 * g->wp[i * nt + j];
+            d[i * nt + j] = g->rho[i * nt + j] * g->vol[i * nt + j] + alpha * s;
+        }
+}
+
+/* ---------------------------------------------------------------------------------------------
+ * PCG with PC1 (Sec. 2.2: "the inverse diagonal of the matrix (point-Jacobi)"). Reading P12:
+ * one stacked system for all components with one alpha and one beta; stop when the
+ * recursively updated residual satisfies ||r||_2 <= tol ||b||_2, tested before each iteration;
+ * the count is the number of x updates; b = 0 gives x = 0 after 0 iterations.
+ * ------------------------------------------------------------------------------------------- */
+static double dot(long long n, const double* a, const double* b) {
+    double s = 0.0;
+    for (long long i = 0; i < n; i++) s += a[i] * b[i];
+    return s;
+}
+
+int og_pcg(const og_grid* g, double alpha, int ncomp, const double* b, double* x, double tol,
+           int max_iter, int fixed_iters, int* iters, double* relres) {
+    long long N = g->N, n = ncomp * N;
+    int nt = g->nt, np = g->np;
+    double bnorm = sqrt(dot(n, b, b));
+    if (bnorm == 0.0) {
+        memset(x, 0, sizeof(double) * n);
+        *iters = 0; *relres = 0.0;
+        return OG_OK;
+    }
+    double* d = (double*)malloc(sizeof(double) * g->nr * nt);
+    double* r = (double*)malloc(sizeof(double) * n);
+    double* z = (double*)malloc(sizeof(double) * n);
+    double* p = (double*)malloc(sizeof(double) * n);
+    double* q = (double*)malloc(sizeof(double) * n);
+    og_diag(g, alpha, d);
+    og_apply_M(g, alpha, ncomp, x, q);
+    for (long long e = 0; e < n; e++) r[e] = b[e] - q[e];
+    for (long long e = 0; e < n; e++) z[e] = r[e] / d[(e % N) / np];
+    for (long long e = 0; e < n; e++) p[e] = z[e];
+    double rz = dot(n, r, z);
+    double rn = sqrt(dot(n, r, r));
+    int k = 0;
+    int status = OG_OK;
+    for (;;) {
+        if (fixed_iters > 0) {
+            if (k >= fixed_iters) break;
+        } else {
+            if (rn <= tol * bnorm) break;
+            if (k >= max_iter) { status = OG_ERR_NOCONV; break; }
+        }
+        og_apply_M(g, alpha, ncomp, p, q);
+        double pq = dot(n, p, q);
+        if (!(pq > 0.0)) { status = OG_ERR_NOCONV; break; }
+        double a = rz / pq;
+        for (long long e = 0; e < n; e++) x[e] += a * p[e];
+        for (long long e = 0; e < n; e++) r[e] -= a * q[e];
+        k++;
+        rn = sqrt(dot(n, r, r));
+        for (long long e = 0; e < n; e++) z[e] = r[e] / d[(e % N) / np];
+        double rz_new = dot(n, r, z);
+        double beta = rz_new / rz;
+        rz = rz_new;
+        for (long long e = 0; e < n; e++) p[e] = z[e] + beta * p[e];
+    }
+    *iters = k;
+    *relres = rn / bnorm;
+    free(d); free(r); free(z); free(p); free(q);
+    return status;
+}
+
+/* ---------------------------------------------------------------------------------------------
+ * Cell-centred B (reading R4): mean of the two opposite faces; in the polar rings the theta
+ * component takes only the non-polar face.
+ * ------------------------------------------------------------------------------------------- */
+static void bcentre_at(const og_grid* g, const double* br, const double* bt, const double* bp,
+                       int i, int j, int k, double* o) {
+    int nt = g->nt;
+    o[0] = 0.5 * (br[IDX(g, i, j, k)] + br[IDX(g, i + 1, j, k)]);
+    if (j == 0) o[1] = bt[IDXT(g, i, 1, k)];
+    else if (j == nt - 1) o[1] = bt[IDXT(g, i, nt - 1, k)];
+    else o[1] = 0.5 * (bt[IDXT(g, i, j, k)] + bt[IDXT(g, i, j + 1, k)]);
+    o[2] = 0.5 * (bp[IDX(g, i, j, k)] + bp[IDX(g, i, j, KP(g, k))]);
+}
+
+void og_bcentre(const og_grid* g, const double* br, const double* bt, const double* bp, double* bc) {
+    for (int i = 0; i < g->nr; i++)
+        for (int j = 0; j < g->nt; j++)
+            for (int k = 0; k < g->np; k++) {
+                double o[3];
+                bcentre_at(g, br, bt, bp, i, j, k, o);
+                for (int c = 0; c < 3; c++) bc[c * g->N + IDX(g, i, j, k)] = o[c];
+            }
+}
+
+/* ---------------------------------------------------------------------------------------------
+ * Current density J = curl B (Eq. 1, code units c = 4 pi = 1) on the edges, by Stokes'
+ * theorem on the dual face around each edge, whose corners are the surrounding cell centres
+ * (reading R4). Polar radial edges use the cap around the pole; the tangential field beyond
+ * r0 and r1 is taken equal to the first interior value (ghost centres mirrored in radius).
+ * ------------------------------------------------------------------------------------------- */
+void og_current_edges(const og_grid* g, const double* br, const double* bt, const double* bp,
+                      double* jr, double* jt, double* jp) {
+    int nr = g->nr, nt = g->nt, np = g->np;
+    double dth = g->dth, dph = g->dph;
+    /* radial edges: (i, j, k), j = 0..nt, at (theta_j, phi_k), dual face at rc_i */
+    for (int i = 0; i < nr; i++) {
+        double rc = g->rc[i];
+        double circ_n = 0.0, circ_s = 0.0;
+        for (int k = 0; k < np; k++) {
+            circ_n += bp[IDX(g, i, 0, k)] * rc * g->sc[0] * dph;
+            circ_s -= bp[IDX(g, i, nt - 1, k)] * rc * g->sc[nt - 1] * dph;
+        }
+        double cap_n = rc * rc * (1.0 - g->cc[0]) * 2.0 * M_PI;
+        double cap_s = rc * rc * (1.0 + g->cc[nt - 1]) * 2.0 * M_PI;
+        for (int k = 0; k < np; k++) {
+            jr[IDXT(g, i, 0, k)] = circ_n / cap_n;
+            jr[IDXT(g, i, nt, k)] = circ_s / cap_s;
+        }
+        for (int j = 1; j < nt; j++) {
+            double area = rc * rc * (g->cc[j - 1] - g->cc[j]) * dph;
+            for (int k = 0; k < np; k++) {
+                double c = bp[IDX(g, i, j, k)] * rc * g->sc[j] * dph
+                         - bp[IDX(g, i, j - 1, k)] * rc * g->sc[j - 1] * dph
+                         - bt[IDXT(g, i, j, k)] * rc * dth
+                         + bt[IDXT(g, i, j, KM(g, k))] * rc * dth;
+                jr[IDXT(g, i, j, k)] = c / area;
+            }
+        }
+    }
+    /* theta edges (i, j, k), i = 0..nr, at (r_i, phi_k); dual face at theta_c_j spanning
+     * r_lo..r_hi (cell centres on either side, mirrored ghosts at the boundaries) */
+    for (int i = 0; i <= nr; i++) {
+        double rlo = (i > 0) ? g->rc[i - 1] : 2.0 * g->r0 - g->rc[0];
+        double rhi = (i < nr) ? g->rc[i] : 2.0 * g->r[nr] - g->rc[nr - 1];
+        int ilo = (i > 0) ? i - 1 : 0;
+        int ihi = (i < nr) ? i : nr - 1;
+        for (int j = 0; j < nt; j++) {
+            double area = g->sc[j] * 0.5 * (rhi * rhi - rlo * rlo) * dph;
+            for (int k = 0; k < np; k++) {
+                double c = bp[IDX(g, ilo, j, k)] * rlo * g->sc[j] * dph
+                         + br[IDX(g, i, j, k)] * (rhi - rlo)
+                         - bp[IDX(g, ihi, j, k)] * rhi * g->sc[j] * dph
+                         - br[IDX(g, i, j, KM(g, k))] * (rhi - rlo);
+                jt[IDX(g, i, j, k)] = c / area;
+            }
+        }
+    }
+    /* phi edges (i, j, k), i = 0..nr, j = 0..nt, at (r_i, theta_j); zero on the polar axis */
+    for (int i = 0; i <= nr; i++) {
+        double rlo = (i > 0) ? g->rc[i - 1] : 2.0 * g->r0 - g->rc[0];
+        double rhi = (i < nr) ? g->rc[i] : 2.0 * g->r[nr] - g->rc[nr - 1];
+        int ilo = (i > 0) ? i - 1 : 0;
+        int ihi = (i < nr) ? i : nr - 1;
+        double area = 0.5 * (rhi * rhi - rlo * rlo) * dth;
+        for (int k = 0; k < np; k++) {
+            jp[IDXT(g, i, 0, k)] = 0.0;
+            jp[IDXT(g, i, nt, k)] = 0.0;
+        }
+        for (int j = 1; j < nt; j++)
+            for (int k = 0; k < np; k++) {
+                double c = br[IDX(g, i, j - 1, k)] * (rhi - rlo)
+                         + bt[IDXT(g, ihi, j, k)] * rhi * dth
+                         - br[IDX(g, i, j, k)] * (rhi - rlo)
+                         - bt[IDXT(g, ilo, j, k)] * rlo * dth;
+                jp[IDXT(g, i, j, k)] = c / area;
+            }
+    }
+}
+
+/* J at cell centres: mean of the four edges of each direction around the cell; the polar
+ * phi edges (zero length) are left out of the phi average. */
+static void current_centre_from_edges(const og_grid* g, const double* jr, const double* jt,
+                                      const double* jp, int i, int j, int k, double* o) {
+    int nt = g->nt;
+    int kp = KP(g, k);
+    o[0] = 0.25 * (jr[IDXT(g, i, j, k)] + jr[IDXT(g, i, j, kp)] + jr[IDXT(g, i, j + 1, k)] + jr[IDXT(g, i, j + 1, kp)]);
+    o[1] = 0.25 * (jt[IDX(g, i, j, k)] + jt[IDX(g, i, j, kp)] + jt[IDX(g, i + 1, j, k)] + jt[IDX(g, i + 1, j, kp)]);
+    if (j == 0) o[2] = 0.5 * (jp[IDXT(g, i, 1, k)] + jp[IDXT(g, i + 1, 1, k)]);
+    else if (j == nt - 1) o[2] = 0.5 * (jp[IDXT(g, i, nt - 1, k)] + jp[IDXT(g, i + 1, nt - 1, k)]);
+    else o[2] = 0.25 * (jp[IDXT(g, i, j, k)] + jp[IDXT(g, i, j + 1, k)] + jp[IDXT(g, i + 1, j, k)] + jp[IDXT(g, i + 1, j + 1, k)]);
+}
+
+typedef struct { double *jr, *jt, *jp; } edges3;
+
+static edges3 edges_alloc(const og_grid* g) {
+    edges3 e;
+    e.jr = (double*)malloc(sizeof(double) * g->nr * (g->nt + 1) * g->np);
+    e.jt = (double*)malloc(sizeof(double) * (g->nr + 1) * g->nt * g->np);
+    e.jp = (double*)malloc(sizeof(double) * (g->nr + 1) * (g->nt + 1) * g->np);
+    return e;
+}
+static void edges_free(edges3 e) { free(e.jr); free(e.jt); free(e.jp); }
+
+void og_current_centre(const og_grid* g, const double* br, const double* bt, const double* bp, double* jc) {
+    edges3 e = edges_alloc(g);
+    og_current_edges(g, br, bt, bp, e.jr, e.jt, e.jp);
+    for (int i = 0; i < g->nr; i++)
+        for (int j = 0; j < g->nt; j++)
+            for (int k = 0; k < g->np; k++) {
+                double o[3];
+                current_centre_from_edges(g, e.jr, e.jt, e.jp, i, j, k, o);
+                for (int c = 0; c < 3; c++) jc[c * g->N + IDX(g, i, j, k)] = o[c];
+            }
+    edges_free(e);
+}
+
+/* ---------------------------------------------------------------------------------------------
+ * Explicit momentum force (Eq. 1: -v.grad v + J x B / rho; Sec. 2.2: explicit upwinding).
+ * Reading R4: first-order upwind differences per direction, chosen by the sign of the cell's
+ * own velocity component, over centre distances; Dirichlet mirror ghost (-u) at r0, zero
+ * gradient at r1, no flux from the pole side. Spherical curvature terms of (v.grad)v added.
+ * Output b = rho_c V_c dt F.
+ * ------------------------------------------------------------------------------------------- */
+static double upwind_r(const og_grid* g, const double* u, double vr, int i, int j, int k) {
+    double uc = u[IDX(g, i, j, k)];
+    if (vr > 0.0) {
+        if (i > 0) return (uc - u[IDX(g, i - 1, j, k)]) / (g->rc[i] - g->rc[i - 1]);
+        return (uc - (-uc)) / (2.0 * (g->rc[0] - g->r0));
+    }
+    if (i < g->nr - 1) return (u[IDX(g, i + 1, j, k)] - uc) / (g->rc[i + 1] - g->rc[i]);
+    return 0.0;
+}
+static double upwind_t(const og_grid* g, const double* u, double vt, int i, int j, int k) {
+    double uc = u[IDX(g, i, j, k)];
+    double h = g->rc[i] * g->dth;
+    if (vt > 0.0) {
+        if (j > 0) return (uc - u[IDX(g, i, j - 1, k)]) / h;
+        return 0.0;
+    }
+    if (j < g->nt - 1) return (u[IDX(g, i, j + 1, k)] - uc) / h;
+    return 0.0;
+}
+static double upwind_p(const og_grid* g, const double* u, double vp, int i, int j, int k) {
+    double uc = u[IDX(g, i, j, k)];
+    double h = g->rc[i] * g->sc[j] * g->dph;
+    if (vp > 0.0) return (uc - u[IDX(g, i, j, KM(g, k))]) / h;
+    return (u[IDX(g, i, j, KP(g, k))] - uc) / h;
+}
+
+void og_force(const og_grid* g, const double* v, const double* br, const double* bt,
+              const double* bp, double dt, double* b) {
+    long long N = g->N;
+    int nt = g->nt;
+    edges3 e = edges_alloc(g);
+    og_current_edges(g, br, bt, bp, e.jr, e.jt, e.jp);
+    const double* vr = v;
+    const double* vt = v + N;
+    const double* vp = v + 2 * N;
+    for (int i = 0; i < g->nr; i++)
+        for (int j = 0; j < nt; j++)
+            for (int k = 0; k < g->np; k++) {
+                long long c = IDX(g, i, j, k);
+                double ur = vr[c], ut = vt[c], up = vp[c];
+                double B[3], J[3];
+                bcentre_at(g, br, bt, bp, i, j, k, B);
+                current_centre_from_edges(g, e.jr, e.jt, e.jp, i, j, k, J);
+                double rr = g->rc[i];
+                double cot = g->cc[j] / g->sc[j];
+                /* (v.grad) of each component */
+                double ar = ur * upwind_r(g, vr, ur, i, j, k) + ut * upwind_t(g, vr, ut, i, j, k) + up * upwind_p(g, vr, up, i, j, k);
+                double at = ur * upwind_r(g, vt, ur, i, j, k) + ut * upwind_t(g, vt, ut, i, j, k) + up * upwind_p(g, vt, up, i, j, k);
+                double ap = ur * upwind_r(g, vp, ur, i, j, k) + ut * upwind_t(g, vp, ut, i, j, k) + up * upwind_p(g, vp, up, i, j, k);
+                /* curvature terms of (v.grad)v in spherical components */
+                ar += -(ut * ut + up * up) / rr;
+                at += (ur * ut - up * up * cot) / rr;
+                ap += (ur * up + ut * up * cot) / rr;
+                double rho = g->rho[i * nt + j];
+                double jxb_r = J[1] * B[2] - J[2] * B[1];
+                double jxb_t = J[2] * B[0] - J[0] * B[2];
+                double jxb_p = J[0] * B[1] - J[1] * B[0];
+                double s = rho * g->vol[i * nt + j] * dt;
+                b[c] = s * (-ar + jxb_r / rho);
+                b[N + c] = s * (-at + jxb_t / rho);
+                b[2 * N + c] = s * (-ap + jxb_p / rho);
+            }
+    edges_free(e);
+}
+
+/* ---------------------------------------------------------------------------------------------
+ * Electric field on edges (Eq. 1 in B form: dB/dt = -curl E, E = -v x B + eta J; reading R5).
+ * E at cell centres, averaged to each edge over the cells sharing it; the polar radial edge
+ * takes the mean of the whole polar ring (k = 0..np-1 in order); tangential E = 0 on r0
+ * (line-tied); at r1 the mean of the two interior cells.
+ * ------------------------------------------------------------------------------------------- */
+void og_efield_edges(const og_grid* g, const double* vbar, const double* br, const double* bt,
+                     const double* bp, double eta, double* er, double* et, double* ep) {
+    int nr = g->nr, nt = g->nt, np = g->np;
+    long long N = g->N;
+    double* ec = (double*)malloc(sizeof(double) * 3 * N);
+    double* jc = NULL;
+    if (eta != 0.0) {
+        jc = (double*)malloc(sizeof(double) * 3 * N);
+        og_current_centre(g, br, bt, bp, jc);
+    }
+    for (int i = 0; i < nr; i++)
+        for (int j = 0; j < nt; j++)
+            for (int k = 0; k < np; k++) {
+                long long c = IDX(g, i, j, k);
+                double B[3];
+                bcentre_at(g, br, bt, bp, i, j, k, B);
+                double ur = vbar[c], ut = vbar[N + c], up = vbar[2 * N + c];
+                double vxb_r = ut * B[2] - up * B[1];
+                double vxb_t = up * B[0] - ur * B[2];
+                double vxb_p = ur * B[1] - ut * B[0];
+                ec[c] = -vxb_r;
+                ec[N + c] = -vxb_t;
+                ec[2 * N + c] = -vxb_p;
+                if (jc) {
+                    ec[c] += eta * jc[c];
+                    ec[N + c] += eta * jc[N + c];
+                    ec[2 * N + c] += eta * jc[2 * N + c];
+                }
+            }
+    const double* Er = ec;
+    const double* Et = ec + N;
+    const double* Ep = ec + 2 * N;
+    /* radial edges */
+    for (int i = 0; i < nr; i++) {
+        double sn = 0.0, ss = 0.0;
+        for (int k = 0; k < np; k++) { sn += Er[IDX(g, i, 0, k)]; ss += Er[IDX(g, i, nt - 1, k)]; }
+        for (int k = 0; k < np; k++) { er[IDXT(g, i, 0, k)] = sn / np; er[IDXT(g, i, nt, k)] = ss / np; }
+        for (int j = 1; j < nt; j++)
+            for (int k = 0; k < np; k++) {
+                int km = KM(g, k);
+                er[IDXT(g, i, j, k)] = 0.25 * (Er[IDX(g, i, j - 1, km)] + Er[IDX(g, i, j - 1, k)] +
+                                               Er[IDX(g, i, j, km)] + Er[IDX(g, i, j, k)]);
+            }
+    }
+    /* theta edges */
+    for (int i = 0; i <= nr; i++)
+        for (int j = 0; j < nt; j++)
+            for (int k = 0; k < np; k++) {
+                int km = KM(g, k);
+                double val;
+                if (i == 0) val = 0.0;
+                else if (i == nr) val = 0.5 * (Et[IDX(g, nr - 1, j, km)] + Et[IDX(g, nr - 1, j, k)]);
+                else val = 0.25 * (Et[IDX(g, i - 1, j, km)] + Et[IDX(g, i - 1, j, k)] +
+                                   Et[IDX(g, i, j, km)] + Et[IDX(g, i, j, k)]);
+                et[IDX(g, i, j, k)] = val;
+            }
+    /* phi edges */
+    for (int i = 0; i <= nr; i++)
+        for (int j = 0; j <= nt; j++)
+            for (int k = 0; k < np; k++) {
+                double val;
+                if (j == 0 || j == nt || i == 0) val = 0.0;
+                else if (i == nr) val = 0.5 * (Ep[IDX(g, nr - 1, j - 1, k)] + Ep[IDX(g, nr - 1, j, k)]);
+                else val = 0.25 * (Ep[IDX(g, i - 1, j - 1, k)] + Ep[IDX(g, i - 1, j, k)] +
+                                   Ep[IDX(g, i, j - 1, k)] + Ep[IDX(g, i, j, k)]);
+                ep[IDXT(g, i, j, k)] = val;
+            }
+    free(ec);
+    free(jc);
+}
+
+/* ---------------------------------------------------------------------------------------------
+ * Constrained-transport update (reading R5): each face flux changes by -dt times the
+ * circulation of E around the face (Stokes), divided by the face area. Polar theta faces have
+ * zero area and stay 0.
+ * ------------------------------------------------------------------------------------------- */
+void og_ct(const og_grid* g, const double* er, const double* et, const double* ep, double dt,
+           double* br, double* bt, double* bp) {
+    int nr = g->nr, nt = g->nt, np = g->np;
+    double dth = g->dth, dph = g->dph;
+    /* radial faces (i, j, k), i = 0..nr */
+    for (int i = 0; i <= nr; i++) {
+        double ri = g->r[i];
+        double lt = ri * dth;
+        for (int j = 0; j < nt; j++) {
+            double area = ri * ri * (g->cn[j] - g->cn[j + 1]) * dph;
+            double lpj = ri * g->sn[j] * dph, lpj1 = ri * g->sn[j + 1] * dph;
+            for (int k = 0; k < np; k++) {
+                double c = et[IDX(g, i, j, k)] * lt + ep[IDXT(g, i, j + 1, k)] * lpj1
+                         - et[IDX(g, i, j, KP(g, k))] * lt - ep[IDXT(g, i, j, k)] * lpj;
+                br[IDX(g, i, j, k)] -= dt * c / area;
+            }
+        }
+    }
+    /* theta faces (i, j, k), interior j */
+    for (int i = 0; i < nr; i++) {
+        double ri = g->r[i], ro = g->r[i + 1];
+        double lr = ro - ri;
+        for (int j = 1; j < nt; j++) {
+            double area = g->sn[j] * 0.5 * (ro * ro - ri * ri) * dph;
+            double lpi = ri * g->sn[j] * dph, lpo = ro * g->sn[j] * dph;
+            for (int k = 0; k < np; k++) {
+                double c = ep[IDXT(g, i, j, k)] * lpi + er[IDXT(g, i, j, KP(g, k))] * lr
+                         - ep[IDXT(g, i + 1, j, k)] * lpo - er[IDXT(g, i, j, k)] * lr;
+                bt[IDXT(g, i, j, k)] -= dt * c / area;
+            }
+        }
+    }
+    /* phi faces (i, j, k) */
+    for (int i = 0; i < nr; i++) {
+        double ri = g->r[i], ro = g->r[i + 1];
+        double lr = ro - ri;
+        double area = 0.5 * (ro * ro - ri * ri) * dth;
+        for (int j = 0; j < nt; j++)
+            for (int k = 0; k < np; k++) {
+                double c = er[IDXT(g, i, j, k)] * lr + et[IDX(g, i + 1, j, k)] * ro * dth
+                         - er[IDXT(g, i, j + 1, k)] * lr - et[IDX(g, i, j, k)] * ri * dth;
+                bp[IDX(g, i, j, k)] -= dt * c / area;
+            }
+    }
+}
+
+void og_divb(const og_grid* g, const double* br, const double* bt, const double* bp, double* div) {
+    int nr = g->nr, nt = g->nt, np = g->np;
+    for (int i = 0; i < nr; i++) {
+        double ri = g->r[i], ro = g->r[i + 1];
+        double ring = 0.5 * (ro * ro - ri * ri);
+        for (int j = 0; j < nt; j++) {
+            double band = g->cn[j] - g->cn[j + 1];
+            double ari = ri * ri * band * g->dph, aro = ro * ro * band * g->dph;
+            double atj = g->sn[j] * ring * g->dph, atj1 = g->sn[j + 1] * ring * g->dph;
+            double ap = ring * g->dth;
+            for (int k = 0; k < np; k++)
+                div[IDX(g, i, j, k)] = br[IDX(g, i + 1, j, k)] * aro - br[IDX(g, i, j, k)] * ari
+                                     + bt[IDXT(g, i, j + 1, k)] * atj1 - bt[IDXT(g, i, j, k)] * atj
+                                     + bp[IDX(g, i, j, KP(g, k))] * ap - bp[IDX(g, i, j, k)] * ap;
+        }
+    }
+}
+
+/* ---------------------------------------------------------------------------------------------
+ * Step coefficients (Sec. 2.1: S = (dt^2 k~^2)^-1 (C_w^2/(1-C_f)^2 - 1), k~^2 the upper limit
+ * of the combined inverse grid spacing). Reading R3: dt = cfl / max_c k~_c |v_c| (clipped to
+ * dt_max, or fixed); C_f = dt max k~|v|, C_w = dt max k~ |B_c| / sqrt(rho_c);
+ * alpha_SI = max(C_w^2/(1-C_f)^2 - 1, 0) / max k~^2 (the dt^2 of the printed S cancels against
+ * the time discretisation of d v / dt); alpha_nu = nu dt.
+ * ------------------------------------------------------------------------------------------- */
+int og_coeffs(const og_grid* g, double nu, double cfl, double dt_fixed, double dt_max,
+              double asi_fixed, const double* v, const double* br, const double* bt,
+              const double* bp, double* out) {
+    long long N = g->N;
+    int nt = g->nt;
+    double mkv = 0.0, mka = 0.0, mk2 = 0.0;
+    for (int i = 0; i < g->nr; i++)
+        for (int j = 0; j < nt; j++) {
+            double kt2 = g->kt2[i * nt + j];
+            double kt = sqrt(kt2);
+            if (kt2 > mk2) mk2 = kt2;
+            for (int k = 0; k < g->np; k++) {
+                long long c = IDX(g, i, j, k);
+                double vv = sqrt(v[c] * v[c] + v[N + c] * v[N + c] + v[2 * N + c] * v[2 * N + c]);
+                double B[3];
+                bcentre_at(g, br, bt, bp, i, j, k, B);
+                double bb = sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+                double a = kt * vv;
+                double w = kt * bb / sqrt(g->rho[i * nt + j]);
+                if (a > mkv) mkv = a;
+                if (w > mka) mka = w;
+            }
+        }
+    double dt;
+    if (dt_fixed > 0.0) dt = dt_fixed;
+    else {
+        if (mkv > 0.0) dt = cfl / mkv;
+        else if (dt_max > 0.0) dt = dt_max;
+        else return OG_ERR_ARG;
+        if (dt_max > 0.0 && dt > dt_max) dt = dt_max;
+    }
+    double cf = dt * mkv, cw = dt * mka;
+    if (!(cf < 1.0)) return OG_ERR_ARG;
+    double X = cw * cw / ((1.0 - cf) * (1.0 - cf)) - 1.0;
+    double asi = (X > 0.0) ? X / mk2 : 0.0;
+    if (asi_fixed >= 0.0) asi = asi_fixed;
+    out[0] = dt; out[1] = cf; out[2] = cw; out[3] = asi; out[4] = nu * dt;
+    return OG_OK;
+}
+
+/* ---------------------------------------------------------------------------------------------
+ * One zero-beta step (Sec. 2.2: explicit predictor-corrector upwinding for the advective and
+ * reactive terms; the semi-implicit term inside the predictor-corrector with two PCG solves;
+ * viscosity by a third PCG solve). Reading R6:
+ *   1. dt, alpha_SI, alpha_nu from (v^n, B^n)
+ *   2. predictor: M_SI d_p = rho V dt F(v^n, B^n), x0 = 0; v_p = v^n + d_p
+ *   3. B^{n+1} = B^n - dt curl_h E(v_bar, B^n), v_bar = (v^n + v_p)/2
+ *   4. corrector: M_SI d_c = rho V dt (F(v^n,B^n) + F(v_p,B^{n+1}))/2, x0 = d_p; v** = v^n + d_c
+ *   5. viscosity: M_nu v^{n+1} = rho V v**, x0 = v**
+ * ------------------------------------------------------------------------------------------- */
+int og_step(const og_grid* g, double nu, double eta, double cfl, double dt_fixed, double dt_max,
+            double asi_fixed, double tol, int max_iter, double* v, double* br, double* bt,
+            double* bp, double* info) {
+    long long N = g->N, n3 = 3 * N;
+    int nt = g->nt, np = g->np;
+    double co[5];
+    int st = og_coeffs(g, nu, cfl, dt_fixed, dt_max, asi_fixed, v, br, bt, bp, co);
+    if (st != OG_OK) return st;
+    double dt = co[0], asi = co[3], anu = co[4];
+    double* b0 = (double*)malloc(sizeof(double) * n3);
+    double* b1 = (double*)malloc(sizeof(double) * n3);
+    double* dlt = (double*)calloc(n3, sizeof(double));
+    double* vp = (double*)malloc(sizeof(double) * n3);
+    double* vb = (double*)malloc(sizeof(double) * n3);
+    edges3 e = edges_alloc(g);
+    int it[3] = {0, 0, 0};
+    double rr[3] = {0, 0, 0};
+    int status = OG_OK, s;
+
+    og_force(g, v, br, bt, bp, dt, b0);
+    s = og_pcg(g, asi, 3, b0, dlt, tol, max_iter, 0, &it[0], &rr[0]);
+    if (s != OG_OK) status = s;
+    for (long long e2 = 0; e2 < n3; e2++) vp[e2] = v[e2] + dlt[e2];
+    for (long long e2 = 0; e2 < n3; e2++) vb[e2] = 0.5 * (v[e2] + vp[e2]);
+    og_efield_edges(g, vb, br, bt, bp, eta, e.jr, e.jt, e.jp);
+    og_ct(g, e.jr, e.jt, e.jp, dt, br, bt, bp);
+    og_force(g, vp, br, bt, bp, dt, b1);
+    for (long long e2 = 0; e2 < n3; e2++) b1[e2] = 0.5 * (b0[e2] + b1[e2]);
+    s = og_pcg(g, asi, 3, b1, dlt, tol, max_iter, 0, &it[1], &rr[1]);
+    if (s != OG_OK) status = s;
+    for (long long e2 = 0; e2 < n3; e2++) v[e2] = v[e2] + dlt[e2];          /* v** */
+    for (int c = 0; c < 3; c++)
+        for (long long q = 0; q < N; q++) {
+            long long ij = q / np;
+            b0[c * N + q] = g->rho[ij] * g->vol[ij] * v[c * N + q];
+        }
+    (void)nt;
+    s = og_pcg(g, anu, 3, b0, v, tol, max_iter, 0, &it[2], &rr[2]);
+    if (s != OG_OK) status = s;
+    if (info) {
+        for (int q = 0; q < 5; q++) info[q] = co[q];
+        for (int q = 0; q < 3; q++) { info[5 + q] = it[q]; info[8 + q] = rr[q]; }
+    }
+    free(b0); free(b1); free(dlt); free(vp); free(vb);
+    edges_free(e);
+    return status;
+}

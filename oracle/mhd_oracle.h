@@ -1,0 +1,82 @@
+/*
+ * Plain FP64 CPU oracle for the zero-beta MHD time step of Caplan et al. (arXiv 1811.02605).
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the test suite, the smoke check and the benchmark's CPU
+ * baseline load this library. The CUDA library shares no code, header, table or constant with
+ * it; both sides take their inputs from the seeded generator in the package's inputs module.
+ *
+ * Everything is double precision, single threaded, written in the order of the definitions
+ * it restates (Sec. 2.1 Eq. 1 for the model, Sec. 2.2 for the scheme family and the PCG
+ * solver with the point-Jacobi preconditioner PC1). Where the paper is silent the readings are
+ * stated beside each function. Compiled with -ffp-contract=off so no multiply-add is fused.
+ *
+ * Layouts (phi fastest, C order). N = nr*nt*np cells.
+ *   vectors      v[c][i][j][k], c = 0 (r), 1 (theta), 2 (phi)
+ *   br [nr+1][nt][np]  bt [nr][nt+1][np]  bp [nr][nt][np]          faces
+ *   er [nr][nt+1][np]  et [nr+1][nt][np]  ep [nr+1][nt+1][np]      edges (E and J)
+ */
+#ifndef MHD_ORACLE_H
+#define MHD_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct og_grid og_grid;
+
+enum { OG_OK = 0, OG_ERR_ARG = 1, OG_ERR_NOCONV = 3 };
+
+og_grid* og_create(int nr, int nt, int np, double r0, double r1, double stretch);
+void og_destroy(og_grid* g);
+
+/* geometry tables exported for tests: r nodes (nr+1), cell volume (nr*nt), k~^2 (nr*nt) */
+void og_radial_nodes(const og_grid* g, double* r);
+void og_volumes(const og_grid* g, double* vol);
+void og_ktilde2(const og_grid* g, double* kt2);
+
+/* q = M_alpha p for ncomp stacked components (Sec. 2.2: the implicit operators are sparse
+ * symmetric stencils). M_alpha = D + alpha K, D = rho_c V_c. */
+void og_apply_M(const og_grid* g, double alpha, int ncomp, const double* p, double* q);
+/* same with the Dirichlet term and D switched off: the pure-Neumann stiffness K (tests) */
+void og_apply_K_neumann(const og_grid* g, int ncomp, const double* p, double* q);
+/* diagonal of M_alpha per (i,j) row, nr*nt entries */
+void og_diag(const og_grid* g, double alpha, double* d);
+
+/* point-Jacobi PCG (PC1). x holds x0 on entry. fixed_iters > 0 runs exactly that many
+ * iterations. Returns OG_OK or OG_ERR_NOCONV. */
+int og_pcg(const og_grid* g, double alpha, int ncomp, const double* b, double* x, double tol,
+           int max_iter, int fixed_iters, int* iters, double* relres);
+
+/* step coefficients: out = {dt, C_f, C_w, alpha_SI, alpha_nu} */
+int og_coeffs(const og_grid* g, double nu, double cfl, double dt_fixed, double dt_max,
+              double asi_fixed, const double* v, const double* br, const double* bt, const double* bp,
+              double* out);
+
+void og_bcentre(const og_grid* g, const double* br, const double* bt, const double* bp,
+                double* bc);
+void og_current_edges(const og_grid* g, const double* br, const double* bt, const double* bp,
+                      double* jr, double* jt, double* jp);
+void og_current_centre(const og_grid* g, const double* br, const double* bt, const double* bp,
+                       double* jc);
+/* b = rho_c V_c dt F(v, B) */
+void og_force(const og_grid* g, const double* v, const double* br, const double* bt,
+              const double* bp, double dt, double* b);
+void og_efield_edges(const og_grid* g, const double* vbar, const double* br, const double* bt,
+                     const double* bp, double eta, double* er, double* et, double* ep);
+/* B <- B - dt * curl_h E */
+void og_ct(const og_grid* g, const double* er, const double* et, const double* ep, double dt,
+           double* br, double* bt, double* bp);
+/* discrete divergence (net outward flux) per cell, N entries */
+void og_divb(const og_grid* g, const double* br, const double* bt, const double* bp, double* div);
+
+/* one predictor-corrector step, in place. dt_fixed > 0 bypasses the CFL rule; asi_fixed >= 0
+ * replaces the computed alpha_SI (frozen map for finite differences). info = {dt, cf, cw, asi, anu, it0, it1, it2,
+ * rr0, rr1, rr2} (11 doubles) */
+int og_step(const og_grid* g, double nu, double eta, double cfl, double dt_fixed, double dt_max,
+            double asi_fixed, double tol, int max_iter, double* v, double* br, double* bt,
+            double* bp, double* info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
