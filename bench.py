@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Benchmark: ms per zero-beta MHD step at 256x256x512 (FP64, with the FP32-inner / FP64
+refinement form beside it) and PCG bandwidth against the HBM roofline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one full predictor-corrector step (coefficients, two momentum-force passes, two
+semi-implicit PCG solves, the constrained-transport induction and the viscous PCG solve) on the
+synthetic flux-rope workload (seeded dipole + 5-mode perturbation + twisted flux rope, seeded
+5-mode velocity). Every input vector is 268-805 MB, larger than the 129 MB L2, so no L2 flush is
+needed between steps. Kernel durations come from CUDA events recorded on the grid's stream
+around each launch inside the timed region.
+
+With N > 1 (torchrun) every rank runs an independent replica of the workload on its own GPU;
+the step has no data-path exchange between replicas. --impl reference times the CPU oracle
+(plain C, one thread) on a bounded sample of the same workload and prints the same JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "fluxrope_256x256x512"
+METRIC = "ms/zero-beta step, PCG HBM GB/s (% peak) at 256x256x512: FP64 vs mixed"
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070  # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz = 1.259 TFLOP/s
+# algorithmic work of one scaled CG iteration per cell (3 components), see the design doc:
+#   bytes: x, r, p read + written once each = 6 passes x 3 x 8 B (FP64), x 4 B (FP32)
+#   FP64 flops of the SpMV kernel: 6 multiply-adds + 1 add per component + 1 dot FMA = 27 flops
+SPMV_FLOPS_PER_CELL = 3 * (2 * 6 + 1 + 2)
+PCG_BYTES_PER_CELL = {"fp64": 6 * 3 * 8, "fp32": 6 * 3 * 4}
+SPMV_BYTES_PER_CELL = {"fp64": 2 * 3 * 8, "fp32": 2 * 3 * 4}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.dev), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def gen_state(name):
+    from paper_1811_02605_gb300 import inputs as I
+    w, st = I.workload(name)
+    return w, st
+
+
+# ----------------------------------------------------------------------------------------------
+# reference arm and CPU baseline: the plain C oracle, one thread, bounded samples
+# ----------------------------------------------------------------------------------------------
+def oracle_sample(w, st, iters_per_step, pcg_iters=2):
+    """Time the oracle's explicit passes once and `pcg_iters` PCG iterations on the step's SI
+    system, and scale to one step with `iters_per_step` PCG iterations. Returns (ms, sample)."""
+    import numpy as np
+    import oracle as O
+    d = w["desc"]
+    g = O.Grid.from_desc(d)
+    v = np.stack([st["vr"], st["vt"], st["vp"]])
+    t0 = time.perf_counter()
+    c = g.coeffs(v, st["br"], st["bt"], st["bp"], nu=w["nu"], cfl=w["cfl"])
+    t1 = time.perf_counter()
+    b = g.force(v, st["br"], st["bt"], st["bp"], c["dt"])
+    t2 = time.perf_counter()
+    er, et, ep = g.efield_edges(v, st["br"], st["bt"], st["bp"], w["eta"])
+    g.ct(er, et, ep, c["dt"], st["br"], st["bt"], st["bp"])
+    t3 = time.perf_counter()
+    g.pcg(c["alpha_si"], b, fixed_iters=1)
+    t4 = time.perf_counter()
+    g.pcg(c["alpha_si"], b, fixed_iters=1 + pcg_iters)
+    t5 = time.perf_counter()
+    per_iter = (t5 - t4) / pcg_iters
+    setup = (t4 - t3) - per_iter  # residual, diagonal and one iteration
+    ms = 1e3 * ((t1 - t0) + 2 * (t2 - t1) + (t3 - t2) + 3 * setup + iters_per_step * per_iter)
+    sample = (f"oracle at {d.nr}x{d.nt}x{d.np}: one coefficient, force and induction pass and "
+              f"{pcg_iters + 2} PCG iterations timed ({t5 - t0:.1f} s), scaled to one step of "
+              f"{iters_per_step} PCG iterations (2 force passes, 3 solve set-ups)")
+    return ms, sample
+
+
+def oracle_iteration_counts(name):
+    """The oracle's own PCG iteration count for the first step of the workload (recorded by
+    tests/golden/make_golden.py), or None."""
+    p = os.path.join(ROOT, "tests", "golden", f"{name}_oracle_step1.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        rec = json.load(f)
+    return int(sum(rec["info"]["iters"]))
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        if rank != 0:
+            dist.barrier()
+            dist.destroy_process_group()
+            return
+    w, st = gen_state(args.workload)
+    iters = oracle_iteration_counts(args.workload) or args.ref_iters
+    vals = []
+    sample = ""
+    for s in range(args.warmup + args.steps):
+        ms, sample = oracle_sample(w, st, iters, pcg_iters=1)
+        if s >= args.warmup:
+            vals.append(ms)
+    value = sum(vals) / len(vals)
+    line = dict(impl="reference", metric=METRIC, value=round(value, 3), unit="ms/step", n_gpus=args.gpus,
+                steps=args.steps, warmup=args.warmup, ms_per_step=round(value, 3), higher_is_better=False,
+                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=args.workload, grid="256x256x512", precision="fp64",
+                            l2="inputs larger than L2"),
+                cpu_baseline=dict(value=round(value, 3), unit="ms/step", cores=1, kind="oracle", sample=sample),
+                e2e=dict(value=round(value, 3), unit="ms/step", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1811_02605_gb300 import build as B
+    B.build()
+    import paper_1811_02605_gb300 as P
+
+    w, st0 = gen_state(args.workload)
+    d = w["desc"]
+    N = d.nr * d.nt * d.np
+    stream = torch.cuda.Stream()
+    g = P.mhd_grid_create(d.nr, d.nt, d.np, d.r0, d.r1, d.stretch, stream)
+
+    def dev_state():
+        with torch.cuda.stream(stream):
+            return {k: torch.from_numpy(v).to("cuda", non_blocking=False) for k, v in st0.items()}
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def run(precision, steps, warmup, profile):
+        ds = dev_state()
+        torch.cuda.synchronize()
+        f = P.make_fields(ds["br"], ds["bt"], ds["bp"], ds["vr"], ds["vt"], ds["vp"])
+        prm = P.make_params(nu=w["nu"], eta=w["eta"], cfl=w["cfl"], tol=w["tol"], precision=precision,
+                            inner_tol=1e-5, max_outer=30)
+        for _ in range(warmup):
+            st, info = P.mhd_step(g, prm, f)
+            if st != P.MHD_OK:
+                raise RuntimeError(f"warm-up step failed: {P.STATUS_NAMES[st]} {P.mhd_last_error(g)}")
+        barrier()
+        P.mhd_profile_enable(g, profile)
+        infos = []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            barrier()
+            e0.record(stream)
+            for _ in range(steps):
+                st, info = P.mhd_step(g, prm, f)
+                if st != P.MHD_OK:
+                    raise RuntimeError(f"step failed: {P.STATUS_NAMES[st]} {P.mhd_last_error(g)}")
+                infos.append(info)
+            e1.record(stream)
+            barrier()
+        ms = e0.elapsed_time(e1) / steps
+        prof = P.mhd_profile_read(g)
+        P.mhd_profile_enable(g, False)
+        return ms, infos, prof, clk.summary(), ds
+
+    def maxr(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    hbm, peak_src = peaks()
+    # ---- FP64 (headline)
+    ms64, infos64, prof64, clk64, ds64 = run(P.PREC_FP64, args.steps, args.warmup, True)
+    ms64 = maxr(ms64)
+    it64 = sum(sum(i["iters"]) for i in infos64) / len(infos64)
+    spmv_ms, spmv_n = prof64["spmv64"]
+    pcg64_ms = sum(prof64[k][0] for k in ("pupdate64", "spmv64", "update64"))
+    pcg64_n = prof64["spmv64"][1]
+    spmv_avg = spmv_ms / max(spmv_n, 1)
+    spmv_tflops = SPMV_FLOPS_PER_CELL * N / (spmv_avg * 1e-3) / 1e12
+    pcg64_gbs = PCG_BYTES_PER_CELL["fp64"] * N * pcg64_n / (pcg64_ms * 1e-3) / 1e9
+    roof = dict(bound="alu", achieved=round(spmv_tflops, 4), peak=round(FP64_PEAK_TFLOPS / 1e3, 4),
+                unit="TFLOP/s", frac=round(spmv_tflops / (FP64_PEAK_TFLOPS / 1e3), 4), traffic=None,
+                kernel="k_spmv_dot<double,2>", avg_launch_ms=round(spmv_avg, 4),
+                peak_source="2 DFMA/clk/SM x 152 SMs x 2.07 GHz (nominal FP64 rate of the part)")
+    # ---- mixed (FP32 inner PCG, FP64 refinement)
+    mixed = None
+    if not args.no_mixed:
+        msm, infosm, profm, clkm, dsm = run(P.PREC_MIXED, args.steps, args.warmup, True)
+        msm = maxr(msm)
+        pcg32_ms = sum(profm[k][0] for k in ("pupdate32", "spmv32", "update32"))
+        pcg32_n = profm["spmv32"][1]
+        pcg32_gbs = PCG_BYTES_PER_CELL["fp32"] * N * pcg32_n / (pcg32_ms * 1e-3) / 1e9
+        sp32_ms, sp32_n = profm["spmv32"]
+        sp32_avg = sp32_ms / max(sp32_n, 1)
+        sp32_gbs = SPMV_BYTES_PER_CELL["fp32"] * N / (sp32_avg * 1e-3) / 1e9
+        err = {k: float(torch.linalg.norm(dsm[k] - ds64[k]) / torch.linalg.norm(ds64[k])) for k in ds64}
+        mixed = dict(ms_per_step=round(msm, 3), speedup_vs_fp64=round(ms64 / msm, 3),
+                     pcg_iters_per_step=sum(sum(i["iters"]) for i in infosm) / len(infosm),
+                     outer_per_step=sum(sum(i["outer"]) for i in infosm) / len(infosm),
+                     max_relres=max(max(i["relres"]) for i in infosm),
+                     pcg_gbs=round(pcg32_gbs, 1), pcg_frac_of_hbm=round(pcg32_gbs / hbm, 4),
+                     spmv32=dict(bound="hbm", achieved=round(sp32_gbs, 1), peak=hbm, unit="GB/s",
+                                 frac=round(sp32_gbs / hbm, 4), avg_launch_ms=round(sp32_avg, 4)),
+                     rel_l2_vs_fp64_gpu_after_steps=err, clocks=clkm,
+                     kernel_ms={k: round(v[0], 3) for k, v in profm.items() if v[1]})
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        ds = dev_state()
+        host = {k: torch.from_numpy(v).pin_memory() for k, v in st0.items()}
+        f = P.make_fields(ds["br"], ds["bt"], ds["bp"], ds["vr"], ds["vt"], ds["vp"])
+        prm = P.make_params(nu=w["nu"], eta=w["eta"], cfl=w["cfl"], tol=w["tol"])
+        ke = max(1, min(args.steps, 2))
+        h2d = sum(t.numel() * 8 for t in host.values())
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(ke):
+            with torch.cuda.stream(stream):
+                for k in ds:
+                    ds[k].copy_(host[k], non_blocking=True)
+            P.mhd_step(g, prm, f)
+            with torch.cuda.stream(stream):
+                for k in ds:
+                    host[k].copy_(ds[k], non_blocking=True)
+            stream.synchronize()
+        e1.record(stream)
+        barrier()
+        e2e = dict(value=round(maxr(e0.elapsed_time(e1) / ke), 3), unit="ms/step", h2d_bytes_per_step=h2d,
+                   d2h_bytes_per_step=h2d)
+    # ---- CPU baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        iters = int(round(it64))
+        ms_cpu, sample = oracle_sample(w, st0, iters, pcg_iters=2)
+        cpu = dict(value=round(ms_cpu, 1), unit="ms/step", cores=1, kind="oracle", sample=sample)
+    launches = sum(v[1] for v in prof64.values())
+    if rank == 0:
+        line = dict(metric=METRIC, value=round(ms64, 3), unit="ms/step", n_gpus=ws, steps=args.steps,
+                    warmup=args.warmup, ms_per_step=round(ms64, 3), higher_is_better=False, scaling="weak",
+                    vs_baseline=None, dtype="f64", data="synthetic",
+                    config=dict(workload=args.workload, grid=f"{d.nr}x{d.nt}x{d.np}", precision="fp64",
+                                parallelism=("replicas" if ws > 1 else "single"),
+                                l2="inputs larger than L2 (no flush)",
+                                pcg_iters_per_step=it64,
+                                dt=[i["dt"] for i in infos64]),
+                    pcg_gbs=dict(fp64=round(pcg64_gbs, 1), fp64_frac_of_hbm=round(pcg64_gbs / hbm, 4),
+                                 peak_gbs=hbm, peak_source=peak_src),
+                    roofline=roof, mixed=mixed, e2e=e2e, cpu_baseline=cpu, clocks=clk64,
+                    gpu_launches=int(launches), kernel_ms={k: round(v[0], 3) for k, v in prof64.items() if v[1]})
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-iters", type=int, default=1000,
+                    help="PCG iterations per step assumed by the reference arm if no oracle record exists")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

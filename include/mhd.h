@@ -1,0 +1,205 @@
+/*
+ * mhd.h -- C ABI of a GB300-native (sm_103a) library for the zero-beta MHD time step of
+ * Caplan et al., "GPU Acceleration of an Established Solar MHD Code using OpenACC"
+ * (arXiv 1811.02605).
+ *
+ * The model (Sec. 2.1, Eq. 1): magnetic field B = curl A advanced by dA/dt = v x curl A -
+ * eta curl curl A (code units: c = 4 pi = 1), velocity advanced by
+ *   dv/dt = -v.grad v + (J x B)/rho + (1/rho) div(nu rho grad v) + (1/rho) div(S rho grad dv/dt),
+ * density frozen (rho = rho0(r) = (r0/r)^2), pressure zero. The scheme (Sec. 2.2): explicit
+ * predictor-corrector upwinding for the advective and reactive terms, the semi-implicit (SI)
+ * term solved implicitly inside the predictor-corrector with two preconditioned conjugate
+ * gradient (PCG) solves, and viscosity by a third PCG solve, all with the point-Jacobi
+ * preconditioner (PC1). Grid (Sec. 2.2: a staggered, logically rectangular, non-uniform mesh):
+ * spherical shell r in [r0, r1] with geometric radial stretch, theta in [0, pi] uniform,
+ * phi periodic; B on faces, E and J on edges, v at cell centres.
+ *
+ * Conventions common to every call:
+ *  - All field and vector pointers are DEVICE pointers to caller-owned, contiguous float64
+ *    arrays, phi fastest (C order), 16-byte aligned. The library never frees them.
+ *  - N = nr*nt*np cells. Array shapes:
+ *      br [nr+1][nt][np]  radial faces at r_i
+ *      bt [nr][nt+1][np]  theta faces at theta_j; j = 0 and j = nt are the poles, held at 0
+ *      bp [nr][nt][np]    phi faces at phi_k
+ *      vr, vt, vp [nr][nt][np] cell centres; "stacked" vectors hold ncomp such blocks back
+ *      to back ([ncomp][nr][nt][np]).
+ *  - A grid owns its metric tables and all workspace. It allocates only in mhd_grid_create
+ *    (and in a solver's first call at a new size for batched solves); mhd_step, pcg_solve and
+ *    the other calls allocate nothing.
+ *  - All work is enqueued on the grid's CUDA stream. Calls that return scalars (step info,
+ *    iteration counts) synchronise that stream once at their end; the others return after
+ *    enqueueing.
+ *  - Status codes only: nothing throws or aborts across the ABI. After an error,
+ *    mhd_last_error(grid) describes it. On MHD_ERR_NOCONV the best iterate is left in x.
+ *  - One grid per stream; a grid is not thread-safe.
+ *  - np must be even (double2 loads along phi); nt >= 2, nr >= 2.
+ */
+#ifndef MHD_H
+#define MHD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mhd_grid_s* mhd_grid_t; /* opaque, library-owned */
+
+typedef enum {
+    MHD_OK = 0,
+    MHD_ERR_ARG = 1,       /* invalid argument (sizes, pointers, parameters) */
+    MHD_ERR_CUDA = 2,      /* a CUDA runtime call failed */
+    MHD_ERR_NOCONV = 3,    /* PCG reached max_iter (or max_outer) before the tolerance */
+    MHD_ERR_NONFINITE = 4, /* NaN or Inf met in a reduction */
+    MHD_ERR_TIMEOUT = 5,   /* a bounded device-side wait gave up (batched persistent solver) */
+    MHD_ERR_OOM = 6        /* device allocation failed */
+} mhd_status_t;
+
+/* Grid: nr x nt x np cells. Radial nodes r_0 = r0, r_{i+1} = r_i + h0 s^i with
+ * h0 = (r1 - r0)(s - 1)/(s^nr - 1) (s = stretch, uniform if s == 1). theta_j = j pi/nt,
+ * phi_k = 2 pi k/np. (Sec. 3: the production run refines the grid strongly near the erupting
+ * region and coarsens it with distance; the geometric stretch stands in for that.) */
+typedef struct {
+    int nr, nt, np;
+    double r0, r1, stretch;
+} mhd_grid_desc_t;
+
+enum { MHD_PREC_FP64 = 0, MHD_PREC_MIXED = 1 };
+
+/* Step and solver parameters.
+ *  nu        kinematic viscosity (Eq. 1), code units
+ *  eta       resistivity (Eq. 1); explicit in E = -v x B + eta J
+ *  cfl       flow CFL number C_f: dt = cfl / max_c(k~_c |v_c|)
+ *  dt_fixed  > 0: use this dt instead of the CFL rule
+ *  dt_max    > 0: upper bound on the CFL dt
+ *  alpha_si_fixed >= 0: use this SI coefficient instead of the computed one (frozen map)
+ *  tol       relative residual ||b - M x||_2 / ||b||_2 at which PCG stops (Sec. 2.2)
+ *  inner_tol mixed precision only: FP32 inner solves stop at inner_tol times the outer residual
+ *  max_iter  PCG iteration cap per solve (inner iterations in mixed precision)
+ *  max_outer mixed precision: cap on FP64 iterative-refinement passes
+ *  precision MHD_PREC_FP64 or MHD_PREC_MIXED (FP32 stencil and inner PCG, FP64 residuals,
+ *            corrections and reductions) */
+typedef struct {
+    double nu, eta, cfl, dt_fixed, dt_max, alpha_si_fixed;
+    double tol, inner_tol;
+    int max_iter, max_outer;
+    int precision;
+} mhd_params_t;
+
+/* Caller-owned DEVICE pointers (layouts above). */
+typedef struct {
+    double *br, *bt, *bp, *vr, *vt, *vp;
+} mhd_fields_t;
+
+/* Per-step report. iters/outer/relres: [0] SI predictor, [1] SI corrector, [2] viscosity.
+ * relres is the final ||r||_2/||b||_2 (recursive residual in FP64 mode, true FP64 residual in
+ * mixed mode). */
+typedef struct {
+    double dt, cf, cw, alpha_si, alpha_nu;
+    int iters[3], outer[3];
+    double relres[3];
+} mhd_step_info_t;
+
+/* Create a grid on the CUDA stream `cuda_stream` (a cudaStream_t; NULL = legacy default
+ * stream) of the current device. Builds the metric tables (exact finite-volume geometry of
+ * spherical cells) and allocates all workspace for one 3-component solve in either precision.
+ * Errors: MHD_ERR_ARG (sizes, r1 <= r0, stretch <= 0, np odd), MHD_ERR_OOM, MHD_ERR_CUDA. */
+mhd_status_t mhd_grid_create(const mhd_grid_desc_t* desc, void* cuda_stream, mhd_grid_t* out);
+
+/* Free the grid's tables and workspace (synchronises its stream). NULL is accepted. */
+mhd_status_t mhd_grid_destroy(mhd_grid_t grid);
+
+/* Element counts of br, bt, bp, vr, vt, vp. */
+mhd_status_t mhd_grid_sizes(mhd_grid_t grid, long long sizes[6]);
+
+/* Step coefficients (Sec. 2.1 definition of S; Sec. 3: the time step varies from step to step):
+ * dt = cfl / max_c(k~_c |v_c|) (or dt_fixed; clipped to dt_max), C_f = dt max k~|v|,
+ * C_w = dt max k~ |B_c|/sqrt(rho_c), alpha_SI = max(C_w^2/(1-C_f)^2 - 1, 0)/max k~^2,
+ * alpha_nu = nu dt, where k~_c^2 = 1/dr^2 + 1/(r dtheta)^2 + 1/(r sin(theta) dphi)^2 at the cell
+ * centre. Fills info->dt, cf, cw, alpha_si, alpha_nu; synchronises. MHD_ERR_ARG if C_f >= 1 or
+ * no dt can be formed (v = 0 without dt_fixed or dt_max). */
+mhd_status_t mhd_step_coeffs(mhd_grid_t grid, const mhd_params_t* params,
+                             const mhd_fields_t* fields, mhd_step_info_t* info);
+
+/* One zero-beta predictor-corrector step, in place on `inout` (Sec. 2.2):
+ *   1. coefficients as in mhd_step_coeffs from (v^n, B^n)
+ *   2. predictor: M_SI d_p = rho V dt F(v^n, B^n), x0 = 0; v_p = v^n + d_p
+ *   3. B^{n+1} = B^n - dt curl_h E, E = -v_bar x B^n + eta J(B^n), v_bar = (v^n + v_p)/2,
+ *      averaged from cell centres to edges (constrained transport: div_h B is unchanged)
+ *   4. corrector: M_SI d_c = rho V dt (F(v^n,B^n) + F(v_p,B^{n+1}))/2, x0 = d_p; v** = v^n + d_c
+ *   5. viscosity: M_nu v^{n+1} = rho V v**, x0 = v**
+ * M_alpha = D + alpha K is the symmetric finite-volume form of rho - alpha div(rho grad .) per
+ * component (see mhd_apply_operator). `info` may be NULL. Returns the first non-OK status of the
+ * three solves (the step still completes), MHD_ERR_ARG for bad parameters. */
+mhd_status_t mhd_step(mhd_grid_t grid, const mhd_params_t* params, mhd_fields_t* inout,
+                      mhd_step_info_t* info);
+
+/* q = M_alpha p for ncomp (1..3) stacked components: the implicit viscous/SI operator
+ * (Eq. 1; Sec. 4.1: the implicit matrices are applied as stencils, never stored):
+ * (M_alpha u)_c = rho_c V_c u_c + alpha sum_faces w_f (u_c - u_nb), w_f = rho A_f / d_f,
+ * Dirichlet u = 0 at r0, Neumann at r1, no flux through the poles, periodic in phi.
+ * p and q: device, [ncomp][nr][nt][np]; must not overlap. Enqueued only. */
+mhd_status_t mhd_apply_operator(mhd_grid_t grid, double alpha, int ncomp, const double* p,
+                                double* q);
+
+/* b = rho_c V_c dt F(v, B) with F = -(v.grad)v + (J x B)/rho (Eq. 1), first-order upwind
+ * advection with spherical curvature terms, J = curl_h B on edges averaged to centres. v from
+ * fields->vr/vt/vp, B from fields->br/bt/bp. b: device [3][nr][nt][np]. Enqueued only. */
+mhd_status_t mhd_force(mhd_grid_t grid, const mhd_fields_t* fields, double dt, double* b);
+
+/* Constrained-transport induction (Eq. 1 in B form): B <- B - dt curl_h E with
+ * E = -vbar x B + eta J on edges. vbar: device [3][nr][nt][np]; B in fields->br/bt/bp updated
+ * in place (fields->v* ignored). Enqueued only. */
+mhd_status_t mhd_induction(mhd_grid_t grid, const double* vbar, double eta, double dt,
+                           mhd_fields_t* fields);
+
+/* Solve M_alpha x = b by PCG with the point-Jacobi preconditioner (Sec. 2.2 PC1), for ncomp
+ * (1..3) stacked components sharing one CG alpha/beta. x holds x0 on entry (NULL-free; pass
+ * zeros for a cold start) and the solution on exit. Stop: ||r||_2 <= tol ||b||_2 (recursive
+ * residual, tested before each iteration; FP64 mode) or on the true FP64 residual (mixed
+ * mode, FP32 inner solves to inner_tol). b = 0 gives x = 0 after 0 iterations.
+ * iters/outer/relres may be NULL. Synchronises. MHD_ERR_NOCONV at max_iter/max_outer,
+ * MHD_ERR_NONFINITE if a reduction is not finite. */
+mhd_status_t pcg_solve(mhd_grid_t grid, double alpha, int ncomp, const double* b, double* x,
+                       const mhd_params_t* params, int* iters, int* outer, double* relres);
+
+/* Batched FP64 PCG: n independent 3-component systems M_alpha[i] x[i] = b[i] on grids[i]
+ * (grids of different sizes allowed; all on the stream of grids[0]) in ONE persistent
+ * cooperative launch per CUDA-graph replay, with per-system scalars and bounded grid barriers.
+ * x[i] holds x0 on entry. iters/relres: host arrays of n (may be NULL). Returns MHD_ERR_NOCONV
+ * if any system missed the tolerance, MHD_ERR_TIMEOUT if a device barrier gave up. */
+mhd_status_t pcg_solve_batched(int n, const mhd_grid_t* grids, const double* alpha,
+                               const double* const* b, double* const* x,
+                               const mhd_params_t* params, int* iters, double* relres);
+
+/* Adjoint (reverse-mode derivative) of one mhd_step with dt frozen to `dt`, alpha_SI to
+ * params->alpha_si_fixed if >= 0 (else the value computed from state_n), alpha_nu = nu dt, and
+ * the upwind directions of the forward step. Given state_n and the cotangent adj_np1 =
+ * dL/d(state_{n+1}) (same layout as the fields), writes adj_n = dL/d(state_n). The step's
+ * intermediates are recomputed from state_n. PCG solves inside use params->tol. adj_n must not
+ * alias adj_np1 or state_n. Synchronises. */
+mhd_status_t mhd_adjoint_step(mhd_grid_t grid, const mhd_params_t* params,
+                              const mhd_fields_t* state_n, double dt,
+                              const mhd_fields_t* adj_np1, mhd_fields_t* adj_n);
+
+/* Diagnostics (not part of the method): device time of the library's kernels, measured with
+ * CUDA events recorded on the grid's stream immediately before and after each launch, summed
+ * per kernel while profiling is enabled. Enabling resets the counters and makes the PCG loop
+ * launch its kernels directly instead of replaying CUDA graphs (so each launch can be
+ * bracketed); results are otherwise identical. */
+enum {
+    MHD_KERNEL_PUPDATE64 = 0, MHD_KERNEL_SPMV64 = 1, MHD_KERNEL_UPDATE64 = 2,
+    MHD_KERNEL_PUPDATE32 = 3, MHD_KERNEL_SPMV32 = 4, MHD_KERNEL_UPDATE32 = 5,
+    MHD_KERNEL_OUTER_RES = 6, MHD_KERNEL_FORCE = 7, MHD_KERNEL_INDUCTION = 8,
+    MHD_KERNEL_COEFFS = 9, MHD_KERNEL_COUNT = 10
+};
+mhd_status_t mhd_profile_enable(mhd_grid_t grid, int enable);
+/* Total milliseconds and launch count of one kernel id since profiling was enabled.
+ * Synchronises the grid's stream. */
+mhd_status_t mhd_profile_read(mhd_grid_t grid, int kernel, double* total_ms, long long* launches);
+
+/* Text of the last error on this grid ("" if none); NULL grid gives the last create error. */
+const char* mhd_last_error(mhd_grid_t grid);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MHD_H */

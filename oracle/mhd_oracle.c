@@ -120,8 +120,8 @@ void og_volumes(const og_grid* g, double* v) { memcpy(v, g->vol, sizeof(double) 
 void og_ktilde2(const og_grid* g, double* k) { memcpy(k, g->kt2, sizeof(double) * g->nr * g->nt); }
 
 /* ---------------------------------------------------------------------------------------------
- * Implicit operator (Eq. 1, viscous and semi-implicit terms; Sec. 4.1 "sparse matrix-vector
- * products (essentially stencil operations)"). Reading R3: the operator (1/rho) div(rho grad u)
+ * Implicit operator (Eq. 1, viscous and semi-implicit terms; Sec. 4.1: sparse matrix-vector
+ * products that are stencil operations). Reading R3: the operator (1/rho) div(rho grad u)
  * acts on each spherical component separately; multiplied by the cell volume it becomes the
  * symmetric finite-volume form M_alpha = D + alpha K with D = rho_c V_c and
  * (K u)_c = sum over faces w_f (u_c - u_nb), Dirichlet u = 0 at r0, Neumann at r1.
@@ -169,7 +169,7 @@ void og_diag(const og_grid* g, double alpha, double* d) {
 }
 
 /* ---------------------------------------------------------------------------------------------
- * PCG with PC1 (Sec. 2.2: "the inverse diagonal of the matrix (point-Jacobi)"). Reading P12:
+ * PCG with PC1 (Sec. 2.2: preconditioning by the inverse of the matrix diagonal). Reading P12:
  * one stacked system for all components with one alpha and one beta; stop when the
  * recursively updated residual satisfies ||r||_2 <= tol ||b||_2, tested before each iteration;
  * the count is the number of x updates; b = 0 gives x = 0 after 0 iterations.

@@ -34,7 +34,7 @@ void og_radial_nodes(const og_grid* g, double* r);
 void og_volumes(const og_grid* g, double* vol);
 void og_ktilde2(const og_grid* g, double* kt2);
 
-/* q = M_alpha p for ncomp stacked components (Sec. 2.2: the implicit operators are sparse
+/* q = M_alpha p for ncomp stacked components (Sec. 4.1: the implicit operators are sparse
  * symmetric stencils). M_alpha = D + alpha K, D = rho_c V_c. */
 void og_apply_M(const og_grid* g, double alpha, int ncomp, const double* p, double* q);
 /* same with the Dirichlet term and D switched off: the pure-Neumann stiffness K (tests) */

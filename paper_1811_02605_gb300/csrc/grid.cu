@@ -1,0 +1,336 @@
+// Grid object: metric tables of the staggered spherical grid and all solver workspace.
+//
+// Geometry (exact finite-volume quantities of spherical cells on the staggered, logically
+// rectangular, non-uniform mesh of Sec. 2.2):
+//   V_ij   = (r_{i+1}^3 - r_i^3)/3 (cos th_j - cos th_{j+1}) dphi
+//   A^r_ij = r_i^2 (cos th_j - cos th_{j+1}) dphi
+//   A^t_ij = sin th_j (r_{i+1}^2 - r_i^2)/2 dphi        (zero at the poles)
+//   A^p_i  = (r_{i+1}^2 - r_i^2)/2 dtheta
+// Stiffness weights of K (rho A / centre distance): radial faces use rho0 at the face radius,
+// theta and phi faces rho at the cell-centre radius; the inner face carries the Dirichlet
+// weight rho0(r0) A^r_0j / (rc_0 - r0).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "mhd_internal.cuh"
+
+namespace mhd {
+
+static std::mutex g_err_mu;
+static std::string g_create_error;
+
+mhd_status_t set_error(mhd_grid_s* g, mhd_status_t st, const std::string& msg) {
+    if (g) g->last_error = msg;
+    else {
+        std::lock_guard<std::mutex> lk(g_err_mu);
+        g_create_error = msg;
+    }
+    return st;
+}
+
+mhd_status_t check_cuda(mhd_grid_s* g, const char* where) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return set_error(g, MHD_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+    return MHD_OK;
+}
+
+int grid_blocks(const mhd_grid_s* g, long long work, int per_sm) {
+    long long b = (work + kThreads - 1) / kThreads;
+    long long cap = (long long)g->num_sms * per_sm;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    if (b > kMaxBlocks) b = kMaxBlocks;
+    return (int)b;
+}
+
+int prof_begin(mhd_grid_s* g, cudaStream_t st, int kernel) {
+    if (!g->prof) return -1;
+    if (g->prof_nslot >= mhd_grid_s::kProfSlots) {
+        cudaStreamSynchronize(st);
+        prof_flush(g);
+    }
+    const int s = g->prof_nslot++;
+    g->prof_kid[s] = kernel;
+    cudaEventRecord(g->prof_ev[2 * s], st);
+    return s;
+}
+
+void prof_end(mhd_grid_s* g, cudaStream_t st, int slot) {
+    if (slot >= 0) cudaEventRecord(g->prof_ev[2 * slot + 1], st);
+}
+
+void prof_flush(mhd_grid_s* g) {
+    for (int s = 0; s < g->prof_nslot; s++) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, g->prof_ev[2 * s], g->prof_ev[2 * s + 1]) == cudaSuccess) {
+            g->prof_ms[g->prof_kid[s]] += ms;
+            g->prof_cnt[g->prof_kid[s]] += 1;
+        }
+    }
+    cudaGetLastError();
+    g->prof_nslot = 0;
+}
+
+}  // namespace mhd
+
+using namespace mhd;
+
+namespace {
+
+struct HostGeo {
+    std::vector<double> r, rc, sn, cn, sc, cc, rho, rhoV, kt2, wr, wt, wp;
+    double max_kt2 = 0;
+};
+
+HostGeo make_geo(const mhd_grid_desc_t& d) {
+    const int nr = d.nr, nt = d.nt, np = d.np;
+    const double pi = 3.14159265358979323846;
+    const double dth = pi / nt, dph = 2.0 * pi / np;
+    HostGeo h;
+    h.r.resize(nr + 1);
+    h.rc.resize(nr);
+    h.sn.resize(nt + 1);
+    h.cn.resize(nt + 1);
+    h.sc.resize(nt);
+    h.cc.resize(nt);
+    h.rho.resize(nr);
+    h.rhoV.resize((size_t)nr * nt);
+    h.kt2.resize((size_t)nr * nt);
+    h.wr.assign((size_t)(nr + 1) * nt, 0.0);
+    h.wt.assign((size_t)nr * (nt + 1), 0.0);
+    h.wp.assign((size_t)nr * nt, 0.0);
+    // radial nodes by repeated multiplication (identical bits on every host)
+    double h0;
+    if (d.stretch == 1.0) {
+        h0 = (d.r1 - d.r0) / nr;
+    } else {
+        double snr = 1.0;
+        for (int i = 0; i < nr; i++) snr *= d.stretch;
+        h0 = (d.r1 - d.r0) * (d.stretch - 1.0) / (snr - 1.0);
+    }
+    h.r[0] = d.r0;
+    double dr = h0;
+    for (int i = 0; i < nr; i++) {
+        h.r[i + 1] = h.r[i] + dr;
+        dr *= d.stretch;
+    }
+    for (int i = 0; i < nr; i++) h.rc[i] = 0.5 * (h.r[i] + h.r[i + 1]);
+    for (int j = 0; j <= nt; j++) {
+        h.sn[j] = std::sin(j * dth);
+        h.cn[j] = std::cos(j * dth);
+    }
+    h.sn[0] = 0.0;
+    h.sn[nt] = 0.0;
+    h.cn[0] = 1.0;
+    h.cn[nt] = -1.0;
+    for (int j = 0; j < nt; j++) {
+        h.sc[j] = std::sin((j + 0.5) * dth);
+        h.cc[j] = std::cos((j + 0.5) * dth);
+    }
+    auto rho0 = [&](double r) { return (d.r0 / r) * (d.r0 / r); };
+    for (int i = 0; i < nr; i++) {
+        const double ri = h.r[i], ro = h.r[i + 1];
+        const double ring = 0.5 * (ro * ro - ri * ri);
+        h.rho[i] = rho0(h.rc[i]);
+        for (int j = 0; j < nt; j++) {
+            const double band = h.cn[j] - h.cn[j + 1];
+            const double vol = (ro * ro * ro - ri * ri * ri) / 3.0 * band * dph;
+            h.rhoV[(size_t)i * nt + j] = h.rho[i] * vol;
+            const double a = ro - ri, b = h.rc[i] * dth, c = h.rc[i] * h.sc[j] * dph;
+            const double k2 = 1.0 / (a * a) + 1.0 / (b * b) + 1.0 / (c * c);
+            h.kt2[(size_t)i * nt + j] = k2;
+            if (k2 > h.max_kt2) h.max_kt2 = k2;
+            h.wp[(size_t)i * nt + j] = h.rho[i] * (ring * dth) / c;
+        }
+        for (int j = 1; j < nt; j++)
+            h.wt[(size_t)i * (nt + 1) + j] = h.rho[i] * (h.sn[j] * ring * dph) / (h.rc[i] * dth);
+    }
+    for (int j = 0; j < nt; j++) {
+        const double band = h.cn[j] - h.cn[j + 1];
+        h.wr[j] = rho0(d.r0) * (d.r0 * d.r0 * band * dph) / (h.rc[0] - d.r0);
+        for (int i = 1; i < nr; i++)
+            h.wr[(size_t)i * nt + j] =
+                rho0(h.r[i]) * (h.r[i] * h.r[i] * band * dph) / (h.rc[i] - h.rc[i - 1]);
+        h.wr[(size_t)nr * nt + j] = 0.0;
+    }
+    return h;
+}
+
+template <typename T>
+bool dalloc(T** p, size_t n, std::vector<void*>& owned) {
+    void* m = nullptr;
+    if (cudaMalloc(&m, n * sizeof(T) + 256) != cudaSuccess) return false;
+    owned.push_back(m);
+    *p = reinterpret_cast<T*>(m);
+    return true;
+}
+
+}  // namespace
+
+extern "C" mhd_status_t mhd_grid_create(const mhd_grid_desc_t* desc, void* cuda_stream,
+                                        mhd_grid_t* out) {
+    if (!desc || !out) return set_error(nullptr, MHD_ERR_ARG, "mhd_grid_create: null argument");
+    *out = nullptr;
+    const mhd_grid_desc_t d = *desc;
+    if (d.nr < 2 || d.nt < 2 || d.np < 2 || (d.np % 2) != 0)
+        return set_error(nullptr, MHD_ERR_ARG, "mhd_grid_create: need nr>=2, nt>=2, np even >= 2");
+    if (!(d.r0 > 0) || !(d.r1 > d.r0) || !(d.stretch > 0))
+        return set_error(nullptr, MHD_ERR_ARG, "mhd_grid_create: need 0 < r0 < r1, stretch > 0");
+    const long long N = (long long)d.nr * d.nt * d.np;
+    if (N > (1LL << 30)) return set_error(nullptr, MHD_ERR_ARG, "mhd_grid_create: grid too large");
+
+    mhd_grid_s* g = new mhd_grid_s();
+    g->d.nr = d.nr;
+    g->d.nt = d.nt;
+    g->d.np = d.np;
+    g->d.N = N;
+    g->desc = d;
+    g->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    cudaGetDevice(&g->device);
+    cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+    g->graph_batch = 16;
+    std::memset(g->iter_graph, 0, sizeof(g->iter_graph));
+
+    HostGeo h = make_geo(d);
+    g->max_kt2 = h.max_kt2;
+    std::vector<void*> owned;
+    const int nr = d.nr, nt = d.nt;
+    const size_t n3 = 3 * (size_t)N;
+    bool ok = true;
+    double *r, *rc, *sn, *cn, *sc, *cc, *rho, *rhoV, *kt2, *wr, *wt, *wp;
+    ok = ok && dalloc(&r, nr + 1, owned) && dalloc(&rc, nr, owned) && dalloc(&sn, nt + 1, owned) &&
+         dalloc(&cn, nt + 1, owned) && dalloc(&sc, nt, owned) && dalloc(&cc, nt, owned) &&
+         dalloc(&rho, nr, owned) && dalloc(&rhoV, (size_t)nr * nt, owned) &&
+         dalloc(&kt2, (size_t)nr * nt, owned) && dalloc(&wr, (size_t)(nr + 1) * nt, owned) &&
+         dalloc(&wt, (size_t)nr * (nt + 1), owned) && dalloc(&wp, (size_t)nr * nt, owned);
+    ok = ok && dalloc(&g->t64.ar, (size_t)(nr + 1) * nt, owned) &&
+         dalloc(&g->t64.at, (size_t)nr * (nt + 1), owned) && dalloc(&g->t64.ap, (size_t)nr * nt, owned) &&
+         dalloc(&g->t64.s, (size_t)nr * nt, owned);
+    ok = ok && dalloc(&g->t32.ar, (size_t)(nr + 1) * nt, owned) &&
+         dalloc(&g->t32.at, (size_t)nr * (nt + 1), owned) && dalloc(&g->t32.ap, (size_t)nr * nt, owned) &&
+         dalloc(&g->t32.s, (size_t)nr * nt, owned);
+    ok = ok && dalloc(&g->tu.dg, (size_t)nr * nt, owned) && dalloc(&g->tu.awr, (size_t)(nr + 1) * nt, owned) &&
+         dalloc(&g->tu.awt, (size_t)nr * (nt + 1), owned) && dalloc(&g->tu.awp, (size_t)nr * nt, owned);
+    ok = ok && dalloc(&g->x64, n3, owned) && dalloc(&g->r64, n3, owned) && dalloc(&g->p64, n3, owned) &&
+         dalloc(&g->q64, n3, owned);
+    ok = ok && dalloc(&g->x32, n3, owned) && dalloc(&g->r32, n3, owned) && dalloc(&g->p32, 2 * n3, owned) &&
+         dalloc(&g->q32, n3, owned);
+    ok = ok && dalloc(&g->b0, n3, owned) && dalloc(&g->b1, n3, owned) && dalloc(&g->dlt, n3, owned);
+    ok = ok && dalloc(&g->er, (size_t)nr * (nt + 1) * d.np, owned) &&
+         dalloc(&g->et, (size_t)(nr + 1) * nt * d.np, owned) &&
+         dalloc(&g->ep, (size_t)(nr + 1) * (nt + 1) * d.np, owned) && dalloc(&g->ec, n3, owned) &&
+         dalloc(&g->ring, 2 * (size_t)nr, owned);
+    ok = ok && dalloc(&g->partials, (size_t)kMaxBlocks * kPartialsPerBlock + 16, owned) &&
+         dalloc(&g->sc, 1, owned) && dalloc(&g->ss, 1, owned);
+    if (!ok) {
+        for (void* m : owned) cudaFree(m);
+        cudaGetLastError();
+        delete g;
+        return set_error(nullptr, MHD_ERR_OOM, "mhd_grid_create: device allocation failed");
+    }
+    if (cudaMallocHost(&g->h_sc, sizeof(PcgScalars)) != cudaSuccess ||
+        cudaMallocHost(&g->h_ss, sizeof(StepScalars)) != cudaSuccess ||
+        cudaMallocHost(&g->h_alpha, 8 * sizeof(double)) != cudaSuccess) {
+        for (void* m : owned) cudaFree(m);
+        cudaGetLastError();
+        delete g;
+        return set_error(nullptr, MHD_ERR_OOM, "mhd_grid_create: pinned host allocation failed");
+    }
+    // the single block of device memory list is kept for destroy
+    auto* keep = new std::vector<void*>(owned);
+    g->geo_mem = keep;
+
+    auto up = [&](double* dst, const std::vector<double>& src) {
+        return cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(double), cudaMemcpyHostToDevice,
+                               g->stream) == cudaSuccess;
+    };
+    ok = up(r, h.r) && up(rc, h.rc) && up(sn, h.sn) && up(cn, h.cn) && up(sc, h.sc) && up(cc, h.cc) &&
+         up(rho, h.rho) && up(rhoV, h.rhoV) && up(kt2, h.kt2) && up(wr, h.wr) && up(wt, h.wt) && up(wp, h.wp);
+    ok = ok && cudaMemsetAsync(g->partials, 0, sizeof(double) * kMaxBlocks * kPartialsPerBlock, g->stream) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(g->sc, 0, sizeof(PcgScalars), g->stream) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(g->ss, 0, sizeof(StepScalars), g->stream) == cudaSuccess;
+    // zero the FP32 p buffers once so the first fused update never reads garbage
+    ok = ok && cudaMemsetAsync(g->p32, 0, sizeof(float) * 2 * n3, g->stream) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(g->p64, 0, sizeof(double) * n3, g->stream) == cudaSuccess;
+    ok = ok && cudaStreamSynchronize(g->stream) == cudaSuccess;
+    if (!ok) {
+        mhd_grid_destroy(g);
+        return set_error(nullptr, MHD_ERR_CUDA, "mhd_grid_create: table upload failed");
+    }
+    Geo& G = g->geo;
+    G.r = r; G.rc = rc; G.sn = sn; G.cn = cn; G.sc = sc; G.cc = cc; G.rho = rho; G.rhoV = rhoV;
+    G.kt2 = kt2; G.wr = wr; G.wt = wt; G.wp = wp;
+    G.r0 = d.r0;
+    G.r1 = h.r[nr];
+    G.dth = 3.14159265358979323846 / nt;
+    G.dph = 2.0 * 3.14159265358979323846 / d.np;
+    G.max_kt2 = h.max_kt2;
+    *out = g;
+    return MHD_OK;
+}
+
+extern "C" mhd_status_t mhd_grid_destroy(mhd_grid_t g) {
+    if (!g) return MHD_OK;
+    cudaStreamSynchronize(g->stream);
+    for (auto& row : g->iter_graph)
+        for (auto& ge : row)
+            if (ge) cudaGraphExecDestroy(ge);
+    if (g->geo_mem) {
+        auto* keep = reinterpret_cast<std::vector<void*>*>(g->geo_mem);
+        for (void* m : *keep) cudaFree(m);
+        delete keep;
+    }
+    if (g->h_sc) cudaFreeHost(g->h_sc);
+    if (g->h_ss) cudaFreeHost(g->h_ss);
+    if (g->h_alpha) cudaFreeHost(g->h_alpha);
+    if (g->prof_ev[0])
+        for (auto& e : g->prof_ev) cudaEventDestroy(e);
+    cudaGetLastError();
+    delete g;
+    return MHD_OK;
+}
+
+extern "C" mhd_status_t mhd_grid_sizes(mhd_grid_t g, long long sizes[6]) {
+    if (!g || !sizes) return MHD_ERR_ARG;
+    const long long nr = g->d.nr, nt = g->d.nt, np = g->d.np;
+    sizes[0] = (nr + 1) * nt * np;
+    sizes[1] = nr * (nt + 1) * np;
+    sizes[2] = nr * nt * np;
+    sizes[3] = sizes[4] = sizes[5] = nr * nt * np;
+    return MHD_OK;
+}
+
+extern "C" mhd_status_t mhd_profile_enable(mhd_grid_t g, int enable) {
+    if (!g) return MHD_ERR_ARG;
+    cudaStreamSynchronize(g->stream);
+    if (enable && !g->prof_ev[0]) {
+        for (auto& e : g->prof_ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return check_cuda(g, "profile events");
+    }
+    g->prof = enable ? 1 : 0;
+    g->prof_nslot = 0;
+    for (int k = 0; k < MHD_KERNEL_COUNT; k++) {
+        g->prof_ms[k] = 0.0;
+        g->prof_cnt[k] = 0;
+    }
+    return MHD_OK;
+}
+
+extern "C" mhd_status_t mhd_profile_read(mhd_grid_t g, int kernel, double* total_ms, long long* launches) {
+    if (!g || kernel < 0 || kernel >= MHD_KERNEL_COUNT) return MHD_ERR_ARG;
+    if (cudaStreamSynchronize(g->stream) != cudaSuccess) return check_cuda(g, "profile sync");
+    prof_flush(g);
+    if (total_ms) *total_ms = g->prof_ms[kernel];
+    if (launches) *launches = g->prof_cnt[kernel];
+    return MHD_OK;
+}
+
+extern "C" const char* mhd_last_error(mhd_grid_t g) {
+    if (g) return g->last_error.c_str();
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    return g_create_error.c_str();
+}

@@ -1,0 +1,168 @@
+// Internal declarations of the sm_103a zero-beta MHD library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "mhd.h"
+
+namespace mhd {
+
+constexpr int kThreads = 256;       // threads per CTA for every grid-stride kernel
+constexpr int kMaxBlocks = 4096;    // capacity of the per-block partial-sum array
+constexpr int kPartialsPerBlock = 4;
+
+// Device-resident scalars of one PCG solve. Written only by the last CTA of a reducing
+// kernel (fixed-order sum of the per-CTA partials, so results are deterministic).
+struct PcgScalars {
+    double rho;      // <r~, r~> (scaled residual, = <r, z> of the unscaled Jacobi PCG)
+    double rr;       // ||r||_2^2 of the unscaled residual (stop test)
+    double bb;       // ||b||_2^2
+    double pq;       // <p~, A~ p~>
+    double alpha, beta;
+    double tol;      // stop when sqrt(rr) <= tol * sqrt(bb)   (FP64 solve / outer loop)
+    double rr_out;   // mixed: squared norm of the current outer FP64 residual
+    double inner_tol;
+    int iter;        // iterations of the current (inner) solve
+    int max_iter;
+    int done;        // 0 running, 1 converged, 2 iteration cap, 3 non-finite, 4 breakdown
+    int outer;       // mixed: outer passes done
+    int outer_done;  // mixed: 0 running, 1 converged, 3 non-finite
+    int total_iter;  // mixed: inner iterations summed over the outer passes
+    unsigned int count;  // last-block ticket
+    unsigned int pad;
+};
+
+// Device-resident scalars of one step.
+struct StepScalars {
+    double dt, cf, cw, alpha_si, alpha_nu;
+    double max_kv2, max_kva2, max_kt2;
+    double alpha_user;   // alpha of a direct operator/solver call
+    int status;      // MHD_OK or MHD_ERR_ARG (C_f >= 1 / no dt)
+    unsigned int count;
+};
+
+struct Dims {
+    int nr, nt, np;
+    int pad;
+    long long N;
+};
+
+// Per-grid FP64 metric tables (device). Built on the host from the grid definition.
+struct Geo {
+    const double* r;     // [nr+1] radial nodes
+    const double* rc;    // [nr]   radial centres
+    const double* sn;    // [nt+1] sin(theta_j), exact 0 at the poles
+    const double* cn;    // [nt+1] cos(theta_j), exact +-1 at the poles
+    const double* sc;    // [nt]   sin of theta centres
+    const double* cc;    // [nt]   cos of theta centres
+    const double* rho;   // [nr]   rho0 at radial centres
+    const double* rhoV;  // [nr*nt] rho_c V_c
+    const double* kt2;   // [nr*nt] k~^2 at cell centres
+    const double* wr;    // [(nr+1)*nt] radial-face weights (wr[0] = Dirichlet weight at r0,
+                         //             wr[nr] = 0: Neumann at r1)
+    const double* wt;    // [nr*(nt+1)] theta-face weights (0 at the poles)
+    const double* wp;    // [nr*nt] phi-face weight (each of the two faces)
+    double r0, r1, dth, dph;
+    double max_kt2;
+};
+
+// Operator tables of M_alpha for one solve, in the Jacobi-scaled form
+// A~ = S M S, S = diag(M)^(-1/2): unit diagonal, off-diagonals -a (a >= 0).
+template <typename T>
+struct OpTab {
+    T* ar;   // [(nr+1)*nt] radial faces (0 at r0 and r1)
+    T* at;   // [nr*(nt+1)] theta faces (0 at the poles)
+    T* ap;   // [nr*nt]     phi faces
+    T* s;    // [nr*nt]     diag^(-1/2)
+};
+
+// Unscaled FP64 tables of the same M_alpha (outer residual of mixed precision).
+struct OpTab64u {
+    double* dg;   // [nr*nt] diagonal
+    double* awr;  // [(nr+1)*nt] alpha * wr with the Dirichlet face zeroed (it is in dg)
+    double* awt;  // [nr*(nt+1)]
+    double* awp;  // [nr*nt]
+};
+
+}  // namespace mhd
+
+// The opaque grid object behind mhd_grid_t.
+struct mhd_grid_s {
+    mhd::Dims d;
+    mhd_grid_desc_t desc;
+    cudaStream_t stream;
+    int device;
+    int num_sms;
+    // host copies of the metric tables
+    double max_kt2;
+    // device allocations
+    void* geo_mem;
+    mhd::Geo geo;
+    mhd::OpTab<double> t64;
+    mhd::OpTab<float> t32;
+    mhd::OpTab64u tu;
+    // FP64 PCG workspace (stacked 3-component vectors, 3N each)
+    double *x64, *r64, *p64, *q64;
+    // FP32 PCG workspace
+    float *x32, *r32, *p32, *q32;
+    // step workspace
+    double *b0, *b1, *dlt;
+    double *er, *et, *ep;   // edge arrays (E or J)
+    double *ec;             // cell-centred E (3N)
+    double *ring;           // [2*nr] polar ring sums
+    double* partials;       // [kMaxBlocks * kPartialsPerBlock]
+    mhd::PcgScalars* sc;    // device
+    mhd::StepScalars* ss;   // device
+    mhd::PcgScalars* h_sc;  // pinned host mirror
+    mhd::StepScalars* h_ss; // pinned host mirror
+    double* h_alpha;        // pinned host scalar staging
+    // CUDA graphs of a batch of PCG iterations, keyed by precision and ncomp
+    cudaGraphExec_t iter_graph[2][4];
+    int graph_batch;
+    std::string last_error;
+    // kernel timing (diagnostics)
+    int prof;
+    static constexpr int kProfSlots = 512;
+    cudaEvent_t prof_ev[2 * kProfSlots];
+    int prof_kid[kProfSlots];
+    int prof_nslot;
+    double prof_ms[MHD_KERNEL_COUNT];
+    long long prof_cnt[MHD_KERNEL_COUNT];
+};
+
+namespace mhd {
+
+// launch helpers
+int grid_blocks(const mhd_grid_s* g, long long work, int per_sm = 4);
+
+// explicit kernels (explicit.cu)
+mhd_status_t coeffs(mhd_grid_s* g, const mhd_params_t* p, const double* vr, const double* vt,
+                    const double* vp, const double* br, const double* bt, const double* bp);
+void current_edges(mhd_grid_s* g, const double* br, const double* bt, const double* bp);
+void force(mhd_grid_s* g, const double* vr, const double* vt, const double* vp,
+           const double* dlt, double dfac, const double* br, const double* bt, const double* bp,
+           const double* dt_dev, double dt_host, const double* b_avg, double* b);
+void induction(mhd_grid_s* g, const double* vr, const double* vt, const double* vp,
+               const double* dlt, double dfac, double eta, const double* dt_dev, double dt_host,
+               double* br, double* bt, double* bp);
+void vstar_rhs(mhd_grid_s* g, double* vr, double* vt, double* vp, const double* dlt, double* b);
+
+// PCG (pcg.cu). alpha is read from device memory (alpha_dev) so a step never syncs on it.
+void build_tables(mhd_grid_s* g, const double* alpha_dev, bool fp32);
+void apply_operator(mhd_grid_s* g, const double* alpha_dev, int nc, const double* p, double* q);
+mhd_status_t solve(mhd_grid_s* g, const double* alpha_dev, int nc, const double* b, double* x,
+                   const double* x0, const mhd_params_t* prm, int* iters, int* outer,
+                   double* relres);
+
+mhd_status_t set_error(mhd_grid_s* g, mhd_status_t st, const std::string& msg);
+
+// kernel timing: bracket a launch with events when profiling is on (returns the slot or -1)
+int prof_begin(mhd_grid_s* g, cudaStream_t st, int kernel);
+void prof_end(mhd_grid_s* g, cudaStream_t st, int slot);
+void prof_flush(mhd_grid_s* g);   // after a stream sync: fold finished slots into the totals
+mhd_status_t check_cuda(mhd_grid_s* g, const char* where);
+
+}  // namespace mhd

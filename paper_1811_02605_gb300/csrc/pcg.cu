@@ -1,0 +1,706 @@
+// PCG with the point-Jacobi preconditioner PC1 (Sec. 2.2) for M_alpha = D + alpha K, on
+// stacked 3-component vectors, in FP64 or FP32-inner / FP64-refinement form.
+//
+// Point-Jacobi PCG on M x = b produces, in exact arithmetic, the same iterates as plain CG on
+// the symmetrically scaled system A~ y = S b with A~ = S M S, S = diag(M)^(-1/2), x = S y:
+// its residual r~ = S r, and <r~, r~> = <r, D^-1 r> is PCG's <r, z>. The scaled form has a unit
+// diagonal, so the stencil needs one multiply-add per neighbour and no preconditioner pass.
+// That matters on this part: FP64 runs at 2 FMA/clk/SM, so the FP64 iteration is bound by its
+// FP64 instruction count, not by HBM.
+//
+// Reductions: every thread accumulates its share in FP64 (FP32 path: compensated FP32 per
+// thread, then FP64), CTAs reduce with warp shuffles, write one partial each, and the last CTA
+// to arrive sums the partials in CTA order and finishes the scalar recurrence (alpha, beta,
+// stop test). Results are deterministic for a fixed launch shape.
+#include <cmath>
+#include <cstdio>
+
+#include "mhd_internal.cuh"
+#include "reduce.cuh"
+
+namespace mhd {
+
+// ------------------------------------------------------------------------------------------
+// vector access along phi
+// ------------------------------------------------------------------------------------------
+template <typename T, int V>
+__device__ __forceinline__ void ldv(const T* __restrict__ p, T (&o)[V]) {
+    if constexpr (sizeof(T) == 8 && V == 2) {
+        double2 t = *reinterpret_cast<const double2*>(p);
+        o[0] = t.x; o[1] = t.y;
+    } else if constexpr (sizeof(T) == 4 && V == 4) {
+        float4 t = *reinterpret_cast<const float4*>(p);
+        o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+    } else if constexpr (sizeof(T) == 4 && V == 2) {
+        float2 t = *reinterpret_cast<const float2*>(p);
+        o[0] = t.x; o[1] = t.y;
+    }
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void stv(T* __restrict__ p, const T (&o)[V]) {
+    if constexpr (sizeof(T) == 8 && V == 2) {
+        *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
+    } else if constexpr (sizeof(T) == 4 && V == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    } else if constexpr (sizeof(T) == 4 && V == 2) {
+        *reinterpret_cast<float2*>(p) = make_float2(o[0], o[1]);
+    }
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void zerov(T (&o)[V]) {
+#pragma unroll
+    for (int e = 0; e < V; e++) o[e] = T(0);
+}
+
+// Per-thread accumulator: plain FP64 for FP64 data; for FP32 data a compensated FP32 sum
+// (Neumaier) that is handed to FP64 once per thread.
+template <typename T>
+struct Acc;
+template <>
+struct Acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ void fma_add(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double get() const { return s; }
+};
+template <>
+struct Acc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        float t = s + x;
+        c += (fabsf(s) >= fabsf(x)) ? ((s - t) + x) : ((x - t) + s);
+        s = t;
+    }
+    __device__ __forceinline__ void fma_add(float a, float b) { add(a * b); }
+    __device__ __forceinline__ double get() const { return (double)s + (double)c; }
+};
+
+__device__ __forceinline__ bool finite(double x) { return isfinite(x); }
+
+// ------------------------------------------------------------------------------------------
+// operator tables for one alpha
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ double diag_at(const Geo& G, int nt, double a, int i, int j) {
+    const double s = G.wr[i * nt + j] + G.wr[(i + 1) * nt + j] + G.wt[i * (nt + 1) + j] +
+                     G.wt[i * (nt + 1) + j + 1] + 2.0 * G.wp[i * nt + j];
+    return G.rhoV[i * nt + j] + a * s;
+}
+
+__global__ void k_tables(Dims d, Geo G, const double* __restrict__ alpha_p, OpTab<double> t,
+                         OpTab<float> t32, OpTab64u tu, int want32) {
+    const int nr = d.nr, nt = d.nt;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nr * nt) return;
+    const int i = idx / nt, j = idx - i * nt;
+    const double a = *alpha_p;
+    const double dc = diag_at(G, nt, a, i, j);
+    const double s = 1.0 / sqrt(dc);
+    const double ar = (i > 0) ? a * G.wr[i * nt + j] * s * (1.0 / sqrt(diag_at(G, nt, a, i - 1, j))) : 0.0;
+    const double at = (j > 0) ? a * G.wt[i * (nt + 1) + j] * s * (1.0 / sqrt(diag_at(G, nt, a, i, j - 1))) : 0.0;
+    const double ap = a * G.wp[idx] * s * s;
+    t.s[idx] = s;
+    t.ar[i * nt + j] = ar;
+    t.at[i * (nt + 1) + j] = at;
+    t.ap[idx] = ap;
+    tu.dg[idx] = dc;
+    tu.awr[i * nt + j] = (i > 0) ? a * G.wr[i * nt + j] : 0.0;
+    tu.awt[i * (nt + 1) + j] = (j > 0) ? a * G.wt[i * (nt + 1) + j] : 0.0;
+    tu.awp[idx] = a * G.wp[idx];
+    if (i == nr - 1) { t.ar[nr * nt + j] = 0.0; tu.awr[nr * nt + j] = 0.0; }
+    if (j == nt - 1) { t.at[i * (nt + 1) + nt] = 0.0; tu.awt[i * (nt + 1) + nt] = 0.0; }
+    if (want32) {
+        t32.s[idx] = (float)s;
+        t32.ar[i * nt + j] = (float)ar;
+        t32.at[i * (nt + 1) + j] = (float)at;
+        t32.ap[idx] = (float)ap;
+        if (i == nr - 1) t32.ar[nr * nt + j] = 0.f;
+        if (j == nt - 1) t32.at[i * (nt + 1) + nt] = 0.f;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// index decomposition of a phi-vector group g -> (i, j, k0)
+// ------------------------------------------------------------------------------------------
+struct Cell {
+    int i, j, k0;
+    long long ij, base;
+};
+template <int V>
+__device__ __forceinline__ Cell decompose(const Dims& d, unsigned int g) {
+    Cell c;
+    const unsigned int npv = d.np / V;
+    const unsigned int ij = g / npv;
+    c.k0 = (int)(g - ij * npv) * V;
+    c.i = (int)(ij / d.nt);
+    c.j = (int)(ij - (unsigned)c.i * d.nt);
+    c.ij = ij;
+    c.base = (long long)ij * d.np + c.k0;
+    return c;
+}
+
+// stencil of the scaled operator at one phi-vector: o = u - sum a_nb u_nb
+template <typename T, int V>
+__device__ __forceinline__ void scaled_stencil(const Dims& d, const Cell& c, const T* __restrict__ u,
+                                               T cr_lo, T cr_hi, T ct_lo, T ct_hi, T cp, T (&v)[V],
+                                               T (&o)[V]) {
+    const long long plane = (long long)d.nt * d.np;
+    ldv<T, V>(u + c.base, v);
+    const long long row = c.base - c.k0;
+    const int km = (c.k0 == 0) ? d.np - 1 : c.k0 - 1;
+    const int kp = (c.k0 + V == d.np) ? 0 : c.k0 + V;
+    const T ukm = u[row + km], ukp = u[row + kp];
+#pragma unroll
+    for (int e = 0; e < V; e++) {
+        const T left = (e == 0) ? ukm : v[e - 1];
+        const T right = (e == V - 1) ? ukp : v[e + 1];
+        o[e] = fma(-cp, left + right, v[e]);
+    }
+    T n[V];
+    if (c.i > 0) {
+        ldv<T, V>(u + c.base - plane, n);
+#pragma unroll
+        for (int e = 0; e < V; e++) o[e] = fma(-cr_lo, n[e], o[e]);
+    }
+    if (c.i < d.nr - 1) {
+        ldv<T, V>(u + c.base + plane, n);
+#pragma unroll
+        for (int e = 0; e < V; e++) o[e] = fma(-cr_hi, n[e], o[e]);
+    }
+    if (c.j > 0) {
+        ldv<T, V>(u + c.base - d.np, n);
+#pragma unroll
+        for (int e = 0; e < V; e++) o[e] = fma(-ct_lo, n[e], o[e]);
+    }
+    if (c.j < d.nt - 1) {
+        ldv<T, V>(u + c.base + d.np, n);
+#pragma unroll
+        for (int e = 0; e < V; e++) o[e] = fma(-ct_hi, n[e], o[e]);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// FP64 / FP32 CG iteration kernels on the scaled system
+// ------------------------------------------------------------------------------------------
+// A1: p = r + beta p
+template <typename T, int V>
+__global__ void __launch_bounds__(kThreads) k_pupdate(Dims d, int nc, const T* __restrict__ r,
+                                                      T* __restrict__ p, const PcgScalars* sc) {
+    if (sc->done) return;
+    const T beta = (T)sc->beta;
+    const unsigned int G = (unsigned int)(d.N / V);
+    for (int c = 0; c < nc; c++) {
+        const T* rc = r + c * d.N;
+        T* pc = p + c * d.N;
+        for (unsigned int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+            T a[V], b[V];
+            ldv<T, V>(rc + (long long)g * V, a);
+            ldv<T, V>(pc + (long long)g * V, b);
+#pragma unroll
+            for (int e = 0; e < V; e++) b[e] = fma(beta, b[e], a[e]);
+            stv<T, V>(pc + (long long)g * V, b);
+        }
+    }
+}
+
+// A2: q = A~ p and <p, q>; last CTA forms alpha = rho / <p, q>
+template <typename T, int V>
+__global__ void __launch_bounds__(kThreads) k_spmv_dot(Dims d, int nc, const T* __restrict__ p,
+                                                       T* __restrict__ q, OpTab<T> t, PcgScalars* sc,
+                                                       double* __restrict__ partials) {
+    if (sc->done) return;
+    const int nt = d.nt;
+    const unsigned int G = (unsigned int)(d.N / V);
+    Acc<T> acc;
+    for (unsigned int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+        const Cell c = decompose<V>(d, g);
+        const T cr_lo = t.ar[c.i * nt + c.j], cr_hi = t.ar[(c.i + 1) * nt + c.j];
+        const T ct_lo = t.at[c.i * (nt + 1) + c.j], ct_hi = t.at[c.i * (nt + 1) + c.j + 1];
+        const T cp = t.ap[c.ij];
+        for (int k = 0; k < nc; k++) {
+            T v[V], o[V];
+            scaled_stencil<T, V>(d, c, p + k * d.N, cr_lo, cr_hi, ct_lo, ct_hi, cp, v, o);
+            stv<T, V>(q + k * d.N + c.base, o);
+#pragma unroll
+            for (int e = 0; e < V; e++) acc.fma_add(v[e], o[e]);
+        }
+    }
+    double val[1] = {acc.get()}, out[1];
+    if (reduce_last<1>(val, partials, &sc->count, out) && threadIdx.x == 0) {
+        const double pq = out[0];
+        sc->pq = pq;
+        if (!finite(pq)) sc->done = 3;
+        else if (!(pq > 0.0)) sc->done = 4;
+        else sc->alpha = sc->rho / pq;
+    }
+}
+
+// B: x += alpha p, r -= alpha q, rho = <r~, r~>, rr = sum dg r~^2; last CTA: beta, stop test
+template <typename T, int V>
+__global__ void __launch_bounds__(kThreads) k_update(Dims d, int nc, T* __restrict__ x,
+                                                     const T* __restrict__ p, T* __restrict__ r,
+                                                     const T* __restrict__ q,
+                                                     const double* __restrict__ dg, PcgScalars* sc,
+                                                     double* __restrict__ partials) {
+    if (sc->done) return;
+    const T al = (T)sc->alpha;
+    const unsigned int G = (unsigned int)(d.N / V);
+    const unsigned int npv = d.np / V;
+    Acc<T> a_rho;
+    double a_rr = 0.0;
+    for (unsigned int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+        const long long off = (long long)g * V;
+        T rs[V];
+        zerov<T, V>(rs);
+        for (int k = 0; k < nc; k++) {
+            T xv[V], pv[V], rv[V], qv[V];
+            ldv<T, V>(x + k * d.N + off, xv);
+            ldv<T, V>(p + k * d.N + off, pv);
+            ldv<T, V>(r + k * d.N + off, rv);
+            ldv<T, V>(q + k * d.N + off, qv);
+#pragma unroll
+            for (int e = 0; e < V; e++) {
+                xv[e] = fma(al, pv[e], xv[e]);
+                rv[e] = fma(-al, qv[e], rv[e]);
+                rs[e] = fma(rv[e], rv[e], rs[e]);
+            }
+            stv<T, V>(x + k * d.N + off, xv);
+            stv<T, V>(r + k * d.N + off, rv);
+        }
+        T cell = rs[0];
+#pragma unroll
+        for (int e = 1; e < V; e++) cell += rs[e];
+        a_rho.add(cell);
+        a_rr = fma(dg[g / npv], (double)cell, a_rr);
+    }
+    double val[2] = {a_rho.get(), a_rr}, out[2];
+    if (reduce_last<2>(val, partials, &sc->count, out) && threadIdx.x == 0) {
+        const double rho = out[0], rr = out[1];
+        sc->iter += 1;
+        sc->total_iter += 1;
+        sc->beta = rho / sc->rho;
+        sc->rho = rho;
+        sc->rr = rr;
+        if (!finite(rr) || !finite(rho)) sc->done = 3;
+        else if (sqrt(rr) <= sc->tol * sqrt(sc->bb)) sc->done = 1;
+        else if (sc->iter >= sc->max_iter) sc->done = 2;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// FP64 solve: set-up and finish
+// ------------------------------------------------------------------------------------------
+// r = b - M x0 (unscaled tables), x~ = x0 / s, r~ = s r, p~ = r~; rho, ||r||^2, ||b||^2
+__global__ void __launch_bounds__(kThreads) k_init64(Dims d, int nc, const double* __restrict__ b,
+                                                     const double* __restrict__ x0, double* __restrict__ xs,
+                                                     double* __restrict__ r, double* __restrict__ p,
+                                                     OpTab<double> t, OpTab64u tu, PcgScalars* sc,
+                                                     double* __restrict__ partials) {
+    const int nt = d.nt;
+    const unsigned int G = (unsigned int)(d.N / 2);
+    const long long plane = (long long)nt * d.np;
+    double a_rho = 0.0, a_rr = 0.0, a_bb = 0.0;
+    for (unsigned int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+        const Cell c = decompose<2>(d, g);
+        const double s = t.s[c.ij];
+        const double dg = tu.dg[c.ij];
+        const double wl = tu.awr[c.i * nt + c.j], wh = tu.awr[(c.i + 1) * nt + c.j];
+        const double tl = tu.awt[c.i * (nt + 1) + c.j], th = tu.awt[c.i * (nt + 1) + c.j + 1];
+        const double wp = tu.awp[c.ij];
+        for (int k = 0; k < nc; k++) {
+            const double* u = x0 + k * d.N;
+            double bv[2], rv[2], xv[2];
+            ldv<double, 2>(b + k * d.N + c.base, bv);
+            ldv<double, 2>(u + c.base, xv);
+            const long long row = c.base - c.k0;
+            const int km = (c.k0 == 0) ? d.np - 1 : c.k0 - 1;
+            const int kp = (c.k0 + 2 == d.np) ? 0 : c.k0 + 2;
+            double n[2];
+            double mx[2];
+            mx[0] = dg * xv[0] - wp * (u[row + km] + xv[1]);
+            mx[1] = dg * xv[1] - wp * (xv[0] + u[row + kp]);
+            if (c.i > 0) { ldv<double, 2>(u + c.base - plane, n); mx[0] -= wl * n[0]; mx[1] -= wl * n[1]; }
+            if (c.i < d.nr - 1) { ldv<double, 2>(u + c.base + plane, n); mx[0] -= wh * n[0]; mx[1] -= wh * n[1]; }
+            if (c.j > 0) { ldv<double, 2>(u + c.base - d.np, n); mx[0] -= tl * n[0]; mx[1] -= tl * n[1]; }
+            if (c.j < nt - 1) { ldv<double, 2>(u + c.base + d.np, n); mx[0] -= th * n[0]; mx[1] -= th * n[1]; }
+            double xsv[2], rsv[2];
+            const double si = sqrt(dg);
+            for (int e = 0; e < 2; e++) {
+                rv[e] = bv[e] - mx[e];
+                rsv[e] = s * rv[e];
+                xsv[e] = xv[e] * si;
+                a_rho = fma(rsv[e], rsv[e], a_rho);
+                a_rr = fma(rv[e], rv[e], a_rr);
+                a_bb = fma(bv[e], bv[e], a_bb);
+            }
+            stv<double, 2>(xs + k * d.N + c.base, xsv);
+            stv<double, 2>(r + k * d.N + c.base, rsv);
+            stv<double, 2>(p + k * d.N + c.base, rsv);
+        }
+    }
+    double val[3] = {a_rho, a_rr, a_bb}, out[3];
+    if (reduce_last<3>(val, partials, &sc->count, out) && threadIdx.x == 0) {
+        sc->rho = out[0];
+        sc->rr = out[1];
+        sc->bb = out[2];
+        sc->beta = 0.0;
+        sc->iter = 0;
+        sc->total_iter = 0;
+        sc->outer = 0;
+        if (!finite(out[0]) || !finite(out[1]) || !finite(out[2])) sc->done = 3;
+        else if (out[2] == 0.0) sc->done = 1;
+        else if (sqrt(out[1]) <= sc->tol * sqrt(out[2])) sc->done = 1;
+        else if (sc->max_iter <= 0) sc->done = 2;
+        else sc->done = 0;
+    }
+}
+
+// x = s x~ (x = 0 when b = 0)
+__global__ void k_finish64(Dims d, int nc, const double* __restrict__ xs, double* __restrict__ x,
+                           const double* __restrict__ s, const PcgScalars* sc) {
+    const bool zero = (sc->bb == 0.0);
+    const unsigned int G = (unsigned int)(d.N / 2);
+    const unsigned int npv = d.np / 2;
+    for (int k = 0; k < nc; k++)
+        for (unsigned int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+            double v[2];
+            ldv<double, 2>(xs + k * d.N + (long long)g * 2, v);
+            const double sv = s[g / npv];
+            v[0] = zero ? 0.0 : sv * v[0];
+            v[1] = zero ? 0.0 : sv * v[1];
+            stv<double, 2>(x + k * d.N + (long long)g * 2, v);
+        }
+}
+
+// ------------------------------------------------------------------------------------------
+// mixed precision: FP64 outer residual and correction around FP32 inner CG
+// ------------------------------------------------------------------------------------------
+// r = b - M x in FP64; inner start: r~32 = float(s r), p~32 = r~32, x~32 = 0
+template <int V>
+__global__ void __launch_bounds__(kThreads) k_outer_res(Dims d, int nc, const double* __restrict__ b,
+                                                        const double* __restrict__ x, float* __restrict__ r32,
+                                                        float* __restrict__ p32, float* __restrict__ x32,
+                                                        OpTab<double> t, OpTab64u tu, PcgScalars* sc,
+                                                        double* __restrict__ partials, int first) {
+    const int nt = d.nt;
+    const unsigned int G = (unsigned int)(d.N / 2);
+    const long long plane = (long long)nt * d.np;
+    double a_rout = 0.0, a_bb = 0.0, a_rho = 0.0, a_rin = 0.0;
+    for (unsigned int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+        const Cell c = decompose<2>(d, g);
+        const double s = t.s[c.ij];
+        const double dg = tu.dg[c.ij];
+        const double wl = tu.awr[c.i * nt + c.j], wh = tu.awr[(c.i + 1) * nt + c.j];
+        const double tl = tu.awt[c.i * (nt + 1) + c.j], th = tu.awt[c.i * (nt + 1) + c.j + 1];
+        const double wp = tu.awp[c.ij];
+        double cell_in = 0.0;
+        for (int k = 0; k < nc; k++) {
+            const double* u = x + k * d.N;
+            double bv[2], xv[2], n[2], mx[2];
+            ldv<double, 2>(b + k * d.N + c.base, bv);
+            ldv<double, 2>(u + c.base, xv);
+            const long long row = c.base - c.k0;
+            const int km = (c.k0 == 0) ? d.np - 1 : c.k0 - 1;
+            const int kp = (c.k0 + 2 == d.np) ? 0 : c.k0 + 2;
+            mx[0] = dg * xv[0] - wp * (u[row + km] + xv[1]);
+            mx[1] = dg * xv[1] - wp * (xv[0] + u[row + kp]);
+            if (c.i > 0) { ldv<double, 2>(u + c.base - plane, n); mx[0] -= wl * n[0]; mx[1] -= wl * n[1]; }
+            if (c.i < d.nr - 1) { ldv<double, 2>(u + c.base + plane, n); mx[0] -= wh * n[0]; mx[1] -= wh * n[1]; }
+            if (c.j > 0) { ldv<double, 2>(u + c.base - d.np, n); mx[0] -= tl * n[0]; mx[1] -= tl * n[1]; }
+            if (c.j < nt - 1) { ldv<double, 2>(u + c.base + d.np, n); mx[0] -= th * n[0]; mx[1] -= th * n[1]; }
+            float rs[2];
+            for (int e = 0; e < 2; e++) {
+                const double rv = bv[e] - mx[e];
+                rs[e] = (float)(s * rv);
+                a_rout = fma(rv, rv, a_rout);
+                if (first) a_bb = fma(bv[e], bv[e], a_bb);
+                const double rd = (double)rs[e];
+                a_rho = fma(rd, rd, a_rho);
+                cell_in = fma(rd, rd, cell_in);
+            }
+            *reinterpret_cast<float2*>(r32 + k * d.N + c.base) = make_float2(rs[0], rs[1]);
+            *reinterpret_cast<float2*>(p32 + k * d.N + c.base) = make_float2(rs[0], rs[1]);
+            *reinterpret_cast<float2*>(x32 + k * d.N + c.base) = make_float2(0.f, 0.f);
+        }
+        a_rin = fma(dg, cell_in, a_rin);
+    }
+    double val[4] = {a_rout, a_bb, a_rho, a_rin}, out[4];
+    if (reduce_last<4>(val, partials, &sc->count, out) && threadIdx.x == 0) {
+        if (first) sc->bb = out[1];
+        sc->rr_out = out[0];
+        sc->rho = out[2];
+        sc->rr = out[3];
+        sc->beta = 0.0;
+        sc->iter = 0;
+        const double bn = sqrt(sc->bb);
+        if (!finite(out[0]) || !finite(out[2])) { sc->done = 3; sc->outer_done = 3; }
+        else if (sc->bb == 0.0 || sqrt(out[0]) <= sc->tol * bn) { sc->done = 1; sc->outer_done = 1; }
+        else {
+            sc->outer_done = 0;
+            sc->done = (sc->max_iter <= 0) ? 2 : 0;
+        }
+    }
+}
+
+// x += s x~32 (FP64 correction)
+__global__ void k_correct(Dims d, int nc, double* __restrict__ x, const float* __restrict__ xs,
+                          const double* __restrict__ s, PcgScalars* sc) {
+    if (sc->outer_done) return;
+    const unsigned int G = (unsigned int)(d.N / 2);
+    const unsigned int npv = d.np / 2;
+    for (int k = 0; k < nc; k++)
+        for (unsigned int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+            double v[2];
+            ldv<double, 2>(x + k * d.N + (long long)g * 2, v);
+            const float2 e = *reinterpret_cast<const float2*>(xs + k * d.N + (long long)g * 2);
+            const double sv = s[g / npv];
+            v[0] = fma(sv, (double)e.x, v[0]);
+            v[1] = fma(sv, (double)e.y, v[1]);
+            stv<double, 2>(x + k * d.N + (long long)g * 2, v);
+        }
+    if (blockIdx.x == 0 && threadIdx.x == 0) sc->outer += 1;
+}
+
+// q = M p (unscaled FP64), for the C-ABI operator call
+__global__ void __launch_bounds__(kThreads) k_apply64(Dims d, int nc, const double* __restrict__ p,
+                                                      double* __restrict__ q, OpTab64u tu) {
+    const int nt = d.nt;
+    const unsigned int G = (unsigned int)(d.N / 2);
+    const long long plane = (long long)nt * d.np;
+    for (unsigned int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+        const Cell c = decompose<2>(d, g);
+        const double dg = tu.dg[c.ij];
+        const double wl = tu.awr[c.i * nt + c.j], wh = tu.awr[(c.i + 1) * nt + c.j];
+        const double tl = tu.awt[c.i * (nt + 1) + c.j], th = tu.awt[c.i * (nt + 1) + c.j + 1];
+        const double wp = tu.awp[c.ij];
+        for (int k = 0; k < nc; k++) {
+            const double* u = p + k * d.N;
+            double xv[2], n[2], mx[2];
+            ldv<double, 2>(u + c.base, xv);
+            const long long row = c.base - c.k0;
+            const int km = (c.k0 == 0) ? d.np - 1 : c.k0 - 1;
+            const int kp = (c.k0 + 2 == d.np) ? 0 : c.k0 + 2;
+            mx[0] = dg * xv[0] - wp * (u[row + km] + xv[1]);
+            mx[1] = dg * xv[1] - wp * (xv[0] + u[row + kp]);
+            if (c.i > 0) { ldv<double, 2>(u + c.base - plane, n); mx[0] -= wl * n[0]; mx[1] -= wl * n[1]; }
+            if (c.i < d.nr - 1) { ldv<double, 2>(u + c.base + plane, n); mx[0] -= wh * n[0]; mx[1] -= wh * n[1]; }
+            if (c.j > 0) { ldv<double, 2>(u + c.base - d.np, n); mx[0] -= tl * n[0]; mx[1] -= tl * n[1]; }
+            if (c.j < nt - 1) { ldv<double, 2>(u + c.base + d.np, n); mx[0] -= th * n[0]; mx[1] -= th * n[1]; }
+            stv<double, 2>(q + k * d.N + c.base, mx);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// host side
+// ------------------------------------------------------------------------------------------
+void build_tables(mhd_grid_s* g, const double* alpha_dev, bool fp32) {
+    const int n = g->d.nr * g->d.nt;
+    k_tables<<<(n + 255) / 256, 256, 0, g->stream>>>(g->d, g->geo, alpha_dev, g->t64, g->t32, g->tu,
+                                                      fp32 ? 1 : 0);
+}
+
+void apply_operator(mhd_grid_s* g, const double* alpha_dev, int nc, const double* p, double* q) {
+    build_tables(g, alpha_dev, false);
+    const int blocks = grid_blocks(g, g->d.N / 2, 8);
+    k_apply64<<<blocks, kThreads, 0, g->stream>>>(g->d, nc, p, q, g->tu);
+}
+
+namespace {
+
+constexpr int kPerSmIter = 4;
+
+bool use_v4(const mhd_grid_s* g) { return (g->d.np % 4) == 0; }
+
+// enqueue one CG iteration (A1, A2, B) of the given precision
+void enqueue_iteration(mhd_grid_s* g, cudaStream_t st, int prec, int nc) {
+    const Dims d = g->d;
+    int s;
+    if (prec == 0) {
+        const int blocks = grid_blocks(g, d.N / 2, kPerSmIter);
+        s = prof_begin(g, st, MHD_KERNEL_PUPDATE64);
+        k_pupdate<double, 2><<<blocks, kThreads, 0, st>>>(d, nc, g->r64, g->p64, g->sc);
+        prof_end(g, st, s);
+        s = prof_begin(g, st, MHD_KERNEL_SPMV64);
+        k_spmv_dot<double, 2><<<blocks, kThreads, 0, st>>>(d, nc, g->p64, g->q64, g->t64, g->sc, g->partials);
+        prof_end(g, st, s);
+        s = prof_begin(g, st, MHD_KERNEL_UPDATE64);
+        k_update<double, 2><<<blocks, kThreads, 0, st>>>(d, nc, g->x64, g->p64, g->r64, g->q64, g->tu.dg, g->sc,
+                                                          g->partials);
+        prof_end(g, st, s);
+    } else if (use_v4(g)) {
+        const int blocks = grid_blocks(g, d.N / 4, kPerSmIter);
+        s = prof_begin(g, st, MHD_KERNEL_PUPDATE32);
+        k_pupdate<float, 4><<<blocks, kThreads, 0, st>>>(d, nc, g->r32, g->p32, g->sc);
+        prof_end(g, st, s);
+        s = prof_begin(g, st, MHD_KERNEL_SPMV32);
+        k_spmv_dot<float, 4><<<blocks, kThreads, 0, st>>>(d, nc, g->p32, g->q32, g->t32, g->sc, g->partials);
+        prof_end(g, st, s);
+        s = prof_begin(g, st, MHD_KERNEL_UPDATE32);
+        k_update<float, 4><<<blocks, kThreads, 0, st>>>(d, nc, g->x32, g->p32, g->r32, g->q32, g->tu.dg, g->sc,
+                                                         g->partials);
+        prof_end(g, st, s);
+    } else {
+        const int blocks = grid_blocks(g, d.N / 2, kPerSmIter);
+        s = prof_begin(g, st, MHD_KERNEL_PUPDATE32);
+        k_pupdate<float, 2><<<blocks, kThreads, 0, st>>>(d, nc, g->r32, g->p32, g->sc);
+        prof_end(g, st, s);
+        s = prof_begin(g, st, MHD_KERNEL_SPMV32);
+        k_spmv_dot<float, 2><<<blocks, kThreads, 0, st>>>(d, nc, g->p32, g->q32, g->t32, g->sc, g->partials);
+        prof_end(g, st, s);
+        s = prof_begin(g, st, MHD_KERNEL_UPDATE32);
+        k_update<float, 2><<<blocks, kThreads, 0, st>>>(d, nc, g->x32, g->p32, g->r32, g->q32, g->tu.dg, g->sc,
+                                                         g->partials);
+        prof_end(g, st, s);
+    }
+}
+
+// a CUDA graph of `graph_batch` iterations; every kernel returns at once after convergence
+mhd_status_t iteration_graph(mhd_grid_s* g, int prec, int nc, cudaGraphExec_t* out) {
+    cudaGraphExec_t& ge = g->iter_graph[prec][nc];
+    if (ge) {
+        *out = ge;
+        return MHD_OK;
+    }
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess)
+        return check_cuda(g, "iteration_graph: stream");
+    cudaGraph_t graph;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return check_cuda(g, "iteration_graph: begin capture");
+    }
+    for (int it = 0; it < g->graph_batch; it++) enqueue_iteration(g, cs, prec, nc);
+    cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return set_error(g, MHD_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&ge, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return set_error(g, MHD_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+    *out = ge;
+    return MHD_OK;
+}
+
+mhd_status_t read_scalars(mhd_grid_s* g) {
+    if (cudaMemcpyAsync(g->h_sc, g->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, g->stream) != cudaSuccess)
+        return check_cuda(g, "read scalars");
+    if (cudaStreamSynchronize(g->stream) != cudaSuccess) return check_cuda(g, "sync");
+    prof_flush(g);
+    return MHD_OK;
+}
+
+// run batches of iterations until the device flags completion
+mhd_status_t run_iterations(mhd_grid_s* g, int prec, int nc) {
+    cudaGraphExec_t ge = nullptr;
+    if (!g->prof) {
+        mhd_status_t st = iteration_graph(g, prec, nc, &ge);
+        if (st != MHD_OK) return st;
+    }
+    for (;;) {
+        if (read_scalars(g) != MHD_OK) return MHD_ERR_CUDA;
+        if (g->h_sc->done) return MHD_OK;
+        if (g->prof) {
+            // direct launches, each bracketed by events
+            for (int it = 0; it < 2 * g->graph_batch; it++) enqueue_iteration(g, g->stream, prec, nc);
+            if (check_cuda(g, "iteration launch") != MHD_OK) return MHD_ERR_CUDA;
+            continue;
+        }
+        // launch two batches per poll to overlap the host round trip with device work
+        if (cudaGraphLaunch(ge, g->stream) != cudaSuccess) return check_cuda(g, "graph launch");
+        if (cudaGraphLaunch(ge, g->stream) != cudaSuccess) return check_cuda(g, "graph launch");
+    }
+}
+
+// set the scalar block for a new solve (enqueued; no host sync)
+__global__ void k_setup(PcgScalars* sc, double tol, double inner_tol, int max_iter) {
+    sc->tol = tol;
+    sc->inner_tol = inner_tol;
+    sc->max_iter = max_iter;
+    sc->done = 0;
+    sc->iter = 0;
+    sc->total_iter = 0;
+    sc->outer = 0;
+    sc->outer_done = 0;
+    sc->rr_out = 0.0;
+    sc->count = 0u;
+}
+
+// mixed: the inner stop test reuses k_update's sqrt(rr) <= tol*sqrt(bb) by swapping in
+// tol := inner_tol and bb := rr_out for the inner solve, then restoring them
+__global__ void k_inner_begin(PcgScalars* sc, double* saved) {
+    saved[0] = sc->tol;
+    saved[1] = sc->bb;
+    sc->tol = sc->inner_tol;
+    sc->bb = sc->rr_out;
+}
+__global__ void k_inner_end(PcgScalars* sc, const double* saved) {
+    sc->tol = saved[0];
+    sc->bb = saved[1];
+}
+
+}  // namespace
+
+mhd_status_t solve(mhd_grid_s* g, const double* alpha_dev, int nc, const double* b, double* x,
+                   const double* x0, const mhd_params_t* prm, int* iters, int* outer, double* relres) {
+    const Dims d = g->d;
+    const bool mixed = (prm->precision == MHD_PREC_MIXED);
+    build_tables(g, alpha_dev, mixed);
+    k_setup<<<1, 1, 0, g->stream>>>(g->sc, prm->tol, prm->inner_tol, prm->max_iter);
+    const int blocks2 = grid_blocks(g, d.N / 2, kPerSmIter);
+    if (!mixed) {
+        k_init64<<<blocks2, kThreads, 0, g->stream>>>(d, nc, b, x0, g->x64, g->r64, g->p64, g->t64, g->tu, g->sc,
+                                                      g->partials);
+        mhd_status_t st = check_cuda(g, "pcg init");
+        if (st != MHD_OK) return st;
+        st = run_iterations(g, 0, nc);
+        if (st != MHD_OK) return st;
+        k_finish64<<<blocks2, kThreads, 0, g->stream>>>(d, nc, g->x64, x, g->t64.s, g->sc);
+        if ((st = check_cuda(g, "pcg finish")) != MHD_OK) return st;
+        if (read_scalars(g) != MHD_OK) return MHD_ERR_CUDA;
+        const PcgScalars& h = *g->h_sc;
+        if (iters) *iters = h.iter;
+        if (outer) *outer = 0;
+        if (relres) *relres = (h.bb > 0) ? std::sqrt(h.rr) / std::sqrt(h.bb) : 0.0;
+        if (h.done == 1) return MHD_OK;
+        if (h.done == 3) return set_error(g, MHD_ERR_NONFINITE, "pcg: non-finite value in a reduction");
+        return set_error(g, MHD_ERR_NOCONV, "pcg: no convergence within max_iter");
+    }
+    // mixed precision: x starts as x0 in FP64 (in place in the caller's x)
+    if (x != x0)
+        cudaMemcpyAsync(x, x0, sizeof(double) * nc * d.N, cudaMemcpyDeviceToDevice, g->stream);
+    double* saved = g->partials + kMaxBlocks * kPartialsPerBlock;  // spare doubles past the partials
+    int outer_done = 0;
+    for (int o = 0; o <= prm->max_outer; o++) {
+        const int ps = prof_begin(g, g->stream, MHD_KERNEL_OUTER_RES);
+        k_outer_res<2><<<blocks2, kThreads, 0, g->stream>>>(d, nc, b, x, g->r32, g->p32, g->x32, g->t64, g->tu,
+                                                            g->sc, g->partials, o == 0 ? 1 : 0);
+        prof_end(g, g->stream, ps);
+        mhd_status_t st = check_cuda(g, "outer residual");
+        if (st != MHD_OK) return st;
+        if (read_scalars(g) != MHD_OK) return MHD_ERR_CUDA;
+        outer_done = g->h_sc->outer_done;
+        if (outer_done || o == prm->max_outer) break;
+        k_inner_begin<<<1, 1, 0, g->stream>>>(g->sc, saved);
+        st = run_iterations(g, 1, nc);
+        if (st != MHD_OK) return st;
+        k_inner_end<<<1, 1, 0, g->stream>>>(g->sc, saved);
+        if (g->h_sc->done == 3) break;
+        k_correct<<<blocks2, kThreads, 0, g->stream>>>(d, nc, x, g->x32, g->t64.s, g->sc);
+        if ((st = check_cuda(g, "correction")) != MHD_OK) return st;
+    }
+    if (read_scalars(g) != MHD_OK) return MHD_ERR_CUDA;
+    const PcgScalars& h = *g->h_sc;
+    if (iters) *iters = h.total_iter;
+    if (outer) *outer = h.outer;
+    if (relres) *relres = (h.bb > 0) ? std::sqrt(h.rr_out) / std::sqrt(h.bb) : 0.0;
+    if (h.bb == 0.0) {
+        cudaMemsetAsync(x, 0, sizeof(double) * nc * d.N, g->stream);
+        return MHD_OK;
+    }
+    if (h.outer_done == 1) return MHD_OK;
+    if (h.outer_done == 3 || h.done == 3) return set_error(g, MHD_ERR_NONFINITE, "pcg: non-finite value");
+    return set_error(g, MHD_ERR_NOCONV, "pcg (mixed): no convergence within max_outer");
+}
+
+}  // namespace mhd

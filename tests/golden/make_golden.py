@@ -1,0 +1,56 @@
+"""Write the oracle's record of one zero-beta step at full size (tests/golden/*.json).
+
+Calls only the CPU oracle and the seeded input generator. The record holds the step
+coefficients, the PCG iteration counts and residuals, per-field L2 norms and the oracle's values
+at seeded sample positions. It serves the full-size GPU parity test (sampled outputs) and gives
+the CPU baseline the oracle's own iteration counts at this size.
+
+    python tests/golden/make_golden.py fluxrope_256x256x512
+"""
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import oracle as O  # noqa: E402
+from paper_1811_02605_gb300 import inputs as I  # noqa: E402
+
+NSAMPLE = 2000
+
+
+def sample_index(shape, seed):
+    rng = np.random.default_rng(seed)
+    n = int(np.prod(shape))
+    return np.sort(rng.choice(n, size=min(NSAMPLE, n), replace=False))
+
+
+def main(name):
+    w, st = I.workload(name)
+    d = w["desc"]
+    g = O.Grid.from_desc(d)
+    t0 = time.time()
+    out, info = g.step(st, nu=w["nu"], eta=w["eta"], cfl=w["cfl"], tol=w["tol"])
+    wall = time.time() - t0
+    rec = dict(workload=name, desc=dict(nr=d.nr, nt=d.nt, np=d.np, r0=d.r0, r1=d.r1, stretch=d.stretch),
+               params=dict(nu=w["nu"], eta=w["eta"], cfl=w["cfl"], tol=w["tol"]),
+               info={k: (v if not isinstance(v, np.floating) else float(v)) for k, v in info.items()},
+               oracle_step_seconds=wall, fields={})
+    rec["info"] = {k: ([float(x) for x in v] if isinstance(v, list) else float(v)) for k, v in info.items()}
+    for k, a in out.items():
+        idx = sample_index(a.shape, sum(map(ord, k)) + 7)
+        rec["fields"][k] = dict(shape=list(a.shape), l2=float(np.linalg.norm(a)),
+                                l2_initial=float(np.linalg.norm(st[k])),
+                                sample_index=idx.tolist(), sample=a.ravel()[idx].tolist())
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"{name}_oracle_step1.json")
+    with open(path, "w") as f:
+        json.dump(rec, f)
+    print(path, rec["info"], wall)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1] if len(sys.argv) > 1 else "fluxrope_256x256x512")
