@@ -180,6 +180,23 @@ mhd_status_t mhd_adjoint_step(mhd_grid_t grid, const mhd_params_t* params,
                               const mhd_fields_t* state_n, double dt,
                               const mhd_fields_t* adj_np1, mhd_fields_t* adj_n);
 
+/* The momentum force of mhd_force for callers that cannot allocate device memory (a host code
+ * that owns all device memory under a fixed budget, a latency-bound loop where cudaMalloc may
+ * synchronise the device, an allocator policy that forbids new allocations). The paper has no
+ * counterpart: it is an interface variant, not part of the method. No grid object is needed:
+ * the grid is described by `desc`, and the metric tables, the current density on edges and the
+ * polar ring sums are kept in one static device array of 10 MiB (1,310,720 doubles) that every
+ * GPU loading this library holds until the process exits. Limits: at most 262,144 cells and the
+ * tables and edge arrays must fit that array; larger grids return MHD_ERR_ARG. The call
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library routine). The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture. All calls share the array: calls whose work
+ * overlaps on the GPU (different streams or host threads) race on it. Inputs and output as in
+ * mhd_force (device pointers); work is enqueued on `cuda_stream` (a cudaStream_t, NULL = legacy
+ * default stream). Errors: MHD_ERR_ARG (null pointer, bad or too large grid), MHD_ERR_CUDA. */
+mhd_status_t mhd_force_noalloc(const mhd_grid_desc_t* desc, const mhd_fields_t* fields, double dt,
+                               double* b, void* cuda_stream);
+
 /* Diagnostics (not part of the method): device time of the library's kernels, measured with
  * CUDA events recorded on the grid's stream immediately before and after each launch, summed
  * per kernel while profiling is enabled. Enabling resets the counters and makes the PCG loop

@@ -27,7 +27,8 @@ PREC_FP64, PREC_MIXED = 0, 1
 # C ABI symbols declared in include/mhd.h
 SYMBOLS = ["mhd_grid_create", "mhd_grid_destroy", "mhd_grid_sizes", "mhd_step_coeffs", "mhd_step",
            "mhd_apply_operator", "mhd_force", "mhd_induction", "pcg_solve", "pcg_solve_batched",
-           "mhd_adjoint_step", "mhd_profile_enable", "mhd_profile_read", "mhd_last_error"]
+           "mhd_adjoint_step", "mhd_force_noalloc", "mhd_profile_enable", "mhd_profile_read",
+           "mhd_last_error"]
 
 KERNELS = ["pupdate64", "spmv64", "update64", "pupdate32", "spmv32", "update32", "outer_res", "force",
            "induction", "coeffs"]
@@ -94,6 +95,7 @@ def lib():
                                             C.POINTER(C.c_double)]
             L.mhd_adjoint_step.argtypes = [vp, C.POINTER(Params), C.POINTER(Fields), d,
                                            C.POINTER(Fields), C.POINTER(Fields)]
+            L.mhd_force_noalloc.argtypes = [C.POINTER(GridDesc), C.POINTER(Fields), d, vp, vp]
             L.mhd_profile_enable.argtypes = [vp, i]
             L.mhd_profile_read.argtypes = [vp, i, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
             L.mhd_last_error.argtypes = [vp]
@@ -259,3 +261,17 @@ def mhd_profile_read(grid: Grid) -> dict:
         _check(lib().mhd_profile_read(grid.handle, k, C.byref(ms), C.byref(n)), grid)
         out[name] = (ms.value, n.value)
     return out
+
+
+def mhd_force_noalloc(desc: GridDesc, fields: Fields, dt: float, b, stream=None):
+    """Momentum force without a grid object and without any device allocation (scratch lives in
+    a static device array of the library; see include/mhd.h). Returns the status code."""
+    import torch
+    if stream is None:
+        s = torch.cuda.current_stream().cuda_stream
+    elif hasattr(stream, "cuda_stream"):
+        s = stream.cuda_stream
+    else:
+        s = int(stream)
+    st = lib().mhd_force_noalloc(C.byref(desc), C.byref(fields), float(dt), _ptr(b, "b"), C.c_void_p(s))
+    return st
