@@ -111,10 +111,16 @@ def dist_env():
     return ws, rank, local
 
 
-def gen_state(name):
+def gen_state(name, grid=None):
+    """Workload inputs; `grid` ("NRxNTxNP") keeps the workload's physics on another grid size."""
     from paper_1811_02605_gb300 import inputs as I
-    w, st = I.workload(name)
-    return w, st
+    if grid is None:
+        return I.workload(name)
+    nr, nt, np_ = (int(x) for x in grid.lower().split("x"))
+    w = dict(I.WORKLOADS[name])
+    d0 = w["desc"]
+    w["desc"] = I.GridDesc(nr, nt, np_, d0.r0, d0.r1, d0.stretch)
+    return w, I.initial_state(w["desc"], w["index"], w["rope"])
 
 
 # ----------------------------------------------------------------------------------------------
@@ -169,7 +175,7 @@ def run_reference(args):
             dist.barrier()
             dist.destroy_process_group()
             return
-    w, st = gen_state(args.workload)
+    w, st = gen_state(args.workload, args.grid)
     iters = oracle_iteration_counts(args.workload) or args.ref_iters
     vals = []
     sample = ""
@@ -209,7 +215,7 @@ def run_ours(args):
     B.build()
     import paper_1811_02605_gb300 as P
 
-    w, st0 = gen_state(args.workload)
+    w, st0 = gen_state(args.workload, args.grid)
     d = w["desc"]
     N = d.nr * d.nt * d.np
     stream = torch.cuda.Stream()
@@ -348,6 +354,31 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_profile_case(args):
+    """A short, fixed piece of the hot path for profilers: the first SI system of the workload,
+    `--profile-iters` FP64 CG iterations, then one mixed-precision outer pass with the same cap."""
+    import torch
+    from paper_1811_02605_gb300 import build as B
+    B.build()
+    import paper_1811_02605_gb300 as P
+    w, st0 = gen_state(args.workload, args.grid)
+    d = w["desc"]
+    g = P.mhd_grid_create(d.nr, d.nt, d.np, d.r0, d.r1, d.stretch)
+    ds = {k: torch.from_numpy(v).cuda() for k, v in st0.items()}
+    f = P.make_fields(ds["br"], ds["bt"], ds["bp"], ds["vr"], ds["vt"], ds["vp"])
+    c = P.mhd_step_coeffs(g, P.make_params(nu=w["nu"], cfl=w["cfl"]), f)
+    b = torch.empty((3, d.nr, d.nt, d.np), dtype=torch.float64, device="cuda")
+    P.mhd_force(g, f, c["dt"], b)
+    out = {}
+    for name, prec in (("fp64", P.PREC_FP64), ("mixed", P.PREC_MIXED)):
+        x = torch.zeros_like(b)
+        prm = P.make_params(tol=1e-30, max_iter=args.profile_iters, precision=prec, max_outer=1)
+        st, it, ou, rr = P.pcg_solve(g, c["alpha_si"], b, x, prm)
+        out[name] = dict(status=P.STATUS_NAMES[st], iters=it, outer=ou, relres=rr)
+    torch.cuda.synchronize()
+    print(json.dumps(dict(profile_case=f"{d.nr}x{d.nt}x{d.np}", alpha_si=c["alpha_si"], **out)), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -355,13 +386,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--grid", default=None, help="NRxNTxNP: the workload's physics on another grid")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run a few CG iterations of the first SI solve (for ncu captures) and exit")
+    ap.add_argument("--profile-iters", type=int, default=6)
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-iters", type=int, default=1000,
                     help="PCG iterations per step assumed by the reference arm if no oracle record exists")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile_case:
+        run_profile_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
