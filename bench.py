@@ -354,6 +354,84 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def ktilde2_max(d):
+    """max over cells of 1/dr^2 + 1/(r dtheta)^2 + 1/(r sin(theta) dphi)^2 (the SI coefficient's
+    grid factor), for choosing each batched system's alpha."""
+    import numpy as np
+    from paper_1811_02605_gb300 import inputs as I
+    r = I.radial_nodes(d)
+    rc = 0.5 * (r[1:] + r[:-1])
+    dr = r[1:] - r[:-1]
+    sc = np.sin((np.arange(d.nt) + 0.5) * math.pi / d.nt)
+    k2 = (1 / dr ** 2)[:, None] + (1 / (rc * math.pi / d.nt) ** 2)[:, None] + \
+        1 / (rc[:, None] * sc[None, :] * 2 * math.pi / d.np) ** 2
+    return float(k2.max())
+
+
+def run_batched(args):
+    """64 independent FP64 solves on grids of uneven size (nt in {32, 48, ..., 128}, nr = nt,
+    np = 2 nt, stretch in [1.02, 1.08]) with smooth seeded right-hand sides, in one persistent
+    launch, against the same 64 solves one after another. Each alpha gives its system the
+    conditioning of the 32x32x64 parity workload's semi-implicit solve at step 0."""
+    import numpy as np
+    import torch
+    from paper_1811_02605_gb300 import build as B
+    B.build()
+    import paper_1811_02605_gb300 as P
+    from paper_1811_02605_gb300 import inputs as I
+    X0 = 4623.0
+    items = I.batched_items(args.batch)
+    grids, bs, alphas, cells = [], [], [], 0
+    for it in items:
+        d = it["desc"]
+        g = P.mhd_grid_create(d.nr, d.nt, d.np, d.r0, d.r1, d.stretch)
+        f = I.smooth_field(d, it["modes"])
+        r = I.radial_nodes(d)
+        th = np.arange(d.nt + 1) * math.pi / d.nt
+        c = np.cos(th)
+        c[0], c[-1] = 1.0, -1.0
+        vol = ((r[1:] ** 3 - r[:-1] ** 3) / 3)[:, None] * (c[:-1] - c[1:])[None, :] * (2 * math.pi / d.np)
+        bs.append(torch.from_numpy(np.ascontiguousarray(f * vol[None, :, :, None])).cuda())
+        grids.append(g)
+        alphas.append(X0 / ktilde2_max(d))
+        cells += d.nr * d.nt * d.np
+    prm = P.make_params(tol=1e-9, max_iter=50000)
+    xs = [torch.zeros_like(b) for b in bs]
+    t0 = time.perf_counter()
+    st, its, rr = P.pcg_solve_batched(grids, alphas, bs, xs, prm)  # first call: plan + autotune
+    t_first = time.perf_counter() - t0
+    times = []
+    for _ in range(args.steps):
+        for x in xs:
+            x.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st, its, rr = P.pcg_solve_batched(grids, alphas, bs, xs, prm)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    seq = []
+    for _ in range(max(1, args.steps // 2)):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for g, a, b in zip(grids, alphas, bs):
+            x = torch.zeros_like(b)
+            P.pcg_solve(g, a, b, x, prm)
+        e1.record()
+        torch.cuda.synchronize()
+        seq.append(e0.elapsed_time(e1))
+    ms = min(times)
+    # algorithmic bytes: 144 B per cell per CG iteration, summed over systems
+    bytes_alg = sum(144.0 * it["desc"].nr * it["desc"].nt * it["desc"].np * n for it, n in zip(items, its))
+    print(json.dumps(dict(workload=f"batched{args.batch}", status=P.STATUS_NAMES[st], ms_per_batch=round(ms, 3),
+                          ms_sequential_single_solves=round(min(seq), 3), speedup=round(min(seq) / ms, 3),
+                          first_call_ms_incl_autotune=round(1e3 * t_first, 1), total_cells=cells,
+                          iters_min=min(its), iters_max=max(its), max_relres=max(rr),
+                          pcg_gbs_algorithmic=round(bytes_alg / (ms * 1e-3) / 1e9, 1))), flush=True)
+
+
 def run_profile_case(args):
     """A short, fixed piece of the hot path for profilers: the first SI system of the workload,
     `--profile-iters` FP64 CG iterations, then one mixed-precision outer pass with the same cap."""
@@ -390,6 +468,8 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="run a few CG iterations of the first SI solve (for ncu captures) and exit")
     ap.add_argument("--profile-iters", type=int, default=6)
+    ap.add_argument("--batched", action="store_true", help="time the 64-system batched solve and exit")
+    ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -398,6 +478,8 @@ def main():
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args)
+    elif args.batched:
+        run_batched(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

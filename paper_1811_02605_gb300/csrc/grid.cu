@@ -276,6 +276,7 @@ extern "C" mhd_status_t mhd_grid_create(const mhd_grid_desc_t* desc, void* cuda_
 extern "C" mhd_status_t mhd_grid_destroy(mhd_grid_t g) {
     if (!g) return MHD_OK;
     cudaStreamSynchronize(g->stream);
+    batched_forget(g);
     for (auto& row : g->iter_graph)
         for (auto& ge : row)
             if (ge) cudaGraphExecDestroy(ge);

@@ -158,6 +158,7 @@ mhd_status_t solve(mhd_grid_s* g, const double* alpha_dev, int nc, const double*
                    double* relres);
 
 mhd_status_t set_error(mhd_grid_s* g, mhd_status_t st, const std::string& msg);
+void batched_forget(mhd_grid_s* g);   // batched.cu: drop cached plans that use g
 
 // kernel timing: bracket a launch with events when profiling is on (returns the slot or -1)
 int prof_begin(mhd_grid_s* g, cudaStream_t st, int kernel);

@@ -1,0 +1,92 @@
+"""Batched persistent PCG (one cooperative launch over many systems of different sizes) against
+single solves of the same systems and against the oracle, system by system; plus the bounded
+barrier's timeout path (fault injected on the host side: a barrier that can never fill)."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_1811_02605_gb300 as P
+from paper_1811_02605_gb300 import inputs as I
+from tests.gpu_util import rel_l2, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+X0 = 4623.0  # C_w^2/(1-C_f)^2 - 1 of the 32x32x64 parity workload at step 0: SI-like conditioning
+
+
+def _items(n, seed=5):
+    rng = np.random.default_rng(seed)
+    items = []
+    for s in range(n):
+        nt = int(rng.choice([6, 8, 12, 16, 24]))
+        d = I.GridDesc(nt, nt, 2 * nt, 1.0, 20.0, float(rng.uniform(1.02, 1.08)))
+        og = O.Grid.from_desc(d)
+        alpha = X0 / og.ktilde2().max()
+        b = I.smooth_field(d, I.draw_modes(rng, 1.0, 1.0 / 20.0)) * og.volumes()[None, :, :, None]
+        items.append((d, og, alpha, b))
+    return items
+
+
+def _run_batched(items, prm):
+    grids = [P.mhd_grid_create(d.nr, d.nt, d.np, d.r0, d.r1, d.stretch) for d, _, _, _ in items]
+    bs = [to_dev(b) for _, _, _, b in items]
+    xs = [torch.zeros_like(b) for b in bs]
+    st, it, rr = P.pcg_solve_batched(grids, [a for _, _, a, _ in items], bs, xs, prm)
+    torch.cuda.synchronize()
+    return grids, bs, xs, st, it, rr
+
+
+def test_batched_matches_single_solves_and_oracle():
+    items = _items(7)
+    prm = P.make_params(tol=1e-9, max_iter=20000)
+    grids, bs, xs, st, it, rr = _run_batched(items, prm)
+    assert st == P.MHD_OK
+    for s, (d, og, alpha, b) in enumerate(items):
+        x1 = torch.zeros_like(bs[s])
+        st1, it1, _, rr1 = P.pcg_solve(grids[s], alpha, bs[s], x1, prm)
+        assert st1 == P.MHD_OK and abs(it[s] - it1) <= 1, (s, it[s], it1)
+        assert rr[s] <= 1e-9
+        xo, ito, _, _ = og.pcg(alpha, b, tol=1e-9)
+        assert abs(it[s] - ito) <= 1, (s, it[s], ito)
+        if it[s] == ito:
+            assert rel_l2(to_np(xs[s]), xo) < 1e-11, s
+        assert rel_l2(to_np(xs[s]), xo) < 1e-8
+    # a replay of the same plan (CUDA graph) from the same start is bit-for-bit identical
+    xs2 = [torch.zeros_like(b) for b in bs]
+    st2, it2, rr2 = P.pcg_solve_batched(grids, [a for _, _, a, _ in items], bs, xs2, prm)
+    assert st2 == P.MHD_OK and it2 == it
+    for s in range(len(items)):
+        assert torch.equal(xs2[s], xs[s])
+    # another start (x0 = 1): different trajectory, same tolerance met
+    xs3 = [torch.ones_like(b) for b in bs]
+    st3, it3, rr3 = P.pcg_solve_batched(grids, [a for _, _, a, _ in items], bs, xs3, prm)
+    assert st3 == P.MHD_OK and max(rr3) <= 1e-9
+
+
+def test_batched_edge_cases():
+    items = _items(3, seed=8)
+    d, og, alpha, b = items[1]
+    items[1] = (d, og, alpha, np.zeros_like(b))  # b = 0 -> x = 0, 0 iterations
+    grids, bs, xs, st, it, rr = _run_batched(items, P.make_params(tol=1e-9))
+    assert st == P.MHD_OK and it[1] == 0 and torch.all(xs[1] == 0)
+    # iteration cap reached -> NOCONV, iterate kept
+    grids, bs, xs, st, it, rr = _run_batched(_items(3, seed=9), P.make_params(tol=1e-14, max_iter=3))
+    assert st == P.MHD_ERR_NOCONV and all(i == 3 for i in it)
+
+
+def test_batched_barrier_timeout_returns_status(monkeypatch):
+    items = _items(2, seed=11)
+    monkeypatch.setenv("MHD_FAULT_BARRIER_MS", "200")
+    grids = [P.mhd_grid_create(d.nr, d.nt, d.np, d.r0, d.r1, d.stretch) for d, _, _, _ in items]
+    bs = [to_dev(b) for _, _, _, b in items]
+    xs = [torch.zeros_like(b) for b in bs]
+    with pytest.raises(P.MhdError) as e:
+        P.pcg_solve_batched(grids, [a for _, _, a, _ in items], bs, xs, P.make_params())
+    assert e.value.status == P.MHD_ERR_TIMEOUT
+    # the context is still usable: the same call without the fault succeeds
+    monkeypatch.delenv("MHD_FAULT_BARRIER_MS")
+    st, it, rr = P.pcg_solve_batched(grids, [a for _, _, a, _ in items], bs, xs, P.make_params())
+    assert st == P.MHD_OK
