@@ -70,7 +70,7 @@ def _declare(L):
     L.og_step.argtypes = [vp, d, d, d, d, d, d, d, i, _dp, _dp, _dp, _dp, _dp]
     if hasattr(L, "og_adjoint_step"):
         L.og_adjoint_step.restype = i
-        L.og_adjoint_step.argtypes = [vp, d, d, d, d, d, i] + [_dp] * 12
+        L.og_adjoint_step.argtypes = [vp, d, d, d, d, d, d, i] + [_dp] * 12
 
 
 def _c(a):
@@ -206,3 +206,19 @@ class Grid:
                    alpha_nu=info[4], iters=[int(info[5]), int(info[6]), int(info[7])],
                    relres=list(info[8:11]))
         return out, inf
+
+
+def _adjoint(self, state, lam, dt, asi, nu=1e-3, eta=0.0, cfl=0.4, tol=1e-13, max_iter=200000):
+    """Cotangent of state n from the cotangent `lam` of state n+1 (dicts with br, bt, bp, vr, vt, vp)."""
+    v = np.ascontiguousarray(np.stack([state["vr"], state["vt"], state["vp"]]), dtype=np.float64)
+    lv1 = np.ascontiguousarray(np.stack([lam["vr"], lam["vt"], lam["vp"]]), dtype=np.float64)
+    s = self.shapes
+    lv = np.empty_like(v)
+    lbr, lbt, lbp = np.empty(s["br"]), np.empty(s["bt"]), np.empty(s["bp"])
+    st = self.L.og_adjoint_step(self.h, nu, eta, cfl, dt, asi, tol, max_iter, v, _c(state["br"]), _c(state["bt"]),
+                                _c(state["bp"]), lv1, _c(lam["br"]), _c(lam["bt"]), _c(lam["bp"]), lv, lbr, lbt, lbp)
+    out = dict(br=lbr, bt=lbt, bp=lbp, vr=lv[0].copy(), vt=lv[1].copy(), vp=lv[2].copy())
+    return out, st
+
+
+Grid.adjoint_step = _adjoint

@@ -689,3 +689,404 @@ int og_step(const og_grid* g, double nu, double eta, double cfl, double dt_fixed
     edges_free(e);
     return status;
 }
+
+/* =============================================================================================
+ * Adjoint of the step (reading P15: dt, alpha_SI, alpha_nu and the upwind directions frozen at
+ * the forward values). Every linear piece of the forward step has its transpose written below as
+ * a loop over the same stencil that scatters the output cotangent back onto the inputs; the
+ * bilinear pieces (v x B, J x B, (v.grad)v) are linearised at the recomputed forward state. The
+ * solves use M^-T = M^-1 (M symmetric).
+ * =========================================================================================== */
+
+/* transpose of og_ct's map E -> dB = -dt curl_h E: lam_E += -dt (circulation weights) lam_B */
+static void ct_T(const og_grid* g, double dt, const double* lbr, const double* lbt, const double* lbp,
+                 double* ler, double* let, double* lep) {
+    int nr = g->nr, nt = g->nt, np = g->np;
+    double dth = g->dth, dph = g->dph;
+    for (int i = 0; i <= nr; i++) {
+        double ri = g->r[i];
+        double lt = ri * dth;
+        for (int j = 0; j < nt; j++) {
+            double area = ri * ri * (g->cn[j] - g->cn[j + 1]) * dph;
+            double lpj = ri * g->sn[j] * dph, lpj1 = ri * g->sn[j + 1] * dph;
+            for (int k = 0; k < np; k++) {
+                double w = -dt * lbr[IDX(g, i, j, k)] / area;
+                let[IDX(g, i, j, k)] += w * lt;
+                lep[IDXT(g, i, j + 1, k)] += w * lpj1;
+                let[IDX(g, i, j, KP(g, k))] -= w * lt;
+                lep[IDXT(g, i, j, k)] -= w * lpj;
+            }
+        }
+    }
+    for (int i = 0; i < nr; i++) {
+        double ri = g->r[i], ro = g->r[i + 1];
+        double lr = ro - ri;
+        for (int j = 1; j < nt; j++) {
+            double area = g->sn[j] * 0.5 * (ro * ro - ri * ri) * dph;
+            double lpi = ri * g->sn[j] * dph, lpo = ro * g->sn[j] * dph;
+            for (int k = 0; k < np; k++) {
+                double w = -dt * lbt[IDXT(g, i, j, k)] / area;
+                lep[IDXT(g, i, j, k)] += w * lpi;
+                ler[IDXT(g, i, j, KP(g, k))] += w * lr;
+                lep[IDXT(g, i + 1, j, k)] -= w * lpo;
+                ler[IDXT(g, i, j, k)] -= w * lr;
+            }
+        }
+    }
+    for (int i = 0; i < nr; i++) {
+        double ri = g->r[i], ro = g->r[i + 1];
+        double lr = ro - ri;
+        double area = 0.5 * (ro * ro - ri * ri) * dth;
+        for (int j = 0; j < nt; j++)
+            for (int k = 0; k < np; k++) {
+                double w = -dt * lbp[IDX(g, i, j, k)] / area;
+                ler[IDXT(g, i, j, k)] += w * lr;
+                let[IDX(g, i + 1, j, k)] += w * ro * dth;
+                ler[IDXT(g, i, j + 1, k)] -= w * lr;
+                let[IDX(g, i, j, k)] -= w * ri * dth;
+            }
+    }
+}
+
+/* transpose of the centre -> edge averaging of E (og_efield_edges): lam_Ec += weights lam_E */
+static void eedges_T(const og_grid* g, const double* ler, const double* let, const double* lep, double* lec) {
+    int nr = g->nr, nt = g->nt, np = g->np;
+    long long N = g->N;
+    double* Er = lec;
+    double* Et = lec + N;
+    double* Ep = lec + 2 * N;
+    for (int i = 0; i < nr; i++) {
+        double sn = 0.0, ss = 0.0;
+        for (int k = 0; k < np; k++) { sn += ler[IDXT(g, i, 0, k)]; ss += ler[IDXT(g, i, nt, k)]; }
+        for (int k = 0; k < np; k++) { Er[IDX(g, i, 0, k)] += sn / np; Er[IDX(g, i, nt - 1, k)] += ss / np; }
+        for (int j = 1; j < nt; j++)
+            for (int k = 0; k < np; k++) {
+                int km = KM(g, k);
+                double w = 0.25 * ler[IDXT(g, i, j, k)];
+                Er[IDX(g, i, j - 1, km)] += w; Er[IDX(g, i, j - 1, k)] += w;
+                Er[IDX(g, i, j, km)] += w; Er[IDX(g, i, j, k)] += w;
+            }
+    }
+    for (int i = 0; i <= nr; i++)
+        for (int j = 0; j < nt; j++)
+            for (int k = 0; k < np; k++) {
+                int km = KM(g, k);
+                double l = let[IDX(g, i, j, k)];
+                if (i == 0) continue;
+                if (i == nr) { Et[IDX(g, nr - 1, j, km)] += 0.5 * l; Et[IDX(g, nr - 1, j, k)] += 0.5 * l; }
+                else {
+                    Et[IDX(g, i - 1, j, km)] += 0.25 * l; Et[IDX(g, i - 1, j, k)] += 0.25 * l;
+                    Et[IDX(g, i, j, km)] += 0.25 * l; Et[IDX(g, i, j, k)] += 0.25 * l;
+                }
+            }
+    for (int i = 0; i <= nr; i++)
+        for (int j = 0; j <= nt; j++)
+            for (int k = 0; k < np; k++) {
+                double l = lep[IDXT(g, i, j, k)];
+                if (j == 0 || j == nt || i == 0) continue;
+                if (i == nr) { Ep[IDX(g, nr - 1, j - 1, k)] += 0.5 * l; Ep[IDX(g, nr - 1, j, k)] += 0.5 * l; }
+                else {
+                    Ep[IDX(g, i - 1, j - 1, k)] += 0.25 * l; Ep[IDX(g, i - 1, j, k)] += 0.25 * l;
+                    Ep[IDX(g, i, j - 1, k)] += 0.25 * l; Ep[IDX(g, i, j, k)] += 0.25 * l;
+                }
+            }
+}
+
+/* transpose of the face -> centre averaging of B (bcentre_at) */
+static void bcentre_T(const og_grid* g, const double* lbc, double* lbr, double* lbt, double* lbp) {
+    int nt = g->nt;
+    long long N = g->N;
+    for (int i = 0; i < g->nr; i++)
+        for (int j = 0; j < nt; j++)
+            for (int k = 0; k < g->np; k++) {
+                long long c = IDX(g, i, j, k);
+                lbr[IDX(g, i, j, k)] += 0.5 * lbc[c];
+                lbr[IDX(g, i + 1, j, k)] += 0.5 * lbc[c];
+                if (j == 0) lbt[IDXT(g, i, 1, k)] += lbc[N + c];
+                else if (j == nt - 1) lbt[IDXT(g, i, nt - 1, k)] += lbc[N + c];
+                else { lbt[IDXT(g, i, j, k)] += 0.5 * lbc[N + c]; lbt[IDXT(g, i, j + 1, k)] += 0.5 * lbc[N + c]; }
+                lbp[IDX(g, i, j, k)] += 0.5 * lbc[2 * N + c];
+                lbp[IDX(g, i, j, KP(g, k))] += 0.5 * lbc[2 * N + c];
+            }
+}
+
+/* transpose of the edge -> centre averaging of J (current_centre_from_edges) */
+static void jcentre_T(const og_grid* g, const double* ljc, double* ljr, double* ljt, double* ljp) {
+    int nt = g->nt;
+    long long N = g->N;
+    for (int i = 0; i < g->nr; i++)
+        for (int j = 0; j < nt; j++)
+            for (int k = 0; k < g->np; k++) {
+                long long c = IDX(g, i, j, k);
+                int kp = KP(g, k);
+                double a = 0.25 * ljc[c], b = 0.25 * ljc[N + c], e = ljc[2 * N + c];
+                ljr[IDXT(g, i, j, k)] += a; ljr[IDXT(g, i, j, kp)] += a;
+                ljr[IDXT(g, i, j + 1, k)] += a; ljr[IDXT(g, i, j + 1, kp)] += a;
+                ljt[IDX(g, i, j, k)] += b; ljt[IDX(g, i, j, kp)] += b;
+                ljt[IDX(g, i + 1, j, k)] += b; ljt[IDX(g, i + 1, j, kp)] += b;
+                if (j == 0) { ljp[IDXT(g, i, 1, k)] += 0.5 * e; ljp[IDXT(g, i + 1, 1, k)] += 0.5 * e; }
+                else if (j == nt - 1) { ljp[IDXT(g, i, nt - 1, k)] += 0.5 * e; ljp[IDXT(g, i + 1, nt - 1, k)] += 0.5 * e; }
+                else {
+                    ljp[IDXT(g, i, j, k)] += 0.25 * e; ljp[IDXT(g, i, j + 1, k)] += 0.25 * e;
+                    ljp[IDXT(g, i + 1, j, k)] += 0.25 * e; ljp[IDXT(g, i + 1, j + 1, k)] += 0.25 * e;
+                }
+            }
+}
+
+/* transpose of og_current_edges (B faces -> J edges) */
+static void curlJ_T(const og_grid* g, const double* ljr, const double* ljt, const double* ljp, double* lbr,
+                    double* lbt, double* lbp) {
+    int nr = g->nr, nt = g->nt, np = g->np;
+    double dth = g->dth, dph = g->dph;
+    for (int i = 0; i < nr; i++) {
+        double rc = g->rc[i];
+        double cap_n = rc * rc * (1.0 - g->cc[0]) * 2.0 * M_PI;
+        double cap_s = rc * rc * (1.0 + g->cc[nt - 1]) * 2.0 * M_PI;
+        double sn = 0.0, ss = 0.0;
+        for (int k = 0; k < np; k++) { sn += ljr[IDXT(g, i, 0, k)]; ss += ljr[IDXT(g, i, nt, k)]; }
+        for (int k = 0; k < np; k++) {
+            lbp[IDX(g, i, 0, k)] += sn / cap_n * (rc * g->sc[0] * dph);
+            lbp[IDX(g, i, nt - 1, k)] -= ss / cap_s * (rc * g->sc[nt - 1] * dph);
+        }
+        for (int j = 1; j < nt; j++) {
+            double area = rc * rc * (g->cc[j - 1] - g->cc[j]) * dph;
+            for (int k = 0; k < np; k++) {
+                double w = ljr[IDXT(g, i, j, k)] / area;
+                lbp[IDX(g, i, j, k)] += w * rc * g->sc[j] * dph;
+                lbp[IDX(g, i, j - 1, k)] -= w * rc * g->sc[j - 1] * dph;
+                lbt[IDXT(g, i, j, k)] -= w * rc * dth;
+                lbt[IDXT(g, i, j, KM(g, k))] += w * rc * dth;
+            }
+        }
+    }
+    for (int i = 0; i <= nr; i++) {
+        double rlo = (i > 0) ? g->rc[i - 1] : 2.0 * g->r0 - g->rc[0];
+        double rhi = (i < nr) ? g->rc[i] : 2.0 * g->r[nr] - g->rc[nr - 1];
+        int ilo = (i > 0) ? i - 1 : 0;
+        int ihi = (i < nr) ? i : nr - 1;
+        for (int j = 0; j < nt; j++) {
+            double area = g->sc[j] * 0.5 * (rhi * rhi - rlo * rlo) * dph;
+            for (int k = 0; k < np; k++) {
+                double w = ljt[IDX(g, i, j, k)] / area;
+                lbp[IDX(g, ilo, j, k)] += w * rlo * g->sc[j] * dph;
+                lbr[IDX(g, i, j, k)] += w * (rhi - rlo);
+                lbp[IDX(g, ihi, j, k)] -= w * rhi * g->sc[j] * dph;
+                lbr[IDX(g, i, j, KM(g, k))] -= w * (rhi - rlo);
+            }
+        }
+        double area = 0.5 * (rhi * rhi - rlo * rlo) * dth;
+        for (int j = 1; j < nt; j++)
+            for (int k = 0; k < np; k++) {
+                double w = ljp[IDXT(g, i, j, k)] / area;
+                lbr[IDX(g, i, j - 1, k)] += w * (rhi - rlo);
+                lbt[IDXT(g, ihi, j, k)] += w * rhi * dth;
+                lbr[IDX(g, i, j, k)] -= w * (rhi - rlo);
+                lbt[IDXT(g, ilo, j, k)] -= w * rlo * dth;
+            }
+    }
+}
+
+/* lam_B += (J-dependence of) the adjoint of a cell-centred J cotangent */
+static void jc_cotangent_to_faces(const og_grid* g, const double* ljc, double* lbr, double* lbt, double* lbp) {
+    edges3 e = edges_alloc(g);
+    memset(e.jr, 0, sizeof(double) * g->nr * (g->nt + 1) * g->np);
+    memset(e.jt, 0, sizeof(double) * (g->nr + 1) * g->nt * g->np);
+    memset(e.jp, 0, sizeof(double) * (g->nr + 1) * (g->nt + 1) * g->np);
+    jcentre_T(g, ljc, e.jr, e.jt, e.jp);
+    curlJ_T(g, e.jr, e.jt, e.jp, lbr, lbt, lbp);
+    edges_free(e);
+}
+
+/* transpose of one upwind difference D_d u at cell (i,j,k) with the frozen direction: scatter
+ * w * (coefficients) onto lu */
+static void upwind_T(const og_grid* g, int dir, double vdir, double w, int i, int j, int k, double* lu) {
+    long long c = IDX(g, i, j, k);
+    if (dir == 0) {
+        if (vdir > 0.0) {
+            if (i > 0) { double h = g->rc[i] - g->rc[i - 1]; lu[c] += w / h; lu[IDX(g, i - 1, j, k)] -= w / h; }
+            else { double h = 2.0 * (g->rc[0] - g->r0); lu[c] += 2.0 * w / h; }
+        } else if (i < g->nr - 1) {
+            double h = g->rc[i + 1] - g->rc[i];
+            lu[IDX(g, i + 1, j, k)] += w / h; lu[c] -= w / h;
+        }
+    } else if (dir == 1) {
+        double h = g->rc[i] * g->dth;
+        if (vdir > 0.0) { if (j > 0) { lu[c] += w / h; lu[IDX(g, i, j - 1, k)] -= w / h; } }
+        else if (j < g->nt - 1) { lu[IDX(g, i, j + 1, k)] += w / h; lu[c] -= w / h; }
+    } else {
+        double h = g->rc[i] * g->sc[j] * g->dph;
+        if (vdir > 0.0) { lu[c] += w / h; lu[IDX(g, i, j, KM(g, k))] -= w / h; }
+        else { lu[IDX(g, i, j, KP(g, k))] += w / h; lu[c] -= w / h; }
+    }
+}
+
+/* adjoint of b = rho V dt F(v, B) at the base (v, B): lam_v += (dF/dv)^T (s lam_b),
+ * lam_B += (dF/dB)^T (s lam_b) */
+static void force_T(const og_grid* g, const double* v, const double* br, const double* bt, const double* bp,
+                    double dt, const double* lb, double* lv, double* lbr, double* lbt, double* lbp) {
+    long long N = g->N;
+    int nt = g->nt;
+    double* jc = (double*)malloc(sizeof(double) * 3 * N);
+    double* ljc = (double*)calloc(3 * N, sizeof(double));
+    double* lbc = (double*)calloc(3 * N, sizeof(double));
+    og_current_centre(g, br, bt, bp, jc);
+    const double* vv[3] = {v, v + N, v + 2 * N};
+    for (int i = 0; i < g->nr; i++)
+        for (int j = 0; j < nt; j++)
+            for (int k = 0; k < g->np; k++) {
+                long long c = IDX(g, i, j, k);
+                double s = g->rho[i * nt + j] * g->vol[i * nt + j] * dt;
+                double rho = g->rho[i * nt + j];
+                double lf[3] = {s * lb[c], s * lb[N + c], s * lb[2 * N + c]};
+                double B[3], J[3] = {jc[c], jc[N + c], jc[2 * N + c]};
+                bcentre_at(g, br, bt, bp, i, j, k, B);
+                /* Lorentz term (J x B)/rho */
+                ljc[c] += (B[1] * lf[2] - B[2] * lf[1]) / rho;
+                ljc[N + c] += (B[2] * lf[0] - B[0] * lf[2]) / rho;
+                ljc[2 * N + c] += (B[0] * lf[1] - B[1] * lf[0]) / rho;
+                lbc[c] += (lf[1] * J[2] - lf[2] * J[1]) / rho;
+                lbc[N + c] += (lf[2] * J[0] - lf[0] * J[2]) / rho;
+                lbc[2 * N + c] += (lf[0] * J[1] - lf[1] * J[0]) / rho;
+                /* advection: adv_m = sum_d u_d D_d(v_m) + curv_m; F = -adv */
+                double u[3] = {vv[0][c], vv[1][c], vv[2][c]};
+                double mu[3] = {-lf[0], -lf[1], -lf[2]};
+                for (int m = 0; m < 3; m++) {
+                    double D[3] = {upwind_r(g, vv[m], u[0], i, j, k), upwind_t(g, vv[m], u[1], i, j, k),
+                                   upwind_p(g, vv[m], u[2], i, j, k)};
+                    for (int d = 0; d < 3; d++) {
+                        lv[d * N + c] += mu[m] * D[d];
+                        upwind_T(g, d, u[d], u[d] * mu[m], i, j, k, lv + m * N);
+                    }
+                }
+                double r = g->rc[i], cot = g->cc[j] / g->sc[j];
+                /* curvature Jacobian rows: r: -(ut^2+up^2)/r; t: (ur ut - up^2 cot)/r; p: (ur up + ut up cot)/r */
+                lv[N + c] += mu[0] * (-2.0 * u[1] / r);
+                lv[2 * N + c] += mu[0] * (-2.0 * u[2] / r);
+                lv[c] += mu[1] * (u[1] / r);
+                lv[N + c] += mu[1] * (u[0] / r);
+                lv[2 * N + c] += mu[1] * (-2.0 * u[2] * cot / r);
+                lv[c] += mu[2] * (u[2] / r);
+                lv[N + c] += mu[2] * (u[2] * cot / r);
+                lv[2 * N + c] += mu[2] * ((u[0] + u[1] * cot) / r);
+            }
+    bcentre_T(g, lbc, lbr, lbt, lbp);
+    jc_cotangent_to_faces(g, ljc, lbr, lbt, lbp);
+    free(jc); free(ljc); free(lbc);
+}
+
+/* adjoint of E edges(vbar, B) given lam_E on edges: lam_vbar += ..., lam_B += ... */
+static void efield_T(const og_grid* g, const double* vb, const double* br, const double* bt, const double* bp,
+                     double eta, const double* ler, const double* let, const double* lep, double* lvb,
+                     double* lbr, double* lbt, double* lbp) {
+    long long N = g->N;
+    double* lec = (double*)calloc(3 * N, sizeof(double));
+    double* lbc = (double*)calloc(3 * N, sizeof(double));
+    eedges_T(g, ler, let, lep, lec);
+    for (int i = 0; i < g->nr; i++)
+        for (int j = 0; j < g->nt; j++)
+            for (int k = 0; k < g->np; k++) {
+                long long c = IDX(g, i, j, k);
+                double B[3], u[3] = {vb[c], vb[N + c], vb[2 * N + c]};
+                double l[3] = {lec[c], lec[N + c], lec[2 * N + c]};
+                bcentre_at(g, br, bt, bp, i, j, k, B);
+                /* E_c = -u x B: lam_u = l x B, lam_B = u x l */
+                lvb[c] += l[1] * B[2] - l[2] * B[1];
+                lvb[N + c] += l[2] * B[0] - l[0] * B[2];
+                lvb[2 * N + c] += l[0] * B[1] - l[1] * B[0];
+                lbc[c] += u[1] * l[2] - u[2] * l[1];
+                lbc[N + c] += u[2] * l[0] - u[0] * l[2];
+                lbc[2 * N + c] += u[0] * l[1] - u[1] * l[0];
+            }
+    bcentre_T(g, lbc, lbr, lbt, lbp);
+    if (eta != 0.0) {
+        for (long long q = 0; q < 3 * N; q++) lec[q] *= eta;
+        jc_cotangent_to_faces(g, lec, lbr, lbt, lbp);
+    }
+    free(lec); free(lbc);
+}
+
+int og_adjoint_step(const og_grid* g, double nu, double eta, double cfl, double dt, double asi_fixed, double tol,
+                    int max_iter, const double* v0, const double* br0, const double* bt0, const double* bp0,
+                    const double* lv1, const double* lbr1, const double* lbt1, const double* lbp1, double* lv,
+                    double* lbr, double* lbt, double* lbp) {
+    long long N = g->N, n3 = 3 * N;
+    int np = g->np;
+    long long nbr = (long long)(g->nr + 1) * g->nt * np, nbt = (long long)g->nr * (g->nt + 1) * np, nbp = N;
+    long long ner = (long long)g->nr * (g->nt + 1) * np, net = (long long)(g->nr + 1) * g->nt * np,
+              nep = (long long)(g->nr + 1) * (g->nt + 1) * np;
+    double co[5];
+    int st = og_coeffs(g, nu, cfl, dt, 0.0, asi_fixed, v0, br0, bt0, bp0, co);
+    if (st != OG_OK) return st;
+    double asi = co[3], anu = co[4];
+    int it, status = OG_OK, s;
+    double rr;
+    /* ---- forward recomputation */
+    double* b0 = (double*)malloc(sizeof(double) * n3);
+    double* b1 = (double*)malloc(sizeof(double) * n3);
+    double* dp = (double*)calloc(n3, sizeof(double));
+    double* vp = (double*)malloc(sizeof(double) * n3);
+    double* vb = (double*)malloc(sizeof(double) * n3);
+    double* B1r = (double*)malloc(sizeof(double) * nbr);
+    double* B1t = (double*)malloc(sizeof(double) * nbt);
+    double* B1p = (double*)malloc(sizeof(double) * nbp);
+    edges3 e = edges_alloc(g);
+    og_force(g, v0, br0, bt0, bp0, dt, b0);
+    s = og_pcg(g, asi, 3, b0, dp, tol, max_iter, 0, &it, &rr);
+    if (s != OG_OK) status = s;
+    for (long long q = 0; q < n3; q++) { vp[q] = v0[q] + dp[q]; vb[q] = 0.5 * (v0[q] + vp[q]); }
+    memcpy(B1r, br0, sizeof(double) * nbr); memcpy(B1t, bt0, sizeof(double) * nbt); memcpy(B1p, bp0, sizeof(double) * nbp);
+    og_efield_edges(g, vb, br0, bt0, bp0, eta, e.jr, e.jt, e.jp);
+    og_ct(g, e.jr, e.jt, e.jp, dt, B1r, B1t, B1p);
+    /* ---- reverse */
+    double* y = (double*)calloc(n3, sizeof(double));
+    double* lb = (double*)calloc(n3, sizeof(double));
+    double* ldp = (double*)calloc(n3, sizeof(double));
+    double* lvp = (double*)calloc(n3, sizeof(double));
+    double* lvb = (double*)calloc(n3, sizeof(double));
+    double* lB1r = (double*)malloc(sizeof(double) * nbr);
+    double* lB1t = (double*)malloc(sizeof(double) * nbt);
+    double* lB1p = (double*)malloc(sizeof(double) * nbp);
+    memset(lv, 0, sizeof(double) * n3);
+    memset(lbr, 0, sizeof(double) * nbr); memset(lbt, 0, sizeof(double) * nbt); memset(lbp, 0, sizeof(double) * nbp);
+    memcpy(lB1r, lbr1, sizeof(double) * nbr); memcpy(lB1t, lbt1, sizeof(double) * nbt); memcpy(lB1p, lbp1, sizeof(double) * nbp);
+    /* 5. v' = M_nu^-1 D v**  ->  lam_v** = D M_nu^-1 lam_v' */
+    s = og_pcg(g, anu, 3, lv1, y, tol, max_iter, 0, &it, &rr);
+    if (s != OG_OK) status = s;
+    for (int c = 0; c < 3; c++)
+        for (long long q = 0; q < N; q++) {
+            long long ij = q / np;
+            double w = g->rho[ij] * g->vol[ij] * y[c * N + q];
+            lv[c * N + q] += w;      /* v** = v + d_c */
+            y[c * N + q] = w;        /* lam_dc */
+        }
+    /* 4. d_c = M_SI^-1 (b0 + b1)/2 */
+    memset(lb, 0, sizeof(double) * n3);
+    s = og_pcg(g, asi, 3, y, lb, tol, max_iter, 0, &it, &rr);   /* lb = M_SI^-1 lam_dc = lam_bc */
+    if (s != OG_OK) status = s;
+    for (long long q = 0; q < n3; q++) { lb[q] *= 0.5; }            /* lam_b0 (partial) = lam_b1 = lam_bc/2 */
+    /* b1 = F(vp, B1): lam_vp, lam_B1 */
+    force_T(g, vp, B1r, B1t, B1p, dt, lb, lvp, lB1r, lB1t, lB1p);
+    /* 3. B1 = B - dt curl E(vb, B): lam_B += lam_B1; lam_E = -dt C^T lam_B1 */
+    for (long long q = 0; q < nbr; q++) lbr[q] += lB1r[q];
+    for (long long q = 0; q < nbt; q++) lbt[q] += lB1t[q];
+    for (long long q = 0; q < nbp; q++) lbp[q] += lB1p[q];
+    memset(e.jr, 0, sizeof(double) * ner); memset(e.jt, 0, sizeof(double) * net); memset(e.jp, 0, sizeof(double) * nep);
+    ct_T(g, dt, lB1r, lB1t, lB1p, e.jr, e.jt, e.jp);
+    efield_T(g, vb, br0, bt0, bp0, eta, e.jr, e.jt, e.jp, lvb, lbr, lbt, lbp);
+    /* vp = v + dp, vb = v + dp/2 */
+    for (long long q = 0; q < n3; q++) {
+        lv[q] += lvp[q] + lvb[q];
+        ldp[q] = lvp[q] + 0.5 * lvb[q];
+    }
+    /* 2. dp = M_SI^-1 b0: lam_b0 += M_SI^-1 lam_dp */
+    memset(y, 0, sizeof(double) * n3);
+    s = og_pcg(g, asi, 3, ldp, y, tol, max_iter, 0, &it, &rr);
+    if (s != OG_OK) status = s;
+    for (long long q = 0; q < n3; q++) lb[q] += y[q];
+    /* b0 = F(v, B) */
+    force_T(g, v0, br0, bt0, bp0, dt, lb, lv, lbr, lbt, lbp);
+    free(b0); free(b1); free(dp); free(vp); free(vb); free(B1r); free(B1t); free(B1p);
+    free(y); free(lb); free(ldp); free(lvp); free(lvb); free(lB1r); free(lB1t); free(lB1p);
+    edges_free(e);
+    return status;
+}

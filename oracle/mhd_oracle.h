@@ -76,6 +76,15 @@ int og_step(const og_grid* g, double nu, double eta, double cfl, double dt_fixed
             double asi_fixed, double tol, int max_iter, double* v, double* br, double* bt,
             double* bp, double* info);
 
+/* Adjoint of og_step with dt = `dt` (fixed), alpha_SI = asi_fixed if >= 0 (else computed from
+ * state n), alpha_nu = nu dt, and the upwind directions of the forward step frozen (reading P15).
+ * Given state n (v [3N], br, bt, bp) and the cotangent of state n+1 (lv1, lbr1, lbt1, lbp1),
+ * writes the cotangent of state n (lv, lbr, lbt, lbp). PCG solves use `tol`. */
+int og_adjoint_step(const og_grid* g, double nu, double eta, double cfl, double dt, double asi_fixed,
+                    double tol, int max_iter, const double* v, const double* br, const double* bt,
+                    const double* bp, const double* lv1, const double* lbr1, const double* lbt1,
+                    const double* lbp1, double* lv, double* lbr, double* lbt, double* lbp);
+
 #ifdef __cplusplus
 }
 #endif
