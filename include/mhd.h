@@ -23,9 +23,10 @@
  *      bp [nr][nt][np]    phi faces at phi_k
  *      vr, vt, vp [nr][nt][np] cell centres; "stacked" vectors hold ncomp such blocks back
  *      to back ([ncomp][nr][nt][np]).
- *  - A grid owns its metric tables and all workspace. It allocates only in mhd_grid_create
- *    (and in a solver's first call at a new size for batched solves); mhd_step, pcg_solve and
- *    the other calls allocate nothing.
+ *  - A grid owns its metric tables and all workspace. It allocates in mhd_grid_create, in the
+ *    first mhd_adjoint_step call on it (adjoint workspace) and in the first pcg_solve_batched
+ *    call for a batch of grids (batch plan); mhd_step, pcg_solve and the other calls allocate
+ *    nothing.
  *  - All work is enqueued on the grid's CUDA stream. Calls that return scalars (step info,
  *    iteration counts) synchronise that stream once at their end; the others return after
  *    enqueueing.

@@ -114,6 +114,7 @@ struct mhd_grid_s {
     double *ec;             // cell-centred E (3N)
     double *ring;           // [2*nr] polar ring sums
     double* partials;       // [kMaxBlocks * kPartialsPerBlock]
+    void* adj_mem;          // adjoint workspace, allocated by the first adjoint call
     mhd::PcgScalars* sc;    // device
     mhd::StepScalars* ss;   // device
     mhd::PcgScalars* h_sc;  // pinned host mirror
@@ -159,6 +160,7 @@ mhd_status_t solve(mhd_grid_s* g, const double* alpha_dev, int nc, const double*
 
 mhd_status_t set_error(mhd_grid_s* g, mhd_status_t st, const std::string& msg);
 void batched_forget(mhd_grid_s* g);   // batched.cu: drop cached plans that use g
+void adjoint_free(mhd_grid_s* g);     // adjoint.cu: release the adjoint workspace
 
 // kernel timing: bracket a launch with events when profiling is on (returns the slot or -1)
 int prof_begin(mhd_grid_s* g, cudaStream_t st, int kernel);

@@ -1,0 +1,125 @@
+"""GPU adjoint step against the oracle's adjoint (itself pinned by central differences), through
+the C ABI, and a central-difference check of the GPU adjoint against the GPU forward step."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_1811_02605_gb300 as P
+from paper_1811_02605_gb300 import inputs as I
+from tests.gpu_util import dev_state, fields, grid, rel_l2, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+KEYS = ("vr", "vt", "vp", "br", "bt", "bp")
+
+
+def _case(d, seed, scale_v=20.0):
+    st = I.initial_state(d, seed, False)
+    for k in ("vr", "vt", "vp"):
+        st[k] = st[k] * scale_v
+    og = O.Grid.from_desc(d)
+    c = og.coeffs(np.stack([st["vr"], st["vt"], st["vp"]]), st["br"], st["bt"], st["bp"], nu=1e-3, cfl=0.3)
+    rng = np.random.default_rng(200 + seed)
+    lam = {k: rng.normal(size=st[k].shape) for k in KEYS}
+    lam["bt"][:, 0] = 0.0
+    lam["bt"][:, -1] = 0.0
+    return st, og, c, lam, rng
+
+
+def _gpu_adjoint(g, st, lam, dt, asi, eta, tol=1e-13):
+    ds, dl = dev_state(st), dev_state(lam)
+    out = {k: torch.empty_like(v) for k, v in ds.items()}
+    prm = P.make_params(nu=1e-3, eta=eta, cfl=0.3, tol=tol, alpha_si_fixed=asi, max_iter=200000)
+    stt = P.mhd_adjoint_step(g, prm, fields(ds), dt, fields(dl), fields(out))
+    torch.cuda.synchronize()
+    return {k: to_np(v) for k, v in out.items()}, stt
+
+
+@pytest.mark.parametrize("d,eta", [(I.GridDesc(6, 6, 12, 1.0, 4.0, 1.1), 0.0),
+                                   (I.GridDesc(9, 7, 10, 1.0, 6.0, 1.08), 2e-3),
+                                   (I.GridDesc(16, 12, 24, 1.0, 10.0, 1.05), 0.0)],
+                         ids=["6x6x12", "9x7x10-eta", "16x12x24"])
+def test_adjoint_matches_oracle(d, eta):
+    st, og, c, lam, rng = _case(d, 0)
+    ref, s1 = og.adjoint_step(st, lam, c["dt"], c["alpha_si"], eta=eta, cfl=0.3, tol=1e-13)
+    got, s2 = _gpu_adjoint(grid(d), st, lam, c["dt"], c["alpha_si"], eta)
+    assert s1 == O.OK and s2 == P.MHD_OK
+    for k in KEYS:
+        assert rel_l2(got[k], ref[k]) < 1e-9, (k, rel_l2(got[k], ref[k]))
+
+
+def test_adjoint_central_differences_on_gpu():
+    d = I.GridDesc(12, 10, 20, 1.0, 8.0, 1.06)
+    st, og, c, lam, rng = _case(d, 3)
+    g = grid(d)
+    dt, asi = c["dt"], c["alpha_si"]
+    adj, s = _gpu_adjoint(g, st, lam, dt, asi, 0.0)
+    prm = P.make_params(nu=1e-3, cfl=0.3, dt_fixed=dt, alpha_si_fixed=asi, tol=1e-14, max_iter=200000)
+
+    def L(x):
+        ds = dev_state(x)
+        stt, info = P.mhd_step(g, prm, fields(ds))
+        assert stt == P.MHD_OK
+        return sum(float(np.sum(lam[k] * to_np(ds[k]))) for k in KEYS)
+
+    for _ in range(3):
+        dv = {k: rng.normal(size=st[k].shape) for k in KEYS}
+        dv["bt"][:, 0] = 0.0
+        dv["bt"][:, -1] = 0.0
+        nx = np.sqrt(sum(np.sum(st[k] ** 2) for k in KEYS))
+        nd = np.sqrt(sum(np.sum(dv[k] ** 2) for k in KEYS))
+        h = 1e-6 * nx / nd
+        fd = (L({k: st[k] + h * dv[k] for k in KEYS}) - L({k: st[k] - h * dv[k] for k in KEYS})) / (2 * h)
+        ad = sum(float(np.sum(adj[k] * dv[k])) for k in KEYS)
+        assert abs(fd - ad) <= 1e-6 * max(abs(fd), abs(ad)), (fd, ad)
+
+
+def test_autograd_checkpointed_steps_match_central_differences():
+    from paper_1811_02605_gb300.autograd import simulate
+    d = I.GridDesc(10, 8, 16, 1.0, 6.0, 1.07)
+    st, og, c, lam, rng = _case(d, 5, scale_v=10.0)
+    g = grid(d)
+    target = torch.from_numpy(I.outer_target(d, 77)).cuda()
+    kw = dict(nu=1e-3, cfl=0.3, tol=1e-13, max_iter=200000)
+    x0 = {k: to_dev(v).requires_grad_(k in ("vr", "vt", "vp", "br")) for k, v in st.items()}
+    out = simulate(g, x0, 7, checkpoint_every=3, **kw)
+    loss = 0.5 * torch.sum((out["br"][-1] - target) ** 2)
+    loss.backward()
+    grad_v = [x0[k].grad.cpu().numpy() for k in ("vr", "vt", "vp")]
+    grad_br0 = x0["br"].grad[0].cpu().numpy()
+    # frozen per-step dt and alpha_SI of the base trajectory for the finite differences
+    base = {k: to_dev(v) for k, v in st.items()}
+    dts, als = [], []
+    f = fields(base)
+    for _ in range(7):
+        s_, info = P.mhd_step(g, P.make_params(**kw), f)
+        dts.append(info["dt"])
+        als.append(info["alpha_si"])
+
+    def L(x):
+        ds = dev_state(x)
+        ff = fields(ds)
+        for n in range(7):
+            P.mhd_step(g, P.make_params(**dict(kw, dt_fixed=dts[n], alpha_si_fixed=als[n], tol=1e-14)), ff)
+        return 0.5 * float(torch.sum((ds["br"][-1] - target) ** 2))
+
+    for trial in range(3):
+        dv = [rng.normal(size=st["vr"].shape) for _ in range(3)]
+        db = rng.normal(size=st["br"][0].shape)
+        nrm = np.sqrt(sum(np.sum(a * a) for a in dv) + np.sum(db * db))
+        dv = [a / nrm for a in dv]
+        db = db / nrm
+        xn = np.sqrt(sum(np.sum(st[k] ** 2) for k in ("vr", "vt", "vp")) + np.sum(st["br"][0] ** 2))
+        h = 1e-6 * xn
+
+        def pert(sg):
+            x = {k: v.copy() for k, v in st.items()}
+            for a, k in zip(dv, ("vr", "vt", "vp")):
+                x[k] = x[k] + sg * h * a
+            x["br"] = x["br"].copy()
+            x["br"][0] = x["br"][0] + sg * h * db
+            return x
+
+        fd = (L(pert(1.0)) - L(pert(-1.0))) / (2 * h)
+        ad = sum(float(np.sum(a * b)) for a, b in zip(grad_v, dv)) + float(np.sum(grad_br0 * db))
+        assert abs(fd - ad) <= 1e-6 * max(abs(fd), abs(ad)), (trial, fd, ad)
