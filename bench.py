@@ -231,12 +231,12 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def run(precision, steps, warmup, profile):
+    def run(precision, steps, warmup, profile, inner_tol=1e-5, restart=1):
         ds = dev_state()
         torch.cuda.synchronize()
         f = P.make_fields(ds["br"], ds["bt"], ds["bp"], ds["vr"], ds["vt"], ds["vp"])
         prm = P.make_params(nu=w["nu"], eta=w["eta"], cfl=w["cfl"], tol=w["tol"], precision=precision,
-                            inner_tol=1e-5, max_outer=30)
+                            inner_tol=inner_tol, max_outer=200, max_iter=20000, mixed_restart=restart)
         for _ in range(warmup):
             st, info = P.mhd_step(g, prm, f)
             if st != P.MHD_OK:
@@ -283,26 +283,39 @@ def run_ours(args):
                 kernel="k_spmv_dot<double,2>", avg_launch_ms=round(spmv_avg, 4),
                 peak_source="2 DFMA/clk/SM x 152 SMs x 2.07 GHz (nominal FP64 rate of the part)")
     # ---- mixed (FP32 inner PCG, FP64 refinement)
-    mixed = None
-    if not args.no_mixed:
-        msm, infosm, profm, clkm, dsm = run(P.PREC_MIXED, args.steps, args.warmup, True)
+    def mixed_entry(inner_tol, restart):
+        msm, infosm, profm, clkm, dsm = run(P.PREC_MIXED, args.steps, args.warmup, True, inner_tol, restart)
         msm = maxr(msm)
         pcg32_ms = sum(profm[k][0] for k in ("pupdate32", "spmv32", "update32"))
         pcg32_n = profm["spmv32"][1]
         pcg32_gbs = PCG_BYTES_PER_CELL["fp32"] * N * pcg32_n / (pcg32_ms * 1e-3) / 1e9
-        sp32_ms, sp32_n = profm["spmv32"]
-        sp32_avg = sp32_ms / max(sp32_n, 1)
-        sp32_gbs = SPMV_BYTES_PER_CELL["fp32"] * N / (sp32_avg * 1e-3) / 1e9
+        tiled = profm["pupdate32"][1] == 0
+        # per-kernel DRAM passes of a 3-component FP32 vector (4 B x 3 per cell per pass)
+        kb = {"spmv32": 3 if tiled else 2, "update32": 5 if tiled else 6, "pupdate32": 3}
+        kernels = {}
+        for k in ("pupdate32", "spmv32", "update32"):
+            ms_k, n_k = profm[k]
+            if n_k:
+                avg = ms_k / n_k
+                gbs = kb[k] * 12 * N / (avg * 1e-3) / 1e9
+                kernels[k] = dict(avg_launch_ms=round(avg, 4), bytes_per_cell=kb[k] * 12, gbs=round(gbs, 1),
+                                  frac_of_hbm=round(gbs / hbm, 4))
         err = {k: float(torch.linalg.norm(dsm[k] - ds64[k]) / torch.linalg.norm(ds64[k])) for k in ds64}
-        mixed = dict(ms_per_step=round(msm, 3), speedup_vs_fp64=round(ms64 / msm, 3),
-                     pcg_iters_per_step=sum(sum(i["iters"]) for i in infosm) / len(infosm),
-                     outer_per_step=sum(sum(i["outer"]) for i in infosm) / len(infosm),
-                     max_relres=max(max(i["relres"]) for i in infosm),
-                     pcg_gbs=round(pcg32_gbs, 1), pcg_frac_of_hbm=round(pcg32_gbs / hbm, 4),
-                     spmv32=dict(bound="hbm", achieved=round(sp32_gbs, 1), peak=hbm, unit="GB/s",
-                                 frac=round(sp32_gbs / hbm, 4), avg_launch_ms=round(sp32_avg, 4)),
-                     rel_l2_vs_fp64_gpu_after_steps=err, clocks=clkm,
-                     kernel_ms={k: round(v[0], 3) for k, v in profm.items() if v[1]})
+        return dict(inner_tol=inner_tol, refinement=("restarted" if restart else "reliable updates"),
+                    ms_per_step=round(msm, 3), speedup_vs_fp64=round(ms64 / msm, 3),
+                    pcg_iters_per_step=sum(sum(i["iters"]) for i in infosm) / len(infosm),
+                    outer_per_step=sum(sum(i["outer"]) for i in infosm) / len(infosm),
+                    max_relres=max(max(i["relres"]) for i in infosm),
+                    pcg_gbs=round(pcg32_gbs, 1), pcg_frac_of_hbm=round(pcg32_gbs / hbm, 4),
+                    kernels=kernels, fp32_kernels=("plane-marching pair (A: p update + stencil, B: stencil + "
+                                                   "update)" if tiled else "split (p update, stencil, update)"),
+                    rel_l2_vs_fp64_gpu_after_steps=err, clocks=clkm,
+                    kernel_ms={k: round(v[0], 3) for k, v in profm.items() if v[1]})
+
+    mixed = mixed_reliable = None
+    if not args.no_mixed:
+        mixed = mixed_entry(1e-5, 1)            # FP32 inner PCG to 1e-5, restarted FP64 refinement
+        mixed_reliable = mixed_entry(0.1, 0)    # FP32 CG with reliable FP64 updates every 10x
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -346,7 +359,7 @@ def run_ours(args):
                                 dt=[i["dt"] for i in infos64]),
                     pcg_gbs=dict(fp64=round(pcg64_gbs, 1), fp64_frac_of_hbm=round(pcg64_gbs / hbm, 4),
                                  peak_gbs=hbm, peak_source=peak_src),
-                    roofline=roof, mixed=mixed, e2e=e2e, cpu_baseline=cpu, clocks=clk64,
+                    roofline=roof, mixed=mixed, mixed_reliable=mixed_reliable, e2e=e2e, cpu_baseline=cpu, clocks=clk64,
                     gpu_launches=int(launches), kernel_ms={k: round(v[0], 3) for k, v in prof64.items() if v[1]})
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -432,6 +445,84 @@ def run_batched(args):
                           pcg_gbs_algorithmic=round(bytes_alg / (ms * 1e-3) / 1e9, 1))), flush=True)
 
 
+def run_adjoint(args):
+    """20 FP64 steps at 128x128x256 with a checkpoint every 5 steps, loss = misfit of the final
+    outer-shell B_r against a smooth seeded target; gradient with respect to the inner-boundary
+    B_r and the initial v by the adjoint chain, checked against central differences of the same
+    frozen-coefficient map on `--fd-dirs` seeded unit directions (h = 1e-6 relative)."""
+    import numpy as np
+    import torch
+    from paper_1811_02605_gb300 import build as B
+    B.build()
+    import paper_1811_02605_gb300 as P
+    from paper_1811_02605_gb300 import inputs as I
+    from paper_1811_02605_gb300.autograd import simulate
+    name = "adjoint_128x128x256"
+    w, st = gen_state(name, args.grid)
+    d = w["desc"]
+    nsteps = args.adj_steps
+    g = P.mhd_grid_create(d.nr, d.nt, d.np, d.r0, d.r1, d.stretch)
+    target = torch.from_numpy(I.outer_target(d, 1811 * 4)).cuda()
+    kw = dict(nu=w["nu"], eta=w["eta"], cfl=w["cfl"], tol=1e-13, max_iter=500000)
+    x0 = {k: torch.from_numpy(v).cuda().requires_grad_(k in ("vr", "vt", "vp", "br")) for k, v in st.items()}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = simulate(g, x0, nsteps, checkpoint_every=5, **kw)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    loss = 0.5 * torch.sum((out["br"][-1] - target) ** 2)
+    loss.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    gv = [x0[k].grad.cpu().numpy() for k in ("vr", "vt", "vp")]
+    gb = x0["br"].grad[0].cpu().numpy()
+    # frozen per-step coefficients of the base trajectory
+    base = {k: torch.from_numpy(v).cuda() for k, v in st.items()}
+    f = P.make_fields(base["br"], base["bt"], base["bp"], base["vr"], base["vt"], base["vp"])
+    dts, als = [], []
+    for _ in range(nsteps):
+        s_, info = P.mhd_step(g, P.make_params(**kw), f)
+        dts.append(info["dt"])
+        als.append(info["alpha_si"])
+
+    def L(x):
+        ds = {k: torch.from_numpy(v).cuda() for k, v in x.items()}
+        ff = P.make_fields(ds["br"], ds["bt"], ds["bp"], ds["vr"], ds["vt"], ds["vp"])
+        for n in range(nsteps):
+            P.mhd_step(g, P.make_params(**dict(kw, dt_fixed=dts[n], alpha_si_fixed=als[n])), ff)
+        return 0.5 * float(torch.sum((ds["br"][-1] - target) ** 2))
+
+    errs = []
+    xn = math.sqrt(sum(float(np.sum(st[k] ** 2)) for k in ("vr", "vt", "vp")) + float(np.sum(st["br"][0] ** 2)))
+    h = 1e-6 * xn
+    t3 = time.perf_counter()
+    for q in range(args.fd_dirs):
+        rng = np.random.default_rng(1811 * 400 + q)
+        dv = [rng.normal(size=st["vr"].shape) for _ in range(3)]
+        db = rng.normal(size=st["br"][0].shape)
+        nrm = math.sqrt(sum(float(np.sum(a * a)) for a in dv) + float(np.sum(db * db)))
+        dv = [a / nrm for a in dv]
+        db = db / nrm
+
+        def pert(sg):
+            x = {k: v.copy() for k, v in st.items()}
+            for a, k in zip(dv, ("vr", "vt", "vp")):
+                x[k] = x[k] + sg * h * a
+            x["br"][0] = x["br"][0] + sg * h * db
+            return x
+
+        fd = (L(pert(1.0)) - L(pert(-1.0))) / (2 * h)
+        ad = sum(float(np.sum(a * b)) for a, b in zip(gv, dv)) + float(np.sum(gb * db))
+        errs.append(abs(fd - ad) / max(abs(fd), abs(ad), 1e-300))
+    t4 = time.perf_counter()
+    print(json.dumps(dict(workload=name, grid=f"{d.nr}x{d.nt}x{d.np}", steps=nsteps, checkpoint_every=5,
+                          tol=kw["tol"], loss=float(loss), forward_s=round(t1 - t0, 3),
+                          backward_s=round(t2 - t1, 3), ms_per_step_fwd_adj=round(1e3 * (t2 - t0) / nsteps, 1),
+                          fd_dirs=args.fd_dirs, fd_rel_err_max=max(errs), fd_rel_err_median=float(np.median(errs)),
+                          fd_seconds=round(t4 - t3, 1), grad_norm_v=math.sqrt(sum(float(np.sum(a * a)) for a in gv)),
+                          grad_norm_br_inner=float(np.linalg.norm(gb)))), flush=True)
+
+
 def run_profile_case(args):
     """A short, fixed piece of the hot path for profilers: the first SI system of the workload,
     `--profile-iters` FP64 CG iterations, then one mixed-precision outer pass with the same cap."""
@@ -470,6 +561,9 @@ def main():
     ap.add_argument("--profile-iters", type=int, default=6)
     ap.add_argument("--batched", action="store_true", help="time the 64-system batched solve and exit")
     ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--adjoint", action="store_true", help="time and check the adjoint workload and exit")
+    ap.add_argument("--adj-steps", type=int, default=20)
+    ap.add_argument("--fd-dirs", type=int, default=16)
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -480,6 +574,8 @@ def main():
         run_profile_case(args)
     elif args.batched:
         run_batched(args)
+    elif args.adjoint:
+        run_adjoint(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -77,12 +77,18 @@ enum { MHD_PREC_FP64 = 0, MHD_PREC_MIXED = 1 };
  *  max_iter  PCG iteration cap per solve (inner iterations in mixed precision)
  *  max_outer mixed precision: cap on FP64 iterative-refinement passes
  *  precision MHD_PREC_FP64 or MHD_PREC_MIXED (FP32 stencil and inner PCG, FP64 residuals,
- *            corrections and reductions) */
+ *            corrections and reductions)
+ *  mixed_restart  mixed precision only. 0 (default): reliable updates. When the FP32 recursive
+ *            residual has fallen by inner_tol, x is corrected in FP64, the true FP64 residual
+ *            replaces the recursive one, and the CG recurrence continues with the same search
+ *            direction. 1: classic iterative refinement, restarting the FP32 CG from the new
+ *            residual at each correction. */
 typedef struct {
     double nu, eta, cfl, dt_fixed, dt_max, alpha_si_fixed;
     double tol, inner_tol;
     int max_iter, max_outer;
     int precision;
+    int mixed_restart;
 } mhd_params_t;
 
 /* Caller-owned DEVICE pointers (layouts above). */

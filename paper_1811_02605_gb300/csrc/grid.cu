@@ -254,8 +254,15 @@ extern "C" mhd_status_t mhd_grid_create(const mhd_grid_desc_t* desc, void* cuda_
     ok = ok && cudaMemsetAsync(g->sc, 0, sizeof(PcgScalars), g->stream) == cudaSuccess;
     ok = ok && cudaMemsetAsync(g->ss, 0, sizeof(StepScalars), g->stream) == cudaSuccess;
     // zero the FP32 p buffers once so the first fused update never reads garbage
+    // every solver vector starts finite (0 * garbage could otherwise be NaN)
     ok = ok && cudaMemsetAsync(g->p32, 0, sizeof(float) * 2 * n3, g->stream) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(g->x32, 0, sizeof(float) * n3, g->stream) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(g->r32, 0, sizeof(float) * n3, g->stream) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(g->q32, 0, sizeof(float) * n3, g->stream) == cudaSuccess;
     ok = ok && cudaMemsetAsync(g->p64, 0, sizeof(double) * n3, g->stream) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(g->x64, 0, sizeof(double) * n3, g->stream) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(g->r64, 0, sizeof(double) * n3, g->stream) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(g->q64, 0, sizeof(double) * n3, g->stream) == cudaSuccess;
     ok = ok && cudaStreamSynchronize(g->stream) == cudaSuccess;
     if (!ok) {
         mhd_grid_destroy(g);

@@ -25,6 +25,7 @@ struct PcgScalars {
     double tol;      // stop when sqrt(rr) <= tol * sqrt(bb)   (FP64 solve / outer loop)
     double rr_out;   // mixed: squared norm of the current outer FP64 residual
     double inner_tol;
+    double rho_prev; // rho of the previous CG iteration (residual replacement keeps the recurrence)
     int iter;        // iterations of the current (inner) solve
     int max_iter;
     int done;        // 0 running, 1 converged, 2 iteration cap, 3 non-finite, 4 breakdown
@@ -32,7 +33,7 @@ struct PcgScalars {
     int outer_done;  // mixed: 0 running, 1 converged, 3 non-finite
     int total_iter;  // mixed: inner iterations summed over the outer passes
     unsigned int count;  // last-block ticket
-    unsigned int pad;
+    int par;         // FP32 tiled path: which of the two p buffers holds the current p
 };
 
 // Device-resident scalars of one step.
@@ -123,6 +124,7 @@ struct mhd_grid_s {
     // CUDA graphs of a batch of PCG iterations, keyed by precision and ncomp
     cudaGraphExec_t iter_graph[2][4];
     int graph_batch;
+    int slab32;             // r-slab length of the tiled FP32 kernels (0: not tuned yet)
     std::string last_error;
     // kernel timing (diagnostics)
     int prof;
@@ -150,6 +152,11 @@ void induction(mhd_grid_s* g, const double* vr, const double* vt, const double* 
                const double* dlt, double dfac, double eta, const double* dt_dev, double dt_host,
                double* br, double* bt, double* bp);
 void vstar_rhs(mhd_grid_s* g, double* vr, double* vt, double* vp, const double* dlt, double* b);
+
+// tiled FP32 CG kernels (tiled.cu)
+bool tiled32_ok(const mhd_grid_s* g);
+int tiled32_blocks(const mhd_grid_s* g, int slab);
+void enqueue_tiled32(mhd_grid_s* g, cudaStream_t st, int nc, int slab, int prof_a, int prof_b);
 
 // PCG (pcg.cu). alpha is read from device memory (alpha_dev) so a step never syncs on it.
 void build_tables(mhd_grid_s* g, const double* alpha_dev, bool fp32);

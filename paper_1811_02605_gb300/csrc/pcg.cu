@@ -279,6 +279,7 @@ __global__ void __launch_bounds__(kThreads) k_update(Dims d, int nc, T* __restri
         const double rho = out[0], rr = out[1];
         sc->iter += 1;
         sc->total_iter += 1;
+        sc->rho_prev = sc->rho;
         sc->beta = rho / sc->rho;
         sc->rho = rho;
         sc->rr = rr;
@@ -376,13 +377,16 @@ __global__ void k_finish64(Dims d, int nc, const double* __restrict__ xs, double
 // ------------------------------------------------------------------------------------------
 // mixed precision: FP64 outer residual and correction around FP32 inner CG
 // ------------------------------------------------------------------------------------------
-// r = b - M x in FP64; inner start: r~32 = float(s r), p~32 = r~32, x~32 = 0
+// r = b - M x in FP64; r~32 = float(s r), x~32 = 0. With restart != 0 the FP32 CG starts afresh
+// (beta = 0, so the next p update gives p~32 = r~32); otherwise the true residual replaces the
+// recursive one and the CG recurrence continues with the same p~32 (reliable update, residual
+// replacement): beta = <r~_true, r~_true> / rho of the previous iteration.
 template <int V>
 __global__ void __launch_bounds__(kThreads) k_outer_res(Dims d, int nc, const double* __restrict__ b,
                                                         const double* __restrict__ x, float* __restrict__ r32,
                                                         float* __restrict__ p32, float* __restrict__ x32,
                                                         OpTab<double> t, OpTab64u tu, PcgScalars* sc,
-                                                        double* __restrict__ partials, int first) {
+                                                        double* __restrict__ partials, int first, int restart) {
     const int nt = d.nt;
     const unsigned int G = (unsigned int)(d.N / 2);
     const long long plane = (long long)nt * d.np;
@@ -420,18 +424,25 @@ __global__ void __launch_bounds__(kThreads) k_outer_res(Dims d, int nc, const do
                 cell_in = fma(rd, rd, cell_in);
             }
             *reinterpret_cast<float2*>(r32 + k * d.N + c.base) = make_float2(rs[0], rs[1]);
-            *reinterpret_cast<float2*>(p32 + k * d.N + c.base) = make_float2(rs[0], rs[1]);
             *reinterpret_cast<float2*>(x32 + k * d.N + c.base) = make_float2(0.f, 0.f);
+            // first pass: p~32 = r~32 so no value left from an earlier solve can reach 0 * p
+            if (first) *reinterpret_cast<float2*>(p32 + k * d.N + c.base) = make_float2(rs[0], rs[1]);
         }
         a_rin = fma(dg, cell_in, a_rin);
     }
     double val[4] = {a_rout, a_bb, a_rho, a_rin}, out[4];
     if (reduce_last<4>(val, partials, &sc->count, out) && threadIdx.x == 0) {
-        if (first) sc->bb = out[1];
+        if (first) {
+            sc->bb = out[1];
+            sc->par = 0;
+        }
         sc->rr_out = out[0];
+        // keep the recurrence only while the replaced residual still agrees with the recursive
+        // one (rho_true <= 4 rho_recursive); otherwise beta = 0 restarts it (p = r next)
+        const bool keep = !restart && sc->rho_prev > 0.0 && out[2] <= 4.0 * sc->rho;
+        sc->beta = keep ? out[2] / sc->rho_prev : 0.0;
         sc->rho = out[2];
         sc->rr = out[3];
-        sc->beta = 0.0;
         sc->iter = 0;
         const double bn = sqrt(sc->bb);
         if (!finite(out[0]) || !finite(out[2])) { sc->done = 3; sc->outer_done = 3; }
@@ -529,6 +540,9 @@ void enqueue_iteration(mhd_grid_s* g, cudaStream_t st, int prec, int nc) {
         k_update<double, 2><<<blocks, kThreads, 0, st>>>(d, nc, g->x64, g->p64, g->r64, g->q64, g->tu.dg, g->sc,
                                                           g->partials);
         prof_end(g, st, s);
+    } else if (tiled32_ok(g) && g->slab32 > 0) {
+        // plane-marching pair, when the autotuner measured it faster than the split kernels
+        enqueue_tiled32(g, st, nc, g->slab32, MHD_KERNEL_SPMV32, MHD_KERNEL_UPDATE32);
     } else if (use_v4(g)) {
         const int blocks = grid_blocks(g, d.N / 4, kPerSmIter);
         s = prof_begin(g, st, MHD_KERNEL_PUPDATE32);
@@ -623,6 +637,8 @@ __global__ void k_setup(PcgScalars* sc, double tol, double inner_tol, int max_it
     sc->outer = 0;
     sc->outer_done = 0;
     sc->rr_out = 0.0;
+    sc->rho_prev = 0.0;
+    sc->par = 0;
     sc->count = 0u;
 }
 
@@ -641,11 +657,87 @@ __global__ void k_inner_end(PcgScalars* sc, const double* saved) {
 
 }  // namespace
 
+namespace {
+__global__ void k_tune_reset(PcgScalars* sc) {
+    sc->done = 0;
+    sc->alpha = 0.0;
+    sc->beta = 0.0;
+    sc->rho = 1.0;
+    sc->tol = 0.0;
+    sc->bb = 1.0;
+    sc->iter = 0;
+    sc->max_iter = 1 << 30;
+    sc->par = 0;
+    sc->count = 0u;
+}
+
+// choose the r-slab length of the tiled FP32 kernels by timing a few iterations of each
+// candidate (alpha = beta = 0, so the vectors are left as they are); run before a solve sets up
+// its scalars
+mhd_status_t tune_slab32(mhd_grid_s* g, int nc) {
+    if (!tiled32_ok(g) || g->slab32 > 0) return MHD_OK;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return check_cuda(g, "tune events");
+    int best = 0;
+    float best_ms = 1e30f;
+    const int prof = g->prof;
+    g->prof = 0;
+    // candidate -1: the split kernels (p update, stencil, update)
+    {
+        k_tune_reset<<<1, 1, 0, g->stream>>>(g->sc);
+        g->slab32 = -1;
+        cudaMemsetAsync(g->r32, 0x3F, sizeof(float) * 3 * (size_t)g->d.N, g->stream);
+        cudaMemsetAsync(g->p32, 0x3F, sizeof(float) * 6 * (size_t)g->d.N, g->stream);
+        enqueue_iteration(g, g->stream, 1, nc);
+        cudaEventRecord(e0, g->stream);
+        for (int it = 0; it < 3; it++) enqueue_iteration(g, g->stream, 1, nc);
+        cudaEventRecord(e1, g->stream);
+        if (cudaEventSynchronize(e1) == cudaSuccess) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            best_ms = ms;
+            best = -1;
+        }
+    }
+    // positive finite vectors (bytes 0x3F: 0.747f) so the timed iterations do real work and no
+    // reduction trips a breakdown flag; x stays unchanged because alpha = 0
+    const size_t n3 = 3 * (size_t)g->d.N;
+    cudaMemsetAsync(g->r32, 0x3F, sizeof(float) * n3, g->stream);
+    cudaMemsetAsync(g->p32, 0x3F, sizeof(float) * 2 * n3, g->stream);
+    for (int slab : {8, 16, 32, 64}) {
+        if (slab > 2 * g->d.nr && best > 0) break;
+        if (tiled32_blocks(g, slab) > kMaxBlocks) continue;
+        k_tune_reset<<<1, 1, 0, g->stream>>>(g->sc);
+        enqueue_tiled32(g, g->stream, nc, slab, 0, 0);
+        cudaEventRecord(e0, g->stream);
+        for (int it = 0; it < 3; it++) enqueue_tiled32(g, g->stream, nc, slab, 0, 0);
+        cudaEventRecord(e1, g->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = slab;
+        }
+    }
+    g->prof = prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best == 0) return set_error(g, MHD_ERR_CUDA, "tiled FP32 kernels: no launchable variant");
+    g->slab32 = best;  // -1: split kernels are faster on this grid
+    return check_cuda(g, "tune slab");
+}
+}  // namespace
+
 mhd_status_t solve(mhd_grid_s* g, const double* alpha_dev, int nc, const double* b, double* x,
                    const double* x0, const mhd_params_t* prm, int* iters, int* outer, double* relres) {
     const Dims d = g->d;
     const bool mixed = (prm->precision == MHD_PREC_MIXED);
     build_tables(g, alpha_dev, mixed);
+    if (mixed && g->slab32 == 0) {
+        mhd_status_t st = tune_slab32(g, 3);
+        if (st != MHD_OK) return st;
+    }
     k_setup<<<1, 1, 0, g->stream>>>(g->sc, prm->tol, prm->inner_tol, prm->max_iter);
     const int blocks2 = grid_blocks(g, d.N / 2, kPerSmIter);
     if (!mixed) {
@@ -673,8 +765,9 @@ mhd_status_t solve(mhd_grid_s* g, const double* alpha_dev, int nc, const double*
     int outer_done = 0;
     for (int o = 0; o <= prm->max_outer; o++) {
         const int ps = prof_begin(g, g->stream, MHD_KERNEL_OUTER_RES);
+        const int restart = (o == 0 || prm->mixed_restart) ? 1 : 0;
         k_outer_res<2><<<blocks2, kThreads, 0, g->stream>>>(d, nc, b, x, g->r32, g->p32, g->x32, g->t64, g->tu,
-                                                            g->sc, g->partials, o == 0 ? 1 : 0);
+                                                            g->sc, g->partials, o == 0 ? 1 : 0, restart);
         prof_end(g, g->stream, ps);
         mhd_status_t st = check_cuda(g, "outer residual");
         if (st != MHD_OK) return st;

@@ -18,10 +18,11 @@ struct OpMax {
 };
 
 // Returns true in the last CTA; there, thread 0 holds the grid-wide results in out[].
+// Works for any block size up to 1024 threads (32 warps).
 template <int K, typename Op = OpSum>
 __device__ __forceinline__ bool reduce_last(double (&v)[K], double* __restrict__ partials,
                                             unsigned int* count, double (&out)[K]) {
-    __shared__ double sm[K][kThreads / 32];
+    __shared__ double sm[K][32];
     __shared__ int is_last;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;

@@ -214,3 +214,40 @@ def test_step_mixed_against_fp64_oracle():
         assert max(info["relres"]) <= 1e-9
         for k in ("vr", "vt", "vp", "br", "bt", "bp"):
             assert rel_l2(gpu[k], ref[k]) <= 1e-7, (n, k, rel_l2(gpu[k], ref[k]))
+
+
+@pytest.mark.parametrize("restart,inner", [(0, 0.1), (1, 1e-5), (0, 1e-5)], ids=["reliable", "restart", "reliable-small"])
+def test_pcg_mixed_tiled_path(restart, inner):
+    # np = 256 takes the plane-marching FP32 kernels; nt = 18 leaves a ragged last row tile
+    d = I.GridDesc(20, 18, 256, 1.0, 10.0, 1.05)
+    g, og = grid(d), O.Grid.from_desc(d)
+    rng = np.random.default_rng(12)
+    b = rng.normal(size=(3, d.nr, d.nt, d.np)) * og.volumes()[None, :, :, None]
+    alpha = 2.0
+    xr, _, _, _ = og.pcg(alpha, b, tol=1e-13)
+    x = torch.zeros(b.shape, dtype=torch.float64, device="cuda")
+    prm = P.make_params(tol=1e-9, inner_tol=inner, precision=P.PREC_MIXED, max_outer=60, max_iter=5000,
+                        mixed_restart=restart)
+    st, it, ou, rr = P.pcg_solve(g, alpha, to_dev(b), x, prm)
+    assert st == P.MHD_OK and rr <= 1e-9
+    res = b - og.apply_M(alpha, to_np(x))
+    assert np.linalg.norm(res) <= 1e-9 * np.linalg.norm(b) * 1.0000001
+    assert rel_l2(to_np(x), xr) < 1e-6
+    # one and two components too
+    for nc in (1, 2):
+        x = torch.zeros((nc,) + b.shape[1:], dtype=torch.float64, device="cuda")
+        st, it, ou, rr = P.pcg_solve(g, alpha, to_dev(b[:nc]), x, prm)
+        assert st == P.MHD_OK and rr <= 1e-9
+        xr1, _, _, _ = og.pcg(alpha, b[:nc], tol=1e-13)
+        assert rel_l2(to_np(x), xr1) < 1e-6
+
+
+def test_step_mixed_tiled_against_fp64_oracle():
+    d = I.GridDesc(16, 16, 128, 1.0, 10.0, 1.05)
+    st0 = I.initial_state(d, 4, False)
+    res = _run_steps(d, st0, 2, dict(nu=1e-3, cfl=0.4, tol=1e-9, precision=P.PREC_MIXED, inner_tol=0.1,
+                                     max_outer=60, max_iter=5000))
+    for n, (stat, info, oinfo, gpu, ref) in enumerate(res):
+        assert stat == P.MHD_OK and max(info["relres"]) <= 1e-9
+        for k in ("vr", "vt", "vp", "br", "bt", "bp"):
+            assert rel_l2(gpu[k], ref[k]) <= 1e-7, (n, k, rel_l2(gpu[k], ref[k]))
