@@ -215,7 +215,7 @@ extern "C" mhd_status_t mhd_grid_create(const mhd_grid_desc_t* desc, void* cuda_
          dalloc(&g->t32.s, (size_t)nr * nt, owned);
     ok = ok && dalloc(&g->tu.dg, (size_t)nr * nt, owned) && dalloc(&g->tu.awr, (size_t)(nr + 1) * nt, owned) &&
          dalloc(&g->tu.awt, (size_t)nr * (nt + 1), owned) && dalloc(&g->tu.awp, (size_t)nr * nt, owned);
-    ok = ok && dalloc(&g->x64, n3, owned) && dalloc(&g->r64, n3, owned) && dalloc(&g->p64, n3, owned) &&
+    ok = ok && dalloc(&g->x64, n3, owned) && dalloc(&g->r64, n3, owned) && dalloc(&g->p64, 2 * n3, owned) &&
          dalloc(&g->q64, n3, owned);
     ok = ok && dalloc(&g->x32, n3, owned) && dalloc(&g->r32, n3, owned) && dalloc(&g->p32, 2 * n3, owned) &&
          dalloc(&g->q32, n3, owned);
@@ -259,7 +259,7 @@ extern "C" mhd_status_t mhd_grid_create(const mhd_grid_desc_t* desc, void* cuda_
     ok = ok && cudaMemsetAsync(g->x32, 0, sizeof(float) * n3, g->stream) == cudaSuccess;
     ok = ok && cudaMemsetAsync(g->r32, 0, sizeof(float) * n3, g->stream) == cudaSuccess;
     ok = ok && cudaMemsetAsync(g->q32, 0, sizeof(float) * n3, g->stream) == cudaSuccess;
-    ok = ok && cudaMemsetAsync(g->p64, 0, sizeof(double) * n3, g->stream) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(g->p64, 0, sizeof(double) * 2 * n3, g->stream) == cudaSuccess;
     ok = ok && cudaMemsetAsync(g->x64, 0, sizeof(double) * n3, g->stream) == cudaSuccess;
     ok = ok && cudaMemsetAsync(g->r64, 0, sizeof(double) * n3, g->stream) == cudaSuccess;
     ok = ok && cudaMemsetAsync(g->q64, 0, sizeof(double) * n3, g->stream) == cudaSuccess;

@@ -105,7 +105,7 @@ struct mhd_grid_s {
     mhd::OpTab<double> t64;
     mhd::OpTab<float> t32;
     mhd::OpTab64u tu;
-    // FP64 PCG workspace (stacked 3-component vectors, 3N each)
+    // FP64 PCG workspace (stacked 3-component vectors, 3N each; p64 holds two buffers)
     double *x64, *r64, *p64, *q64;
     // FP32 PCG workspace
     float *x32, *r32, *p32, *q32;
@@ -124,7 +124,8 @@ struct mhd_grid_s {
     // CUDA graphs of a batch of PCG iterations, keyed by precision and ncomp
     cudaGraphExec_t iter_graph[2][4];
     int graph_batch;
-    int slab32;             // r-slab length of the tiled FP32 kernels (0: not tuned yet)
+    int slab32;             // r-slab length of the tiled FP32 kernels (0: not tuned, -1: split kernels)
+    int slab64;             // same for the FP64 fused p-update + stencil kernel
     std::string last_error;
     // kernel timing (diagnostics)
     int prof;
@@ -157,6 +158,7 @@ void vstar_rhs(mhd_grid_s* g, double* vr, double* vt, double* vp, const double* 
 bool tiled32_ok(const mhd_grid_s* g);
 int tiled32_blocks(const mhd_grid_s* g, int slab);
 void enqueue_tiled32(mhd_grid_s* g, cudaStream_t st, int nc, int slab, int prof_a, int prof_b);
+void enqueue_tiled64_a(mhd_grid_s* g, cudaStream_t st, int slab, int prof_id);
 
 // PCG (pcg.cu). alpha is read from device memory (alpha_dev) so a step never syncs on it.
 void build_tables(mhd_grid_s* g, const double* alpha_dev, bool fp32);

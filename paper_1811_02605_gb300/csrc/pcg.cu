@@ -14,6 +14,7 @@
 // stop test). Results are deterministic for a fixed launch shape.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 
 #include "mhd_internal.cuh"
 #include "reduce.cuh"
@@ -184,13 +185,14 @@ __device__ __forceinline__ void scaled_stencil(const Dims& d, const Cell& c, con
 // FP64 / FP32 CG iteration kernels on the scaled system
 // ------------------------------------------------------------------------------------------
 // A1: p = r + beta p
-template <typename T, int V>
-__global__ void __launch_bounds__(kThreads) k_pupdate(Dims d, int nc, const T* __restrict__ r,
+template <typename T, int V, int NC>
+__global__ void __launch_bounds__(kThreads) k_pupdate(Dims d, const T* __restrict__ r,
                                                       T* __restrict__ p, const PcgScalars* sc) {
     if (sc->done) return;
     const T beta = (T)sc->beta;
     const unsigned int G = (unsigned int)(d.N / V);
-    for (int c = 0; c < nc; c++) {
+#pragma unroll
+    for (int c = 0; c < NC; c++) {
         const T* rc = r + c * d.N;
         T* pc = p + c * d.N;
         for (unsigned int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
@@ -205,8 +207,8 @@ __global__ void __launch_bounds__(kThreads) k_pupdate(Dims d, int nc, const T* _
 }
 
 // A2: q = A~ p and <p, q>; last CTA forms alpha = rho / <p, q>
-template <typename T, int V>
-__global__ void __launch_bounds__(kThreads) k_spmv_dot(Dims d, int nc, const T* __restrict__ p,
+template <typename T, int V, int NC>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 4) k_spmv_dot(Dims d, const T* __restrict__ p,
                                                        T* __restrict__ q, OpTab<T> t, PcgScalars* sc,
                                                        double* __restrict__ partials) {
     if (sc->done) return;
@@ -218,7 +220,10 @@ __global__ void __launch_bounds__(kThreads) k_spmv_dot(Dims d, int nc, const T* 
         const T cr_lo = t.ar[c.i * nt + c.j], cr_hi = t.ar[(c.i + 1) * nt + c.j];
         const T ct_lo = t.at[c.i * (nt + 1) + c.j], ct_hi = t.at[c.i * (nt + 1) + c.j + 1];
         const T cp = t.ap[c.ij];
-        for (int k = 0; k < nc; k++) {
+        // one component at a time: holding all three components' neighbours at once raises the
+        // register count past two CTAs per SM and was measured slower
+#pragma unroll 1
+        for (int k = 0; k < NC; k++) {
             T v[V], o[V];
             scaled_stencil<T, V>(d, c, p + k * d.N, cr_lo, cr_hi, ct_lo, ct_hi, cp, v, o);
             stv<T, V>(q + k * d.N + c.base, o);
@@ -236,14 +241,17 @@ __global__ void __launch_bounds__(kThreads) k_spmv_dot(Dims d, int nc, const T* 
     }
 }
 
-// B: x += alpha p, r -= alpha q, rho = <r~, r~>, rr = sum dg r~^2; last CTA: beta, stop test
-template <typename T, int V>
-__global__ void __launch_bounds__(kThreads) k_update(Dims d, int nc, T* __restrict__ x,
-                                                     const T* __restrict__ p, T* __restrict__ r,
+// B: x += alpha p, r -= alpha q, rho = <r~, r~>, rr = sum dg r~^2; last CTA: beta, stop test.
+// PAR: p lives in the buffer that a fused p-update kernel just wrote (the other half of a double
+// buffer of stride 3N, chosen by the device-side parity), and the parity flips at the end.
+template <typename T, int V, int NC, bool PAR = false>
+__global__ void __launch_bounds__(kThreads) k_update(Dims d, T* __restrict__ x,
+                                                     const T* __restrict__ p_in, T* __restrict__ r,
                                                      const T* __restrict__ q,
                                                      const double* __restrict__ dg, PcgScalars* sc,
                                                      double* __restrict__ partials) {
     if (sc->done) return;
+    const T* __restrict__ p = PAR ? p_in + (long long)(1 - sc->par) * 3 * d.N : p_in;
     const T al = (T)sc->alpha;
     const unsigned int G = (unsigned int)(d.N / V);
     const unsigned int npv = d.np / V;
@@ -253,7 +261,8 @@ __global__ void __launch_bounds__(kThreads) k_update(Dims d, int nc, T* __restri
         const long long off = (long long)g * V;
         T rs[V];
         zerov<T, V>(rs);
-        for (int k = 0; k < nc; k++) {
+#pragma unroll
+        for (int k = 0; k < NC; k++) {
             T xv[V], pv[V], rv[V], qv[V];
             ldv<T, V>(x + k * d.N + off, xv);
             ldv<T, V>(p + k * d.N + off, pv);
@@ -283,6 +292,7 @@ __global__ void __launch_bounds__(kThreads) k_update(Dims d, int nc, T* __restri
         sc->beta = rho / sc->rho;
         sc->rho = rho;
         sc->rr = rr;
+        if (PAR) sc->par = 1 - sc->par;
         if (!finite(rr) || !finite(rho)) sc->done = 3;
         else if (sqrt(rr) <= sc->tol * sqrt(sc->bb)) sc->done = 1;
         else if (sc->iter >= sc->max_iter) sc->done = 2;
@@ -349,6 +359,7 @@ __global__ void __launch_bounds__(kThreads) k_init64(Dims d, int nc, const doubl
         sc->iter = 0;
         sc->total_iter = 0;
         sc->outer = 0;
+        sc->par = 0;
         if (!finite(out[0]) || !finite(out[1]) || !finite(out[2])) sc->done = 3;
         else if (out[2] == 0.0) sc->done = 1;
         else if (sqrt(out[1]) <= sc->tol * sqrt(out[2])) sc->done = 1;
@@ -524,49 +535,54 @@ constexpr int kPerSmIter = 4;
 
 bool use_v4(const mhd_grid_s* g) { return (g->d.np % 4) == 0; }
 
-// enqueue one CG iteration (A1, A2, B) of the given precision
+// enqueue one CG iteration (p update, stencil + <p,q>, update) of the given precision
+template <typename T, int V, int NC>
+void enqueue_split(mhd_grid_s* g, cudaStream_t st, T* x, T* r, T* p, T* q, const OpTab<T>& t, int blocks,
+                   int prof0) {
+    const Dims d = g->d;
+    int s = prof_begin(g, st, prof0);
+    k_pupdate<T, V, NC><<<blocks, kThreads, 0, st>>>(d, r, p, g->sc);
+    prof_end(g, st, s);
+    s = prof_begin(g, st, prof0 + 1);
+    // the FP32 stencil is latency-bound: 6 CTAs per SM instead of 4 for more loads in flight
+    const int bs = (sizeof(T) == 4) ? grid_blocks(g, d.N / V, 6) : blocks;
+    k_spmv_dot<T, V, NC><<<bs, kThreads, 0, st>>>(d, p, q, t, g->sc, g->partials);
+    prof_end(g, st, s);
+    s = prof_begin(g, st, prof0 + 2);
+    k_update<T, V, NC><<<blocks, kThreads, 0, st>>>(d, x, p, r, q, g->tu.dg, g->sc, g->partials);
+    prof_end(g, st, s);
+}
+
+template <typename T, int V>
+void enqueue_split_nc(mhd_grid_s* g, cudaStream_t st, int nc, T* x, T* r, T* p, T* q, const OpTab<T>& t,
+                      int blocks, int prof0) {
+    if (nc == 3) enqueue_split<T, V, 3>(g, st, x, r, p, q, t, blocks, prof0);
+    else if (nc == 2) enqueue_split<T, V, 2>(g, st, x, r, p, q, t, blocks, prof0);
+    else enqueue_split<T, V, 1>(g, st, x, r, p, q, t, blocks, prof0);
+}
+
 void enqueue_iteration(mhd_grid_s* g, cudaStream_t st, int prec, int nc) {
     const Dims d = g->d;
-    int s;
-    if (prec == 0) {
+    if (prec == 0 && nc == 3 && tiled32_ok(g) && g->slab64 > 0) {
+        // fused p update + stencil (p double-buffered), then the update reading the new p
         const int blocks = grid_blocks(g, d.N / 2, kPerSmIter);
-        s = prof_begin(g, st, MHD_KERNEL_PUPDATE64);
-        k_pupdate<double, 2><<<blocks, kThreads, 0, st>>>(d, nc, g->r64, g->p64, g->sc);
+        enqueue_tiled64_a(g, st, g->slab64, MHD_KERNEL_SPMV64);
+        const int s = prof_begin(g, st, MHD_KERNEL_UPDATE64);
+        k_update<double, 2, 3, true><<<blocks, kThreads, 0, st>>>(d, g->x64, g->p64, g->r64, g->q64, g->tu.dg,
+                                                                   g->sc, g->partials);
         prof_end(g, st, s);
-        s = prof_begin(g, st, MHD_KERNEL_SPMV64);
-        k_spmv_dot<double, 2><<<blocks, kThreads, 0, st>>>(d, nc, g->p64, g->q64, g->t64, g->sc, g->partials);
-        prof_end(g, st, s);
-        s = prof_begin(g, st, MHD_KERNEL_UPDATE64);
-        k_update<double, 2><<<blocks, kThreads, 0, st>>>(d, nc, g->x64, g->p64, g->r64, g->q64, g->tu.dg, g->sc,
-                                                          g->partials);
-        prof_end(g, st, s);
+    } else if (prec == 0) {
+        enqueue_split_nc<double, 2>(g, st, nc, g->x64, g->r64, g->p64, g->q64, g->t64,
+                                    grid_blocks(g, d.N / 2, kPerSmIter), MHD_KERNEL_PUPDATE64);
     } else if (tiled32_ok(g) && g->slab32 > 0) {
         // plane-marching pair, when the autotuner measured it faster than the split kernels
         enqueue_tiled32(g, st, nc, g->slab32, MHD_KERNEL_SPMV32, MHD_KERNEL_UPDATE32);
     } else if (use_v4(g)) {
-        const int blocks = grid_blocks(g, d.N / 4, kPerSmIter);
-        s = prof_begin(g, st, MHD_KERNEL_PUPDATE32);
-        k_pupdate<float, 4><<<blocks, kThreads, 0, st>>>(d, nc, g->r32, g->p32, g->sc);
-        prof_end(g, st, s);
-        s = prof_begin(g, st, MHD_KERNEL_SPMV32);
-        k_spmv_dot<float, 4><<<blocks, kThreads, 0, st>>>(d, nc, g->p32, g->q32, g->t32, g->sc, g->partials);
-        prof_end(g, st, s);
-        s = prof_begin(g, st, MHD_KERNEL_UPDATE32);
-        k_update<float, 4><<<blocks, kThreads, 0, st>>>(d, nc, g->x32, g->p32, g->r32, g->q32, g->tu.dg, g->sc,
-                                                         g->partials);
-        prof_end(g, st, s);
+        enqueue_split_nc<float, 4>(g, st, nc, g->x32, g->r32, g->p32, g->q32, g->t32,
+                                   grid_blocks(g, d.N / 4, kPerSmIter), MHD_KERNEL_PUPDATE32);
     } else {
-        const int blocks = grid_blocks(g, d.N / 2, kPerSmIter);
-        s = prof_begin(g, st, MHD_KERNEL_PUPDATE32);
-        k_pupdate<float, 2><<<blocks, kThreads, 0, st>>>(d, nc, g->r32, g->p32, g->sc);
-        prof_end(g, st, s);
-        s = prof_begin(g, st, MHD_KERNEL_SPMV32);
-        k_spmv_dot<float, 2><<<blocks, kThreads, 0, st>>>(d, nc, g->p32, g->q32, g->t32, g->sc, g->partials);
-        prof_end(g, st, s);
-        s = prof_begin(g, st, MHD_KERNEL_UPDATE32);
-        k_update<float, 2><<<blocks, kThreads, 0, st>>>(d, nc, g->x32, g->p32, g->r32, g->q32, g->tu.dg, g->sc,
-                                                         g->partials);
-        prof_end(g, st, s);
+        enqueue_split_nc<float, 2>(g, st, nc, g->x32, g->r32, g->p32, g->q32, g->t32,
+                                   grid_blocks(g, d.N / 2, kPerSmIter), MHD_KERNEL_PUPDATE32);
     }
 }
 
@@ -674,8 +690,18 @@ __global__ void k_tune_reset(PcgScalars* sc) {
 // choose the r-slab length of the tiled FP32 kernels by timing a few iterations of each
 // candidate (alpha = beta = 0, so the vectors are left as they are); run before a solve sets up
 // its scalars
+// Diagnostics: MHD_FORCE_SLAB=<n> skips the timing and uses slab n (-1: split kernels).
+int forced_slab() {
+    const char* f = std::getenv("MHD_FORCE_SLAB");
+    return f ? (int)std::strtol(f, nullptr, 10) : 0;
+}
+
 mhd_status_t tune_slab32(mhd_grid_s* g, int nc) {
     if (!tiled32_ok(g) || g->slab32 > 0) return MHD_OK;
+    if (const int f = forced_slab()) {
+        g->slab32 = (f > 0 && tiled32_blocks(g, f) <= kMaxBlocks) ? f : -1;
+        return MHD_OK;
+    }
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return check_cuda(g, "tune events");
     int best = 0;
@@ -729,6 +755,49 @@ mhd_status_t tune_slab32(mhd_grid_s* g, int nc) {
 }
 }  // namespace
 
+namespace {
+// FP64: time the split iteration against the fused tiled kernel A at each slab length (alpha =
+// beta = 0 on positive finite vectors) and keep the fastest
+mhd_status_t tune_slab64(mhd_grid_s* g) {
+    if (!tiled32_ok(g) || g->slab64 != 0) return MHD_OK;
+    if (const int f = forced_slab()) {
+        g->slab64 = (f > 0 && tiled32_blocks(g, f) <= kMaxBlocks) ? f : -1;
+        return MHD_OK;
+    }
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return check_cuda(g, "tune events");
+    const int prof = g->prof;
+    g->prof = 0;
+    const size_t n3 = 3 * (size_t)g->d.N;
+    cudaMemsetAsync(g->r64, 0x3F, sizeof(double) * n3, g->stream);
+    cudaMemsetAsync(g->p64, 0x3F, sizeof(double) * 2 * n3, g->stream);
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int slab : {-1, 8, 16, 32, 64}) {
+        if (slab > 0 && (tiled32_blocks(g, slab) > kMaxBlocks || (slab > 2 * g->d.nr && best != 0))) continue;
+        g->slab64 = slab;
+        k_tune_reset<<<1, 1, 0, g->stream>>>(g->sc);
+        enqueue_iteration(g, g->stream, 0, 3);
+        cudaEventRecord(e0, g->stream);
+        for (int it = 0; it < 2; it++) enqueue_iteration(g, g->stream, 0, 3);
+        cudaEventRecord(e1, g->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = slab;
+        }
+    }
+    g->prof = prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    g->slab64 = (best == 0) ? -1 : best;
+    cudaMemsetAsync(g->p64, 0, sizeof(double) * 2 * n3, g->stream);
+    return check_cuda(g, "tune slab64");
+}
+}  // namespace
+
 mhd_status_t solve(mhd_grid_s* g, const double* alpha_dev, int nc, const double* b, double* x,
                    const double* x0, const mhd_params_t* prm, int* iters, int* outer, double* relres) {
     const Dims d = g->d;
@@ -736,6 +805,10 @@ mhd_status_t solve(mhd_grid_s* g, const double* alpha_dev, int nc, const double*
     build_tables(g, alpha_dev, mixed);
     if (mixed && g->slab32 == 0) {
         mhd_status_t st = tune_slab32(g, 3);
+        if (st != MHD_OK) return st;
+    }
+    if (!mixed && nc == 3 && g->slab64 == 0) {
+        mhd_status_t st = tune_slab64(g);
         if (st != MHD_OK) return st;
     }
     k_setup<<<1, 1, 0, g->stream>>>(g->sc, prm->tol, prm->inner_tol, prm->max_iter);

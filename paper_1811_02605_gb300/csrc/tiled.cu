@@ -343,4 +343,148 @@ void enqueue_tiled32(mhd_grid_s* g, cudaStream_t st, int nc, int slab, int prof_
     prof_end(g, st, s);
 }
 
+// ---------------------------------------------------------------------------------------------
+// FP64: fused p update + stencil + <p, q> with q stored (the FP64 iteration is bound by its FP64
+// instruction count, so q is kept rather than recomputed). Replaces the split p-update and
+// stencil kernels: the p update then costs ~1.25 FMA per point inside an ALU-bound kernel
+// instead of a separate memory-bound pass.
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+__device__ __forceinline__ void ld4d(const double* __restrict__ a, double (&o)[4]) {
+    const double2 u = *reinterpret_cast<const double2*>(a);
+    const double2 v = *reinterpret_cast<const double2*>(a + 2);
+    o[0] = u.x;
+    o[1] = u.y;
+    o[2] = v.x;
+    o[3] = v.y;
+}
+__device__ __forceinline__ void st4d(double* __restrict__ a, const double (&o)[4]) {
+    *reinterpret_cast<double2*>(a) = make_double2(o[0], o[1]);
+    *reinterpret_cast<double2*>(a + 2) = make_double2(o[2], o[3]);
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(WARPS * 32, 1) k_tiled_a64(Dims d, const double* __restrict__ r,
+                                                              double* __restrict__ pbuf, double* __restrict__ q,
+                                                              OpTab<double> t, PcgScalars* sc,
+                                                              double* __restrict__ partials, int slab) {
+    __shared__ __align__(16) double sm[3][WARPS * SW];
+    if (sc->done) return;
+    const long long N = d.N;
+    const double beta = sc->beta;
+    const int par = sc->par;
+    const double* __restrict__ pold = pbuf + (long long)par * 3 * N;
+    double* __restrict__ pnew = pbuf + (long long)(1 - par) * 3 * N;
+    const Tile T = tile_of(d, slab);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = T.j0 - 1 + w;
+    const bool row_ok = (j >= 0 && j < d.nt);
+    const bool interior = row_ok && w >= 1 && w <= TJ;
+    const int kq = T.k0 + lane * 4;
+    const int kl = (T.k0 == 0) ? d.np - 1 : T.k0 - 1;
+    const int kr = (T.k0 + TK == d.np) ? 0 : T.k0 + TK;
+    const long long plane = (long long)d.nt * d.np;
+    auto pnew4 = [&](int i, int c, double (&o)[4]) {
+        const long long base = c * N + (long long)i * plane + (long long)j * d.np + kq;
+        double rv[4], pv[4];
+        ld4d(r + base, rv);
+        ld4d(pold + base, pv);
+#pragma unroll
+        for (int e = 0; e < 4; e++) o[e] = fma(beta, pv[e], rv[e]);
+    };
+    auto pnew1 = [&](int i, int c, int k) {
+        const long long idx = c * N + (long long)i * plane + (long long)j * d.np + k;
+        return fma(beta, pold[idx], r[idx]);
+    };
+    double pm[3][4], pc[3][4], pn[3][4];
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+#pragma unroll
+        for (int e = 0; e < 4; e++) pm[c][e] = pc[c][e] = pn[c][e] = 0.0;
+    if (row_ok && T.i0 < T.i1) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            pnew4(T.i0, c, pc[c]);
+            if (interior && T.i0 > 0) pnew4(T.i0 - 1, c, pm[c]);
+        }
+    }
+    double acc = 0.0;
+    for (int i = T.i0; i < T.i1; i++) {
+        if (interior && i + 1 < d.nr) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) pnew4(i + 1, c, pn[c]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+#pragma unroll
+                for (int e = 0; e < 4; e++) pn[c][e] = 0.0;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            st4d(&sm[c][w * SW + 4 + lane * 4], pc[c]);
+            if (lane == 0) sm[c][w * SW + 3] = row_ok ? pnew1(i, c, kl) : 0.0;
+            if (lane == 31) sm[c][w * SW + 4 + TK] = row_ok ? pnew1(i, c, kr) : 0.0;
+        }
+        __syncthreads();
+        if (interior) {
+            const double ar_lo = t.ar[i * d.nt + j], ar_hi = t.ar[(i + 1) * d.nt + j];
+            const double at_lo = t.at[i * (d.nt + 1) + j], at_hi = t.at[i * (d.nt + 1) + j + 1];
+            const double ap = t.ap[i * d.nt + j];
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const double* row = &sm[c][w * SW + 4 + lane * 4];
+                double up[4], dn[4], qv[4];
+                ld4d(row - SW, up);
+                ld4d(row + SW, dn);
+                const double lft = row[-1], rgt = row[4];
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    const double l = (e == 0) ? lft : pc[c][e - 1];
+                    const double rr = (e == 3) ? rgt : pc[c][e + 1];
+                    double o = fma(-ap, l + rr, pc[c][e]);
+                    if (j > 0) o = fma(-at_lo, up[e], o);
+                    if (j < d.nt - 1) o = fma(-at_hi, dn[e], o);
+                    if (i > 0) o = fma(-ar_lo, pm[c][e], o);
+                    if (i < d.nr - 1) o = fma(-ar_hi, pn[c][e], o);
+                    qv[e] = o;
+                    acc = fma(pc[c][e], o, acc);
+                }
+                const long long base = c * N + (long long)i * plane + (long long)j * d.np + kq;
+                st4d(pnew + base, pc[c]);
+                st4d(q + base, qv);
+            }
+        }
+        __syncthreads();
+        if (interior) {
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    pm[c][e] = pc[c][e];
+                    pc[c][e] = pn[c][e];
+                }
+        } else if (row_ok && i + 1 < T.i1) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) pnew4(i + 1, c, pc[c]);
+        }
+    }
+    double val[1] = {acc}, out[1];
+    if (reduce_last<1>(val, partials, &sc->count, out) && threadIdx.x == 0) {
+        const double pq = out[0];
+        sc->pq = pq;
+        if (!isfinite(pq)) sc->done = 3;
+        else if (!(pq > 0.0)) sc->done = 4;
+        else sc->alpha = sc->rho / pq;
+    }
+}
+
+void enqueue_tiled64_a(mhd_grid_s* g, cudaStream_t st, int slab, int prof_id) {
+    const int blocks = tiled32_blocks(g, slab);
+    const int s = prof_begin(g, st, prof_id);
+    k_tiled_a64<<<blocks, WARPS * 32, 0, st>>>(g->d, g->r64, g->p64, g->q64, g->t64, g->sc, g->partials, slab);
+    prof_end(g, st, s);
+}
+
 }  // namespace mhd

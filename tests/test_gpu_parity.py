@@ -251,3 +251,36 @@ def test_step_mixed_tiled_against_fp64_oracle():
         assert stat == P.MHD_OK and max(info["relres"]) <= 1e-9
         for k in ("vr", "vt", "vp", "br", "bt", "bp"):
             assert rel_l2(gpu[k], ref[k]) <= 1e-7, (n, k, rel_l2(gpu[k], ref[k]))
+
+
+def test_pcg_fp64_tiled_path_matches_oracle():
+    # np = 256: the FP64 solve may use the fused p-update + stencil kernel (autotuned per grid)
+    d = I.GridDesc(20, 18, 256, 1.0, 10.0, 1.05)
+    g, og = grid(d), O.Grid.from_desc(d)
+    rng = np.random.default_rng(21)
+    b = rng.normal(size=(3, d.nr, d.nt, d.np)) * og.volumes()[None, :, :, None]
+    x0 = rng.normal(size=b.shape) * 0.01
+    for alpha in (0.3, 6.0):
+        x = to_dev(x0)
+        st, it, ou, rr = P.pcg_solve(g, alpha, to_dev(b), x, P.make_params(tol=1e-9, max_iter=5000))
+        xr, itr, _, s2 = og.pcg(alpha, b, x0=x0, tol=1e-9, max_iter=5000)
+        assert st == P.MHD_OK and abs(it - itr) <= 1, (it, itr)
+        if it == itr:
+            assert rel_l2(to_np(x), xr) < 1e-11
+    for k in (1, 3, 11):
+        x = torch.zeros(b.shape, dtype=torch.float64, device="cuda")
+        st, it, ou, rr = P.pcg_solve(g, 2.0, to_dev(b), x, P.make_params(tol=1e-30, max_iter=k))
+        xr, _, _, _ = og.pcg(2.0, b, fixed_iters=k)
+        assert it == k and rel_l2(to_np(x), xr) < 1e-12, k
+
+
+def test_step_fp64_tiled_grid_parity():
+    d = I.GridDesc(16, 16, 128, 1.0, 10.0, 1.05)
+    st0 = I.initial_state(d, 6, False)
+    res = _run_steps(d, st0, 3, dict(nu=1e-3, cfl=0.4, tol=1e-9))
+    for n, (stat, info, oinfo, gpu, ref) in enumerate(res):
+        assert stat == P.MHD_OK
+        for q in range(3):
+            assert abs(info["iters"][q] - oinfo["iters"][q]) <= 1
+        for k in ("vr", "vt", "vp", "br", "bt", "bp"):
+            assert rel_l2(gpu[k], ref[k]) <= 1e-11, (n, k, rel_l2(gpu[k], ref[k]))
