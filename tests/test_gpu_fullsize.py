@@ -1,0 +1,50 @@
+"""Full-size parity: the flux-rope workload at 256x256x512 (33.5M cells), FP64, one step in the
+launch configuration bench.py times, against the oracle's record of the same step
+(tests/golden/fluxrope_256x256x512_oracle_step1.json, written by tests/golden/make_golden.py from
+the CPU oracle alone; the oracle needs ~1.5 h for this step). Compared: step coefficients, PCG
+iteration counts (+-1), per-field L2 norms and the values at 2000 seeded positions per field."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import paper_1811_02605_gb300 as P
+from paper_1811_02605_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                      "fluxrope_256x256x512_oracle_step1.json")
+
+
+@pytest.mark.skipif(not os.path.exists(GOLDEN), reason="oracle record not generated")
+def test_fluxrope_256x256x512_first_step_matches_oracle_record():
+    rec = json.load(open(GOLDEN))
+    w, st = I.workload(rec["workload"])
+    d = w["desc"]
+    assert [d.nr, d.nt, d.np] == [rec["desc"]["nr"], rec["desc"]["nt"], rec["desc"]["np"]]
+    stream = torch.cuda.Stream()
+    g = P.mhd_grid_create(d.nr, d.nt, d.np, d.r0, d.r1, d.stretch, stream)
+    ds = {k: torch.from_numpy(v).cuda() for k, v in st.items()}
+    del st
+    f = P.make_fields(ds["br"], ds["bt"], ds["bp"], ds["vr"], ds["vt"], ds["vp"])
+    prm = P.make_params(nu=rec["params"]["nu"], eta=rec["params"]["eta"], cfl=rec["params"]["cfl"],
+                        tol=rec["params"]["tol"])
+    status, info = P.mhd_step(g, prm, f)
+    torch.cuda.synchronize()
+    assert status == P.MHD_OK
+    ri = rec["info"]
+    for k in ("dt", "cf", "cw", "alpha_si", "alpha_nu"):
+        assert abs(info[k] - ri[k]) <= 1e-12 * abs(ri[k]), (k, info[k], ri[k])
+    for q in range(3):
+        assert abs(info["iters"][q] - int(ri["iters"][q])) <= 1, (info["iters"], ri["iters"])
+    for k, fr in rec["fields"].items():
+        a = ds[k].reshape(-1)
+        idx = torch.tensor(fr["sample_index"], dtype=torch.long, device="cuda")
+        got = a[idx].cpu().numpy()
+        ref = np.array(fr["sample"])
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err <= 1e-10, (k, err)
+        l2 = float(torch.linalg.norm(a))
+        assert abs(l2 - fr["l2"]) <= 1e-11 * fr["l2"], (k, l2, fr["l2"])
