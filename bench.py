@@ -37,6 +37,12 @@ FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070  # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.0
 #   FP64 flops of the SpMV kernel: 6 multiply-adds + 1 add per component + 1 dot FMA = 27 flops
 SPMV_FLOPS_PER_CELL = 3 * (2 * 6 + 1 + 2)
 PCG_BYTES_PER_CELL = {"fp64": 6 * 3 * 8, "fp32": 6 * 3 * 4}
+# DRAM bytes (read + write) per cell of one k_spmv_dot<double,2,3> launch, measured with ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum = 369.8 MB + 172.4 MB) on the flux-rope physics at
+# 160x160x320 (8.19M cells, vectors larger than L2); scaled by the cell count for the roofline's
+# traffic field. 48 B per cell is algorithmic: the extra reads are i+-1 planes re-read from DRAM,
+# which costs nothing while the FP64 pipe binds.
+SPMV64_DRAM_BYTES_PER_CELL = (369.818624e6 + 172.424192e6) / (160 * 160 * 320)
 SPMV_BYTES_PER_CELL = {"fp64": 2 * 3 * 8, "fp32": 2 * 3 * 4}
 
 
@@ -231,7 +237,7 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def run(precision, steps, warmup, profile, inner_tol=1e-5, restart=1):
+    def run(precision, steps, warmup, profile, inner_tol=1e-5, restart=1, snapshot=None):
         ds = dev_state()
         torch.cuda.synchronize()
         f = P.make_fields(ds["br"], ds["bt"], ds["bp"], ds["vr"], ds["vt"], ds["vp"])
@@ -242,6 +248,9 @@ def run_ours(args):
             if st != P.MHD_OK:
                 raise RuntimeError(f"warm-up step failed: {P.STATUS_NAMES[st]} {P.mhd_last_error(g)}")
         barrier()
+        if snapshot is not None:  # state at the start of the timed region, for the end-to-end leg
+            for k in ds:
+                snapshot[k] = ds[k].cpu().pin_memory()
         P.mhd_profile_enable(g, profile)
         infos = []
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -269,7 +278,8 @@ def run_ours(args):
 
     hbm, peak_src = peaks()
     # ---- FP64 (headline)
-    ms64, infos64, prof64, clk64, ds64 = run(P.PREC_FP64, args.steps, args.warmup, True)
+    snap = {}
+    ms64, infos64, prof64, clk64, ds64 = run(P.PREC_FP64, args.steps, args.warmup, True, snapshot=snap)
     ms64 = maxr(ms64)
     it64 = sum(sum(i["iters"]) for i in infos64) / len(infos64)
     spmv_ms, spmv_n = prof64["spmv64"]
@@ -279,8 +289,10 @@ def run_ours(args):
     spmv_tflops = SPMV_FLOPS_PER_CELL * N / (spmv_avg * 1e-3) / 1e12
     pcg64_gbs = PCG_BYTES_PER_CELL["fp64"] * N * pcg64_n / (pcg64_ms * 1e-3) / 1e9
     roof = dict(bound="alu", achieved=round(spmv_tflops, 4), peak=round(FP64_PEAK_TFLOPS / 1e3, 4),
-                unit="TFLOP/s", frac=round(spmv_tflops / (FP64_PEAK_TFLOPS / 1e3), 4), traffic=None,
-                kernel="k_spmv_dot<double,2>", avg_launch_ms=round(spmv_avg, 4),
+                unit="TFLOP/s", frac=round(spmv_tflops / (FP64_PEAK_TFLOPS / 1e3), 4),
+                traffic=(int(SPMV64_DRAM_BYTES_PER_CELL * N) if prof64["pupdate64"][1] else None),
+                traffic_algorithmic=int(SPMV_BYTES_PER_CELL["fp64"] * N),
+                kernel="k_spmv_dot<double,2,3>", avg_launch_ms=round(spmv_avg, 4),
                 peak_source="2 DFMA/clk/SM x 152 SMs x 2.07 GHz (nominal FP64 rate of the part)")
     # ---- mixed (FP32 inner PCG, FP64 refinement)
     def mixed_entry(inner_tol, restart):
@@ -316,31 +328,33 @@ def run_ours(args):
     if not args.no_mixed:
         mixed = mixed_entry(1e-5, 1)            # FP32 inner PCG to 1e-5, restarted FP64 refinement
         mixed_reliable = mixed_entry(0.1, 0)    # FP32 CG with reliable FP64 updates every 10x
-    # ---- end to end through the C ABI with host buffers
+    # ---- end to end through the C ABI with host buffers: every step uploads the state at the
+    # start of the timed region from pinned host memory, runs mhd_step and reads the new state back
     e2e = None
     if not args.no_e2e:
         ds = dev_state()
-        host = {k: torch.from_numpy(v).pin_memory() for k, v in st0.items()}
+        out = {k: torch.empty_like(v, device="cpu").pin_memory() for k, v in snap.items()}
         f = P.make_fields(ds["br"], ds["bt"], ds["bp"], ds["vr"], ds["vt"], ds["vp"])
         prm = P.make_params(nu=w["nu"], eta=w["eta"], cfl=w["cfl"], tol=w["tol"])
         ke = max(1, min(args.steps, 2))
-        h2d = sum(t.numel() * 8 for t in host.values())
+        h2d = sum(t.numel() * 8 for t in snap.values())
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(ke):
             with torch.cuda.stream(stream):
                 for k in ds:
-                    ds[k].copy_(host[k], non_blocking=True)
+                    ds[k].copy_(snap[k], non_blocking=True)
             P.mhd_step(g, prm, f)
             with torch.cuda.stream(stream):
                 for k in ds:
-                    host[k].copy_(ds[k], non_blocking=True)
+                    out[k].copy_(ds[k], non_blocking=True)
             stream.synchronize()
         e1.record(stream)
         barrier()
         e2e = dict(value=round(maxr(e0.elapsed_time(e1) / ke), 3), unit="ms/step", h2d_bytes_per_step=h2d,
-                   d2h_bytes_per_step=h2d)
+                   d2h_bytes_per_step=h2d,
+                   note="each step starts from the state at the start of the timed region (host copy)")
     # ---- CPU baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -492,7 +506,8 @@ def run_adjoint(args):
             P.mhd_step(g, P.make_params(**dict(kw, dt_fixed=dts[n], alpha_si_fixed=als[n])), ff)
         return 0.5 * float(torch.sum((ds["br"][-1] - target) ** 2))
 
-    errs = []
+    errs, errs_g = [], []
+    gnorm = math.sqrt(sum(float(np.sum(a * a)) for a in gv) + float(np.sum(gb * gb)))
     xn = math.sqrt(sum(float(np.sum(st[k] ** 2)) for k in ("vr", "vt", "vp")) + float(np.sum(st["br"][0] ** 2)))
     h = 1e-6 * xn
     t3 = time.perf_counter()
@@ -514,13 +529,52 @@ def run_adjoint(args):
         fd = (L(pert(1.0)) - L(pert(-1.0))) / (2 * h)
         ad = sum(float(np.sum(a * b)) for a, b in zip(gv, dv)) + float(np.sum(gb * db))
         errs.append(abs(fd - ad) / max(abs(fd), abs(ad), 1e-300))
+        errs_g.append(abs(fd - ad) / gnorm)   # |d| = 1: error on the gradient's own scale
     t4 = time.perf_counter()
     print(json.dumps(dict(workload=name, grid=f"{d.nr}x{d.nt}x{d.np}", steps=nsteps, checkpoint_every=5,
                           tol=kw["tol"], loss=float(loss), forward_s=round(t1 - t0, 3),
                           backward_s=round(t2 - t1, 3), ms_per_step_fwd_adj=round(1e3 * (t2 - t0) / nsteps, 1),
                           fd_dirs=args.fd_dirs, fd_rel_err_max=max(errs), fd_rel_err_median=float(np.median(errs)),
+                          fd_err_over_grad_norm_max=max(errs_g),
                           fd_seconds=round(t4 - t3, 1), grad_norm_v=math.sqrt(sum(float(np.sum(a * a)) for a in gv)),
                           grad_norm_br_inner=float(np.linalg.norm(gb)))), flush=True)
+
+
+def run_refinement_study(args):
+    """The workload's first semi-implicit solve in FP64 and in mixed precision with restarted
+    refinement and with reliable updates over a range of inner tolerances (iterations, FP64
+    corrections, wall time)."""
+    import torch
+    from paper_1811_02605_gb300 import build as B
+    B.build()
+    import paper_1811_02605_gb300 as P
+    w, st0 = gen_state(args.workload, args.grid)
+    d = w["desc"]
+    g = P.mhd_grid_create(d.nr, d.nt, d.np, d.r0, d.r1, d.stretch)
+    ds = {k: torch.from_numpy(v).cuda() for k, v in st0.items()}
+    f = P.make_fields(ds["br"], ds["bt"], ds["bp"], ds["vr"], ds["vt"], ds["vp"])
+    c = P.mhd_step_coeffs(g, P.make_params(nu=w["nu"], cfl=w["cfl"]), f)
+    b = torch.empty((3, d.nr, d.nt, d.np), dtype=torch.float64, device="cuda")
+    P.mhd_force(g, f, c["dt"], b)
+    rows = []
+
+    def one(name, **kw):
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        s, it, ou, rr = P.pcg_solve(g, c["alpha_si"], b, x, P.make_params(tol=w["tol"], **kw))
+        torch.cuda.synchronize()
+        rows.append(dict(variant=name, status=P.STATUS_NAMES[s], iters=it, corrections=ou, relres=rr,
+                         seconds=round(time.perf_counter() - t, 4), **{k: v for k, v in kw.items() if k != "precision"}))
+
+    one("fp64")
+    one("mixed warm-up", precision=1, inner_tol=0.1, max_outer=200)   # first mixed solve tunes kernels
+    for restart in (1, 0):
+        for itol in (1e-5, 1e-3, 1e-2, 1e-1, 0.3):
+            one("restarted" if restart else "reliable", precision=1, inner_tol=itol, max_outer=200,
+                max_iter=20000, mixed_restart=restart)
+    print(json.dumps(dict(workload=args.workload, grid=f"{d.nr}x{d.nt}x{d.np}", alpha_si=c["alpha_si"],
+                          rows=rows)), flush=True)
 
 
 def run_profile_case(args):
@@ -562,6 +616,8 @@ def main():
     ap.add_argument("--batched", action="store_true", help="time the 64-system batched solve and exit")
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--adjoint", action="store_true", help="time and check the adjoint workload and exit")
+    ap.add_argument("--refinement-study", action="store_true",
+                    help="first SI solve: FP64 vs mixed (restarted / reliable updates) over inner tolerances")
     ap.add_argument("--adj-steps", type=int, default=20)
     ap.add_argument("--fd-dirs", type=int, default=16)
     ap.add_argument("--no-mixed", action="store_true")
@@ -576,6 +632,8 @@ def main():
         run_batched(args)
     elif args.adjoint:
         run_adjoint(args)
+    elif args.refinement_study:
+        run_refinement_study(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
