@@ -222,3 +222,47 @@ def _adjoint(self, state, lam, dt, asi, nu=1e-3, eta=0.0, cfl=0.4, tol=1e-13, ma
 
 
 Grid.adjoint_step = _adjoint
+
+
+def _rkl2_decl(L):
+    if not getattr(L, "_rkl2_declared", False):
+        _dp2 = _dp
+        L.og_rkl2_stages.restype = C.c_int
+        L.og_rkl2_stages.argtypes = [C.c_void_p, C.c_double, C.c_double]
+        L.og_rkl2.restype = C.c_int
+        L.og_rkl2.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int, _dp2]
+        L.og_step_sts.restype = C.c_int
+        L.og_step_sts.argtypes = [C.c_void_p] + [C.c_double] * 7 + [C.c_int] + [_dp2] * 5
+        L._rkl2_declared = True
+
+
+def _rkl2_stages(self, nu, dt):
+    _rkl2_decl(self.L)
+    return self.L.og_rkl2_stages(self.h, nu, dt)
+
+
+def _rkl2(self, v, nu, dt, stages=0):
+    """v [3, nr, nt, np] advanced over dt by RKL2 super time-stepping; returns (v_new, stages)."""
+    _rkl2_decl(self.L)
+    x = _c(v).copy()
+    s = self.L.og_rkl2(self.h, nu, dt, stages, x)
+    return x, s
+
+
+def _step_sts(self, state, nu=1e-3, eta=0.0, cfl=0.4, dt_fixed=0.0, dt_max=0.0, asi_fixed=-1.0, tol=1e-9,
+              max_iter=100000):
+    """og_step with the viscous PCG solve replaced by RKL2 (info iters[2] = stage count)."""
+    _rkl2_decl(self.L)
+    v = np.ascontiguousarray(np.stack([state["vr"], state["vt"], state["vp"]]), dtype=np.float64)
+    br, bt, bp = _c(state["br"]).copy(), _c(state["bt"]).copy(), _c(state["bp"]).copy()
+    info = np.zeros(11)
+    st = self.L.og_step_sts(self.h, nu, eta, cfl, dt_fixed, dt_max, asi_fixed, tol, max_iter, v, br, bt, bp, info)
+    out = dict(br=br, bt=bt, bp=bp, vr=v[0].copy(), vt=v[1].copy(), vp=v[2].copy())
+    inf = dict(status=st, dt=info[0], cf=info[1], cw=info[2], alpha_si=info[3], alpha_nu=info[4],
+               iters=[int(info[5]), int(info[6]), int(info[7])], relres=list(info[8:11]))
+    return out, inf
+
+
+Grid.rkl2_stages = _rkl2_stages
+Grid.rkl2 = _rkl2
+Grid.step_sts = _step_sts

@@ -1090,3 +1090,89 @@ int og_adjoint_step(const og_grid* g, double nu, double eta, double cfl, double 
     edges_free(e);
     return status;
 }
+
+/* =============================================================================================
+ * Viscosity by RKL2 super time-stepping (Sec. 2.2: the STS option for the viscous term, the
+ * paper's GPU choice in algorithm 3; the method is the second-order Runge-Kutta-Legendre scheme of
+ * Meyer, Balsara & Aslam 2014). It integrates rho V dv/dt = -nu K v over dt explicitly with s
+ * stages:
+ *   b_j = (j^2 + j - 2) / (2 j (j + 1)) for j >= 2, b_0 = b_1 = 1/3, a_j = 1 - b_j,
+ *   w1 = 4 / (s^2 + s - 2),
+ *   Y_1 = Y_0 + (b_1 w1) dt L(Y_0)
+ *   Y_j = mu_j Y_{j-1} + nv_j Y_{j-2} + (1 - mu_j - nv_j) Y_0 + mu_j w1 dt L(Y_{j-1})
+ *         - a_{j-1} mu_j w1 dt L(Y_0),   j = 2..s,
+ *   with mu_j = (2j - 1)/j b_j/b_{j-1}, nv_j = -(j - 1)/j b_j/b_{j-2}, L(v) = -nu D^-1 K v.
+ * The stage count is the smallest s >= 2 with (s^2 + s - 2)/2 >= dt lambda_max, lambda_max
+ * bounded above by Gershgorin: nu max_c (2 sum_f w_f + w_Dirichlet) / (rho_c V_c).
+ * =========================================================================================== */
+static double rkl2_b(int j) { return (j < 2) ? 1.0 / 3.0 : (double)(j * j + j - 2) / (2.0 * j * (j + 1)); }
+
+int og_rkl2_stages(const og_grid* g, double nu, double dt) {
+    int nr = g->nr, nt = g->nt;
+    double lam = 0.0;
+    for (int i = 0; i < nr; i++)
+        for (int j = 0; j < nt; j++) {
+            double s = g->wr[i * nt + j] + g->wr[(i + 1) * nt + j] + g->wt[i * (nt + 1) + j] +
+                       g->wt[i * (nt + 1) + j + 1] + 2.0 * g->wp[i * nt + j];
+            double off = s - (i == 0 ? g->wr[j] : 0.0);  /* the Dirichlet weight has no partner */
+            double l = nu * (s + off) / (g->rho[i * nt + j] * g->vol[i * nt + j]);
+            if (l > lam) lam = l;
+        }
+    int s = 2;
+    while ((double)(s * s + s - 2) / 2.0 < dt * lam) s++;
+    return s;
+}
+
+/* v (3N) advanced in place by s RKL2 stages over dt; s <= 0 picks the stage count */
+int og_rkl2(const og_grid* g, double nu, double dt, int s, double* v) {
+    long long N = g->N, n3 = 3 * N;
+    int np = g->np;
+    if (s <= 0) s = og_rkl2_stages(g, nu, dt);
+    double w1 = 4.0 / (double)(s * s + s - 2);
+    double* y0 = (double*)malloc(sizeof(double) * n3);
+    double* ly0 = (double*)malloc(sizeof(double) * n3);
+    double* ym1 = (double*)malloc(sizeof(double) * n3);
+    double* ym2 = (double*)malloc(sizeof(double) * n3);
+    double* yj = (double*)malloc(sizeof(double) * n3);
+    double* lk = (double*)malloc(sizeof(double) * n3);
+    memcpy(y0, v, sizeof(double) * n3);
+    /* L(Y) = -nu D^-1 K Y, K with its Dirichlet term, D = rho V */
+    apply_op(g, 1.0, 0, 1, 3, y0, lk);
+    for (long long q = 0; q < n3; q++) {
+        long long ij = (q % N) / np;
+        ly0[q] = -nu * lk[q] / (g->rho[ij] * g->vol[ij]);
+    }
+    for (long long q = 0; q < n3; q++) { ym2[q] = y0[q]; ym1[q] = y0[q] + rkl2_b(1) * w1 * dt * ly0[q]; }
+    for (int j = 2; j <= s; j++) {
+        double bj = rkl2_b(j), bj1 = rkl2_b(j - 1), bj2 = rkl2_b(j - 2);
+        double mu = (2.0 * j - 1.0) / j * bj / bj1;
+        double nv = -(j - 1.0) / j * bj / bj2;
+        double mut = mu * w1;
+        double gat = -(1.0 - bj1) * mut;
+        apply_op(g, 1.0, 0, 1, 3, ym1, lk);
+        for (long long q = 0; q < n3; q++) {
+            long long ij = (q % N) / np;
+            double l = -nu * lk[q] / (g->rho[ij] * g->vol[ij]);
+            yj[q] = mu * ym1[q] + nv * ym2[q] + (1.0 - mu - nv) * y0[q] + mut * dt * l + gat * dt * ly0[q];
+        }
+        double* t = ym2; ym2 = ym1; ym1 = yj; yj = t;
+    }
+    memcpy(v, ym1, sizeof(double) * n3);
+    free(y0); free(ly0); free(ym1); free(ym2); free(yj); free(lk);
+    return s;
+}
+
+/* og_step with viscosity by RKL2 (algorithm 3 of the paper: SI by PCG, viscosity by STS);
+ * info[7] holds the stage count */
+int og_step_sts(const og_grid* g, double nu, double eta, double cfl, double dt_fixed, double dt_max,
+                double asi_fixed, double tol, int max_iter, double* v, double* br, double* bt, double* bp,
+                double* info) {
+    /* the step up to v** is og_step's with nu = 0: M_0 = D makes the viscous solve the identity */
+    double co[5];
+    int st = og_coeffs(g, nu, cfl, dt_fixed, dt_max, asi_fixed, v, br, bt, bp, co);
+    if (st != OG_OK) return st;
+    st = og_step(g, 0.0, eta, cfl, co[0], 0.0, co[3], tol, max_iter, v, br, bt, bp, info);
+    int s = og_rkl2(g, nu, co[0], 0, v);
+    if (info) { info[4] = co[4]; info[7] = s; info[10] = 0.0; }
+    return st;
+}

@@ -85,6 +85,15 @@ int og_adjoint_step(const og_grid* g, double nu, double eta, double cfl, double 
                     const double* bp, const double* lv1, const double* lbr1, const double* lbt1,
                     const double* lbp1, double* lv, double* lbr, double* lbt, double* lbp);
 
+/* Viscosity by RKL2 super time-stepping: stage count for (nu, dt), and v (3N) advanced in place
+ * over dt with s stages (s <= 0: chosen by og_rkl2_stages). Returns s. */
+int og_rkl2_stages(const og_grid* g, double nu, double dt);
+int og_rkl2(const og_grid* g, double nu, double dt, int s, double* v);
+/* og_step with the viscous PCG solve replaced by RKL2 (info[7] = stage count) */
+int og_step_sts(const og_grid* g, double nu, double eta, double cfl, double dt_fixed, double dt_max,
+                double asi_fixed, double tol, int max_iter, double* v, double* br, double* bt, double* bp,
+                double* info);
+
 #ifdef __cplusplus
 }
 #endif
