@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "fluxrope_256x256x512"
 METRIC = "ms/zero-beta step, PCG HBM GB/s (% peak) at 256x256x512: FP64 vs mixed"
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070  # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz = 1.259 TFLOP/s
-# algorithmic work of one scaled CG iteration per cell (3 components), see the design doc:
+# algorithmic work of one scaled CG iteration per cell (3 components):
 #   bytes: x, r, p read + written once each = 6 passes x 3 x 8 B (FP64), x 4 B (FP32)
 #   FP64 flops of the SpMV kernel: 6 multiply-adds + 1 add per component + 1 dot FMA = 27 flops
 SPMV_FLOPS_PER_CELL = 3 * (2 * 6 + 1 + 2)
@@ -44,6 +44,12 @@ PCG_BYTES_PER_CELL = {"fp64": 6 * 3 * 8, "fp32": 6 * 3 * 4}
 # which costs nothing while the FP64 pipe binds.
 SPMV64_DRAM_BYTES_PER_CELL = (369.818624e6 + 172.424192e6) / (160 * 160 * 320)
 SPMV_BYTES_PER_CELL = {"fp64": 2 * 3 * 8, "fp32": 2 * 3 * 4}
+# one RKL2 stage per cell (3 components, difference form): the 7-point K stencil of D_{j-1} folded
+# with the mu term (1 multiply, 1 add, 5 FMAs), the nv D_{j-2} and ly0 terms (2 FMAs) = 16 flops
+# per component, plus the per-cell share of the 6 stage coefficients (3 flops); bytes: D_{j-1},
+# D_{j-2} and ly0 read, D_j written = 4 x 3 x 8 B
+STS_FLOPS_PER_CELL = 3 * 16 + 3
+STS_BYTES_PER_CELL = 4 * 3 * 8
 
 
 def peaks():
@@ -237,12 +243,13 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def run(precision, steps, warmup, profile, inner_tol=1e-5, restart=1, snapshot=None):
+    def run(precision, steps, warmup, profile, inner_tol=1e-5, restart=1, snapshot=None, sts=0):
         ds = dev_state()
         torch.cuda.synchronize()
         f = P.make_fields(ds["br"], ds["bt"], ds["bp"], ds["vr"], ds["vt"], ds["vp"])
         prm = P.make_params(nu=w["nu"], eta=w["eta"], cfl=w["cfl"], tol=w["tol"], precision=precision,
-                            inner_tol=inner_tol, max_outer=200, max_iter=20000, mixed_restart=restart)
+                            inner_tol=inner_tol, max_outer=200, max_iter=20000, mixed_restart=restart,
+                            viscosity_sts=sts)
         for _ in range(warmup):
             st, info = P.mhd_step(g, prm, f)
             if st != P.MHD_OK:
@@ -285,6 +292,9 @@ def run_ours(args):
     spmv_ms, spmv_n = prof64["spmv64"]
     pcg64_ms = sum(prof64[k][0] for k in ("pupdate64", "spmv64", "update64"))
     pcg64_n = prof64["spmv64"][1]
+    # share of the FP64 PCG time spent in the viscous solves (by iteration count)
+    visc_it = sum(i["iters"][2] for i in infos64)
+    visc64_ms = pcg64_ms * visc_it / max(pcg64_n, 1) / len(infos64)
     spmv_avg = spmv_ms / max(spmv_n, 1)
     spmv_tflops = SPMV_FLOPS_PER_CELL * N / (spmv_avg * 1e-3) / 1e12
     pcg64_gbs = PCG_BYTES_PER_CELL["fp64"] * N * pcg64_n / (pcg64_ms * 1e-3) / 1e9
@@ -328,6 +338,35 @@ def run_ours(args):
     if not args.no_mixed:
         mixed = mixed_entry(1e-5, 1)            # FP32 inner PCG to 1e-5, restarted FP64 refinement
         mixed_reliable = mixed_entry(0.1, 0)    # FP32 CG with reliable FP64 updates every 10x
+
+    # ---- viscosity by RKL2 super time-stepping (the SI solves unchanged)
+    def sts_entry(precision, inner_tol=0.1, restart=0):
+        mss, infoss, profs, clks, dss = run(precision, args.steps, args.warmup, True, inner_tol, restart, sts=1)
+        mss = maxr(mss)
+        stages = sum(i["iters"][2] for i in infoss)
+        st_ms, st_n = profs["sts"]
+        per_stage = st_ms / max(stages, 1)
+        tflops = STS_FLOPS_PER_CELL * N / (per_stage * 1e-3) / 1e12
+        gbs = STS_BYTES_PER_CELL * N / (per_stage * 1e-3) / 1e9
+        err = {k: float(torch.linalg.norm(dss[k] - ds64[k]) / torch.linalg.norm(ds64[k])) for k in ds64}
+        return dict(si_precision=("fp64" if precision == P.PREC_FP64 else "mixed, reliable updates, inner_tol "
+                                  f"{inner_tol}"),
+                    ms_per_step=round(mss, 3), speedup_vs_fp64=round(ms64 / mss, 3),
+                    stages_per_step=stages / len(infoss),
+                    si_pcg_iters_per_step=sum(i["iters"][0] + i["iters"][1] for i in infoss) / len(infoss),
+                    sts_ms_per_step=round(st_ms / len(infoss), 3), ms_per_stage=round(per_stage, 4),
+                    stage_roofline=dict(bound="alu", achieved=round(tflops, 4), peak=round(FP64_PEAK_TFLOPS / 1e3, 4),
+                                        unit="TFLOP/s", frac=round(tflops / (FP64_PEAK_TFLOPS / 1e3), 4),
+                                        gbs=round(gbs, 1), frac_of_hbm=round(gbs / hbm, 4)),
+                    pcg_viscous_ms_per_step_fp64=round(visc64_ms, 3),
+                    rel_l2_vs_fp64_pcg_viscosity_after_steps=err, clocks=clks,
+                    kernel_ms={k: round(v[0], 3) for k, v in profs.items() if v[1]})
+
+    sts = sts_mixed = None
+    if not args.no_sts:
+        sts = sts_entry(P.PREC_FP64)
+        if not args.no_mixed:
+            sts_mixed = sts_entry(P.PREC_MIXED)
     # ---- end to end through the C ABI with host buffers: every step uploads the state at the
     # start of the timed region from pinned host memory, runs mhd_step and reads the new state back
     e2e = None
@@ -373,7 +412,8 @@ def run_ours(args):
                                 dt=[i["dt"] for i in infos64]),
                     pcg_gbs=dict(fp64=round(pcg64_gbs, 1), fp64_frac_of_hbm=round(pcg64_gbs / hbm, 4),
                                  peak_gbs=hbm, peak_source=peak_src),
-                    roofline=roof, mixed=mixed, mixed_reliable=mixed_reliable, e2e=e2e, cpu_baseline=cpu, clocks=clk64,
+                    roofline=roof, mixed=mixed, mixed_reliable=mixed_reliable, sts=sts, sts_mixed_reliable=sts_mixed,
+                    e2e=e2e, cpu_baseline=cpu, clocks=clk64,
                     gpu_launches=int(launches), kernel_ms={k: round(v[0], 3) for k, v in prof64.items() if v[1]})
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -621,6 +661,7 @@ def main():
     ap.add_argument("--adj-steps", type=int, default=20)
     ap.add_argument("--fd-dirs", type=int, default=16)
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-sts", action="store_true", help="skip the RKL2-viscosity entries")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-iters", type=int, default=1000,

@@ -82,13 +82,20 @@ enum { MHD_PREC_FP64 = 0, MHD_PREC_MIXED = 1 };
  *            residual has fallen by inner_tol, x is corrected in FP64, the true FP64 residual
  *            replaces the recursive one, and the CG recurrence continues with the same search
  *            direction. 1: classic iterative refinement, restarting the FP32 CG from the new
- *            residual at each correction. */
+ *            residual at each correction.
+ *  viscosity_sts  0 (default): viscosity by the implicit solve M_nu v^{n+1} = rho V v** (PCG).
+ *            1: viscosity by RKL2 super time-stepping (second-order Runge-Kutta-Legendre, the
+ *            STS option of Sec. 2.2 / algorithm 3): rho V dv/dt = -nu K v is advanced explicitly
+ *            from v** over dt in s stages, s the smallest s >= 2 with (s^2 + s - 2)/2 >=
+ *            dt lambda, lambda the Gershgorin bound of nu (rho V)^-1 K. info->iters[2] then holds
+ *            s and outer[2], relres[2] are 0. Always FP64 (the SI solves keep `precision`). */
 typedef struct {
     double nu, eta, cfl, dt_fixed, dt_max, alpha_si_fixed;
     double tol, inner_tol;
     int max_iter, max_outer;
     int precision;
     int mixed_restart;
+    int viscosity_sts;
 } mhd_params_t;
 
 /* Caller-owned DEVICE pointers (layouts above). */
@@ -181,8 +188,10 @@ mhd_status_t pcg_solve_batched(int n, const mhd_grid_t* grids, const double* alp
  * params->alpha_si_fixed if >= 0 (else the value computed from state_n), alpha_nu = nu dt, and
  * the upwind directions of the forward step. Given state_n and the cotangent adj_np1 =
  * dL/d(state_{n+1}) (same layout as the fields), writes adj_n = dL/d(state_n). The step's
- * intermediates are recomputed from state_n. PCG solves inside use params->tol. adj_n must not
- * alias adj_np1 or state_n. Synchronises. */
+ * intermediates are recomputed from state_n. PCG solves inside use params->tol. With
+ * params->viscosity_sts = 1 it differentiates the RKL2 step (same stage count): the viscous
+ * transpose is D P D^-1 with D = rho V and P the stage polynomial. adj_n must not alias adj_np1
+ * or state_n. Synchronises. */
 mhd_status_t mhd_adjoint_step(mhd_grid_t grid, const mhd_params_t* params,
                               const mhd_fields_t* state_n, double dt,
                               const mhd_fields_t* adj_np1, mhd_fields_t* adj_n);
@@ -213,7 +222,7 @@ enum {
     MHD_KERNEL_PUPDATE64 = 0, MHD_KERNEL_SPMV64 = 1, MHD_KERNEL_UPDATE64 = 2,
     MHD_KERNEL_PUPDATE32 = 3, MHD_KERNEL_SPMV32 = 4, MHD_KERNEL_UPDATE32 = 5,
     MHD_KERNEL_OUTER_RES = 6, MHD_KERNEL_FORCE = 7, MHD_KERNEL_INDUCTION = 8,
-    MHD_KERNEL_COEFFS = 9, MHD_KERNEL_COUNT = 10
+    MHD_KERNEL_COEFFS = 9, MHD_KERNEL_STS = 10, MHD_KERNEL_COUNT = 11
 };
 mhd_status_t mhd_profile_enable(mhd_grid_t grid, int enable);
 /* Total milliseconds and launch count of one kernel id since profiling was enabled.

@@ -71,6 +71,14 @@ def _declare(L):
     if hasattr(L, "og_adjoint_step"):
         L.og_adjoint_step.restype = i
         L.og_adjoint_step.argtypes = [vp, d, d, d, d, d, d, i] + [_dp] * 12
+        L.og_adjoint_step_sts.restype = i
+        L.og_adjoint_step_sts.argtypes = [vp, d, d, d, d, d, d, i] + [_dp] * 12
+        L.og_rkl2_stages.restype = i
+        L.og_rkl2_stages.argtypes = [vp, d, d]
+        L.og_rkl2.restype = i
+        L.og_rkl2.argtypes = [vp, d, d, i, _dp]
+        L.og_step_sts.restype = i
+        L.og_step_sts.argtypes = [vp] + [d] * 7 + [i] + [_dp] * 5
 
 
 def _c(a):
@@ -208,15 +216,17 @@ class Grid:
         return out, inf
 
 
-def _adjoint(self, state, lam, dt, asi, nu=1e-3, eta=0.0, cfl=0.4, tol=1e-13, max_iter=200000):
-    """Cotangent of state n from the cotangent `lam` of state n+1 (dicts with br, bt, bp, vr, vt, vp)."""
+def _adjoint(self, state, lam, dt, asi, nu=1e-3, eta=0.0, cfl=0.4, tol=1e-13, max_iter=200000, sts=False):
+    """Cotangent of state n from the cotangent `lam` of state n+1 (dicts with br, bt, bp, vr, vt, vp).
+    sts=True: adjoint of step_sts (viscosity by RKL2) instead of step."""
     v = np.ascontiguousarray(np.stack([state["vr"], state["vt"], state["vp"]]), dtype=np.float64)
     lv1 = np.ascontiguousarray(np.stack([lam["vr"], lam["vt"], lam["vp"]]), dtype=np.float64)
     s = self.shapes
     lv = np.empty_like(v)
     lbr, lbt, lbp = np.empty(s["br"]), np.empty(s["bt"]), np.empty(s["bp"])
-    st = self.L.og_adjoint_step(self.h, nu, eta, cfl, dt, asi, tol, max_iter, v, _c(state["br"]), _c(state["bt"]),
-                                _c(state["bp"]), lv1, _c(lam["br"]), _c(lam["bt"]), _c(lam["bp"]), lv, lbr, lbt, lbp)
+    fn = self.L.og_adjoint_step_sts if sts else self.L.og_adjoint_step
+    st = fn(self.h, nu, eta, cfl, dt, asi, tol, max_iter, v, _c(state["br"]), _c(state["bt"]),
+            _c(state["bp"]), lv1, _c(lam["br"]), _c(lam["bt"]), _c(lam["bp"]), lv, lbr, lbt, lbp)
     out = dict(br=lbr, bt=lbt, bp=lbp, vr=lv[0].copy(), vt=lv[1].copy(), vp=lv[2].copy())
     return out, st
 
@@ -224,26 +234,12 @@ def _adjoint(self, state, lam, dt, asi, nu=1e-3, eta=0.0, cfl=0.4, tol=1e-13, ma
 Grid.adjoint_step = _adjoint
 
 
-def _rkl2_decl(L):
-    if not getattr(L, "_rkl2_declared", False):
-        _dp2 = _dp
-        L.og_rkl2_stages.restype = C.c_int
-        L.og_rkl2_stages.argtypes = [C.c_void_p, C.c_double, C.c_double]
-        L.og_rkl2.restype = C.c_int
-        L.og_rkl2.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int, _dp2]
-        L.og_step_sts.restype = C.c_int
-        L.og_step_sts.argtypes = [C.c_void_p] + [C.c_double] * 7 + [C.c_int] + [_dp2] * 5
-        L._rkl2_declared = True
-
-
 def _rkl2_stages(self, nu, dt):
-    _rkl2_decl(self.L)
     return self.L.og_rkl2_stages(self.h, nu, dt)
 
 
 def _rkl2(self, v, nu, dt, stages=0):
     """v [3, nr, nt, np] advanced over dt by RKL2 super time-stepping; returns (v_new, stages)."""
-    _rkl2_decl(self.L)
     x = _c(v).copy()
     s = self.L.og_rkl2(self.h, nu, dt, stages, x)
     return x, s
@@ -252,7 +248,6 @@ def _rkl2(self, v, nu, dt, stages=0):
 def _step_sts(self, state, nu=1e-3, eta=0.0, cfl=0.4, dt_fixed=0.0, dt_max=0.0, asi_fixed=-1.0, tol=1e-9,
               max_iter=100000):
     """og_step with the viscous PCG solve replaced by RKL2 (info iters[2] = stage count)."""
-    _rkl2_decl(self.L)
     v = np.ascontiguousarray(np.stack([state["vr"], state["vt"], state["vp"]]), dtype=np.float64)
     br, bt, bp = _c(state["br"]).copy(), _c(state["bt"]).copy(), _c(state["bp"]).copy()
     info = np.zeros(11)

@@ -1005,10 +1005,10 @@ static void efield_T(const og_grid* g, const double* vb, const double* br, const
     free(lec); free(lbc);
 }
 
-int og_adjoint_step(const og_grid* g, double nu, double eta, double cfl, double dt, double asi_fixed, double tol,
-                    int max_iter, const double* v0, const double* br0, const double* bt0, const double* bp0,
-                    const double* lv1, const double* lbr1, const double* lbt1, const double* lbp1, double* lv,
-                    double* lbr, double* lbt, double* lbp) {
+static int adjoint_step(const og_grid* g, double nu, double eta, double cfl, double dt, double asi_fixed,
+                        double tol, int max_iter, int sts, const double* v0, const double* br0, const double* bt0,
+                        const double* bp0, const double* lv1, const double* lbr1, const double* lbt1,
+                        const double* lbp1, double* lv, double* lbr, double* lbt, double* lbp) {
     long long N = g->N, n3 = 3 * N;
     int np = g->np;
     long long nbr = (long long)(g->nr + 1) * g->nt * np, nbt = (long long)g->nr * (g->nt + 1) * np, nbp = N;
@@ -1049,9 +1049,20 @@ int og_adjoint_step(const og_grid* g, double nu, double eta, double cfl, double 
     memset(lv, 0, sizeof(double) * n3);
     memset(lbr, 0, sizeof(double) * nbr); memset(lbt, 0, sizeof(double) * nbt); memset(lbp, 0, sizeof(double) * nbp);
     memcpy(lB1r, lbr1, sizeof(double) * nbr); memcpy(lB1t, lbt1, sizeof(double) * nbt); memcpy(lB1p, lbp1, sizeof(double) * nbp);
-    /* 5. v' = M_nu^-1 D v**  ->  lam_v** = D M_nu^-1 lam_v' */
-    s = og_pcg(g, anu, 3, lv1, y, tol, max_iter, 0, &it, &rr);
-    if (s != OG_OK) status = s;
+    if (sts) {
+        /* 5. v' = P v** with P the RKL2 polynomial in dt L, L = -nu D^-1 K; K symmetric gives
+         * P^T = D P D^-1, so lam_v** = D P (D^-1 lam_v') (the D factor is applied below) */
+        for (int c = 0; c < 3; c++)
+            for (long long q = 0; q < N; q++) {
+                long long ij = q / np;
+                y[c * N + q] = lv1[c * N + q] / (g->rho[ij] * g->vol[ij]);
+            }
+        og_rkl2(g, nu, dt, 0, y);
+    } else {
+        /* 5. v' = M_nu^-1 D v**  ->  lam_v** = D M_nu^-1 lam_v' */
+        s = og_pcg(g, anu, 3, lv1, y, tol, max_iter, 0, &it, &rr);
+        if (s != OG_OK) status = s;
+    }
     for (int c = 0; c < 3; c++)
         for (long long q = 0; q < N; q++) {
             long long ij = q / np;
@@ -1175,4 +1186,21 @@ int og_step_sts(const og_grid* g, double nu, double eta, double cfl, double dt_f
     int s = og_rkl2(g, nu, co[0], 0, v);
     if (info) { info[4] = co[4]; info[7] = s; info[10] = 0.0; }
     return st;
+}
+
+int og_adjoint_step(const og_grid* g, double nu, double eta, double cfl, double dt, double asi_fixed, double tol,
+                    int max_iter, const double* v0, const double* br0, const double* bt0, const double* bp0,
+                    const double* lv1, const double* lbr1, const double* lbt1, const double* lbp1, double* lv,
+                    double* lbr, double* lbt, double* lbp) {
+    return adjoint_step(g, nu, eta, cfl, dt, asi_fixed, tol, max_iter, 0, v0, br0, bt0, bp0, lv1, lbr1, lbt1, lbp1,
+                        lv, lbr, lbt, lbp);
+}
+
+/* adjoint of og_step_sts (same frozen map: dt, alpha_SI, the stage count, upwind directions) */
+int og_adjoint_step_sts(const og_grid* g, double nu, double eta, double cfl, double dt, double asi_fixed,
+                        double tol, int max_iter, const double* v0, const double* br0, const double* bt0,
+                        const double* bp0, const double* lv1, const double* lbr1, const double* lbt1,
+                        const double* lbp1, double* lv, double* lbr, double* lbt, double* lbp) {
+    return adjoint_step(g, nu, eta, cfl, dt, asi_fixed, tol, max_iter, 1, v0, br0, bt0, bp0, lv1, lbr1, lbt1, lbp1,
+                        lv, lbr, lbt, lbp);
 }

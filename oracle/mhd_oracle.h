@@ -84,6 +84,10 @@ int og_adjoint_step(const og_grid* g, double nu, double eta, double cfl, double 
                     double tol, int max_iter, const double* v, const double* br, const double* bt,
                     const double* bp, const double* lv1, const double* lbr1, const double* lbt1,
                     const double* lbp1, double* lv, double* lbr, double* lbt, double* lbp);
+int og_adjoint_step_sts(const og_grid* g, double nu, double eta, double cfl, double dt, double asi_fixed,
+                    double tol, int max_iter, const double* v, const double* br, const double* bt,
+                    const double* bp, const double* lv1, const double* lbr1, const double* lbt1,
+                    const double* lbp1, double* lv, double* lbr, double* lbt, double* lbp);
 
 /* Viscosity by RKL2 super time-stepping: stage count for (nu, dt), and v (3N) advanced in place
  * over dt with s stages (s <= 0: chosen by og_rkl2_stages). Returns s. */

@@ -531,6 +531,12 @@ __global__ void k_scale_rhov(Dims d, Geo G, double* __restrict__ y, double* __re
     }
 }
 
+__global__ void k_unscale_rhov(Dims d, Geo G, const double* __restrict__ x, double* __restrict__ y) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < 3 * d.N;
+         q += (long long)gridDim.x * blockDim.x)
+        y[q] = x[q] / G.rhoV[(q % d.N) / d.np];
+}
+
 struct AdjWork {
     double *b1r, *b1t, *b1p;          // B^{n+1}
     double *lb1r, *lb1t, *lb1p;       // cotangent of B^{n+1}
@@ -554,8 +560,8 @@ extern "C" mhd_status_t mhd_adjoint_step(mhd_grid_t g, const mhd_params_t* p, co
                                          const mhd_fields_t* a1, mhd_fields_t* a0) {
     if (!g) return MHD_ERR_ARG;
     if (!p || !s0 || !a1 || !a0 || !(dt > 0.0)) return set_error(g, MHD_ERR_ARG, "mhd_adjoint_step: bad argument");
-    if (p->precision != MHD_PREC_FP64 || !(p->tol > 0.0))
-        return set_error(g, MHD_ERR_ARG, "mhd_adjoint_step: FP64 only, tol > 0");
+    if (p->precision != MHD_PREC_FP64 || !(p->tol > 0.0) || (p->viscosity_sts != 0 && p->viscosity_sts != 1))
+        return set_error(g, MHD_ERR_ARG, "mhd_adjoint_step: FP64 only, tol > 0, viscosity_sts 0 or 1");
     const mhd_fields_t* fl[3] = {s0, a1, a0};
     for (const mhd_fields_t* f : fl)
         if (!f->br || !f->bt || !f->bp || !f->vr || !f->vt || !f->vp)
@@ -627,10 +633,17 @@ extern "C" mhd_status_t mhd_adjoint_step(mhd_grid_t g, const mhd_params_t* p, co
     cudaMemcpyAsync(w.lvb + 2 * N, a1->vp, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
     cudaMemsetAsync(w.lv, 0, sizeof(double) * n3, st);
     cudaMemsetAsync(w.y, 0, sizeof(double) * n3, st);
-    // 5. viscous solve
-    stt = solve(g, anu, 3, w.lvb, w.y, w.y, p, nullptr, nullptr, nullptr);
-    if (stt == MHD_ERR_CUDA) return stt;
-    note(stt);
+    if (p->viscosity_sts) {
+        // 5. v' = P v**, P the RKL2 polynomial in dt L (L = -nu D^-1 K, K symmetric), so
+        // P^T = D P D^-1: y = P (D^-1 lam_v'), the D factor follows
+        k_unscale_rhov<<<bc, kThreads, 0, st>>>(d, g->geo, w.lvb, w.y);
+        sts_advance(g, p->nu, &g->ss->dt, dt, w.y);
+    } else {
+        // 5. viscous solve
+        stt = solve(g, anu, 3, w.lvb, w.y, w.y, p, nullptr, nullptr, nullptr);
+        if (stt == MHD_ERR_CUDA) return stt;
+        note(stt);
+    }
     k_scale_rhov<<<bc, kThreads, 0, st>>>(d, g->geo, w.y, w.lv);   // lv = D y, y = lam_dc
     // 4. corrector solve: lam_bc = M_SI^-1 lam_dc; lam_b = lam_bc / 2
     cudaMemsetAsync(w.lb, 0, sizeof(double) * n3, st);

@@ -9,6 +9,7 @@
 // Stiffness weights of K (rho A / centre distance): radial faces use rho0 at the face radius,
 // theta and phi faces rho at the cell-centre radius; the inner face carries the Dirichlet
 // weight rho0(r0) A^r_0j / (rc_0 - r0).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -223,7 +224,7 @@ extern "C" mhd_status_t mhd_grid_create(const mhd_grid_desc_t* desc, void* cuda_
     ok = ok && dalloc(&g->er, (size_t)nr * (nt + 1) * d.np, owned) &&
          dalloc(&g->et, (size_t)(nr + 1) * nt * d.np, owned) &&
          dalloc(&g->ep, (size_t)(nr + 1) * (nt + 1) * d.np, owned) && dalloc(&g->ec, n3, owned) &&
-         dalloc(&g->ring, 2 * (size_t)nr, owned);
+         dalloc(&g->ring, 2 * (size_t)nr, owned) && dalloc(&g->sts_tab, 8 * (size_t)nr * nt, owned);
     ok = ok && dalloc(&g->partials, (size_t)kMaxBlocks * kPartialsPerBlock + 16, owned) &&
          dalloc(&g->sc, 1, owned) && dalloc(&g->ss, 1, owned);
     if (!ok) {
@@ -276,6 +277,16 @@ extern "C" mhd_status_t mhd_grid_create(const mhd_grid_desc_t* desc, void* cuda_
     G.dth = 3.14159265358979323846 / nt;
     G.dph = 2.0 * 3.14159265358979323846 / d.np;
     G.max_kt2 = h.max_kt2;
+    // row sums of |D^-1 K| (the Dirichlet weight sits on the diagonal only)
+    double lam = 0.0;
+    for (int i = 0; i < nr; i++)
+        for (int j = 0; j < nt; j++) {
+            const double s = h.wr[(size_t)i * nt + j] + h.wr[(size_t)(i + 1) * nt + j] + h.wt[(size_t)i * (nt + 1) + j] +
+                             h.wt[(size_t)i * (nt + 1) + j + 1] + 2.0 * h.wp[(size_t)i * nt + j];
+            const double off = s - (i == 0 ? h.wr[j] : 0.0);
+            lam = std::max(lam, (s + off) / h.rhoV[(size_t)i * nt + j]);
+        }
+    g->visc_lambda_unit = lam;
     *out = g;
     return MHD_OK;
 }

@@ -114,6 +114,7 @@ struct mhd_grid_s {
     double *er, *et, *ep;   // edge arrays (E or J)
     double *ec;             // cell-centred E (3N)
     double *ring;           // [2*nr] polar ring sums
+    double *sts_tab;        // [8*nr*nt] RKL2 stage coefficients (nu dt / (rho V) times K's weights)
     double* partials;       // [kMaxBlocks * kPartialsPerBlock]
     void* adj_mem;          // adjoint workspace, allocated by the first adjoint call
     mhd::PcgScalars* sc;    // device
@@ -126,6 +127,7 @@ struct mhd_grid_s {
     int graph_batch;
     int slab32;             // r-slab length of the tiled FP32 kernels (0: not tuned, -1: split kernels)
     int slab64;             // same for the FP64 fused p-update + stencil kernel
+    double visc_lambda_unit; // Gershgorin bound on the spectral radius of D^-1 K (nu = 1)
     std::string last_error;
     // kernel timing (diagnostics)
     int prof;
@@ -153,6 +155,8 @@ void induction(mhd_grid_s* g, const double* vr, const double* vt, const double* 
                const double* dlt, double dfac, double eta, const double* dt_dev, double dt_host,
                double* br, double* bt, double* bp);
 void vstar_rhs(mhd_grid_s* g, double* vr, double* vt, double* vp, const double* dlt, double* b);
+int sts_stages(const mhd_grid_s* g, double nu, double dt);
+int sts_advance(mhd_grid_s* g, double nu, const double* dt_dev, double dt_host, double* y);
 
 // tiled FP32 CG kernels (tiled.cu)
 bool tiled32_ok(const mhd_grid_s* g);

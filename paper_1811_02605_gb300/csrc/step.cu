@@ -21,6 +21,8 @@ mhd_status_t check_params(mhd_grid_s* g, const mhd_params_t* p) {
         return set_error(g, MHD_ERR_ARG, "params: mixed precision needs 0 < inner_tol < 1, max_outer >= 1");
     if (!(p->nu >= 0.0) || !(p->cfl > 0.0))
         return set_error(g, MHD_ERR_ARG, "params: need nu >= 0 and cfl > 0");
+    if (p->viscosity_sts != 0 && p->viscosity_sts != 1)
+        return set_error(g, MHD_ERR_ARG, "params: viscosity_sts must be 0 (implicit PCG) or 1 (RKL2)");
     return MHD_OK;
 }
 
@@ -101,9 +103,16 @@ extern "C" mhd_status_t mhd_step(mhd_grid_t g, const mhd_params_t* p, mhd_fields
     cudaMemcpyAsync(g->b1 + d.N, f->vt, bytes3 / 3, cudaMemcpyDeviceToDevice, g->stream);
     cudaMemcpyAsync(g->b1 + 2 * d.N, f->vp, bytes3 / 3, cudaMemcpyDeviceToDevice, g->stream);
     vstar_rhs(g, g->b1, g->b1 + d.N, g->b1 + 2 * d.N, g->dlt, g->b0);
-    st = solve(g, &g->ss->alpha_nu, 3, g->b0, g->b1, g->b1, p, &it[2], &ou[2], &rr[2]);
-    if (st == MHD_ERR_CUDA) return st;
-    if (st != MHD_OK && worst == MHD_OK) worst = st;
+    if (p->viscosity_sts) {
+        // RKL2 super time-stepping of rho V dv/dt = -nu K v from v** over dt (algorithm 3)
+        ps = prof_begin(g, g->stream, MHD_KERNEL_STS);
+        it[2] = sts_advance(g, p->nu, dt_dev, g->h_ss->dt, g->b1);
+        prof_end(g, g->stream, ps);
+    } else {
+        st = solve(g, &g->ss->alpha_nu, 3, g->b0, g->b1, g->b1, p, &it[2], &ou[2], &rr[2]);
+        if (st == MHD_ERR_CUDA) return st;
+        if (st != MHD_OK && worst == MHD_OK) worst = st;
+    }
     cudaMemcpyAsync(f->vr, g->b1, bytes3 / 3, cudaMemcpyDeviceToDevice, g->stream);
     cudaMemcpyAsync(f->vt, g->b1 + d.N, bytes3 / 3, cudaMemcpyDeviceToDevice, g->stream);
     cudaMemcpyAsync(f->vp, g->b1 + 2 * d.N, bytes3 / 3, cudaMemcpyDeviceToDevice, g->stream);

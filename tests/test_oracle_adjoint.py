@@ -32,13 +32,14 @@ def _setup(seed=0, eta=0.0, scale_v=20.0, d=I.GridDesc(6, 6, 12, 1.0, 4.0, 1.1))
     return g, st, c, lam, rng
 
 
-def _fd_check(g, st, c, lam, rng, eta, ndir=4):
+def _fd_check(g, st, c, lam, rng, eta, ndir=4, sts=False, nu=1e-3):
     dt, asi = c["dt"], c["alpha_si"]
-    adj, status = g.adjoint_step(st, lam, dt, asi, eta=eta, cfl=0.3)
+    adj, status = g.adjoint_step(st, lam, dt, asi, nu=nu, eta=eta, cfl=0.3, sts=sts)
     assert status == O.OK
+    fwd = g.step_sts if sts else g.step
 
     def L(x):
-        out, info = g.step(x, nu=1e-3, eta=eta, cfl=0.3, dt_fixed=dt, asi_fixed=asi, tol=1e-14, max_iter=200000)
+        out, info = fwd(x, nu=nu, eta=eta, cfl=0.3, dt_fixed=dt, asi_fixed=asi, tol=1e-14, max_iter=200000)
         assert info["status"] == O.OK
         return _dot(lam, out)
 
@@ -83,3 +84,27 @@ def test_inner_boundary_flux_gradient_nonzero():
     g, st, c, lam, rng = _setup(3)
     a, _ = g.adjoint_step(st, lam, c["dt"], c["alpha_si"])
     assert np.abs(a["br"][0]).max() > 0.0
+
+
+def test_adjoint_of_sts_step_matches_central_differences():
+    # viscosity by RKL2 with enough stages that the polynomial is far from the identity
+    g, st, c, lam, rng = _setup(3)
+    nu = 1.0
+    assert g.rkl2_stages(nu, c["dt"]) >= 5
+    errs = _fd_check(g, st, c, lam, rng, 0.0, ndir=3, sts=True, nu=nu)
+    assert max(errs) < 1e-6, errs
+
+
+def test_rkl2_polynomial_is_self_adjoint_in_the_mass_inner_product():
+    # P(dt L) with L = -nu D^-1 K and K symmetric satisfies <u, D P v> = <P u, D v>; the adjoint of
+    # the STS step relies on it (P^T = D P D^-1)
+    d = I.GridDesc(6, 6, 12, 1.0, 4.0, 1.1)
+    g = O.Grid.from_desc(d)
+    rng = np.random.default_rng(7)
+    u, v = rng.normal(size=(2, 3, d.nr, d.nt, d.np))
+    D = g.apply_M(0.0, np.ones((1, d.nr, d.nt, d.np)))   # M_0 = D = rho V
+    pu, s = g.rkl2(u, 1.0, 0.1)
+    pv, _ = g.rkl2(v, 1.0, 0.1)
+    assert s >= 5
+    a, b = float(np.sum(u * D * pv)), float(np.sum(pu * D * v))
+    assert abs(a - b) <= 1e-12 * (abs(a) + abs(b))
