@@ -57,6 +57,8 @@ def _declare(L):
     L.og_diag.argtypes = [vp, d, _dp]
     L.og_pcg.restype = i
     L.og_pcg.argtypes = [vp, d, i, _dp, _dp, d, i, i, C.POINTER(C.c_int), C.POINTER(C.c_double)]
+    L.og_pcg_cg.restype = i
+    L.og_pcg_cg.argtypes = L.og_pcg.argtypes
     L.og_coeffs.restype = i
     L.og_coeffs.argtypes = [vp, d, d, d, d, d, _dp, _dp, _dp, _dp, _dp]
     L.og_bcentre.argtypes = [vp, _dp, _dp, _dp, _dp]
@@ -68,6 +70,8 @@ def _declare(L):
     L.og_divb.argtypes = [vp, _dp, _dp, _dp, _dp]
     L.og_step.restype = i
     L.og_step.argtypes = [vp, d, d, d, d, d, d, d, i, _dp, _dp, _dp, _dp, _dp]
+    L.og_step_cg.restype = i
+    L.og_step_cg.argtypes = L.og_step.argtypes
     if hasattr(L, "og_adjoint_step"):
         L.og_adjoint_step.restype = i
         L.og_adjoint_step.argtypes = [vp, d, d, d, d, d, d, i] + [_dp] * 12
@@ -147,13 +151,14 @@ class Grid:
         self.L.og_diag(self.h, alpha, o)
         return o
 
-    def pcg(self, alpha, b, x0=None, tol=1e-9, max_iter=100000, fixed_iters=0):
+    def pcg(self, alpha, b, x0=None, tol=1e-9, max_iter=100000, fixed_iters=0, cg=False):
+        """Jacobi PCG; cg=True: the single-reduction (Chronopoulos-Gear) form."""
         b = _c(b)
         x = np.zeros_like(b) if x0 is None else _c(x0).copy()
         it = C.c_int(0)
         rr = C.c_double(0)
-        st = self.L.og_pcg(self.h, alpha, b.size // self.N, b, x, tol, max_iter, fixed_iters,
-                           C.byref(it), C.byref(rr))
+        fn = self.L.og_pcg_cg if cg else self.L.og_pcg
+        st = fn(self.h, alpha, b.size // self.N, b, x, tol, max_iter, fixed_iters, C.byref(it), C.byref(rr))
         return x, it.value, rr.value, st
 
     def coeffs(self, v, br, bt, bp, nu=1e-3, cfl=0.4, dt_fixed=0.0, dt_max=0.0, asi_fixed=-1.0):
@@ -202,13 +207,14 @@ class Grid:
         return o
 
     def step(self, state, nu=1e-3, eta=0.0, cfl=0.4, dt_fixed=0.0, dt_max=0.0, asi_fixed=-1.0,
-             tol=1e-9, max_iter=100000):
-        """One step on a copy of `state` (dict br, bt, bp, vr, vt, vp). Returns (new, info)."""
+             tol=1e-9, max_iter=100000, cg=False):
+        """One step on a copy of `state` (dict br, bt, bp, vr, vt, vp). Returns (new, info).
+        cg=True: every solve in the single-reduction PCG form."""
         v = np.ascontiguousarray(np.stack([state["vr"], state["vt"], state["vp"]]), dtype=np.float64)
         br, bt, bp = _c(state["br"]).copy(), _c(state["bt"]).copy(), _c(state["bp"]).copy()
         info = np.zeros(11)
-        st = self.L.og_step(self.h, nu, eta, cfl, dt_fixed, dt_max, asi_fixed, tol, max_iter, v, br,
-                            bt, bp, info)
+        fn = self.L.og_step_cg if cg else self.L.og_step
+        st = fn(self.h, nu, eta, cfl, dt_fixed, dt_max, asi_fixed, tol, max_iter, v, br, bt, bp, info)
         out = dict(br=br, bt=bt, bp=bp, vr=v[0].copy(), vt=v[1].copy(), vp=v[2].copy())
         inf = dict(status=st, dt=info[0], cf=info[1], cw=info[2], alpha_si=info[3],
                    alpha_nu=info[4], iters=[int(info[5]), int(info[6]), int(info[7])],

@@ -232,6 +232,74 @@ int og_pcg(const og_grid* g, double alpha, int ncomp, const double* b, double* x
 }
 
 /* ---------------------------------------------------------------------------------------------
+ * The same Jacobi PCG in the single-reduction form of Chronopoulos & Gear (1989): the search
+ * direction's image s = M p is carried by its own recurrence, so both inner products of an
+ * iteration, (r, u) and (M u, u) with u = D^-1 r, come from one pass after one operator
+ * application. In exact arithmetic the iterates are those of og_pcg; the stop test, the count and
+ * the b = 0 case are the same.
+ * ------------------------------------------------------------------------------------------- */
+int og_pcg_cg(const og_grid* g, double alpha, int ncomp, const double* b, double* x, double tol,
+              int max_iter, int fixed_iters, int* iters, double* relres) {
+    long long N = g->N, n = ncomp * N;
+    int nt = g->nt, np = g->np;
+    double bnorm = sqrt(dot(n, b, b));
+    if (bnorm == 0.0) {
+        memset(x, 0, sizeof(double) * n);
+        *iters = 0; *relres = 0.0;
+        return OG_OK;
+    }
+    double* d = (double*)malloc(sizeof(double) * g->nr * nt);
+    double* r = (double*)malloc(sizeof(double) * n);
+    double* u = (double*)malloc(sizeof(double) * n);
+    double* w = (double*)malloc(sizeof(double) * n);
+    double* p = (double*)calloc(n, sizeof(double));
+    double* sv = (double*)calloc(n, sizeof(double));
+    og_diag(g, alpha, d);
+    og_apply_M(g, alpha, ncomp, x, w);
+    for (long long e = 0; e < n; e++) r[e] = b[e] - w[e];
+    for (long long e = 0; e < n; e++) u[e] = r[e] / d[(e % N) / np];
+    og_apply_M(g, alpha, ncomp, u, w);
+    double gam = dot(n, r, u), del = dot(n, w, u);
+    double rn = sqrt(dot(n, r, r));
+    double a = 0.0, gam_old = 0.0;
+    int k = 0;
+    int status = OG_OK;
+    for (;;) {
+        if (fixed_iters > 0) {
+            if (k >= fixed_iters) break;
+        } else {
+            if (rn <= tol * bnorm) break;
+            if (k >= max_iter) { status = OG_ERR_NOCONV; break; }
+        }
+        double beta, den;
+        if (k == 0) {
+            beta = 0.0;
+            den = del;
+        } else {
+            beta = gam / gam_old;
+            den = del - beta * gam / a;
+        }
+        if (!(den > 0.0)) { status = OG_ERR_NOCONV; break; }
+        a = gam / den;
+        for (long long e = 0; e < n; e++) p[e] = u[e] + beta * p[e];
+        for (long long e = 0; e < n; e++) sv[e] = w[e] + beta * sv[e];
+        for (long long e = 0; e < n; e++) x[e] += a * p[e];
+        for (long long e = 0; e < n; e++) r[e] -= a * sv[e];
+        k++;
+        for (long long e = 0; e < n; e++) u[e] = r[e] / d[(e % N) / np];
+        og_apply_M(g, alpha, ncomp, u, w);
+        gam_old = gam;
+        gam = dot(n, r, u);
+        del = dot(n, w, u);
+        rn = sqrt(dot(n, r, r));
+    }
+    *iters = k;
+    *relres = rn / bnorm;
+    free(d); free(r); free(u); free(w); free(p); free(sv);
+    return status;
+}
+
+/* ---------------------------------------------------------------------------------------------
  * Cell-centred B (reading R4): mean of the two opposite faces; in the polar rings the theta
  * component takes only the non-polar face.
  * ------------------------------------------------------------------------------------------- */
@@ -642,9 +710,11 @@ int og_coeffs(const og_grid* g, double nu, double cfl, double dt_fixed, double d
  *   4. corrector: M_SI d_c = rho V dt (F(v^n,B^n) + F(v_p,B^{n+1}))/2, x0 = d_p; v** = v^n + d_c
  *   5. viscosity: M_nu v^{n+1} = rho V v**, x0 = v**
  * ------------------------------------------------------------------------------------------- */
-int og_step(const og_grid* g, double nu, double eta, double cfl, double dt_fixed, double dt_max,
-            double asi_fixed, double tol, int max_iter, double* v, double* br, double* bt,
-            double* bp, double* info) {
+typedef int (*pcg_fn)(const og_grid*, double, int, const double*, double*, double, int, int, int*, double*);
+
+static int step_impl(const og_grid* g, pcg_fn pcg, double nu, double eta, double cfl, double dt_fixed,
+                     double dt_max, double asi_fixed, double tol, int max_iter, double* v, double* br,
+                     double* bt, double* bp, double* info) {
     long long N = g->N, n3 = 3 * N;
     int nt = g->nt, np = g->np;
     double co[5];
@@ -662,7 +732,7 @@ int og_step(const og_grid* g, double nu, double eta, double cfl, double dt_fixed
     int status = OG_OK, s;
 
     og_force(g, v, br, bt, bp, dt, b0);
-    s = og_pcg(g, asi, 3, b0, dlt, tol, max_iter, 0, &it[0], &rr[0]);
+    s = pcg(g, asi, 3, b0, dlt, tol, max_iter, 0, &it[0], &rr[0]);
     if (s != OG_OK) status = s;
     for (long long e2 = 0; e2 < n3; e2++) vp[e2] = v[e2] + dlt[e2];
     for (long long e2 = 0; e2 < n3; e2++) vb[e2] = 0.5 * (v[e2] + vp[e2]);
@@ -670,7 +740,7 @@ int og_step(const og_grid* g, double nu, double eta, double cfl, double dt_fixed
     og_ct(g, e.jr, e.jt, e.jp, dt, br, bt, bp);
     og_force(g, vp, br, bt, bp, dt, b1);
     for (long long e2 = 0; e2 < n3; e2++) b1[e2] = 0.5 * (b0[e2] + b1[e2]);
-    s = og_pcg(g, asi, 3, b1, dlt, tol, max_iter, 0, &it[1], &rr[1]);
+    s = pcg(g, asi, 3, b1, dlt, tol, max_iter, 0, &it[1], &rr[1]);
     if (s != OG_OK) status = s;
     for (long long e2 = 0; e2 < n3; e2++) v[e2] = v[e2] + dlt[e2];          /* v** */
     for (int c = 0; c < 3; c++)
@@ -679,7 +749,7 @@ int og_step(const og_grid* g, double nu, double eta, double cfl, double dt_fixed
             b0[c * N + q] = g->rho[ij] * g->vol[ij] * v[c * N + q];
         }
     (void)nt;
-    s = og_pcg(g, anu, 3, b0, v, tol, max_iter, 0, &it[2], &rr[2]);
+    s = pcg(g, anu, 3, b0, v, tol, max_iter, 0, &it[2], &rr[2]);
     if (s != OG_OK) status = s;
     if (info) {
         for (int q = 0; q < 5; q++) info[q] = co[q];
@@ -688,6 +758,20 @@ int og_step(const og_grid* g, double nu, double eta, double cfl, double dt_fixed
     free(b0); free(b1); free(dlt); free(vp); free(vb);
     edges_free(e);
     return status;
+}
+
+int og_step(const og_grid* g, double nu, double eta, double cfl, double dt_fixed, double dt_max,
+            double asi_fixed, double tol, int max_iter, double* v, double* br, double* bt,
+            double* bp, double* info) {
+    return step_impl(g, og_pcg, nu, eta, cfl, dt_fixed, dt_max, asi_fixed, tol, max_iter, v, br, bt, bp, info);
+}
+
+/* og_step with every solve in the single-reduction PCG form (og_pcg_cg) */
+int og_step_cg(const og_grid* g, double nu, double eta, double cfl, double dt_fixed, double dt_max,
+               double asi_fixed, double tol, int max_iter, double* v, double* br, double* bt,
+               double* bp, double* info) {
+    return step_impl(g, og_pcg_cg, nu, eta, cfl, dt_fixed, dt_max, asi_fixed, tol, max_iter, v, br, bt, bp,
+                     info);
 }
 
 /* =============================================================================================

@@ -46,6 +46,9 @@ void og_diag(const og_grid* g, double alpha, double* d);
  * iterations. Returns OG_OK or OG_ERR_NOCONV. */
 int og_pcg(const og_grid* g, double alpha, int ncomp, const double* b, double* x, double tol,
            int max_iter, int fixed_iters, int* iters, double* relres);
+/* og_pcg in the single-reduction (Chronopoulos-Gear) form */
+int og_pcg_cg(const og_grid* g, double alpha, int ncomp, const double* b, double* x, double tol,
+           int max_iter, int fixed_iters, int* iters, double* relres);
 
 /* step coefficients: out = {dt, C_f, C_w, alpha_SI, alpha_nu} */
 int og_coeffs(const og_grid* g, double nu, double cfl, double dt_fixed, double dt_max,
@@ -73,6 +76,9 @@ void og_divb(const og_grid* g, const double* br, const double* bt, const double*
  * replaces the computed alpha_SI (frozen map for finite differences). info = {dt, cf, cw, asi, anu, it0, it1, it2,
  * rr0, rr1, rr2} (11 doubles) */
 int og_step(const og_grid* g, double nu, double eta, double cfl, double dt_fixed, double dt_max,
+            double asi_fixed, double tol, int max_iter, double* v, double* br, double* bt,
+            double* bp, double* info);
+int og_step_cg(const og_grid* g, double nu, double eta, double cfl, double dt_fixed, double dt_max,
             double asi_fixed, double tol, int max_iter, double* v, double* br, double* bt,
             double* bp, double* info);
 

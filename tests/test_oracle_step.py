@@ -81,3 +81,17 @@ def test_viscous_solve_alone():
     # without viscosity and field the step is the explicit predictor-corrector alone
     for k in ("br", "bt", "bp"):
         assert np.all(out0[k] == 0.0)
+
+
+def test_step_with_single_reduction_pcg_agrees_within_solver_tolerance():
+    # the two PCG forms share their iterates up to rounding, so a step differs by O(tol) at most
+    d = I.GridDesc(8, 8, 16, 1.0, 10.0, 1.05)
+    st = I.initial_state(d, 0, False)
+    g = O.Grid.from_desc(d)
+    a, ia = g.step(st, tol=1e-10)
+    b, ib = g.step(st, tol=1e-10, cg=True)
+    assert ia["status"] == O.OK and ib["status"] == O.OK
+    for q in range(3):
+        assert abs(ia["iters"][q] - ib["iters"][q]) <= 1
+    for k in ("vr", "vt", "vp", "br", "bt", "bp"):
+        assert np.linalg.norm(a[k] - b[k]) <= 1e-8 * np.linalg.norm(a[k]), k
