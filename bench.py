@@ -243,13 +243,13 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def run(precision, steps, warmup, profile, inner_tol=1e-5, restart=1, snapshot=None, sts=0):
+    def run(precision, steps, warmup, profile, inner_tol=1e-5, restart=1, snapshot=None, sts=0, variant=0):
         ds = dev_state()
         torch.cuda.synchronize()
         f = P.make_fields(ds["br"], ds["bt"], ds["bp"], ds["vr"], ds["vt"], ds["vp"])
         prm = P.make_params(nu=w["nu"], eta=w["eta"], cfl=w["cfl"], tol=w["tol"], precision=precision,
                             inner_tol=inner_tol, max_outer=200, max_iter=20000, mixed_restart=restart,
-                            viscosity_sts=sts)
+                            viscosity_sts=sts, pcg_variant=variant)
         for _ in range(warmup):
             st, info = P.mhd_step(g, prm, f)
             if st != P.MHD_OK:
@@ -362,6 +362,22 @@ def run_ours(args):
                     rel_l2_vs_fp64_pcg_viscosity_after_steps=err, clocks=clks,
                     kernel_ms={k: round(v[0], 3) for k, v in profs.items() if v[1]})
 
+    # ---- FP64 with the single-reduction (Chronopoulos-Gear) PCG form
+    pcg_cg = None
+    if not args.no_cg:
+        msc, infosc, profc, clkc, dsc = run(P.PREC_FP64, args.steps, args.warmup, True, variant=1)
+        msc = maxr(msc)
+        itc = sum(sum(i["iters"]) for i in infosc) / len(infosc)
+        c_ms = profc["spmv64"][0] + profc["update64"][0]
+        c_n = profc["spmv64"][1]
+        pcg_cg = dict(ms_per_step=round(msc, 3), speedup_vs_fp64=round(ms64 / msc, 3), pcg_iters_per_step=itc,
+                      ms_per_iteration=round(c_ms / max(c_n, 1), 4),
+                      ms_per_iteration_hestenes_stiefel=round(pcg64_ms / max(pcg64_n, 1), 4),
+                      kernels_per_iteration=2,
+                      rel_l2_vs_fp64_after_steps={k: float(torch.linalg.norm(dsc[k] - ds64[k]) /
+                                                           torch.linalg.norm(ds64[k])) for k in ds64},
+                      clocks=clkc, kernel_ms={k: round(v[0], 3) for k, v in profc.items() if v[1]})
+
     sts = sts_mixed = None
     if not args.no_sts:
         sts = sts_entry(P.PREC_FP64)
@@ -412,7 +428,7 @@ def run_ours(args):
                                 dt=[i["dt"] for i in infos64]),
                     pcg_gbs=dict(fp64=round(pcg64_gbs, 1), fp64_frac_of_hbm=round(pcg64_gbs / hbm, 4),
                                  peak_gbs=hbm, peak_source=peak_src),
-                    roofline=roof, mixed=mixed, mixed_reliable=mixed_reliable, sts=sts, sts_mixed_reliable=sts_mixed,
+                    roofline=roof, mixed=mixed, mixed_reliable=mixed_reliable, sts=sts, sts_mixed_reliable=sts_mixed, pcg_single_reduction=pcg_cg,
                     e2e=e2e, cpu_baseline=cpu, clocks=clk64,
                     gpu_launches=int(launches), kernel_ms={k: round(v[0], 3) for k, v in prof64.items() if v[1]})
         print(json.dumps(line), flush=True)
@@ -662,6 +678,7 @@ def main():
     ap.add_argument("--fd-dirs", type=int, default=16)
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-sts", action="store_true", help="skip the RKL2-viscosity entries")
+    ap.add_argument("--no-cg", action="store_true", help="skip the single-reduction PCG entry")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-iters", type=int, default=1000,

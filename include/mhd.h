@@ -88,7 +88,14 @@ enum { MHD_PREC_FP64 = 0, MHD_PREC_MIXED = 1 };
  *            STS option of Sec. 2.2 / algorithm 3): rho V dv/dt = -nu K v is advanced explicitly
  *            from v** over dt in s stages, s the smallest s >= 2 with (s^2 + s - 2)/2 >=
  *            dt lambda, lambda the Gershgorin bound of nu (rho V)^-1 K. info->iters[2] then holds
- *            s and outer[2], relres[2] are 0. Always FP64 (the SI solves keep `precision`). */
+ *            s and outer[2], relres[2] are 0. Always FP64 (the SI solves keep `precision`).
+ *  pcg_variant  0 (default): Hestenes-Stiefel PCG (three kernels and two reductions per
+ *            iteration). 1: the same Jacobi PCG in the single-reduction form of Chronopoulos &
+ *            Gear (1989): s = M p is updated by its own recurrence, so one operator application
+ *            gives both inner products and an iteration is two kernels with one reduction. Same
+ *            iterates in exact arithmetic; rounding differs. FP64 only (MHD_ERR_ARG with
+ *            precision = MHD_PREC_MIXED); applies to every solve of pcg_solve, mhd_step and
+ *            mhd_adjoint_step (pcg_solve_batched ignores it). */
 typedef struct {
     double nu, eta, cfl, dt_fixed, dt_max, alpha_si_fixed;
     double tol, inner_tol;
@@ -96,6 +103,7 @@ typedef struct {
     int precision;
     int mixed_restart;
     int viscosity_sts;
+    int pcg_variant;
 } mhd_params_t;
 
 /* Caller-owned DEVICE pointers (layouts above). */

@@ -44,7 +44,7 @@ class Params(C.Structure):
                 ("dt_fixed", C.c_double), ("dt_max", C.c_double), ("alpha_si_fixed", C.c_double),
                 ("tol", C.c_double), ("inner_tol", C.c_double),
                 ("max_iter", C.c_int), ("max_outer", C.c_int), ("precision", C.c_int),
-                ("mixed_restart", C.c_int), ("viscosity_sts", C.c_int)]
+                ("mixed_restart", C.c_int), ("viscosity_sts", C.c_int), ("pcg_variant", C.c_int)]
 
 
 class Fields(C.Structure):
@@ -131,9 +131,9 @@ def _check(st, grid=None, soft=(MHD_OK,)):
 
 def make_params(nu=1e-3, eta=0.0, cfl=0.4, dt_fixed=0.0, dt_max=0.0, alpha_si_fixed=-1.0, tol=1e-9,
                 inner_tol=1e-5, max_iter=100000, max_outer=30, precision=PREC_FP64,
-                mixed_restart=0, viscosity_sts=0) -> Params:
+                mixed_restart=0, viscosity_sts=0, pcg_variant=0) -> Params:
     return Params(nu, eta, cfl, dt_fixed, dt_max, alpha_si_fixed, tol, inner_tol, max_iter, max_outer,
-                  precision, mixed_restart, viscosity_sts)
+                  precision, mixed_restart, viscosity_sts, pcg_variant)
 
 
 def make_fields(br, bt, bp, vr=None, vt=None, vp=None) -> Fields:

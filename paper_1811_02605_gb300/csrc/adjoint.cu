@@ -560,8 +560,9 @@ extern "C" mhd_status_t mhd_adjoint_step(mhd_grid_t g, const mhd_params_t* p, co
                                          const mhd_fields_t* a1, mhd_fields_t* a0) {
     if (!g) return MHD_ERR_ARG;
     if (!p || !s0 || !a1 || !a0 || !(dt > 0.0)) return set_error(g, MHD_ERR_ARG, "mhd_adjoint_step: bad argument");
-    if (p->precision != MHD_PREC_FP64 || !(p->tol > 0.0) || (p->viscosity_sts != 0 && p->viscosity_sts != 1))
-        return set_error(g, MHD_ERR_ARG, "mhd_adjoint_step: FP64 only, tol > 0, viscosity_sts 0 or 1");
+    if (p->precision != MHD_PREC_FP64 || !(p->tol > 0.0) || (p->viscosity_sts != 0 && p->viscosity_sts != 1) ||
+        (p->pcg_variant != 0 && p->pcg_variant != 1))
+        return set_error(g, MHD_ERR_ARG, "mhd_adjoint_step: FP64 only, tol > 0, viscosity_sts and pcg_variant 0 or 1");
     const mhd_fields_t* fl[3] = {s0, a1, a0};
     for (const mhd_fields_t* f : fl)
         if (!f->br || !f->bt || !f->bp || !f->vr || !f->vt || !f->vp)

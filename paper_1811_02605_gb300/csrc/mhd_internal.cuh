@@ -122,8 +122,9 @@ struct mhd_grid_s {
     mhd::PcgScalars* h_sc;  // pinned host mirror
     mhd::StepScalars* h_ss; // pinned host mirror
     double* h_alpha;        // pinned host scalar staging
-    // CUDA graphs of a batch of PCG iterations, keyed by precision and ncomp
-    cudaGraphExec_t iter_graph[2][4];
+    // CUDA graphs of a batch of PCG iterations, keyed by kind (FP64, FP32 inner, FP64
+    // single-reduction) and ncomp
+    cudaGraphExec_t iter_graph[3][4];
     int graph_batch;
     int slab32;             // r-slab length of the tiled FP32 kernels (0: not tuned, -1: split kernels)
     int slab64;             // same for the FP64 fused p-update + stencil kernel

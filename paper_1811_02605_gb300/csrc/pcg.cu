@@ -300,6 +300,112 @@ __global__ void __launch_bounds__(kThreads) k_update(Dims d, T* __restrict__ x,
 }
 
 // ------------------------------------------------------------------------------------------
+// single-reduction (Chronopoulos-Gear) form, FP64: s = A~ p is carried by its own recurrence,
+// so one stencil pass w = A~ r yields every inner product of an iteration
+// ------------------------------------------------------------------------------------------
+// C1: w = A~ r, gamma = <r~, r~>, delta = <w, r~>, rr = sum dg r~^2; last CTA: stop test on the
+// current residual, then beta, alpha (first iteration: beta = 0, alpha = gamma / delta) and the
+// iteration count of the update that follows
+template <int NC>
+__global__ void __launch_bounds__(kThreads, 4) k_cg_spmv(Dims d, const double* __restrict__ r,
+                                                         double* __restrict__ w, OpTab<double> t,
+                                                         const double* __restrict__ dg, PcgScalars* sc,
+                                                         double* __restrict__ partials) {
+    if (sc->done) return;
+    const int nt = d.nt;
+    const unsigned int G = (unsigned int)(d.N / 2);
+    double a_g = 0.0, a_d = 0.0, a_rr = 0.0;
+    for (unsigned int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+        const Cell c = decompose<2>(d, g);
+        const double cr_lo = t.ar[c.i * nt + c.j], cr_hi = t.ar[(c.i + 1) * nt + c.j];
+        const double ct_lo = t.at[c.i * (nt + 1) + c.j], ct_hi = t.at[c.i * (nt + 1) + c.j + 1];
+        const double cp = t.ap[c.ij];
+        double cell = 0.0;
+#pragma unroll 1
+        for (int k = 0; k < NC; k++) {
+            double v[2], o[2];
+            scaled_stencil<double, 2>(d, c, r + k * d.N, cr_lo, cr_hi, ct_lo, ct_hi, cp, v, o);
+            stv<double, 2>(w + k * d.N + c.base, o);
+            cell = fma(v[0], v[0], fma(v[1], v[1], cell));
+            a_d = fma(v[0], o[0], fma(v[1], o[1], a_d));
+        }
+        a_g += cell;
+        a_rr = fma(dg[c.ij], cell, a_rr);
+    }
+    double val[3] = {a_g, a_d, a_rr}, out[3];
+    if (reduce_last<3>(val, partials, &sc->count, out) && threadIdx.x == 0) {
+        const double gam = out[0], del = out[1], rr = out[2];
+        sc->rr = rr;
+        if (!finite(gam) || !finite(del) || !finite(rr)) {
+            sc->done = 3;
+        } else if (sqrt(rr) <= sc->tol * sqrt(sc->bb)) {
+            sc->done = 1;
+        } else if (sc->iter >= sc->max_iter) {
+            sc->done = 2;
+        } else {
+            const bool first = (sc->iter == 0);
+            const double beta = first ? 0.0 : gam / sc->rho;
+            const double den = first ? del : del - beta * gam / sc->alpha;
+            if (!(den > 0.0)) {
+                sc->done = 4;
+            } else {
+                sc->beta = beta;
+                sc->alpha = gam / den;
+                sc->rho_prev = sc->rho;
+                sc->rho = gam;
+                sc->pq = den;
+                sc->iter += 1;
+                sc->total_iter += 1;
+            }
+        }
+    }
+}
+
+// C2: p = r~ + beta p, s = w + beta s, x~ += alpha p, r~ -= alpha s (first iteration: p = r~,
+// s = w, whatever the buffers held)
+template <int NC>
+__global__ void __launch_bounds__(kThreads) k_cg_update(Dims d, double* __restrict__ x, double* __restrict__ p,
+                                                        double* __restrict__ s, double* __restrict__ r,
+                                                        const double* __restrict__ w, const PcgScalars* sc) {
+    if (sc->done) return;
+    const double al = sc->alpha, be = sc->beta;
+    const bool first = (sc->iter == 1);
+    const unsigned int G = (unsigned int)(d.N / 2);
+    for (unsigned int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+        const long long off = (long long)g * 2;
+#pragma unroll
+        for (int k = 0; k < NC; k++) {
+            const long long o = k * d.N + off;
+            double xv[2], pv[2], sv[2], rv[2], wv[2];
+            ldv<double, 2>(r + o, rv);
+            ldv<double, 2>(w + o, wv);
+            ldv<double, 2>(x + o, xv);
+            if (first) {
+                pv[0] = rv[0]; pv[1] = rv[1];
+                sv[0] = wv[0]; sv[1] = wv[1];
+            } else {
+                ldv<double, 2>(p + o, pv);
+                ldv<double, 2>(s + o, sv);
+#pragma unroll
+                for (int e = 0; e < 2; e++) {
+                    pv[e] = fma(be, pv[e], rv[e]);
+                    sv[e] = fma(be, sv[e], wv[e]);
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < 2; e++) {
+                xv[e] = fma(al, pv[e], xv[e]);
+                rv[e] = fma(-al, sv[e], rv[e]);
+            }
+            stv<double, 2>(p + o, pv);
+            stv<double, 2>(s + o, sv);
+            stv<double, 2>(x + o, xv);
+            stv<double, 2>(r + o, rv);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // FP64 solve: set-up and finish
 // ------------------------------------------------------------------------------------------
 // r = b - M x0 (unscaled tables), x~ = x0 / s, r~ = s r, p~ = r~; rho, ||r||^2, ||b||^2
@@ -561,9 +667,27 @@ void enqueue_split_nc(mhd_grid_s* g, cudaStream_t st, int nc, T* x, T* r, T* p, 
     else enqueue_split<T, V, 1>(g, st, x, r, p, q, t, blocks, prof0);
 }
 
+template <int NC>
+void enqueue_cg(mhd_grid_s* g, cudaStream_t st, int blocks) {
+    const Dims d = g->d;
+    double* s_vec = g->p64 + 3 * (size_t)d.N;   // second half of the p double buffer
+    int ps = prof_begin(g, st, MHD_KERNEL_SPMV64);
+    k_cg_spmv<NC><<<blocks, kThreads, 0, st>>>(d, g->r64, g->q64, g->t64, g->tu.dg, g->sc, g->partials);
+    prof_end(g, st, ps);
+    ps = prof_begin(g, st, MHD_KERNEL_UPDATE64);
+    k_cg_update<NC><<<blocks, kThreads, 0, st>>>(d, g->x64, g->p64, s_vec, g->r64, g->q64, g->sc);
+    prof_end(g, st, ps);
+}
+
+// kind: 0 FP64 Hestenes-Stiefel, 1 FP32 inner (Hestenes-Stiefel), 2 FP64 single-reduction
 void enqueue_iteration(mhd_grid_s* g, cudaStream_t st, int prec, int nc) {
     const Dims d = g->d;
-    if (prec == 0 && nc == 3 && tiled32_ok(g) && g->slab64 > 0) {
+    if (prec == 2) {
+        const int blocks = grid_blocks(g, d.N / 2, kPerSmIter);
+        if (nc == 3) enqueue_cg<3>(g, st, blocks);
+        else if (nc == 2) enqueue_cg<2>(g, st, blocks);
+        else enqueue_cg<1>(g, st, blocks);
+    } else if (prec == 0 && nc == 3 && tiled32_ok(g) && g->slab64 > 0) {
         // fused p update + stencil (p double-buffered), then the update reading the new p
         const int blocks = grid_blocks(g, d.N / 2, kPerSmIter);
         enqueue_tiled64_a(g, st, g->slab64, MHD_KERNEL_SPMV64);
@@ -807,7 +931,7 @@ mhd_status_t solve(mhd_grid_s* g, const double* alpha_dev, int nc, const double*
         mhd_status_t st = tune_slab32(g, 3);
         if (st != MHD_OK) return st;
     }
-    if (!mixed && nc == 3 && g->slab64 == 0) {
+    if (!mixed && nc == 3 && g->slab64 == 0 && prm->pcg_variant == 0) {
         mhd_status_t st = tune_slab64(g);
         if (st != MHD_OK) return st;
     }
@@ -818,7 +942,7 @@ mhd_status_t solve(mhd_grid_s* g, const double* alpha_dev, int nc, const double*
                                                       g->partials);
         mhd_status_t st = check_cuda(g, "pcg init");
         if (st != MHD_OK) return st;
-        st = run_iterations(g, 0, nc);
+        st = run_iterations(g, prm->pcg_variant == 1 ? 2 : 0, nc);
         if (st != MHD_OK) return st;
         k_finish64<<<blocks2, kThreads, 0, g->stream>>>(d, nc, g->x64, x, g->t64.s, g->sc);
         if ((st = check_cuda(g, "pcg finish")) != MHD_OK) return st;
@@ -829,6 +953,7 @@ mhd_status_t solve(mhd_grid_s* g, const double* alpha_dev, int nc, const double*
         if (relres) *relres = (h.bb > 0) ? std::sqrt(h.rr) / std::sqrt(h.bb) : 0.0;
         if (h.done == 1) return MHD_OK;
         if (h.done == 3) return set_error(g, MHD_ERR_NONFINITE, "pcg: non-finite value in a reduction");
+        if (h.done == 4) return set_error(g, MHD_ERR_NOCONV, "pcg: breakdown (operator not positive definite)");
         return set_error(g, MHD_ERR_NOCONV, "pcg: no convergence within max_iter");
     }
     // mixed precision: x starts as x0 in FP64 (in place in the caller's x)

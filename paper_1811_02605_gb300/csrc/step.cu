@@ -23,6 +23,10 @@ mhd_status_t check_params(mhd_grid_s* g, const mhd_params_t* p) {
         return set_error(g, MHD_ERR_ARG, "params: need nu >= 0 and cfl > 0");
     if (p->viscosity_sts != 0 && p->viscosity_sts != 1)
         return set_error(g, MHD_ERR_ARG, "params: viscosity_sts must be 0 (implicit PCG) or 1 (RKL2)");
+    if (p->pcg_variant != 0 && p->pcg_variant != 1)
+        return set_error(g, MHD_ERR_ARG, "params: pcg_variant must be 0 (Hestenes-Stiefel) or 1 (single reduction)");
+    if (p->pcg_variant == 1 && p->precision != MHD_PREC_FP64)
+        return set_error(g, MHD_ERR_ARG, "params: the single-reduction PCG form is FP64 only");
     return MHD_OK;
 }
 
