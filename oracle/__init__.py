@@ -72,6 +72,17 @@ def _declare(L):
     L.og_step.argtypes = [vp, d, d, d, d, d, d, d, i, _dp, _dp, _dp, _dp, _dp]
     L.og_step_cg.restype = i
     L.og_step_cg.argtypes = L.og_step.argtypes
+    L.og_step_opts.restype = i
+    L.og_step_opts.argtypes = [vp, i, d, d, d, d, d, d, d, i, _dp, _dp, _dp, _dp, _dp]
+    L.og_res_size.restype = C.c_longlong
+    L.og_res_size.argtypes = [vp]
+    L.og_res_current.argtypes = [vp] + [_dp] * 6
+    L.og_res_apply.argtypes = [vp, d, _dp, _dp]
+    L.og_res_diag.argtypes = [vp, d, _dp]
+    L.og_res_pcg.restype = i
+    L.og_res_pcg.argtypes = [vp, d, _dp, _dp, d, i, i, C.POINTER(C.c_int), C.POINTER(C.c_double)]
+    L.og_res_solve.restype = i
+    L.og_res_solve.argtypes = [vp, d, _dp, _dp, _dp, d, i, C.POINTER(C.c_int), C.POINTER(C.c_double)]
     if hasattr(L, "og_adjoint_step"):
         L.og_adjoint_step.restype = i
         L.og_adjoint_step.argtypes = [vp, d, d, d, d, d, d, i] + [_dp] * 12
@@ -83,6 +94,9 @@ def _declare(L):
         L.og_rkl2.argtypes = [vp, d, d, i, _dp]
         L.og_step_sts.restype = i
         L.og_step_sts.argtypes = [vp] + [d] * 7 + [i] + [_dp] * 5
+
+
+OPT_PCG_CG, OPT_STS, OPT_RES_IMPLICIT = 1, 2, 4
 
 
 def _c(a):
@@ -207,19 +221,65 @@ class Grid:
         return o
 
     def step(self, state, nu=1e-3, eta=0.0, cfl=0.4, dt_fixed=0.0, dt_max=0.0, asi_fixed=-1.0,
-             tol=1e-9, max_iter=100000, cg=False):
+             tol=1e-9, max_iter=100000, cg=False, sts=False, res_implicit=False):
         """One step on a copy of `state` (dict br, bt, bp, vr, vt, vp). Returns (new, info).
-        cg=True: every solve in the single-reduction PCG form."""
+        cg: every solve in the single-reduction PCG form; sts: viscosity by RKL2 (iters[2] =
+        stages); res_implicit: resistivity by the implicit face solve (info res_iters, res_relres)."""
         v = np.ascontiguousarray(np.stack([state["vr"], state["vt"], state["vp"]]), dtype=np.float64)
         br, bt, bp = _c(state["br"]).copy(), _c(state["bt"]).copy(), _c(state["bp"]).copy()
-        info = np.zeros(11)
-        fn = self.L.og_step_cg if cg else self.L.og_step
-        st = fn(self.h, nu, eta, cfl, dt_fixed, dt_max, asi_fixed, tol, max_iter, v, br, bt, bp, info)
+        info = np.zeros(13)
+        opts = (OPT_PCG_CG if cg else 0) | (OPT_STS if sts else 0) | (OPT_RES_IMPLICIT if res_implicit else 0)
+        st = self.L.og_step_opts(self.h, opts, nu, eta, cfl, dt_fixed, dt_max, asi_fixed, tol, max_iter, v, br,
+                                 bt, bp, info)
         out = dict(br=br, bt=bt, bp=bp, vr=v[0].copy(), vt=v[1].copy(), vp=v[2].copy())
         inf = dict(status=st, dt=info[0], cf=info[1], cw=info[2], alpha_si=info[3],
                    alpha_nu=info[4], iters=[int(info[5]), int(info[6]), int(info[7])],
                    relres=list(info[8:11]))
+        if res_implicit:
+            inf["res_iters"], inf["res_relres"] = int(info[11]), float(info[12])
         return out, inf
+
+    # implicit resistivity: stacked face vectors [br | bt | bp]
+    @property
+    def res_size(self):
+        return int(self.L.og_res_size(self.h))
+
+    def res_split(self, x):
+        s = self.shapes
+        nbr, nbt = int(np.prod(s["br"])), int(np.prod(s["bt"]))
+        return (x[:nbr].reshape(s["br"]), x[nbr:nbr + nbt].reshape(s["bt"]), x[nbr + nbt:].reshape(s["bp"]))
+
+    def res_stack(self, br, bt, bp):
+        return np.concatenate([_c(br).ravel(), _c(bt).ravel(), _c(bp).ravel()])
+
+    def res_current(self, br, bt, bp):
+        s = self.shapes
+        jr, jt, jp = np.empty(s["er"]), np.empty(s["et"]), np.empty(s["ep"])
+        self.L.og_res_current(self.h, _c(br), _c(bt), _c(bp), jr, jt, jp)
+        return jr, jt, jp
+
+    def res_apply(self, dte, x):
+        y = np.empty(self.res_size)
+        self.L.og_res_apply(self.h, dte, _c(x), y)
+        return y
+
+    def res_diag(self, dte):
+        y = np.empty(self.res_size)
+        self.L.og_res_diag(self.h, dte, y)
+        return y
+
+    def res_pcg(self, dte, b, x0=None, tol=1e-9, max_iter=100000, fixed_iters=0):
+        b = _c(b)
+        x = np.zeros_like(b) if x0 is None else _c(x0).copy()
+        it, rr = C.c_int(0), C.c_double(0)
+        st = self.L.og_res_pcg(self.h, dte, b, x, tol, max_iter, fixed_iters, C.byref(it), C.byref(rr))
+        return x, it.value, rr.value, st
+
+    def res_solve(self, dte, br, bt, bp, tol=1e-9, max_iter=100000):
+        br, bt, bp = _c(br).copy(), _c(bt).copy(), _c(bp).copy()
+        it, rr = C.c_int(0), C.c_double(0)
+        st = self.L.og_res_solve(self.h, dte, br, bt, bp, tol, max_iter, C.byref(it), C.byref(rr))
+        return (br, bt, bp), it.value, rr.value, st
 
 
 def _adjoint(self, state, lam, dt, asi, nu=1e-3, eta=0.0, cfl=0.4, tol=1e-13, max_iter=200000, sts=False):
@@ -251,19 +311,11 @@ def _rkl2(self, v, nu, dt, stages=0):
     return x, s
 
 
-def _step_sts(self, state, nu=1e-3, eta=0.0, cfl=0.4, dt_fixed=0.0, dt_max=0.0, asi_fixed=-1.0, tol=1e-9,
-              max_iter=100000):
-    """og_step with the viscous PCG solve replaced by RKL2 (info iters[2] = stage count)."""
-    v = np.ascontiguousarray(np.stack([state["vr"], state["vt"], state["vp"]]), dtype=np.float64)
-    br, bt, bp = _c(state["br"]).copy(), _c(state["bt"]).copy(), _c(state["bp"]).copy()
-    info = np.zeros(11)
-    st = self.L.og_step_sts(self.h, nu, eta, cfl, dt_fixed, dt_max, asi_fixed, tol, max_iter, v, br, bt, bp, info)
-    out = dict(br=br, bt=bt, bp=bp, vr=v[0].copy(), vt=v[1].copy(), vp=v[2].copy())
-    inf = dict(status=st, dt=info[0], cf=info[1], cw=info[2], alpha_si=info[3], alpha_nu=info[4],
-               iters=[int(info[5]), int(info[6]), int(info[7])], relres=list(info[8:11]))
-    return out, inf
+def _step_sts(self, state, **kw):
+    """step with the viscous PCG solve replaced by RKL2 (info iters[2] = stage count)."""
+    return self.step(state, sts=True, **kw)
 
 
+Grid.step_sts = _step_sts
 Grid.rkl2_stages = _rkl2_stages
 Grid.rkl2 = _rkl2
-Grid.step_sts = _step_sts

@@ -712,9 +712,14 @@ int og_coeffs(const og_grid* g, double nu, double cfl, double dt_fixed, double d
  * ------------------------------------------------------------------------------------------- */
 typedef int (*pcg_fn)(const og_grid*, double, int, const double*, double*, double, int, int, int*, double*);
 
-static int step_impl(const og_grid* g, pcg_fn pcg, double nu, double eta, double cfl, double dt_fixed,
+/* the step of algorithm 1 with the options of og_step_opts (info: 11 entries, 13 with
+ * OG_OPT_RES_IMPLICIT) */
+static int step_impl(const og_grid* g, int opts, double nu, double eta, double cfl, double dt_fixed,
                      double dt_max, double asi_fixed, double tol, int max_iter, double* v, double* br,
                      double* bt, double* bp, double* info) {
+    pcg_fn pcg = (opts & OG_OPT_PCG_CG) ? og_pcg_cg : og_pcg;
+    int res_it = 0;
+    double res_rr = 0.0;
     long long N = g->N, n3 = 3 * N;
     int nt = g->nt, np = g->np;
     double co[5];
@@ -736,8 +741,16 @@ static int step_impl(const og_grid* g, pcg_fn pcg, double nu, double eta, double
     if (s != OG_OK) status = s;
     for (long long e2 = 0; e2 < n3; e2++) vp[e2] = v[e2] + dlt[e2];
     for (long long e2 = 0; e2 < n3; e2++) vb[e2] = 0.5 * (v[e2] + vp[e2]);
-    og_efield_edges(g, vb, br, bt, bp, eta, e.jr, e.jt, e.jp);
-    og_ct(g, e.jr, e.jt, e.jp, dt, br, bt, bp);
+    if (opts & OG_OPT_RES_IMPLICIT) {
+        /* ideal CT update, then the resistive solve on the faces */
+        og_efield_edges(g, vb, br, bt, bp, 0.0, e.jr, e.jt, e.jp);
+        og_ct(g, e.jr, e.jt, e.jp, dt, br, bt, bp);
+        s = og_res_solve(g, dt * eta, br, bt, bp, tol, max_iter, &res_it, &res_rr);
+        if (s != OG_OK) status = s;
+    } else {
+        og_efield_edges(g, vb, br, bt, bp, eta, e.jr, e.jt, e.jp);
+        og_ct(g, e.jr, e.jt, e.jp, dt, br, bt, bp);
+    }
     og_force(g, vp, br, bt, bp, dt, b1);
     for (long long e2 = 0; e2 < n3; e2++) b1[e2] = 0.5 * (b0[e2] + b1[e2]);
     s = pcg(g, asi, 3, b1, dlt, tol, max_iter, 0, &it[1], &rr[1]);
@@ -749,11 +762,16 @@ static int step_impl(const og_grid* g, pcg_fn pcg, double nu, double eta, double
             b0[c * N + q] = g->rho[ij] * g->vol[ij] * v[c * N + q];
         }
     (void)nt;
-    s = pcg(g, anu, 3, b0, v, tol, max_iter, 0, &it[2], &rr[2]);
-    if (s != OG_OK) status = s;
+    if (opts & OG_OPT_STS) {
+        it[2] = og_rkl2(g, nu, dt, 0, v);   /* viscosity by RKL2 from v** (algorithm 3) */
+    } else {
+        s = pcg(g, anu, 3, b0, v, tol, max_iter, 0, &it[2], &rr[2]);
+        if (s != OG_OK) status = s;
+    }
     if (info) {
         for (int q = 0; q < 5; q++) info[q] = co[q];
         for (int q = 0; q < 3; q++) { info[5 + q] = it[q]; info[8 + q] = rr[q]; }
+        if (opts & OG_OPT_RES_IMPLICIT) { info[11] = res_it; info[12] = res_rr; }
     }
     free(b0); free(b1); free(dlt); free(vp); free(vb);
     edges_free(e);
@@ -763,15 +781,21 @@ static int step_impl(const og_grid* g, pcg_fn pcg, double nu, double eta, double
 int og_step(const og_grid* g, double nu, double eta, double cfl, double dt_fixed, double dt_max,
             double asi_fixed, double tol, int max_iter, double* v, double* br, double* bt,
             double* bp, double* info) {
-    return step_impl(g, og_pcg, nu, eta, cfl, dt_fixed, dt_max, asi_fixed, tol, max_iter, v, br, bt, bp, info);
+    return step_impl(g, 0, nu, eta, cfl, dt_fixed, dt_max, asi_fixed, tol, max_iter, v, br, bt, bp, info);
 }
 
 /* og_step with every solve in the single-reduction PCG form (og_pcg_cg) */
 int og_step_cg(const og_grid* g, double nu, double eta, double cfl, double dt_fixed, double dt_max,
                double asi_fixed, double tol, int max_iter, double* v, double* br, double* bt,
                double* bp, double* info) {
-    return step_impl(g, og_pcg_cg, nu, eta, cfl, dt_fixed, dt_max, asi_fixed, tol, max_iter, v, br, bt, bp,
+    return step_impl(g, OG_OPT_PCG_CG, nu, eta, cfl, dt_fixed, dt_max, asi_fixed, tol, max_iter, v, br, bt, bp,
                      info);
+}
+
+int og_step_opts(const og_grid* g, int opts, double nu, double eta, double cfl, double dt_fixed, double dt_max,
+                 double asi_fixed, double tol, int max_iter, double* v, double* br, double* bt, double* bp,
+                 double* info) {
+    return step_impl(g, opts, nu, eta, cfl, dt_fixed, dt_max, asi_fixed, tol, max_iter, v, br, bt, bp, info);
 }
 
 /* =============================================================================================
@@ -1262,14 +1286,7 @@ int og_rkl2(const og_grid* g, double nu, double dt, int s, double* v) {
 int og_step_sts(const og_grid* g, double nu, double eta, double cfl, double dt_fixed, double dt_max,
                 double asi_fixed, double tol, int max_iter, double* v, double* br, double* bt, double* bp,
                 double* info) {
-    /* the step up to v** is og_step's with nu = 0: M_0 = D makes the viscous solve the identity */
-    double co[5];
-    int st = og_coeffs(g, nu, cfl, dt_fixed, dt_max, asi_fixed, v, br, bt, bp, co);
-    if (st != OG_OK) return st;
-    st = og_step(g, 0.0, eta, cfl, co[0], 0.0, co[3], tol, max_iter, v, br, bt, bp, info);
-    int s = og_rkl2(g, nu, co[0], 0, v);
-    if (info) { info[4] = co[4]; info[7] = s; info[10] = 0.0; }
-    return st;
+    return step_impl(g, OG_OPT_STS, nu, eta, cfl, dt_fixed, dt_max, asi_fixed, tol, max_iter, v, br, bt, bp, info);
 }
 
 int og_adjoint_step(const og_grid* g, double nu, double eta, double cfl, double dt, double asi_fixed, double tol,
@@ -1287,4 +1304,207 @@ int og_adjoint_step_sts(const og_grid* g, double nu, double eta, double cfl, dou
                         const double* lbp1, double* lv, double* lbr, double* lbt, double* lbp) {
     return adjoint_step(g, nu, eta, cfl, dt, asi_fixed, tol, max_iter, 1, v0, br0, bt0, bp0, lv1, lbr1, lbt1, lbp1,
                         lv, lbr, lbt, lbp);
+}
+
+/* =============================================================================================
+ * Implicit resistivity (Eq. 1: the -eta curl curl A term; Sec. 2.2: diffusive terms by PCG,
+ * the resistive solve always well conditioned and always with PC1). Reading R8, in B form:
+ * after the ideal CT update B* = B^n - dt curl_h E(v_bar, B^n) with eta = 0, solve
+ *     B^{n+1} + dt eta curl_h J(B^{n+1}) = B*,
+ * curl_h the face circulation of og_ct and J_e = (1/A*_e) sum_f s_fe l*_f B_f the circulation of
+ * B around the dual face of edge e (og_current_edges on interior edges): s_fe is the sign that
+ * og_ct gives edge e in face f and l*_f the centre-to-centre distance across f. Tangential edges
+ * on r0 and r1 carry no resistive E (line-tied inner wall; no resistive flux through the outer
+ * one), so every dual loop in the system is complete and B_r on both walls is unchanged. With
+ * the face weights W_f = A_f l*_f the system
+ *     W (B + dte curl_h J(B)) = W B*,   dte = dt eta,
+ * is W + dte G^T diag(l_e / A*_e) G with G_ef = s_fe l*_f: symmetric positive definite. The
+ * unknown is the stacked face vector [br | bt | bp]; the polar theta faces (zero area, stored
+ * 0) are identity rows.
+ * =========================================================================================== */
+static double lstar_r(const og_grid* g, int i) {
+    if (i == 0) return g->rc[0] - g->r0;
+    if (i == g->nr) return g->r[g->nr] - g->rc[g->nr - 1];
+    return g->rc[i] - g->rc[i - 1];
+}
+
+long long og_res_size(const og_grid* g) {
+    return (long long)(g->nr + 1) * g->nt * g->np + (long long)g->nr * (g->nt + 1) * g->np + g->N;
+}
+
+/* W_f per face, stacked */
+static void res_weights(const og_grid* g, double* w) {
+    int nr = g->nr, nt = g->nt, np = g->np;
+    double dth = g->dth, dph = g->dph;
+    double* wr = w;
+    double* wt = w + (long long)(nr + 1) * nt * np;
+    double* wp = wt + (long long)nr * (nt + 1) * np;
+    for (int i = 0; i <= nr; i++)
+        for (int j = 0; j < nt; j++) {
+            double a = g->r[i] * g->r[i] * (g->cn[j] - g->cn[j + 1]) * dph;
+            for (int k = 0; k < np; k++) wr[IDX(g, i, j, k)] = a * lstar_r(g, i);
+        }
+    for (int i = 0; i < nr; i++)
+        for (int j = 0; j <= nt; j++) {
+            double a = g->sn[j] * 0.5 * (g->r[i + 1] * g->r[i + 1] - g->r[i] * g->r[i]) * dph;
+            double wv = (j == 0 || j == nt) ? 1.0 : a * g->rc[i] * dth;
+            for (int k = 0; k < np; k++) wt[IDXT(g, i, j, k)] = wv;
+        }
+    for (int i = 0; i < nr; i++)
+        for (int j = 0; j < nt; j++) {
+            double a = 0.5 * (g->r[i + 1] * g->r[i + 1] - g->r[i] * g->r[i]) * dth;
+            for (int k = 0; k < np; k++) wp[IDX(g, i, j, k)] = a * g->rc[i] * g->sc[j] * dph;
+        }
+}
+
+/* J of the resistive operator on the edge arrays (og_current_edges layouts) */
+void og_res_current(const og_grid* g, const double* br, const double* bt, const double* bp, double* jr,
+                    double* jt, double* jp) {
+    int nr = g->nr, nt = g->nt, np = g->np;
+    og_current_edges(g, br, bt, bp, jr, jt, jp);
+    for (int j = 0; j < nt; j++)
+        for (int k = 0; k < np; k++) {
+            jt[IDX(g, 0, j, k)] = 0.0;
+            jt[IDX(g, nr, j, k)] = 0.0;
+        }
+    for (int j = 0; j <= nt; j++)
+        for (int k = 0; k < np; k++) {
+            jp[IDXT(g, 0, j, k)] = 0.0;
+            jp[IDXT(g, nr, j, k)] = 0.0;
+        }
+}
+
+/* y = W (x + dte curl_h J(x)) on stacked face vectors */
+void og_res_apply(const og_grid* g, double dte, const double* x, double* y) {
+    int nr = g->nr, nt = g->nt, np = g->np;
+    long long nbr = (long long)(nr + 1) * nt * np, nbt = (long long)nr * (nt + 1) * np, n = og_res_size(g);
+    edges3 e = edges_alloc(g);
+    double* w = (double*)malloc(sizeof(double) * n);
+    og_res_current(g, x, x + nbr, x + nbr + nbt, e.jr, e.jt, e.jp);
+    memcpy(y, x, sizeof(double) * n);
+    og_ct(g, e.jr, e.jt, e.jp, -dte, y, y + nbr, y + nbr + nbt);
+    res_weights(g, w);
+    for (long long q = 0; q < n; q++) y[q] *= w[q];
+    free(w);
+    edges_free(e);
+}
+
+/* diagonal of the system: W_f + dte l*_f^2 sum over the edges of f in the system of l_e / A*_e */
+void og_res_diag(const og_grid* g, double dte, double* d) {
+    int nr = g->nr, nt = g->nt, np = g->np;
+    double dth = g->dth, dph = g->dph;
+    long long nbr = (long long)(nr + 1) * nt * np, nbt = (long long)nr * (nt + 1) * np;
+    res_weights(g, d);
+    double* dr = d;
+    double* dt_ = d + nbr;
+    double* dp = d + nbr + nbt;
+    /* dual-face areas: radial edge (shell i, node j), theta edge (node i, centre j), phi edge
+     * (node i, node j); interior edges only */
+#define ASR(i, j) (g->rc[i] * g->rc[i] * (g->cc[(j) - 1] - g->cc[j]) * dph)
+#define AST(i, j) (g->sc[j] * 0.5 * (g->rc[i] * g->rc[i] - g->rc[(i) - 1] * g->rc[(i) - 1]) * dph)
+#define ASP(i) (0.5 * (g->rc[i] * g->rc[i] - g->rc[(i) - 1] * g->rc[(i) - 1]) * dth)
+    for (int i = 1; i < nr; i++)
+        for (int j = 0; j < nt; j++) {
+            double ls = lstar_r(g, i);
+            double sum = 2.0 * g->r[i] * dth / AST(i, j);
+            if (j >= 1) sum += g->r[i] * g->sn[j] * dph / ASP(i);
+            if (j + 1 <= nt - 1) sum += g->r[i] * g->sn[j + 1] * dph / ASP(i);
+            for (int k = 0; k < np; k++) dr[IDX(g, i, j, k)] += dte * ls * ls * sum;
+        }
+    for (int i = 0; i < nr; i++)
+        for (int j = 1; j < nt; j++) {
+            double ls = g->rc[i] * dth, lr = g->r[i + 1] - g->r[i];
+            double sum = 2.0 * lr / ASR(i, j);
+            if (i >= 1) sum += g->r[i] * g->sn[j] * dph / ASP(i);
+            if (i + 1 <= nr - 1) sum += g->r[i + 1] * g->sn[j] * dph / ASP(i + 1);
+            for (int k = 0; k < np; k++) dt_[IDXT(g, i, j, k)] += dte * ls * ls * sum;
+        }
+    for (int i = 0; i < nr; i++) {
+        double lr = g->r[i + 1] - g->r[i];
+        double cap_n = g->rc[i] * g->rc[i] * (1.0 - g->cc[0]) * 2.0 * M_PI;
+        double cap_s = g->rc[i] * g->rc[i] * (1.0 + g->cc[nt - 1]) * 2.0 * M_PI;
+        for (int j = 0; j < nt; j++) {
+            double ls = g->rc[i] * g->sc[j] * dph;
+            double sum = lr / (j == 0 ? cap_n : ASR(i, j)) + lr / (j == nt - 1 ? cap_s : ASR(i, j + 1));
+            if (i >= 1) sum += g->r[i] * dth / AST(i, j);
+            if (i + 1 <= nr - 1) sum += g->r[i + 1] * dth / AST(i + 1, j);
+            for (int k = 0; k < np; k++) dp[IDX(g, i, j, k)] += dte * ls * ls * sum;
+        }
+    }
+#undef ASR
+#undef AST
+#undef ASP
+}
+
+/* Jacobi PCG on the resistive system (same stop test, count and b = 0 rule as og_pcg) */
+int og_res_pcg(const og_grid* g, double dte, const double* b, double* x, double tol, int max_iter,
+               int fixed_iters, int* iters, double* relres) {
+    long long n = og_res_size(g);
+    double bnorm = sqrt(dot(n, b, b));
+    if (bnorm == 0.0) {
+        memset(x, 0, sizeof(double) * n);
+        *iters = 0; *relres = 0.0;
+        return OG_OK;
+    }
+    double* d = (double*)malloc(sizeof(double) * n);
+    double* r = (double*)malloc(sizeof(double) * n);
+    double* z = (double*)malloc(sizeof(double) * n);
+    double* p = (double*)malloc(sizeof(double) * n);
+    double* q = (double*)malloc(sizeof(double) * n);
+    og_res_diag(g, dte, d);
+    og_res_apply(g, dte, x, q);
+    for (long long e = 0; e < n; e++) r[e] = b[e] - q[e];
+    for (long long e = 0; e < n; e++) z[e] = r[e] / d[e];
+    for (long long e = 0; e < n; e++) p[e] = z[e];
+    double rz = dot(n, r, z);
+    double rn = sqrt(dot(n, r, r));
+    int k = 0, status = OG_OK;
+    for (;;) {
+        if (fixed_iters > 0) {
+            if (k >= fixed_iters) break;
+        } else {
+            if (rn <= tol * bnorm) break;
+            if (k >= max_iter) { status = OG_ERR_NOCONV; break; }
+        }
+        og_res_apply(g, dte, p, q);
+        double pq = dot(n, p, q);
+        if (!(pq > 0.0)) { status = OG_ERR_NOCONV; break; }
+        double a = rz / pq;
+        for (long long e = 0; e < n; e++) x[e] += a * p[e];
+        for (long long e = 0; e < n; e++) r[e] -= a * q[e];
+        k++;
+        rn = sqrt(dot(n, r, r));
+        for (long long e = 0; e < n; e++) z[e] = r[e] / d[e];
+        double rz_new = dot(n, r, z);
+        double beta = rz_new / rz;
+        rz = rz_new;
+        for (long long e = 0; e < n; e++) p[e] = z[e] + beta * p[e];
+    }
+    *iters = k;
+    *relres = rn / bnorm;
+    free(d); free(r); free(z); free(p); free(q);
+    return status;
+}
+
+/* B (three face arrays) <- B* - dte curl_h J(x), x the PCG solution of W (x + dte curl_h J(x)) = W B*
+ * started from B*: the final update is a CT circulation, so div_h B keeps its value to rounding
+ * whatever the solver tolerance, and B differs from x by the solver error only */
+int og_res_solve(const og_grid* g, double dte, double* br, double* bt, double* bp, double tol, int max_iter,
+                 int* iters, double* relres) {
+    int nr = g->nr, nt = g->nt, np = g->np;
+    long long nbr = (long long)(nr + 1) * nt * np, nbt = (long long)nr * (nt + 1) * np, n = og_res_size(g);
+    double* x = (double*)malloc(sizeof(double) * n);
+    double* b = (double*)malloc(sizeof(double) * n);
+    memcpy(x, br, sizeof(double) * nbr);
+    memcpy(x + nbr, bt, sizeof(double) * nbt);
+    memcpy(x + nbr + nbt, bp, sizeof(double) * g->N);
+    res_weights(g, b);
+    for (long long q = 0; q < n; q++) b[q] *= x[q];
+    int st = og_res_pcg(g, dte, b, x, tol, max_iter, 0, iters, relres);
+    edges3 e = edges_alloc(g);
+    og_res_current(g, x, x + nbr, x + nbr + nbt, e.jr, e.jt, e.jp);
+    og_ct(g, e.jr, e.jt, e.jp, dte, br, bt, bp);
+    edges_free(e);
+    free(x); free(b);
+    return st;
 }

@@ -75,6 +75,8 @@ void og_divb(const og_grid* g, const double* br, const double* bt, const double*
 /* one predictor-corrector step, in place. dt_fixed > 0 bypasses the CFL rule; asi_fixed >= 0
  * replaces the computed alpha_SI (frozen map for finite differences). info = {dt, cf, cw, asi, anu, it0, it1, it2,
  * rr0, rr1, rr2} (11 doubles) */
+/* step options (bit mask) of og_step_opts */
+enum { OG_OPT_PCG_CG = 1, OG_OPT_STS = 2, OG_OPT_RES_IMPLICIT = 4 };
 int og_step(const og_grid* g, double nu, double eta, double cfl, double dt_fixed, double dt_max,
             double asi_fixed, double tol, int max_iter, double* v, double* br, double* bt,
             double* bp, double* info);
@@ -103,6 +105,25 @@ int og_rkl2(const og_grid* g, double nu, double dt, int s, double* v);
 int og_step_sts(const og_grid* g, double nu, double eta, double cfl, double dt_fixed, double dt_max,
                 double asi_fixed, double tol, int max_iter, double* v, double* br, double* bt, double* bp,
                 double* info);
+
+
+/* og_step with options: OG_OPT_PCG_CG every solve in the single-reduction form, OG_OPT_STS
+ * viscosity by RKL2, OG_OPT_RES_IMPLICIT resistivity by the implicit face solve (info then has
+ * 13 entries: [11] its iterations, [12] its relative residual) */
+int og_step_opts(const og_grid* g, int opts, double nu, double eta, double cfl, double dt_fixed, double dt_max,
+                 double asi_fixed, double tol, int max_iter, double* v, double* br, double* bt, double* bp,
+                 double* info);
+
+/* implicit resistivity: stacked face vectors [br | bt | bp] of og_res_size entries */
+long long og_res_size(const og_grid* g);
+void og_res_current(const og_grid* g, const double* br, const double* bt, const double* bp, double* jr,
+                    double* jt, double* jp);
+void og_res_apply(const og_grid* g, double dte, const double* x, double* y);
+void og_res_diag(const og_grid* g, double dte, double* d);
+int og_res_pcg(const og_grid* g, double dte, const double* b, double* x, double tol, int max_iter,
+               int fixed_iters, int* iters, double* relres);
+int og_res_solve(const og_grid* g, double dte, double* br, double* bt, double* bp, double tol, int max_iter,
+                 int* iters, double* relres);
 
 #ifdef __cplusplus
 }
