@@ -95,7 +95,17 @@ enum { MHD_PREC_FP64 = 0, MHD_PREC_MIXED = 1 };
  *            gives both inner products and an iteration is two kernels with one reduction. Same
  *            iterates in exact arithmetic; rounding differs. FP64 only (MHD_ERR_ARG with
  *            precision = MHD_PREC_MIXED); applies to every solve of pcg_solve, mhd_step and
- *            mhd_adjoint_step (pcg_solve_batched ignores it). */
+ *            mhd_adjoint_step (pcg_solve_batched ignores it).
+ *  resistivity_implicit  0 (default): resistivity explicit, E = -v x B + eta J in the CT update.
+ *            1: resistivity implicit (Eq. 1's -eta curl curl term, Sec. 2.2: PCG with PC1): after
+ *            the ideal CT update to B*, solve W (B + dt eta curl_h J(B)) = W B* on the faces,
+ *            curl_h the CT face circulation, J on each edge the circulation of B around the
+ *            edge's dual face over its area (0 on the tangential edges of r0 and r1), W_f = face
+ *            area x centre-to-centre distance across the face (SPD system); then B = B* - dt eta
+ *            curl_h J(x) from the solution x, which keeps div_h B to rounding. Uses tol and
+ *            max_iter; FP64 (either precision setting). info->iters_res / relres_res report it.
+ *            The first such step allocates its workspace (4 face vectors). mhd_adjoint_step
+ *            rejects it (MHD_ERR_ARG). */
 typedef struct {
     double nu, eta, cfl, dt_fixed, dt_max, alpha_si_fixed;
     double tol, inner_tol;
@@ -104,6 +114,7 @@ typedef struct {
     int mixed_restart;
     int viscosity_sts;
     int pcg_variant;
+    int resistivity_implicit;
 } mhd_params_t;
 
 /* Caller-owned DEVICE pointers (layouts above). */
@@ -118,6 +129,8 @@ typedef struct {
     double dt, cf, cw, alpha_si, alpha_nu;
     int iters[3], outer[3];
     double relres[3];
+    int iters_res;      /* implicit resistivity: PCG iterations (0 otherwise) */
+    double relres_res;  /* implicit resistivity: final ||r||_2 / ||b||_2 */
 } mhd_step_info_t;
 
 /* Create a grid on the CUDA stream `cuda_stream` (a cudaStream_t; NULL = legacy default
@@ -230,7 +243,7 @@ enum {
     MHD_KERNEL_PUPDATE64 = 0, MHD_KERNEL_SPMV64 = 1, MHD_KERNEL_UPDATE64 = 2,
     MHD_KERNEL_PUPDATE32 = 3, MHD_KERNEL_SPMV32 = 4, MHD_KERNEL_UPDATE32 = 5,
     MHD_KERNEL_OUTER_RES = 6, MHD_KERNEL_FORCE = 7, MHD_KERNEL_INDUCTION = 8,
-    MHD_KERNEL_COEFFS = 9, MHD_KERNEL_STS = 10, MHD_KERNEL_COUNT = 11
+    MHD_KERNEL_COEFFS = 9, MHD_KERNEL_STS = 10, MHD_KERNEL_RES = 11, MHD_KERNEL_COUNT = 12
 };
 mhd_status_t mhd_profile_enable(mhd_grid_t grid, int enable);
 /* Total milliseconds and launch count of one kernel id since profiling was enabled.

@@ -21,14 +21,6 @@ namespace mhd {
 
 namespace {
 
-__device__ __forceinline__ long long ix(const Dims& d, int i, int j, int k) {
-    return ((long long)i * d.nt + j) * d.np + k;
-}
-__device__ __forceinline__ long long ixt(const Dims& d, int i, int j, int k) {
-    return ((long long)i * (d.nt + 1) + j) * d.np + k;
-}
-__device__ __forceinline__ int kp1(const Dims& d, int k) { return (k + 1 == d.np) ? 0 : k + 1; }
-__device__ __forceinline__ int km1(const Dims& d, int k) { return (k == 0) ? d.np - 1 : k - 1; }
 
 // cell-centred B: mean of opposite faces; polar rings take B_theta from the non-polar face
 __device__ __forceinline__ void bcentre(const Dims& d, const double* __restrict__ br,
@@ -171,13 +163,19 @@ __global__ void __launch_bounds__(kThreads) k_jr(Dims d, Geo G, const double* __
     }
 }
 
+// walls_zero: the resistive operator's current, 0 on the tangential edges of r0 and r1
 __global__ void __launch_bounds__(kThreads) k_jt(Dims d, Geo G, const double* __restrict__ br,
-                                                 const double* __restrict__ bp, double* __restrict__ jt) {
+                                                 const double* __restrict__ bp, double* __restrict__ jt,
+                                                 int walls_zero) {
     const long long n = (long long)(d.nr + 1) * d.nt * d.np;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
         const int k = (int)(e % d.np);
         const long long q = e / d.np;
         const int j = (int)(q % d.nt), i = (int)(q / d.nt);
+        if (walls_zero && (i == 0 || i == d.nr)) {
+            jt[e] = 0.0;
+            continue;
+        }
         const double rlo = (i > 0) ? G.rc[i - 1] : 2.0 * G.r0 - G.rc[0];
         const double rhi = (i < d.nr) ? G.rc[i] : 2.0 * G.r1 - G.rc[d.nr - 1];
         const int ilo = (i > 0) ? i - 1 : 0, ihi = (i < d.nr) ? i : d.nr - 1;
@@ -189,13 +187,14 @@ __global__ void __launch_bounds__(kThreads) k_jt(Dims d, Geo G, const double* __
 }
 
 __global__ void __launch_bounds__(kThreads) k_jp(Dims d, Geo G, const double* __restrict__ br,
-                                                 const double* __restrict__ bt, double* __restrict__ jp) {
+                                                 const double* __restrict__ bt, double* __restrict__ jp,
+                                                 int walls_zero) {
     const long long n = (long long)(d.nr + 1) * (d.nt + 1) * d.np;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
         const int k = (int)(e % d.np);
         const long long q = e / d.np;
         const int j = (int)(q % (d.nt + 1)), i = (int)(q / (d.nt + 1));
-        if (j == 0 || j == d.nt) {
+        if (j == 0 || j == d.nt || (walls_zero && (i == 0 || i == d.nr))) {
             jp[e] = 0.0;
             continue;
         }
@@ -209,14 +208,16 @@ __global__ void __launch_bounds__(kThreads) k_jp(Dims d, Geo G, const double* __
     }
 }
 
-void current_edges(mhd_grid_s* g, const double* br, const double* bt, const double* bp) {
+void current_edges(mhd_grid_s* g, const double* br, const double* bt, const double* bp, bool walls_zero,
+                   cudaStream_t st) {
     const Dims d = g->d;
-    k_ring<<<2 * d.nr, kThreads, 0, g->stream>>>(d, bp, g->ring);
+    if (!st) st = g->stream;
+    k_ring<<<2 * d.nr, kThreads, 0, st>>>(d, bp, g->ring);
     const long long n = (long long)(d.nr + 1) * (d.nt + 1) * d.np;
     const int blocks = grid_blocks(g, n, 8);
-    k_jr<<<blocks, kThreads, 0, g->stream>>>(d, g->geo, bt, bp, g->ring, g->er);
-    k_jt<<<blocks, kThreads, 0, g->stream>>>(d, g->geo, br, bp, g->et);
-    k_jp<<<blocks, kThreads, 0, g->stream>>>(d, g->geo, br, bt, g->ep);
+    k_jr<<<blocks, kThreads, 0, st>>>(d, g->geo, bt, bp, g->ring, g->er);
+    k_jt<<<blocks, kThreads, 0, st>>>(d, g->geo, br, bp, g->et, walls_zero ? 1 : 0);
+    k_jp<<<blocks, kThreads, 0, st>>>(d, g->geo, br, bt, g->ep, walls_zero ? 1 : 0);
 }
 
 // J at a cell centre from the edge arrays (polar phi edges left out)
@@ -485,6 +486,13 @@ void induction(mhd_grid_s* g, const double* vr, const double* vt, const double* 
     k_eedges<<<grid_blocks(g, ne, 8), kThreads, 0, g->stream>>>(d, g->ec, g->ring, g->er, g->et, g->ep);
     k_ct<<<grid_blocks(g, ne, 8), kThreads, 0, g->stream>>>(d, g->geo, g->er, g->et, g->ep, dt_dev, dt_host, br, bt,
                                                            bp);
+}
+
+void ct_apply(mhd_grid_s* g, const double* dt_dev, double* br, double* bt, double* bp) {
+    const Dims d = g->d;
+    const long long ne = (long long)d.nr * (d.nt + 1) * d.np + (long long)(d.nr + 1) * d.nt * d.np +
+                         (long long)(d.nr + 1) * (d.nt + 1) * d.np;
+    k_ct<<<grid_blocks(g, ne, 8), kThreads, 0, g->stream>>>(d, g->geo, g->er, g->et, g->ep, dt_dev, 0.0, br, bt, bp);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -34,6 +34,7 @@ struct PcgScalars {
     int total_iter;  // mixed: inner iterations summed over the outer passes
     unsigned int count;  // last-block ticket
     int par;         // FP32 tiled path: which of the two p buffers holds the current p
+    double dte;      // implicit resistivity: dt eta of the current solve
 };
 
 // Device-resident scalars of one step.
@@ -50,6 +51,16 @@ struct Dims {
     int pad;
     long long N;
 };
+
+// flat indices of the field layouts: [nr(+1)][nt][np] (ix) and [nr][nt+1][np] (ixt); periodic phi
+__device__ __forceinline__ long long ix(const Dims& d, int i, int j, int k) {
+    return ((long long)i * d.nt + j) * d.np + k;
+}
+__device__ __forceinline__ long long ixt(const Dims& d, int i, int j, int k) {
+    return ((long long)i * (d.nt + 1) + j) * d.np + k;
+}
+__device__ __forceinline__ int kp1(const Dims& d, int k) { return (k + 1 == d.np) ? 0 : k + 1; }
+__device__ __forceinline__ int km1(const Dims& d, int k) { return (k == 0) ? d.np - 1 : k - 1; }
 
 // Per-grid FP64 metric tables (device). Built on the host from the grid definition.
 struct Geo {
@@ -117,6 +128,7 @@ struct mhd_grid_s {
     double *sts_tab;        // [8*nr*nt] RKL2 stage coefficients (nu dt / (rho V) times K's weights)
     double* partials;       // [kMaxBlocks * kPartialsPerBlock]
     void* adj_mem;          // adjoint workspace, allocated by the first adjoint call
+    void* res_mem;          // implicit-resistivity workspace, allocated by the first such step
     mhd::PcgScalars* sc;    // device
     mhd::StepScalars* ss;   // device
     mhd::PcgScalars* h_sc;  // pinned host mirror
@@ -148,7 +160,10 @@ int grid_blocks(const mhd_grid_s* g, long long work, int per_sm = 4);
 // explicit kernels (explicit.cu)
 mhd_status_t coeffs(mhd_grid_s* g, const mhd_params_t* p, const double* vr, const double* vt,
                     const double* vp, const double* br, const double* bt, const double* bp);
-void current_edges(mhd_grid_s* g, const double* br, const double* bt, const double* bp);
+void current_edges(mhd_grid_s* g, const double* br, const double* bt, const double* bp, bool walls_zero = false,
+                   cudaStream_t st = nullptr);
+// B -= dt curl_h E with E in the grid's edge arrays (dt from the device scalar)
+void ct_apply(mhd_grid_s* g, const double* dt_dev, double* br, double* bt, double* bp);
 void force(mhd_grid_s* g, const double* vr, const double* vt, const double* vp,
            const double* dlt, double dfac, const double* br, const double* bt, const double* bp,
            const double* dt_dev, double dt_host, const double* b_avg, double* b);
@@ -157,6 +172,9 @@ void induction(mhd_grid_s* g, const double* vr, const double* vt, const double* 
                double* br, double* bt, double* bp);
 void vstar_rhs(mhd_grid_s* g, double* vr, double* vt, double* vp, const double* dlt, double* b);
 int sts_stages(const mhd_grid_s* g, double nu, double dt);
+mhd_status_t res_solve(mhd_grid_s* g, const double* dt_dev, double eta, double* br, double* bt, double* bp,
+                       const mhd_params_t* p, int* iters, double* relres);
+void res_free(mhd_grid_s* g);
 int sts_advance(mhd_grid_s* g, double nu, const double* dt_dev, double dt_host, double* y);
 
 // tiled FP32 CG kernels (tiled.cu)

@@ -1,0 +1,424 @@
+// Implicit resistivity (Eq. 1: the -eta curl curl A term; Sec. 2.2: diffusive terms by PCG, the
+// resistive solve always well conditioned and always with PC1), in B form on the faces.
+//
+// After the ideal CT update B* = B^n - dt curl_h E(v_bar, B^n), solve
+//     W (x + dte curl_h J(x)) = W B*,   dte = dt eta,
+// with J on the edges the circulation of x around each edge's dual face divided by its area (the
+// edge current of the explicit path, set to 0 on the tangential edges of r0 and r1), curl_h the
+// CT face circulation, and W_f = A_f l*_f (face area times the centre-to-centre distance across
+// the face; half distances on the walls). With these weights J is the weighted adjoint of
+// curl_h, so the system is symmetric positive definite. Point-Jacobi PCG on the stacked face
+// vector [br | bt | bp] (polar theta faces: identity rows), then B = B* - dte curl_h J(x): the
+// last update is a CT circulation, so div_h B keeps its value to rounding whatever the tolerance.
+//
+// Per iteration: edge current of p (ring sums + three edge kernels), q = M p with <p, q>, the
+// x / r update with <r, z> and ||r||^2, and p = z + beta p; the scalar recurrence runs in the
+// last CTA of each reducing kernel, and batches of iterations replay as one CUDA graph.
+#include <cmath>
+#include <vector>
+
+#include "mhd_internal.cuh"
+#include "reduce.cuh"
+
+namespace mhd {
+
+namespace {
+
+struct ResSizes {
+    long long nbr, nbt, nbp, nf;   // face counts per family and total
+    int tr, tt, tp;                // per-(i, j) table sizes
+};
+
+ResSizes res_sizes(const Dims& d) {
+    ResSizes z;
+    z.nbr = (long long)(d.nr + 1) * d.nt * d.np;
+    z.nbt = (long long)d.nr * (d.nt + 1) * d.np;
+    z.nbp = (long long)d.nr * d.nt * d.np;
+    z.nf = z.nbr + z.nbt + z.nbp;
+    z.tr = (d.nr + 1) * d.nt;
+    z.tt = d.nr * (d.nt + 1);
+    z.tp = d.nr * d.nt;
+    return z;
+}
+
+// Per-(i, j) tables of each face family, stacked [r | theta | phi]:
+//   w   = W_f = A_f l*_f            (1 on the polar theta faces)
+//   dc  = l*_f^2 sum over the edges of f in the system of l_e / A*_e   (diag = w + dte dc)
+//   ls  = l*_f
+struct ResTab {
+    const double *w, *dc, *ls;
+};
+
+// flat face index -> (family, table index, i, j, k)
+struct Face {
+    int fam, i, j, k;
+    int t;
+};
+__device__ __forceinline__ Face face_of(const Dims& d, long long f) {
+    Face o;
+    const long long nbr = (long long)(d.nr + 1) * d.nt * d.np;
+    const long long nbt = (long long)d.nr * (d.nt + 1) * d.np;
+    long long q;
+    if (f < nbr) {
+        o.fam = 0;
+        q = f;
+        o.k = (int)(q % d.np);
+        q /= d.np;
+        o.j = (int)(q % d.nt);
+        o.i = (int)(q / d.nt);
+        o.t = (int)q;
+    } else if (f < nbr + nbt) {
+        o.fam = 1;
+        q = f - nbr;
+        o.k = (int)(q % d.np);
+        q /= d.np;
+        o.j = (int)(q % (d.nt + 1));
+        o.i = (int)(q / (d.nt + 1));
+        o.t = (d.nr + 1) * d.nt + (int)q;
+    } else {
+        o.fam = 2;
+        q = f - nbr - nbt;
+        o.k = (int)(q % d.np);
+        q /= d.np;
+        o.j = (int)(q % d.nt);
+        o.i = (int)(q / d.nt);
+        o.t = (d.nr + 1) * d.nt + d.nr * (d.nt + 1) + (int)q;
+    }
+    return o;
+}
+
+// circulation of the edge current around face f (the CT circulation of og_ct's sign convention;
+// the polar radial edges read the ring values the current kernels wrote into every k)
+__device__ __forceinline__ double face_circ(const Dims& d, const Geo& G, const Face& F, const double* __restrict__ er,
+                                            const double* __restrict__ et, const double* __restrict__ ep) {
+    const int i = F.i, j = F.j, k = F.k;
+    if (F.fam == 0) {
+        const double ri = G.r[i];
+        const double lt = ri * G.dth;
+        const double lpj = ri * G.sn[j] * G.dph, lpj1 = ri * G.sn[j + 1] * G.dph;
+        return et[ix(d, i, j, k)] * lt + ep[ixt(d, i, j + 1, k)] * lpj1 - et[ix(d, i, j, kp1(d, k))] * lt -
+               ep[ixt(d, i, j, k)] * lpj;
+    }
+    const double ri = G.r[i], ro = G.r[i + 1];
+    const double lr = ro - ri;
+    if (F.fam == 1) {
+        if (j == 0 || j == d.nt) return 0.0;
+        const double lpi = ri * G.sn[j] * G.dph, lpo = ro * G.sn[j] * G.dph;
+        return ep[ixt(d, i, j, k)] * lpi + er[ixt(d, i, j, kp1(d, k))] * lr - ep[ixt(d, i + 1, j, k)] * lpo -
+               er[ixt(d, i, j, k)] * lr;
+    }
+    return er[ixt(d, i, j, k)] * lr + et[ix(d, i + 1, j, k)] * ro * G.dth - er[ixt(d, i, j + 1, k)] * lr -
+           et[ix(d, i, j, k)] * ri * G.dth;
+}
+
+__global__ void k_res_setup(PcgScalars* sc, double tol, int max_iter, const double* __restrict__ dt_dev, double eta) {
+    sc->tol = tol;
+    sc->max_iter = max_iter;
+    sc->done = 0;
+    sc->iter = 0;
+    sc->total_iter = 0;
+    sc->outer = 0;
+    sc->count = 0u;
+    sc->dte = *dt_dev * eta;
+}
+
+// the edge current of x0 is in the edge arrays: r = b - M x0 with b = W x0 (x0 = B*), so
+// r = -dte l* circ; x = x0, p = r / diag; rho = <r, z>, rr = ||r||^2, bb = ||b||^2
+__global__ void __launch_bounds__(kThreads) k_res_init(Dims d, Geo G, ResTab T, const double* __restrict__ x0,
+                                                       const double* __restrict__ er, const double* __restrict__ et,
+                                                       const double* __restrict__ ep, double* __restrict__ x,
+                                                       double* __restrict__ r, double* __restrict__ p, PcgScalars* sc,
+                                                       double* __restrict__ partials, long long nf) {
+    const double dte = sc->dte;
+    double a_rho = 0.0, a_rr = 0.0, a_bb = 0.0;
+    for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf; f += (long long)gridDim.x * blockDim.x) {
+        const Face F = face_of(d, f);
+        const double xv = x0[f];
+        const double w = T.w[F.t];
+        const double rv = -dte * T.ls[F.t] * face_circ(d, G, F, er, et, ep);
+        const double dg = fma(dte, T.dc[F.t], w);
+        const double z = rv / dg;
+        x[f] = xv;
+        r[f] = rv;
+        p[f] = z;
+        const double b = w * xv;
+        a_rho = fma(rv, z, a_rho);
+        a_rr = fma(rv, rv, a_rr);
+        a_bb = fma(b, b, a_bb);
+    }
+    double val[3] = {a_rho, a_rr, a_bb}, out[3];
+    if (reduce_last<3>(val, partials, &sc->count, out) && threadIdx.x == 0) {
+        sc->rho = out[0];
+        sc->rr = out[1];
+        sc->bb = out[2];
+        sc->beta = 0.0;
+        if (!isfinite(out[0]) || !isfinite(out[1]) || !isfinite(out[2])) sc->done = 3;
+        else if (out[2] == 0.0 || sqrt(out[1]) <= sc->tol * sqrt(out[2])) sc->done = 1;
+        else if (sc->max_iter <= 0) sc->done = 2;
+    }
+}
+
+// q = W p + dte l* circ(J(p)), <p, q>; last CTA: alpha
+__global__ void __launch_bounds__(kThreads) k_res_apply(Dims d, Geo G, ResTab T, const double* __restrict__ p,
+                                                        const double* __restrict__ er, const double* __restrict__ et,
+                                                        const double* __restrict__ ep, double* __restrict__ q,
+                                                        PcgScalars* sc, double* __restrict__ partials, long long nf) {
+    if (sc->done) return;
+    const double dte = sc->dte;
+    double a = 0.0;
+    for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf; f += (long long)gridDim.x * blockDim.x) {
+        const Face F = face_of(d, f);
+        const double pv = p[f];
+        const double qv = fma(T.w[F.t], pv, dte * T.ls[F.t] * face_circ(d, G, F, er, et, ep));
+        q[f] = qv;
+        a = fma(pv, qv, a);
+    }
+    double val[1] = {a}, out[1];
+    if (reduce_last<1>(val, partials, &sc->count, out) && threadIdx.x == 0) {
+        const double pq = out[0];
+        sc->pq = pq;
+        if (!isfinite(pq)) sc->done = 3;
+        else if (!(pq > 0.0)) sc->done = 4;
+        else sc->alpha = sc->rho / pq;
+    }
+}
+
+// x += alpha p, r -= alpha q, rho = <r, r / diag>, rr = ||r||^2; last CTA: beta, stop test
+__global__ void __launch_bounds__(kThreads) k_res_update(Dims d, ResTab T, double* __restrict__ x,
+                                                         const double* __restrict__ p, double* __restrict__ r,
+                                                         const double* __restrict__ q, PcgScalars* sc,
+                                                         double* __restrict__ partials, long long nf) {
+    if (sc->done) return;
+    const double al = sc->alpha, dte = sc->dte;
+    double a_rho = 0.0, a_rr = 0.0;
+    for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf; f += (long long)gridDim.x * blockDim.x) {
+        const Face F = face_of(d, f);
+        x[f] = fma(al, p[f], x[f]);
+        const double rv = fma(-al, q[f], r[f]);
+        r[f] = rv;
+        const double dg = fma(dte, T.dc[F.t], T.w[F.t]);
+        a_rho = fma(rv, rv / dg, a_rho);
+        a_rr = fma(rv, rv, a_rr);
+    }
+    double val[2] = {a_rho, a_rr}, out[2];
+    if (reduce_last<2>(val, partials, &sc->count, out) && threadIdx.x == 0) {
+        const double rho = out[0], rr = out[1];
+        sc->iter += 1;
+        sc->total_iter += 1;
+        sc->beta = rho / sc->rho;
+        sc->rho = rho;
+        sc->rr = rr;
+        if (!isfinite(rr) || !isfinite(rho)) sc->done = 3;
+        else if (sqrt(rr) <= sc->tol * sqrt(sc->bb)) sc->done = 1;
+        else if (sc->iter >= sc->max_iter) sc->done = 2;
+    }
+}
+
+// p = r / diag + beta p
+__global__ void __launch_bounds__(kThreads) k_res_pupdate(Dims d, ResTab T, const double* __restrict__ r,
+                                                          double* __restrict__ p, const PcgScalars* sc, long long nf) {
+    if (sc->done) return;
+    const double be = sc->beta, dte = sc->dte;
+    for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf; f += (long long)gridDim.x * blockDim.x) {
+        const Face F = face_of(d, f);
+        const double dg = fma(dte, T.dc[F.t], T.w[F.t]);
+        p[f] = fma(be, p[f], r[f] / dg);
+    }
+}
+
+// host tables (FP64, from the grid definition)
+void res_tables(const mhd_grid_s* g, std::vector<double>& w, std::vector<double>& dc, std::vector<double>& ls) {
+    const Dims d = g->d;
+    const int nr = d.nr, nt = d.nt, np = d.np;
+    const double PI = 3.14159265358979323846;
+    const double dth = PI / nt, dph = 2.0 * PI / np;
+    // grid nodes as the library builds them (radial nodes by repeated multiplication)
+    std::vector<double> r(nr + 1), rc(nr), sn(nt + 1), cn(nt + 1), sc(nt), cc(nt);
+    cudaMemcpy(r.data(), g->geo.r, sizeof(double) * (nr + 1), cudaMemcpyDeviceToHost);
+    cudaMemcpy(rc.data(), g->geo.rc, sizeof(double) * nr, cudaMemcpyDeviceToHost);
+    cudaMemcpy(sn.data(), g->geo.sn, sizeof(double) * (nt + 1), cudaMemcpyDeviceToHost);
+    cudaMemcpy(cn.data(), g->geo.cn, sizeof(double) * (nt + 1), cudaMemcpyDeviceToHost);
+    cudaMemcpy(sc.data(), g->geo.sc, sizeof(double) * nt, cudaMemcpyDeviceToHost);
+    cudaMemcpy(cc.data(), g->geo.cc, sizeof(double) * nt, cudaMemcpyDeviceToHost);
+    auto lsr = [&](int i) { return i == 0 ? rc[0] - r[0] : (i == nr ? r[nr] - rc[nr - 1] : rc[i] - rc[i - 1]); };
+    // dual-face areas of the interior edges: radial (shell i, node j), theta (node i, centre j),
+    // phi (node i, any j)
+    auto asr = [&](int i, int j) { return rc[i] * rc[i] * (cc[j - 1] - cc[j]) * dph; };
+    auto ast = [&](int i, int j) { return sc[j] * 0.5 * (rc[i] * rc[i] - rc[i - 1] * rc[i - 1]) * dph; };
+    auto asp = [&](int i) { return 0.5 * (rc[i] * rc[i] - rc[i - 1] * rc[i - 1]) * dth; };
+    const int tr = (nr + 1) * nt, tt = nr * (nt + 1), tp = nr * nt;
+    w.assign(tr + tt + tp, 0.0);
+    dc.assign(tr + tt + tp, 0.0);
+    ls.assign(tr + tt + tp, 0.0);
+    for (int i = 0; i <= nr; i++)
+        for (int j = 0; j < nt; j++) {
+            const int t = i * nt + j;
+            const double l = lsr(i);
+            ls[t] = l;
+            w[t] = r[i] * r[i] * (cn[j] - cn[j + 1]) * dph * l;
+            if (i >= 1 && i <= nr - 1) {
+                double s = 2.0 * r[i] * dth / ast(i, j);
+                if (j >= 1) s += r[i] * sn[j] * dph / asp(i);
+                if (j + 1 <= nt - 1) s += r[i] * sn[j + 1] * dph / asp(i);
+                dc[t] = l * l * s;
+            }
+        }
+    for (int i = 0; i < nr; i++)
+        for (int j = 0; j <= nt; j++) {
+            const int t = tr + i * (nt + 1) + j;
+            const double l = rc[i] * dth;
+            ls[t] = l;
+            if (j == 0 || j == nt) {
+                w[t] = 1.0;
+                continue;
+            }
+            w[t] = sn[j] * 0.5 * (r[i + 1] * r[i + 1] - r[i] * r[i]) * dph * l;
+            const double lr = r[i + 1] - r[i];
+            double s = 2.0 * lr / asr(i, j);
+            if (i >= 1) s += r[i] * sn[j] * dph / asp(i);
+            if (i + 1 <= nr - 1) s += r[i + 1] * sn[j] * dph / asp(i + 1);
+            dc[t] = l * l * s;
+        }
+    for (int i = 0; i < nr; i++) {
+        const double lr = r[i + 1] - r[i];
+        const double cap_n = rc[i] * rc[i] * (1.0 - cc[0]) * 2.0 * PI;
+        const double cap_s = rc[i] * rc[i] * (1.0 + cc[nt - 1]) * 2.0 * PI;
+        for (int j = 0; j < nt; j++) {
+            const int t = tr + tt + i * nt + j;
+            const double l = rc[i] * sc[j] * dph;
+            ls[t] = l;
+            w[t] = 0.5 * (r[i + 1] * r[i + 1] - r[i] * r[i]) * dth * l;
+            double s = lr / (j == 0 ? cap_n : asr(i, j)) + lr / (j == nt - 1 ? cap_s : asr(i, j + 1));
+            if (i >= 1) s += r[i] * dth / ast(i, j);
+            if (i + 1 <= nr - 1) s += r[i + 1] * dth / ast(i + 1, j);
+            dc[t] = l * l * s;
+        }
+    }
+}
+
+struct ResWork {
+    double *x, *r, *p, *q;    // nf each
+    double *w, *dc, *ls;      // per-(i, j) tables
+    cudaGraphExec_t graph;
+};
+
+mhd_status_t res_workspace(mhd_grid_s* g, ResWork** out) {
+    if (g->res_mem) {
+        *out = reinterpret_cast<ResWork*>(g->res_mem);
+        return MHD_OK;
+    }
+    const ResSizes z = res_sizes(g->d);
+    auto* w = new ResWork{};
+    const size_t nt_tab = (size_t)z.tr + z.tt + z.tp;
+    double* m = nullptr;
+    if (cudaMalloc(&m, sizeof(double) * (4 * (size_t)z.nf + 3 * nt_tab)) != cudaSuccess) {
+        delete w;
+        cudaGetLastError();
+        return set_error(g, MHD_ERR_OOM, "implicit resistivity: workspace allocation failed");
+    }
+    w->x = m;
+    w->r = m + z.nf;
+    w->p = m + 2 * z.nf;
+    w->q = m + 3 * z.nf;
+    w->w = m + 4 * z.nf;
+    w->dc = w->w + nt_tab;
+    w->ls = w->dc + nt_tab;
+    std::vector<double> hw, hdc, hls;
+    res_tables(g, hw, hdc, hls);
+    cudaMemcpy(w->w, hw.data(), sizeof(double) * nt_tab, cudaMemcpyHostToDevice);
+    cudaMemcpy(w->dc, hdc.data(), sizeof(double) * nt_tab, cudaMemcpyHostToDevice);
+    cudaMemcpy(w->ls, hls.data(), sizeof(double) * nt_tab, cudaMemcpyHostToDevice);
+    g->res_mem = w;
+    *out = w;
+    return check_cuda(g, "implicit resistivity workspace");
+}
+
+void res_enqueue_iteration(mhd_grid_s* g, cudaStream_t st, ResWork* w) {
+    const Dims d = g->d;
+    const ResSizes z = res_sizes(d);
+    const ResTab T{w->w, w->dc, w->ls};
+    const int blocks = grid_blocks(g, z.nf, 8);
+    current_edges(g, w->p, w->p + z.nbr, w->p + z.nbr + z.nbt, true, st);
+    k_res_apply<<<blocks, kThreads, 0, st>>>(d, g->geo, T, w->p, g->er, g->et, g->ep, w->q, g->sc, g->partials, z.nf);
+    k_res_update<<<blocks, kThreads, 0, st>>>(d, T, w->x, w->p, w->r, w->q, g->sc, g->partials, z.nf);
+    k_res_pupdate<<<blocks, kThreads, 0, st>>>(d, T, w->r, w->p, g->sc, z.nf);
+}
+
+mhd_status_t res_graph(mhd_grid_s* g, ResWork* w) {
+    if (w->graph) return MHD_OK;
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return check_cuda(g, "res graph stream");
+    cudaGraph_t graph;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return check_cuda(g, "res graph capture");
+    }
+    for (int it = 0; it < g->graph_batch; it++) res_enqueue_iteration(g, cs, w);
+    cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return set_error(g, MHD_ERR_CUDA, std::string("res end capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&w->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return set_error(g, MHD_ERR_CUDA, std::string("res instantiate: ") + cudaGetErrorString(e));
+    return MHD_OK;
+}
+
+mhd_status_t res_read(mhd_grid_s* g) {
+    if (cudaMemcpyAsync(g->h_sc, g->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, g->stream) != cudaSuccess)
+        return check_cuda(g, "res read scalars");
+    if (cudaStreamSynchronize(g->stream) != cudaSuccess) return check_cuda(g, "res sync");
+    return MHD_OK;
+}
+
+}  // namespace
+
+void res_free(mhd_grid_s* g) {
+    if (!g->res_mem) return;
+    auto* w = reinterpret_cast<ResWork*>(g->res_mem);
+    if (w->graph) cudaGraphExecDestroy(w->graph);
+    cudaFree(w->x);
+    delete w;
+    g->res_mem = nullptr;
+}
+
+// B (caller's face arrays, holding B*) <- B* - dte curl_h J(x), x the PCG solution; dte = dt eta
+// with dt the step's device scalar
+mhd_status_t res_solve(mhd_grid_s* g, const double* dt_dev, double eta, double* br, double* bt, double* bp,
+                       const mhd_params_t* p, int* iters, double* relres) {
+    ResWork* w = nullptr;
+    mhd_status_t st = res_workspace(g, &w);
+    if (st != MHD_OK) return st;
+    if ((st = res_graph(g, w)) != MHD_OK) return st;
+    const Dims d = g->d;
+    const ResSizes z = res_sizes(d);
+    const ResTab T{w->w, w->dc, w->ls};
+    const int blocks = grid_blocks(g, z.nf, 8);
+    // x0 = B* gathered into the stacked vector
+    cudaMemcpyAsync(w->q, br, sizeof(double) * z.nbr, cudaMemcpyDeviceToDevice, g->stream);
+    cudaMemcpyAsync(w->q + z.nbr, bt, sizeof(double) * z.nbt, cudaMemcpyDeviceToDevice, g->stream);
+    cudaMemcpyAsync(w->q + z.nbr + z.nbt, bp, sizeof(double) * z.nbp, cudaMemcpyDeviceToDevice, g->stream);
+    k_res_setup<<<1, 1, 0, g->stream>>>(g->sc, p->tol, p->max_iter, dt_dev, eta);
+    current_edges(g, br, bt, bp, true);
+    k_res_init<<<blocks, kThreads, 0, g->stream>>>(d, g->geo, T, w->q, g->er, g->et, g->ep, w->x, w->r, w->p, g->sc,
+                                                   g->partials, z.nf);
+    if ((st = check_cuda(g, "res init")) != MHD_OK) return st;
+    for (;;) {
+        if ((st = res_read(g)) != MHD_OK) return st;
+        if (g->h_sc->done) break;
+        if (cudaGraphLaunch(w->graph, g->stream) != cudaSuccess) return check_cuda(g, "res graph launch");
+        if (cudaGraphLaunch(w->graph, g->stream) != cudaSuccess) return check_cuda(g, "res graph launch");
+    }
+    const PcgScalars h = *g->h_sc;
+    // B = B* - dte curl_h J(x)
+    current_edges(g, w->x, w->x + z.nbr, w->x + z.nbr + z.nbt, true);
+    ct_apply(g, &g->sc->dte, br, bt, bp);
+    if ((st = check_cuda(g, "res final update")) != MHD_OK) return st;
+    if (iters) *iters = h.iter;
+    if (relres) *relres = (h.bb > 0) ? std::sqrt(h.rr) / std::sqrt(h.bb) : 0.0;
+    if (h.done == 1) return MHD_OK;
+    if (h.done == 3) return set_error(g, MHD_ERR_NONFINITE, "resistive pcg: non-finite value");
+    if (h.done == 4) return set_error(g, MHD_ERR_NOCONV, "resistive pcg: breakdown");
+    return set_error(g, MHD_ERR_NOCONV, "resistive pcg: no convergence within max_iter");
+}
+
+}  // namespace mhd

@@ -27,6 +27,9 @@ mhd_status_t check_params(mhd_grid_s* g, const mhd_params_t* p) {
         return set_error(g, MHD_ERR_ARG, "params: pcg_variant must be 0 (Hestenes-Stiefel) or 1 (single reduction)");
     if (p->pcg_variant == 1 && p->precision != MHD_PREC_FP64)
         return set_error(g, MHD_ERR_ARG, "params: the single-reduction PCG form is FP64 only");
+    if (p->resistivity_implicit != 0 && p->resistivity_implicit != 1)
+        return set_error(g, MHD_ERR_ARG, "params: resistivity_implicit must be 0 or 1");
+    if (!(p->eta >= 0.0)) return set_error(g, MHD_ERR_ARG, "params: need eta >= 0");
     return MHD_OK;
 }
 
@@ -92,9 +95,20 @@ extern "C" mhd_status_t mhd_step(mhd_grid_t g, const mhd_params_t* p, mhd_fields
     if (st == MHD_ERR_CUDA) return st;
     if (st != MHD_OK && worst == MHD_OK) worst = st;
     // 3. B^{n+1} = B^n - dt curl_h E(v^n + d_p / 2, B^n)
+    int it_res = 0;
+    double rr_res = 0.0;
     ps = prof_begin(g, g->stream, MHD_KERNEL_INDUCTION);
-    induction(g, f->vr, f->vt, f->vp, g->dlt, 0.5, p->eta, dt_dev, 0.0, f->br, f->bt, f->bp);
+    induction(g, f->vr, f->vt, f->vp, g->dlt, 0.5, p->resistivity_implicit ? 0.0 : p->eta, dt_dev, 0.0, f->br,
+              f->bt, f->bp);
     prof_end(g, g->stream, ps);
+    if (p->resistivity_implicit) {
+        // resistive part implicit on the faces: W (B + dt eta curl_h J(B)) = W B*
+        ps = prof_begin(g, g->stream, MHD_KERNEL_RES);
+        st = res_solve(g, dt_dev, p->eta, f->br, f->bt, f->bp, p, &it_res, &rr_res);
+        prof_end(g, g->stream, ps);
+        if (st == MHD_ERR_CUDA || st == MHD_ERR_OOM) return st;
+        if (st != MHD_OK && worst == MHD_OK) worst = st;
+    }
     // 4. corrector: M_SI d_c = (b0 + rho V dt F(v^n + d_p, B^{n+1})) / 2, x0 = d_p
     ps = prof_begin(g, g->stream, MHD_KERNEL_FORCE);
     force(g, f->vr, f->vt, f->vp, g->dlt, 1.0, f->br, f->bt, f->bp, dt_dev, 0.0, g->b0, g->b1);
@@ -135,6 +149,8 @@ extern "C" mhd_status_t mhd_step(mhd_grid_t g, const mhd_params_t* p, mhd_fields
             info->outer[q] = ou[q];
             info->relres[q] = rr[q];
         }
+        info->iters_res = it_res;
+        info->relres_res = rr_res;
     }
     return worst;
 }
