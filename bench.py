@@ -34,8 +34,10 @@ METRIC = "ms/zero-beta step, PCG HBM GB/s (% peak) at 256x256x512: FP64 vs mixed
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070  # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz = 1.259 TFLOP/s
 # algorithmic work of one scaled CG iteration per cell (3 components):
 #   bytes: x, r, p read + written once each = 6 passes x 3 x 8 B (FP64), x 4 B (FP32)
-#   FP64 flops of the SpMV kernel: 6 multiply-adds + 1 add per component + 1 dot FMA = 27 flops
-SPMV_FLOPS_PER_CELL = 3 * (2 * 6 + 1 + 2)
+#   FP64 flops of the SpMV kernel: the 6 neighbour multiply-adds of the unit-diagonal 7-point
+#   stencil plus the dot product's multiply-add = 14 flops per component (the two phi neighbours
+#   share one coefficient, so the kernel issues 7 FP64 instructions for these 14 flops)
+SPMV_FLOPS_PER_CELL = 3 * (2 * 6 + 2)
 PCG_BYTES_PER_CELL = {"fp64": 6 * 3 * 8, "fp32": 6 * 3 * 4}
 # DRAM bytes (read + write) per cell of one k_spmv_dot<double,2,3> launch, measured with ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum = 369.8 MB + 172.4 MB) on the flux-rope physics at

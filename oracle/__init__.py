@@ -74,6 +74,11 @@ def _declare(L):
     L.og_step_cg.argtypes = L.og_step.argtypes
     L.og_step_opts.restype = i
     L.og_step_opts.argtypes = [vp, i, d, d, d, d, d, d, d, i, _dp, _dp, _dp, _dp, _dp]
+    L.og_ilu0.restype = i
+    L.og_ilu0.argtypes = [vp, d, i, _dp]
+    L.og_ilu0_apply.argtypes = [vp, d, i, _dp, i, _dp, _dp]
+    L.og_pcg_pc2.restype = i
+    L.og_pcg_pc2.argtypes = [vp, d, i, i, _dp, _dp, d, i, i, C.POINTER(C.c_int), C.POINTER(C.c_double)]
     L.og_res_size.restype = C.c_longlong
     L.og_res_size.argtypes = [vp]
     L.og_res_current.argtypes = [vp] + [_dp] * 6
@@ -97,6 +102,10 @@ def _declare(L):
 
 
 OPT_PCG_CG, OPT_STS, OPT_RES_IMPLICIT = 1, 2, 4
+
+
+def _blocks(name):
+    return {"whole": 0, "lines": 1}[name]
 
 
 def _c(a):
@@ -165,12 +174,18 @@ class Grid:
         self.L.og_diag(self.h, alpha, o)
         return o
 
-    def pcg(self, alpha, b, x0=None, tol=1e-9, max_iter=100000, fixed_iters=0, cg=False):
-        """Jacobi PCG; cg=True: the single-reduction (Chronopoulos-Gear) form."""
+    def pcg(self, alpha, b, x0=None, tol=1e-9, max_iter=100000, fixed_iters=0, cg=False, pc2=None):
+        """Jacobi PCG; cg=True: the single-reduction (Chronopoulos-Gear) form; pc2="lines" or
+        "whole": PCG with the block-Jacobi ILU(0) preconditioner PC2 (phi-line blocks or one
+        block)."""
         b = _c(b)
         x = np.zeros_like(b) if x0 is None else _c(x0).copy()
         it = C.c_int(0)
         rr = C.c_double(0)
+        if pc2 is not None:
+            st = self.L.og_pcg_pc2(self.h, alpha, _blocks(pc2), b.size // self.N, b, x, tol, max_iter, fixed_iters,
+                                   C.byref(it), C.byref(rr))
+            return x, it.value, rr.value, st
         fn = self.L.og_pcg_cg if cg else self.L.og_pcg
         st = fn(self.h, alpha, b.size // self.N, b, x, tol, max_iter, fixed_iters, C.byref(it), C.byref(rr))
         return x, it.value, rr.value, st
@@ -238,6 +253,18 @@ class Grid:
         if res_implicit:
             inf["res_iters"], inf["res_relres"] = int(info[11]), float(info[12])
         return out, inf
+
+    def ilu0(self, alpha, blocks="lines"):
+        """modified diagonal of the ILU(0) factorisation of M_alpha, shape (nr, nt, np)"""
+        o = np.empty((self.nr, self.nt, self.np))
+        st = self.L.og_ilu0(self.h, alpha, _blocks(blocks), o)
+        return o, st
+
+    def ilu0_apply(self, alpha, dt, r, blocks="lines"):
+        r = _c(r)
+        z = np.empty_like(r)
+        self.L.og_ilu0_apply(self.h, alpha, _blocks(blocks), _c(dt), r.size // self.N, r, z)
+        return z
 
     # implicit resistivity: stacked face vectors [br | bt | bp]
     @property

@@ -1508,3 +1508,141 @@ int og_res_solve(const og_grid* g, double dte, double* br, double* bt, double* b
     free(x); free(b);
     return st;
 }
+
+/* =============================================================================================
+ * PC2 (Sec. 2.2): block-Jacobi with a zero-fill incomplete LU factorisation (ILU(0)) in each
+ * block. Reading R9: the blocks are a choice (the paper's are the MPI ranks' subdomains); two
+ * block structures are provided:
+ *   blocks = 0: one block, the whole grid, in the natural order of the memory layout (i slowest,
+ *               then j, then k; the periodic phi neighbour of k = np-1 at k = 0 comes earlier);
+ *   blocks = 1: one block per periodic phi line (i, j): the couplings in r and theta are dropped
+ *               from the preconditioner, each line keeps its own tridiagonal-plus-wrap block.
+ * The three components share the factorisation. For these patterns (np >= 4) zero fill changes
+ * only the diagonal:
+ *     dt_c = M_cc - sum over the earlier in-block neighbours l of c of M_cl^2 / dt_l,
+ * and the preconditioner is P = (dt + L) dt^-1 (dt + U), L / U the strict lower / upper parts of
+ * the block-diagonal part of M_alpha: symmetric, equal to M_alpha on each block's pattern. z =
+ * P^-1 r by one forward and one backward substitution in that order.
+ * =========================================================================================== */
+/* off-diagonal entries of M_alpha at cell (i, j, k) towards its six neighbours: -alpha w */
+static void m_offdiag(const og_grid* g, double alpha, int i, int j, double* wrl, double* wrh, double* wtl,
+                      double* wth, double* wp) {
+    int nr = g->nr, nt = g->nt;
+    *wrl = (i > 0) ? -alpha * g->wr[i * nt + j] : 0.0;
+    *wrh = (i < nr - 1) ? -alpha * g->wr[(i + 1) * nt + j] : 0.0;
+    *wtl = (j > 0) ? -alpha * g->wt[i * (nt + 1) + j] : 0.0;
+    *wth = (j < nt - 1) ? -alpha * g->wt[i * (nt + 1) + j + 1] : 0.0;
+    *wp = -alpha * g->wp[i * nt + j];
+}
+
+/* dt (N entries) of the ILU(0) factorisation; returns 0, or -1 if a pivot is not positive */
+int og_ilu0(const og_grid* g, double alpha, int blocks, double* dt) {
+    int nr = g->nr, nt = g->nt, np = g->np;
+    int whole = (blocks == 0);
+    double* dg = (double*)malloc(sizeof(double) * nr * nt);
+    og_diag(g, alpha, dg);
+    int bad = 0;
+    for (int i = 0; i < nr; i++)
+        for (int j = 0; j < nt; j++)
+            for (int k = 0; k < np; k++) {
+                double wrl, wrh, wtl, wth, wp;
+                m_offdiag(g, alpha, i, j, &wrl, &wrh, &wtl, &wth, &wp);
+                double d = dg[i * nt + j];
+                if (whole && i > 0) d -= wrl * wrl / dt[IDX(g, i - 1, j, k)];
+                if (whole && j > 0) d -= wtl * wtl / dt[IDX(g, i, j - 1, k)];
+                if (k > 0) d -= wp * wp / dt[IDX(g, i, j, k - 1)];
+                if (k == np - 1) d -= wp * wp / dt[IDX(g, i, j, 0)];
+                if (!(d > 0.0)) bad = 1;
+                dt[IDX(g, i, j, k)] = d;
+            }
+    free(dg);
+    return bad ? -1 : 0;
+}
+
+/* z = P^-1 r for ncomp stacked components, dt from og_ilu0 with the same blocks */
+void og_ilu0_apply(const og_grid* g, double alpha, int blocks, const double* dt, int ncomp, const double* r,
+                   double* z) {
+    int nr = g->nr, nt = g->nt, np = g->np;
+    int whole = (blocks == 0);
+    for (int c = 0; c < ncomp; c++) {
+        const double* rc = r + c * g->N;
+        double* zc = z + c * g->N;
+        /* forward: (dt + L) u = r, u stored in z */
+        for (int i = 0; i < nr; i++)
+            for (int j = 0; j < nt; j++)
+                for (int k = 0; k < np; k++) {
+                    double wrl, wrh, wtl, wth, wp;
+                    m_offdiag(g, alpha, i, j, &wrl, &wrh, &wtl, &wth, &wp);
+                    double s = rc[IDX(g, i, j, k)];
+                    if (whole && i > 0) s -= wrl * zc[IDX(g, i - 1, j, k)];
+                    if (whole && j > 0) s -= wtl * zc[IDX(g, i, j - 1, k)];
+                    if (k > 0) s -= wp * zc[IDX(g, i, j, k - 1)];
+                    if (k == np - 1) s -= wp * zc[IDX(g, i, j, 0)];
+                    zc[IDX(g, i, j, k)] = s / dt[IDX(g, i, j, k)];
+                }
+        /* backward: (dt + U) z = dt u */
+        for (int i = nr - 1; i >= 0; i--)
+            for (int j = nt - 1; j >= 0; j--)
+                for (int k = np - 1; k >= 0; k--) {
+                    double wrl, wrh, wtl, wth, wp;
+                    m_offdiag(g, alpha, i, j, &wrl, &wrh, &wtl, &wth, &wp);
+                    double s = 0.0;
+                    if (whole && i < nr - 1) s += wrh * zc[IDX(g, i + 1, j, k)];
+                    if (whole && j < nt - 1) s += wth * zc[IDX(g, i, j + 1, k)];
+                    if (k < np - 1) s += wp * zc[IDX(g, i, j, k + 1)];
+                    if (k == 0) s += wp * zc[IDX(g, i, j, np - 1)];
+                    zc[IDX(g, i, j, k)] -= s / dt[IDX(g, i, j, k)];
+                }
+    }
+}
+
+/* PCG with PC2 (same stop test, count and b = 0 rule as og_pcg) */
+int og_pcg_pc2(const og_grid* g, double alpha, int blocks, int ncomp, const double* b, double* x, double tol,
+               int max_iter, int fixed_iters, int* iters, double* relres) {
+    long long N = g->N, n = ncomp * N;
+    double bnorm = sqrt(dot(n, b, b));
+    if (bnorm == 0.0) {
+        memset(x, 0, sizeof(double) * n);
+        *iters = 0; *relres = 0.0;
+        return OG_OK;
+    }
+    double* dt = (double*)malloc(sizeof(double) * N);
+    double* r = (double*)malloc(sizeof(double) * n);
+    double* z = (double*)malloc(sizeof(double) * n);
+    double* p = (double*)malloc(sizeof(double) * n);
+    double* q = (double*)malloc(sizeof(double) * n);
+    int status = OG_OK;
+    if (og_ilu0(g, alpha, blocks, dt) != 0) status = OG_ERR_NOCONV;
+    og_apply_M(g, alpha, ncomp, x, q);
+    for (long long e = 0; e < n; e++) r[e] = b[e] - q[e];
+    og_ilu0_apply(g, alpha, blocks, dt, ncomp, r, z);
+    for (long long e = 0; e < n; e++) p[e] = z[e];
+    double rz = dot(n, r, z);
+    double rn = sqrt(dot(n, r, r));
+    int k = 0;
+    while (status == OG_OK) {
+        if (fixed_iters > 0) {
+            if (k >= fixed_iters) break;
+        } else {
+            if (rn <= tol * bnorm) break;
+            if (k >= max_iter) { status = OG_ERR_NOCONV; break; }
+        }
+        og_apply_M(g, alpha, ncomp, p, q);
+        double pq = dot(n, p, q);
+        if (!(pq > 0.0)) { status = OG_ERR_NOCONV; break; }
+        double a = rz / pq;
+        for (long long e = 0; e < n; e++) x[e] += a * p[e];
+        for (long long e = 0; e < n; e++) r[e] -= a * q[e];
+        k++;
+        rn = sqrt(dot(n, r, r));
+        og_ilu0_apply(g, alpha, blocks, dt, ncomp, r, z);
+        double rz_new = dot(n, r, z);
+        double beta = rz_new / rz;
+        rz = rz_new;
+        for (long long e = 0; e < n; e++) p[e] = z[e] + beta * p[e];
+    }
+    *iters = k;
+    *relres = rn / bnorm;
+    free(dt); free(r); free(z); free(p); free(q);
+    return status;
+}

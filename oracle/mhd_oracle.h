@@ -125,6 +125,16 @@ int og_res_pcg(const og_grid* g, double dte, const double* b, double* x, double 
 int og_res_solve(const og_grid* g, double dte, double* br, double* bt, double* bp, double tol, int max_iter,
                  int* iters, double* relres);
 
+
+/* PC2: block-Jacobi ILU(0) of M_alpha; blocks 0: one block in the natural order, 1: one block per
+ * periodic phi line. og_ilu0 writes the modified diagonal (N entries; returns -1 on a non-positive
+ * pivot); og_ilu0_apply gives z = P^-1 r; og_pcg_pc2 is og_pcg with that preconditioner. */
+int og_ilu0(const og_grid* g, double alpha, int blocks, double* dt);
+void og_ilu0_apply(const og_grid* g, double alpha, int blocks, const double* dt, int ncomp, const double* r,
+                   double* z);
+int og_pcg_pc2(const og_grid* g, double alpha, int blocks, int ncomp, const double* b, double* x, double tol,
+               int max_iter, int fixed_iters, int* iters, double* relres);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,25 +16,33 @@ GRIDS = [I.GridDesc(6, 6, 12, 1.0, 4.0, 1.1), I.GridDesc(9, 7, 10, 1.0, 6.0, 1.0
          I.GridDesc(32, 32, 64, 1.0, 20.0, 1.05)]
 
 
+# (eta, tol, iteration slack). At eta = 5e-3 the workload tolerance 1e-9 already resolves the
+# 1e-11 gate. At eta = 0.05 the face system is ill conditioned (about 250 iterations on 32x32x64):
+# two solutions that each meet tol 1e-9 or even 1e-12 differ by up to 2e-10 in the small B_phi
+# (measured on the oracle alone, tol 1e-12 against 1e-14), so the gate is applied with every solve
+# at tol 3e-14, where the counts near the rounding floor may differ by a few.
+CASES = [(5e-3, 1e-9, 1), (0.05, 3e-14, 8)]
+
+
 @pytest.mark.parametrize("d", GRIDS, ids=lambda d: f"{d.nr}x{d.nt}x{d.np}")
-@pytest.mark.parametrize("eta", [5e-3, 0.05])
-def test_implicit_resistivity_step_parity(d, eta):
+@pytest.mark.parametrize("eta,tol,slack", CASES, ids=["eta5e-3", "eta5e-2"])
+def test_implicit_resistivity_step_parity(d, eta, tol, slack):
     st0 = I.initial_state(d, 2, False)
     g, og = grid(d), O.Grid.from_desc(d)
     ds = dev_state(st0)
     f = fields(ds)
     s = st0
-    prm = P.make_params(nu=1e-3, eta=eta, cfl=0.4, tol=1e-9, resistivity_implicit=1)
+    prm = P.make_params(nu=1e-3, eta=eta, cfl=0.4, tol=tol, max_iter=100000, resistivity_implicit=1)
     div0 = og.divb(st0["br"], st0["bt"], st0["bp"])
     for n in range(3):
         stat, info = P.mhd_step(g, prm, f)
         torch.cuda.synchronize()
-        s, oinfo = og.step(s, nu=1e-3, eta=eta, cfl=0.4, tol=1e-9, res_implicit=True)
+        s, oinfo = og.step(s, nu=1e-3, eta=eta, cfl=0.4, tol=tol, max_iter=100000, res_implicit=True)
         assert stat == P.MHD_OK and oinfo["status"] == O.OK
-        assert abs(info["iters_res"] - oinfo["res_iters"]) <= 1, (info["iters_res"], oinfo["res_iters"])
-        assert info["iters_res"] >= 1 and info["relres_res"] <= 1e-9
+        assert abs(info["iters_res"] - oinfo["res_iters"]) <= slack, (info["iters_res"], oinfo["res_iters"])
+        assert info["iters_res"] >= 1 and info["relres_res"] <= tol
         for q in range(3):
-            assert abs(info["iters"][q] - oinfo["iters"][q]) <= 1
+            assert abs(info["iters"][q] - oinfo["iters"][q]) <= slack
         for k in KEYS:
             e = rel_l2(to_np(ds[k]), s[k])
             assert e <= 1e-11, (n, k, e)
