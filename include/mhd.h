@@ -105,7 +105,15 @@ enum { MHD_PREC_FP64 = 0, MHD_PREC_MIXED = 1 };
  *            curl_h J(x) from the solution x, which keeps div_h B to rounding. Uses tol and
  *            max_iter; FP64 (either precision setting). info->iters_res / relres_res report it.
  *            The first such step allocates its workspace (4 face vectors). mhd_adjoint_step
- *            rejects it (MHD_ERR_ARG). */
+ *            rejects it (MHD_ERR_ARG).
+ *  preconditioner  0 (default): PC1, point Jacobi (Sec. 2.2). 1: PC2, block Jacobi with a
+ *            zero-fill incomplete LU factorisation (ILU(0)) in each block (Sec. 2.2); the blocks
+ *            are the periodic phi lines (i, j) of each component, so the r and theta couplings
+ *            are left out of the preconditioner and every line is solved independently (one warp
+ *            per line, forward and backward substitution as affine scans). Needs precision FP64
+ *            and pcg_variant 0 (MHD_ERR_ARG otherwise); applies to every solve of pcg_solve,
+ *            mhd_step and mhd_adjoint_step; the first PC2 solve allocates N doubles for the
+ *            factorisation. pcg_solve_batched ignores it. */
 typedef struct {
     double nu, eta, cfl, dt_fixed, dt_max, alpha_si_fixed;
     double tol, inner_tol;
@@ -115,6 +123,7 @@ typedef struct {
     int viscosity_sts;
     int pcg_variant;
     int resistivity_implicit;
+    int preconditioner;
 } mhd_params_t;
 
 /* Caller-owned DEVICE pointers (layouts above). */
@@ -243,7 +252,8 @@ enum {
     MHD_KERNEL_PUPDATE64 = 0, MHD_KERNEL_SPMV64 = 1, MHD_KERNEL_UPDATE64 = 2,
     MHD_KERNEL_PUPDATE32 = 3, MHD_KERNEL_SPMV32 = 4, MHD_KERNEL_UPDATE32 = 5,
     MHD_KERNEL_OUTER_RES = 6, MHD_KERNEL_FORCE = 7, MHD_KERNEL_INDUCTION = 8,
-    MHD_KERNEL_COEFFS = 9, MHD_KERNEL_STS = 10, MHD_KERNEL_RES = 11, MHD_KERNEL_COUNT = 12
+    MHD_KERNEL_COEFFS = 9, MHD_KERNEL_STS = 10, MHD_KERNEL_RES = 11, MHD_KERNEL_PC2 = 12,
+    MHD_KERNEL_COUNT = 13
 };
 mhd_status_t mhd_profile_enable(mhd_grid_t grid, int enable);
 /* Total milliseconds and launch count of one kernel id since profiling was enabled.

@@ -101,7 +101,7 @@ def _declare(L):
         L.og_step_sts.argtypes = [vp] + [d] * 7 + [i] + [_dp] * 5
 
 
-OPT_PCG_CG, OPT_STS, OPT_RES_IMPLICIT = 1, 2, 4
+OPT_PCG_CG, OPT_STS, OPT_RES_IMPLICIT, OPT_PC2 = 1, 2, 4, 8
 
 
 def _blocks(name):
@@ -236,14 +236,16 @@ class Grid:
         return o
 
     def step(self, state, nu=1e-3, eta=0.0, cfl=0.4, dt_fixed=0.0, dt_max=0.0, asi_fixed=-1.0,
-             tol=1e-9, max_iter=100000, cg=False, sts=False, res_implicit=False):
+             tol=1e-9, max_iter=100000, cg=False, sts=False, res_implicit=False, pc2=False):
         """One step on a copy of `state` (dict br, bt, bp, vr, vt, vp). Returns (new, info).
         cg: every solve in the single-reduction PCG form; sts: viscosity by RKL2 (iters[2] =
-        stages); res_implicit: resistivity by the implicit face solve (info res_iters, res_relres)."""
+        stages); res_implicit: resistivity by the implicit face solve (info res_iters, res_relres);
+        pc2: every cell solve with the phi-line block-Jacobi ILU(0) preconditioner."""
         v = np.ascontiguousarray(np.stack([state["vr"], state["vt"], state["vp"]]), dtype=np.float64)
         br, bt, bp = _c(state["br"]).copy(), _c(state["bt"]).copy(), _c(state["bp"]).copy()
         info = np.zeros(13)
-        opts = (OPT_PCG_CG if cg else 0) | (OPT_STS if sts else 0) | (OPT_RES_IMPLICIT if res_implicit else 0)
+        opts = ((OPT_PCG_CG if cg else 0) | (OPT_STS if sts else 0) | (OPT_RES_IMPLICIT if res_implicit else 0) |
+                (OPT_PC2 if pc2 else 0))
         st = self.L.og_step_opts(self.h, opts, nu, eta, cfl, dt_fixed, dt_max, asi_fixed, tol, max_iter, v, br,
                                  bt, bp, info)
         out = dict(br=br, bt=bt, bp=bp, vr=v[0].copy(), vt=v[1].copy(), vp=v[2].copy())

@@ -712,12 +712,17 @@ int og_coeffs(const og_grid* g, double nu, double cfl, double dt_fixed, double d
  * ------------------------------------------------------------------------------------------- */
 typedef int (*pcg_fn)(const og_grid*, double, int, const double*, double*, double, int, int, int*, double*);
 
+static int pcg_pc2_lines(const og_grid* g, double alpha, int ncomp, const double* b, double* x, double tol,
+                         int max_iter, int fixed_iters, int* iters, double* relres) {
+    return og_pcg_pc2(g, alpha, 1, ncomp, b, x, tol, max_iter, fixed_iters, iters, relres);
+}
+
 /* the step of algorithm 1 with the options of og_step_opts (info: 11 entries, 13 with
  * OG_OPT_RES_IMPLICIT) */
 static int step_impl(const og_grid* g, int opts, double nu, double eta, double cfl, double dt_fixed,
                      double dt_max, double asi_fixed, double tol, int max_iter, double* v, double* br,
                      double* bt, double* bp, double* info) {
-    pcg_fn pcg = (opts & OG_OPT_PCG_CG) ? og_pcg_cg : og_pcg;
+    pcg_fn pcg = (opts & OG_OPT_PC2) ? pcg_pc2_lines : ((opts & OG_OPT_PCG_CG) ? og_pcg_cg : og_pcg);
     int res_it = 0;
     double res_rr = 0.0;
     long long N = g->N, n3 = 3 * N;

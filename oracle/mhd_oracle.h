@@ -76,7 +76,7 @@ void og_divb(const og_grid* g, const double* br, const double* bt, const double*
  * replaces the computed alpha_SI (frozen map for finite differences). info = {dt, cf, cw, asi, anu, it0, it1, it2,
  * rr0, rr1, rr2} (11 doubles) */
 /* step options (bit mask) of og_step_opts */
-enum { OG_OPT_PCG_CG = 1, OG_OPT_STS = 2, OG_OPT_RES_IMPLICIT = 4 };
+enum { OG_OPT_PCG_CG = 1, OG_OPT_STS = 2, OG_OPT_RES_IMPLICIT = 4, OG_OPT_PC2 = 8 };
 int og_step(const og_grid* g, double nu, double eta, double cfl, double dt_fixed, double dt_max,
             double asi_fixed, double tol, int max_iter, double* v, double* br, double* bt,
             double* bp, double* info);
@@ -109,7 +109,8 @@ int og_step_sts(const og_grid* g, double nu, double eta, double cfl, double dt_f
 
 /* og_step with options: OG_OPT_PCG_CG every solve in the single-reduction form, OG_OPT_STS
  * viscosity by RKL2, OG_OPT_RES_IMPLICIT resistivity by the implicit face solve (info then has
- * 13 entries: [11] its iterations, [12] its relative residual) */
+ * 13 entries: [11] its iterations, [12] its relative residual), OG_OPT_PC2 every cell solve
+ * preconditioned by PC2 with phi-line blocks */
 int og_step_opts(const og_grid* g, int opts, double nu, double eta, double cfl, double dt_fixed, double dt_max,
                  double asi_fixed, double tol, int max_iter, double* v, double* br, double* bt, double* bp,
                  double* info);

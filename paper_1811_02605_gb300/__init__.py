@@ -31,7 +31,7 @@ SYMBOLS = ["mhd_grid_create", "mhd_grid_destroy", "mhd_grid_sizes", "mhd_step_co
            "mhd_last_error"]
 
 KERNELS = ["pupdate64", "spmv64", "update64", "pupdate32", "spmv32", "update32", "outer_res", "force",
-           "induction", "coeffs", "sts", "res"]
+           "induction", "coeffs", "sts", "res", "pc2"]
 
 
 class GridDesc(C.Structure):
@@ -45,7 +45,7 @@ class Params(C.Structure):
                 ("tol", C.c_double), ("inner_tol", C.c_double),
                 ("max_iter", C.c_int), ("max_outer", C.c_int), ("precision", C.c_int),
                 ("mixed_restart", C.c_int), ("viscosity_sts", C.c_int), ("pcg_variant", C.c_int),
-                ("resistivity_implicit", C.c_int)]
+                ("resistivity_implicit", C.c_int), ("preconditioner", C.c_int)]
 
 
 class Fields(C.Structure):
@@ -134,9 +134,10 @@ def _check(st, grid=None, soft=(MHD_OK,)):
 
 def make_params(nu=1e-3, eta=0.0, cfl=0.4, dt_fixed=0.0, dt_max=0.0, alpha_si_fixed=-1.0, tol=1e-9,
                 inner_tol=1e-5, max_iter=100000, max_outer=30, precision=PREC_FP64,
-                mixed_restart=0, viscosity_sts=0, pcg_variant=0, resistivity_implicit=0) -> Params:
+                mixed_restart=0, viscosity_sts=0, pcg_variant=0, resistivity_implicit=0,
+                preconditioner=0) -> Params:
     return Params(nu, eta, cfl, dt_fixed, dt_max, alpha_si_fixed, tol, inner_tol, max_iter, max_outer,
-                  precision, mixed_restart, viscosity_sts, pcg_variant, resistivity_implicit)
+                  precision, mixed_restart, viscosity_sts, pcg_variant, resistivity_implicit, preconditioner)
 
 
 def make_fields(br, bt, bp, vr=None, vt=None, vp=None) -> Fields:

@@ -297,6 +297,7 @@ extern "C" mhd_status_t mhd_grid_destroy(mhd_grid_t g) {
     batched_forget(g);
     adjoint_free(g);
     res_free(g);
+    pc2_free(g);
     for (auto& row : g->iter_graph)
         for (auto& ge : row)
             if (ge) cudaGraphExecDestroy(ge);

@@ -129,6 +129,7 @@ struct mhd_grid_s {
     double* partials;       // [kMaxBlocks * kPartialsPerBlock]
     void* adj_mem;          // adjoint workspace, allocated by the first adjoint call
     void* res_mem;          // implicit-resistivity workspace, allocated by the first such step
+    void* pc2_mem;          // PC2 workspace (1 / dt of the phi-line ILU(0)), allocated by the first PC2 solve
     mhd::PcgScalars* sc;    // device
     mhd::StepScalars* ss;   // device
     mhd::PcgScalars* h_sc;  // pinned host mirror
@@ -175,6 +176,9 @@ int sts_stages(const mhd_grid_s* g, double nu, double dt);
 mhd_status_t res_solve(mhd_grid_s* g, const double* dt_dev, double eta, double* br, double* bt, double* bp,
                        const mhd_params_t* p, int* iters, double* relres);
 void res_free(mhd_grid_s* g);
+mhd_status_t pc2_solve(mhd_grid_s* g, int nc, const double* b, double* x, const double* x0, const mhd_params_t* prm,
+                       int* iters, int* outer, double* relres);
+void pc2_free(mhd_grid_s* g);
 int sts_advance(mhd_grid_s* g, double nu, const double* dt_dev, double dt_host, double* y);
 
 // tiled FP32 CG kernels (tiled.cu)

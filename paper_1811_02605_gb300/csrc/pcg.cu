@@ -927,6 +927,7 @@ mhd_status_t solve(mhd_grid_s* g, const double* alpha_dev, int nc, const double*
     const Dims d = g->d;
     const bool mixed = (prm->precision == MHD_PREC_MIXED);
     build_tables(g, alpha_dev, mixed);
+    if (prm->preconditioner == 1) return pc2_solve(g, nc, b, x, x0, prm, iters, outer, relres);
     if (mixed && g->slab32 == 0) {
         mhd_status_t st = tune_slab32(g, 3);
         if (st != MHD_OK) return st;

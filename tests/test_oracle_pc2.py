@@ -93,3 +93,15 @@ def test_line_blocks_capture_the_polar_phi_coupling():
     _, il, _, _ = g.pcg(c["alpha_si"], b, tol=1e-9, pc2="lines")
     _, iw, _, _ = g.pcg(c["alpha_si"], b, tol=1e-9, pc2="whole")
     assert iw <= il < i1 / 3, (i1, il, iw)
+
+
+def test_step_with_pc2_agrees_within_solver_tolerance():
+    d = I.GridDesc(8, 8, 16, 1.0, 10.0, 1.05)
+    st = I.initial_state(d, 0, False)
+    g = O.Grid.from_desc(d)
+    a, ia = g.step(st, tol=1e-11)
+    b, ib = g.step(st, tol=1e-11, pc2=True)
+    assert ia["status"] == O.OK and ib["status"] == O.OK
+    assert ib["iters"][0] < ia["iters"][0]
+    for k in ("vr", "vt", "vp", "br", "bt", "bp"):
+        assert np.linalg.norm(a[k] - b[k]) <= 1e-8 * np.linalg.norm(a[k]), k
