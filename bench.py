@@ -52,6 +52,9 @@ SPMV_BYTES_PER_CELL = {"fp64": 2 * 3 * 8, "fp32": 2 * 3 * 4}
 # D_{j-2} and ly0 read, D_j written = 4 x 3 x 8 B
 STS_FLOPS_PER_CELL = 3 * 16 + 3
 STS_BYTES_PER_CELL = 4 * 3 * 8
+# PC2 line kernel per cell: x, p, r, q read, x, r, z written (7 x 3 x 8 B) plus 1/dt (8 B, shared
+# by the three components)
+PC2_LINE_BYTES_PER_CELL = 7 * 3 * 8 + 8
 
 
 def peaks():
@@ -245,13 +248,13 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def run(precision, steps, warmup, profile, inner_tol=1e-5, restart=1, snapshot=None, sts=0, variant=0):
+    def run(precision, steps, warmup, profile, inner_tol=1e-5, restart=1, snapshot=None, sts=0, variant=0, pc=0):
         ds = dev_state()
         torch.cuda.synchronize()
         f = P.make_fields(ds["br"], ds["bt"], ds["bp"], ds["vr"], ds["vt"], ds["vp"])
         prm = P.make_params(nu=w["nu"], eta=w["eta"], cfl=w["cfl"], tol=w["tol"], precision=precision,
                             inner_tol=inner_tol, max_outer=200, max_iter=20000, mixed_restart=restart,
-                            viscosity_sts=sts, pcg_variant=variant)
+                            viscosity_sts=sts, pcg_variant=variant, preconditioner=pc)
         for _ in range(warmup):
             st, info = P.mhd_step(g, prm, f)
             if st != P.MHD_OK:
@@ -294,12 +297,13 @@ def run_ours(args):
     spmv_ms, spmv_n = prof64["spmv64"]
     pcg64_ms = sum(prof64[k][0] for k in ("pupdate64", "spmv64", "update64"))
     pcg64_n = prof64["spmv64"][1]
+    it64_total = max(sum(sum(i["iters"]) for i in infos64), 1)   # CG iterations actually run
     # share of the FP64 PCG time spent in the viscous solves (by iteration count)
     visc_it = sum(i["iters"][2] for i in infos64)
-    visc64_ms = pcg64_ms * visc_it / max(pcg64_n, 1) / len(infos64)
-    spmv_avg = spmv_ms / max(spmv_n, 1)
+    visc64_ms = pcg64_ms * visc_it / it64_total / len(infos64)
+    spmv_avg = spmv_ms / max(min(spmv_n, sum(sum(i["iters"]) for i in infos64)), 1)
     spmv_tflops = SPMV_FLOPS_PER_CELL * N / (spmv_avg * 1e-3) / 1e12
-    pcg64_gbs = PCG_BYTES_PER_CELL["fp64"] * N * pcg64_n / (pcg64_ms * 1e-3) / 1e9
+    pcg64_gbs = PCG_BYTES_PER_CELL["fp64"] * N * it64_total / (pcg64_ms * 1e-3) / 1e9
     roof = dict(bound="alu", achieved=round(spmv_tflops, 4), peak=round(FP64_PEAK_TFLOPS / 1e3, 4),
                 unit="TFLOP/s", frac=round(spmv_tflops / (FP64_PEAK_TFLOPS / 1e3), 4),
                 traffic=(int(SPMV64_DRAM_BYTES_PER_CELL * N) if prof64["pupdate64"][1] else None),
@@ -311,7 +315,7 @@ def run_ours(args):
         msm, infosm, profm, clkm, dsm = run(P.PREC_MIXED, args.steps, args.warmup, True, inner_tol, restart)
         msm = maxr(msm)
         pcg32_ms = sum(profm[k][0] for k in ("pupdate32", "spmv32", "update32"))
-        pcg32_n = profm["spmv32"][1]
+        pcg32_n = max(sum(sum(i["iters"]) for i in infosm), 1)   # inner CG iterations actually run
         pcg32_gbs = PCG_BYTES_PER_CELL["fp32"] * N * pcg32_n / (pcg32_ms * 1e-3) / 1e9
         tiled = profm["pupdate32"][1] == 0
         # per-kernel DRAM passes of a 3-component FP32 vector (4 B x 3 per cell per pass)
@@ -320,7 +324,7 @@ def run_ours(args):
         for k in ("pupdate32", "spmv32", "update32"):
             ms_k, n_k = profm[k]
             if n_k:
-                avg = ms_k / n_k
+                avg = ms_k / pcg32_n   # one launch per inner iteration that ran
                 gbs = kb[k] * 12 * N / (avg * 1e-3) / 1e9
                 kernels[k] = dict(avg_launch_ms=round(avg, 4), bytes_per_cell=kb[k] * 12, gbs=round(gbs, 1),
                                   frac_of_hbm=round(gbs / hbm, 4))
@@ -373,12 +377,38 @@ def run_ours(args):
         c_ms = profc["spmv64"][0] + profc["update64"][0]
         c_n = profc["spmv64"][1]
         pcg_cg = dict(ms_per_step=round(msc, 3), speedup_vs_fp64=round(ms64 / msc, 3), pcg_iters_per_step=itc,
-                      ms_per_iteration=round(c_ms / max(c_n, 1), 4),
-                      ms_per_iteration_hestenes_stiefel=round(pcg64_ms / max(pcg64_n, 1), 4),
+                      ms_per_iteration=round(c_ms / max(sum(sum(i["iters"]) for i in infosc), 1), 4),
+                      ms_per_iteration_hestenes_stiefel=round(pcg64_ms / it64_total, 4),
                       kernels_per_iteration=2,
                       rel_l2_vs_fp64_after_steps={k: float(torch.linalg.norm(dsc[k] - ds64[k]) /
                                                            torch.linalg.norm(ds64[k])) for k in ds64},
                       clocks=clkc, kernel_ms={k: round(v[0], 3) for k, v in profc.items() if v[1]})
+
+    # ---- PC2: block-Jacobi ILU(0) on phi lines (FP64), alone and with RKL2 viscosity
+    def pc2_entry(sts_flag):
+        msp, infosp, profp, clkp, dsp = run(P.PREC_FP64, args.steps, args.warmup, True, sts=sts_flag, pc=1)
+        msp = maxr(msp)
+        # per iteration: summed kernel time over the CG iterations actually run (launches that return
+        # at once after convergence last a few microseconds and are not iterations)
+        n_it = sum(sum(i["iters"][:2] if sts_flag else i["iters"]) for i in infosp)
+        per_it = {k: round(profp[k][0] / max(n_it, 1), 4) for k in ("pupdate64", "spmv64", "pc2")}
+        line_ms = profp["pc2"][0] / max(n_it, 1)
+        return dict(viscosity=("RKL2" if sts_flag else "PCG+PC2"), ms_per_step=round(msp, 3),
+                    speedup_vs_fp64=round(ms64 / msp, 3),
+                    pcg_iters_per_step=[sum(i["iters"][q] for i in infosp) / len(infosp) for q in range(3)],
+                    pcg_iters_per_step_pc1=[sum(i["iters"][q] for i in infos64) / len(infos64) for q in range(3)],
+                    ms_per_iteration=round(sum(per_it.values()), 4), ms_per_iteration_pc1=round(pcg64_ms / it64_total, 4),
+                    kernel_ms_per_iteration=per_it,
+                    line_kernel_gbs=round(PC2_LINE_BYTES_PER_CELL * N / (line_ms * 1e-3) / 1e9, 1),
+                    rel_l2_vs_fp64_after_steps={k: float(torch.linalg.norm(dsp[k] - ds64[k]) /
+                                                         torch.linalg.norm(ds64[k])) for k in ds64},
+                    clocks=clkp, kernel_ms={k: round(v[0], 3) for k, v in profp.items() if v[1]})
+
+    pc2 = pc2_sts = None
+    if not args.no_pc2:
+        pc2 = pc2_entry(0)
+        if not args.no_sts:
+            pc2_sts = pc2_entry(1)
 
     sts = sts_mixed = None
     if not args.no_sts:
@@ -431,6 +461,7 @@ def run_ours(args):
                     pcg_gbs=dict(fp64=round(pcg64_gbs, 1), fp64_frac_of_hbm=round(pcg64_gbs / hbm, 4),
                                  peak_gbs=hbm, peak_source=peak_src),
                     roofline=roof, mixed=mixed, mixed_reliable=mixed_reliable, sts=sts, sts_mixed_reliable=sts_mixed, pcg_single_reduction=pcg_cg,
+                    pc2=pc2, pc2_sts=pc2_sts,
                     e2e=e2e, cpu_baseline=cpu, clocks=clk64,
                     gpu_launches=int(launches), kernel_ms={k: round(v[0], 3) for k, v in prof64.items() if v[1]})
         print(json.dumps(line), flush=True)
@@ -651,11 +682,23 @@ def run_profile_case(args):
     b = torch.empty((3, d.nr, d.nt, d.np), dtype=torch.float64, device="cuda")
     P.mhd_force(g, f, c["dt"], b)
     out = {}
-    for name, prec in (("fp64", P.PREC_FP64), ("mixed", P.PREC_MIXED)):
+    legs = args.profile_legs.split(",")
+    for name, prec, pc in (("fp64", P.PREC_FP64, 0), ("mixed", P.PREC_MIXED, 0), ("pc2", P.PREC_FP64, 1)):
+        if name not in legs:
+            continue
         x = torch.zeros_like(b)
-        prm = P.make_params(tol=1e-30, max_iter=args.profile_iters, precision=prec, max_outer=1)
+        prm = P.make_params(tol=1e-30, max_iter=args.profile_iters, precision=prec, max_outer=1, preconditioner=pc)
         st, it, ou, rr = P.pcg_solve(g, c["alpha_si"], b, x, prm)
         out[name] = dict(status=P.STATUS_NAMES[st], iters=it, outer=ou, relres=rr)
+    # whole steps with capped cell solves: the RKL2 stages (sts) or the implicit resistive solve (res)
+    for name, kw in (("sts", dict(viscosity_sts=1)), ("res", dict(resistivity_implicit=1, eta=1e-2))):
+        if name not in legs:
+            continue
+        dsc = {k: v.clone() for k, v in ds.items()}
+        fc = P.make_fields(dsc["br"], dsc["bt"], dsc["bp"], dsc["vr"], dsc["vt"], dsc["vp"])
+        prm = P.make_params(nu=w["nu"], cfl=w["cfl"], tol=1e-30, max_iter=args.profile_iters, **kw)
+        st, info = P.mhd_step(g, prm, fc)
+        out[name] = dict(status=P.STATUS_NAMES[st], stages=info["iters"][2], res_iters=info["iters_res"])
     torch.cuda.synchronize()
     print(json.dumps(dict(profile_case=f"{d.nr}x{d.nt}x{d.np}", alpha_si=c["alpha_si"], **out)), flush=True)
 
@@ -671,6 +714,8 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="run a few CG iterations of the first SI solve (for ncu captures) and exit")
     ap.add_argument("--profile-iters", type=int, default=6)
+    ap.add_argument("--profile-legs", default="fp64,mixed",
+                    help="--profile-case pieces: fp64, mixed, pc2 (capped solves), sts, res (capped steps)")
     ap.add_argument("--batched", action="store_true", help="time the 64-system batched solve and exit")
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--adjoint", action="store_true", help="time and check the adjoint workload and exit")
@@ -681,6 +726,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-sts", action="store_true", help="skip the RKL2-viscosity entries")
     ap.add_argument("--no-cg", action="store_true", help="skip the single-reduction PCG entry")
+    ap.add_argument("--no-pc2", action="store_true", help="skip the PC2 entries")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-iters", type=int, default=1000,
