@@ -679,10 +679,32 @@ void enqueue_cg(mhd_grid_s* g, cudaStream_t st, int blocks) {
     prof_end(g, st, ps);
 }
 
-// kind: 0 FP64 Hestenes-Stiefel, 1 FP32 inner (Hestenes-Stiefel), 2 FP64 single-reduction
+// PC2 on the scaled system: p~ = z~ + beta p~, q~ = A~ p~ with <p~, q~>, then the phi-line kernel
+template <int NC>
+void enqueue_pc2(mhd_grid_s* g, cudaStream_t st, int blocks) {
+    const Dims d = g->d;
+    double* z = g->p64 + 3 * (size_t)d.N;
+    int ps = prof_begin(g, st, MHD_KERNEL_PUPDATE64);
+    k_pupdate<double, 2, NC><<<blocks, kThreads, 0, st>>>(d, z, g->p64, g->sc);
+    prof_end(g, st, ps);
+    ps = prof_begin(g, st, MHD_KERNEL_SPMV64);
+    k_spmv_dot<double, 2, NC><<<blocks, kThreads, 0, st>>>(d, g->p64, g->q64, g->t64, g->sc, g->partials);
+    prof_end(g, st, ps);
+    ps = prof_begin(g, st, MHD_KERNEL_PC2);
+    pc2_enqueue_line(g, st, NC);
+    prof_end(g, st, ps);
+}
+
+// kind: 0 FP64 Hestenes-Stiefel, 1 FP32 inner (Hestenes-Stiefel), 2 FP64 single-reduction,
+// 3 FP64 with PC2
 void enqueue_iteration(mhd_grid_s* g, cudaStream_t st, int prec, int nc) {
     const Dims d = g->d;
-    if (prec == 2) {
+    if (prec == 3) {
+        const int blocks = grid_blocks(g, d.N / 2, kPerSmIter);
+        if (nc == 3) enqueue_pc2<3>(g, st, blocks);
+        else if (nc == 2) enqueue_pc2<2>(g, st, blocks);
+        else enqueue_pc2<1>(g, st, blocks);
+    } else if (prec == 2) {
         const int blocks = grid_blocks(g, d.N / 2, kPerSmIter);
         if (nc == 3) enqueue_cg<3>(g, st, blocks);
         else if (nc == 2) enqueue_cg<2>(g, st, blocks);
@@ -927,12 +949,11 @@ mhd_status_t solve(mhd_grid_s* g, const double* alpha_dev, int nc, const double*
     const Dims d = g->d;
     const bool mixed = (prm->precision == MHD_PREC_MIXED);
     build_tables(g, alpha_dev, mixed);
-    if (prm->preconditioner == 1) return pc2_solve(g, nc, b, x, x0, prm, iters, outer, relres);
     if (mixed && g->slab32 == 0) {
         mhd_status_t st = tune_slab32(g, 3);
         if (st != MHD_OK) return st;
     }
-    if (!mixed && nc == 3 && g->slab64 == 0 && prm->pcg_variant == 0) {
+    if (!mixed && nc == 3 && g->slab64 == 0 && prm->pcg_variant == 0 && prm->preconditioner == 0) {
         mhd_status_t st = tune_slab64(g);
         if (st != MHD_OK) return st;
     }
@@ -943,7 +964,8 @@ mhd_status_t solve(mhd_grid_s* g, const double* alpha_dev, int nc, const double*
                                                       g->partials);
         mhd_status_t st = check_cuda(g, "pcg init");
         if (st != MHD_OK) return st;
-        st = run_iterations(g, prm->pcg_variant == 1 ? 2 : 0, nc);
+        if (prm->preconditioner == 1 && (st = pc2_prepare(g, nc)) != MHD_OK) return st;
+        st = run_iterations(g, prm->preconditioner == 1 ? 3 : (prm->pcg_variant == 1 ? 2 : 0), nc);
         if (st != MHD_OK) return st;
         k_finish64<<<blocks2, kThreads, 0, g->stream>>>(d, nc, g->x64, x, g->t64.s, g->sc);
         if ((st = check_cuda(g, "pcg finish")) != MHD_OK) return st;
