@@ -66,7 +66,9 @@ __host__ __device__ inline int padded_len(int np) {
 // One warp per phi line of the scaled system: (unless INIT) x~ += alpha p~, r~ -= alpha q~; then
 // z~ = P~^-1 r~; <r~, z~> and ||r||^2 = sum dg r~^2. INIT sets p~ = z~. Last CTA: beta (0 for
 // INIT), stop test.
-template <int NC, bool INIT>
+// SEG > 0: the segment length S is a compile-time constant (np in (32 (SEG - 1), 32 SEG]), so the
+// segment loops unroll and their shared-memory loads issue together; SEG = 0: any np.
+template <int NC, bool INIT, int SEG>
 __global__ void __launch_bounds__(kThreads) k_pc2_line(Dims d, OpTab<double> t, const double* __restrict__ dgv,
                                                        const double* __restrict__ idt, double* __restrict__ x,
                                                        double* __restrict__ p, double* __restrict__ r,
@@ -77,13 +79,13 @@ __global__ void __launch_bounds__(kThreads) k_pc2_line(Dims d, OpTab<double> t, 
     const int warps = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int np = d.np;
-    const int S = (np + 31) >> 5;
+    const int S = SEG > 0 ? SEG : (np + 31) >> 5;
     const int P = padded_len(np);
     double* ib = smem + (size_t)warp * 3 * P;   // 1 / dt_k
     double* gb = ib + P;                        // w / dt_k
     double* ub = gb + P;                        // work line
     const double al = INIT ? 0.0 : sc->alpha;
-    const int k0 = lane * S, k1 = min(k0 + S, np);
+    const int k0 = lane * S;
     double a_rz = 0.0, a_rr = 0.0;
     const int nl = d.nr * d.nt;
     for (int line = blockIdx.x * warps + warp; line < nl; line += gridDim.x * warps) {
@@ -95,12 +97,18 @@ __global__ void __launch_bounds__(kThreads) k_pc2_line(Dims d, OpTab<double> t, 
             gb[k + k / S] = w * id;
         }
         __syncwarp();
-        // component-independent multipliers: forward a_k (a_0 = 0), backward c_k (c_{np-1} = 0)
+        // component-independent multipliers: forward a_k (a_0 = 0), backward c_k (c_{np-1} = 0);
+        // element k0 + t of this lane's segment sits at s0 + t
+        const int s0 = lane * (S + 1);
         double A = 1.0, Cm = 1.0;
-        for (int k = k0; k < k1; k++) {
-            const double g = gb[k + k / S];
-            A *= (k == 0) ? 0.0 : g;
-            Cm *= (k == np - 1) ? 0.0 : g;
+#pragma unroll
+        for (int tt = 0; tt < S; tt++) {
+            const int k = k0 + tt;
+            if (k < np) {
+                const double g = gb[s0 + tt];
+                A *= (k == 0) ? 0.0 : g;
+                Cm *= (k == np - 1) ? 0.0 : g;
+            }
         }
         double As[5], Cs[5];
 #pragma unroll
@@ -130,12 +138,16 @@ __global__ void __launch_bounds__(kThreads) k_pc2_line(Dims d, OpTab<double> t, 
             const double u0 = ub[0] * ib[0];
             __syncwarp();
             double B = 0.0;
-            for (int k = k0; k < k1; k++) {
-                const int s = k + k / S;
-                double bk = ub[s] * ib[s];
-                if (k == np - 1) bk = fma(gb[s], u0, bk);
-                ub[s] = bk;
-                B = fma((k == 0) ? 0.0 : gb[s], B, bk);
+#pragma unroll
+            for (int tt = 0; tt < S; tt++) {
+                const int k = k0 + tt;
+                if (k < np) {
+                    const int sx = s0 + tt;
+                    double bk = ub[sx] * ib[sx];
+                    if (k == np - 1) bk = fma(gb[sx], u0, bk);
+                    ub[sx] = bk;
+                    B = fma((k == 0) ? 0.0 : gb[sx], B, bk);
+                }
             }
 #pragma unroll
             for (int st = 0; st < 5; st++) {
@@ -145,22 +157,30 @@ __global__ void __launch_bounds__(kThreads) k_pc2_line(Dims d, OpTab<double> t, 
             }
             double u = __shfl_up_sync(kFull, B, 1);
             if (lane == 0) u = 0.0;
-            for (int k = k0; k < k1; k++) {
-                const int s = k + k / S;
-                u = fma((k == 0) ? 0.0 : gb[s], u, ub[s]);
-                ub[s] = u;
+#pragma unroll
+            for (int tt = 0; tt < S; tt++) {
+                const int k = k0 + tt;
+                if (k < np) {
+                    const int sx = s0 + tt;
+                    u = fma((k == 0) ? 0.0 : gb[sx], u, ub[sx]);
+                    ub[sx] = u;
+                }
             }
             __syncwarp();
             // backward: z_{np-1} = u_{np-1}; z_k = u_k + w z_{k+1} / dt_k; the first also + w z_{np-1} / dt_0
             const double zl = ub[(np - 1) + (np - 1) / S];
             __syncwarp();
             double E = 0.0;
-            for (int k = k1 - 1; k >= k0; k--) {
-                const int s = k + k / S;
-                double e = ub[s];
-                if (k == 0) e = fma(gb[s], zl, e);
-                ub[s] = e;
-                E = fma((k == np - 1) ? 0.0 : gb[s], E, e);
+#pragma unroll
+            for (int tt = S - 1; tt >= 0; tt--) {
+                const int k = k0 + tt;
+                if (k < np) {
+                    const int sx = s0 + tt;
+                    double e = ub[sx];
+                    if (k == 0) e = fma(gb[sx], zl, e);
+                    ub[sx] = e;
+                    E = fma((k == np - 1) ? 0.0 : gb[sx], E, e);
+                }
             }
 #pragma unroll
             for (int st = 0; st < 5; st++) {
@@ -170,10 +190,14 @@ __global__ void __launch_bounds__(kThreads) k_pc2_line(Dims d, OpTab<double> t, 
             }
             double zz = __shfl_down_sync(kFull, E, 1);
             if (lane == 31) zz = 0.0;
-            for (int k = k1 - 1; k >= k0; k--) {
-                const int s = k + k / S;
-                zz = fma((k == np - 1) ? 0.0 : gb[s], zz, ub[s]);
-                ub[s] = zz;
+#pragma unroll
+            for (int tt = S - 1; tt >= 0; tt--) {
+                const int k = k0 + tt;
+                if (k < np) {
+                    const int sx = s0 + tt;
+                    zz = fma((k == np - 1) ? 0.0 : gb[sx], zz, ub[sx]);
+                    ub[sx] = zz;
+                }
             }
             __syncwarp();
             for (int k = lane; k < np; k += 32) {
@@ -209,15 +233,19 @@ __global__ void __launch_bounds__(kThreads) k_pc2_line(Dims d, OpTab<double> t, 
 
 size_t line_smem(const Dims& d, int warps) { return (size_t)warps * 3 * padded_len(d.np) * sizeof(double); }
 
-template <bool INIT>
+template <bool INIT, int SEG>
 cudaError_t set_smem(size_t bytes) {
-    cudaError_t e = cudaFuncSetAttribute(k_pc2_line<1, INIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaError_t e = cudaFuncSetAttribute(k_pc2_line<1, INIT, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bytes);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_pc2_line<2, INIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        e = cudaFuncSetAttribute(k_pc2_line<2, INIT, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_pc2_line<3, INIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        e = cudaFuncSetAttribute(k_pc2_line<3, INIT, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     return e;
 }
+
+// compile-time segment length for np in [481, 512] (16 elements per lane), else the generic kernel
+int seg_of(const Dims& d) { return ((d.np + 31) / 32 == 16) ? 16 : 0; }
 
 mhd_status_t pc2_workspace(mhd_grid_s* g, Pc2Work** out) {
     if (g->pc2_mem) {
@@ -236,13 +264,16 @@ mhd_status_t pc2_workspace(mhd_grid_s* g, Pc2Work** out) {
     }
     w->warps = warps;
     w->smem = line_smem(g->d, warps);
-    if (set_smem<false>(w->smem) != cudaSuccess || set_smem<true>(w->smem) != cudaSuccess) {
+    const bool s16 = seg_of(g->d) == 16;
+    if ((s16 ? set_smem<false, 16>(w->smem) : set_smem<false, 0>(w->smem)) != cudaSuccess ||
+        (s16 ? set_smem<true, 16>(w->smem) : set_smem<true, 0>(w->smem)) != cudaSuccess) {
         cudaFree(w->idt);
         delete w;
         return check_cuda(g, "PC2: shared memory attribute");
     }
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pc2_line<3, false>, 32 * warps, w->smem);
+    if (s16) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pc2_line<3, false, 16>, 32 * warps, w->smem);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pc2_line<3, false, 0>, 32 * warps, w->smem);
     if (per_sm < 1) per_sm = 1;
     const int nl = g->d.nr * g->d.nt;
     w->line_blocks = std::min(std::min(g->num_sms * per_sm, (nl + warps - 1) / warps), kMaxBlocks);
@@ -251,20 +282,26 @@ mhd_status_t pc2_workspace(mhd_grid_s* g, Pc2Work** out) {
     return MHD_OK;
 }
 
-template <bool INIT>
-void launch_line(mhd_grid_s* g, cudaStream_t st, const Pc2Work* w, int nc) {
+template <bool INIT, int SEG>
+void launch_line_seg(mhd_grid_s* g, cudaStream_t st, const Pc2Work* w, int nc) {
     const Dims d = g->d;
     double* z = g->p64 + 3 * (size_t)d.N;
     const dim3 grid(w->line_blocks), block(32 * w->warps);
     if (nc == 3)
-        k_pc2_line<3, INIT><<<grid, block, w->smem, st>>>(d, g->t64, g->tu.dg, w->idt, g->x64, g->p64, g->r64, g->q64,
-                                                           z, g->sc, g->partials);
+        k_pc2_line<3, INIT, SEG><<<grid, block, w->smem, st>>>(d, g->t64, g->tu.dg, w->idt, g->x64, g->p64, g->r64,
+                                                                g->q64, z, g->sc, g->partials);
     else if (nc == 2)
-        k_pc2_line<2, INIT><<<grid, block, w->smem, st>>>(d, g->t64, g->tu.dg, w->idt, g->x64, g->p64, g->r64, g->q64,
-                                                           z, g->sc, g->partials);
+        k_pc2_line<2, INIT, SEG><<<grid, block, w->smem, st>>>(d, g->t64, g->tu.dg, w->idt, g->x64, g->p64, g->r64,
+                                                                g->q64, z, g->sc, g->partials);
     else
-        k_pc2_line<1, INIT><<<grid, block, w->smem, st>>>(d, g->t64, g->tu.dg, w->idt, g->x64, g->p64, g->r64, g->q64,
-                                                           z, g->sc, g->partials);
+        k_pc2_line<1, INIT, SEG><<<grid, block, w->smem, st>>>(d, g->t64, g->tu.dg, w->idt, g->x64, g->p64, g->r64,
+                                                                g->q64, z, g->sc, g->partials);
+}
+
+template <bool INIT>
+void launch_line(mhd_grid_s* g, cudaStream_t st, const Pc2Work* w, int nc) {
+    if (seg_of(g->d) == 16) launch_line_seg<INIT, 16>(g, st, w, nc);
+    else launch_line_seg<INIT, 0>(g, st, w, nc);
 }
 
 }  // namespace
