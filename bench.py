@@ -385,9 +385,21 @@ def run_ours(args):
                       clocks=clkc, kernel_ms={k: round(v[0], 3) for k, v in profc.items() if v[1]})
 
     # ---- PC2: block-Jacobi ILU(0) on phi lines (FP64), alone and with RKL2 viscosity
-    def pc2_entry(sts_flag):
-        msp, infosp, profp, clkp, dsp = run(P.PREC_FP64, args.steps, args.warmup, True, sts=sts_flag, pc=1)
+    def pc2_entry(sts_flag, precision=P.PREC_FP64):
+        msp, infosp, profp, clkp, dsp = run(precision, args.steps, args.warmup, True, inner_tol=0.1, restart=0,
+                                            sts=sts_flag, pc=1)
         msp = maxr(msp)
+        if precision == P.PREC_MIXED:
+            n_it = max(sum(sum(i["iters"]) for i in infosp), 1)
+            return dict(viscosity="PCG+PC2", si_precision="mixed, reliable updates, inner_tol 0.1",
+                        ms_per_step=round(msp, 3), speedup_vs_fp64=round(ms64 / msp, 3),
+                        pcg_iters_per_step=[sum(i["iters"][q] for i in infosp) / len(infosp) for q in range(3)],
+                        outer_per_step=sum(sum(i["outer"]) for i in infosp) / len(infosp),
+                        max_relres=max(max(i["relres"]) for i in infosp),
+                        kernel_ms_per_iteration={k: round(profp[k][0] / n_it, 4) for k in ("pupdate32", "spmv32", "pc2")},
+                        rel_l2_vs_fp64_after_steps={k: float(torch.linalg.norm(dsp[k] - ds64[k]) /
+                                                             torch.linalg.norm(ds64[k])) for k in ds64},
+                        clocks=clkp, kernel_ms={k: round(v[0], 3) for k, v in profp.items() if v[1]})
         # per iteration: summed kernel time over the CG iterations actually run (launches that return
         # at once after convergence last a few microseconds and are not iterations)
         n_it = sum(sum(i["iters"][:2] if sts_flag else i["iters"]) for i in infosp)
@@ -404,11 +416,13 @@ def run_ours(args):
                                                          torch.linalg.norm(ds64[k])) for k in ds64},
                     clocks=clkp, kernel_ms={k: round(v[0], 3) for k, v in profp.items() if v[1]})
 
-    pc2 = pc2_sts = None
+    pc2 = pc2_sts = pc2_mixed = None
     if not args.no_pc2:
         pc2 = pc2_entry(0)
         if not args.no_sts:
             pc2_sts = pc2_entry(1)
+        if not args.no_mixed:
+            pc2_mixed = pc2_entry(0, P.PREC_MIXED)
 
     sts = sts_mixed = None
     if not args.no_sts:
@@ -461,7 +475,7 @@ def run_ours(args):
                     pcg_gbs=dict(fp64=round(pcg64_gbs, 1), fp64_frac_of_hbm=round(pcg64_gbs / hbm, 4),
                                  peak_gbs=hbm, peak_source=peak_src),
                     roofline=roof, mixed=mixed, mixed_reliable=mixed_reliable, sts=sts, sts_mixed_reliable=sts_mixed, pcg_single_reduction=pcg_cg,
-                    pc2=pc2, pc2_sts=pc2_sts,
+                    pc2=pc2, pc2_sts=pc2_sts, pc2_mixed_reliable=pc2_mixed,
                     e2e=e2e, cpu_baseline=cpu, clocks=clk64,
                     gpu_launches=int(launches), kernel_ms={k: round(v[0], 3) for k, v in prof64.items() if v[1]})
         print(json.dumps(line), flush=True)

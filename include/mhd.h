@@ -110,9 +110,11 @@ enum { MHD_PREC_FP64 = 0, MHD_PREC_MIXED = 1 };
  *            zero-fill incomplete LU factorisation (ILU(0)) in each block (Sec. 2.2); the blocks
  *            are the periodic phi lines (i, j) of each component, so the r and theta couplings
  *            are left out of the preconditioner and every line is solved independently (one warp
- *            per line, forward and backward substitution as affine scans). Needs precision FP64
- *            and pcg_variant 0 (MHD_ERR_ARG otherwise); applies to every solve of pcg_solve,
- *            mhd_step and mhd_adjoint_step; the first PC2 solve allocates N doubles for the
+ *            per line, forward and backward substitution as affine scans). In mixed precision
+ *            the FP32 inner solves use it too (FP32 factor copy; after each FP64 residual
+ *            replacement one preconditioner pass recomputes z and <r, z>). Needs pcg_variant 0
+ *            (MHD_ERR_ARG otherwise); applies to every solve of pcg_solve, mhd_step and
+ *            mhd_adjoint_step; the first PC2 solve allocates N doubles + N floats for the
  *            factorisation. pcg_solve_batched ignores it. */
 typedef struct {
     double nu, eta, cfl, dt_fixed, dt_max, alpha_si_fixed;

@@ -136,8 +136,8 @@ struct mhd_grid_s {
     mhd::StepScalars* h_ss; // pinned host mirror
     double* h_alpha;        // pinned host scalar staging
     // CUDA graphs of a batch of PCG iterations, keyed by kind (FP64, FP32 inner, FP64
-    // single-reduction, FP64 PC2) and ncomp
-    cudaGraphExec_t iter_graph[4][4];
+    // single-reduction, FP64 PC2, FP32 inner PC2) and ncomp
+    cudaGraphExec_t iter_graph[5][4];
     int graph_batch;
     int slab32;             // r-slab length of the tiled FP32 kernels (0: not tuned, -1: split kernels)
     int slab64;             // same for the FP64 fused p-update + stencil kernel
@@ -176,8 +176,10 @@ int sts_stages(const mhd_grid_s* g, double nu, double dt);
 mhd_status_t res_solve(mhd_grid_s* g, const double* dt_dev, double eta, double* br, double* bt, double* bp,
                        const mhd_params_t* p, int* iters, double* relres);
 void res_free(mhd_grid_s* g);
-mhd_status_t pc2_prepare(mhd_grid_s* g, int nc);
-void pc2_enqueue_line(mhd_grid_s* g, cudaStream_t st, int nc);
+mhd_status_t pc2_factor(mhd_grid_s* g);
+void pc2_init64(mhd_grid_s* g, int nc);
+void pc2_reliable32(mhd_grid_s* g, int nc, int restart);
+void pc2_enqueue_line(mhd_grid_s* g, cudaStream_t st, int nc, bool fp32);
 void pc2_free(mhd_grid_s* g);
 int sts_advance(mhd_grid_s* g, double nu, const double* dt_dev, double dt_host, double* y);
 

@@ -503,7 +503,8 @@ __global__ void __launch_bounds__(kThreads) k_outer_res(Dims d, int nc, const do
                                                         const double* __restrict__ x, float* __restrict__ r32,
                                                         float* __restrict__ p32, float* __restrict__ x32,
                                                         OpTab<double> t, OpTab64u tu, PcgScalars* sc,
-                                                        double* __restrict__ partials, int first, int restart) {
+                                                        double* __restrict__ partials, int first, int restart,
+                                                        int pc2) {
     const int nt = d.nt;
     const unsigned int G = (unsigned int)(d.N / 2);
     const long long plane = (long long)nt * d.np;
@@ -556,9 +557,12 @@ __global__ void __launch_bounds__(kThreads) k_outer_res(Dims d, int nc, const do
         sc->rr_out = out[0];
         // keep the recurrence only while the replaced residual still agrees with the recursive
         // one (rho_true <= 4 rho_recursive); otherwise beta = 0 restarts it (p = r next)
-        const bool keep = !restart && sc->rho_prev > 0.0 && out[2] <= 4.0 * sc->rho;
-        sc->beta = keep ? out[2] / sc->rho_prev : 0.0;
-        sc->rho = out[2];
+        // (with PC2 the preconditioner pass that follows forms rho = <r, z> and takes this decision)
+        if (!pc2) {
+            const bool keep = !restart && sc->rho_prev > 0.0 && out[2] <= 4.0 * sc->rho;
+            sc->beta = keep ? out[2] / sc->rho_prev : 0.0;
+            sc->rho = out[2];
+        }
         sc->rr = out[3];
         sc->iter = 0;
         const double bn = sqrt(sc->bb);
@@ -691,15 +695,42 @@ void enqueue_pc2(mhd_grid_s* g, cudaStream_t st, int blocks) {
     k_spmv_dot<double, 2, NC><<<blocks, kThreads, 0, st>>>(d, g->p64, g->q64, g->t64, g->sc, g->partials);
     prof_end(g, st, ps);
     ps = prof_begin(g, st, MHD_KERNEL_PC2);
-    pc2_enqueue_line(g, st, NC);
+    pc2_enqueue_line(g, st, NC, false);
     prof_end(g, st, ps);
 }
 
+// the same for the FP32 inner solves of mixed precision
+template <typename T, int V, int NC>
+void enqueue_pc2_32(mhd_grid_s* g, cudaStream_t st) {
+    const Dims d = g->d;
+    float* z = g->p32 + 3 * (size_t)d.N;
+    int ps = prof_begin(g, st, MHD_KERNEL_PUPDATE32);
+    k_pupdate<float, V, NC><<<grid_blocks(g, d.N / V, kPerSmIter), kThreads, 0, st>>>(d, z, g->p32, g->sc);
+    prof_end(g, st, ps);
+    ps = prof_begin(g, st, MHD_KERNEL_SPMV32);
+    k_spmv_dot<float, V, NC><<<grid_blocks(g, d.N / V, 6), kThreads, 0, st>>>(d, g->p32, g->q32, g->t32, g->sc,
+                                                                              g->partials);
+    prof_end(g, st, ps);
+    ps = prof_begin(g, st, MHD_KERNEL_PC2);
+    pc2_enqueue_line(g, st, NC, true);
+    prof_end(g, st, ps);
+}
+
+template <int V>
+void enqueue_pc2_32_nc(mhd_grid_s* g, cudaStream_t st, int nc) {
+    if (nc == 3) enqueue_pc2_32<float, V, 3>(g, st);
+    else if (nc == 2) enqueue_pc2_32<float, V, 2>(g, st);
+    else enqueue_pc2_32<float, V, 1>(g, st);
+}
+
 // kind: 0 FP64 Hestenes-Stiefel, 1 FP32 inner (Hestenes-Stiefel), 2 FP64 single-reduction,
-// 3 FP64 with PC2
+// 3 FP64 with PC2, 4 FP32 inner with PC2
 void enqueue_iteration(mhd_grid_s* g, cudaStream_t st, int prec, int nc) {
     const Dims d = g->d;
-    if (prec == 3) {
+    if (prec == 4) {
+        if (use_v4(g)) enqueue_pc2_32_nc<4>(g, st, nc);
+        else enqueue_pc2_32_nc<2>(g, st, nc);
+    } else if (prec == 3) {
         const int blocks = grid_blocks(g, d.N / 2, kPerSmIter);
         if (nc == 3) enqueue_pc2<3>(g, st, blocks);
         else if (nc == 2) enqueue_pc2<2>(g, st, blocks);
@@ -949,7 +980,8 @@ mhd_status_t solve(mhd_grid_s* g, const double* alpha_dev, int nc, const double*
     const Dims d = g->d;
     const bool mixed = (prm->precision == MHD_PREC_MIXED);
     build_tables(g, alpha_dev, mixed);
-    if (mixed && g->slab32 == 0) {
+    const bool pc2 = (prm->preconditioner == 1);
+    if (mixed && g->slab32 == 0 && !pc2) {
         mhd_status_t st = tune_slab32(g, 3);
         if (st != MHD_OK) return st;
     }
@@ -964,8 +996,11 @@ mhd_status_t solve(mhd_grid_s* g, const double* alpha_dev, int nc, const double*
                                                       g->partials);
         mhd_status_t st = check_cuda(g, "pcg init");
         if (st != MHD_OK) return st;
-        if (prm->preconditioner == 1 && (st = pc2_prepare(g, nc)) != MHD_OK) return st;
-        st = run_iterations(g, prm->preconditioner == 1 ? 3 : (prm->pcg_variant == 1 ? 2 : 0), nc);
+        if (pc2) {
+            if ((st = pc2_factor(g)) != MHD_OK) return st;
+            pc2_init64(g, nc);
+        }
+        st = run_iterations(g, pc2 ? 3 : (prm->pcg_variant == 1 ? 2 : 0), nc);
         if (st != MHD_OK) return st;
         k_finish64<<<blocks2, kThreads, 0, g->stream>>>(d, nc, g->x64, x, g->t64.s, g->sc);
         if ((st = check_cuda(g, "pcg finish")) != MHD_OK) return st;
@@ -983,12 +1018,17 @@ mhd_status_t solve(mhd_grid_s* g, const double* alpha_dev, int nc, const double*
     if (x != x0)
         cudaMemcpyAsync(x, x0, sizeof(double) * nc * d.N, cudaMemcpyDeviceToDevice, g->stream);
     double* saved = g->partials + kMaxBlocks * kPartialsPerBlock;  // spare doubles past the partials
+    if (pc2) {
+        mhd_status_t st = pc2_factor(g);
+        if (st != MHD_OK) return st;
+    }
     int outer_done = 0;
     for (int o = 0; o <= prm->max_outer; o++) {
         const int ps = prof_begin(g, g->stream, MHD_KERNEL_OUTER_RES);
         const int restart = (o == 0 || prm->mixed_restart) ? 1 : 0;
         k_outer_res<2><<<blocks2, kThreads, 0, g->stream>>>(d, nc, b, x, g->r32, g->p32, g->x32, g->t64, g->tu,
-                                                            g->sc, g->partials, o == 0 ? 1 : 0, restart);
+                                                            g->sc, g->partials, o == 0 ? 1 : 0, restart, pc2 ? 1 : 0);
+        if (pc2) pc2_reliable32(g, nc, restart);
         prof_end(g, g->stream, ps);
         mhd_status_t st = check_cuda(g, "outer residual");
         if (st != MHD_OK) return st;
@@ -996,7 +1036,7 @@ mhd_status_t solve(mhd_grid_s* g, const double* alpha_dev, int nc, const double*
         outer_done = g->h_sc->outer_done;
         if (outer_done || o == prm->max_outer) break;
         k_inner_begin<<<1, 1, 0, g->stream>>>(g->sc, saved);
-        st = run_iterations(g, 1, nc);
+        st = run_iterations(g, pc2 ? 4 : 1, nc);
         if (st != MHD_OK) return st;
         k_inner_end<<<1, 1, 0, g->stream>>>(g->sc, saved);
         if (g->h_sc->done == 3) break;

@@ -29,8 +29,8 @@ mhd_status_t check_params(mhd_grid_s* g, const mhd_params_t* p) {
         return set_error(g, MHD_ERR_ARG, "params: the single-reduction PCG form is FP64 only");
     if (p->preconditioner != 0 && p->preconditioner != 1)
         return set_error(g, MHD_ERR_ARG, "params: preconditioner must be 0 (PC1) or 1 (PC2)");
-    if (p->preconditioner == 1 && (p->precision != MHD_PREC_FP64 || p->pcg_variant != 0))
-        return set_error(g, MHD_ERR_ARG, "params: PC2 runs with precision FP64 and pcg_variant 0");
+    if (p->preconditioner == 1 && p->pcg_variant != 0)
+        return set_error(g, MHD_ERR_ARG, "params: PC2 runs with pcg_variant 0");
     if (p->resistivity_implicit != 0 && p->resistivity_implicit != 1)
         return set_error(g, MHD_ERR_ARG, "params: resistivity_implicit must be 0 or 1");
     if (!(p->eta >= 0.0)) return set_error(g, MHD_ERR_ARG, "params: need eta >= 0");

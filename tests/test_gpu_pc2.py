@@ -59,8 +59,7 @@ def test_pcg_pc2_edge_cases():
     b = torch.ones_like(z)
     st, it, ou, rr = P.pcg_solve(g, 0.0, b, x, P.make_params(tol=1e-12, preconditioner=1))   # M = D: exact
     assert st == P.MHD_OK and it == 1
-    for bad in (dict(preconditioner=1, precision=P.PREC_MIXED), dict(preconditioner=1, pcg_variant=1),
-                dict(preconditioner=2)):
+    for bad in (dict(preconditioner=1, pcg_variant=1), dict(preconditioner=2)):
         with pytest.raises(P.MhdError):
             P.pcg_solve(g, 1.0, b, x, P.make_params(**bad))
 
@@ -107,3 +106,43 @@ def test_adjoint_with_pc2_solves_matches_oracle():
     assert s1 == O.OK and s2 == P.MHD_OK
     for k in KEYS:
         assert rel_l2(to_np(out[k]), ref[k]) < 1e-9, k
+
+
+@pytest.mark.parametrize("d", [GRIDS[1], GRIDS[3], GRIDS[4]], ids=lambda d: f"{d.nr}x{d.nt}x{d.np}")
+@pytest.mark.parametrize("restart,inner", [(0, 0.1), (1, 1e-5)], ids=["reliable", "restart"])
+def test_pcg_mixed_pc2_reaches_fp64_tolerance(d, restart, inner):
+    # FP32 inner PCG with the FP32 phi-line preconditioner, FP64 residual replacement: the TRUE FP64
+    # residual reaches tol and the solution matches the oracle's converged one
+    g, og = grid(d), O.Grid.from_desc(d)
+    rng = np.random.default_rng(31)
+    b = rng.normal(size=(3, d.nr, d.nt, d.np)) * og.volumes()[None, :, :, None]
+    alpha = 4.0
+    xr, _, _, _ = og.pcg(alpha, b, tol=1e-13, pc2="lines")
+    for nc in (3, 1):
+        x = torch.zeros((nc,) + b.shape[1:], dtype=torch.float64, device="cuda")
+        prm = P.make_params(tol=1e-9, inner_tol=inner, precision=P.PREC_MIXED, max_outer=60, max_iter=5000,
+                            mixed_restart=restart, preconditioner=1)
+        st, it, ou, rr = P.pcg_solve(g, alpha, to_dev(b[:nc]), x, prm)
+        assert st == P.MHD_OK and rr <= 1e-9 and ou >= 1
+        res = b[:nc] - og.apply_M(alpha, to_np(x))
+        assert np.linalg.norm(res) <= 1e-9 * np.linalg.norm(b[:nc]) * 1.0000001
+        assert rel_l2(to_np(x), xr[:nc]) < 1e-6
+
+
+def test_step_mixed_pc2_against_fp64_oracle():
+    w, st0 = I.workload("parity_32x32x64")
+    d = w["desc"]
+    g, og = grid(d), O.Grid.from_desc(d)
+    ds = dev_state(st0)
+    f = fields(ds)
+    s = st0
+    prm = P.make_params(nu=w["nu"], cfl=w["cfl"], tol=w["tol"], precision=P.PREC_MIXED, inner_tol=0.1,
+                        max_outer=60, max_iter=5000, preconditioner=1)
+    for n in range(3):
+        stat, info = P.mhd_step(g, prm, f)
+        torch.cuda.synchronize()
+        s, oinfo = og.step(s, nu=w["nu"], cfl=w["cfl"], tol=w["tol"], pc2=True)
+        assert stat == P.MHD_OK and max(info["relres"]) <= 1e-9
+        for k in KEYS:
+            e = rel_l2(to_np(ds[k]), s[k])
+            assert e <= 1e-7, (n, k, e)
