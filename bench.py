@@ -697,7 +697,8 @@ def run_profile_case(args):
     P.mhd_force(g, f, c["dt"], b)
     out = {}
     legs = args.profile_legs.split(",")
-    for name, prec, pc in (("fp64", P.PREC_FP64, 0), ("mixed", P.PREC_MIXED, 0), ("pc2", P.PREC_FP64, 1)):
+    for name, prec, pc in (("fp64", P.PREC_FP64, 0), ("mixed", P.PREC_MIXED, 0), ("pc2", P.PREC_FP64, 1),
+                           ("pc2mixed", P.PREC_MIXED, 1)):
         if name not in legs:
             continue
         x = torch.zeros_like(b)
@@ -729,7 +730,7 @@ def main():
                     help="run a few CG iterations of the first SI solve (for ncu captures) and exit")
     ap.add_argument("--profile-iters", type=int, default=6)
     ap.add_argument("--profile-legs", default="fp64,mixed",
-                    help="--profile-case pieces: fp64, mixed, pc2 (capped solves), sts, res (capped steps)")
+                    help="--profile-case pieces: fp64, mixed, pc2, pc2mixed (capped solves), sts, res (capped steps)")
     ap.add_argument("--batched", action="store_true", help="time the 64-system batched solve and exit")
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--adjoint", action="store_true", help="time and check the adjoint workload and exit")
