@@ -672,10 +672,17 @@ def run_refinement_study(args):
 
     one("fp64")
     one("mixed warm-up", precision=1, inner_tol=0.1, max_outer=200)   # first mixed solve tunes kernels
-    for restart in (1, 0):
-        for itol in (1e-5, 1e-3, 1e-2, 1e-1, 0.3):
-            one("restarted" if restart else "reliable", precision=1, inner_tol=itol, max_outer=200,
-                max_iter=20000, mixed_restart=restart)
+    if not args.pc2_only:
+        for restart in (1, 0):
+            for itol in (1e-5, 1e-3, 1e-2, 1e-1, 0.3):
+                one("restarted" if restart else "reliable", precision=1, inner_tol=itol, max_outer=200,
+                    max_iter=20000, mixed_restart=restart)
+    # the same first solve with PC2 (phi-line block-Jacobi ILU(0)), FP64 and mixed
+    one("fp64 pc2", preconditioner=1)
+    one("mixed pc2 warm-up", precision=1, inner_tol=0.1, max_outer=200, preconditioner=1)
+    for itol in (1e-3, 1e-2, 3e-2, 1e-1, 0.3):
+        one("reliable pc2", precision=1, inner_tol=itol, max_outer=200, max_iter=20000, mixed_restart=0,
+            preconditioner=1)
     print(json.dumps(dict(workload=args.workload, grid=f"{d.nr}x{d.nt}x{d.np}", alpha_si=c["alpha_si"],
                           rows=rows)), flush=True)
 
@@ -742,6 +749,7 @@ def main():
     ap.add_argument("--no-sts", action="store_true", help="skip the RKL2-viscosity entries")
     ap.add_argument("--no-cg", action="store_true", help="skip the single-reduction PCG entry")
     ap.add_argument("--no-pc2", action="store_true", help="skip the PC2 entries")
+    ap.add_argument("--pc2-only", action="store_true", help="--refinement-study: only the PC2 rows")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-iters", type=int, default=1000,

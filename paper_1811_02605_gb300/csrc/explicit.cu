@@ -251,34 +251,35 @@ __global__ void __launch_bounds__(kThreads) k_force(Dims d, Geo G, Vel v, const 
         double u[3];
         v.at(c, u);
         const double rc = G.rc[i];
-        // upwind differences of the three components along r, theta, phi
+        // upwind differences of the three components along r, theta, phi (one reciprocal per
+        // distance: FP64 division is a long instruction sequence on this part)
         double Dr[3], Dt[3], Dp[3];
         if (u[0] > 0.0) {
             if (i > 0) {
                 double n[3];
                 v.at(c - (long long)d.nt * d.np, n);
-                const double h = rc - G.rc[i - 1];
-                for (int m = 0; m < 3; m++) Dr[m] = (u[m] - n[m]) / h;
+                const double ih = 1.0 / (rc - G.rc[i - 1]);
+                for (int m = 0; m < 3; m++) Dr[m] = (u[m] - n[m]) * ih;
             } else {
-                const double h = 2.0 * (G.rc[0] - G.r0);
-                for (int m = 0; m < 3; m++) Dr[m] = (u[m] - (-u[m])) / h;
+                const double ih = 1.0 / (2.0 * (G.rc[0] - G.r0));
+                for (int m = 0; m < 3; m++) Dr[m] = (u[m] - (-u[m])) * ih;
             }
         } else {
             if (i < d.nr - 1) {
                 double n[3];
                 v.at(c + (long long)d.nt * d.np, n);
-                const double h = G.rc[i + 1] - rc;
-                for (int m = 0; m < 3; m++) Dr[m] = (n[m] - u[m]) / h;
+                const double ih = 1.0 / (G.rc[i + 1] - rc);
+                for (int m = 0; m < 3; m++) Dr[m] = (n[m] - u[m]) * ih;
             } else {
                 for (int m = 0; m < 3; m++) Dr[m] = 0.0;
             }
         }
-        const double ht = rc * G.dth;
+        const double iht = 1.0 / (rc * G.dth);
         if (u[1] > 0.0) {
             if (j > 0) {
                 double n[3];
                 v.at(c - d.np, n);
-                for (int m = 0; m < 3; m++) Dt[m] = (u[m] - n[m]) / ht;
+                for (int m = 0; m < 3; m++) Dt[m] = (u[m] - n[m]) * iht;
             } else {
                 for (int m = 0; m < 3; m++) Dt[m] = 0.0;
             }
@@ -286,39 +287,40 @@ __global__ void __launch_bounds__(kThreads) k_force(Dims d, Geo G, Vel v, const 
             if (j < d.nt - 1) {
                 double n[3];
                 v.at(c + d.np, n);
-                for (int m = 0; m < 3; m++) Dt[m] = (n[m] - u[m]) / ht;
+                for (int m = 0; m < 3; m++) Dt[m] = (n[m] - u[m]) * iht;
             } else {
                 for (int m = 0; m < 3; m++) Dt[m] = 0.0;
             }
         }
-        const double hp = rc * G.sc[j] * G.dph;
+        const double ihp = 1.0 / (rc * G.sc[j] * G.dph);
         {
             double n[3];
             if (u[2] > 0.0) {
                 v.at(c - k + km1(d, k), n);
-                for (int m = 0; m < 3; m++) Dp[m] = (u[m] - n[m]) / hp;
+                for (int m = 0; m < 3; m++) Dp[m] = (u[m] - n[m]) * ihp;
             } else {
                 v.at(c - k + kp1(d, k), n);
-                for (int m = 0; m < 3; m++) Dp[m] = (n[m] - u[m]) / hp;
+                for (int m = 0; m < 3; m++) Dp[m] = (n[m] - u[m]) * ihp;
             }
         }
         double adv[3];
         for (int m = 0; m < 3; m++) adv[m] = u[0] * Dr[m] + u[1] * Dt[m] + u[2] * Dp[m];
         const double cot = G.cc[j] / G.sc[j];
-        adv[0] += -(u[1] * u[1] + u[2] * u[2]) / rc;
-        adv[1] += (u[0] * u[1] - u[2] * u[2] * cot) / rc;
-        adv[2] += (u[0] * u[2] + u[1] * u[2] * cot) / rc;
+        const double irc = 1.0 / rc;
+        adv[0] += -(u[1] * u[1] + u[2] * u[2]) * irc;
+        adv[1] += (u[0] * u[1] - u[2] * u[2] * cot) * irc;
+        adv[2] += (u[0] * u[2] + u[1] * u[2] * cot) * irc;
         double B[3], J[3];
         bcentre(d, br, bt, bp, i, j, k, B);
         jcentre(d, jr, jt, jp, i, j, k, J);
-        const double rho = G.rho[i];
+        const double irho = 1.0 / G.rho[i];
         const double jxb0 = J[1] * B[2] - J[2] * B[1];
         const double jxb1 = J[2] * B[0] - J[0] * B[2];
         const double jxb2 = J[0] * B[1] - J[1] * B[0];
         const double s = G.rhoV[ij] * dt;
-        double f0 = s * (-adv[0] + jxb0 / rho);
-        double f1 = s * (-adv[1] + jxb1 / rho);
-        double f2 = s * (-adv[2] + jxb2 / rho);
+        double f0 = s * (-adv[0] + jxb0 * irho);
+        double f1 = s * (-adv[1] + jxb1 * irho);
+        double f2 = s * (-adv[2] + jxb2 * irho);
         if (b_avg) {
             f0 = 0.5 * (b_avg[c] + f0);
             f1 = 0.5 * (b_avg[d.N + c] + f1);
