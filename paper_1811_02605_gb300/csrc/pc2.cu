@@ -20,7 +20,8 @@
 // forward step and as z_{np-1} in the first backward one, both known before the replays.
 //
 // FP64 solves use the line kernel in double; the mixed-precision inner solves use it in float
-// (vectors, factor and scans in FP32, compensated FP32 dot partials handed to FP64 per thread),
+// (vectors, factor and scans in FP32; each lane's dot partials over one line, at most 3 np / 32
+// products, are formed in FP32 and summed over lines in FP64),
 // with the FP64 outer residual of the reliable-update scheme followed by one preconditioner pass
 // that recomputes z and <r, z> for the replaced residual.
 #include <cmath>
@@ -68,27 +69,6 @@ __global__ void k_pc2_factor(Dims d, OpTab<double> t, double* __restrict__ idt, 
     }
 }
 
-// per-thread dot accumulator: FP64 for FP64 data, compensated FP32 (Neumaier) for FP32 data
-template <typename T>
-struct Dot;
-template <>
-struct Dot<double> {
-    double s = 0.0;
-    __device__ __forceinline__ void fma_add(double a, double b) { s = fma(a, b, s); }
-    __device__ __forceinline__ double get() const { return s; }
-};
-template <>
-struct Dot<float> {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void fma_add(float a, float b) {
-        const float x = a * b;
-        const float t = s + x;
-        c += (fabsf(s) >= fabsf(x)) ? ((s - t) + x) : ((x - t) + s);
-        s = t;
-    }
-    __device__ __forceinline__ double get() const { return (double)s + (double)c; }
-};
-
 // Shared memory per warp: 1/dt, w/dt and a work line, each np + ceil(np / S) elements (one pad
 // after each lane segment of S = ceil(np / 32) elements; element k sits at k + k / S).
 __host__ __device__ inline int padded_len(int np) {
@@ -103,8 +83,9 @@ __host__ __device__ inline int padded_len(int np) {
 //   kReliable: z~ = P~^-1 r~ for the replaced residual; last CTA: rho = <r~, z~>, and the
 //              recurrence continues (beta = rho / rho_prev) while rho stays within 4x of the
 //              recursive one, else restarts (beta = 0); the stop flags are the outer kernel's.
-// SEG > 0: the segment length S is a compile-time constant, so the segment loops unroll and their
-// shared-memory loads issue together; SEG = 0: any np.
+// SEG > 0: np = 32 SEG exactly, so the segment length is a compile-time constant: the segment
+// loops unroll (their shared-memory loads issue together) and the bounds tests vanish (the first
+// and last elements of the line are lane 0's first and lane 31's last). SEG = 0: any np.
 template <typename T, int NC, int MODE, int SEG>
 __global__ void __launch_bounds__(kThreads) k_pc2_line(Dims d, OpTab<T> t, const double* __restrict__ dgv,
                                                        const T* __restrict__ idt, T* __restrict__ x,
@@ -126,8 +107,12 @@ __global__ void __launch_bounds__(kThreads) k_pc2_line(Dims d, OpTab<T> t, const
     const T zero = T(0);
     const int k0 = lane * S;
     const int s0 = lane * (S + 1);         // element k0 + t of this lane's segment sits at s0 + t
-    Dot<T> a_rz;
-    double a_rr = 0.0;
+    constexpr bool exact = SEG > 0;
+    // element k0 + t is in the line / is its first / is its last element
+#define IN_LINE(tt) (exact || k0 + (tt) < np)
+#define FIRST(tt) ((tt) == 0 && lane == 0)
+#define LAST(tt) (exact ? ((tt) == S - 1 && lane == 31) : (k0 + (tt) == np - 1))
+    double a_rz = 0.0, a_rr = 0.0;   // per-line partials (in T) are added here in FP64
     const int nl = d.nr * d.nt;
     for (int line = blockIdx.x * warps + warp; line < nl; line += gridDim.x * warps) {
         const T w = t.ap[line];
@@ -142,11 +127,10 @@ __global__ void __launch_bounds__(kThreads) k_pc2_line(Dims d, OpTab<T> t, const
         T A = T(1), Cm = T(1);
 #pragma unroll
         for (int tt = 0; tt < S; tt++) {
-            const int k = k0 + tt;
-            if (k < np) {
+            if (IN_LINE(tt)) {
                 const T g = gb[s0 + tt];
-                A *= (k == 0) ? zero : g;
-                Cm *= (k == np - 1) ? zero : g;
+                A *= FIRST(tt) ? zero : g;
+                Cm *= LAST(tt) ? zero : g;
             }
         }
         T As[5], Cs[5];
@@ -159,7 +143,7 @@ __global__ void __launch_bounds__(kThreads) k_pc2_line(Dims d, OpTab<T> t, const
             if (lane >= o) A *= Ao;
             if (lane + o < 32) Cm *= Co;
         }
-        Dot<T> line_rr;
+        T line_rz = zero, line_rr = zero;
 #pragma unroll 1
         for (int c = 0; c < NC; c++) {
             const long long off = c * d.N + base;
@@ -179,13 +163,12 @@ __global__ void __launch_bounds__(kThreads) k_pc2_line(Dims d, OpTab<T> t, const
             T B = zero;
 #pragma unroll
             for (int tt = 0; tt < S; tt++) {
-                const int k = k0 + tt;
-                if (k < np) {
+                if (IN_LINE(tt)) {
                     const int sx = s0 + tt;
                     T bk = ub[sx] * ib[sx];
-                    if (k == np - 1) bk = fma(gb[sx], u0, bk);
+                    if (LAST(tt)) bk = fma(gb[sx], u0, bk);
                     ub[sx] = bk;
-                    B = fma((k == 0) ? zero : gb[sx], B, bk);
+                    B = fma(FIRST(tt) ? zero : gb[sx], B, bk);
                 }
             }
 #pragma unroll
@@ -198,10 +181,9 @@ __global__ void __launch_bounds__(kThreads) k_pc2_line(Dims d, OpTab<T> t, const
             if (lane == 0) u = zero;
 #pragma unroll
             for (int tt = 0; tt < S; tt++) {
-                const int k = k0 + tt;
-                if (k < np) {
+                if (IN_LINE(tt)) {
                     const int sx = s0 + tt;
-                    u = fma((k == 0) ? zero : gb[sx], u, ub[sx]);
+                    u = fma(FIRST(tt) ? zero : gb[sx], u, ub[sx]);
                     ub[sx] = u;
                 }
             }
@@ -212,13 +194,12 @@ __global__ void __launch_bounds__(kThreads) k_pc2_line(Dims d, OpTab<T> t, const
             T E = zero;
 #pragma unroll
             for (int tt = S - 1; tt >= 0; tt--) {
-                const int k = k0 + tt;
-                if (k < np) {
+                if (IN_LINE(tt)) {
                     const int sx = s0 + tt;
                     T e = ub[sx];
-                    if (k == 0) e = fma(gb[sx], zl, e);
+                    if (FIRST(tt)) e = fma(gb[sx], zl, e);
                     ub[sx] = e;
-                    E = fma((k == np - 1) ? zero : gb[sx], E, e);
+                    E = fma(LAST(tt) ? zero : gb[sx], E, e);
                 }
             }
 #pragma unroll
@@ -231,10 +212,9 @@ __global__ void __launch_bounds__(kThreads) k_pc2_line(Dims d, OpTab<T> t, const
             if (lane == 31) zz = zero;
 #pragma unroll
             for (int tt = S - 1; tt >= 0; tt--) {
-                const int k = k0 + tt;
-                if (k < np) {
+                if (IN_LINE(tt)) {
                     const int sx = s0 + tt;
-                    zz = fma((k == np - 1) ? zero : gb[sx], zz, ub[sx]);
+                    zz = fma(LAST(tt) ? zero : gb[sx], zz, ub[sx]);
                     ub[sx] = zz;
                 }
             }
@@ -244,14 +224,18 @@ __global__ void __launch_bounds__(kThreads) k_pc2_line(Dims d, OpTab<T> t, const
                 const T rv = r[off + k];
                 z[off + k] = zv;
                 if (MODE == kInit) p[off + k] = zv;
-                a_rz.fma_add(rv, zv);
-                line_rr.fma_add(rv, rv);
+                line_rz = fma(rv, zv, line_rz);
+                line_rr = fma(rv, rv, line_rr);
             }
             __syncwarp();
         }
-        a_rr = fma(dgv[line], line_rr.get(), a_rr);
+        a_rz += (double)line_rz;
+        a_rr = fma(dgv[line], (double)line_rr, a_rr);
     }
-    double val[2] = {a_rz.get(), a_rr}, out[2];
+#undef IN_LINE
+#undef FIRST
+#undef LAST
+    double val[2] = {a_rz, a_rr}, out[2];
     if (reduce_last<2>(val, partials, &sc->count, out) && threadIdx.x == 0) {
         const double rz = out[0], rr = out[1];
         if (MODE == kReliable) {
@@ -289,8 +273,8 @@ size_t line_smem(const Dims& d, int warps) {
     return (size_t)warps * 3 * padded_len(d.np) * sizeof(T);
 }
 
-// compile-time segment length for np in [481, 512] (16 elements per lane), else the generic kernel
-int seg_of(const Dims& d) { return ((d.np + 31) / 32 == 16) ? 16 : 0; }
+// compile-time segment length for np = 512 (16 elements per lane), else the generic kernel
+int seg_of(const Dims& d) { return (d.np == 512) ? 16 : 0; }
 
 template <typename T, int MODE, int SEG>
 cudaError_t set_smem(size_t bytes) {
