@@ -55,6 +55,8 @@ STS_BYTES_PER_CELL = 4 * 3 * 8
 # PC2 line kernel per cell: x, p, r, q read, x, r, z written (7 x 3 x 8 B) plus 1/dt (8 B, shared
 # by the three components)
 PC2_LINE_BYTES_PER_CELL = 7 * 3 * 8 + 8
+# resistivity of the explicit-against-implicit comparison (the workload itself has eta = 0)
+RES_ETA = 1e-3
 
 
 def peaks():
@@ -248,13 +250,15 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def run(precision, steps, warmup, profile, inner_tol=1e-5, restart=1, snapshot=None, sts=0, variant=0, pc=0):
+    def run(precision, steps, warmup, profile, inner_tol=1e-5, restart=1, snapshot=None, sts=0, variant=0, pc=0,
+            eta=None, res=0):
         ds = dev_state()
         torch.cuda.synchronize()
         f = P.make_fields(ds["br"], ds["bt"], ds["bp"], ds["vr"], ds["vt"], ds["vp"])
-        prm = P.make_params(nu=w["nu"], eta=w["eta"], cfl=w["cfl"], tol=w["tol"], precision=precision,
-                            inner_tol=inner_tol, max_outer=200, max_iter=20000, mixed_restart=restart,
-                            viscosity_sts=sts, pcg_variant=variant, preconditioner=pc)
+        prm = P.make_params(nu=w["nu"], eta=w["eta"] if eta is None else eta, cfl=w["cfl"], tol=w["tol"],
+                            precision=precision, inner_tol=inner_tol, max_outer=200, max_iter=20000,
+                            mixed_restart=restart, viscosity_sts=sts, pcg_variant=variant, preconditioner=pc,
+                            resistivity_implicit=res)
         for _ in range(warmup):
             st, info = P.mhd_step(g, prm, f)
             if st != P.MHD_OK:
@@ -424,6 +428,23 @@ def run_ours(args):
         if not args.no_mixed:
             pc2_mixed = pc2_entry(0, P.PREC_MIXED)
 
+    # ---- resistivity eta = RES_ETA: explicit (eta J in E) against the implicit face solve, PC2 solves
+    res_entry = None
+    if not args.no_res:
+        mse, infose, profe, clke, dse = run(P.PREC_FP64, args.steps, args.warmup, True, pc=1, eta=RES_ETA, res=0)
+        msi, infosi, profi, clki, dsi = run(P.PREC_FP64, args.steps, args.warmup, True, pc=1, eta=RES_ETA, res=1)
+        mse, msi = maxr(mse), maxr(msi)
+        n_res = max(sum(i["iters_res"] for i in infosi), 1)
+        res_entry = dict(eta=RES_ETA, cell_solves="FP64 PC2",
+                         ms_per_step_explicit_resistivity=round(mse, 3), ms_per_step_implicit_resistivity=round(msi, 3),
+                         resistive_iters_per_step=n_res / len(infosi),
+                         resistive_solve_ms_per_step=round(profi["res"][0] / len(infosi), 3),
+                         ms_per_resistive_iteration=round(profi["res"][0] / n_res, 4),
+                         max_resistive_relres=max(i["relres_res"] for i in infosi),
+                         rel_l2_implicit_vs_explicit_after_steps={k: float(torch.linalg.norm(dsi[k] - dse[k]) /
+                                                                          torch.linalg.norm(dse[k])) for k in dse},
+                         clocks=clki)
+
     sts = sts_mixed = None
     if not args.no_sts:
         sts = sts_entry(P.PREC_FP64)
@@ -475,7 +496,7 @@ def run_ours(args):
                     pcg_gbs=dict(fp64=round(pcg64_gbs, 1), fp64_frac_of_hbm=round(pcg64_gbs / hbm, 4),
                                  peak_gbs=hbm, peak_source=peak_src),
                     roofline=roof, mixed=mixed, mixed_reliable=mixed_reliable, sts=sts, sts_mixed_reliable=sts_mixed, pcg_single_reduction=pcg_cg,
-                    pc2=pc2, pc2_sts=pc2_sts, pc2_mixed_reliable=pc2_mixed,
+                    pc2=pc2, pc2_sts=pc2_sts, pc2_mixed_reliable=pc2_mixed, resistivity=res_entry,
                     e2e=e2e, cpu_baseline=cpu, clocks=clk64,
                     gpu_launches=int(launches), kernel_ms={k: round(v[0], 3) for k, v in prof64.items() if v[1]})
         print(json.dumps(line), flush=True)
@@ -749,6 +770,7 @@ def main():
     ap.add_argument("--no-sts", action="store_true", help="skip the RKL2-viscosity entries")
     ap.add_argument("--no-cg", action="store_true", help="skip the single-reduction PCG entry")
     ap.add_argument("--no-pc2", action="store_true", help="skip the PC2 entries")
+    ap.add_argument("--no-res", action="store_true", help="skip the resistivity entry")
     ap.add_argument("--pc2-only", action="store_true", help="--refinement-study: only the PC2 rows")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -105,7 +105,7 @@ enum { MHD_PREC_FP64 = 0, MHD_PREC_MIXED = 1 };
  *            curl_h J(x) from the solution x, which keeps div_h B to rounding. Uses tol and
  *            max_iter; FP64 (either precision setting). info->iters_res / relres_res report it.
  *            The first such step allocates its workspace (4 face vectors). mhd_adjoint_step
- *            rejects it (MHD_ERR_ARG).
+ *            differentiates it: the face solve's transpose is W M^-1 (one more face PCG solve).
  *  preconditioner  0 (default): PC1, point Jacobi (Sec. 2.2). 1: PC2, block Jacobi with a
  *            zero-fill incomplete LU factorisation (ILU(0)) in each block (Sec. 2.2); the blocks
  *            are the periodic phi lines (i, j) of each component, so the r and theta couplings

@@ -93,6 +93,8 @@ def _declare(L):
         L.og_adjoint_step.argtypes = [vp, d, d, d, d, d, d, i] + [_dp] * 12
         L.og_adjoint_step_sts.restype = i
         L.og_adjoint_step_sts.argtypes = [vp, d, d, d, d, d, d, i] + [_dp] * 12
+        L.og_adjoint_step_opts.restype = i
+        L.og_adjoint_step_opts.argtypes = [vp, i, d, d, d, d, d, d, i] + [_dp] * 12
         L.og_rkl2_stages.restype = i
         L.og_rkl2_stages.argtypes = [vp, d, d]
         L.og_rkl2.restype = i
@@ -311,17 +313,20 @@ class Grid:
         return (br, bt, bp), it.value, rr.value, st
 
 
-def _adjoint(self, state, lam, dt, asi, nu=1e-3, eta=0.0, cfl=0.4, tol=1e-13, max_iter=200000, sts=False):
+def _adjoint(self, state, lam, dt, asi, nu=1e-3, eta=0.0, cfl=0.4, tol=1e-13, max_iter=200000, sts=False,
+             res_implicit=False):
     """Cotangent of state n from the cotangent `lam` of state n+1 (dicts with br, bt, bp, vr, vt, vp).
-    sts=True: adjoint of step_sts (viscosity by RKL2) instead of step."""
+    sts / res_implicit: adjoint of the step with viscosity by RKL2 / resistivity by the implicit
+    face solve."""
     v = np.ascontiguousarray(np.stack([state["vr"], state["vt"], state["vp"]]), dtype=np.float64)
     lv1 = np.ascontiguousarray(np.stack([lam["vr"], lam["vt"], lam["vp"]]), dtype=np.float64)
     s = self.shapes
     lv = np.empty_like(v)
     lbr, lbt, lbp = np.empty(s["br"]), np.empty(s["bt"]), np.empty(s["bp"])
-    fn = self.L.og_adjoint_step_sts if sts else self.L.og_adjoint_step
-    st = fn(self.h, nu, eta, cfl, dt, asi, tol, max_iter, v, _c(state["br"]), _c(state["bt"]),
-            _c(state["bp"]), lv1, _c(lam["br"]), _c(lam["bt"]), _c(lam["bp"]), lv, lbr, lbt, lbp)
+    opts = (OPT_STS if sts else 0) | (OPT_RES_IMPLICIT if res_implicit else 0)
+    st = self.L.og_adjoint_step_opts(self.h, opts, nu, eta, cfl, dt, asi, tol, max_iter, v, _c(state["br"]),
+                                     _c(state["bt"]), _c(state["bp"]), lv1, _c(lam["br"]), _c(lam["bt"]),
+                                     _c(lam["bp"]), lv, lbr, lbt, lbp)
     out = dict(br=lbr, bt=lbt, bp=lbp, vr=lv[0].copy(), vt=lv[1].copy(), vp=lv[2].copy())
     return out, st
 

@@ -35,6 +35,7 @@ struct og_grid {
 #define KM(g, k) (((k) + (g)->np - 1) % (g)->np)
 
 static double rho0(const og_grid* g, double r) { return (g->r0 / r) * (g->r0 / r); }
+static void res_weights(const og_grid* g, double* w);
 
 /* ---------------------------------------------------------------------------------------------
  * Grid (reading R2: geometric radial stretch, uniform theta in [0,pi], periodic phi; exact
@@ -1119,7 +1120,7 @@ static void efield_T(const og_grid* g, const double* vb, const double* br, const
 }
 
 static int adjoint_step(const og_grid* g, double nu, double eta, double cfl, double dt, double asi_fixed,
-                        double tol, int max_iter, int sts, const double* v0, const double* br0, const double* bt0,
+                        double tol, int max_iter, int opts, const double* v0, const double* br0, const double* bt0,
                         const double* bp0, const double* lv1, const double* lbr1, const double* lbt1,
                         const double* lbp1, double* lv, double* lbr, double* lbt, double* lbp) {
     long long N = g->N, n3 = 3 * N;
@@ -1148,8 +1149,16 @@ static int adjoint_step(const og_grid* g, double nu, double eta, double cfl, dou
     if (s != OG_OK) status = s;
     for (long long q = 0; q < n3; q++) { vp[q] = v0[q] + dp[q]; vb[q] = 0.5 * (v0[q] + vp[q]); }
     memcpy(B1r, br0, sizeof(double) * nbr); memcpy(B1t, bt0, sizeof(double) * nbt); memcpy(B1p, bp0, sizeof(double) * nbp);
-    og_efield_edges(g, vb, br0, bt0, bp0, eta, e.jr, e.jt, e.jp);
+    const int res = (opts & OG_OPT_RES_IMPLICIT) != 0;
+    const double eta_e = res ? 0.0 : eta;   /* resistivity in E (explicit) or in the face solve */
+    og_efield_edges(g, vb, br0, bt0, bp0, eta_e, e.jr, e.jt, e.jp);
     og_ct(g, e.jr, e.jt, e.jp, dt, B1r, B1t, B1p);
+    if (res) {
+        int rit;
+        double rrr;
+        s = og_res_solve(g, dt * eta, B1r, B1t, B1p, tol, max_iter, &rit, &rrr);
+        if (s != OG_OK) status = s;
+    }
     /* ---- reverse */
     double* y = (double*)calloc(n3, sizeof(double));
     double* lb = (double*)calloc(n3, sizeof(double));
@@ -1162,7 +1171,7 @@ static int adjoint_step(const og_grid* g, double nu, double eta, double cfl, dou
     memset(lv, 0, sizeof(double) * n3);
     memset(lbr, 0, sizeof(double) * nbr); memset(lbt, 0, sizeof(double) * nbt); memset(lbp, 0, sizeof(double) * nbp);
     memcpy(lB1r, lbr1, sizeof(double) * nbr); memcpy(lB1t, lbt1, sizeof(double) * nbt); memcpy(lB1p, lbp1, sizeof(double) * nbp);
-    if (sts) {
+    if (opts & OG_OPT_STS) {
         /* 5. v' = P v** with P the RKL2 polynomial in dt L, L = -nu D^-1 K; K symmetric gives
          * P^T = D P D^-1, so lam_v** = D P (D^-1 lam_v') (the D factor is applied below) */
         for (int c = 0; c < 3; c++)
@@ -1190,13 +1199,35 @@ static int adjoint_step(const og_grid* g, double nu, double eta, double cfl, dou
     for (long long q = 0; q < n3; q++) { lb[q] *= 0.5; }            /* lam_b0 (partial) = lam_b1 = lam_bc/2 */
     /* b1 = F(vp, B1): lam_vp, lam_B1 */
     force_T(g, vp, B1r, B1t, B1p, dt, lb, lvp, lB1r, lB1t, lB1p);
-    /* 3. B1 = B - dt curl E(vb, B): lam_B += lam_B1; lam_E = -dt C^T lam_B1 */
+    if (res) {
+        /* 3b. B1 = R B*, R = M_res^-1 W for the exact face solve (W (x + dte curl_h J x) = W B*
+         * gives B* - dte curl_h J x = x), so lam_B* = W M_res^-1 lam_B1 (M_res symmetric) */
+        long long nf = og_res_size(g);
+        double* lb1 = (double*)malloc(sizeof(double) * nf);
+        double* yr = (double*)calloc(nf, sizeof(double));
+        double* wv = (double*)malloc(sizeof(double) * nf);
+        memcpy(lb1, lB1r, sizeof(double) * nbr);
+        memcpy(lb1 + nbr, lB1t, sizeof(double) * nbt);
+        memcpy(lb1 + nbr + nbt, lB1p, sizeof(double) * nbp);
+        int rit;
+        double rrr;
+        s = og_res_pcg(g, dt * eta, lb1, yr, tol, max_iter, 0, &rit, &rrr);
+        if (s != OG_OK) status = s;
+        res_weights(g, wv);
+        for (long long q = 0; q < nf; q++) yr[q] *= wv[q];
+        memcpy(lB1r, yr, sizeof(double) * nbr);
+        memcpy(lB1t, yr + nbr, sizeof(double) * nbt);
+        memcpy(lB1p, yr + nbr + nbt, sizeof(double) * nbp);
+        free(lb1); free(yr); free(wv);
+    }
+    /* 3. B* = B - dt curl E(vb, B) (B1 itself without the face solve): lam_B += lam_B*;
+     * lam_E = -dt C^T lam_B* */
     for (long long q = 0; q < nbr; q++) lbr[q] += lB1r[q];
     for (long long q = 0; q < nbt; q++) lbt[q] += lB1t[q];
     for (long long q = 0; q < nbp; q++) lbp[q] += lB1p[q];
     memset(e.jr, 0, sizeof(double) * ner); memset(e.jt, 0, sizeof(double) * net); memset(e.jp, 0, sizeof(double) * nep);
     ct_T(g, dt, lB1r, lB1t, lB1p, e.jr, e.jt, e.jp);
-    efield_T(g, vb, br0, bt0, bp0, eta, e.jr, e.jt, e.jp, lvb, lbr, lbt, lbp);
+    efield_T(g, vb, br0, bt0, bp0, eta_e, e.jr, e.jt, e.jp, lvb, lbr, lbt, lbp);
     /* vp = v + dp, vb = v + dp/2 */
     for (long long q = 0; q < n3; q++) {
         lv[q] += lvp[q] + lvb[q];
@@ -1307,8 +1338,18 @@ int og_adjoint_step_sts(const og_grid* g, double nu, double eta, double cfl, dou
                         double tol, int max_iter, const double* v0, const double* br0, const double* bt0,
                         const double* bp0, const double* lv1, const double* lbr1, const double* lbt1,
                         const double* lbp1, double* lv, double* lbr, double* lbt, double* lbp) {
-    return adjoint_step(g, nu, eta, cfl, dt, asi_fixed, tol, max_iter, 1, v0, br0, bt0, bp0, lv1, lbr1, lbt1, lbp1,
-                        lv, lbr, lbt, lbp);
+    return adjoint_step(g, nu, eta, cfl, dt, asi_fixed, tol, max_iter, OG_OPT_STS, v0, br0, bt0, bp0, lv1, lbr1,
+                        lbt1, lbp1, lv, lbr, lbt, lbp);
+}
+
+/* adjoint of og_step_opts with OG_OPT_STS and / or OG_OPT_RES_IMPLICIT (the other options do not
+ * change the map) */
+int og_adjoint_step_opts(const og_grid* g, int opts, double nu, double eta, double cfl, double dt, double asi_fixed,
+                         double tol, int max_iter, const double* v0, const double* br0, const double* bt0,
+                         const double* bp0, const double* lv1, const double* lbr1, const double* lbt1,
+                         const double* lbp1, double* lv, double* lbr, double* lbt, double* lbp) {
+    return adjoint_step(g, nu, eta, cfl, dt, asi_fixed, tol, max_iter, opts, v0, br0, bt0, bp0, lv1, lbr1, lbt1,
+                        lbp1, lv, lbr, lbt, lbp);
 }
 
 /* =============================================================================================

@@ -136,6 +136,13 @@ void og_ilu0_apply(const og_grid* g, double alpha, int blocks, const double* dt,
 int og_pcg_pc2(const og_grid* g, double alpha, int blocks, int ncomp, const double* b, double* x, double tol,
                int max_iter, int fixed_iters, int* iters, double* relres);
 
+
+/* adjoint of og_step_opts with OG_OPT_STS and / or OG_OPT_RES_IMPLICIT */
+int og_adjoint_step_opts(const og_grid* g, int opts, double nu, double eta, double cfl, double dt, double asi_fixed,
+                         double tol, int max_iter, const double* v0, const double* br0, const double* bt0,
+                         const double* bp0, const double* lv1, const double* lbr1, const double* lbt1,
+                         const double* lbp1, double* lv, double* lbr, double* lbt, double* lbp);
+
 #ifdef __cplusplus
 }
 #endif

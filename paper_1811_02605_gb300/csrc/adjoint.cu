@@ -553,9 +553,9 @@ extern "C" mhd_status_t mhd_adjoint_step(mhd_grid_t g, const mhd_params_t* p, co
     if (!g) return MHD_ERR_ARG;
     if (!p || !s0 || !a1 || !a0 || !(dt > 0.0)) return set_error(g, MHD_ERR_ARG, "mhd_adjoint_step: bad argument");
     if (p->precision != MHD_PREC_FP64 || !(p->tol > 0.0) || (p->viscosity_sts != 0 && p->viscosity_sts != 1) ||
-        (p->pcg_variant != 0 && p->pcg_variant != 1) || p->resistivity_implicit != 0 ||
+        (p->pcg_variant != 0 && p->pcg_variant != 1) || (p->resistivity_implicit != 0 && p->resistivity_implicit != 1) ||
         (p->preconditioner != 0 && p->preconditioner != 1) || (p->preconditioner == 1 && p->pcg_variant != 0))
-        return set_error(g, MHD_ERR_ARG, "mhd_adjoint_step: FP64 only, tol > 0, viscosity_sts and pcg_variant 0 or 1, explicit resistivity");
+        return set_error(g, MHD_ERR_ARG, "mhd_adjoint_step: FP64 only, tol > 0, option flags 0 or 1");
     const mhd_fields_t* fl[3] = {s0, a1, a0};
     for (const mhd_fields_t* f : fl)
         if (!f->br || !f->bt || !f->bp || !f->vr || !f->vt || !f->vp)
@@ -589,7 +589,8 @@ extern "C" mhd_status_t mhd_adjoint_step(mhd_grid_t g, const mhd_params_t* p, co
     const int be = grid_blocks(g, ne, 8);
     const long long nf = nbr + nbt + nbp;
     const int bf = grid_blocks(g, nf, 8);
-    const double eta = p->eta;
+    const bool res = (p->resistivity_implicit == 1);
+    const double eta = res ? 0.0 : p->eta;   // resistivity in E (explicit) or in the face solve
 
     // coefficients with dt frozen (alpha_SI frozen too if given)
     mhd_params_t pf = *p;
@@ -619,6 +620,11 @@ extern "C" mhd_status_t mhd_adjoint_step(mhd_grid_t g, const mhd_params_t* p, co
     cudaMemcpyAsync(w.b1t, s0->bt, sizeof(double) * nbt, cudaMemcpyDeviceToDevice, st);
     cudaMemcpyAsync(w.b1p, s0->bp, sizeof(double) * nbp, cudaMemcpyDeviceToDevice, st);
     induction(g, s0->vr, s0->vt, s0->vp, g->dlt, 0.5, eta, nullptr, dt, w.b1r, w.b1t, w.b1p);
+    if (res) {
+        stt = res_solve(g, &g->ss->dt, p->eta, w.b1r, w.b1t, w.b1p, p, nullptr, nullptr);
+        if (stt == MHD_ERR_CUDA || stt == MHD_ERR_OOM) return stt;
+        note(stt);
+    }
 
     // ---- reverse
     // stacked copy of lam_v' and zeroed accumulators
@@ -656,7 +662,14 @@ extern "C" mhd_status_t mhd_adjoint_step(mhd_grid_t g, const mhd_params_t* p, co
     k_jcentre_T<<<be, kThreads, 0, st>>>(d, w.ljc, g->er, g->et, g->ep);
     k_ring_edges<<<2 * d.nr, kThreads, 0, st>>>(d, g->er, g->ring);
     k_face_T<<<bf, kThreads, 0, st>>>(d, g->geo, w.lbc, g->er, g->et, g->ep, g->ring, 1, w.lb1r, w.lb1t, w.lb1p);
-    // 3. B^{n+1} = B - dt curl E(vbar, B): lam_B = lam_B^{n+1} (copy into the output), lam_E
+    if (res) {
+        // B^{n+1} = M_res^-1 W B* (the face solve): lam_B* = W M_res^-1 lam_B^{n+1}
+        stt = res_transpose(g, &g->ss->dt, p->eta, w.lb1r, w.lb1t, w.lb1p, p);
+        if (stt == MHD_ERR_CUDA || stt == MHD_ERR_OOM) return stt;
+        note(stt);
+    }
+    // 3. B* = B - dt curl E(vbar, B) (B^{n+1} itself without a face solve): lam_B = lam_B*
+    // (copy into the output), lam_E
     cudaMemcpyAsync(a0->br, w.lb1r, sizeof(double) * nbr, cudaMemcpyDeviceToDevice, st);
     cudaMemcpyAsync(a0->bt, w.lb1t, sizeof(double) * nbt, cudaMemcpyDeviceToDevice, st);
     cudaMemcpyAsync(a0->bp, w.lb1p, sizeof(double) * nbp, cudaMemcpyDeviceToDevice, st);

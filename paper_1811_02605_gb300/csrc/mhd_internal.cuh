@@ -175,6 +175,8 @@ void vstar_rhs(mhd_grid_s* g, double* vr, double* vt, double* vp, const double* 
 int sts_stages(const mhd_grid_s* g, double nu, double dt);
 mhd_status_t res_solve(mhd_grid_s* g, const double* dt_dev, double eta, double* br, double* bt, double* bp,
                        const mhd_params_t* p, int* iters, double* relres);
+mhd_status_t res_transpose(mhd_grid_s* g, const double* dt_dev, double eta, double* lr, double* lt, double* lp,
+                           const mhd_params_t* p);
 void res_free(mhd_grid_s* g);
 mhd_status_t pc2_factor(mhd_grid_s* g);
 void pc2_init64(mhd_grid_s* g, int nc);

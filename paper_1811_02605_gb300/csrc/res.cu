@@ -158,6 +158,48 @@ __global__ void __launch_bounds__(kThreads) k_res_init(Dims d, Geo G, ResTab T, 
     }
 }
 
+// general right-hand side from x0 = 0: x = 0, r = b, p = r / diag; rho, ||r||^2, ||b||^2
+__global__ void __launch_bounds__(kThreads) k_res_init_rhs(Dims d, ResTab T, const double* __restrict__ b,
+                                                           double* __restrict__ x, double* __restrict__ r,
+                                                           double* __restrict__ p, PcgScalars* sc,
+                                                           double* __restrict__ partials, long long nf) {
+    const double dte = sc->dte;
+    double a_rho = 0.0, a_rr = 0.0;
+    for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf; f += (long long)gridDim.x * blockDim.x) {
+        const Face F = face_of(d, f);
+        const double rv = b[f];
+        const double z = rv / fma(dte, T.dc[F.t], T.w[F.t]);
+        x[f] = 0.0;
+        r[f] = rv;
+        p[f] = z;
+        a_rho = fma(rv, z, a_rho);
+        a_rr = fma(rv, rv, a_rr);
+    }
+    double val[2] = {a_rho, a_rr}, out[2];
+    if (reduce_last<2>(val, partials, &sc->count, out) && threadIdx.x == 0) {
+        sc->rho = out[0];
+        sc->rr = out[1];
+        sc->bb = out[1];
+        sc->beta = 0.0;
+        if (!isfinite(out[0]) || !isfinite(out[1])) sc->done = 3;
+        else if (out[1] == 0.0) sc->done = 1;
+        else if (sc->max_iter <= 0) sc->done = 2;
+    }
+}
+
+// out (three face arrays) = W x
+__global__ void k_res_scale_w(Dims d, ResTab T, const double* __restrict__ x, double* __restrict__ br,
+                              double* __restrict__ bt, double* __restrict__ bp, long long nbr, long long nbt,
+                              long long nf) {
+    for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf; f += (long long)gridDim.x * blockDim.x) {
+        const Face F = face_of(d, f);
+        const double v = T.w[F.t] * x[f];
+        if (f < nbr) br[f] = v;
+        else if (f < nbr + nbt) bt[f - nbr] = v;
+        else bp[f - nbr - nbt] = v;
+    }
+}
+
 // q = W p + dte l* circ(J(p)), <p, q>; last CTA: alpha
 __global__ void __launch_bounds__(kThreads) k_res_apply(Dims d, Geo G, ResTab T, const double* __restrict__ p,
                                                         const double* __restrict__ er, const double* __restrict__ et,
@@ -379,6 +421,39 @@ void res_free(mhd_grid_s* g) {
     cudaFree(w->x);
     delete w;
     g->res_mem = nullptr;
+}
+
+// Transpose of the resistive map for the adjoint: with an exact solve the step's B = B* - dte
+// curl_h J(x) equals x = M^-1 W B*, so its transpose is W M^-1. In place on the three face arrays:
+// lam <- W y with M y = lam (PCG from y = 0, tolerance and cap from p).
+mhd_status_t res_transpose(mhd_grid_s* g, const double* dt_dev, double eta, double* lr, double* lt, double* lp,
+                           const mhd_params_t* p) {
+    ResWork* w = nullptr;
+    mhd_status_t st = res_workspace(g, &w);
+    if (st != MHD_OK) return st;
+    if ((st = res_graph(g, w)) != MHD_OK) return st;
+    const Dims d = g->d;
+    const ResSizes z = res_sizes(d);
+    const ResTab T{w->w, w->dc, w->ls};
+    const int blocks = grid_blocks(g, z.nf, 8);
+    cudaMemcpyAsync(w->q, lr, sizeof(double) * z.nbr, cudaMemcpyDeviceToDevice, g->stream);
+    cudaMemcpyAsync(w->q + z.nbr, lt, sizeof(double) * z.nbt, cudaMemcpyDeviceToDevice, g->stream);
+    cudaMemcpyAsync(w->q + z.nbr + z.nbt, lp, sizeof(double) * z.nbp, cudaMemcpyDeviceToDevice, g->stream);
+    k_res_setup<<<1, 1, 0, g->stream>>>(g->sc, p->tol, p->max_iter, dt_dev, eta);
+    k_res_init_rhs<<<blocks, kThreads, 0, g->stream>>>(d, T, w->q, w->x, w->r, w->p, g->sc, g->partials, z.nf);
+    if ((st = check_cuda(g, "res transpose init")) != MHD_OK) return st;
+    for (;;) {
+        if ((st = res_read(g)) != MHD_OK) return st;
+        if (g->h_sc->done) break;
+        if (cudaGraphLaunch(w->graph, g->stream) != cudaSuccess) return check_cuda(g, "res graph launch");
+        if (cudaGraphLaunch(w->graph, g->stream) != cudaSuccess) return check_cuda(g, "res graph launch");
+    }
+    const int done = g->h_sc->done;
+    k_res_scale_w<<<blocks, kThreads, 0, g->stream>>>(d, T, w->x, lr, lt, lp, z.nbr, z.nbt, z.nf);
+    if ((st = check_cuda(g, "res transpose scale")) != MHD_OK) return st;
+    if (done == 1) return MHD_OK;
+    if (done == 3) return set_error(g, MHD_ERR_NONFINITE, "resistive transpose: non-finite value");
+    return set_error(g, MHD_ERR_NOCONV, "resistive transpose: no convergence within max_iter");
 }
 
 // B (caller's face arrays, holding B*) <- B* - dte curl_h J(x), x the PCG solution; dte = dt eta

@@ -63,13 +63,34 @@ def test_implicit_resistivity_zero_eta_is_the_ideal_step():
         assert rel_l2(to_np(a[k]), to_np(b[k])) <= 1e-13, k
 
 
-def test_implicit_resistivity_rejected_by_adjoint_and_bad_flag():
+def test_implicit_resistivity_bad_flag_rejected():
     d = GRIDS[0]
     g = grid(d)
     st = dev_state(I.initial_state(d, 0, False))
-    out = {k: torch.empty_like(v) for k, v in st.items()}
-    with pytest.raises(P.MhdError):
-        P.mhd_adjoint_step(g, P.make_params(eta=1e-3, resistivity_implicit=1), fields(st), 0.01, fields(st),
-                           fields(out))
     with pytest.raises(P.MhdError):
         P.mhd_step(g, P.make_params(resistivity_implicit=2), fields(st))
+
+
+@pytest.mark.parametrize("d", [GRIDS[0], GRIDS[1]], ids=lambda d: f"{d.nr}x{d.nt}x{d.np}")
+def test_adjoint_with_implicit_resistivity_matches_oracle(d):
+    st = I.initial_state(d, 1, False)
+    for k in ("vr", "vt", "vp"):
+        st[k] = st[k] * 20.0
+    og = O.Grid.from_desc(d)
+    eta = 0.05
+    c = og.coeffs(np.stack([st["vr"], st["vt"], st["vp"]]), st["br"], st["bt"], st["bp"], nu=1e-3, cfl=0.3)
+    rng = np.random.default_rng(301)
+    lam = {k: rng.normal(size=st[k].shape) for k in KEYS}
+    lam["bt"][:, 0] = 0.0
+    lam["bt"][:, -1] = 0.0
+    ref, s1 = og.adjoint_step(st, lam, c["dt"], c["alpha_si"], eta=eta, cfl=0.3, tol=1e-13, res_implicit=True)
+    ds, dl = dev_state(st), dev_state(lam)
+    out = {k: torch.empty_like(v) for k, v in ds.items()}
+    prm = P.make_params(nu=1e-3, eta=eta, cfl=0.3, tol=1e-13, alpha_si_fixed=c["alpha_si"], max_iter=200000,
+                        resistivity_implicit=1)
+    s2 = P.mhd_adjoint_step(grid(d), prm, fields(ds), c["dt"], fields(dl), fields(out))
+    torch.cuda.synchronize()
+    assert s1 == O.OK and s2 == P.MHD_OK
+    for k in KEYS:
+        e = rel_l2(to_np(out[k]), ref[k])
+        assert e < 1e-9, (k, e)

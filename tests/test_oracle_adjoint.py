@@ -32,14 +32,14 @@ def _setup(seed=0, eta=0.0, scale_v=20.0, d=I.GridDesc(6, 6, 12, 1.0, 4.0, 1.1))
     return g, st, c, lam, rng
 
 
-def _fd_check(g, st, c, lam, rng, eta, ndir=4, sts=False, nu=1e-3):
+def _fd_check(g, st, c, lam, rng, eta, ndir=4, sts=False, nu=1e-3, res_implicit=False):
     dt, asi = c["dt"], c["alpha_si"]
-    adj, status = g.adjoint_step(st, lam, dt, asi, nu=nu, eta=eta, cfl=0.3, sts=sts)
+    adj, status = g.adjoint_step(st, lam, dt, asi, nu=nu, eta=eta, cfl=0.3, sts=sts, res_implicit=res_implicit)
     assert status == O.OK
-    fwd = g.step_sts if sts else g.step
 
     def L(x):
-        out, info = fwd(x, nu=nu, eta=eta, cfl=0.3, dt_fixed=dt, asi_fixed=asi, tol=1e-14, max_iter=200000)
+        out, info = g.step(x, nu=nu, eta=eta, cfl=0.3, dt_fixed=dt, asi_fixed=asi, tol=1e-14, max_iter=200000,
+                           sts=sts, res_implicit=res_implicit)
         assert info["status"] == O.OK
         return _dot(lam, out)
 
@@ -108,3 +108,11 @@ def test_rkl2_polynomial_is_self_adjoint_in_the_mass_inner_product():
     assert s >= 5
     a, b = float(np.sum(u * D * pv)), float(np.sum(pu * D * v))
     assert abs(a - b) <= 1e-12 * (abs(a) + abs(b))
+
+
+def test_adjoint_with_implicit_resistivity_matches_central_differences():
+    # the resistive face solve's transpose is W M_res^-1 (M_res symmetric); a large eta makes the
+    # solve far from the identity
+    g, st, c, lam, rng = _setup(4)
+    errs = _fd_check(g, st, c, lam, rng, 0.05, ndir=3, res_implicit=True)
+    assert max(errs) < 1e-6, errs
