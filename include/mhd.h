@@ -147,7 +147,8 @@ typedef struct {
 /* Create a grid on the CUDA stream `cuda_stream` (a cudaStream_t; NULL = legacy default
  * stream) of the current device. Builds the metric tables (exact finite-volume geometry of
  * spherical cells) and allocates all workspace for one 3-component solve in either precision.
- * Errors: MHD_ERR_ARG (sizes, r1 <= r0, stretch <= 0, np odd), MHD_ERR_OOM, MHD_ERR_CUDA. */
+ * Errors: MHD_ERR_ARG (sizes, r1 <= r0, stretch <= 0, np odd, 3 (nr+1)(nt+1) np >= 2^31),
+ * MHD_ERR_OOM, MHD_ERR_CUDA. */
 mhd_status_t mhd_grid_create(const mhd_grid_desc_t* desc, void* cuda_stream, mhd_grid_t* out);
 
 /* Free the grid's tables and workspace (synchronises its stream). NULL is accepted. */

@@ -113,8 +113,9 @@ __global__ void __launch_bounds__(kThreads) k_adjF_cell(Dims d, Geo G, VelA v, c
     const long long N = d.N;
     const long long plane = (long long)d.nt * d.np;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(c % d.np);
-        const long long ij = c / d.np;
+        int k;
+        unsigned int ij;
+        split_np(d, c, k, ij);
         const int j = (int)(ij % d.nt), i = (int)(ij / d.nt);
         const double s = G.rhoV[ij] * dt;
         const double rho = G.rho[i];
@@ -233,8 +234,9 @@ __global__ void __launch_bounds__(kThreads) k_adjE_cell(Dims d, VelA v, const do
                                                         double* __restrict__ ljc) {
     const long long N = d.N;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(c % d.np);
-        const long long ij = c / d.np;
+        int k;
+        unsigned int ij;
+        split_np(d, c, k, ij);
         const int j = (int)(ij % d.nt), i = (int)(ij / d.nt);
         double B[3], u[3];
         bcen(d, br, bt, bp, i, j, k, B);
@@ -283,8 +285,9 @@ __global__ void __launch_bounds__(kThreads) k_jcentre_T(Dims d, const double* __
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n_r + n_t + n_p;
          e += (long long)gridDim.x * blockDim.x) {
         if (e < n_r) {
-            const int k = (int)(e % d.np);
-            const long long q = e / d.np;
+            int k;
+            unsigned int q;
+            split_np(d, e, k, q);
             const int j = (int)(q % (d.nt + 1)), i = (int)(q / (d.nt + 1));
             const int km = km1(d, k);
             double s = 0.0;
@@ -293,8 +296,9 @@ __global__ void __launch_bounds__(kThreads) k_jcentre_T(Dims d, const double* __
             ljr[e] = 0.25 * s;
         } else if (e < n_r + n_t) {
             const long long f = e - n_r;
-            const int k = (int)(f % d.np);
-            const long long q = f / d.np;
+            int k;
+            unsigned int q;
+            split_np(d, f, k, q);
             const int j = (int)(q % d.nt), i = (int)(q / d.nt);
             const int km = km1(d, k);
             double s = 0.0;
@@ -303,8 +307,9 @@ __global__ void __launch_bounds__(kThreads) k_jcentre_T(Dims d, const double* __
             ljt[f] = 0.25 * s;
         } else {
             const long long f = e - n_r - n_t;
-            const int k = (int)(f % d.np);
-            const long long q = f / d.np;
+            int k;
+            unsigned int q;
+            split_np(d, f, k, q);
             const int j = (int)(q % (d.nt + 1)), i = (int)(q / (d.nt + 1));
             double s = 0.0;
             if (j >= 1 && j <= d.nt - 1) {
@@ -354,8 +359,9 @@ __global__ void __launch_bounds__(kThreads) k_face_T(Dims d, Geo G, const double
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n_r + n_t + n_p;
          e += (long long)gridDim.x * blockDim.x) {
         if (e < n_r) {
-            const int k = (int)(e % d.np);
-            const long long q = e / d.np;
+            int k;
+            unsigned int q;
+            split_np(d, e, k, q);
             const int j = (int)(q % nt), i = (int)(q / nt);
             double s = 0.0;
             if (i >= 1) s += 0.5 * lbc[ix(d, i - 1, j, k)];
@@ -369,8 +375,9 @@ __global__ void __launch_bounds__(kThreads) k_face_T(Dims d, Geo G, const double
             lbr[e] += s;
         } else if (e < n_r + n_t) {
             const long long f = e - n_r;
-            const int k = (int)(f % d.np);
-            const long long q = f / d.np;
+            int k;
+            unsigned int q;
+            split_np(d, f, k, q);
             const int j = (int)(q % (nt + 1)), i = (int)(q / (nt + 1));
             double s = 0.0;
             for (int jc = j - 1; jc <= j; jc++) {
@@ -392,8 +399,9 @@ __global__ void __launch_bounds__(kThreads) k_face_T(Dims d, Geo G, const double
             lbt[f] += s;
         } else {
             const long long f = e - n_r - n_t;
-            const int k = (int)(f % d.np);
-            const long long q = f / d.np;
+            int k;
+            unsigned int q;
+            split_np(d, f, k, q);
             const int j = (int)(q % nt), i = (int)(q / nt);
             double s = 0.5 * (lbc[2 * N + ix(d, i, j, k)] + lbc[2 * N + ix(d, i, j, km1(d, k))]);
             if (has_j) {
@@ -438,8 +446,9 @@ __global__ void __launch_bounds__(kThreads) k_ct_T(Dims d, Geo G, double dt, con
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n_r + n_t + n_p;
          e += (long long)gridDim.x * blockDim.x) {
         if (e < n_r) {
-            const int k = (int)(e % d.np);
-            const long long q = e / d.np;
+            int k;
+            unsigned int q;
+            split_np(d, e, k, q);
             const int j = (int)(q % (nt + 1)), i = (int)(q / (nt + 1));
             const double lr = G.r[i + 1] - G.r[i];
             double s = 0.0;
@@ -449,8 +458,9 @@ __global__ void __launch_bounds__(kThreads) k_ct_T(Dims d, Geo G, double dt, con
             ler[e] = s;
         } else if (e < n_r + n_t) {
             const long long f = e - n_r;
-            const int k = (int)(f % d.np);
-            const long long q = f / d.np;
+            int k;
+            unsigned int q;
+            split_np(d, f, k, q);
             const int j = (int)(q % nt), i = (int)(q / nt);
             const double lt = G.r[i] * G.dth;
             double s = lt * (wbr(i, j, k) - wbr(i, j, km1(d, k)));
@@ -459,8 +469,9 @@ __global__ void __launch_bounds__(kThreads) k_ct_T(Dims d, Geo G, double dt, con
             let[f] = s;
         } else {
             const long long f = e - n_r - n_t;
-            const int k = (int)(f % d.np);
-            const long long q = f / d.np;
+            int k;
+            unsigned int q;
+            split_np(d, f, k, q);
             const int j = (int)(q % (nt + 1)), i = (int)(q / (nt + 1));
             const double lp = G.r[i] * G.sn[j] * G.dph;
             double s = 0.0;
@@ -482,8 +493,9 @@ __global__ void __launch_bounds__(kThreads) k_eedges_T(Dims d, const double* __r
     const long long N = d.N;
     const int nr = d.nr, nt = d.nt;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(c % d.np);
-        const long long ij = c / d.np;
+        int k;
+        unsigned int ij;
+        split_np(d, c, k, ij);
         const int j = (int)(ij % nt), i = (int)(ij / nt);
         const int kp = kp1(d, k);
         double sr = 0.0;

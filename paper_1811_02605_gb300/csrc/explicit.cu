@@ -63,8 +63,9 @@ __global__ void __launch_bounds__(kThreads) k_coeffs(Dims d, Geo G, Vel v, const
     double mkv = 0.0, mka = 0.0;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < d.N;
          c += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(c % d.np);
-        const long long ij = c / d.np;
+        int k;
+        unsigned int ij;
+        split_np(d, c, k, ij);
         const int j = (int)(ij % d.nt), i = (int)(ij / d.nt);
         double u[3], B[3];
         v.at(c, u);
@@ -142,8 +143,9 @@ __global__ void __launch_bounds__(kThreads) k_jr(Dims d, Geo G, const double* __
                                                  double* __restrict__ jr) {
     const long long n = (long long)d.nr * (d.nt + 1) * d.np;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(e % d.np);
-        const long long q = e / d.np;
+        int k;
+        unsigned int q;
+        split_np(d, e, k, q);
         const int j = (int)(q % (d.nt + 1)), i = (int)(q / (d.nt + 1));
         const double rc = G.rc[i];
         double val;
@@ -169,8 +171,9 @@ __global__ void __launch_bounds__(kThreads) k_jt(Dims d, Geo G, const double* __
                                                  int walls_zero) {
     const long long n = (long long)(d.nr + 1) * d.nt * d.np;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(e % d.np);
-        const long long q = e / d.np;
+        int k;
+        unsigned int q;
+        split_np(d, e, k, q);
         const int j = (int)(q % d.nt), i = (int)(q / d.nt);
         if (walls_zero && (i == 0 || i == d.nr)) {
             jt[e] = 0.0;
@@ -191,8 +194,9 @@ __global__ void __launch_bounds__(kThreads) k_jp(Dims d, Geo G, const double* __
                                                  int walls_zero) {
     const long long n = (long long)(d.nr + 1) * (d.nt + 1) * d.np;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(e % d.np);
-        const long long q = e / d.np;
+        int k;
+        unsigned int q;
+        split_np(d, e, k, q);
         const int j = (int)(q % (d.nt + 1)), i = (int)(q / (d.nt + 1));
         if (j == 0 || j == d.nt || (walls_zero && (i == 0 || i == d.nr))) {
             jp[e] = 0.0;
@@ -245,8 +249,9 @@ __global__ void __launch_bounds__(kThreads) k_force(Dims d, Geo G, Vel v, const 
     const double dt = dt_dev ? *dt_dev : dt_host;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < d.N;
          c += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(c % d.np);
-        const long long ij = c / d.np;
+        int k;
+        unsigned int ij;
+        split_np(d, c, k, ij);
         const int j = (int)(ij % d.nt), i = (int)(ij / d.nt);
         double u[3];
         v.at(c, u);
@@ -352,8 +357,9 @@ __global__ void __launch_bounds__(kThreads) k_ecentre(Dims d, Vel v, const doubl
                                                       double* __restrict__ ec) {
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < d.N;
          c += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(c % d.np);
-        const long long ij = c / d.np;
+        int k;
+        unsigned int ij;
+        split_np(d, c, k, ij);
         const int j = (int)(ij % d.nt), i = (int)(ij / d.nt);
         double u[3], B[3];
         v.at(c, u);
@@ -386,8 +392,9 @@ __global__ void __launch_bounds__(kThreads) k_eedges(Dims d, const double* __res
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n_r + n_t + n_p;
          e += (long long)gridDim.x * blockDim.x) {
         if (e < n_r) {
-            const int k = (int)(e % d.np);
-            const long long q = e / d.np;
+            int k;
+            unsigned int q;
+            split_np(d, e, k, q);
             const int j = (int)(q % (d.nt + 1)), i = (int)(q / (d.nt + 1));
             double val;
             if (j == 0) val = ring[i] / d.np;
@@ -399,8 +406,9 @@ __global__ void __launch_bounds__(kThreads) k_eedges(Dims d, const double* __res
             er[e] = val;
         } else if (e < n_r + n_t) {
             const long long f = e - n_r;
-            const int k = (int)(f % d.np);
-            const long long q = f / d.np;
+            int k;
+            unsigned int q;
+            split_np(d, f, k, q);
             const int j = (int)(q % d.nt), i = (int)(q / d.nt);
             const int km = km1(d, k);
             double val;
@@ -411,8 +419,9 @@ __global__ void __launch_bounds__(kThreads) k_eedges(Dims d, const double* __res
             et[f] = val;
         } else {
             const long long f = e - n_r - n_t;
-            const int k = (int)(f % d.np);
-            const long long q = f / d.np;
+            int k;
+            unsigned int q;
+            split_np(d, f, k, q);
             const int j = (int)(q % (d.nt + 1)), i = (int)(q / (d.nt + 1));
             double val;
             if (j == 0 || j == d.nt || i == 0) val = 0.0;
@@ -437,8 +446,9 @@ __global__ void __launch_bounds__(kThreads) k_ct(Dims d, Geo G, const double* __
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n_r + n_t + n_p;
          e += (long long)gridDim.x * blockDim.x) {
         if (e < n_r) {
-            const int k = (int)(e % d.np);
-            const long long q = e / d.np;
+            int k;
+            unsigned int q;
+            split_np(d, e, k, q);
             const int j = (int)(q % d.nt), i = (int)(q / d.nt);
             const double ri = G.r[i];
             const double lt = ri * G.dth;
@@ -449,8 +459,9 @@ __global__ void __launch_bounds__(kThreads) k_ct(Dims d, Geo G, const double* __
             br[e] -= dt * c / area;
         } else if (e < n_r + n_t) {
             const long long f = e - n_r;
-            const int k = (int)(f % d.np);
-            const long long q = f / d.np;
+            int k;
+            unsigned int q;
+            split_np(d, f, k, q);
             const int j = (int)(q % (d.nt + 1)), i = (int)(q / (d.nt + 1));
             if (j == 0 || j == d.nt) continue;
             const double ri = G.r[i], ro = G.r[i + 1];
@@ -462,8 +473,9 @@ __global__ void __launch_bounds__(kThreads) k_ct(Dims d, Geo G, const double* __
             bt[f] -= dt * c / area;
         } else {
             const long long f = e - n_r - n_t;
-            const int k = (int)(f % d.np);
-            const long long q = f / d.np;
+            int k;
+            unsigned int q;
+            split_np(d, f, k, q);
             const int j = (int)(q % d.nt), i = (int)(q / d.nt);
             const double ri = G.r[i], ro = G.r[i + 1];
             const double lr = ro - ri;
@@ -504,7 +516,7 @@ __global__ void k_vstar(Dims d, Geo G, double* __restrict__ vr, double* __restri
                         const double* __restrict__ dlt, double* __restrict__ b) {
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < d.N;
          c += (long long)gridDim.x * blockDim.x) {
-        const double w = G.rhoV[c / d.np];
+        const double w = G.rhoV[(unsigned int)c / (unsigned int)d.np];
         const double a = vr[c] + dlt[c], e = vt[c] + dlt[d.N + c], f = vp[c] + dlt[2 * d.N + c];
         vr[c] = a;
         vt[c] = e;

@@ -182,7 +182,9 @@ extern "C" mhd_status_t mhd_grid_create(const mhd_grid_desc_t* desc, void* cuda_
     if (!(d.r0 > 0) || !(d.r1 > d.r0) || !(d.stretch > 0))
         return set_error(nullptr, MHD_ERR_ARG, "mhd_grid_create: need 0 < r0 < r1, stretch > 0");
     const long long N = (long long)d.nr * d.nt * d.np;
-    if (N > (1LL << 30)) return set_error(nullptr, MHD_ERR_ARG, "mhd_grid_create: grid too large");
+    // every flat index the kernels split (three face or edge families together) stays below 2^31
+    if (N > (1LL << 30) || 3LL * (d.nr + 1) * (d.nt + 1) * d.np >= (1LL << 31))
+        return set_error(nullptr, MHD_ERR_ARG, "mhd_grid_create: grid too large");
 
     mhd_grid_s* g = new mhd_grid_s();
     g->d.nr = d.nr;

@@ -61,6 +61,13 @@ __device__ __forceinline__ long long ixt(const Dims& d, int i, int j, int k) {
 }
 __device__ __forceinline__ int kp1(const Dims& d, int k) { return (k + 1 == d.np) ? 0 : k + 1; }
 __device__ __forceinline__ int km1(const Dims& d, int k) { return (k == 0) ? d.np - 1 : k - 1; }
+// (phi index, row) of a flat index of an array made of rows of np elements; every array of a grid
+// has fewer than 2^31 elements (checked at grid creation), so 32-bit division suffices
+__device__ __forceinline__ void split_np(const Dims& d, long long e, int& k, unsigned int& row) {
+    const unsigned int u = (unsigned int)e;
+    row = u / (unsigned int)d.np;
+    k = (int)(u - row * (unsigned int)d.np);
+}
 
 // Per-grid FP64 metric tables (device). Built on the host from the grid definition.
 struct Geo {

@@ -49,42 +49,42 @@ struct ResTab {
     const double *w, *dc, *ls;
 };
 
-// flat face index -> (family, table index, i, j, k)
+// flat face index -> (family, table index, i, j, k). The stacked face vector is a sequence of
+// rows of np faces (r-face rows, then theta-face rows, then phi-face rows) in the same order as the
+// per-(i, j) tables, so the table index is f / np; 32-bit arithmetic (nf < 2^31 is checked on
+// the host).
 struct Face {
     int fam, i, j, k;
     int t;
 };
 __device__ __forceinline__ Face face_of(const Dims& d, long long f) {
     Face o;
-    const long long nbr = (long long)(d.nr + 1) * d.nt * d.np;
-    const long long nbt = (long long)d.nr * (d.nt + 1) * d.np;
-    long long q;
-    if (f < nbr) {
+    const unsigned int uf = (unsigned int)f;
+    const unsigned int row = uf / (unsigned int)d.np;
+    o.k = (int)(uf - row * (unsigned int)d.np);
+    o.t = (int)row;
+    const unsigned int tr = (unsigned int)((d.nr + 1) * d.nt), tt = (unsigned int)(d.nr * (d.nt + 1));
+    if (row < tr) {
         o.fam = 0;
-        q = f;
-        o.k = (int)(q % d.np);
-        q /= d.np;
-        o.j = (int)(q % d.nt);
-        o.i = (int)(q / d.nt);
-        o.t = (int)q;
-    } else if (f < nbr + nbt) {
+        o.i = (int)(row / (unsigned int)d.nt);
+        o.j = (int)(row - (unsigned int)o.i * d.nt);
+    } else if (row < tr + tt) {
         o.fam = 1;
-        q = f - nbr;
-        o.k = (int)(q % d.np);
-        q /= d.np;
-        o.j = (int)(q % (d.nt + 1));
-        o.i = (int)(q / (d.nt + 1));
-        o.t = (d.nr + 1) * d.nt + (int)q;
+        const unsigned int q = row - tr;
+        o.i = (int)(q / (unsigned int)(d.nt + 1));
+        o.j = (int)(q - (unsigned int)o.i * (d.nt + 1));
     } else {
         o.fam = 2;
-        q = f - nbr - nbt;
-        o.k = (int)(q % d.np);
-        q /= d.np;
-        o.j = (int)(q % d.nt);
-        o.i = (int)(q / d.nt);
-        o.t = (d.nr + 1) * d.nt + d.nr * (d.nt + 1) + (int)q;
+        const unsigned int q = row - tr - tt;
+        o.i = (int)(q / (unsigned int)d.nt);
+        o.j = (int)(q - (unsigned int)o.i * d.nt);
     }
     return o;
+}
+
+// table index alone
+__device__ __forceinline__ int face_row(const Dims& d, long long f) {
+    return (int)((unsigned int)f / (unsigned int)d.np);
 }
 
 // circulation of the edge current around face f (the CT circulation of og_ct's sign convention;
@@ -166,9 +166,9 @@ __global__ void __launch_bounds__(kThreads) k_res_init_rhs(Dims d, ResTab T, con
     const double dte = sc->dte;
     double a_rho = 0.0, a_rr = 0.0;
     for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf; f += (long long)gridDim.x * blockDim.x) {
-        const Face F = face_of(d, f);
+        const int t = face_row(d, f);
         const double rv = b[f];
-        const double z = rv / fma(dte, T.dc[F.t], T.w[F.t]);
+        const double z = rv / fma(dte, T.dc[t], T.w[t]);
         x[f] = 0.0;
         r[f] = rv;
         p[f] = z;
@@ -192,8 +192,7 @@ __global__ void k_res_scale_w(Dims d, ResTab T, const double* __restrict__ x, do
                               double* __restrict__ bt, double* __restrict__ bp, long long nbr, long long nbt,
                               long long nf) {
     for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf; f += (long long)gridDim.x * blockDim.x) {
-        const Face F = face_of(d, f);
-        const double v = T.w[F.t] * x[f];
+        const double v = T.w[face_row(d, f)] * x[f];
         if (f < nbr) br[f] = v;
         else if (f < nbr + nbt) bt[f - nbr] = v;
         else bp[f - nbr - nbt] = v;
@@ -234,11 +233,11 @@ __global__ void __launch_bounds__(kThreads) k_res_update(Dims d, ResTab T, doubl
     const double al = sc->alpha, dte = sc->dte;
     double a_rho = 0.0, a_rr = 0.0;
     for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf; f += (long long)gridDim.x * blockDim.x) {
-        const Face F = face_of(d, f);
+        const int t = face_row(d, f);
         x[f] = fma(al, p[f], x[f]);
         const double rv = fma(-al, q[f], r[f]);
         r[f] = rv;
-        const double dg = fma(dte, T.dc[F.t], T.w[F.t]);
+        const double dg = fma(dte, T.dc[t], T.w[t]);
         a_rho = fma(rv, rv / dg, a_rho);
         a_rr = fma(rv, rv, a_rr);
     }
@@ -262,8 +261,8 @@ __global__ void __launch_bounds__(kThreads) k_res_pupdate(Dims d, ResTab T, cons
     if (sc->done) return;
     const double be = sc->beta, dte = sc->dte;
     for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf; f += (long long)gridDim.x * blockDim.x) {
-        const Face F = face_of(d, f);
-        const double dg = fma(dte, T.dc[F.t], T.w[F.t]);
+        const int t = face_row(d, f);
+        const double dg = fma(dte, T.dc[t], T.w[t]);
         p[f] = fma(be, p[f], r[f] / dg);
     }
 }
@@ -350,6 +349,7 @@ mhd_status_t res_workspace(mhd_grid_s* g, ResWork** out) {
         return MHD_OK;
     }
     const ResSizes z = res_sizes(g->d);
+    if (z.nf >= (1LL << 31)) return set_error(g, MHD_ERR_ARG, "implicit resistivity: grid too large (2^31 faces)");
     auto* w = new ResWork{};
     const size_t nt_tab = (size_t)z.tr + z.tt + z.tp;
     double* m = nullptr;
