@@ -463,22 +463,35 @@ def run_ours(args):
         ke = max(1, min(args.steps, 2))
         h2d = sum(t.numel() * 8 for t in snap.values())
         barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev = lambda: torch.cuda.Event(enable_timing=True)
+        e0, e1 = ev(), ev()
+        parts = {"h2d_ms": 0.0, "step_ms": 0.0, "d2h_ms": 0.0}
         e0.record(stream)
         for _ in range(ke):
+            a, b_, c_, d_ = ev(), ev(), ev(), ev()
+            a.record(stream)
             with torch.cuda.stream(stream):
                 for k in ds:
                     ds[k].copy_(snap[k], non_blocking=True)
-            P.mhd_step(g, prm, f)
+            b_.record(stream)
+            st_e, info_e = P.mhd_step(g, prm, f)
+            c_.record(stream)
             with torch.cuda.stream(stream):
                 for k in ds:
                     out[k].copy_(ds[k], non_blocking=True)
+            d_.record(stream)
             stream.synchronize()
+            parts["h2d_ms"] += a.elapsed_time(b_) / ke
+            parts["step_ms"] += b_.elapsed_time(c_) / ke
+            parts["d2h_ms"] += c_.elapsed_time(d_) / ke
         e1.record(stream)
         barrier()
         e2e = dict(value=round(maxr(e0.elapsed_time(e1) / ke), 3), unit="ms/step", h2d_bytes_per_step=h2d,
-                   d2h_bytes_per_step=h2d,
-                   note="each step starts from the state at the start of the timed region (host copy)")
+                   d2h_bytes_per_step=h2d, **{k: round(v, 3) for k, v in parts.items()},
+                   pcg_iters_per_step=sum(info_e["iters"]),
+                   note="each step starts from the state at the start of the timed region (host copy); "
+                        "step_ms is that step alone, so it differs from the timed steps' mean by the "
+                        "iteration count of that one step")
     # ---- CPU baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

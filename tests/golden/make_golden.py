@@ -5,7 +5,8 @@ coefficients, the PCG iteration counts and residuals, per-field L2 norms and the
 at seeded sample positions. It serves the full-size GPU parity test (sampled outputs) and gives
 the CPU baseline the oracle's own iteration counts at this size.
 
-    python tests/golden/make_golden.py fluxrope_256x256x512
+    python tests/golden/make_golden.py fluxrope_256x256x512          # PC1 (point Jacobi)
+    python tests/golden/make_golden.py fluxrope_256x256x512 --pc2    # PC2 (phi-line ILU(0))
 """
 import json
 import os
@@ -29,15 +30,15 @@ def sample_index(shape, seed):
     return np.sort(rng.choice(n, size=min(NSAMPLE, n), replace=False))
 
 
-def main(name):
+def main(name, pc2=False):
     w, st = I.workload(name)
     d = w["desc"]
     g = O.Grid.from_desc(d)
     t0 = time.time()
-    out, info = g.step(st, nu=w["nu"], eta=w["eta"], cfl=w["cfl"], tol=w["tol"])
+    out, info = g.step(st, nu=w["nu"], eta=w["eta"], cfl=w["cfl"], tol=w["tol"], pc2=pc2)
     wall = time.time() - t0
     rec = dict(workload=name, desc=dict(nr=d.nr, nt=d.nt, np=d.np, r0=d.r0, r1=d.r1, stretch=d.stretch),
-               params=dict(nu=w["nu"], eta=w["eta"], cfl=w["cfl"], tol=w["tol"]),
+               params=dict(nu=w["nu"], eta=w["eta"], cfl=w["cfl"], tol=w["tol"], preconditioner=1 if pc2 else 0),
                info={k: (v if not isinstance(v, np.floating) else float(v)) for k, v in info.items()},
                oracle_step_seconds=wall, fields={})
     rec["info"] = {k: ([float(x) for x in v] if isinstance(v, list) else float(v)) for k, v in info.items()}
@@ -46,11 +47,13 @@ def main(name):
         rec["fields"][k] = dict(shape=list(a.shape), l2=float(np.linalg.norm(a)),
                                 l2_initial=float(np.linalg.norm(st[k])),
                                 sample_index=idx.tolist(), sample=a.ravel()[idx].tolist())
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"{name}_oracle_step1.json")
+    tag = "_pc2" if pc2 else ""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"{name}_oracle{tag}_step1.json")
     with open(path, "w") as f:
         json.dump(rec, f)
     print(path, rec["info"], wall)
 
 
 if __name__ == "__main__":
-    main(sys.argv[1] if len(sys.argv) > 1 else "fluxrope_256x256x512")
+    args = [a for a in sys.argv[1:] if not a.startswith("--")]
+    main(args[0] if args else "fluxrope_256x256x512", pc2="--pc2" in sys.argv)
