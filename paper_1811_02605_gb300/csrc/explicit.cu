@@ -502,6 +502,10 @@ void induction(mhd_grid_s* g, const double* vr, const double* vt, const double* 
                                                            bp);
 }
 
+void ring_sums(mhd_grid_s* g, const double* a, cudaStream_t st) {
+    k_ring<<<2 * g->d.nr, kThreads, 0, st ? st : g->stream>>>(g->d, a, g->ring);
+}
+
 void ct_apply(mhd_grid_s* g, const double* dt_dev, double* br, double* bt, double* bp) {
     const Dims d = g->d;
     const long long ne = (long long)d.nr * (d.nt + 1) * d.np + (long long)(d.nr + 1) * d.nt * d.np +

@@ -170,6 +170,8 @@ mhd_status_t coeffs(mhd_grid_s* g, const mhd_params_t* p, const double* vr, cons
                     const double* vp, const double* br, const double* bt, const double* bp);
 void current_edges(mhd_grid_s* g, const double* br, const double* bt, const double* bp, bool walls_zero = false,
                    cudaStream_t st = nullptr);
+// polar ring sums of a cell-centred array into the grid's ring buffer (north rows, then south)
+void ring_sums(mhd_grid_s* g, const double* a, cudaStream_t st);
 // B -= dt curl_h E with E in the grid's edge arrays (dt from the device scalar)
 void ct_apply(mhd_grid_s* g, const double* dt_dev, double* br, double* bt, double* bp);
 void force(mhd_grid_s* g, const double* vr, const double* vt, const double* vp,
