@@ -1,8 +1,9 @@
 """Full-size parity: the flux-rope workload at 256x256x512 (33.5M cells), FP64, one step in the
 launch configuration bench.py times, against the oracle's record of the same step
-(tests/golden/fluxrope_256x256x512_oracle_step1.json, written by tests/golden/make_golden.py from
-the CPU oracle alone; the oracle needs ~1.5 h for this step). Compared: step coefficients, PCG
-iteration counts (+-1), per-field L2 norms and the values at 2000 seeded positions per field."""
+(tests/golden/fluxrope_256x256x512_oracle_step1.json, and ..._oracle_pc2_step1.json for the step
+with PC2, written by tests/golden/make_golden.py from the CPU oracle alone; the oracle needs ~1.5 h
+for the Jacobi step). Compared: step coefficients, PCG iteration counts (+-1), per-field L2 norms
+and the values at 2000 seeded positions per field."""
 import json
 import os
 
@@ -14,13 +15,23 @@ import paper_1811_02605_gb300 as P
 from paper_1811_02605_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
-GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
-                      "fluxrope_256x256x512_oracle_step1.json")
+HERE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+GOLDEN = os.path.join(HERE, "fluxrope_256x256x512_oracle_step1.json")
+GOLDEN_PC2 = os.path.join(HERE, "fluxrope_256x256x512_oracle_pc2_step1.json")
 
 
 @pytest.mark.skipif(not os.path.exists(GOLDEN), reason="oracle record not generated")
 def test_fluxrope_256x256x512_first_step_matches_oracle_record():
-    rec = json.load(open(GOLDEN))
+    _check_record(GOLDEN)
+
+
+@pytest.mark.skipif(not os.path.exists(GOLDEN_PC2), reason="oracle record not generated")
+def test_fluxrope_256x256x512_first_step_pc2_matches_oracle_record():
+    _check_record(GOLDEN_PC2)
+
+
+def _check_record(path):
+    rec = json.load(open(path))
     w, st = I.workload(rec["workload"])
     d = w["desc"]
     assert [d.nr, d.nt, d.np] == [rec["desc"]["nr"], rec["desc"]["nt"], rec["desc"]["np"]]
@@ -30,7 +41,7 @@ def test_fluxrope_256x256x512_first_step_matches_oracle_record():
     del st
     f = P.make_fields(ds["br"], ds["bt"], ds["bp"], ds["vr"], ds["vt"], ds["vp"])
     prm = P.make_params(nu=rec["params"]["nu"], eta=rec["params"]["eta"], cfl=rec["params"]["cfl"],
-                        tol=rec["params"]["tol"])
+                        tol=rec["params"]["tol"], preconditioner=rec["params"].get("preconditioner", 0))
     status, info = P.mhd_step(g, prm, f)
     torch.cuda.synchronize()
     assert status == P.MHD_OK
