@@ -112,17 +112,12 @@ __global__ void __launch_bounds__(kThreads) k_pc2_line(Dims d, OpTab<T> t, const
 #define IN_LINE(tt) (exact || k0 + (tt) < np)
 #define FIRST(tt) ((tt) == 0 && lane == 0)
 #define LAST(tt) (exact ? ((tt) == S - 1 && lane == 31) : (k0 + (tt) == np - 1))
-    // coalesced passes over a line: lane, lane + 32, ...; with np = 32 SEG the trip count is a
-    // compile-time constant, so these loops unroll and their global loads are issued together
-    const int nsweep = exact ? SEG : (np + 31 - lane) / 32;
     double a_rz = 0.0, a_rr = 0.0;   // per-line partials (in T) are added here in FP64
     const int nl = d.nr * d.nt;
     for (int line = blockIdx.x * warps + warp; line < nl; line += gridDim.x * warps) {
         const T w = t.ap[line];
         const long long base = (long long)line * np;
-#pragma unroll 8
-        for (int m = 0; m < nsweep; m++) {
-            const int k = lane + 32 * m;
+        for (int k = lane; k < np; k += 32) {
             const T id = idt[base + k];
             ib[k + k / S] = id;
             gb[k + k / S] = w * id;
@@ -152,9 +147,7 @@ __global__ void __launch_bounds__(kThreads) k_pc2_line(Dims d, OpTab<T> t, const
 #pragma unroll 1
         for (int c = 0; c < NC; c++) {
             const long long off = c * d.N + base;
-#pragma unroll 8
-            for (int m = 0; m < nsweep; m++) {
-                const int k = lane + 32 * m;
+            for (int k = lane; k < np; k += 32) {
                 T rv = r[off + k];
                 if (MODE == kIter) {
                     x[off + k] = fma(al, p[off + k], x[off + k]);
@@ -226,9 +219,7 @@ __global__ void __launch_bounds__(kThreads) k_pc2_line(Dims d, OpTab<T> t, const
                 }
             }
             __syncwarp();
-#pragma unroll 8
-            for (int m = 0; m < nsweep; m++) {
-                const int k = lane + 32 * m;
+            for (int k = lane; k < np; k += 32) {
                 const T zv = ub[k + k / S];
                 const T rv = r[off + k];
                 z[off + k] = zv;
