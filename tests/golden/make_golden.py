@@ -7,6 +7,7 @@ the CPU baseline the oracle's own iteration counts at this size.
 
     python tests/golden/make_golden.py fluxrope_256x256x512          # PC1 (point Jacobi)
     python tests/golden/make_golden.py fluxrope_256x256x512 --pc2    # PC2 (phi-line ILU(0))
+    python tests/golden/make_golden.py fluxrope_256x256x512 --pc2 --sts   # PC2, RKL2 viscosity
 """
 import json
 import os
@@ -30,15 +31,16 @@ def sample_index(shape, seed):
     return np.sort(rng.choice(n, size=min(NSAMPLE, n), replace=False))
 
 
-def main(name, pc2=False):
+def main(name, pc2=False, sts=False):
     w, st = I.workload(name)
     d = w["desc"]
     g = O.Grid.from_desc(d)
     t0 = time.time()
-    out, info = g.step(st, nu=w["nu"], eta=w["eta"], cfl=w["cfl"], tol=w["tol"], pc2=pc2)
+    out, info = g.step(st, nu=w["nu"], eta=w["eta"], cfl=w["cfl"], tol=w["tol"], pc2=pc2, sts=sts)
     wall = time.time() - t0
     rec = dict(workload=name, desc=dict(nr=d.nr, nt=d.nt, np=d.np, r0=d.r0, r1=d.r1, stretch=d.stretch),
-               params=dict(nu=w["nu"], eta=w["eta"], cfl=w["cfl"], tol=w["tol"], preconditioner=1 if pc2 else 0),
+               params=dict(nu=w["nu"], eta=w["eta"], cfl=w["cfl"], tol=w["tol"], preconditioner=1 if pc2 else 0,
+                           viscosity_sts=1 if sts else 0),
                info={k: (v if not isinstance(v, np.floating) else float(v)) for k, v in info.items()},
                oracle_step_seconds=wall, fields={})
     rec["info"] = {k: ([float(x) for x in v] if isinstance(v, list) else float(v)) for k, v in info.items()}
@@ -47,7 +49,7 @@ def main(name, pc2=False):
         rec["fields"][k] = dict(shape=list(a.shape), l2=float(np.linalg.norm(a)),
                                 l2_initial=float(np.linalg.norm(st[k])),
                                 sample_index=idx.tolist(), sample=a.ravel()[idx].tolist())
-    tag = "_pc2" if pc2 else ""
+    tag = ("_pc2" if pc2 else "") + ("_sts" if sts else "")
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"{name}_oracle{tag}_step1.json")
     with open(path, "w") as f:
         json.dump(rec, f)
@@ -56,4 +58,4 @@ def main(name, pc2=False):
 
 if __name__ == "__main__":
     args = [a for a in sys.argv[1:] if not a.startswith("--")]
-    main(args[0] if args else "fluxrope_256x256x512", pc2="--pc2" in sys.argv)
+    main(args[0] if args else "fluxrope_256x256x512", pc2="--pc2" in sys.argv, sts="--sts" in sys.argv)

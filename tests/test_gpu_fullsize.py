@@ -18,6 +18,7 @@ pytestmark = pytest.mark.gpu
 HERE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 GOLDEN = os.path.join(HERE, "fluxrope_256x256x512_oracle_step1.json")
 GOLDEN_PC2 = os.path.join(HERE, "fluxrope_256x256x512_oracle_pc2_step1.json")
+GOLDEN_PC2_STS = os.path.join(HERE, "fluxrope_256x256x512_oracle_pc2_sts_step1.json")
 
 
 @pytest.mark.skipif(not os.path.exists(GOLDEN), reason="oracle record not generated")
@@ -28,6 +29,11 @@ def test_fluxrope_256x256x512_first_step_matches_oracle_record():
 @pytest.mark.skipif(not os.path.exists(GOLDEN_PC2), reason="oracle record not generated")
 def test_fluxrope_256x256x512_first_step_pc2_matches_oracle_record():
     _check_record(GOLDEN_PC2)
+
+
+@pytest.mark.skipif(not os.path.exists(GOLDEN_PC2_STS), reason="oracle record not generated")
+def test_fluxrope_256x256x512_first_step_pc2_sts_matches_oracle_record():
+    _check_record(GOLDEN_PC2_STS)
 
 
 def _check_record(path):
@@ -41,7 +47,8 @@ def _check_record(path):
     del st
     f = P.make_fields(ds["br"], ds["bt"], ds["bp"], ds["vr"], ds["vt"], ds["vp"])
     prm = P.make_params(nu=rec["params"]["nu"], eta=rec["params"]["eta"], cfl=rec["params"]["cfl"],
-                        tol=rec["params"]["tol"], preconditioner=rec["params"].get("preconditioner", 0))
+                        tol=rec["params"]["tol"], preconditioner=rec["params"].get("preconditioner", 0),
+                        viscosity_sts=rec["params"].get("viscosity_sts", 0))
     status, info = P.mhd_step(g, prm, f)
     torch.cuda.synchronize()
     assert status == P.MHD_OK
