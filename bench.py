@@ -52,8 +52,8 @@ SPMV_BYTES_PER_CELL = {"fp64": 2 * 3 * 8, "fp32": 2 * 3 * 4}
 # D_{j-2} and ly0 read, D_j written = 4 x 3 x 8 B
 STS_FLOPS_PER_CELL = 3 * 16 + 3
 STS_BYTES_PER_CELL = 4 * 3 * 8
-# PC2 line kernel per cell: x, p, r, q read, x, r, z written (7 x 3 x 8 B) plus 1/dt (8 B, shared
-# by the three components)
+# FP64 PC2 line kernel per cell: x, p, r, q read, x, r, z written (7 x 3 x 8 B) plus 1/dt (8 B,
+# shared by the three components)
 PC2_LINE_BYTES_PER_CELL = 7 * 3 * 8 + 8
 # resistivity of the explicit-against-implicit comparison (the workload itself has eta = 0)
 RES_ETA = 1e-3
@@ -308,6 +308,16 @@ def run_ours(args):
     spmv_avg = spmv_ms / max(min(spmv_n, sum(sum(i["iters"]) for i in infos64)), 1)
     spmv_tflops = SPMV_FLOPS_PER_CELL * N / (spmv_avg * 1e-3) / 1e12
     pcg64_gbs = PCG_BYTES_PER_CELL["fp64"] * N * it64_total / (pcg64_ms * 1e-3) / 1e9
+    # per-kernel DRAM passes of a 3-component FP64 vector (8 B x 3 per cell per pass): the p update
+    # also adds the previous alpha p to x (r, p, x in; p, x out), the update reads r, q and writes r
+    kernels64 = {}
+    for k, passes in (("pupdate64", 5), ("spmv64", 2), ("update64", 3)):
+        ms_k, n_k = prof64[k]
+        if n_k:
+            avg = ms_k / it64_total
+            gbs = passes * 24 * N / (avg * 1e-3) / 1e9
+            kernels64[k] = dict(avg_launch_ms=round(avg, 4), bytes_per_cell=passes * 24, gbs=round(gbs, 1),
+                                frac_of_hbm=round(gbs / hbm, 4))
     roof = dict(bound="alu", achieved=round(spmv_tflops, 4), peak=round(FP64_PEAK_TFLOPS / 1e3, 4),
                 unit="TFLOP/s", frac=round(spmv_tflops / (FP64_PEAK_TFLOPS / 1e3), 4),
                 traffic=(int(SPMV64_DRAM_BYTES_PER_CELL * N) if prof64["pupdate64"][1] else None),
@@ -323,7 +333,9 @@ def run_ours(args):
         pcg32_gbs = PCG_BYTES_PER_CELL["fp32"] * N * pcg32_n / (pcg32_ms * 1e-3) / 1e9
         tiled = profm["pupdate32"][1] == 0
         # per-kernel DRAM passes of a 3-component FP32 vector (4 B x 3 per cell per pass)
-        kb = {"spmv32": 3 if tiled else 2, "update32": 5 if tiled else 6, "pupdate32": 3}
+        # split form: the p update also adds the previous alpha p to x (r, p, x in; p, x out) and the
+        # update kernel reads r, q and writes r
+        kb = {"spmv32": 3 if tiled else 2, "update32": 5 if tiled else 3, "pupdate32": 5}
         kernels = {}
         for k in ("pupdate32", "spmv32", "update32"):
             ms_k, n_k = profm[k]
@@ -509,7 +521,7 @@ def run_ours(args):
                                 pcg_iters_per_step=it64,
                                 dt=[i["dt"] for i in infos64]),
                     pcg_gbs=dict(fp64=round(pcg64_gbs, 1), fp64_frac_of_hbm=round(pcg64_gbs / hbm, 4),
-                                 peak_gbs=hbm, peak_source=peak_src),
+                                 peak_gbs=hbm, peak_source=peak_src, kernels=kernels64),
                     roofline=roof, mixed=mixed, mixed_reliable=mixed_reliable, sts=sts, sts_mixed_reliable=sts_mixed, pcg_single_reduction=pcg_cg,
                     pc2=pc2, pc2_sts=pc2_sts, pc2_mixed_reliable=pc2_mixed, resistivity=res_entry,
                     e2e=e2e, cpu_baseline=cpu, clocks=clk64,
@@ -723,6 +735,66 @@ def run_refinement_study(args):
                           rows=rows)), flush=True)
 
 
+def run_accuracy_study(args):
+    """`--acc-steps` steps (default 20) of the workload from its initial state with each solver
+    form; per-field relative L2 distance to the FP64 point-Jacobi run after every 5 steps, the
+    largest final relative residual of any solve, and ms per step (CUDA events)."""
+    import torch
+    from paper_1811_02605_gb300 import build as B
+    B.build()
+    import paper_1811_02605_gb300 as P
+    w, st0 = gen_state(args.workload, args.grid)
+    d = w["desc"]
+    stream = torch.cuda.Stream()
+    g = P.mhd_grid_create(d.nr, d.nt, d.np, d.r0, d.r1, d.stretch, stream)
+    marks = [s for s in range(5, args.acc_steps + 1, 5)] or [args.acc_steps]
+    if marks[-1] != args.acc_steps:
+        marks.append(args.acc_steps)
+    variants = [
+        ("fp64_pc1", dict()),
+        ("mixed_restarted_1e-5", dict(precision=P.PREC_MIXED, inner_tol=1e-5, mixed_restart=1)),
+        ("mixed_reliable_0.1", dict(precision=P.PREC_MIXED, inner_tol=0.1, mixed_restart=0)),
+        ("fp64_pc2", dict(preconditioner=1)),
+        ("mixed_pc2_reliable_1e-3", dict(precision=P.PREC_MIXED, inner_tol=1e-3, mixed_restart=0,
+                                         preconditioner=1)),
+    ]
+    ref = {}
+    rows = []
+    for name, kw in variants:
+        with torch.cuda.stream(stream):
+            ds = {k: torch.from_numpy(v).to("cuda") for k, v in st0.items()}
+        torch.cuda.synchronize()
+        f = P.make_fields(ds["br"], ds["bt"], ds["bp"], ds["vr"], ds["vt"], ds["vp"])
+        prm = P.make_params(nu=w["nu"], eta=w["eta"], cfl=w["cfl"], tol=w["tol"], max_outer=200,
+                            max_iter=20000, **kw)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        errs, iters, worst, ms = {}, 0, 0.0, 0.0
+        for s in range(1, args.acc_steps + 1):
+            e0.record(stream)
+            st, info = P.mhd_step(g, prm, f)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if st != P.MHD_OK:
+                raise RuntimeError(f"{name} step {s}: {P.STATUS_NAMES[st]} {P.mhd_last_error(g)}")
+            ms += e0.elapsed_time(e1)
+            iters += sum(info["iters"])
+            worst = max(worst, max(info["relres"]))
+            if s in marks:
+                if name == "fp64_pc1":
+                    ref[s] = {k: v.clone() for k, v in ds.items()}
+                else:
+                    errs[s] = {k: float(torch.linalg.norm(ds[k] - ref[s][k]) / torch.linalg.norm(ref[s][k]))
+                               for k in ds}
+        rows.append(dict(variant=name, ms_per_step=round(ms / args.acc_steps, 3),
+                         pcg_iters_per_step=round(iters / args.acc_steps, 2), max_final_relres=worst,
+                         rel_l2_vs_fp64_pc1={str(s): e for s, e in errs.items()}))
+        del ds, f
+    print(json.dumps(dict(accuracy_study=f"{d.nr}x{d.nt}x{d.np}", workload=args.workload,
+                          steps=args.acc_steps, reference="FP64 point-Jacobi PCG on the GPU (the same "
+                          "path matches the oracle's record of the first step at this size)", rows=rows)),
+          flush=True)
+
+
 def run_profile_case(args):
     """A short, fixed piece of the hot path for profilers: the first SI system of the workload,
     `--profile-iters` FP64 CG iterations, then one mixed-precision outer pass with the same cap."""
@@ -779,6 +851,9 @@ def main():
     ap.add_argument("--adjoint", action="store_true", help="time and check the adjoint workload and exit")
     ap.add_argument("--refinement-study", action="store_true",
                     help="first SI solve: FP64 vs mixed (restarted / reliable updates) over inner tolerances")
+    ap.add_argument("--accuracy-study", action="store_true",
+                    help="--acc-steps steps with each solver form; per-field error against FP64 point-Jacobi")
+    ap.add_argument("--acc-steps", type=int, default=20)
     ap.add_argument("--adj-steps", type=int, default=20)
     ap.add_argument("--fd-dirs", type=int, default=16)
     ap.add_argument("--no-mixed", action="store_true")
@@ -800,6 +875,8 @@ def main():
         run_adjoint(args)
     elif args.refinement_study:
         run_refinement_study(args)
+    elif args.accuracy_study:
+        run_accuracy_study(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -33,8 +33,8 @@ __global__ void k_tables(Dims d, Geo G, const double* __restrict__ alpha_p, OpTa
 __global__ void k_init64(Dims d, int nc, const double* __restrict__ b, const double* __restrict__ x0,
                          double* __restrict__ xs, double* __restrict__ r, double* __restrict__ p, OpTab<double> t,
                          OpTab64u tu, PcgScalars* sc, double* __restrict__ partials);
-__global__ void k_finish64(Dims d, int nc, const double* __restrict__ xs, double* __restrict__ x,
-                           const double* __restrict__ s, const PcgScalars* sc);
+__global__ void k_finish64(Dims d, int nc, const double* __restrict__ xs, const double* __restrict__ p,
+                           double* __restrict__ x, const double* __restrict__ s, const PcgScalars* sc);
 }  // namespace mhd
 
 using namespace mhd;
@@ -420,6 +420,7 @@ __global__ void k_batch_setup(PcgScalars* const* scs, int n, double tol, int max
     sc->total_iter = 0;
     sc->outer = 0;
     sc->outer_done = 0;
+    sc->ax = 0.0;
     sc->count = 0u;
 }
 
@@ -457,7 +458,7 @@ void enqueue_batch(Plan& P, cudaStream_t st, bool finish, int max_iter_override)
         for (int s = 0; s < P.n; s++) {
             mhd_grid_s* g = P.grids[s];
             const int blocks = grid_blocks(g, g->d.N / 2, 4);
-            k_finish64<<<blocks, kThreads, 0, st>>>(g->d, 3, g->x64, P.x[s], g->t64.s, g->sc);
+            k_finish64<<<blocks, kThreads, 0, st>>>(g->d, 3, g->x64, g->p64, P.x[s], g->t64.s, g->sc);
         }
     }
 }

@@ -138,37 +138,29 @@ __global__ void k_ring(Dims d, const double* __restrict__ a, double* __restrict_
 // ------------------------------------------------------------------------------------------
 // current density on edges
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_jr(Dims d, Geo G, const double* __restrict__ bt,
-                                                 const double* __restrict__ bp, const double* __restrict__ ring,
-                                                 double* __restrict__ jr) {
+__global__ void __launch_bounds__(kThreads) k_jr(Dims d, const double* __restrict__ cr,
+                                                 const double* __restrict__ bt, const double* __restrict__ bp,
+                                                 const double* __restrict__ ring, double* __restrict__ jr) {
     const long long n = (long long)d.nr * (d.nt + 1) * d.np;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
         int k;
         unsigned int q;
         split_np(d, e, k, q);
         const int j = (int)(q % (d.nt + 1)), i = (int)(q / (d.nt + 1));
-        const double rc = G.rc[i];
+        const double* c = cr + 4 * (size_t)q;
         double val;
-        if (j == 0) {
-            const double circ = ring[i] * (rc * G.sc[0] * G.dph);
-            val = circ / (rc * rc * (1.0 - G.cc[0]) * 6.283185307179586);
-        } else if (j == d.nt) {
-            const double circ = -ring[d.nr + i] * (rc * G.sc[d.nt - 1] * G.dph);
-            val = circ / (rc * rc * (1.0 + G.cc[d.nt - 1]) * 6.283185307179586);
-        } else {
-            const double area = rc * rc * (G.cc[j - 1] - G.cc[j]) * G.dph;
-            const double c = bp[ix(d, i, j, k)] * rc * G.sc[j] * G.dph - bp[ix(d, i, j - 1, k)] * rc * G.sc[j - 1] * G.dph -
-                             bt[ixt(d, i, j, k)] * rc * G.dth + bt[ixt(d, i, j, km1(d, k))] * rc * G.dth;
-            val = c / area;
-        }
+        if (j == 0) val = ring[i] * c[3];                   // north cap circulation / cap area
+        else if (j == d.nt) val = -ring[d.nr + i] * c[3];   // south cap
+        else val = c[0] * bp[ix(d, i, j, k)] - c[1] * bp[ix(d, i, j - 1, k)] -
+                   c[2] * (bt[ixt(d, i, j, k)] - bt[ixt(d, i, j, km1(d, k))]);
         jr[e] = val;
     }
 }
 
 // walls_zero: the resistive operator's current, 0 on the tangential edges of r0 and r1
-__global__ void __launch_bounds__(kThreads) k_jt(Dims d, Geo G, const double* __restrict__ br,
-                                                 const double* __restrict__ bp, double* __restrict__ jt,
-                                                 int walls_zero) {
+__global__ void __launch_bounds__(kThreads) k_jt(Dims d, const double* __restrict__ ct,
+                                                 const double* __restrict__ br, const double* __restrict__ bp,
+                                                 double* __restrict__ jt, int walls_zero) {
     const long long n = (long long)(d.nr + 1) * d.nt * d.np;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
         int k;
@@ -179,19 +171,17 @@ __global__ void __launch_bounds__(kThreads) k_jt(Dims d, Geo G, const double* __
             jt[e] = 0.0;
             continue;
         }
-        const double rlo = (i > 0) ? G.rc[i - 1] : 2.0 * G.r0 - G.rc[0];
-        const double rhi = (i < d.nr) ? G.rc[i] : 2.0 * G.r1 - G.rc[d.nr - 1];
+        // ghost B_phi beyond r0 / r1 = the first interior value (at the mirrored radius in the table)
         const int ilo = (i > 0) ? i - 1 : 0, ihi = (i < d.nr) ? i : d.nr - 1;
-        const double area = G.sc[j] * 0.5 * (rhi * rhi - rlo * rlo) * G.dph;
-        const double c = bp[ix(d, ilo, j, k)] * rlo * G.sc[j] * G.dph + br[ix(d, i, j, k)] * (rhi - rlo) -
-                         bp[ix(d, ihi, j, k)] * rhi * G.sc[j] * G.dph - br[ix(d, i, j, km1(d, k))] * (rhi - rlo);
-        jt[e] = c / area;
+        const double* c = ct + 3 * (size_t)q;
+        jt[e] = c[0] * bp[ix(d, ilo, j, k)] + c[1] * (br[ix(d, i, j, k)] - br[ix(d, i, j, km1(d, k))]) -
+                c[2] * bp[ix(d, ihi, j, k)];
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_jp(Dims d, Geo G, const double* __restrict__ br,
-                                                 const double* __restrict__ bt, double* __restrict__ jp,
-                                                 int walls_zero) {
+__global__ void __launch_bounds__(kThreads) k_jp(Dims d, const double* __restrict__ cp,
+                                                 const double* __restrict__ br, const double* __restrict__ bt,
+                                                 double* __restrict__ jp, int walls_zero) {
     const long long n = (long long)(d.nr + 1) * (d.nt + 1) * d.np;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
         int k;
@@ -202,13 +192,10 @@ __global__ void __launch_bounds__(kThreads) k_jp(Dims d, Geo G, const double* __
             jp[e] = 0.0;
             continue;
         }
-        const double rlo = (i > 0) ? G.rc[i - 1] : 2.0 * G.r0 - G.rc[0];
-        const double rhi = (i < d.nr) ? G.rc[i] : 2.0 * G.r1 - G.rc[d.nr - 1];
         const int ilo = (i > 0) ? i - 1 : 0, ihi = (i < d.nr) ? i : d.nr - 1;
-        const double area = 0.5 * (rhi * rhi - rlo * rlo) * G.dth;
-        const double c = br[ix(d, i, j - 1, k)] * (rhi - rlo) + bt[ixt(d, ihi, j, k)] * rhi * G.dth -
-                         br[ix(d, i, j, k)] * (rhi - rlo) - bt[ixt(d, ilo, j, k)] * rlo * G.dth;
-        jp[e] = c / area;
+        const double* c = cp + 3 * (size_t)q;
+        jp[e] = c[0] * (br[ix(d, i, j - 1, k)] - br[ix(d, i, j, k)]) + c[1] * bt[ixt(d, ihi, j, k)] -
+                c[2] * bt[ixt(d, ilo, j, k)];
     }
 }
 
@@ -219,9 +206,9 @@ void current_edges(mhd_grid_s* g, const double* br, const double* bt, const doub
     k_ring<<<2 * d.nr, kThreads, 0, st>>>(d, bp, g->ring);
     const long long n = (long long)(d.nr + 1) * (d.nt + 1) * d.np;
     const int blocks = grid_blocks(g, n, 8);
-    k_jr<<<blocks, kThreads, 0, st>>>(d, g->geo, bt, bp, g->ring, g->er);
-    k_jt<<<blocks, kThreads, 0, st>>>(d, g->geo, br, bp, g->et, walls_zero ? 1 : 0);
-    k_jp<<<blocks, kThreads, 0, st>>>(d, g->geo, br, bt, g->ep, walls_zero ? 1 : 0);
+    k_jr<<<blocks, kThreads, 0, st>>>(d, g->ex.jr, bt, bp, g->ring, g->er);
+    k_jt<<<blocks, kThreads, 0, st>>>(d, g->ex.jt, br, bp, g->et, walls_zero ? 1 : 0);
+    k_jp<<<blocks, kThreads, 0, st>>>(d, g->ex.jp, br, bt, g->ep, walls_zero ? 1 : 0);
 }
 
 // J at a cell centre from the edge arrays (polar phi edges left out)
@@ -240,7 +227,7 @@ __device__ __forceinline__ void jcentre(const Dims& d, const double* __restrict_
 // ------------------------------------------------------------------------------------------
 // momentum force
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_force(Dims d, Geo G, Vel v, const double* __restrict__ br,
+__global__ void __launch_bounds__(kThreads) k_force(Dims d, Geo G, ExTab X, Vel v, const double* __restrict__ br,
                                                     const double* __restrict__ bt, const double* __restrict__ bp,
                                                     const double* __restrict__ jr, const double* __restrict__ jt,
                                                     const double* __restrict__ jp, const double* __restrict__ dt_dev,
@@ -255,31 +242,31 @@ __global__ void __launch_bounds__(kThreads) k_force(Dims d, Geo G, Vel v, const 
         const int j = (int)(ij % d.nt), i = (int)(ij / d.nt);
         double u[3];
         v.at(c, u);
-        const double rc = G.rc[i];
-        // upwind differences of the three components along r, theta, phi (one reciprocal per
-        // distance: FP64 division is a long instruction sequence on this part)
+        // per-shell reciprocals: 1/d_lo, 1/d_hi, 1/rc, 1/rho, 1/(rc dth)
+        const double* sh = X.sh + 5 * (size_t)i;
+        // upwind differences of the three components along r, theta, phi
         double Dr[3], Dt[3], Dp[3];
         if (u[0] > 0.0) {
             if (i > 0) {
                 double n[3];
                 v.at(c - (long long)d.nt * d.np, n);
-                const double ih = 1.0 / (rc - G.rc[i - 1]);
+                const double ih = sh[0];
                 for (int m = 0; m < 3; m++) Dr[m] = (u[m] - n[m]) * ih;
             } else {
-                const double ih = 1.0 / (2.0 * (G.rc[0] - G.r0));
+                const double ih = sh[0];   // Dirichlet mirror ghost at distance 2 (rc_0 - r0)
                 for (int m = 0; m < 3; m++) Dr[m] = (u[m] - (-u[m])) * ih;
             }
         } else {
             if (i < d.nr - 1) {
                 double n[3];
                 v.at(c + (long long)d.nt * d.np, n);
-                const double ih = 1.0 / (G.rc[i + 1] - rc);
+                const double ih = sh[1];
                 for (int m = 0; m < 3; m++) Dr[m] = (n[m] - u[m]) * ih;
             } else {
                 for (int m = 0; m < 3; m++) Dr[m] = 0.0;
             }
         }
-        const double iht = 1.0 / (rc * G.dth);
+        const double iht = sh[4];
         if (u[1] > 0.0) {
             if (j > 0) {
                 double n[3];
@@ -297,7 +284,7 @@ __global__ void __launch_bounds__(kThreads) k_force(Dims d, Geo G, Vel v, const 
                 for (int m = 0; m < 3; m++) Dt[m] = 0.0;
             }
         }
-        const double ihp = 1.0 / (rc * G.sc[j] * G.dph);
+        const double ihp = X.ihp[ij];
         {
             double n[3];
             if (u[2] > 0.0) {
@@ -310,15 +297,15 @@ __global__ void __launch_bounds__(kThreads) k_force(Dims d, Geo G, Vel v, const 
         }
         double adv[3];
         for (int m = 0; m < 3; m++) adv[m] = u[0] * Dr[m] + u[1] * Dt[m] + u[2] * Dp[m];
-        const double cot = G.cc[j] / G.sc[j];
-        const double irc = 1.0 / rc;
+        const double cot = X.cot[j];
+        const double irc = sh[2];
         adv[0] += -(u[1] * u[1] + u[2] * u[2]) * irc;
         adv[1] += (u[0] * u[1] - u[2] * u[2] * cot) * irc;
         adv[2] += (u[0] * u[2] + u[1] * u[2] * cot) * irc;
         double B[3], J[3];
         bcentre(d, br, bt, bp, i, j, k, B);
         jcentre(d, jr, jt, jp, i, j, k, J);
-        const double irho = 1.0 / G.rho[i];
+        const double irho = sh[3];
         const double jxb0 = J[1] * B[2] - J[2] * B[1];
         const double jxb1 = J[2] * B[0] - J[0] * B[2];
         const double jxb2 = J[0] * B[1] - J[1] * B[0];
@@ -343,7 +330,7 @@ void force(mhd_grid_s* g, const double* vr, const double* vt, const double* vp, 
     current_edges(g, br, bt, bp);
     Vel v{vr, vt, vp, dlt, dfac, g->d.N};
     const int blocks = grid_blocks(g, g->d.N, 8);
-    k_force<<<blocks, kThreads, 0, g->stream>>>(g->d, g->geo, v, br, bt, bp, g->er, g->et, g->ep, dt_dev, dt_host,
+    k_force<<<blocks, kThreads, 0, g->stream>>>(g->d, g->geo, g->ex, v, br, bt, bp, g->er, g->et, g->ep, dt_dev, dt_host,
                                                 b_avg, b);
 }
 
@@ -434,7 +421,7 @@ __global__ void __launch_bounds__(kThreads) k_eedges(Dims d, const double* __res
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_ct(Dims d, Geo G, const double* __restrict__ er,
+__global__ void __launch_bounds__(kThreads) k_ct(Dims d, ExTab X, const double* __restrict__ er,
                                                  const double* __restrict__ et, const double* __restrict__ ep,
                                                  const double* __restrict__ dt_dev, double dt_host,
                                                  double* __restrict__ br, double* __restrict__ bt,
@@ -450,13 +437,10 @@ __global__ void __launch_bounds__(kThreads) k_ct(Dims d, Geo G, const double* __
             unsigned int q;
             split_np(d, e, k, q);
             const int j = (int)(q % d.nt), i = (int)(q / d.nt);
-            const double ri = G.r[i];
-            const double lt = ri * G.dth;
-            const double area = ri * ri * (G.cn[j] - G.cn[j + 1]) * G.dph;
-            const double lpj = ri * G.sn[j] * G.dph, lpj1 = ri * G.sn[j + 1] * G.dph;
-            const double c = et[ix(d, i, j, k)] * lt + ep[ixt(d, i, j + 1, k)] * lpj1 - et[ix(d, i, j, kp1(d, k))] * lt -
-                             ep[ixt(d, i, j, k)] * lpj;
-            br[e] -= dt * c / area;
+            const double* c = X.fr + 3 * (size_t)q;
+            const double circ = c[0] * (et[ix(d, i, j, k)] - et[ix(d, i, j, kp1(d, k))]) +
+                                c[1] * ep[ixt(d, i, j + 1, k)] - c[2] * ep[ixt(d, i, j, k)];
+            br[e] -= dt * circ;
         } else if (e < n_r + n_t) {
             const long long f = e - n_r;
             int k;
@@ -464,25 +448,20 @@ __global__ void __launch_bounds__(kThreads) k_ct(Dims d, Geo G, const double* __
             split_np(d, f, k, q);
             const int j = (int)(q % (d.nt + 1)), i = (int)(q / (d.nt + 1));
             if (j == 0 || j == d.nt) continue;
-            const double ri = G.r[i], ro = G.r[i + 1];
-            const double lr = ro - ri;
-            const double area = G.sn[j] * 0.5 * (ro * ro - ri * ri) * G.dph;
-            const double lpi = ri * G.sn[j] * G.dph, lpo = ro * G.sn[j] * G.dph;
-            const double c = ep[ixt(d, i, j, k)] * lpi + er[ixt(d, i, j, kp1(d, k))] * lr - ep[ixt(d, i + 1, j, k)] * lpo -
-                             er[ixt(d, i, j, k)] * lr;
-            bt[f] -= dt * c / area;
+            const double* c = X.ft + 3 * (size_t)q;
+            const double circ = c[0] * ep[ixt(d, i, j, k)] + c[1] * (er[ixt(d, i, j, kp1(d, k))] - er[ixt(d, i, j, k)]) -
+                                c[2] * ep[ixt(d, i + 1, j, k)];
+            bt[f] -= dt * circ;
         } else {
             const long long f = e - n_r - n_t;
             int k;
             unsigned int q;
             split_np(d, f, k, q);
             const int j = (int)(q % d.nt), i = (int)(q / d.nt);
-            const double ri = G.r[i], ro = G.r[i + 1];
-            const double lr = ro - ri;
-            const double area = 0.5 * (ro * ro - ri * ri) * G.dth;
-            const double c = er[ixt(d, i, j, k)] * lr + et[ix(d, i + 1, j, k)] * ro * G.dth - er[ixt(d, i, j + 1, k)] * lr -
-                             et[ix(d, i, j, k)] * ri * G.dth;
-            bp[f] -= dt * c / area;
+            const double* c = X.fp + 3 * (size_t)q;
+            const double circ = c[0] * (er[ixt(d, i, j, k)] - er[ixt(d, i, j + 1, k)]) + c[1] * et[ix(d, i + 1, j, k)] -
+                                c[2] * et[ix(d, i, j, k)];
+            bp[f] -= dt * circ;
         }
     }
 }
@@ -498,7 +477,7 @@ void induction(mhd_grid_s* g, const double* vr, const double* vt, const double* 
     const long long ne = (long long)d.nr * (d.nt + 1) * d.np + (long long)(d.nr + 1) * d.nt * d.np +
                          (long long)(d.nr + 1) * (d.nt + 1) * d.np;
     k_eedges<<<grid_blocks(g, ne, 8), kThreads, 0, g->stream>>>(d, g->ec, g->ring, g->er, g->et, g->ep);
-    k_ct<<<grid_blocks(g, ne, 8), kThreads, 0, g->stream>>>(d, g->geo, g->er, g->et, g->ep, dt_dev, dt_host, br, bt,
+    k_ct<<<grid_blocks(g, ne, 8), kThreads, 0, g->stream>>>(d, g->ex, g->er, g->et, g->ep, dt_dev, dt_host, br, bt,
                                                            bp);
 }
 
@@ -510,7 +489,7 @@ void ct_apply(mhd_grid_s* g, const double* dt_dev, double* br, double* bt, doubl
     const Dims d = g->d;
     const long long ne = (long long)d.nr * (d.nt + 1) * d.np + (long long)(d.nr + 1) * d.nt * d.np +
                          (long long)(d.nr + 1) * (d.nt + 1) * d.np;
-    k_ct<<<grid_blocks(g, ne, 8), kThreads, 0, g->stream>>>(d, g->geo, g->er, g->et, g->ep, dt_dev, 0.0, br, bt, bp);
+    k_ct<<<grid_blocks(g, ne, 8), kThreads, 0, g->stream>>>(d, g->ex, g->er, g->et, g->ep, dt_dev, 0.0, br, bt, bp);
 }
 
 // ------------------------------------------------------------------------------------------

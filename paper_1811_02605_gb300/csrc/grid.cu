@@ -161,6 +161,43 @@ HostGeo make_geo(const mhd_grid_desc_t& d) {
     return h;
 }
 
+// geometric factors of the explicit kernels (ExTab); the same expressions as the kernels would
+// form per element, so the per-cell reciprocals keep their bits
+struct HostEx {
+    std::vector<double> sh, ihp, cot, jr, jt, jp, fr, ft, fp;
+};
+
+HostEx make_ex(const HostGeo& h, const mhd_grid_desc_t& d) {
+    const int nr = d.nr, nt = d.nt;
+    const double pi = 3.14159265358979323846;
+    GeoView g{h.r.data(), h.rc.data(), h.sn.data(), h.cn.data(), h.sc.data(), h.cc.data(), h.rho.data(),
+              nr, nt, d.r0, pi / nt, 2.0 * pi / d.np};
+    HostEx x;
+    x.sh.assign(5 * (size_t)nr, 0.0);
+    x.ihp.assign((size_t)nr * nt, 0.0);
+    x.cot.assign(nt, 0.0);
+    x.jr.assign(4 * (size_t)nr * (nt + 1), 0.0);
+    x.jt.assign(3 * (size_t)(nr + 1) * nt, 0.0);
+    x.jp.assign(3 * (size_t)(nr + 1) * (nt + 1), 0.0);
+    x.fr.assign(3 * (size_t)(nr + 1) * nt, 0.0);
+    x.ft.assign(3 * (size_t)nr * (nt + 1), 0.0);
+    x.fp.assign(3 * (size_t)nr * nt, 0.0);
+    for (int i = 0; i < nr; i++) {
+        ex_shell(g, i, &x.sh[5 * (size_t)i]);
+        for (int j = 0; j < nt; j++) x.ihp[(size_t)i * nt + j] = ex_ihp(g, i, j);
+        for (int j = 0; j <= nt; j++) ex_jr(g, i, j, &x.jr[4 * ((size_t)i * (nt + 1) + j)]);
+        for (int j = 0; j <= nt; j++) ex_ft(g, i, j, &x.ft[3 * ((size_t)i * (nt + 1) + j)]);
+        for (int j = 0; j < nt; j++) ex_fp(g, i, j, &x.fp[3 * ((size_t)i * nt + j)]);
+    }
+    for (int j = 0; j < nt; j++) x.cot[j] = ex_cot(g, j);
+    for (int i = 0; i <= nr; i++) {
+        for (int j = 0; j < nt; j++) ex_jt(g, i, j, &x.jt[3 * ((size_t)i * nt + j)]);
+        for (int j = 0; j <= nt; j++) ex_jp(g, i, j, &x.jp[3 * ((size_t)i * (nt + 1) + j)]);
+        for (int j = 0; j < nt; j++) ex_fr(g, i, j, &x.fr[3 * ((size_t)i * nt + j)]);
+    }
+    return x;
+}
+
 template <typename T>
 bool dalloc(T** p, size_t n, std::vector<void*>& owned) {
     void* m = nullptr;
@@ -199,6 +236,7 @@ extern "C" mhd_status_t mhd_grid_create(const mhd_grid_desc_t* desc, void* cuda_
     std::memset(g->iter_graph, 0, sizeof(g->iter_graph));
 
     HostGeo h = make_geo(d);
+    HostEx hx = make_ex(h, d);
     g->max_kt2 = h.max_kt2;
     std::vector<void*> owned;
     const int nr = d.nr, nt = d.nt;
@@ -210,6 +248,11 @@ extern "C" mhd_status_t mhd_grid_create(const mhd_grid_desc_t* desc, void* cuda_
          dalloc(&rho, nr, owned) && dalloc(&rhoV, (size_t)nr * nt, owned) &&
          dalloc(&kt2, (size_t)nr * nt, owned) && dalloc(&wr, (size_t)(nr + 1) * nt, owned) &&
          dalloc(&wt, (size_t)nr * (nt + 1), owned) && dalloc(&wp, (size_t)nr * nt, owned);
+    double *x_sh, *x_ihp, *x_cot, *x_jr, *x_jt, *x_jp, *x_fr, *x_ft, *x_fp;
+    ok = ok && dalloc(&x_sh, hx.sh.size(), owned) && dalloc(&x_ihp, hx.ihp.size(), owned) &&
+         dalloc(&x_cot, hx.cot.size(), owned) && dalloc(&x_jr, hx.jr.size(), owned) &&
+         dalloc(&x_jt, hx.jt.size(), owned) && dalloc(&x_jp, hx.jp.size(), owned) &&
+         dalloc(&x_fr, hx.fr.size(), owned) && dalloc(&x_ft, hx.ft.size(), owned) && dalloc(&x_fp, hx.fp.size(), owned);
     ok = ok && dalloc(&g->t64.ar, (size_t)(nr + 1) * nt, owned) &&
          dalloc(&g->t64.at, (size_t)nr * (nt + 1), owned) && dalloc(&g->t64.ap, (size_t)nr * nt, owned) &&
          dalloc(&g->t64.s, (size_t)nr * nt, owned);
@@ -253,6 +296,8 @@ extern "C" mhd_status_t mhd_grid_create(const mhd_grid_desc_t* desc, void* cuda_
     };
     ok = up(r, h.r) && up(rc, h.rc) && up(sn, h.sn) && up(cn, h.cn) && up(sc, h.sc) && up(cc, h.cc) &&
          up(rho, h.rho) && up(rhoV, h.rhoV) && up(kt2, h.kt2) && up(wr, h.wr) && up(wt, h.wt) && up(wp, h.wp);
+    ok = ok && up(x_sh, hx.sh) && up(x_ihp, hx.ihp) && up(x_cot, hx.cot) && up(x_jr, hx.jr) && up(x_jt, hx.jt) &&
+         up(x_jp, hx.jp) && up(x_fr, hx.fr) && up(x_ft, hx.ft) && up(x_fp, hx.fp);
     ok = ok && cudaMemsetAsync(g->partials, 0, sizeof(double) * kMaxBlocks * kPartialsPerBlock, g->stream) == cudaSuccess;
     ok = ok && cudaMemsetAsync(g->sc, 0, sizeof(PcgScalars), g->stream) == cudaSuccess;
     ok = ok && cudaMemsetAsync(g->ss, 0, sizeof(StepScalars), g->stream) == cudaSuccess;
@@ -279,6 +324,9 @@ extern "C" mhd_status_t mhd_grid_create(const mhd_grid_desc_t* desc, void* cuda_
     G.dth = 3.14159265358979323846 / nt;
     G.dph = 2.0 * 3.14159265358979323846 / d.np;
     G.max_kt2 = h.max_kt2;
+    ExTab& X = g->ex;
+    X.sh = x_sh; X.ihp = x_ihp; X.cot = x_cot; X.jr = x_jr; X.jt = x_jt; X.jp = x_jp;
+    X.fr = x_fr; X.ft = x_ft; X.fp = x_fp;
     // row sums of |D^-1 K| (the Dirichlet weight sits on the diagonal only)
     double lam = 0.0;
     for (int i = 0; i < nr; i++)

@@ -35,6 +35,7 @@ struct PcgScalars {
     unsigned int count;  // last-block ticket
     int par;         // FP32 tiled path: which of the two p buffers holds the current p
     double dte;      // implicit resistivity: dt eta of the current solve
+    double ax;       // alpha of the last CG iteration whose alpha p~ has not yet been added to x~
 };
 
 // Device-resident scalars of one step.
@@ -98,6 +99,109 @@ struct OpTab {
     T* s;    // [nr*nt]     diag^(-1/2)
 };
 
+// Geometric factors of the explicit kernels, formed once on the host at grid creation so that no
+// explicit kernel divides (FP64 division is a long instruction sequence on this part, and these
+// kernels are bound by the FP64 pipe). A row is the np elements of one (i, j).
+struct ExTab {
+    const double* sh;    // [5*nr] per shell: 1/(rc_i - rc_{i-1}) (at i = 0: 1/(2 (rc_0 - r0))),
+                         //        1/(rc_{i+1} - rc_i) (0 at i = nr-1), 1/rc_i, 1/rho_i, 1/(rc_i dth)
+    const double* ihp;   // [nr*nt] 1/(rc_i sin(theta_j) dph)
+    const double* cot;   // [nt] cot of the theta centres
+    const double* jr;    // [4*nr*(nt+1)] radial-edge rows: dual lengths / dual area (3), polar cap factor
+    const double* jt;    // [3*(nr+1)*nt] theta-edge rows (ghost radii on r0 and r1)
+    const double* jp;    // [3*(nr+1)*(nt+1)] phi-edge rows (0 on the polar rows)
+    const double* fr;    // [3*(nr+1)*nt] r-face rows: edge lengths / face area
+    const double* ft;    // [3*nr*(nt+1)] theta-face rows (0 on the polar rows)
+    const double* fp;    // [3*nr*nt] phi-face rows
+};
+
+// The entries of ExTab from the 1-D metric tables, one row at a time; the host builds the grid's
+// tables with these and the no-allocation force path builds its own on the device.
+struct GeoView {
+    const double *r, *rc, *sn, *cn, *sc, *cc, *rho;
+    int nr, nt;
+    double r0, dth, dph;   // r1 is r[nr]
+};
+__host__ __device__ inline void ex_shell(const GeoView& g, int i, double* o) {
+    const double* rc = g.rc;
+    o[0] = (i > 0) ? 1.0 / (rc[i] - rc[i - 1]) : 1.0 / (2.0 * (rc[0] - g.r0));
+    o[1] = (i < g.nr - 1) ? 1.0 / (rc[i + 1] - rc[i]) : 0.0;
+    o[2] = 1.0 / rc[i];
+    o[3] = 1.0 / g.rho[i];
+    o[4] = 1.0 / (rc[i] * g.dth);
+}
+__host__ __device__ inline double ex_ihp(const GeoView& g, int i, int j) {
+    return 1.0 / (g.rc[i] * g.sc[j] * g.dph);
+}
+__host__ __device__ inline double ex_cot(const GeoView& g, int j) { return g.cc[j] / g.sc[j]; }
+// radial edge (i, j), j in [0, nt]: interior rows {rc sin_j dph, rc sin_{j-1} dph, rc dth} / dual
+// area; polar rows (j = 0, nt): the cap factor in o[3]
+__host__ __device__ inline void ex_jr(const GeoView& g, int i, int j, double* o) {
+    const double rc = g.rc[i], twopi = 6.283185307179586;
+    o[0] = o[1] = o[2] = o[3] = 0.0;
+    if (j == 0) {
+        o[3] = (rc * g.sc[0] * g.dph) / (rc * rc * (1.0 - g.cc[0]) * twopi);
+    } else if (j == g.nt) {
+        o[3] = (rc * g.sc[g.nt - 1] * g.dph) / (rc * rc * (1.0 + g.cc[g.nt - 1]) * twopi);
+    } else {
+        const double area = rc * rc * (g.cc[j - 1] - g.cc[j]) * g.dph;
+        o[0] = rc * g.sc[j] * g.dph / area;
+        o[1] = rc * g.sc[j - 1] * g.dph / area;
+        o[2] = rc * g.dth / area;
+    }
+}
+// radii on either side of the node shell i in [0, nr] (ghost radii mirrored at r0 and r1)
+__host__ __device__ inline void ex_rlohi(const GeoView& g, int i, double& rlo, double& rhi) {
+    rlo = (i > 0) ? g.rc[i - 1] : 2.0 * g.r0 - g.rc[0];
+    rhi = (i < g.nr) ? g.rc[i] : 2.0 * g.r[g.nr] - g.rc[g.nr - 1];
+}
+// theta edge (i, j), i in [0, nr]
+__host__ __device__ inline void ex_jt(const GeoView& g, int i, int j, double* o) {
+    double rlo, rhi;
+    ex_rlohi(g, i, rlo, rhi);
+    const double area = g.sc[j] * 0.5 * (rhi * rhi - rlo * rlo) * g.dph;
+    o[0] = rlo * g.sc[j] * g.dph / area;
+    o[1] = (rhi - rlo) / area;
+    o[2] = rhi * g.sc[j] * g.dph / area;
+}
+// phi edge (i, j), i in [0, nr], j in [0, nt] (0 on the polar rows)
+__host__ __device__ inline void ex_jp(const GeoView& g, int i, int j, double* o) {
+    o[0] = o[1] = o[2] = 0.0;
+    if (j == 0 || j == g.nt) return;
+    double rlo, rhi;
+    ex_rlohi(g, i, rlo, rhi);
+    const double area = 0.5 * (rhi * rhi - rlo * rlo) * g.dth;
+    o[0] = (rhi - rlo) / area;
+    o[1] = rhi * g.dth / area;
+    o[2] = rlo * g.dth / area;
+}
+// r face (i, j), i in [0, nr]: {r dth, r sin_{j+1} dph, r sin_j dph} / face area
+__host__ __device__ inline void ex_fr(const GeoView& g, int i, int j, double* o) {
+    const double ri = g.r[i];
+    const double area = ri * ri * (g.cn[j] - g.cn[j + 1]) * g.dph;
+    o[0] = ri * g.dth / area;
+    o[1] = ri * g.sn[j + 1] * g.dph / area;
+    o[2] = ri * g.sn[j] * g.dph / area;
+}
+// theta face (i, j), j in [0, nt] (0 on the polar rows): {ri sin_j dph, dr, ro sin_j dph} / area
+__host__ __device__ inline void ex_ft(const GeoView& g, int i, int j, double* o) {
+    o[0] = o[1] = o[2] = 0.0;
+    if (j == 0 || j == g.nt) return;
+    const double ri = g.r[i], ro = g.r[i + 1];
+    const double area = g.sn[j] * 0.5 * (ro * ro - ri * ri) * g.dph;
+    o[0] = ri * g.sn[j] * g.dph / area;
+    o[1] = (ro - ri) / area;
+    o[2] = ro * g.sn[j] * g.dph / area;
+}
+// phi face (i, j): {dr, ro dth, ri dth} / face area
+__host__ __device__ inline void ex_fp(const GeoView& g, int i, int j, double* o) {
+    const double ri = g.r[i], ro = g.r[i + 1];
+    const double area = 0.5 * (ro * ro - ri * ri) * g.dth;
+    o[0] = (ro - ri) / area;
+    o[1] = ro * g.dth / area;
+    o[2] = ri * g.dth / area;
+}
+
 // Unscaled FP64 tables of the same M_alpha (outer residual of mixed precision).
 struct OpTab64u {
     double* dg;   // [nr*nt] diagonal
@@ -120,6 +224,7 @@ struct mhd_grid_s {
     // device allocations
     void* geo_mem;
     mhd::Geo geo;
+    mhd::ExTab ex;
     mhd::OpTab<double> t64;
     mhd::OpTab<float> t32;
     mhd::OpTab64u tu;

@@ -76,6 +76,21 @@ __global__ void k_noalloc_tables(int nr, int nt, double r0, double dth, double d
     }
 }
 
+// the explicit kernels' geometric factors (the force's per-shell, per-row and per-edge-row tables),
+// one thread per (i, j) of the (nr + 1) x (nt + 1) node grid
+__global__ void k_noalloc_ex(mhd::GeoView g, double* sh, double* ihp, double* cot, double* jr, double* jt, double* jp) {
+    const int nr = g.nr, nt = g.nt;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (nr + 1) * (nt + 1)) return;
+    const int i = idx / (nt + 1), j = idx - i * (nt + 1);
+    if (i < nr && j == 0) mhd::ex_shell(g, i, sh + 5 * (size_t)i);
+    if (i == 0 && j < nt) cot[j] = mhd::ex_cot(g, j);
+    if (i < nr && j < nt) ihp[(size_t)i * nt + j] = mhd::ex_ihp(g, i, j);
+    if (i < nr) mhd::ex_jr(g, i, j, jr + 4 * ((size_t)i * (nt + 1) + j));
+    if (j < nt) mhd::ex_jt(g, i, j, jt + 3 * ((size_t)i * nt + j));
+    mhd::ex_jp(g, i, j, jp + 3 * ((size_t)i * (nt + 1) + j));
+}
+
 double* scratch_for_current_device(int* dev_out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
@@ -102,10 +117,12 @@ extern "C" mhd_status_t mhd_force_noalloc(const mhd_grid_desc_t* desc, const mhd
     if (!(d.r0 > 0) || !(d.r1 > d.r0) || !(d.stretch > 0)) return MHD_ERR_ARG;
     const long long N = (long long)d.nr * d.nt * d.np;
     const long long nr = d.nr, nt = d.nt, np = d.np;
-    // scratch layout (doubles): r, rc, sn, cn, sc, cc, rho, rhoV, jr, jt, jp, ring
-    const long long n_tab = (nr + 1) + nr + 2 * (nt + 1) + 2 * nt + nr + nr * nt;
+    // scratch layout (doubles): r, rc, sn, cn, sc, cc, rho, rhoV, the explicit tables (shell, 1/(r sin
+    // dph), cot, edge rows), jr, jt, jp, ring
+    const long long n_ex = 5 * nr + nr * nt + nt + 4 * nr * (nt + 1) + 3 * (nr + 1) * nt + 3 * (nr + 1) * (nt + 1);
+    const long long n_tab = (nr + 1) + nr + 2 * (nt + 1) + 2 * nt + nr + nr * nt + n_ex;
     const long long n_edge = nr * (nt + 1) * np + (nr + 1) * nt * np + (nr + 1) * (nt + 1) * np;
-    const long long need = n_tab + n_edge + 2 * nr + 8 * 16;  // +16 doubles alignment slack per table
+    const long long need = n_tab + n_edge + 2 * nr + 18 * 16;  // +16 doubles alignment slack per table
     if (N > kMaxCells || need > kScratchDoubles) return MHD_ERR_ARG;
 
     int dev = 0;
@@ -125,6 +142,12 @@ extern "C" mhd_status_t mhd_force_noalloc(const mhd_grid_desc_t* desc, const mhd
     double* cc = take(nt);
     double* rho = take(nr);
     double* rhoV = take(nr * nt);
+    double* x_sh = take(5 * nr);
+    double* x_ihp = take(nr * nt);
+    double* x_cot = take(nt);
+    double* x_jr = take(4 * nr * (nt + 1));
+    double* x_jt = take(3 * (nr + 1) * nt);
+    double* x_jp = take(3 * (nr + 1) * (nt + 1));
     double* jr = take(nr * (nt + 1) * np);
     double* jt = take((nr + 1) * nt * np);
     double* jp = take((nr + 1) * (nt + 1) * np);
@@ -174,6 +197,13 @@ extern "C" mhd_status_t mhd_force_noalloc(const mhd_grid_desc_t* desc, const mhd
     v.geo.r1 = r_last;
     v.geo.dth = dth;
     v.geo.dph = dph;
+    v.ex.sh = x_sh;
+    v.ex.ihp = x_ihp;
+    v.ex.cot = x_cot;
+    v.ex.jr = x_jr;
+    v.ex.jt = x_jt;
+    v.ex.jp = x_jp;
+    v.ex.fr = v.ex.ft = v.ex.fp = nullptr;   // CT face factors: not used by the force
     v.er = jr;
     v.et = jt;
     v.ep = jp;
@@ -183,6 +213,9 @@ extern "C" mhd_status_t mhd_force_noalloc(const mhd_grid_desc_t* desc, const mhd
     const long long nt_work = nr * nt > nt + 1 ? nr * nt : nt + 1;
     k_noalloc_tables<<<(int)((nt_work + 255) / 256), 256, 0, v.stream>>>(d.nr, d.nt, d.r0, dth, dph, r, rc, sn, cn,
                                                                          sc, cc, rho, rhoV);
+    const mhd::GeoView gv{r, rc, sn, cn, sc, cc, rho, d.nr, d.nt, d.r0, dth, dph};
+    const long long nodes = (nr + 1) * (nt + 1);
+    k_noalloc_ex<<<(int)((nodes + 255) / 256), 256, 0, v.stream>>>(gv, x_sh, x_ihp, x_cot, x_jr, x_jt, x_jp);
     mhd::force(&v, f->vr, f->vt, f->vp, nullptr, 0.0, f->br, f->bt, f->bp, nullptr, dt, nullptr, b);
     if (cudaGetLastError() != cudaSuccess) return MHD_ERR_CUDA;
     return MHD_OK;

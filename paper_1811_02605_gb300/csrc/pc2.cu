@@ -77,8 +77,11 @@ __host__ __device__ inline int padded_len(int np) {
 }
 
 // One warp per phi line of the scaled system.
-//   kIter:     x~ += alpha p~, r~ -= alpha q~; z~ = P~^-1 r~; <r~, z~> and ||r||^2 = sum dg r~^2;
-//              last CTA: beta = rho_new / rho, stop test, iteration count.
+//   kIter:     x~ += alpha p~ (FP64), r~ -= alpha q~; z~ = P~^-1 r~; <r~, z~> and
+//              ||r||^2 = sum dg r~^2; last CTA: beta = rho_new / rho, stop test, iteration count.
+//              FP32 defers the x update: alpha is handed on in sc->ax, and the p update of the
+//              next iteration (or the correction kernel when the inner solve stops here) adds
+//              alpha p~ to x~.
 //   kInit:     z~ = P~^-1 r~, p~ = z~; last CTA: rho, beta = 0, stop test (after the FP64 set-up).
 //   kReliable: z~ = P~^-1 r~ for the replaced residual; last CTA: rho = <r~, z~>, and the
 //              recurrence continues (beta = rho / rho_prev) while rho stays within 4x of the
@@ -108,6 +111,9 @@ __global__ void __launch_bounds__(kThreads) k_pc2_line(Dims d, OpTab<T> t, const
     const int k0 = lane * S;
     const int s0 = lane * (S + 1);         // element k0 + t of this lane's segment sits at s0 + t
     constexpr bool exact = SEG > 0;
+    // FP32: x~ += alpha p~ moves to the next p update, which leaves this HBM-bound kernel 52 instead
+    // of 88 B per cell; FP64: the kernel is bound by its FP64 instructions and the x update stays here
+    constexpr bool kDeferX = sizeof(T) == 4;
     // element k0 + t is in the line / is its first / is its last element
 #define IN_LINE(tt) (exact || k0 + (tt) < np)
 #define FIRST(tt) ((tt) == 0 && lane == 0)
@@ -150,7 +156,7 @@ __global__ void __launch_bounds__(kThreads) k_pc2_line(Dims d, OpTab<T> t, const
             for (int k = lane; k < np; k += 32) {
                 T rv = r[off + k];
                 if (MODE == kIter) {
-                    x[off + k] = fma(al, p[off + k], x[off + k]);
+                    if constexpr (!kDeferX) x[off + k] = fma(al, p[off + k], x[off + k]);
                     rv = fma(-al, q[off + k], rv);
                     r[off + k] = rv;
                 }
@@ -258,6 +264,7 @@ __global__ void __launch_bounds__(kThreads) k_pc2_line(Dims d, OpTab<T> t, const
             sc->total_iter += 1;
             sc->beta = rz / sc->rho;
             sc->rho_prev = sc->rho;
+            if (kDeferX) sc->ax = sc->alpha;   // x~ += alpha p~ is left to the next p update
         }
         sc->rho = rz;
         sc->rr = rr;

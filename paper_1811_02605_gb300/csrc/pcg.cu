@@ -184,12 +184,16 @@ __device__ __forceinline__ void scaled_stencil(const Dims& d, const Cell& c, con
 // ------------------------------------------------------------------------------------------
 // FP64 / FP32 CG iteration kernels on the scaled system
 // ------------------------------------------------------------------------------------------
-// A1: p = r + beta p
-template <typename T, int V, int NC>
+// A1: p = r + beta p. XD (deferred x update): first x += alpha_prev p with the alpha of the
+// previous iteration (sc->ax), so the update kernel B need not read p or touch x; the product
+// and its rounding are those of an immediate x update, one kernel later.
+template <typename T, int V, int NC, bool XD = false>
 __global__ void __launch_bounds__(kThreads) k_pupdate(Dims d, const T* __restrict__ r,
-                                                      T* __restrict__ p, const PcgScalars* sc) {
+                                                      T* __restrict__ p, T* __restrict__ x,
+                                                      const PcgScalars* sc) {
     if (sc->done) return;
     const T beta = (T)sc->beta;
+    const T ax = XD ? (T)sc->ax : T(0);
     const unsigned int G = (unsigned int)(d.N / V);
 #pragma unroll
     for (int c = 0; c < NC; c++) {
@@ -199,6 +203,13 @@ __global__ void __launch_bounds__(kThreads) k_pupdate(Dims d, const T* __restric
             T a[V], b[V];
             ldv<T, V>(rc + (long long)g * V, a);
             ldv<T, V>(pc + (long long)g * V, b);
+            if constexpr (XD) {
+                T xv[V];
+                ldv<T, V>(x + c * d.N + (long long)g * V, xv);
+#pragma unroll
+                for (int e = 0; e < V; e++) xv[e] = fma(ax, b[e], xv[e]);
+                stv<T, V>(x + c * d.N + (long long)g * V, xv);
+            }
 #pragma unroll
             for (int e = 0; e < V; e++) b[e] = fma(beta, b[e], a[e]);
             stv<T, V>(pc + (long long)g * V, b);
@@ -235,6 +246,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 4) k_spmv_dot(D
     if (reduce_last<1>(val, partials, &sc->count, out) && threadIdx.x == 0) {
         const double pq = out[0];
         sc->pq = pq;
+        sc->ax = 0.0;   // the p update of this iteration has applied any deferred x update
         if (!finite(pq)) sc->done = 3;
         else if (!(pq > 0.0)) sc->done = 4;
         else sc->alpha = sc->rho / pq;
@@ -244,7 +256,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 4) k_spmv_dot(D
 // B: x += alpha p, r -= alpha q, rho = <r~, r~>, rr = sum dg r~^2; last CTA: beta, stop test.
 // PAR: p lives in the buffer that a fused p-update kernel just wrote (the other half of a double
 // buffer of stride 3N, chosen by the device-side parity), and the parity flips at the end.
-template <typename T, int V, int NC, bool PAR = false>
+// XD: x is left alone and alpha is handed on in sc->ax to the next p update (or to the finish or
+// correction kernel when the solve stops here).
+template <typename T, int V, int NC, bool PAR = false, bool XD = false>
 __global__ void __launch_bounds__(kThreads) k_update(Dims d, T* __restrict__ x,
                                                      const T* __restrict__ p_in, T* __restrict__ r,
                                                      const T* __restrict__ q,
@@ -263,18 +277,22 @@ __global__ void __launch_bounds__(kThreads) k_update(Dims d, T* __restrict__ x,
         zerov<T, V>(rs);
 #pragma unroll
         for (int k = 0; k < NC; k++) {
-            T xv[V], pv[V], rv[V], qv[V];
-            ldv<T, V>(x + k * d.N + off, xv);
-            ldv<T, V>(p + k * d.N + off, pv);
+            T rv[V], qv[V];
             ldv<T, V>(r + k * d.N + off, rv);
             ldv<T, V>(q + k * d.N + off, qv);
+            if constexpr (!XD) {
+                T xv[V], pv[V];
+                ldv<T, V>(x + k * d.N + off, xv);
+                ldv<T, V>(p + k * d.N + off, pv);
+#pragma unroll
+                for (int e = 0; e < V; e++) xv[e] = fma(al, pv[e], xv[e]);
+                stv<T, V>(x + k * d.N + off, xv);
+            }
 #pragma unroll
             for (int e = 0; e < V; e++) {
-                xv[e] = fma(al, pv[e], xv[e]);
                 rv[e] = fma(-al, qv[e], rv[e]);
                 rs[e] = fma(rv[e], rv[e], rs[e]);
             }
-            stv<T, V>(x + k * d.N + off, xv);
             stv<T, V>(r + k * d.N + off, rv);
         }
         T cell = rs[0];
@@ -292,6 +310,7 @@ __global__ void __launch_bounds__(kThreads) k_update(Dims d, T* __restrict__ x,
         sc->beta = rho / sc->rho;
         sc->rho = rho;
         sc->rr = rr;
+        if (XD) sc->ax = sc->alpha;
         if (PAR) sc->par = 1 - sc->par;
         if (!finite(rr) || !finite(rho)) sc->done = 3;
         else if (sqrt(rr) <= sc->tol * sqrt(sc->bb)) sc->done = 1;
@@ -466,6 +485,7 @@ __global__ void __launch_bounds__(kThreads) k_init64(Dims d, int nc, const doubl
         sc->total_iter = 0;
         sc->outer = 0;
         sc->par = 0;
+        sc->ax = 0.0;
         if (!finite(out[0]) || !finite(out[1]) || !finite(out[2])) sc->done = 3;
         else if (out[2] == 0.0) sc->done = 1;
         else if (sqrt(out[1]) <= sc->tol * sqrt(out[2])) sc->done = 1;
@@ -474,16 +494,23 @@ __global__ void __launch_bounds__(kThreads) k_init64(Dims d, int nc, const doubl
     }
 }
 
-// x = s x~ (x = 0 when b = 0)
-__global__ void k_finish64(Dims d, int nc, const double* __restrict__ xs, double* __restrict__ x,
-                           const double* __restrict__ s, const PcgScalars* sc) {
+// x = s (x~ + ax p~) (x = 0 when b = 0); ax is the deferred x update of the last iteration
+__global__ void k_finish64(Dims d, int nc, const double* __restrict__ xs, const double* __restrict__ p,
+                           double* __restrict__ x, const double* __restrict__ s, const PcgScalars* sc) {
     const bool zero = (sc->bb == 0.0);
+    const double ax = sc->ax;
     const unsigned int G = (unsigned int)(d.N / 2);
     const unsigned int npv = d.np / 2;
     for (int k = 0; k < nc; k++)
         for (unsigned int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
             double v[2];
             ldv<double, 2>(xs + k * d.N + (long long)g * 2, v);
+            if (ax != 0.0) {
+                double pv[2];
+                ldv<double, 2>(p + k * d.N + (long long)g * 2, pv);
+                v[0] = fma(ax, pv[0], v[0]);
+                v[1] = fma(ax, pv[1], v[1]);
+            }
             const double sv = s[g / npv];
             v[0] = zero ? 0.0 : sv * v[0];
             v[1] = zero ? 0.0 : sv * v[1];
@@ -555,6 +582,7 @@ __global__ void __launch_bounds__(kThreads) k_outer_res(Dims d, int nc, const do
             sc->par = 0;
         }
         sc->rr_out = out[0];
+        sc->ax = 0.0;   // k_correct has absorbed the deferred x update into x
         // keep the recurrence only while the replaced residual still agrees with the recursive
         // one (rho_true <= 4 rho_recursive); otherwise beta = 0 restarts it (p = r next)
         // (with PC2 the preconditioner pass that follows forms rho = <r, z> and takes this decision)
@@ -575,17 +603,24 @@ __global__ void __launch_bounds__(kThreads) k_outer_res(Dims d, int nc, const do
     }
 }
 
-// x += s x~32 (FP64 correction)
+// x += s (x~32 + ax p~32) (FP64 correction; ax p~32, formed in FP32, is the deferred x update of
+// the last inner iteration)
 __global__ void k_correct(Dims d, int nc, double* __restrict__ x, const float* __restrict__ xs,
-                          const double* __restrict__ s, PcgScalars* sc) {
+                          const float* __restrict__ p, const double* __restrict__ s, PcgScalars* sc) {
     if (sc->outer_done) return;
+    const float ax = (float)sc->ax;
     const unsigned int G = (unsigned int)(d.N / 2);
     const unsigned int npv = d.np / 2;
     for (int k = 0; k < nc; k++)
         for (unsigned int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
             double v[2];
             ldv<double, 2>(x + k * d.N + (long long)g * 2, v);
-            const float2 e = *reinterpret_cast<const float2*>(xs + k * d.N + (long long)g * 2);
+            float2 e = *reinterpret_cast<const float2*>(xs + k * d.N + (long long)g * 2);
+            if (ax != 0.f) {
+                const float2 pv = *reinterpret_cast<const float2*>(p + k * d.N + (long long)g * 2);
+                e.x = fmaf(ax, pv.x, e.x);
+                e.y = fmaf(ax, pv.y, e.y);
+            }
             const double sv = s[g / npv];
             v[0] = fma(sv, (double)e.x, v[0]);
             v[1] = fma(sv, (double)e.y, v[1]);
@@ -651,7 +686,7 @@ void enqueue_split(mhd_grid_s* g, cudaStream_t st, T* x, T* r, T* p, T* q, const
                    int prof0) {
     const Dims d = g->d;
     int s = prof_begin(g, st, prof0);
-    k_pupdate<T, V, NC><<<blocks, kThreads, 0, st>>>(d, r, p, g->sc);
+    k_pupdate<T, V, NC, true><<<blocks, kThreads, 0, st>>>(d, r, p, x, g->sc);
     prof_end(g, st, s);
     s = prof_begin(g, st, prof0 + 1);
     // the FP32 stencil is latency-bound: 6 CTAs per SM instead of 4 for more loads in flight
@@ -659,7 +694,7 @@ void enqueue_split(mhd_grid_s* g, cudaStream_t st, T* x, T* r, T* p, T* q, const
     k_spmv_dot<T, V, NC><<<bs, kThreads, 0, st>>>(d, p, q, t, g->sc, g->partials);
     prof_end(g, st, s);
     s = prof_begin(g, st, prof0 + 2);
-    k_update<T, V, NC><<<blocks, kThreads, 0, st>>>(d, x, p, r, q, g->tu.dg, g->sc, g->partials);
+    k_update<T, V, NC, false, true><<<blocks, kThreads, 0, st>>>(d, x, p, r, q, g->tu.dg, g->sc, g->partials);
     prof_end(g, st, s);
 }
 
@@ -689,7 +724,7 @@ void enqueue_pc2(mhd_grid_s* g, cudaStream_t st, int blocks) {
     const Dims d = g->d;
     double* z = g->p64 + 3 * (size_t)d.N;
     int ps = prof_begin(g, st, MHD_KERNEL_PUPDATE64);
-    k_pupdate<double, 2, NC><<<blocks, kThreads, 0, st>>>(d, z, g->p64, g->sc);
+    k_pupdate<double, 2, NC><<<blocks, kThreads, 0, st>>>(d, z, g->p64, nullptr, g->sc);
     prof_end(g, st, ps);
     ps = prof_begin(g, st, MHD_KERNEL_SPMV64);
     k_spmv_dot<double, 2, NC><<<blocks, kThreads, 0, st>>>(d, g->p64, g->q64, g->t64, g->sc, g->partials);
@@ -705,7 +740,8 @@ void enqueue_pc2_32(mhd_grid_s* g, cudaStream_t st) {
     const Dims d = g->d;
     float* z = g->p32 + 3 * (size_t)d.N;
     int ps = prof_begin(g, st, MHD_KERNEL_PUPDATE32);
-    k_pupdate<float, V, NC><<<grid_blocks(g, d.N / V, kPerSmIter), kThreads, 0, st>>>(d, z, g->p32, g->sc);
+    k_pupdate<float, V, NC, true><<<grid_blocks(g, d.N / V, kPerSmIter), kThreads, 0, st>>>(d, z, g->p32, g->x32,
+                                                                                            g->sc);
     prof_end(g, st, ps);
     ps = prof_begin(g, st, MHD_KERNEL_SPMV32);
     k_spmv_dot<float, V, NC><<<grid_blocks(g, d.N / V, 6), kThreads, 0, st>>>(d, g->p32, g->q32, g->t32, g->sc,
@@ -832,6 +868,7 @@ __global__ void k_setup(PcgScalars* sc, double tol, double inner_tol, int max_it
     sc->rr_out = 0.0;
     sc->rho_prev = 0.0;
     sc->par = 0;
+    sc->ax = 0.0;
     sc->count = 0u;
 }
 
@@ -861,6 +898,7 @@ __global__ void k_tune_reset(PcgScalars* sc) {
     sc->iter = 0;
     sc->max_iter = 1 << 30;
     sc->par = 0;
+    sc->ax = 0.0;
     sc->count = 0u;
 }
 
@@ -1002,7 +1040,7 @@ mhd_status_t solve(mhd_grid_s* g, const double* alpha_dev, int nc, const double*
         }
         st = run_iterations(g, pc2 ? 3 : (prm->pcg_variant == 1 ? 2 : 0), nc);
         if (st != MHD_OK) return st;
-        k_finish64<<<blocks2, kThreads, 0, g->stream>>>(d, nc, g->x64, x, g->t64.s, g->sc);
+        k_finish64<<<blocks2, kThreads, 0, g->stream>>>(d, nc, g->x64, g->p64, x, g->t64.s, g->sc);
         if ((st = check_cuda(g, "pcg finish")) != MHD_OK) return st;
         if (read_scalars(g) != MHD_OK) return MHD_ERR_CUDA;
         const PcgScalars& h = *g->h_sc;
@@ -1040,7 +1078,7 @@ mhd_status_t solve(mhd_grid_s* g, const double* alpha_dev, int nc, const double*
         if (st != MHD_OK) return st;
         k_inner_end<<<1, 1, 0, g->stream>>>(g->sc, saved);
         if (g->h_sc->done == 3) break;
-        k_correct<<<blocks2, kThreads, 0, g->stream>>>(d, nc, x, g->x32, g->t64.s, g->sc);
+        k_correct<<<blocks2, kThreads, 0, g->stream>>>(d, nc, x, g->x32, g->p32, g->t64.s, g->sc);
         if ((st = check_cuda(g, "correction")) != MHD_OK) return st;
     }
     if (read_scalars(g) != MHD_OK) return MHD_ERR_CUDA;
