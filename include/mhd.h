@@ -256,7 +256,8 @@ enum {
     MHD_KERNEL_PUPDATE32 = 3, MHD_KERNEL_SPMV32 = 4, MHD_KERNEL_UPDATE32 = 5,
     MHD_KERNEL_OUTER_RES = 6, MHD_KERNEL_FORCE = 7, MHD_KERNEL_INDUCTION = 8,
     MHD_KERNEL_COEFFS = 9, MHD_KERNEL_STS = 10, MHD_KERNEL_RES = 11, MHD_KERNEL_PC2 = 12,
-    MHD_KERNEL_COUNT = 13
+    MHD_KERNEL_PSPMV32 = 13, /* FP32 p update folded into the stencil */
+    MHD_KERNEL_COUNT = 14
 };
 mhd_status_t mhd_profile_enable(mhd_grid_t grid, int enable);
 /* Total milliseconds and launch count of one kernel id since profiling was enabled.

@@ -251,7 +251,8 @@ struct mhd_grid_s {
     // single-reduction, FP64 PC2, FP32 inner PC2) and ncomp
     cudaGraphExec_t iter_graph[5][4];
     int graph_batch;
-    int slab32;             // r-slab length of the tiled FP32 kernels (0: not tuned, -1: split kernels)
+    int slab32;             // FP32 CG kernels: r-slab length of the tiled pair (> 0), split kernels (-1),
+                            // p update folded into the stencil (-2); 0: not tuned
     int slab64;             // same for the FP64 fused p-update + stencil kernel
     double visc_lambda_unit; // Gershgorin bound on the spectral radius of D^-1 K (nu = 1)
     std::string last_error;

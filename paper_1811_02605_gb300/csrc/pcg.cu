@@ -253,6 +253,98 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 4) k_spmv_dot(D
     }
 }
 
+// A1+A2 for the FP32 inner iteration in one pass: p~ = r~ + beta p~_old is formed at the cell and,
+// from r~ and p~_old, at each of its six neighbours (the same fma as the p update kernel, so every
+// value equals the one its own thread stores); the cell's p~ goes to the other half of the p double
+// buffer (sc->par names the half holding the current p~; the update kernel flips it), x~ gets the
+// deferred ax p~_old, and q~ = A~ p~ with <p~, q~>. Per cell: r~, p~_old and x~ in; p~, x~ and q~
+// out (6 passes against the 8 of the separate p update and stencil); the neighbour reads are L1 and
+// L2 hits. Last CTA: alpha = rho / <p~, q~>.
+template <int V, int NC>
+__global__ void __launch_bounds__(kThreads, 4) k_pspmv32(Dims d, const float* __restrict__ r,
+                                                         float* __restrict__ pbuf, float* __restrict__ x,
+                                                         float* __restrict__ q, OpTab<float> t, PcgScalars* sc,
+                                                         double* __restrict__ partials) {
+    if (sc->done) return;
+    const int par = sc->par;
+    const float* __restrict__ pold = pbuf + (long long)par * 3 * d.N;
+    float* __restrict__ pnew = pbuf + (long long)(1 - par) * 3 * d.N;
+    const float beta = (float)sc->beta, ax = (float)sc->ax;
+    const int nt = d.nt;
+    const long long plane = (long long)nt * d.np;
+    const unsigned int G = (unsigned int)(d.N / V);
+    Acc<float> acc;
+    for (unsigned int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+        const Cell c = decompose<V>(d, g);
+        const float cr_lo = t.ar[c.i * nt + c.j], cr_hi = t.ar[(c.i + 1) * nt + c.j];
+        const float ct_lo = t.at[c.i * (nt + 1) + c.j], ct_hi = t.at[c.i * (nt + 1) + c.j + 1];
+        const float cp = t.ap[c.ij];
+        const long long row = c.base - c.k0;
+        const int km = (c.k0 == 0) ? d.np - 1 : c.k0 - 1;
+        const int kp = (c.k0 + V == d.np) ? 0 : c.k0 + V;
+#pragma unroll 1
+        for (int k = 0; k < NC; k++) {
+            const float* rk = r + k * d.N;
+            const float* pk = pold + k * d.N;
+            float rv[V], pv[V], xv[V], v[V], o[V], nr_[V], np_[V];
+            ldv<float, V>(rk + c.base, rv);
+            ldv<float, V>(pk + c.base, pv);
+            ldv<float, V>(x + k * d.N + c.base, xv);
+#pragma unroll
+            for (int e = 0; e < V; e++) {
+                v[e] = fmaf(beta, pv[e], rv[e]);
+                xv[e] = fmaf(ax, pv[e], xv[e]);
+            }
+            stv<float, V>(x + k * d.N + c.base, xv);
+            stv<float, V>(pnew + k * d.N + c.base, v);
+            const float ukm = fmaf(beta, pk[row + km], rk[row + km]);
+            const float ukp = fmaf(beta, pk[row + kp], rk[row + kp]);
+#pragma unroll
+            for (int e = 0; e < V; e++) {
+                const float left = (e == 0) ? ukm : v[e - 1];
+                const float right = (e == V - 1) ? ukp : v[e + 1];
+                o[e] = fmaf(-cp, left + right, v[e]);
+            }
+            if (c.i > 0) {
+                ldv<float, V>(rk + c.base - plane, nr_);
+                ldv<float, V>(pk + c.base - plane, np_);
+#pragma unroll
+                for (int e = 0; e < V; e++) o[e] = fmaf(-cr_lo, fmaf(beta, np_[e], nr_[e]), o[e]);
+            }
+            if (c.i < d.nr - 1) {
+                ldv<float, V>(rk + c.base + plane, nr_);
+                ldv<float, V>(pk + c.base + plane, np_);
+#pragma unroll
+                for (int e = 0; e < V; e++) o[e] = fmaf(-cr_hi, fmaf(beta, np_[e], nr_[e]), o[e]);
+            }
+            if (c.j > 0) {
+                ldv<float, V>(rk + c.base - d.np, nr_);
+                ldv<float, V>(pk + c.base - d.np, np_);
+#pragma unroll
+                for (int e = 0; e < V; e++) o[e] = fmaf(-ct_lo, fmaf(beta, np_[e], nr_[e]), o[e]);
+            }
+            if (c.j < d.nt - 1) {
+                ldv<float, V>(rk + c.base + d.np, nr_);
+                ldv<float, V>(pk + c.base + d.np, np_);
+#pragma unroll
+                for (int e = 0; e < V; e++) o[e] = fmaf(-ct_hi, fmaf(beta, np_[e], nr_[e]), o[e]);
+            }
+            stv<float, V>(q + k * d.N + c.base, o);
+#pragma unroll
+            for (int e = 0; e < V; e++) acc.fma_add(v[e], o[e]);
+        }
+    }
+    double val[1] = {acc.get()}, out[1];
+    if (reduce_last<1>(val, partials, &sc->count, out) && threadIdx.x == 0) {
+        const double pq = out[0];
+        sc->pq = pq;
+        sc->ax = 0.0;   // applied above
+        if (!finite(pq)) sc->done = 3;
+        else if (!(pq > 0.0)) sc->done = 4;
+        else sc->alpha = sc->rho / pq;
+    }
+}
+
 // B: x += alpha p, r -= alpha q, rho = <r~, r~>, rr = sum dg r~^2; last CTA: beta, stop test.
 // PAR: p lives in the buffer that a fused p-update kernel just wrote (the other half of a double
 // buffer of stride 3N, chosen by the device-side parity), and the parity flips at the end.
@@ -609,6 +701,7 @@ __global__ void k_correct(Dims d, int nc, double* __restrict__ x, const float* _
                           const float* __restrict__ p, const double* __restrict__ s, PcgScalars* sc) {
     if (sc->outer_done) return;
     const float ax = (float)sc->ax;
+    p += (long long)sc->par * 3 * d.N;   // the half of the p double buffer holding the current p~
     const unsigned int G = (unsigned int)(d.N / 2);
     const unsigned int npv = d.np / 2;
     for (int k = 0; k < nc; k++)
@@ -696,6 +789,27 @@ void enqueue_split(mhd_grid_s* g, cudaStream_t st, T* x, T* r, T* p, T* q, const
     s = prof_begin(g, st, prof0 + 2);
     k_update<T, V, NC, false, true><<<blocks, kThreads, 0, st>>>(d, x, p, r, q, g->tu.dg, g->sc, g->partials);
     prof_end(g, st, s);
+}
+
+// FP32 inner iteration with the p update folded into the stencil (p~ double-buffered)
+template <int V, int NC>
+void enqueue_fused32(mhd_grid_s* g, cudaStream_t st) {
+    const Dims d = g->d;
+    int s = prof_begin(g, st, MHD_KERNEL_PSPMV32);
+    k_pspmv32<V, NC><<<grid_blocks(g, d.N / V, 4), kThreads, 0, st>>>(d, g->r32, g->p32, g->x32, g->q32, g->t32,
+                                                                      g->sc, g->partials);
+    prof_end(g, st, s);
+    s = prof_begin(g, st, MHD_KERNEL_UPDATE32);
+    k_update<float, V, NC, true, true><<<grid_blocks(g, d.N / V, kPerSmIter), kThreads, 0, st>>>(
+        d, g->x32, g->p32, g->r32, g->q32, g->tu.dg, g->sc, g->partials);
+    prof_end(g, st, s);
+}
+
+template <int V>
+void enqueue_fused32_nc(mhd_grid_s* g, cudaStream_t st, int nc) {
+    if (nc == 3) enqueue_fused32<V, 3>(g, st);
+    else if (nc == 2) enqueue_fused32<V, 2>(g, st);
+    else enqueue_fused32<V, 1>(g, st);
 }
 
 template <typename T, int V>
@@ -787,6 +901,10 @@ void enqueue_iteration(mhd_grid_s* g, cudaStream_t st, int prec, int nc) {
     } else if (prec == 0) {
         enqueue_split_nc<double, 2>(g, st, nc, g->x64, g->r64, g->p64, g->q64, g->t64,
                                     grid_blocks(g, d.N / 2, kPerSmIter), MHD_KERNEL_PUPDATE64);
+    } else if (g->slab32 == -2) {
+        // p update folded into the stencil, when the autotuner measured it fastest
+        if (use_v4(g)) enqueue_fused32_nc<4>(g, st, nc);
+        else enqueue_fused32_nc<2>(g, st, nc);
     } else if (tiled32_ok(g) && g->slab32 > 0) {
         // plane-marching pair, when the autotuner measured it faster than the split kernels
         enqueue_tiled32(g, st, nc, g->slab32, MHD_KERNEL_SPMV32, MHD_KERNEL_UPDATE32);
@@ -905,16 +1023,18 @@ __global__ void k_tune_reset(PcgScalars* sc) {
 // choose the r-slab length of the tiled FP32 kernels by timing a few iterations of each
 // candidate (alpha = beta = 0, so the vectors are left as they are); run before a solve sets up
 // its scalars
-// Diagnostics: MHD_FORCE_SLAB=<n> skips the timing and uses slab n (-1: split kernels).
+// Diagnostics: MHD_FORCE_SLAB=<n> skips the timing and uses slab n (-1: split kernels, -2 (FP32
+// only): the p update folded into the stencil).
 int forced_slab() {
     const char* f = std::getenv("MHD_FORCE_SLAB");
     return f ? (int)std::strtol(f, nullptr, 10) : 0;
 }
 
 mhd_status_t tune_slab32(mhd_grid_s* g, int nc) {
-    if (!tiled32_ok(g) || g->slab32 > 0) return MHD_OK;
+    if (g->slab32 != 0) return MHD_OK;
     if (const int f = forced_slab()) {
-        g->slab32 = (f > 0 && tiled32_blocks(g, f) <= kMaxBlocks) ? f : -1;
+        if (f == -2) g->slab32 = -2;
+        else g->slab32 = (f > 0 && tiled32_ok(g) && tiled32_blocks(g, f) <= kMaxBlocks) ? f : -1;
         return MHD_OK;
     }
     cudaEvent_t e0, e1;
@@ -923,29 +1043,33 @@ mhd_status_t tune_slab32(mhd_grid_s* g, int nc) {
     float best_ms = 1e30f;
     const int prof = g->prof;
     g->prof = 0;
-    // candidate -1: the split kernels (p update, stencil, update)
-    {
+    // positive finite vectors (bytes 0x3F: 0.747f) so the timed iterations do real work and no
+    // reduction trips a breakdown flag (the solve's set-up overwrites every vector afterwards)
+    const size_t n3 = 3 * (size_t)g->d.N;
+    // candidates -1: the split kernels (p update, stencil, update); -2: the p update folded into
+    // the stencil, then the update
+    for (int cand : {-1, -2}) {
         k_tune_reset<<<1, 1, 0, g->stream>>>(g->sc);
-        g->slab32 = -1;
-        cudaMemsetAsync(g->r32, 0x3F, sizeof(float) * 3 * (size_t)g->d.N, g->stream);
-        cudaMemsetAsync(g->p32, 0x3F, sizeof(float) * 6 * (size_t)g->d.N, g->stream);
+        g->slab32 = cand;
+        cudaMemsetAsync(g->r32, 0x3F, sizeof(float) * n3, g->stream);
+        cudaMemsetAsync(g->p32, 0x3F, sizeof(float) * 2 * n3, g->stream);
+        cudaMemsetAsync(g->x32, 0, sizeof(float) * n3, g->stream);
         enqueue_iteration(g, g->stream, 1, nc);
         cudaEventRecord(e0, g->stream);
         for (int it = 0; it < 3; it++) enqueue_iteration(g, g->stream, 1, nc);
         cudaEventRecord(e1, g->stream);
-        if (cudaEventSynchronize(e1) == cudaSuccess) {
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
+        if (cudaEventSynchronize(e1) != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
             best_ms = ms;
-            best = -1;
+            best = cand;
         }
     }
-    // positive finite vectors (bytes 0x3F: 0.747f) so the timed iterations do real work and no
-    // reduction trips a breakdown flag; x stays unchanged because alpha = 0
-    const size_t n3 = 3 * (size_t)g->d.N;
     cudaMemsetAsync(g->r32, 0x3F, sizeof(float) * n3, g->stream);
     cudaMemsetAsync(g->p32, 0x3F, sizeof(float) * 2 * n3, g->stream);
     for (int slab : {8, 16, 32, 64}) {
+        if (!tiled32_ok(g)) break;
         if (slab > 2 * g->d.nr && best > 0) break;
         if (tiled32_blocks(g, slab) > kMaxBlocks) continue;
         k_tune_reset<<<1, 1, 0, g->stream>>>(g->sc);
@@ -964,8 +1088,8 @@ mhd_status_t tune_slab32(mhd_grid_s* g, int nc) {
     g->prof = prof;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (best == 0) return set_error(g, MHD_ERR_CUDA, "tiled FP32 kernels: no launchable variant");
-    g->slab32 = best;  // -1: split kernels are faster on this grid
+    if (best == 0) return set_error(g, MHD_ERR_CUDA, "FP32 CG kernels: no launchable variant");
+    g->slab32 = best;  // -1: split kernels, -2: p update folded into the stencil, > 0: tiled slab
     return check_cuda(g, "tune slab");
 }
 }  // namespace

@@ -1,0 +1,80 @@
+"""The FP32 inner-iteration variants of mixed-precision PCG, each forced in turn (MHD_FORCE_SLAB is
+read when a grid tunes its FP32 kernels): -1 the split kernels (p update, stencil, update), -2 the p
+update folded into the stencil with p double-buffered, 16 the plane-marching pair. Each must reach
+the FP64 tolerance on the true residual and agree with the oracle's FP64 solution (Sec. 2.2 PCG;
+mixed precision is the FP32-inner / FP64-refinement reading of the solver)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_1811_02605_gb300 as P
+from paper_1811_02605_gb300 import inputs as I
+from tests.gpu_util import grid, rel_l2, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+def _system(d, seed):
+    og = O.Grid.from_desc(d)
+    rng = np.random.default_rng(seed)
+    b = rng.normal(size=(3, d.nr, d.nt, d.np)) * og.volumes()[None, :, :, None]
+    return og, b
+
+
+@pytest.mark.parametrize("variant", ["-1", "-2", "16"])
+@pytest.mark.parametrize("restart,inner", [(0, 0.1), (1, 1e-5)])
+def test_mixed_variant_matches_fp64_oracle(monkeypatch, variant, restart, inner):
+    # np = 256 (float4 groups, plane-marching tiles possible); nt = 18 leaves a ragged row tile
+    d = I.GridDesc(20, 18, 256, 1.0, 10.0, 1.05)
+    monkeypatch.setenv("MHD_FORCE_SLAB", variant)
+    g = grid(d)
+    og, b = _system(d, 31)
+    alpha = 2.0
+    xr, itr, _, _ = og.pcg(alpha, b, tol=1e-13)
+    prm = P.make_params(tol=1e-9, inner_tol=inner, precision=P.PREC_MIXED, max_outer=60, max_iter=5000,
+                        mixed_restart=restart)
+    for nc in (3, 1, 2):
+        x = torch.zeros((nc,) + b.shape[1:], dtype=torch.float64, device="cuda")
+        st, it, ou, rr = P.pcg_solve(g, alpha, to_dev(b[:nc]), x, prm)
+        assert st == P.MHD_OK and rr <= 1e-9, (variant, nc, st, rr)
+        res = b[:nc] - og.apply_M(alpha, to_np(x))
+        assert np.linalg.norm(res) <= 1e-9 * np.linalg.norm(b[:nc]) * 1.0000001
+        ref = xr if nc == 3 else og.pcg(alpha, b[:nc], tol=1e-13)[0]
+        assert rel_l2(to_np(x), ref) < 1e-6, (variant, nc)
+
+
+def test_fused_variant_float2_groups_and_nonzero_start(monkeypatch):
+    # np = 250: not a multiple of 4, so the FP32 kernels work on float2 groups; x0 != 0
+    d = I.GridDesc(12, 14, 250, 1.0, 6.0, 1.04)
+    monkeypatch.setenv("MHD_FORCE_SLAB", "-2")
+    g = grid(d)
+    og, b = _system(d, 32)
+    rng = np.random.default_rng(33)
+    x0 = rng.normal(size=b.shape) * 0.05
+    for alpha in (0.4, 7.0):
+        xr, _, _, _ = og.pcg(alpha, b, x0=x0, tol=1e-13)
+        x = to_dev(x0)
+        prm = P.make_params(tol=1e-9, inner_tol=0.1, precision=P.PREC_MIXED, max_outer=60, max_iter=5000)
+        st, it, ou, rr = P.pcg_solve(g, alpha, to_dev(b), x, prm)
+        assert st == P.MHD_OK and rr <= 1e-9
+        assert rel_l2(to_np(x), xr) < 1e-6, alpha
+
+
+def test_fused_and_split_take_the_same_iterations(monkeypatch):
+    # the fused kernel forms every p value with the same fma as the p update kernel, so the two
+    # variants differ only in the reduction order of <p, q> (launch shape): iteration and
+    # correction counts agree to within one
+    d = I.GridDesc(24, 20, 128, 1.0, 10.0, 1.05)
+    og, b = _system(d, 34)
+    out = {}
+    for variant in ("-1", "-2"):
+        monkeypatch.setenv("MHD_FORCE_SLAB", variant)
+        g = grid(d)
+        x = torch.zeros(b.shape, dtype=torch.float64, device="cuda")
+        prm = P.make_params(tol=1e-9, inner_tol=0.1, precision=P.PREC_MIXED, max_outer=60, max_iter=5000)
+        st, it, ou, rr = P.pcg_solve(g, 3.0, to_dev(b), x, prm)
+        assert st == P.MHD_OK
+        out[variant] = (it, ou, to_np(x))
+    assert abs(out["-1"][0] - out["-2"][0]) <= 1 and abs(out["-1"][1] - out["-2"][1]) <= 1
+    assert rel_l2(out["-2"][2], out["-1"][2]) < 1e-6
