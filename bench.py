@@ -417,7 +417,8 @@ def run_ours(args):
                         pcg_iters_per_step=[sum(i["iters"][q] for i in infosp) / len(infosp) for q in range(3)],
                         outer_per_step=sum(sum(i["outer"]) for i in infosp) / len(infosp),
                         max_relres=max(max(i["relres"]) for i in infosp),
-                        kernel_ms_per_iteration={k: round(profp[k][0] / n_it, 4) for k in ("pupdate32", "spmv32", "pc2")},
+                        kernel_ms_per_iteration={k: round(profp[k][0] / n_it, 4)
+                                                 for k in ("pupdate32", "spmv32", "pspmv32", "pc2") if profp[k][1]},
                         rel_l2_vs_fp64_after_steps={k: float(torch.linalg.norm(dsp[k] - ds64[k]) /
                                                              torch.linalg.norm(ds64[k])) for k in ds64},
                         clocks=clkp, kernel_ms={k: round(v[0], 3) for k, v in profp.items() if v[1]})

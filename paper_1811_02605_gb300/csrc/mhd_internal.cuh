@@ -254,6 +254,7 @@ struct mhd_grid_s {
     int slab32;             // FP32 CG kernels: r-slab length of the tiled pair (> 0), split kernels (-1),
                             // p update folded into the stencil (-2); 0: not tuned
     int slab64;             // same for the FP64 fused p-update + stencil kernel
+    int pc2_fused32;        // FP32 PC2 iteration: p update folded into the stencil (1) or split (-1); 0: unset
     double visc_lambda_unit; // Gershgorin bound on the spectral radius of D^-1 K (nu = 1)
     std::string last_error;
     // kernel timing (diagnostics)
@@ -298,6 +299,7 @@ void pc2_init64(mhd_grid_s* g, int nc);
 void pc2_reliable32(mhd_grid_s* g, int nc, int restart);
 void pc2_enqueue_line(mhd_grid_s* g, cudaStream_t st, int nc, bool fp32);
 void pc2_free(mhd_grid_s* g);
+float* pc2_z32(mhd_grid_s* g);   // z~ of the FP32 PC2 iteration (3N floats, PC2 workspace)
 int sts_advance(mhd_grid_s* g, double nu, const double* dt_dev, double dt_host, double* y);
 
 // tiled FP32 CG kernels (tiled.cu)

@@ -40,6 +40,7 @@ enum { kIter = 0, kInit = 1, kReliable = 2 };
 struct Pc2Work {
     double* idt;      // [N] 1 / dt of the scaled lines (FP64)
     float* idt32;     // [N] the same in FP32
+    float* z32;       // [3N] z~ of the FP32 iteration (the p double buffer keeps both halves for p~)
     int warps[2];     // warps per CTA of the line kernel, [0] FP64, [1] FP32
     size_t smem[2];   // its dynamic shared memory
     int line_blocks[2];
@@ -335,17 +336,22 @@ mhd_status_t pc2_workspace(mhd_grid_s* g, Pc2Work** out) {
     auto* w = new Pc2Work{};
     const size_t N = (size_t)g->d.N;
     if (cudaMalloc(&w->idt, sizeof(double) * N) != cudaSuccess ||
-        cudaMalloc(&w->idt32, sizeof(float) * N) != cudaSuccess) {
+        cudaMalloc(&w->idt32, sizeof(float) * N) != cudaSuccess ||
+        cudaMalloc(&w->z32, sizeof(float) * 3 * N) != cudaSuccess) {
         if (w->idt) cudaFree(w->idt);
+        if (w->idt32) cudaFree(w->idt32);
         delete w;
         cudaGetLastError();
         return set_error(g, MHD_ERR_OOM, "PC2: workspace allocation failed");
     }
     mhd_status_t st = line_shape<double>(g, w, 0);
     if (st == MHD_OK) st = line_shape<float>(g, w, 1);
+    if (st == MHD_OK && cudaMemsetAsync(w->z32, 0, sizeof(float) * 3 * N, g->stream) != cudaSuccess)
+        st = check_cuda(g, "PC2: workspace clear");
     if (st != MHD_OK) {
         cudaFree(w->idt);
         cudaFree(w->idt32);
+        cudaFree(w->z32);
         delete w;
         return st;
     }
@@ -368,7 +374,10 @@ void launch_seg(mhd_grid_s* g, cudaStream_t st, const Pc2Work* w, int nc, int re
     } else {
         x = g->x32; p = g->p32; r = g->r32; q = g->q32; idt = w->idt32; t = g->t32;
     }
-    T* z = p + 3 * (size_t)d.N;   // second half of the p double buffer
+    // z~: FP64 in the second half of the p double buffer, FP32 in the workspace
+    T* z;
+    if constexpr (sizeof(T) == 8) z = p + 3 * (size_t)d.N;
+    else z = w->z32;
     if (nc == 3)
         k_pc2_line<T, 3, MODE, SEG><<<grid, block, sm, st>>>(d, t, g->tu.dg, idt, x, p, r, q, z, g->sc, g->partials,
                                                               restart);
@@ -394,9 +403,12 @@ void pc2_free(mhd_grid_s* g) {
     auto* w = reinterpret_cast<Pc2Work*>(g->pc2_mem);
     cudaFree(w->idt);
     cudaFree(w->idt32);
+    cudaFree(w->z32);
     delete w;
     g->pc2_mem = nullptr;
 }
+
+float* pc2_z32(mhd_grid_s* g) { return reinterpret_cast<Pc2Work*>(g->pc2_mem)->z32; }
 
 // factorise the lines of A~ for the current tables (FP64 and FP32 copies)
 mhd_status_t pc2_factor(mhd_grid_s* g) {

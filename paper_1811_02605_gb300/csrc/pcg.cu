@@ -256,10 +256,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 4) k_spmv_dot(D
 // A1+A2 for the FP32 inner iteration in one pass: p~ = r~ + beta p~_old is formed at the cell and,
 // from r~ and p~_old, at each of its six neighbours (the same fma as the p update kernel, so every
 // value equals the one its own thread stores); the cell's p~ goes to the other half of the p double
-// buffer (sc->par names the half holding the current p~; the update kernel flips it), x~ gets the
-// deferred ax p~_old, and q~ = A~ p~ with <p~, q~>. Per cell: r~, p~_old and x~ in; p~, x~ and q~
-// out (6 passes against the 8 of the separate p update and stencil); the neighbour reads are L1 and
-// L2 hits. Last CTA: alpha = rho / <p~, q~>.
+// buffer (sc->par names the half holding the current p~), x~ gets the deferred ax p~_old, and
+// q~ = A~ p~ with <p~, q~>. Per cell: r~ (with PC2: z~), p~_old and x~ in; p~, x~ and q~ out (6
+// passes against the 8 of the separate p update and stencil); the neighbour reads are L1 and L2
+// hits. Last CTA: alpha = rho / <p~, q~>, and par flips (every CTA read it at its start).
 template <int V, int NC>
 __global__ void __launch_bounds__(kThreads, 4) k_pspmv32(Dims d, const float* __restrict__ r,
                                                          float* __restrict__ pbuf, float* __restrict__ x,
@@ -339,6 +339,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_pspmv32(Dims d, const float* __
         const double pq = out[0];
         sc->pq = pq;
         sc->ax = 0.0;   // applied above
+        sc->par = 1 - par;
         if (!finite(pq)) sc->done = 3;
         else if (!(pq > 0.0)) sc->done = 4;
         else sc->alpha = sc->rho / pq;
@@ -800,7 +801,7 @@ void enqueue_fused32(mhd_grid_s* g, cudaStream_t st) {
                                                                       g->sc, g->partials);
     prof_end(g, st, s);
     s = prof_begin(g, st, MHD_KERNEL_UPDATE32);
-    k_update<float, V, NC, true, true><<<grid_blocks(g, d.N / V, kPerSmIter), kThreads, 0, st>>>(
+    k_update<float, V, NC, false, true><<<grid_blocks(g, d.N / V, kPerSmIter), kThreads, 0, st>>>(
         d, g->x32, g->p32, g->r32, g->q32, g->tu.dg, g->sc, g->partials);
     prof_end(g, st, s);
 }
@@ -848,20 +849,28 @@ void enqueue_pc2(mhd_grid_s* g, cudaStream_t st, int blocks) {
     prof_end(g, st, ps);
 }
 
-// the same for the FP32 inner solves of mixed precision
+// the same for the FP32 inner solves of mixed precision; z~ lives in the PC2 workspace, and with
+// the fused variant p~ alternates between the two halves of the p double buffer
 template <typename T, int V, int NC>
 void enqueue_pc2_32(mhd_grid_s* g, cudaStream_t st) {
     const Dims d = g->d;
-    float* z = g->p32 + 3 * (size_t)d.N;
-    int ps = prof_begin(g, st, MHD_KERNEL_PUPDATE32);
-    k_pupdate<float, V, NC, true><<<grid_blocks(g, d.N / V, kPerSmIter), kThreads, 0, st>>>(d, z, g->p32, g->x32,
-                                                                                            g->sc);
-    prof_end(g, st, ps);
-    ps = prof_begin(g, st, MHD_KERNEL_SPMV32);
-    k_spmv_dot<float, V, NC><<<grid_blocks(g, d.N / V, 6), kThreads, 0, st>>>(d, g->p32, g->q32, g->t32, g->sc,
-                                                                              g->partials);
-    prof_end(g, st, ps);
-    ps = prof_begin(g, st, MHD_KERNEL_PC2);
+    float* z = pc2_z32(g);
+    if (g->pc2_fused32 > 0) {
+        const int ps = prof_begin(g, st, MHD_KERNEL_PSPMV32);
+        k_pspmv32<V, NC><<<grid_blocks(g, d.N / V, 4), kThreads, 0, st>>>(d, z, g->p32, g->x32, g->q32, g->t32, g->sc,
+                                                                          g->partials);
+        prof_end(g, st, ps);
+    } else {
+        int ps = prof_begin(g, st, MHD_KERNEL_PUPDATE32);
+        k_pupdate<float, V, NC, true><<<grid_blocks(g, d.N / V, kPerSmIter), kThreads, 0, st>>>(d, z, g->p32, g->x32,
+                                                                                                g->sc);
+        prof_end(g, st, ps);
+        ps = prof_begin(g, st, MHD_KERNEL_SPMV32);
+        k_spmv_dot<float, V, NC><<<grid_blocks(g, d.N / V, 6), kThreads, 0, st>>>(d, g->p32, g->q32, g->t32, g->sc,
+                                                                                  g->partials);
+        prof_end(g, st, ps);
+    }
+    const int ps = prof_begin(g, st, MHD_KERNEL_PC2);
     pc2_enqueue_line(g, st, NC, true);
     prof_end(g, st, ps);
 }
@@ -1183,6 +1192,9 @@ mhd_status_t solve(mhd_grid_s* g, const double* alpha_dev, int nc, const double*
     if (pc2) {
         mhd_status_t st = pc2_factor(g);
         if (st != MHD_OK) return st;
+        // the FP32 PC2 iteration folds the p update into the stencil unless the split kernels are
+        // forced (MHD_FORCE_SLAB=-1): measured faster at every size tried
+        if (g->pc2_fused32 == 0) g->pc2_fused32 = (forced_slab() == -1) ? -1 : 1;
     }
     int outer_done = 0;
     for (int o = 0; o <= prm->max_outer; o++) {

@@ -78,3 +78,27 @@ def test_fused_and_split_take_the_same_iterations(monkeypatch):
         out[variant] = (it, ou, to_np(x))
     assert abs(out["-1"][0] - out["-2"][0]) <= 1 and abs(out["-1"][1] - out["-2"][1]) <= 1
     assert rel_l2(out["-2"][2], out["-1"][2]) < 1e-6
+
+
+@pytest.mark.parametrize("variant", ["-1", "-2"])
+@pytest.mark.parametrize("d", [I.GridDesc(10, 12, 64, 1.0, 5.0, 1.06), I.GridDesc(8, 10, 90, 1.0, 4.0, 1.05)],
+                         ids=lambda d: f"{d.nr}x{d.nt}x{d.np}")
+def test_mixed_pc2_variant_matches_fp64_oracle(monkeypatch, variant, d):
+    # the FP32 PC2 iteration with the p update split (-1) or folded into the stencil (-2; z~ in the
+    # PC2 workspace, p~ alternating between the halves of the p double buffer); np = 90 takes the
+    # float2 groups and the generic line kernel
+    monkeypatch.setenv("MHD_FORCE_SLAB", variant)
+    g = grid(d)
+    og, b = _system(d, 35)
+    alpha = 4.0
+    xr, _, _, _ = og.pcg(alpha, b, tol=1e-13, pc2="lines")
+    for restart, inner in ((0, 1e-3), (1, 1e-5)):
+        for nc in (3, 2):
+            x = torch.zeros((nc,) + b.shape[1:], dtype=torch.float64, device="cuda")
+            prm = P.make_params(tol=1e-9, inner_tol=inner, precision=P.PREC_MIXED, max_outer=60, max_iter=5000,
+                                mixed_restart=restart, preconditioner=1)
+            st, it, ou, rr = P.pcg_solve(g, alpha, to_dev(b[:nc]), x, prm)
+            assert st == P.MHD_OK and rr <= 1e-9, (variant, restart, nc, st, rr)
+            res = b[:nc] - og.apply_M(alpha, to_np(x))
+            assert np.linalg.norm(res) <= 1e-9 * np.linalg.norm(b[:nc]) * 1.0000001
+            assert rel_l2(to_np(x), xr[:nc]) < 1e-6, (variant, restart, nc)
