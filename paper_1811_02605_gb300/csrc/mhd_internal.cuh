@@ -272,6 +272,23 @@ namespace mhd {
 // launch helpers
 int grid_blocks(const mhd_grid_s* g, long long work, int per_sm = 4);
 
+// CTAs of kThreads threads that one SM holds at once for kernel K (its registers and static
+// shared memory permitting), looked up once per kernel. A grid-stride kernel launched with more
+// CTAs than fit in one wave, but not a whole number of waves, leaves most SMs idle during the last
+// partial wave; launching exactly one resident wave avoids that.
+template <auto K>
+int resident_per_sm() {
+    static const int n = [] {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, K, kThreads, 0) != cudaSuccess) {
+            cudaGetLastError();
+            b = 1;
+        }
+        return b > 0 ? b : 1;
+    }();
+    return n;
+}
+
 // explicit kernels (explicit.cu)
 mhd_status_t coeffs(mhd_grid_s* g, const mhd_params_t* p, const double* vr, const double* vt,
                     const double* vp, const double* br, const double* bt, const double* bp);

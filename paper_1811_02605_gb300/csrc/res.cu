@@ -504,20 +504,21 @@ void res_current(mhd_grid_s* g, cudaStream_t st, const ResWork* w, const double*
     const double *br = v, *bt = v + z.nbr, *bp = v + z.nbr + z.nbt;
     ring_sums(g, bp, st);
     const long long n = (long long)(d.nr + 1) * (d.nt + 1) * d.np;
-    const int blocks = grid_blocks(g, n, 8);
-    k_res_jr<<<blocks, kThreads, 0, st>>>(d, w->cr, g->ring, bt, bp, g->er);
-    k_res_jt<<<blocks, kThreads, 0, st>>>(d, w->ct, br, bp, g->et);
-    k_res_jp<<<blocks, kThreads, 0, st>>>(d, w->cp, br, bt, g->ep);
+    k_res_jr<<<grid_blocks(g, n, resident_per_sm<k_res_jr>()), kThreads, 0, st>>>(d, w->cr, g->ring, bt, bp, g->er);
+    k_res_jt<<<grid_blocks(g, n, resident_per_sm<k_res_jt>()), kThreads, 0, st>>>(d, w->ct, br, bp, g->et);
+    k_res_jp<<<grid_blocks(g, n, resident_per_sm<k_res_jp>()), kThreads, 0, st>>>(d, w->cp, br, bt, g->ep);
 }
 
 void res_enqueue_iteration(mhd_grid_s* g, cudaStream_t st, ResWork* w) {
     const Dims d = g->d;
     const ResSizes z = res_sizes(d);
-    const int blocks = grid_blocks(g, z.nf, 8);
     res_current(g, st, w, w->p);
-    k_res_apply<<<blocks, kThreads, 0, st>>>(d, w->w, w->co, w->p, g->er, g->et, g->ep, w->q, g->sc, g->partials, z.nf);
-    k_res_update<<<blocks, kThreads, 0, st>>>(d, w->co, w->x, w->p, w->r, w->q, g->sc, g->partials, z.nf);
-    k_res_pupdate<<<blocks, kThreads, 0, st>>>(d, w->co, w->r, w->p, g->sc, z.nf);
+    k_res_apply<<<grid_blocks(g, z.nf, resident_per_sm<k_res_apply>()), kThreads, 0, st>>>(
+        d, w->w, w->co, w->p, g->er, g->et, g->ep, w->q, g->sc, g->partials, z.nf);
+    k_res_update<<<grid_blocks(g, z.nf, resident_per_sm<k_res_update>()), kThreads, 0, st>>>(
+        d, w->co, w->x, w->p, w->r, w->q, g->sc, g->partials, z.nf);
+    k_res_pupdate<<<grid_blocks(g, z.nf, resident_per_sm<k_res_pupdate>()), kThreads, 0, st>>>(d, w->co, w->r, w->p,
+                                                                                               g->sc, z.nf);
 }
 
 mhd_status_t res_graph(mhd_grid_s* g, ResWork* w) {
