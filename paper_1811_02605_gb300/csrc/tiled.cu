@@ -1,6 +1,6 @@
 // FP32 CG iteration in two plane-marching kernels (the inner solve of the mixed-precision path).
 //
-// The split form (p update, stencil, update) moves 11 passes of a 3-component vector per
+// The split form (p update, stencil, update) moves 10 passes of a 3-component vector per
 // iteration. Here:
 //   A: p_new = r + beta p_old at every point the stencil needs, q = A~ p_new, <p_new, q>;
 //      writes p_new only (3 passes: r, p_old in, p_new out)
