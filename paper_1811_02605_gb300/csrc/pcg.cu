@@ -8,6 +8,12 @@
 // That matters on this part: FP64 runs at 2 FMA/clk/SM, so the FP64 iteration is bound by its
 // FP64 instruction count, not by HBM.
 //
+// One iteration is three kernels: the p update (which also adds the previous iteration's alpha p
+// to x: the x update is deferred by one kernel, so the update kernel need not read p or x), the
+// stencil with <p, q>, and the r update with the dot products and the stop test. In the FP32
+// inner solves the first two can run as one kernel with p double-buffered (chosen per grid by
+// timing).
+//
 // Reductions: every thread accumulates its share in FP64 (FP32 path: compensated FP32 per
 // thread, then FP64), CTAs reduce with warp shuffles, write one partial each, and the last CTA
 // to arrive sums the partials in CTA order and finishes the scalar recurrence (alpha, beta,
