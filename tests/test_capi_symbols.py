@@ -35,10 +35,25 @@ def test_oracle_builds_and_is_separate():
     import oracle
     path = oracle.build()
     assert os.path.exists(path)
-    # the product library never links the oracle
+    # the product library never links the oracle: none of its sources lives under oracle/, and
+    # none of the oracle's entry points is exported
     from paper_1811_02605_gb300 import build as B
-    lib_bytes = open(B.build(), "rb").read()
-    assert b"og_pcg" not in lib_bytes and b"mhd_oracle" not in lib_bytes
+    assert all(os.sep + "oracle" + os.sep not in src for src in B.sources())
+    lib = ctypes.CDLL(B.build())
+    for name in ("og_pcg", "og_step", "og_force", "og_ilu0"):
+        assert not hasattr(lib, name), name
+
+
+def test_binding_kernel_names_match_the_header():
+    # the diagnostics' kernel ids (MHD_KERNEL_*) and the binding's name list agree in number
+    src = open(os.path.join(ROOT, "include", "mhd.h")).read()
+    count = int(re.search(r"MHD_KERNEL_COUNT\s*=\s*(\d+)", src).group(1))
+    import paper_1811_02605_gb300 as P
+    assert len(P.KERNELS) == count
+    ids = dict((m.group(1).lower(), int(m.group(2)))
+               for m in re.finditer(r"MHD_KERNEL_(\w+)\s*=\s*(\d+)", src) if m.group(1) != "COUNT")
+    for k, name in enumerate(P.KERNELS):
+        assert ids.get(name) == k, (name, k)
 
 
 def test_binding_rejects_missing_library(tmp_path, monkeypatch):
