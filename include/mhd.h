@@ -115,7 +115,12 @@ enum { MHD_PREC_FP64 = 0, MHD_PREC_MIXED = 1 };
  *            replacement one preconditioner pass recomputes z and <r, z>). Needs pcg_variant 0
  *            (MHD_ERR_ARG otherwise); applies to every solve of pcg_solve, mhd_step and
  *            mhd_adjoint_step; the first PC2 solve allocates N doubles + N floats for the
- *            factorisation. pcg_solve_batched ignores it. */
+ *            factorisation and 3N floats for z of the FP32 iteration. pcg_solve_batched ignores it.
+ *
+ * Kernel variants of the FP32 inner iteration (split p update and stencil, the two folded into
+ * one kernel, or plane-marching tiles) are chosen per grid by timing on its first mixed solve;
+ * results agree to the order of one dot product's reduction. Diagnostics only: the environment
+ * variable MHD_FORCE_SLAB skips the timing (-1 split, -2 folded, n > 0 tiles of n planes). */
 typedef struct {
     double nu, eta, cfl, dt_fixed, dt_max, alpha_si_fixed;
     double tol, inner_tol;
