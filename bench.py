@@ -230,6 +230,11 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if not args.all_entries:
+            # N replicas of the same workload: the headline and the end-to-end leg are the scaling
+            # measurement; the per-configuration entries are the single-GPU line's (N GPUs stay held
+            # for about a minute of timed work instead of several)
+            args.no_mixed = args.no_cg = args.no_pc2 = args.no_res = args.no_sts = True
     from paper_1811_02605_gb300 import build as B
     B.build()
     import paper_1811_02605_gb300 as P
@@ -867,6 +872,8 @@ def main():
     ap.add_argument("--no-res", action="store_true", help="skip the resistivity entry")
     ap.add_argument("--pc2-only", action="store_true", help="--refinement-study: only the PC2 rows")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--all-entries", action="store_true",
+                    help="with N > 1 ranks, also time the mixed, RKL2, single-reduction, PC2 and resistivity entries")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-iters", type=int, default=1000,
                     help="PCG iterations per step assumed by the reference arm if no oracle record exists")
