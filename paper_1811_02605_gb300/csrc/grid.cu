@@ -161,8 +161,8 @@ HostGeo make_geo(const mhd_grid_desc_t& d) {
     return h;
 }
 
-// geometric factors of the explicit kernels (ExTab); the same expressions as the kernels would
-// form per element, so the per-cell reciprocals keep their bits
+// geometric factors of the explicit kernels (ExTab), one row at a time from the 1-D metric tables
+// (the ex_* row functions); each factor is evaluated once here instead of once per element
 struct HostEx {
     std::vector<double> sh, ihp, cot, jr, jt, jp, fr, ft, fp;
 };
