@@ -301,16 +301,45 @@ int og_pcg_cg(const og_grid* g, double alpha, int ncomp, const double* b, double
 }
 
 /* ---------------------------------------------------------------------------------------------
- * Cell-centred B (reading R4): mean of the two opposite faces; in the polar rings the theta
- * component takes only the non-polar face.
+ * Pole values along a meridian (reading R4, polar rings). Near a pole, the theta and phi
+ * components of a smooth vector field, followed along the meridian phi towards the pole, tend
+ * to the horizontal field on the axis projected on (cos phi, sin phi) and on (-sin phi, cos phi):
+ * pure first harmonics in phi. The value at the pole along the meridian of cell k is therefore
+ * taken as the first phi harmonic of the ring of values next to the pole, fitted by the discrete
+ * Fourier projection a = (2/np) sum_m f_m cos(phi_m), b = (2/np) sum_m f_m sin(phi_m) over the
+ * ring's centres phi_m, and evaluated at phi_k: a cos(phi_k) + b sin(phi_k). The projection
+ * removes the ring's harmonics 0 and 2, which carry the field's O(h) change between the ring and
+ * the axis, so the pole value is second-order accurate (np >= 3).
+ * ------------------------------------------------------------------------------------------- */
+static double first_harmonic_at(const og_grid* g, const double* row, int k) {
+    double a = 0.0, b = 0.0;
+    for (int m = 0; m < g->np; m++) {
+        double ph = (m + 0.5) * g->dph;
+        a += row[m] * cos(ph);
+        b += row[m] * sin(ph);
+    }
+    double ph = (k + 0.5) * g->dph;
+    return (2.0 / g->np) * (a * cos(ph) + b * sin(ph));
+}
+
+/* ---------------------------------------------------------------------------------------------
+ * Cell-centred B (reading R4): mean of the two opposite faces. In the two polar rings the theta
+ * component is the mean of its non-polar face and of its pole value along the cell's meridian:
+ * the first harmonic of the B_theta ring on the faces j = 1 (north) or nt-1 (south), divided by
+ * cos(dtheta), the factor by which the horizontal part of the theta unit vector shrinks between
+ * the axis and that ring (so a uniform field's pole value is exact).
  * ------------------------------------------------------------------------------------------- */
 static void bcentre_at(const og_grid* g, const double* br, const double* bt, const double* bp,
                        int i, int j, int k, double* o) {
     int nt = g->nt;
     o[0] = 0.5 * (br[IDX(g, i, j, k)] + br[IDX(g, i + 1, j, k)]);
-    if (j == 0) o[1] = bt[IDXT(g, i, 1, k)];
-    else if (j == nt - 1) o[1] = bt[IDXT(g, i, nt - 1, k)];
-    else o[1] = 0.5 * (bt[IDXT(g, i, j, k)] + bt[IDXT(g, i, j + 1, k)]);
+    if (j == 0 || j == nt - 1) {
+        int jf = (j == 0) ? 1 : nt - 1;
+        double pole = first_harmonic_at(g, &bt[IDXT(g, i, jf, 0)], k) / cos(g->dth);
+        o[1] = 0.5 * (bt[IDXT(g, i, jf, k)] + pole);
+    } else {
+        o[1] = 0.5 * (bt[IDXT(g, i, j, k)] + bt[IDXT(g, i, j + 1, k)]);
+    }
     o[2] = 0.5 * (bp[IDX(g, i, j, k)] + bp[IDX(g, i, j, KP(g, k))]);
 }
 
@@ -906,6 +935,16 @@ static void eedges_T(const og_grid* g, const double* ler, const double* let, con
             }
 }
 
+/* transpose of first_harmonic_at for one output cell k with weight w: the map f -> pole value
+ * has the matrix (2/np)(cos phi_k cos phi_m + sin phi_k sin phi_m), so column k is added to row */
+static void first_harmonic_T(const og_grid* g, double* row, int k, double w) {
+    double phk = (k + 0.5) * g->dph;
+    for (int m = 0; m < g->np; m++) {
+        double ph = (m + 0.5) * g->dph;
+        row[m] += w * (2.0 / g->np) * (cos(ph) * cos(phk) + sin(ph) * sin(phk));
+    }
+}
+
 /* transpose of the face -> centre averaging of B (bcentre_at) */
 static void bcentre_T(const og_grid* g, const double* lbc, double* lbr, double* lbt, double* lbp) {
     int nt = g->nt;
@@ -916,9 +955,14 @@ static void bcentre_T(const og_grid* g, const double* lbc, double* lbr, double* 
                 long long c = IDX(g, i, j, k);
                 lbr[IDX(g, i, j, k)] += 0.5 * lbc[c];
                 lbr[IDX(g, i + 1, j, k)] += 0.5 * lbc[c];
-                if (j == 0) lbt[IDXT(g, i, 1, k)] += lbc[N + c];
-                else if (j == nt - 1) lbt[IDXT(g, i, nt - 1, k)] += lbc[N + c];
-                else { lbt[IDXT(g, i, j, k)] += 0.5 * lbc[N + c]; lbt[IDXT(g, i, j + 1, k)] += 0.5 * lbc[N + c]; }
+                if (j == 0 || j == nt - 1) {
+                    int jf = (j == 0) ? 1 : nt - 1;
+                    lbt[IDXT(g, i, jf, k)] += 0.5 * lbc[N + c];
+                    first_harmonic_T(g, &lbt[IDXT(g, i, jf, 0)], k, 0.5 * lbc[N + c] / cos(g->dth));
+                } else {
+                    lbt[IDXT(g, i, j, k)] += 0.5 * lbc[N + c];
+                    lbt[IDXT(g, i, j + 1, k)] += 0.5 * lbc[N + c];
+                }
                 lbp[IDX(g, i, j, k)] += 0.5 * lbc[2 * N + c];
                 lbp[IDX(g, i, j, KP(g, k))] += 0.5 * lbc[2 * N + c];
             }

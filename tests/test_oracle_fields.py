@@ -166,9 +166,20 @@ def test_ct_line_tied_inner_boundary_and_static():
     assert np.array_equal(br3, st["br"]) and np.array_equal(bt3, st["bt"]) and np.array_equal(bp3, st["bp"])
 
 
-def _ct_translation_error(nr):
-    # v uniform, B dipole: dB/dt = curl(v x B) = -(v.grad)B; compare on phi faces away from
-    # the two polar rings (whose theta average uses only the non-polar face) and r boundaries
+def _dipole_rate(V0, X):
+    # dB/dt = curl(v x B) = -(v.grad)B for uniform v and the dipole, by central differences
+    h = 1e-6
+    dB = np.zeros_like(X)
+    for a in range(3):
+        e = np.zeros((3, 1, 1, 1))
+        e[a] = 1.0
+        dB -= V0[a] * (dipole_B(X + h * e) - dipole_B(X - h * e)) / (2 * h)
+    return dB
+
+
+def _ct_translation_errors(nr):
+    """Error of dB/dt from one CT update of a dipole carried by a uniform flow, on the three face
+    families, split into the rows next to the poles and the rest (r boundaries left out)."""
     d, g = _grid(nr)
     br, bt, bp = I.magnetic_field(d, dipole=True)
     R, TH, PH = centres(d)
@@ -176,32 +187,127 @@ def _ct_translation_error(nr):
     v = np.ascontiguousarray(to_sph(np.broadcast_to(V0.reshape(3, 1, 1, 1), (3,) + R.shape), TH, PH))
     er, et, ep = g.efield_edges(v, br, bt, bp)
     dt = 1e-3
-    _, _, bp2 = g.ct(er, et, ep, dt, br, bt, bp)
+    br2, bt2, bp2 = g.ct(er, et, ep, dt, br, bt, bp)
     r = I.radial_nodes(d)
     rc = 0.5 * (r[1:] + r[:-1])
     thc = (np.arange(nr) + 0.5) * math.pi / nr
+    thn = np.arange(nr + 1) * math.pi / nr
     phn = np.arange(2 * nr) * 2 * math.pi / (2 * nr)
-    RR, TT, PP = np.meshgrid(rc, thc, phn, indexing="ij")
-    Xf = cart(RR, TT, PP)
-    h = 1e-6
-    dB = np.zeros_like(Xf)
-    for a in range(3):
-        e = np.zeros((3, 1, 1, 1))
-        e[a] = 1.0
-        dB -= V0[a] * (dipole_B(Xf + h * e) - dipole_B(Xf - h * e)) / (2 * h)
-    ex = -dB[0] * np.sin(PP) + dB[1] * np.cos(PP)
-    num = (bp2 - bp) / dt
-    w = ((num - ex) * RR ** 3)[2:-2, 2:-2]
-    return float(np.sqrt(np.mean(w ** 2)))
+    phc = (np.arange(2 * nr) + 0.5) * 2 * math.pi / (2 * nr)
+    rms = lambda a: float(np.sqrt(np.mean(a ** 2)))
+    out = {}
+    RR, TT, PP = np.meshgrid(rc, thc, phn, indexing="ij")          # phi faces
+    dB = _dipole_rate(V0, cart(RR, TT, PP))
+    e = ((bp2 - bp) / dt - (-dB[0] * np.sin(PP) + dB[1] * np.cos(PP))) * RR ** 3
+    out["bp_all"], out["bp_pole"] = rms(e[2:-2]), rms(e[2:-2][:, [0, -1]])
+    RR, TT, PP = np.meshgrid(rc, thn, phc, indexing="ij")          # theta faces
+    dB = _dipole_rate(V0, cart(RR, TT, PP))
+    e = ((bt2 - bt) / dt - to_sph(dB, TT, PP)[1]) * RR ** 3
+    out["bt_all"], out["bt_pole"] = rms(e[2:-2, 1:-1]), rms(e[2:-2][:, [1, -2]])
+    RR, TT, PP = np.meshgrid(r, thc, phc, indexing="ij")           # r faces
+    dB = _dipole_rate(V0, cart(RR, TT, PP))
+    e = ((br2 - br) / dt - to_sph(dB, TT, PP)[0]) * RR ** 3
+    out["br_pole"] = rms(e[2:-2][:, [0, -1]])
+    return out
 
 
-def test_ct_translation_second_order_away_from_poles():
-    errs = [_ct_translation_error(nr) for nr in (16, 32, 64)]
+@pytest.fixture(scope="module")
+def ct_translation():
+    return [_ct_translation_errors(nr) for nr in (16, 32, 64)]
+
+
+def test_ct_translation_second_order_over_all_theta(ct_translation):
+    # every theta row, the two polar rings included
+    for key in ("bp_all", "bt_all"):
+        errs = [e[key] for e in ct_translation]
+        r = _rates(errs)
+        assert r[-1] > 3.0 and r[-1] > r[0], (key, errs)
+
+
+def test_ct_translation_converges_in_polar_rings(ct_translation):
+    # the faces next to the poles: phi and theta faces at second order; the polar-cap r faces at
+    # first order (their flux average of B_r's first phi harmonic, which grows like sin(theta),
+    # is centred at theta ~ 2 dth / 3 rather than at the cell's dth / 2)
+    for key, lo in (("bp_pole", 3.0), ("bt_pole", 3.0), ("br_pole", 1.8)):
+        errs = [e[key] for e in ct_translation]
+        r = _rates(errs)
+        assert r[-1] > lo and errs[-1] < errs[0], (key, errs, r)
+
+
+_U = np.array([0.3, -0.2, 0.5])
+
+
+def _uniform_potential(x):
+    # A = U x x / 2, so B = curl A = U
+    return 0.5 * np.stack([_U[1] * x[2] - _U[2] * x[1], _U[2] * x[0] - _U[0] * x[2], _U[0] * x[1] - _U[1] * x[0]])
+
+
+def test_bcentre_polar_pole_value_is_first_harmonic_over_cos_dtheta():
+    # B_theta,c in a polar ring is the mean of the face value and the pole value. Face rings next
+    # to the poles made of phi harmonics 0, 1 and 2 (random amplitudes per shell): the pole value
+    # along meridian phi_k must be the harmonic-1 part divided by cos(dth), to round-off
+    rng = np.random.default_rng(7)
+    for nr, np_ in ((6, 8), (8, 16), (5, 12)):
+        d = I.GridDesc(nr, nr, np_, 1.0, 4.0, 1.1)
+        g = O.Grid.from_desc(d)
+        br, bt, bp = zero_faces(d)
+        phc = (np.arange(np_) + 0.5) * 2 * math.pi / np_
+        c = math.cos(math.pi / nr)
+        for j, jf in ((0, 1), (nr - 1, nr - 1)):
+            a1, b1, a0, a2, b2 = rng.normal(size=(5, nr, 1))
+            h1 = a1 * np.cos(phc) + b1 * np.sin(phc)
+            bt[:, jf] = c * h1 + a0 + a2 * np.cos(2 * phc) + b2 * np.sin(2 * phc)
+            bc = g.bcentre(br, bt, bp)
+            pole = 2 * bc[1][:, j] - bt[:, jf]
+            assert np.abs(pole - h1).max() < 1e-13, (nr, np_, j)
+
+
+def _bcentre_polar_errors(nr):
+    d, g = _grid(nr)
+    br, bt, bp = I.magnetic_field(d, dipole=True, potential=_uniform_potential)
+    R, TH, PH = centres(d)
+    ex = to_sph(dipole_B(cart(R, TH, PH)) + _U.reshape(3, 1, 1, 1), TH, PH)
+    e = (g.bcentre(br, bt, bp) - ex)[:, 1:-1][:, :, [0, -1]]
+    return [float(np.sqrt(np.mean(e[c] ** 2))) for c in range(3)]
+
+
+def test_bcentre_polar_rings_convergence():
+    # dipole plus a uniform field (horizontal on the axis): B_theta and B_phi at the polar-ring
+    # centres at second order; B_r at first order (the polar-cap face centroid, as above)
+    errs = np.array([_bcentre_polar_errors(nr) for nr in (8, 16, 32)])
+    for c, lo in ((0, 1.8), (1, 3.5), (2, 3.5)):
+        r = _rates(list(errs[:, c]))
+        assert r[-1] > lo, (c, errs[:, c], r)
+
+
+def _polar_axis_er_error(nr):
+    d, g = _grid(nr)
+    br, bt, bp = I.magnetic_field(d, dipole=True, potential=_uniform_potential)
+    R, TH, PH = centres(d)
+    V0 = np.array([1.0, 0.5, 0.2])
+    v = np.ascontiguousarray(to_sph(np.broadcast_to(V0.reshape(3, 1, 1, 1), (3,) + R.shape), TH, PH))
+    er, _, _ = g.efield_edges(v, br, bt, bp)
+    r = I.radial_nodes(d)
+    rc = 0.5 * (r[1:] + r[:-1])
+    errs = []
+    for s, col in ((1.0, 0), (-1.0, -1)):       # r-hat is +z on the north axis, -z on the south
+        X = np.stack([0 * rc, 0 * rc, s * rc])
+        B = dipole_B(X[:, :, None, None])[:, :, 0, 0] + _U[:, None]
+        Ez = -(V0[0] * B[1] - V0[1] * B[0])
+        assert np.all(er[:, col, :] == er[:, col, :1])
+        errs.append(er[:, col, 0] - s * Ez)
+    return float(np.sqrt(np.mean(np.concatenate(errs) ** 2)))
+
+
+def test_efield_polar_axis_value_second_order():
+    # the polar radial edge takes the mean of E_r over the polar ring: for a uniform flow across a
+    # dipole plus a uniform field it tends to E_r = -(v x B).r_hat on the axis at second order
+    errs = [_polar_axis_er_error(nr) for nr in (8, 16, 32)]
     r = _rates(errs)
-    assert r[-1] > 3.0 and r[-1] > r[0], errs
+    assert r[-1] > 3.7 and errs[-1] < 1e-3, (errs, r)
 
 
-def test_efield_outer_edges_two_cell_mean_and_polar_ring_mean():
+def test_efield_outer_edges_two_cell_mean_and_polar_ring_single_valued():
     d = I.GridDesc(4, 4, 6, 1.0, 3.0, 1.0)
     g = O.Grid.from_desc(d)
     rng = np.random.default_rng(2)
