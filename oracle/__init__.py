@@ -52,6 +52,8 @@ def _declare(L):
     L.og_destroy.argtypes = [vp]
     for name in ("og_radial_nodes", "og_volumes", "og_ktilde2"):
         getattr(L, name).argtypes = [vp, _dp]
+    L.og_dot.restype = d
+    L.og_dot.argtypes = [C.c_longlong, _dp, _dp]
     L.og_apply_M.argtypes = [vp, d, i, _dp, _dp]
     L.og_apply_K_neumann.argtypes = [vp, i, _dp, _dp]
     L.og_diag.argtypes = [vp, d, _dp]
@@ -112,6 +114,13 @@ def _blocks(name):
 
 def _c(a):
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def dot(a, b):
+    """The oracle's inner product (compensated, as in every PCG of the oracle)."""
+    a, b = _c(a).ravel(), _c(b).ravel()
+    assert a.size == b.size
+    return lib().og_dot(a.size, a, b)
 
 
 class Grid:

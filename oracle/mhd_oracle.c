@@ -175,11 +175,26 @@ void og_diag(const og_grid* g, double alpha, double* d) {
  * recursively updated residual satisfies ||r||_2 <= tol ||b||_2, tested before each iteration;
  * the count is the number of x updates; b = 0 gives x = 0 after 0 iterations.
  * ------------------------------------------------------------------------------------------- */
+/* Inner product (reading P12: FP64 dot products whose value does not depend on the order of the
+ * terms beyond rounding). Algorithm Dot2 of Ogita, Rump & Oishi (2005): each product is split
+ * exactly into p + e (e, its rounding error, from an fma), the products are summed with Knuth's
+ * error-free TwoSum, and the collected errors are added at the end. The result is as accurate as a
+ * sum taken in twice the working precision and then rounded, whatever the length, so the PCG
+ * scalars alpha and beta carry no summation-order error of this side's own. */
 static double dot(long long n, const double* a, const double* b) {
-    double s = 0.0;
-    for (long long i = 0; i < n; i++) s += a[i] * b[i];
-    return s;
+    double s = 0.0, c = 0.0;
+    for (long long i = 0; i < n; i++) {
+        double p = a[i] * b[i];
+        double pe = fma(a[i], b[i], -p);
+        double t = s + p;
+        double z = t - s;
+        c += ((s - (t - z)) + (p - z)) + pe;
+        s = t;
+    }
+    return s + c;
 }
+
+double og_dot(long long n, const double* a, const double* b) { return dot(n, a, b); }
 
 int og_pcg(const og_grid* g, double alpha, int ncomp, const double* b, double* x, double tol,
            int max_iter, int fixed_iters, int* iters, double* relres) {

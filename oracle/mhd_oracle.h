@@ -42,6 +42,9 @@ void og_apply_K_neumann(const og_grid* g, int ncomp, const double* p, double* q)
 /* diagonal of M_alpha per (i,j) row, nr*nt entries */
 void og_diag(const og_grid* g, double alpha, double* d);
 
+/* the inner product every PCG form of the oracle uses (compensated, reading P12) */
+double og_dot(long long n, const double* a, const double* b);
+
 /* point-Jacobi PCG (PC1). x holds x0 on entry. fixed_iters > 0 runs exactly that many
  * iterations. Returns OG_OK or OG_ERR_NOCONV. */
 int og_pcg(const og_grid* g, double alpha, int ncomp, const double* b, double* x, double tol,

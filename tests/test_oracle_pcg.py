@@ -106,3 +106,25 @@ def test_single_reduction_form_matches_hestenes_stiefel_iterates():
         _, ia, _, _ = g.pcg(alpha, b, tol=1e-9)
         _, ib, _, _ = g.pcg(alpha, b, tol=1e-9, cg=True)
         assert abs(ia - ib) <= 1, (ia, ib)
+
+
+def test_dot_is_compensated():
+    # reading P12: the oracle's inner product does not depend on the order of the terms beyond
+    # rounding. Terms with heavy cancellation: the exact value (rational arithmetic on the float
+    # inputs) rounded to double must be reproduced to within 2 ulps, for the terms in any order
+    from fractions import Fraction
+    rng = np.random.default_rng(31)
+    n = 4000
+    a = rng.normal(size=n) * np.exp(rng.uniform(-20, 20, size=n))
+    b = rng.normal(size=n)
+    b[n // 2:] = -a[: n // 2] * b[: n // 2] / a[n // 2:]     # products cancel pairwise up to rounding
+    b[-1] = 1.0
+    exact = float(sum(Fraction(x) * Fraction(y) for x, y in zip(a, b)))
+    for perm in (np.arange(n), rng.permutation(n), np.arange(n)[::-1]):
+        got = O.dot(a[perm], b[perm])
+        assert abs(got - exact) <= 2 * np.spacing(abs(exact)), (got, exact)
+    # a plain sequential sum of the same terms is far off (the check has teeth)
+    naive = 0.0
+    for x, y in zip(a, b):
+        naive += x * y
+    assert abs(naive - exact) > 1e3 * np.spacing(abs(exact))
