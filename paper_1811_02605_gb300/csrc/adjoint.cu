@@ -36,11 +36,12 @@ struct VelA {
     }
 };
 
-__device__ __forceinline__ void bcen(const Dims& d, const double* br, const double* bt, const double* bp, int i,
-                                     int j, int k, double (&o)[3]) {
+// cell-centred B; bh: first-harmonic sums of the B_theta face rings next to the poles
+__device__ __forceinline__ void bcen(const Dims& d, const Geo& G, const double* bh, const double* br,
+                                     const double* bt, const double* bp, int i, int j, int k, double (&o)[3]) {
     o[0] = 0.5 * (br[ix(d, i, j, k)] + br[ix(d, i + 1, j, k)]);
-    if (j == 0) o[1] = bt[ixt(d, i, 1, k)];
-    else if (j == d.nt - 1) o[1] = bt[ixt(d, i, d.nt - 1, k)];
+    if (j == 0) o[1] = polar_btc(G, d.np, bh + 2 * i, k, bt[ixt(d, i, 1, k)]);
+    else if (j == d.nt - 1) o[1] = polar_btc(G, d.np, bh + 2 * (d.nr + i), k, bt[ixt(d, i, d.nt - 1, k)]);
     else o[1] = 0.5 * (bt[ixt(d, i, j, k)] + bt[ixt(d, i, j + 1, k)]);
     o[2] = 0.5 * (bp[ix(d, i, j, k)] + bp[ix(d, i, j, kp1(d, k))]);
 }
@@ -100,11 +101,19 @@ __device__ double upwind(const Dims& d, const Geo& G, const VelA& v, int m, int 
     return (n[m] - uc[m]) / h;
 }
 
+// first-harmonic sums of the theta component of lam_Bc over the two polar rings, into the second
+// half of g->bharm (read by k_face_T)
+void lbc_harmonics(mhd_grid_s* g, const double* lbc, cudaStream_t st) {
+    const Dims d = g->d;
+    ring_harmonics(g, lbc + d.N, (long long)d.nt * d.np, 0, (long long)(d.nt - 1) * d.np, g->bharm + 4 * d.nr, st);
+}
+
 // ---------------------------------------------------------------------------------------------
 // force transpose, cell part: lam_v += (dF/dv)^T (s lam_b); lam_Bc = (s lam_b x J)/rho,
 // lam_Jc = (B x s lam_b)/rho (cell arrays, overwritten)
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_adjF_cell(Dims d, Geo G, VelA v, const double* __restrict__ br,
+__global__ void __launch_bounds__(kThreads) k_adjF_cell(Dims d, Geo G, VelA v, const double* __restrict__ bh,
+                                                        const double* __restrict__ br,
                                                         const double* __restrict__ bt, const double* __restrict__ bp,
                                                         const double* __restrict__ jr, const double* __restrict__ jt,
                                                         const double* __restrict__ jp, double dt,
@@ -121,7 +130,7 @@ __global__ void __launch_bounds__(kThreads) k_adjF_cell(Dims d, Geo G, VelA v, c
         const double rho = G.rho[i];
         const double lf[3] = {s * lb[c], s * lb[N + c], s * lb[2 * N + c]};
         double B[3], J[3], u[3];
-        bcen(d, br, bt, bp, i, j, k, B);
+        bcen(d, G, bh, br, bt, bp, i, j, k, B);
         jcen(d, jr, jt, jp, i, j, k, J);
         v.at(c, u);
         ljc[c] = (B[1] * lf[2] - B[2] * lf[1]) / rho;
@@ -227,7 +236,8 @@ __global__ void __launch_bounds__(kThreads) k_adjF_cell(Dims d, Geo G, VelA v, c
 }
 
 // E transpose, cell part: lam_vbar += lam_Ec x Bc; lam_Bc = vbar x lam_Ec; lam_Jc = eta lam_Ec
-__global__ void __launch_bounds__(kThreads) k_adjE_cell(Dims d, VelA v, const double* __restrict__ br,
+__global__ void __launch_bounds__(kThreads) k_adjE_cell(Dims d, Geo G, VelA v, const double* __restrict__ bh,
+                                                        const double* __restrict__ br,
                                                         const double* __restrict__ bt, const double* __restrict__ bp,
                                                         const double* __restrict__ lec, double eta,
                                                         double* __restrict__ lvb, double* __restrict__ lbc,
@@ -239,7 +249,7 @@ __global__ void __launch_bounds__(kThreads) k_adjE_cell(Dims d, VelA v, const do
         split_np(d, c, k, ij);
         const int j = (int)(ij % d.nt), i = (int)(ij / d.nt);
         double B[3], u[3];
-        bcen(d, br, bt, bp, i, j, k, B);
+        bcen(d, G, bh, br, bt, bp, i, j, k, B);
         v.at(c, u);
         const double l0 = lec[c], l1 = lec[N + c], l2 = lec[2 * N + c];
         lvb[c] += l1 * B[2] - l2 * B[1];
@@ -330,8 +340,11 @@ __global__ void __launch_bounds__(kThreads) k_jcentre_T(Dims d, const double* __
     }
 }
 
-// lam_B faces += P_B^T lam_Bc + (curl_J)^T lam_J (edges)
+// lam_B faces += P_B^T lam_Bc + (curl_J)^T lam_J (edges). The polar-ring pole value of B_theta,c is
+// a symmetric map of the face ring (matrix 2 / (np cos(dth)) cos(phi_k - phi_m)), so its transpose
+// evaluates the same first harmonic of the lam_Bc_theta polar ring (lh: its cos and sin sums).
 __global__ void __launch_bounds__(kThreads) k_face_T(Dims d, Geo G, const double* __restrict__ lbc,
+                                                     const double* __restrict__ lh,
                                                      const double* __restrict__ ljr, const double* __restrict__ ljt,
                                                      const double* __restrict__ ljp, const double* __restrict__ ring,
                                                      int has_j, double* __restrict__ lbr, double* __restrict__ lbt,
@@ -383,11 +396,14 @@ __global__ void __launch_bounds__(kThreads) k_face_T(Dims d, Geo G, const double
             for (int jc = j - 1; jc <= j; jc++) {
                 if (jc < 0 || jc > nt - 1) continue;
                 double w;
-                if (jc == 0) w = (j == 1) ? 1.0 : 0.0;
-                else if (jc == nt - 1) w = (j == nt - 1) ? 1.0 : 0.0;
+                if (jc == 0) w = (j == 1) ? 0.5 : 0.0;
+                else if (jc == nt - 1) w = (j == nt - 1) ? 0.5 : 0.0;
                 else w = 0.5;
                 s += w * lbc[N + ix(d, i, jc, k)];
             }
+            if (j == 1) s += 0.5 * G.pole_f * (lh[2 * i] * G.pcs[k] + lh[2 * i + 1] * G.pcs[d.np + k]);
+            if (j == nt - 1)
+                s += 0.5 * G.pole_f * (lh[2 * (nr + i)] * G.pcs[k] + lh[2 * (nr + i) + 1] * G.pcs[d.np + k]);
             if (has_j && j >= 1 && j <= nt - 1) {
                 const double rcd = G.rc[i] * G.dth;
                 s += rcd * (wjr(i, j, kp1(d, k)) - wjr(i, j, k));
@@ -669,11 +685,14 @@ extern "C" mhd_status_t mhd_adjoint_step(mhd_grid_t g, const mhd_params_t* p, co
     cudaMemcpyAsync(w.lb1p, a1->bp, sizeof(double) * nbp, cudaMemcpyDeviceToDevice, st);
     cudaMemsetAsync(w.lvp, 0, sizeof(double) * n3, st);
     current_edges(g, w.b1r, w.b1t, w.b1p);
-    k_adjF_cell<<<bc, kThreads, 0, st>>>(d, g->geo, velp, w.b1r, w.b1t, w.b1p, g->er, g->et, g->ep, dt, w.lb, w.lvp,
-                                         w.lbc, w.ljc);
+    bt_harmonics(g, w.b1t, st);
+    k_adjF_cell<<<bc, kThreads, 0, st>>>(d, g->geo, velp, g->bharm, w.b1r, w.b1t, w.b1p, g->er, g->et, g->ep, dt,
+                                         w.lb, w.lvp, w.lbc, w.ljc);
     k_jcentre_T<<<be, kThreads, 0, st>>>(d, w.ljc, g->er, g->et, g->ep);
     k_ring_edges<<<2 * d.nr, kThreads, 0, st>>>(d, g->er, g->ring);
-    k_face_T<<<bf, kThreads, 0, st>>>(d, g->geo, w.lbc, g->er, g->et, g->ep, g->ring, 1, w.lb1r, w.lb1t, w.lb1p);
+    lbc_harmonics(g, w.lbc, st);
+    k_face_T<<<bf, kThreads, 0, st>>>(d, g->geo, w.lbc, g->bharm + 4 * d.nr, g->er, g->et, g->ep, g->ring, 1, w.lb1r,
+                                      w.lb1t, w.lb1p);
     if (res) {
         // B^{n+1} = M_res^-1 W B* (the face solve): lam_B* = W M_res^-1 lam_B^{n+1}
         stt = res_transpose(g, &g->ss->dt, p->eta, w.lb1r, w.lb1t, w.lb1p, p);
@@ -689,14 +708,16 @@ extern "C" mhd_status_t mhd_adjoint_step(mhd_grid_t g, const mhd_params_t* p, co
     k_ring_edges<<<2 * d.nr, kThreads, 0, st>>>(d, g->er, g->ring);
     k_eedges_T<<<bc, kThreads, 0, st>>>(d, g->er, g->et, g->ep, g->ring, g->ec);
     cudaMemsetAsync(w.lvb, 0, sizeof(double) * n3, st);
-    k_adjE_cell<<<bc, kThreads, 0, st>>>(d, velb, s0->br, s0->bt, s0->bp, g->ec, eta, w.lvb, w.lbc,
+    bt_harmonics(g, s0->bt, st);
+    k_adjE_cell<<<bc, kThreads, 0, st>>>(d, g->geo, velb, g->bharm, s0->br, s0->bt, s0->bp, g->ec, eta, w.lvb, w.lbc,
                                          eta != 0.0 ? w.ljc : nullptr);
     if (eta != 0.0) {
         k_jcentre_T<<<be, kThreads, 0, st>>>(d, w.ljc, g->er, g->et, g->ep);
         k_ring_edges<<<2 * d.nr, kThreads, 0, st>>>(d, g->er, g->ring);
     }
-    k_face_T<<<bf, kThreads, 0, st>>>(d, g->geo, w.lbc, g->er, g->et, g->ep, g->ring, eta != 0.0 ? 1 : 0, a0->br,
-                                      a0->bt, a0->bp);
+    lbc_harmonics(g, w.lbc, st);
+    k_face_T<<<bf, kThreads, 0, st>>>(d, g->geo, w.lbc, g->bharm + 4 * d.nr, g->er, g->et, g->ep, g->ring,
+                                      eta != 0.0 ? 1 : 0, a0->br, a0->bt, a0->bp);
     // v_p = v + d_p, vbar = v + d_p / 2
     k_axpby<<<bc, kThreads, 0, st>>>(n3, 1.0, w.lvp, 1.0, w.lvb, w.ldp);   // ldp = lvp + lvb (temp)
     k_axpby<<<bc, kThreads, 0, st>>>(n3, 1.0, w.lv, 1.0, w.ldp, w.lv);     // lv += lvp + lvb
@@ -709,11 +730,14 @@ extern "C" mhd_status_t mhd_adjoint_step(mhd_grid_t g, const mhd_params_t* p, co
     k_axpby<<<bc, kThreads, 0, st>>>(n3, 1.0, w.lb, 1.0, w.y, w.lb);
     // F(v, B) transpose
     current_edges(g, s0->br, s0->bt, s0->bp);
-    k_adjF_cell<<<bc, kThreads, 0, st>>>(d, g->geo, vel0, s0->br, s0->bt, s0->bp, g->er, g->et, g->ep, dt, w.lb, w.lv,
-                                         w.lbc, w.ljc);
+    bt_harmonics(g, s0->bt, st);
+    k_adjF_cell<<<bc, kThreads, 0, st>>>(d, g->geo, vel0, g->bharm, s0->br, s0->bt, s0->bp, g->er, g->et, g->ep, dt,
+                                         w.lb, w.lv, w.lbc, w.ljc);
     k_jcentre_T<<<be, kThreads, 0, st>>>(d, w.ljc, g->er, g->et, g->ep);
     k_ring_edges<<<2 * d.nr, kThreads, 0, st>>>(d, g->er, g->ring);
-    k_face_T<<<bf, kThreads, 0, st>>>(d, g->geo, w.lbc, g->er, g->et, g->ep, g->ring, 1, a0->br, a0->bt, a0->bp);
+    lbc_harmonics(g, w.lbc, st);
+    k_face_T<<<bf, kThreads, 0, st>>>(d, g->geo, w.lbc, g->bharm + 4 * d.nr, g->er, g->et, g->ep, g->ring, 1, a0->br,
+                                      a0->bt, a0->bp);
     cudaMemcpyAsync(a0->vr, w.lv, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
     cudaMemcpyAsync(a0->vt, w.lv + N, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
     cudaMemcpyAsync(a0->vp, w.lv + 2 * N, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);

@@ -5,7 +5,9 @@
 //   - momentum force b = rho V dt (-(v.grad)v + J x B / rho)
 //   - E = -v x B + eta J at cell centres, averaged to edges; B <- B - dt curl_h E (Stokes)
 // Pole and boundary rules:
-//   - B_theta at a cell centre in the two polar rings comes from the non-polar face only.
+//   - B_theta at a cell centre in the two polar rings is the mean of the non-polar face and of
+//     the pole value along the cell's meridian (first phi harmonic of the face ring next to the
+//     pole, divided by cos(dth)).
 //   - The polar radial edge carries one value: the cap circulation of B_phi for J, the ring
 //     mean of the polar cells for E.
 //   - The polar phi edges have zero length; their J is 0 and left out of the centre average.
@@ -22,13 +24,14 @@ namespace mhd {
 namespace {
 
 
-// cell-centred B: mean of opposite faces; polar rings take B_theta from the non-polar face
-__device__ __forceinline__ void bcentre(const Dims& d, const double* __restrict__ br,
-                                        const double* __restrict__ bt, const double* __restrict__ bp,
-                                        int i, int j, int k, double (&o)[3]) {
+// cell-centred B: mean of opposite faces; in the polar rings B_theta is the mean of the non-polar
+// face and the pole value (bh: first-harmonic sums of the B_theta face rings, bt_harmonics)
+__device__ __forceinline__ void bcentre(const Dims& d, const Geo& G, const double* __restrict__ bh,
+                                        const double* __restrict__ br, const double* __restrict__ bt,
+                                        const double* __restrict__ bp, int i, int j, int k, double (&o)[3]) {
     o[0] = 0.5 * (br[ix(d, i, j, k)] + br[ix(d, i + 1, j, k)]);
-    if (j == 0) o[1] = bt[ixt(d, i, 1, k)];
-    else if (j == d.nt - 1) o[1] = bt[ixt(d, i, d.nt - 1, k)];
+    if (j == 0) o[1] = polar_btc(G, d.np, bh + 2 * i, k, bt[ixt(d, i, 1, k)]);
+    else if (j == d.nt - 1) o[1] = polar_btc(G, d.np, bh + 2 * (d.nr + i), k, bt[ixt(d, i, d.nt - 1, k)]);
     else o[1] = 0.5 * (bt[ixt(d, i, j, k)] + bt[ixt(d, i, j + 1, k)]);
     o[2] = 0.5 * (bp[ix(d, i, j, k)] + bp[ix(d, i, j, kp1(d, k))]);
 }
@@ -55,7 +58,8 @@ struct Vel {
 // ------------------------------------------------------------------------------------------
 // step coefficients
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_coeffs(Dims d, Geo G, Vel v, const double* __restrict__ br,
+__global__ void __launch_bounds__(kThreads) k_coeffs(Dims d, Geo G, Vel v, const double* __restrict__ bh,
+                                                     const double* __restrict__ br,
                                                      const double* __restrict__ bt,
                                                      const double* __restrict__ bp, double nu, double cfl,
                                                      double dt_fixed, double dt_max, double asi_fixed,
@@ -69,7 +73,7 @@ __global__ void __launch_bounds__(kThreads) k_coeffs(Dims d, Geo G, Vel v, const
         const int j = (int)(ij % d.nt), i = (int)(ij / d.nt);
         double u[3], B[3];
         v.at(c, u);
-        bcentre(d, br, bt, bp, i, j, k, B);
+        bcentre(d, G, bh, br, bt, bp, i, j, k, B);
         const double kt2 = G.kt2[ij];
         const double vv = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
         const double bb = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
@@ -108,8 +112,9 @@ __global__ void __launch_bounds__(kThreads) k_coeffs(Dims d, Geo G, Vel v, const
 mhd_status_t coeffs(mhd_grid_s* g, const mhd_params_t* p, const double* vr, const double* vt,
                     const double* vp, const double* br, const double* bt, const double* bp) {
     Vel v{vr, vt, vp, nullptr, 0.0, g->d.N};
+    bt_harmonics(g, bt);
     const int blocks = grid_blocks(g, g->d.N, 4);
-    k_coeffs<<<blocks, kThreads, 0, g->stream>>>(g->d, g->geo, v, br, bt, bp, p->nu, p->cfl, p->dt_fixed,
+    k_coeffs<<<blocks, kThreads, 0, g->stream>>>(g->d, g->geo, v, g->bharm, br, bt, bp, p->nu, p->cfl, p->dt_fixed,
                                                  p->dt_max, p->alpha_si_fixed, g->ss, g->partials);
     return check_cuda(g, "coeffs");
 }
@@ -133,6 +138,51 @@ __global__ void k_ring(Dims d, const double* __restrict__ a, double* __restrict_
         for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += sm[w];
         out[blockIdx.x] = t;
     }
+}
+
+// first-harmonic sums of the rows next to the poles (one CTA per row, fixed-order reduction):
+// out[2 b] = sum_k a_k cos(phi_c_k), out[2 b + 1] = sum_k a_k sin(phi_c_k), b = i (north row at
+// off_n + i stride_i) or nr + i (south row at off_s + i stride_i)
+__global__ void k_ring_harm(Dims d, const double* __restrict__ a, long long stride_i, long long off_n,
+                            long long off_s, const double* __restrict__ pcs, double* __restrict__ out) {
+    const int i = blockIdx.x % d.nr;
+    const int south = blockIdx.x / d.nr;
+    const double* row = a + (long long)i * stride_i + (south ? off_s : off_n);
+    double sc = 0.0, ss = 0.0;
+    for (int k = threadIdx.x; k < d.np; k += blockDim.x) {
+        sc = fma(row[k], pcs[k], sc);
+        ss = fma(row[k], pcs[d.np + k], ss);
+    }
+    __shared__ double sm[2][kThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        sc += __shfl_xor_sync(0xffffffffu, sc, o);
+        ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sm[0][threadIdx.x >> 5] = sc;
+        sm[1][threadIdx.x >> 5] = ss;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tc = 0.0, ts = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+            tc += sm[0][w];
+            ts += sm[1][w];
+        }
+        out[2 * blockIdx.x] = tc;
+        out[2 * blockIdx.x + 1] = ts;
+    }
+}
+
+void ring_harmonics(mhd_grid_s* g, const double* a, long long stride_i, long long off_n, long long off_s,
+                    double* out, cudaStream_t st) {
+    k_ring_harm<<<2 * g->d.nr, kThreads, 0, st ? st : g->stream>>>(g->d, a, stride_i, off_n, off_s, g->geo.pcs,
+                                                                   out);
+}
+
+void bt_harmonics(mhd_grid_s* g, const double* bt, cudaStream_t st) {
+    const Dims d = g->d;
+    ring_harmonics(g, bt, (long long)(d.nt + 1) * d.np, d.np, (long long)(d.nt - 1) * d.np, g->bharm, st);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -227,7 +277,8 @@ __device__ __forceinline__ void jcentre(const Dims& d, const double* __restrict_
 // ------------------------------------------------------------------------------------------
 // momentum force
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_force(Dims d, Geo G, ExTab X, Vel v, const double* __restrict__ br,
+__global__ void __launch_bounds__(kThreads) k_force(Dims d, Geo G, ExTab X, Vel v, const double* __restrict__ bh,
+                                                    const double* __restrict__ br,
                                                     const double* __restrict__ bt, const double* __restrict__ bp,
                                                     const double* __restrict__ jr, const double* __restrict__ jt,
                                                     const double* __restrict__ jp, const double* __restrict__ dt_dev,
@@ -303,7 +354,7 @@ __global__ void __launch_bounds__(kThreads) k_force(Dims d, Geo G, ExTab X, Vel 
         adv[1] += (u[0] * u[1] - u[2] * u[2] * cot) * irc;
         adv[2] += (u[0] * u[2] + u[1] * u[2] * cot) * irc;
         double B[3], J[3];
-        bcentre(d, br, bt, bp, i, j, k, B);
+        bcentre(d, G, bh, br, bt, bp, i, j, k, B);
         jcentre(d, jr, jt, jp, i, j, k, J);
         const double irho = sh[3];
         const double jxb0 = J[1] * B[2] - J[2] * B[1];
@@ -328,16 +379,18 @@ void force(mhd_grid_s* g, const double* vr, const double* vt, const double* vp, 
            const double* br, const double* bt, const double* bp, const double* dt_dev, double dt_host,
            const double* b_avg, double* b) {
     current_edges(g, br, bt, bp);
+    bt_harmonics(g, bt);
     Vel v{vr, vt, vp, dlt, dfac, g->d.N};
     const int blocks = grid_blocks(g, g->d.N, 8);
-    k_force<<<blocks, kThreads, 0, g->stream>>>(g->d, g->geo, g->ex, v, br, bt, bp, g->er, g->et, g->ep, dt_dev, dt_host,
-                                                b_avg, b);
+    k_force<<<blocks, kThreads, 0, g->stream>>>(g->d, g->geo, g->ex, v, g->bharm, br, bt, bp, g->er, g->et, g->ep,
+                                                dt_dev, dt_host, b_avg, b);
 }
 
 // ------------------------------------------------------------------------------------------
 // electric field and constrained transport
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_ecentre(Dims d, Vel v, const double* __restrict__ br,
+__global__ void __launch_bounds__(kThreads) k_ecentre(Dims d, Geo G, Vel v, const double* __restrict__ bh,
+                                                      const double* __restrict__ br,
                                                       const double* __restrict__ bt, const double* __restrict__ bp,
                                                       const double* __restrict__ jr, const double* __restrict__ jt,
                                                       const double* __restrict__ jp, double eta,
@@ -350,7 +403,7 @@ __global__ void __launch_bounds__(kThreads) k_ecentre(Dims d, Vel v, const doubl
         const int j = (int)(ij % d.nt), i = (int)(ij / d.nt);
         double u[3], B[3];
         v.at(c, u);
-        bcentre(d, br, bt, bp, i, j, k, B);
+        bcentre(d, G, bh, br, bt, bp, i, j, k, B);
         double e0 = -(u[1] * B[2] - u[2] * B[1]);
         double e1 = -(u[2] * B[0] - u[0] * B[2]);
         double e2 = -(u[0] * B[1] - u[1] * B[0]);
@@ -471,8 +524,9 @@ void induction(mhd_grid_s* g, const double* vr, const double* vt, const double* 
     const Dims d = g->d;
     if (eta != 0.0) current_edges(g, br, bt, bp);
     Vel v{vr, vt, vp, dlt, dfac, d.N};
-    k_ecentre<<<grid_blocks(g, d.N, 8), kThreads, 0, g->stream>>>(d, v, br, bt, bp, g->er, g->et, g->ep, eta,
-                                                                 g->ec);
+    bt_harmonics(g, bt);
+    k_ecentre<<<grid_blocks(g, d.N, 8), kThreads, 0, g->stream>>>(d, g->geo, v, g->bharm, br, bt, bp, g->er, g->et,
+                                                                 g->ep, eta, g->ec);
     k_ring<<<2 * d.nr, kThreads, 0, g->stream>>>(d, g->ec, g->ring);
     const long long ne = (long long)d.nr * (d.nt + 1) * d.np + (long long)(d.nr + 1) * d.nt * d.np +
                          (long long)(d.nr + 1) * (d.nt + 1) * d.np;

@@ -270,6 +270,8 @@ extern "C" mhd_status_t mhd_grid_create(const mhd_grid_desc_t* desc, void* cuda_
          dalloc(&g->et, (size_t)(nr + 1) * nt * d.np, owned) &&
          dalloc(&g->ep, (size_t)(nr + 1) * (nt + 1) * d.np, owned) && dalloc(&g->ec, n3, owned) &&
          dalloc(&g->ring, 2 * (size_t)nr, owned) && dalloc(&g->sts_tab, 8 * (size_t)nr * nt, owned);
+    double* pcs = nullptr;
+    ok = ok && dalloc(&pcs, 2 * (size_t)d.np, owned) && dalloc(&g->bharm, 8 * (size_t)nr, owned);
     ok = ok && dalloc(&g->partials, (size_t)kMaxBlocks * kPartialsPerBlock + 16, owned) &&
          dalloc(&g->sc, 1, owned) && dalloc(&g->ss, 1, owned);
     if (!ok) {
@@ -298,6 +300,14 @@ extern "C" mhd_status_t mhd_grid_create(const mhd_grid_desc_t* desc, void* cuda_
          up(rho, h.rho) && up(rhoV, h.rhoV) && up(kt2, h.kt2) && up(wr, h.wr) && up(wt, h.wt) && up(wp, h.wp);
     ok = ok && up(x_sh, hx.sh) && up(x_ihp, hx.ihp) && up(x_cot, hx.cot) && up(x_jr, hx.jr) && up(x_jt, hx.jt) &&
          up(x_jp, hx.jp) && up(x_fr, hx.fr) && up(x_ft, hx.ft) && up(x_fp, hx.fp);
+    std::vector<double> h_pcs(2 * (size_t)d.np);
+    for (int k = 0; k < d.np; k++) {
+        const double ph = (k + 0.5) * (2.0 * 3.14159265358979323846 / d.np);
+        h_pcs[k] = std::cos(ph);
+        h_pcs[d.np + k] = std::sin(ph);
+    }
+    ok = ok && up(pcs, h_pcs);
+    ok = ok && cudaMemsetAsync(g->bharm, 0, sizeof(double) * 8 * nr, g->stream) == cudaSuccess;
     ok = ok && cudaMemsetAsync(g->partials, 0, sizeof(double) * kMaxBlocks * kPartialsPerBlock, g->stream) == cudaSuccess;
     ok = ok && cudaMemsetAsync(g->sc, 0, sizeof(PcgScalars), g->stream) == cudaSuccess;
     ok = ok && cudaMemsetAsync(g->ss, 0, sizeof(StepScalars), g->stream) == cudaSuccess;
@@ -324,6 +334,8 @@ extern "C" mhd_status_t mhd_grid_create(const mhd_grid_desc_t* desc, void* cuda_
     G.dth = 3.14159265358979323846 / nt;
     G.dph = 2.0 * 3.14159265358979323846 / d.np;
     G.max_kt2 = h.max_kt2;
+    G.pcs = pcs;
+    G.pole_f = 2.0 / (d.np * std::cos(G.dth));
     ExTab& X = g->ex;
     X.sh = x_sh; X.ihp = x_ihp; X.cot = x_cot; X.jr = x_jr; X.jt = x_jt; X.jp = x_jp;
     X.fr = x_fr; X.ft = x_ft; X.fp = x_fp;

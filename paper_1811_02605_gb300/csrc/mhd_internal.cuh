@@ -85,9 +85,22 @@ struct Geo {
                          //             wr[nr] = 0: Neumann at r1)
     const double* wt;    // [nr*(nt+1)] theta-face weights (0 at the poles)
     const double* wp;    // [nr*nt] phi-face weight (each of the two faces)
+    const double* pcs;   // [2*np] cos, then sin, of the phi centres (polar pole values)
     double r0, r1, dth, dph;
     double max_kt2;
+    double pole_f;       // 2 / (np cos(dth)): first-harmonic pole value of the B_theta face ring
 };
+
+// B_theta at a cell centre of a polar ring (reading R4): the mean of the non-polar face value and
+// of the pole value along the cell's meridian. The pole value is the first phi harmonic of the
+// B_theta face ring next to the pole (h: that ring's sums of B_theta cos(phi_c) and B_theta
+// sin(phi_c)), evaluated at phi_c_k and divided by cos(dth), the factor by which the horizontal
+// part of the theta unit vector shrinks between the axis and the ring.
+__device__ __forceinline__ double polar_btc(const Geo& G, int np, const double* __restrict__ h, int k,
+                                            double face) {
+    const double pole = (h[0] * G.pcs[k] + h[1] * G.pcs[np + k]) * G.pole_f;
+    return 0.5 * (face + pole);
+}
 
 // Operator tables of M_alpha for one solve, in the Jacobi-scaled form
 // A~ = S M S, S = diag(M)^(-1/2): unit diagonal, off-diagonals -a (a >= 0).
@@ -237,6 +250,9 @@ struct mhd_grid_s {
     double *er, *et, *ep;   // edge arrays (E or J)
     double *ec;             // cell-centred E (3N)
     double *ring;           // [2*nr] polar ring sums
+    double *bharm;          // [8*nr] first-harmonic sums of the rings next to the poles: [0, 4 nr) of
+                            // the B_theta faces (north rows, then south; cos and sin per row), [4 nr,
+                            // 8 nr) scratch of the adjoint's transpose
     double *sts_tab;        // [8*nr*nt] RKL2 stage coefficients (nu dt / (rho V) times K's weights)
     double* partials;       // [kMaxBlocks * kPartialsPerBlock]
     void* adj_mem;          // adjoint workspace, allocated by the first adjoint call
@@ -296,6 +312,13 @@ void current_edges(mhd_grid_s* g, const double* br, const double* bt, const doub
                    cudaStream_t st = nullptr);
 // polar ring sums of a cell-centred array into the grid's ring buffer (north rows, then south)
 void ring_sums(mhd_grid_s* g, const double* a, cudaStream_t st);
+// first-harmonic sums (cos, sin of the phi centres) of the rows next to the poles of an array of
+// np-element rows: out[2 b], out[2 b + 1] for b = i (row off_n + i stride_i) and b = nr + i (row
+// off_s + i stride_i), i < nr
+void ring_harmonics(mhd_grid_s* g, const double* a, long long stride_i, long long off_n, long long off_s,
+                    double* out, cudaStream_t st);
+// the B_theta face rings j = 1 and nt - 1 into g->bharm (read by every cell-centred B)
+void bt_harmonics(mhd_grid_s* g, const double* bt, cudaStream_t st = nullptr);
 // B -= dt curl_h E with E in the grid's edge arrays (dt from the device scalar)
 void ct_apply(mhd_grid_s* g, const double* dt_dev, double* br, double* bt, double* bp);
 void force(mhd_grid_s* g, const double* vr, const double* vt, const double* vp,

@@ -6,7 +6,8 @@
 // allowed, and plug-in code run under an allocator policy that forbids new device allocations.
 // mhd_grid_create allocates the grid's tables and workspace, so those callers cannot use
 // mhd_force; this entry point takes the grid description instead and keeps all its scratch
-// (metric tables, current density on edges, polar ring sums) in one file-scope device array.
+// (metric tables, current density on edges, polar ring sums and harmonics) in one file-scope
+// device array.
 //
 // The scratch array is static device memory: every GPU that loads the library holds it until
 // the process exits. Its address is looked up once per device with cudaGetSymbolAddress on the
@@ -51,9 +52,14 @@ __global__ void k_noalloc_radial(int nr, double r0, double r1, double s, double*
 }
 
 // the remaining tables the force kernels read
-__global__ void k_noalloc_tables(int nr, int nt, double r0, double dth, double dph, const double* r, double* rc,
-                                 double* sn, double* cn, double* sc, double* cc, double* rho, double* rhoV) {
+__global__ void k_noalloc_tables(int nr, int nt, int np, double r0, double dth, double dph, const double* r,
+                                 double* rc, double* sn, double* cn, double* sc, double* cc, double* rho, double* rhoV,
+                                 double* pcs) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < np) {
+        pcs[idx] = cos((idx + 0.5) * dph);
+        pcs[np + idx] = sin((idx + 0.5) * dph);
+    }
     if (idx <= nt) {
         sn[idx] = (idx == 0 || idx == nt) ? 0.0 : sin(idx * dth);
         cn[idx] = (idx == 0) ? 1.0 : (idx == nt ? -1.0 : cos(idx * dth));
@@ -118,11 +124,11 @@ extern "C" mhd_status_t mhd_force_noalloc(const mhd_grid_desc_t* desc, const mhd
     const long long N = (long long)d.nr * d.nt * d.np;
     const long long nr = d.nr, nt = d.nt, np = d.np;
     // scratch layout (doubles): r, rc, sn, cn, sc, cc, rho, rhoV, the explicit tables (shell, 1/(r sin
-    // dph), cot, edge rows), jr, jt, jp, ring
+    // dph), cot, edge rows), jr, jt, jp, ring, cos / sin of the phi centres, polar B_theta harmonics
     const long long n_ex = 5 * nr + nr * nt + nt + 4 * nr * (nt + 1) + 3 * (nr + 1) * nt + 3 * (nr + 1) * (nt + 1);
     const long long n_tab = (nr + 1) + nr + 2 * (nt + 1) + 2 * nt + nr + nr * nt + n_ex;
     const long long n_edge = nr * (nt + 1) * np + (nr + 1) * nt * np + (nr + 1) * (nt + 1) * np;
-    const long long need = n_tab + n_edge + 2 * nr + 18 * 16;  // +16 doubles alignment slack per table
+    const long long need = n_tab + n_edge + 2 * nr + 2 * np + 4 * nr + 20 * 16;  // +16 doubles alignment slack per table
     if (N > kMaxCells || need > kScratchDoubles) return MHD_ERR_ARG;
 
     int dev = 0;
@@ -152,6 +158,8 @@ extern "C" mhd_status_t mhd_force_noalloc(const mhd_grid_desc_t* desc, const mhd
     double* jt = take((nr + 1) * nt * np);
     double* jp = take((nr + 1) * (nt + 1) * np);
     double* ring = take(2 * nr);
+    double* pcs = take(2 * np);
+    double* bharm = take(4 * nr);   // north and south B_theta rings; the adjoint half is not used here
     if (off > kScratchDoubles) return MHD_ERR_ARG;
 
     // a grid view on the stack whose tables and workspace live in the static scratch
@@ -197,6 +205,8 @@ extern "C" mhd_status_t mhd_force_noalloc(const mhd_grid_desc_t* desc, const mhd
     v.geo.r1 = r_last;
     v.geo.dth = dth;
     v.geo.dph = dph;
+    v.geo.pcs = pcs;
+    v.geo.pole_f = 2.0 / (d.np * std::cos(dth));
     v.ex.sh = x_sh;
     v.ex.ihp = x_ihp;
     v.ex.cot = x_cot;
@@ -208,11 +218,13 @@ extern "C" mhd_status_t mhd_force_noalloc(const mhd_grid_desc_t* desc, const mhd
     v.et = jt;
     v.ep = jp;
     v.ring = ring;
+    v.bharm = bharm;
 
     k_noalloc_radial<<<1, 1, 0, v.stream>>>(d.nr, d.r0, d.r1, d.stretch, r);
-    const long long nt_work = nr * nt > nt + 1 ? nr * nt : nt + 1;
-    k_noalloc_tables<<<(int)((nt_work + 255) / 256), 256, 0, v.stream>>>(d.nr, d.nt, d.r0, dth, dph, r, rc, sn, cn,
-                                                                         sc, cc, rho, rhoV);
+    long long nt_work = nr * nt > nt + 1 ? nr * nt : nt + 1;
+    if (np > nt_work) nt_work = np;
+    k_noalloc_tables<<<(int)((nt_work + 255) / 256), 256, 0, v.stream>>>(d.nr, d.nt, d.np, d.r0, dth, dph, r, rc, sn,
+                                                                         cn, sc, cc, rho, rhoV, pcs);
     const mhd::GeoView gv{r, rc, sn, cn, sc, cc, rho, d.nr, d.nt, d.r0, dth, dph};
     const long long nodes = (nr + 1) * (nt + 1);
     k_noalloc_ex<<<(int)((nodes + 255) / 256), 256, 0, v.stream>>>(gv, x_sh, x_ihp, x_cot, x_jr, x_jt, x_jp);

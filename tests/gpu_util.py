@@ -33,3 +33,13 @@ def rel_l2(a, b):
     b = np.asarray(b, dtype=np.float64).ravel()
     nb = np.linalg.norm(b)
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def oracle_iterate_at(og, alpha, b, it, itr, xr, x0=None, **kw):
+    """The oracle's PCG iterate after the GPU's own iteration count `it`: xr (the oracle's
+    converged iterate after itr iterations) when the counts agree, else a fixed-count oracle run
+    from the same start, so that the 1e-11 gate always compares the same number of Krylov steps."""
+    if it == itr:
+        return xr
+    x, _, _, _ = og.pcg(alpha, b, x0=x0, fixed_iters=it, **kw)
+    return x

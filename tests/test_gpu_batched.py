@@ -10,7 +10,9 @@ import torch
 import oracle as O
 import paper_1811_02605_gb300 as P
 from paper_1811_02605_gb300 import inputs as I
-from tests.gpu_util import rel_l2, to_dev, to_np
+from concurrent.futures import ThreadPoolExecutor
+
+from tests.gpu_util import oracle_iterate_at, rel_l2, to_dev, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -51,9 +53,8 @@ def test_batched_matches_single_solves_and_oracle():
         assert rr[s] <= 1e-9
         xo, ito, _, _ = og.pcg(alpha, b, tol=1e-9)
         assert abs(it[s] - ito) <= 1, (s, it[s], ito)
-        if it[s] == ito:
-            assert rel_l2(to_np(xs[s]), xo) < 1e-11, s
-        assert rel_l2(to_np(xs[s]), xo) < 1e-8
+        xo = oracle_iterate_at(og, alpha, b, it[s], ito, xo)
+        assert rel_l2(to_np(xs[s]), xo) < 1e-11, (s, it[s], ito)
     # a replay of the same plan (CUDA graph) from the same start is bit-for-bit identical
     xs2 = [torch.zeros_like(b) for b in bs]
     st2, it2, rr2 = P.pcg_solve_batched(grids, [a for _, _, a, _ in items], bs, xs2, prm)
@@ -64,6 +65,54 @@ def test_batched_matches_single_solves_and_oracle():
     xs3 = [torch.ones_like(b) for b in bs]
     st3, it3, rr3 = P.pcg_solve_batched(grids, [a for _, _, a, _ in items], bs, xs3, prm)
     assert st3 == P.MHD_OK and max(rr3) <= 1e-9
+
+
+def _configured_items(indices):
+    # systems of the 64-item batched workload (nt in {32, 48, ..., 128}, nr = nt, np = 2 nt,
+    # stretch in [1.02, 1.08], smooth 5-mode right-hand side)
+    all_items = I.batched_items(64)
+    out = []
+    for q in indices:
+        it = all_items[q]
+        d = it["desc"]
+        og = O.Grid.from_desc(d)
+        out.append((d, og, X0 / og.ktilde2().max(), I.smooth_field(d, it["modes"]) * og.volumes()[None, :, :, None]))
+    return out
+
+
+def test_batched_configured_sizes_match_oracle():
+    # nt = 32, 48, 64, 80 in one launch, each against the oracle (oracle solves run in threads: the
+    # ctypes calls release the GIL). At the workload tolerance 1e-9: iteration counts within one.
+    # At this SI-like conditioning two correct CG implementations stopped at tol agree to about 1%
+    # of their distance from the exact solution (measured on the oracle against itself with another
+    # summation order: 2.4e-11 at nt = 32 and 1.7e-10 at nt = 48 for tol 1e-9, 2.8e-13 and 1.7e-12
+    # for tol 1e-11), so the 1e-11 field gate is applied to the solves at tol 1e-11.
+    items = _configured_items([2, 6, 0, 8])
+    assert sorted(d.nt for d, _, _, _ in items) == [32, 48, 64, 80]
+    for tol in (1e-9, 1e-11):
+        grids, bs, xs, st, it, rr = _run_batched(items, P.make_params(tol=tol, max_iter=20000))
+        assert st == P.MHD_OK
+        with ThreadPoolExecutor(len(items)) as ex:
+            refs = list(ex.map(lambda t: t[1].pcg(t[2], t[3], tol=tol), items))
+        for s, ((d, og, alpha, b), (xo, ito, _, _)) in enumerate(zip(items, refs)):
+            assert abs(it[s] - ito) <= 1 and rr[s] <= tol, (tol, d.nt, it[s], ito)
+            if tol <= 1e-11:
+                xo = oracle_iterate_at(og, alpha, b, it[s], ito, xo)
+                assert rel_l2(to_np(xs[s]), xo) < 1e-11, (d.nt, it[s], ito)
+
+
+def test_batched_largest_sizes_fixed_iterations_match_oracle():
+    # nt = 128, 112, 96 (up to 4.2M cells per system): 8 iterations of every system in one launch
+    # against 8 oracle iterations (a full oracle solve at this size takes minutes; beyond about 10
+    # iterations the CG trajectory at this conditioning amplifies rounding differences)
+    items = _configured_items([4, 7, 1])
+    assert sorted(d.nt for d, _, _, _ in items) == [96, 112, 128]
+    grids, bs, xs, st, it, rr = _run_batched(items, P.make_params(tol=1e-30, max_iter=8))
+    assert st == P.MHD_ERR_NOCONV and all(i == 8 for i in it)
+    with ThreadPoolExecutor(len(items)) as ex:
+        refs = list(ex.map(lambda t: t[1].pcg(t[2], t[3], fixed_iters=8)[0], items))
+    for s, (d, _, _, _) in enumerate(items):
+        assert rel_l2(to_np(xs[s]), refs[s]) < 1e-11, d.nt
 
 
 def test_batched_edge_cases():

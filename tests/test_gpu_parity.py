@@ -4,8 +4,9 @@ Tolerances: the explicit kernels and the operator evaluate the same formulas in 
 rounding order (and with fused multiply-adds), so they agree to a few ulps relative to the
 largest term (1e-13 relative L2 for the operator, 1e-11 for the force, whose components are
 small differences of larger terms). PCG at tol 1e-9: same iteration count within +-1 and solution
-within 1e-11 relative L2 of the oracle's iterate (both follow the same Krylov recurrence; the
-scaled form differs only in rounding)."""
+within 1e-11 relative L2 of the oracle's iterate after the same number of iterations (both follow
+the same Krylov recurrence; the scaled form differs only in rounding; when the counts differ by one
+the oracle is rerun for exactly the GPU's count)."""
 import math
 
 import numpy as np
@@ -15,7 +16,7 @@ import torch
 import oracle as O
 import paper_1811_02605_gb300 as P
 from paper_1811_02605_gb300 import inputs as I
-from tests.gpu_util import dev_state, fields, grid, rel_l2, to_dev, to_np
+from tests.gpu_util import dev_state, fields, grid, oracle_iterate_at, rel_l2, to_dev, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -111,9 +112,8 @@ def test_pcg_fp64_matches_oracle(d):
         assert st == P.MHD_OK and str_ == O.OK
         assert abs(it - itr) <= 1, (it, itr)
         assert rr <= 1e-9
-        if it == itr:
-            assert rel_l2(to_np(x), xr) < 1e-11
-        assert rel_l2(to_np(x), xr) < 1e-8
+        xo = oracle_iterate_at(og, alpha, b, it, itr, xr, x0=x0)
+        assert rel_l2(to_np(x), xo) < 1e-11, (it, itr)
 
 
 def test_pcg_fixed_iteration_trajectory():
@@ -265,8 +265,8 @@ def test_pcg_fp64_tiled_path_matches_oracle():
         st, it, ou, rr = P.pcg_solve(g, alpha, to_dev(b), x, P.make_params(tol=1e-9, max_iter=5000))
         xr, itr, _, s2 = og.pcg(alpha, b, x0=x0, tol=1e-9, max_iter=5000)
         assert st == P.MHD_OK and abs(it - itr) <= 1, (it, itr)
-        if it == itr:
-            assert rel_l2(to_np(x), xr) < 1e-11
+        xo = oracle_iterate_at(og, alpha, b, it, itr, xr, x0=x0)
+        assert rel_l2(to_np(x), xo) < 1e-11, (it, itr)
     for k in (1, 3, 11):
         x = torch.zeros(b.shape, dtype=torch.float64, device="cuda")
         st, it, ou, rr = P.pcg_solve(g, 2.0, to_dev(b), x, P.make_params(tol=1e-30, max_iter=k))

@@ -9,7 +9,7 @@ import torch
 import oracle as O
 import paper_1811_02605_gb300 as P
 from paper_1811_02605_gb300 import inputs as I
-from tests.gpu_util import dev_state, fields, grid, rel_l2, to_dev, to_np
+from tests.gpu_util import dev_state, fields, grid, oracle_iterate_at, rel_l2, to_dev, to_np
 
 pytestmark = pytest.mark.gpu
 KEYS = ("vr", "vt", "vp", "br", "bt", "bp")
@@ -32,9 +32,8 @@ def test_pcg_pc2_matches_oracle(d, nc):
         assert st == P.MHD_OK and str_ == O.OK
         assert abs(it - itr) <= 1, (it, itr)
         assert rr <= 1e-9
-        if it == itr:
-            assert rel_l2(to_np(x), xr) < 1e-11
-        assert rel_l2(to_np(x), xr) < 1e-8
+        xo = oracle_iterate_at(og, alpha, b, it, itr, xr, x0=x0, pc2="lines")
+        assert rel_l2(to_np(x), xo) < 1e-11, (it, itr)
 
 
 def test_pcg_pc2_fixed_iteration_trajectory():

@@ -1,6 +1,6 @@
 """GPU single-reduction (Chronopoulos-Gear) Jacobi PCG against the oracle's og_pcg_cg and
 og_step_cg, through the C ABI: iteration counts within one, solutions and fields within 1e-11
-rel-L2 where the counts agree (the same gates as the Hestenes-Stiefel form)."""
+rel-L2 of the oracle's iterate after the GPU's own iteration count (the same gates as the Hestenes-Stiefel form)."""
 import numpy as np
 import pytest
 import torch
@@ -8,7 +8,7 @@ import torch
 import oracle as O
 import paper_1811_02605_gb300 as P
 from paper_1811_02605_gb300 import inputs as I
-from tests.gpu_util import dev_state, fields, grid, rel_l2, to_dev, to_np
+from tests.gpu_util import dev_state, fields, grid, oracle_iterate_at, rel_l2, to_dev, to_np
 
 pytestmark = pytest.mark.gpu
 KEYS = ("vr", "vt", "vp", "br", "bt", "bp")
@@ -30,9 +30,8 @@ def test_pcg_cg_matches_oracle(d, nc):
         assert st == P.MHD_OK and str_ == O.OK
         assert abs(it - itr) <= 1, (it, itr)
         assert rr <= 1e-9
-        if it == itr:
-            assert rel_l2(to_np(x), xr) < 1e-11
-        assert rel_l2(to_np(x), xr) < 1e-8
+        xo = oracle_iterate_at(og, alpha, b, it, itr, xr, x0=x0, cg=True)
+        assert rel_l2(to_np(x), xo) < 1e-11, (it, itr)
 
 
 def test_pcg_cg_fixed_iteration_trajectory():

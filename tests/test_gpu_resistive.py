@@ -1,6 +1,7 @@
 """GPU implicit resistivity (Eq. 1 curl-curl term by PCG with PC1, Sec. 2.2) against the oracle's
 og_step_opts(OG_OPT_RES_IMPLICIT), through the C ABI: fields within 1e-11 rel-L2 per step and
-iteration counts within one, div B and the wall fluxes kept."""
+iteration counts within one (at eta = 0.05, on a trajectory of fixed length), div B and the wall
+fluxes kept."""
 import numpy as np
 import pytest
 import torch
@@ -16,39 +17,78 @@ GRIDS = [I.GridDesc(6, 6, 12, 1.0, 4.0, 1.1), I.GridDesc(9, 7, 10, 1.0, 6.0, 1.0
          I.GridDesc(32, 32, 64, 1.0, 20.0, 1.05)]
 
 
-# (eta, tol, iteration slack). At eta = 5e-3 the workload tolerance 1e-9 already resolves the
-# 1e-11 gate. At eta = 0.05 the face system is ill conditioned (about 250 iterations on 32x32x64):
-# two solutions that each meet tol 1e-9 or even 1e-12 differ by up to 2e-10 in the small B_phi
-# (measured on the oracle alone, tol 1e-12 against 1e-14), so the gate is applied with every solve
-# at tol 3e-14, where the counts near the rounding floor may differ by a few.
-CASES = [(5e-3, 1e-9, 1), (0.05, 3e-14, 8)]
-
-
-@pytest.mark.parametrize("d", GRIDS, ids=lambda d: f"{d.nr}x{d.nt}x{d.np}")
-@pytest.mark.parametrize("eta,tol,slack", CASES, ids=["eta5e-3", "eta5e-2"])
-def test_implicit_resistivity_step_parity(d, eta, tol, slack):
+def _steps(d, eta, tol, max_iter, nsteps=3):
     st0 = I.initial_state(d, 2, False)
     g, og = grid(d), O.Grid.from_desc(d)
     ds = dev_state(st0)
     f = fields(ds)
     s = st0
-    prm = P.make_params(nu=1e-3, eta=eta, cfl=0.4, tol=tol, max_iter=100000, resistivity_implicit=1)
-    div0 = og.divb(st0["br"], st0["bt"], st0["bp"])
-    for n in range(3):
+    prm = P.make_params(nu=1e-3, eta=eta, cfl=0.4, tol=tol, max_iter=max_iter, resistivity_implicit=1)
+    out = []
+    for n in range(nsteps):
         stat, info = P.mhd_step(g, prm, f)
         torch.cuda.synchronize()
-        s, oinfo = og.step(s, nu=1e-3, eta=eta, cfl=0.4, tol=tol, max_iter=100000, res_implicit=True)
-        assert stat == P.MHD_OK and oinfo["status"] == O.OK
-        assert abs(info["iters_res"] - oinfo["res_iters"]) <= slack, (info["iters_res"], oinfo["res_iters"])
-        assert info["iters_res"] >= 1 and info["relres_res"] <= tol
-        for q in range(3):
-            assert abs(info["iters"][q] - oinfo["iters"][q]) <= slack
-        for k in KEYS:
-            e = rel_l2(to_np(ds[k]), s[k])
-            assert e <= 1e-11, (n, k, e)
-    got = {k: to_np(v) for k, v in ds.items()}
+        s, oinfo = og.step(s, nu=1e-3, eta=eta, cfl=0.4, tol=tol, max_iter=max_iter, res_implicit=True)
+        out.append((stat, info, oinfo, {k: to_np(v) for k, v in ds.items()}, s))
+    return st0, og, out
+
+
+def _invariants(og, st0, got):
+    div0 = og.divb(st0["br"], st0["bt"], st0["bp"])
     assert np.abs(og.divb(got["br"], got["bt"], got["bp"]) - div0).max() <= 1e-12 * np.abs(st0["br"]).max()
     assert np.array_equal(got["br"][0], st0["br"][0])
+
+
+def _check_counts(res, tol):
+    for n, (stat, info, oinfo, got, ref) in enumerate(res):
+        assert stat == P.MHD_OK and oinfo["status"] == O.OK
+        assert abs(info["iters_res"] - oinfo["res_iters"]) <= 1, (n, info["iters_res"], oinfo["res_iters"])
+        assert info["iters_res"] >= 1 and info["relres_res"] <= tol
+        for q in range(3):
+            assert abs(info["iters"][q] - oinfo["iters"][q]) <= 1, (n, info["iters"], oinfo["iters"])
+
+
+def _check_fields(res, gate):
+    for n, (stat, info, oinfo, got, ref) in enumerate(res):
+        for k in KEYS:
+            e = rel_l2(got[k], ref[k])
+            assert e <= gate, (n, k, e)
+
+
+# Every solve of a step (SI, viscous, resistive) runs at the tolerance given. At the workload
+# tolerance 1e-9 the iteration counts agree within one. Converged iterates of two correct CG
+# implementations agree to about 1% of their distance from the exact solution, which at tol 1e-9
+# and this conditioning is above 1e-11 in the small B_phi (1.5e-11 at eta = 5e-3), so the 1e-11
+# field gate is applied to steps at tol 1e-11.
+@pytest.mark.parametrize("d", GRIDS, ids=lambda d: f"{d.nr}x{d.nt}x{d.np}")
+def test_implicit_resistivity_step_parity(d):
+    st0, og, res = _steps(d, 5e-3, 1e-9, 100000)
+    _check_counts(res, 1e-9)
+    _invariants(og, st0, res[-1][3])
+    st0, og, res = _steps(d, 5e-3, 1e-11, 100000)
+    _check_counts(res, 1e-11)
+    _check_fields(res, 1e-11)
+    _invariants(og, st0, res[-1][3])
+
+
+@pytest.mark.parametrize("d", GRIDS, ids=lambda d: f"{d.nr}x{d.nt}x{d.np}")
+def test_implicit_resistivity_strong_eta_parity(d):
+    # eta = 0.05: the face system is ill conditioned (about 250 iterations on 32x32x64). Counts
+    # within one at tol 1e-9; the 1e-11 field gate on a trajectory of fixed length (every solve of
+    # both sides stops at exactly 10 iterations; beyond that CG at this conditioning amplifies
+    # rounding differences) and on steps converged to tol 1e-12
+    st0, og, res = _steps(d, 0.05, 1e-9, 100000)
+    _check_counts(res, 1e-9)
+    _invariants(og, st0, res[-1][3])
+    st0, og, res = _steps(d, 0.05, 1e-30, 10)
+    for n, (stat, info, oinfo, got, ref) in enumerate(res):
+        assert stat == P.MHD_ERR_NOCONV and oinfo["status"] == O.ERR_NOCONV
+        assert info["iters_res"] == 10 == oinfo["res_iters"]
+    _check_fields(res, 1e-11)
+    _invariants(og, st0, res[-1][3])
+    st0, og, res = _steps(d, 0.05, 1e-12, 100000)
+    _check_counts(res, 1e-12)
+    _check_fields(res, 1e-11)
 
 
 def test_implicit_resistivity_zero_eta_is_the_ideal_step():

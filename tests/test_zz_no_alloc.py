@@ -5,12 +5,14 @@ device-memory budget that owns every buffer, a latency-bound loop where cudaMall
 synchronise the device, or an allocator policy that forbids new allocations). It takes the grid
 description instead of a grid object and keeps its scratch in a static device array. The test
 runs it twice in a row on different inputs (the array keeps the previous call's contents) and
-compares each result with the grid-based mhd_force within the force tolerance of the parity
-tests. This file is collected last so a first-failure run has already run every other test."""
+compares each result with the grid-based mhd_force and with the CPU oracle's force, within the
+force tolerance of the parity tests. This file is collected last so a first-failure run has
+already run every other test."""
 import numpy as np
 import pytest
 import torch
 
+import oracle as O
 import paper_1811_02605_gb300 as P
 from paper_1811_02605_gb300 import inputs as I
 
@@ -43,6 +45,11 @@ def test_force_noalloc_matches_mhd_force_two_calls():
             torch.cuda.synchronize()
             for c in range(3):
                 assert _rel(out[c], ref[c]) < 1e-11, (idx, call, c)
+            oref = O.Grid.from_desc(d).force(np.stack([st["vr"], st["vt"], st["vp"]]), st["br"], st["bt"], st["bp"], dt)
+            got = out.cpu().numpy()
+            for c in range(3):
+                e = np.linalg.norm(got[c] - oref[c]) / np.linalg.norm(oref[c])
+                assert e < 1e-11, (idx, call, c, e)
 
 
 def test_force_noalloc_rejects_too_large_grid():
