@@ -333,17 +333,21 @@ def run_ours(args):
     def mixed_entry(inner_tol, restart):
         msm, infosm, profm, clkm, dsm = run(P.PREC_MIXED, args.steps, args.warmup, True, inner_tol, restart)
         msm = maxr(msm)
-        pcg32_ms = sum(profm[k][0] for k in ("pupdate32", "spmv32", "update32", "pspmv32"))
+        pcg32_ms = sum(profm[k][0] for k in ("pupdate32", "spmv32", "update32", "pspmv32", "pfold32", "rupd32"))
         pcg32_n = max(sum(sum(i["iters"]) for i in infosm), 1)   # inner CG iterations actually run
         pcg32_gbs = PCG_BYTES_PER_CELL["fp32"] * N * pcg32_n / (pcg32_ms * 1e-3) / 1e9
         fused = profm["pspmv32"][1] > 0
-        tiled = not fused and profm["pupdate32"][1] == 0
+        recompute = profm["pfold32"][1] > 0
+        tiled = not fused and not recompute and profm["pupdate32"][1] == 0
         # per-kernel DRAM passes of a 3-component FP32 vector (4 B x 3 per cell per pass)
         # split form: the p update also adds the previous alpha p to x (r, p, x in; p, x out) and the
-        # update kernel reads r, q and writes r; fused form: r, p, x in, p, x, q out, then the update
-        kb = {"spmv32": 3 if tiled else 2, "update32": 5 if tiled else 3, "pupdate32": 5, "pspmv32": 6}
+        # update kernel reads r, q and writes r; fused form: r, p, x in, p, x, q out, then the update;
+        # recompute pair: r, p_old in, p out; then p, r in, r out, and every second iteration x,
+        # p_prev in, x out (4.5 on average)
+        kb = {"spmv32": 3 if tiled else 2, "update32": 5 if tiled else 3, "pupdate32": 5, "pspmv32": 6,
+              "pfold32": 3, "rupd32": 4.5}
         kernels = {}
-        for k in ("pupdate32", "spmv32", "pspmv32", "update32"):
+        for k in ("pupdate32", "spmv32", "pspmv32", "update32", "pfold32", "rupd32"):
             ms_k, n_k = profm[k]
             if n_k:
                 avg = ms_k / pcg32_n   # one launch per inner iteration that ran
@@ -359,6 +363,9 @@ def run_ours(args):
                     pcg_gbs=round(pcg32_gbs, 1), pcg_frac_of_hbm=round(pcg32_gbs / hbm, 4),
                     kernels=kernels, fp32_kernels=("plane-marching pair (A: p update + stencil, B: stencil + "
                                                    "update)" if tiled else
+                                                   "recompute pair (p update folded into <p, Ap>; r update "
+                                                   "with Ap recomputed, x every second iteration)" if recompute
+                                                   else
                                                    "p update folded into the stencil, then the update" if fused
                                                    else "split (p update, stencil, update)"),
                     rel_l2_vs_fp64_gpu_after_steps=err, clocks=clkm,

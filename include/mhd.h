@@ -118,9 +118,11 @@ enum { MHD_PREC_FP64 = 0, MHD_PREC_MIXED = 1 };
  *            factorisation and 3N floats for z of the FP32 iteration. pcg_solve_batched ignores it.
  *
  * Kernel variants of the FP32 inner iteration (split p update and stencil, the two folded into
- * one kernel, or plane-marching tiles) are chosen per grid by timing on its first mixed solve;
- * results agree to the order of one dot product's reduction. Diagnostics only: the environment
- * variable MHD_FORCE_SLAB skips the timing (-1 split, -2 folded, n > 0 tiles of n planes). */
+ * one kernel, the recompute pair that stores no A p, or plane-marching tiles) are chosen per grid
+ * by timing on its first mixed solve; results agree to the order of one dot product's reduction.
+ * Diagnostics only: the environment variable MHD_FORCE_SLAB skips the timing (-1 split, -2
+ * folded, -3 recompute pair, -4 recompute pair with the second kernel walking the grid backwards,
+ * n > 0 tiles of n planes). */
 typedef struct {
     double nu, eta, cfl, dt_fixed, dt_max, alpha_si_fixed;
     double tol, inner_tol;
@@ -262,7 +264,9 @@ enum {
     MHD_KERNEL_OUTER_RES = 6, MHD_KERNEL_FORCE = 7, MHD_KERNEL_INDUCTION = 8,
     MHD_KERNEL_COEFFS = 9, MHD_KERNEL_STS = 10, MHD_KERNEL_RES = 11, MHD_KERNEL_PC2 = 12,
     MHD_KERNEL_PSPMV32 = 13, /* FP32 p update folded into the stencil */
-    MHD_KERNEL_COUNT = 14
+    MHD_KERNEL_PFOLD32 = 14, /* FP32 p update folded into <p, A p>, no q stored */
+    MHD_KERNEL_RUPD32 = 15,  /* FP32 r update with A p recomputed, x every second iteration */
+    MHD_KERNEL_COUNT = 16
 };
 mhd_status_t mhd_profile_enable(mhd_grid_t grid, int enable);
 /* Total milliseconds and launch count of one kernel id since profiling was enabled.

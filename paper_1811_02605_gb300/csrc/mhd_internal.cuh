@@ -28,7 +28,8 @@ struct PcgScalars {
     double rho_prev; // rho of the previous CG iteration (residual replacement keeps the recurrence)
     int iter;        // iterations of the current (inner) solve
     int max_iter;
-    int done;        // 0 running, 1 converged, 2 iteration cap, 3 non-finite, 4 breakdown
+    int done;        // 0 running, 1 converged, 2 iteration cap, 3 non-finite, 4 breakdown, 6 device
+                     // wait timeout (bulk-copy pipeline)
     int outer;       // mixed: outer passes done
     int outer_done;  // mixed: 0 running, 1 converged, 3 non-finite
     int total_iter;  // mixed: inner iterations summed over the outer passes
@@ -268,7 +269,9 @@ struct mhd_grid_s {
     cudaGraphExec_t iter_graph[5][4];
     int graph_batch;
     int slab32;             // FP32 CG kernels: r-slab length of the tiled pair (> 0), split kernels (-1),
-                            // p update folded into the stencil (-2); 0: not tuned
+                            // p update folded into the stencil (-2), recompute pair (-3, -4 with the
+                            // r update walking backwards), bulk-staged pair with units of L planes
+                            // (-100 - L); 0: not tuned
     int slab64;             // same for the FP64 fused p-update + stencil kernel
     int pc2_fused32;        // FP32 PC2 iteration: p update folded into the stencil (1) or split (-1); 0: unset
     double visc_lambda_unit; // Gershgorin bound on the spectral radius of D^-1 K (nu = 1)
@@ -347,6 +350,10 @@ bool tiled32_ok(const mhd_grid_s* g);
 int tiled32_blocks(const mhd_grid_s* g, int slab);
 void enqueue_tiled32(mhd_grid_s* g, cudaStream_t st, int nc, int slab, int prof_a, int prof_b);
 void enqueue_tiled64_a(mhd_grid_s* g, cudaStream_t st, int slab, int prof_id);
+
+// FP32 CG iteration as a bulk-copy-staged plane-marching pair (bulk.cu); slab: planes per work unit
+bool bulk32_ok(const mhd_grid_s* g);
+void enqueue_bulk32(mhd_grid_s* g, cudaStream_t st, int nc, int slab);
 
 // PCG (pcg.cu). alpha is read from device memory (alpha_dev) so a step never syncs on it.
 void build_tables(mhd_grid_s* g, const double* alpha_dev, bool fp32);

@@ -352,6 +352,186 @@ __global__ void __launch_bounds__(kThreads, 4) k_pspmv32(Dims d, const float* __
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// FP32 inner iteration without a stored q~ (the recompute pair), two kernels per iteration:
+//   P (k_pfold32): p~ = r~ + beta p~_old at the cell and, from r~ and p~_old, at its six
+//      neighbours (the fma of the p update kernel), so <p~, A~ p~> needs no q~ in memory; p~ goes
+//      to the other half of the p double buffer. r~ and p~_old in, p~ out: 3 passes.
+//   R (k_rupd32): q~ = A~ p~ once more from the stored p~ (the same expression in the same order,
+//      so the same bits as P's on-the-fly values), r~ -= alpha q~ with <r~, r~> and sum dg r~^2.
+//      x~ is updated two iterations at a time: on every second iteration
+//      x~ = fma(alpha_k, p~_k, fma(alpha_{k-1}, p~_{k-1}, x~)), the two roundings of two single
+//      updates, with p~_{k-1} still in the other half of the double buffer (sc->ax holds
+//      alpha_{k-1} while an update is pending). p~ and r~ in, r~ out, and on every second
+//      iteration x~ and p~_{k-1} in, x~ out: 4.5 passes on average.
+// The iterates equal those of the split kernels up to the order of the <p~, q~> reduction.
+// REV: R walks the groups from the last to the first, so it starts on the p~ that P wrote last
+// (still in L2) and ends on the r~ that the next P reads first.
+// Neighbour loads are unconditional: at a wall the address is clamped to the cell itself and the
+// coefficient of that face is exactly 0 in the tables, so fma(-0, u, o) = o and the result has the
+// same bits as the branching form, while every load of the stencil can be in flight at once.
+template <int V>
+struct Nbr {
+    long long im, ip, jm, jp;   // offsets of the four neighbour groups (0 at a wall)
+    __device__ __forceinline__ Nbr(const Dims& d, const Cell& c) {
+        const long long plane = (long long)d.nt * d.np;
+        im = (c.i > 0) ? -plane : 0;
+        ip = (c.i < d.nr - 1) ? plane : 0;
+        jm = (c.j > 0) ? -(long long)d.np : 0;
+        jp = (c.j < d.nt - 1) ? (long long)d.np : 0;
+    }
+};
+
+template <int V, int NC, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_pfold32(Dims d, const float* __restrict__ r,
+                                                            float* __restrict__ pbuf, OpTab<float> t,
+                                                            PcgScalars* sc, double* __restrict__ partials) {
+    if (sc->done) return;
+    const int par = sc->par;
+    const float* __restrict__ pold = pbuf + (long long)par * 3 * d.N;
+    float* __restrict__ pnew = pbuf + (long long)(1 - par) * 3 * d.N;
+    const float beta = (float)sc->beta;
+    const int nt = d.nt;
+    const unsigned int G = (unsigned int)(d.N / V);
+    Acc<float> acc;
+    for (unsigned int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+        const Cell c = decompose<V>(d, g);
+        const Nbr<V> nb(d, c);
+        const float cr_lo = t.ar[c.i * nt + c.j], cr_hi = t.ar[(c.i + 1) * nt + c.j];
+        const float ct_lo = t.at[c.i * (nt + 1) + c.j], ct_hi = t.at[c.i * (nt + 1) + c.j + 1];
+        const float cp = t.ap[c.ij];
+        const long long row = c.base - c.k0;
+        const int km = (c.k0 == 0) ? d.np - 1 : c.k0 - 1;
+        const int kp = (c.k0 + V == d.np) ? 0 : c.k0 + V;
+#pragma unroll 1
+        for (int k = 0; k < NC; k++) {
+            const float* rk = r + k * d.N;
+            const float* pk = pold + k * d.N;
+            float rv[V], pv[V], v[V], o[V], a0[V], a1[V], b0[V], b1[V], c0[V], c1[V], e0[V], e1[V];
+            ldv<float, V>(rk + c.base, rv);
+            ldv<float, V>(pk + c.base, pv);
+            const float rkm = rk[row + km], pkm = pk[row + km], rkp = rk[row + kp], pkp = pk[row + kp];
+            ldv<float, V>(rk + c.base + nb.im, a0);
+            ldv<float, V>(pk + c.base + nb.im, a1);
+            ldv<float, V>(rk + c.base + nb.ip, b0);
+            ldv<float, V>(pk + c.base + nb.ip, b1);
+            ldv<float, V>(rk + c.base + nb.jm, c0);
+            ldv<float, V>(pk + c.base + nb.jm, c1);
+            ldv<float, V>(rk + c.base + nb.jp, e0);
+            ldv<float, V>(pk + c.base + nb.jp, e1);
+#pragma unroll
+            for (int e = 0; e < V; e++) v[e] = fmaf(beta, pv[e], rv[e]);
+            stv<float, V>(pnew + k * d.N + c.base, v);
+            const float ukm = fmaf(beta, pkm, rkm);
+            const float ukp = fmaf(beta, pkp, rkp);
+#pragma unroll
+            for (int e = 0; e < V; e++) {
+                const float left = (e == 0) ? ukm : v[e - 1];
+                const float right = (e == V - 1) ? ukp : v[e + 1];
+                o[e] = fmaf(-cp, left + right, v[e]);
+                o[e] = fmaf(-cr_lo, fmaf(beta, a1[e], a0[e]), o[e]);
+                o[e] = fmaf(-cr_hi, fmaf(beta, b1[e], b0[e]), o[e]);
+                o[e] = fmaf(-ct_lo, fmaf(beta, c1[e], c0[e]), o[e]);
+                o[e] = fmaf(-ct_hi, fmaf(beta, e1[e], e0[e]), o[e]);
+            }
+#pragma unroll
+            for (int e = 0; e < V; e++) acc.fma_add(v[e], o[e]);
+        }
+    }
+    double val[1] = {acc.get()}, out[1];
+    if (reduce_last<1>(val, partials, &sc->count, out) && threadIdx.x == 0) {
+        const double pq = out[0];
+        sc->pq = pq;
+        sc->par = 1 - par;
+        if (!finite(pq)) sc->done = 3;
+        else if (!(pq > 0.0)) sc->done = 4;
+        else sc->alpha = sc->rho / pq;
+    }
+}
+
+template <int V, int NC, bool REV, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_rupd32(Dims d, float* __restrict__ x, float* __restrict__ r,
+                                                           const float* __restrict__ pbuf, OpTab<float> t,
+                                                           const double* __restrict__ dg, PcgScalars* sc,
+                                                           double* __restrict__ partials) {
+    if (sc->done) return;
+    const int par = sc->par;   // P has flipped it: the half holding p~_k
+    const float* __restrict__ p = pbuf + (long long)par * 3 * d.N;
+    const float* __restrict__ pprev = pbuf + (long long)(1 - par) * 3 * d.N;
+    const float al = (float)sc->alpha;
+    const float axp = (float)sc->ax;
+    const bool pair = (sc->ax != 0.0);
+    const int nt = d.nt;
+    const unsigned int G = (unsigned int)(d.N / V);
+    Acc<float> a_rho;
+    double a_rr = 0.0;
+    for (unsigned int g0 = blockIdx.x * blockDim.x + threadIdx.x; g0 < G; g0 += gridDim.x * blockDim.x) {
+        const unsigned int g = REV ? G - 1u - g0 : g0;
+        const Cell c = decompose<V>(d, g);
+        const Nbr<V> nb(d, c);
+        const float cr_lo = t.ar[c.i * nt + c.j], cr_hi = t.ar[(c.i + 1) * nt + c.j];
+        const float ct_lo = t.at[c.i * (nt + 1) + c.j], ct_hi = t.at[c.i * (nt + 1) + c.j + 1];
+        const float cp = t.ap[c.ij];
+        const long long row = c.base - c.k0;
+        const int km = (c.k0 == 0) ? d.np - 1 : c.k0 - 1;
+        const int kp = (c.k0 + V == d.np) ? 0 : c.k0 + V;
+        float rs[V];
+        zerov<float, V>(rs);
+#pragma unroll 1
+        for (int k = 0; k < NC; k++) {
+            const float* pk = p + k * d.N;
+            float v[V], o[V], rv[V], a[V], b[V], cc[V], e4[V];
+            ldv<float, V>(pk + c.base, v);
+            const float ukm = pk[row + km], ukp = pk[row + kp];
+            ldv<float, V>(pk + c.base + nb.im, a);
+            ldv<float, V>(pk + c.base + nb.ip, b);
+            ldv<float, V>(pk + c.base + nb.jm, cc);
+            ldv<float, V>(pk + c.base + nb.jp, e4);
+            ldv<float, V>(r + k * d.N + c.base, rv);
+#pragma unroll
+            for (int e = 0; e < V; e++) {
+                const float left = (e == 0) ? ukm : v[e - 1];
+                const float right = (e == V - 1) ? ukp : v[e + 1];
+                o[e] = fmaf(-cp, left + right, v[e]);
+                o[e] = fmaf(-cr_lo, a[e], o[e]);
+                o[e] = fmaf(-cr_hi, b[e], o[e]);
+                o[e] = fmaf(-ct_lo, cc[e], o[e]);
+                o[e] = fmaf(-ct_hi, e4[e], o[e]);
+                rv[e] = fmaf(-al, o[e], rv[e]);
+                rs[e] = fmaf(rv[e], rv[e], rs[e]);
+            }
+            stv<float, V>(r + k * d.N + c.base, rv);
+            if (pair) {
+                float xv[V], pp[V];
+                ldv<float, V>(x + k * d.N + c.base, xv);
+                ldv<float, V>(pprev + k * d.N + c.base, pp);
+#pragma unroll
+                for (int e = 0; e < V; e++) xv[e] = fmaf(al, v[e], fmaf(axp, pp[e], xv[e]));
+                stv<float, V>(x + k * d.N + c.base, xv);
+            }
+        }
+        float cell = rs[0];
+#pragma unroll
+        for (int e = 1; e < V; e++) cell += rs[e];
+        a_rho.add(cell);
+        a_rr = fma(dg[c.ij], (double)cell, a_rr);
+    }
+    double val[2] = {a_rho.get(), a_rr}, out[2];
+    if (reduce_last<2>(val, partials, &sc->count, out) && threadIdx.x == 0) {
+        const double rho = out[0], rr = out[1];
+        sc->iter += 1;
+        sc->total_iter += 1;
+        sc->rho_prev = sc->rho;
+        sc->beta = rho / sc->rho;
+        sc->rho = rho;
+        sc->rr = rr;
+        sc->ax = pair ? 0.0 : sc->alpha;   // pending: alpha_k p~_k, p~_k in the current half
+        if (!finite(rr) || !finite(rho)) sc->done = 3;
+        else if (sqrt(rr) <= sc->tol * sqrt(sc->bb)) sc->done = 1;
+        else if (sc->iter >= sc->max_iter) sc->done = 2;
+    }
+}
+
 // B: x += alpha p, r -= alpha q, rho = <r~, r~>, rr = sum dg r~^2; last CTA: beta, stop test.
 // PAR: p lives in the buffer that a fused p-update kernel just wrote (the other half of a double
 // buffer of stride 3N, chosen by the device-side parity), and the parity flips at the end.
@@ -817,6 +997,40 @@ void enqueue_fused32(mhd_grid_s* g, cudaStream_t st) {
     prof_end(g, st, s);
 }
 
+// FP32 inner iteration by the recompute pair (no q~ stored; x~ updated every second iteration); MINB:
+// CTAs per SM the kernels are compiled for (registers per thread 65536 / (256 MINB))
+template <int V, int NC, int MINB>
+void enqueue_recompute32(mhd_grid_s* g, cudaStream_t st, bool rev) {
+    const Dims d = g->d;
+    int s = prof_begin(g, st, MHD_KERNEL_PFOLD32);
+    k_pfold32<V, NC, MINB><<<grid_blocks(g, d.N / V, resident_per_sm<k_pfold32<V, NC, MINB>>()), kThreads, 0, st>>>(
+        d, g->r32, g->p32, g->t32, g->sc, g->partials);
+    prof_end(g, st, s);
+    s = prof_begin(g, st, MHD_KERNEL_RUPD32);
+    if (rev)
+        k_rupd32<V, NC, true, MINB><<<grid_blocks(g, d.N / V, resident_per_sm<k_rupd32<V, NC, true, MINB>>()), kThreads,
+                                      0, st>>>(d, g->x32, g->r32, g->p32, g->t32, g->tu.dg, g->sc, g->partials);
+    else
+        k_rupd32<V, NC, false, MINB><<<grid_blocks(g, d.N / V, resident_per_sm<k_rupd32<V, NC, false, MINB>>()),
+                                       kThreads, 0, st>>>(d, g->x32, g->r32, g->p32, g->t32, g->tu.dg, g->sc,
+                                                          g->partials);
+    prof_end(g, st, s);
+}
+
+template <int V, int MINB>
+void enqueue_recompute32_nc(mhd_grid_s* g, cudaStream_t st, int nc, bool rev) {
+    if (nc == 3) enqueue_recompute32<V, 3, MINB>(g, st, rev);
+    else if (nc == 2) enqueue_recompute32<V, 2, MINB>(g, st, rev);
+    else enqueue_recompute32<V, 1, MINB>(g, st, rev);
+}
+
+// -3 / -4: 4 CTAs per SM (64 registers); -5: 6 CTAs per SM (40 registers), forwards
+template <int V>
+void enqueue_recompute32_var(mhd_grid_s* g, cudaStream_t st, int nc) {
+    if (g->slab32 == -5) enqueue_recompute32_nc<V, 6>(g, st, nc, false);
+    else enqueue_recompute32_nc<V, 4>(g, st, nc, g->slab32 == -4);
+}
+
 template <int V>
 void enqueue_fused32_nc(mhd_grid_s* g, cudaStream_t st, int nc) {
     if (nc == 3) enqueue_fused32<V, 3>(g, st);
@@ -921,6 +1135,14 @@ void enqueue_iteration(mhd_grid_s* g, cudaStream_t st, int prec, int nc) {
     } else if (prec == 0) {
         enqueue_split_nc<double, 2>(g, st, nc, g->x64, g->r64, g->p64, g->q64, g->t64,
                                     grid_blocks(g, d.N / 2, kPerSmIter), MHD_KERNEL_PUPDATE64);
+    } else if (g->slab32 <= -100) {
+        // plane-marching pair with bulk-copy staging, when the autotuner measured it fastest
+        enqueue_bulk32(g, st, nc, -100 - g->slab32);
+    } else if (g->slab32 == -3 || g->slab32 == -4 || g->slab32 == -5) {
+        // recompute pair, when the autotuner measured it fastest (-4: the r update walks backwards,
+        // -5: compiled for 6 CTAs per SM)
+        if (use_v4(g)) enqueue_recompute32_var<4>(g, st, nc);
+        else enqueue_recompute32_var<2>(g, st, nc);
     } else if (g->slab32 == -2) {
         // p update folded into the stencil, when the autotuner measured it fastest
         if (use_v4(g)) enqueue_fused32_nc<4>(g, st, nc);
@@ -1053,7 +1275,8 @@ int forced_slab() {
 mhd_status_t tune_slab32(mhd_grid_s* g, int nc) {
     if (g->slab32 != 0) return MHD_OK;
     if (const int f = forced_slab()) {
-        if (f == -2) g->slab32 = -2;
+        if (f == -2 || f == -3 || f == -4 || f == -5) g->slab32 = f;
+        else if (f <= -100) g->slab32 = (bulk32_ok(g) && f < -100) ? f : -1;
         else g->slab32 = (f > 0 && tiled32_ok(g) && tiled32_blocks(g, f) <= kMaxBlocks) ? f : -1;
         return MHD_OK;
     }
@@ -1067,8 +1290,12 @@ mhd_status_t tune_slab32(mhd_grid_s* g, int nc) {
     // reduction trips a breakdown flag (the solve's set-up overwrites every vector afterwards)
     const size_t n3 = 3 * (size_t)g->d.N;
     // candidates -1: the split kernels (p update, stencil, update); -2: the p update folded into
-    // the stencil, then the update
-    for (int cand : {-1, -2}) {
+    // the stencil, then the update; -3, -4, -5: the recompute pair (no q~ stored), forwards, with
+    // the r update walking backwards, or at 6 CTAs per SM; -132, -164: the same pair as
+    // plane-marching kernels staged by bulk copies (units of 32 or 64 planes). Four iterations each after one untimed: an even count, so
+    // each is timed with its x updates.
+    for (int cand : {-1, -2, -3, -4, -5, -132, -164}) {
+        if (cand <= -100 && !bulk32_ok(g)) continue;
         k_tune_reset<<<1, 1, 0, g->stream>>>(g->sc);
         g->slab32 = cand;
         cudaMemsetAsync(g->r32, 0x3F, sizeof(float) * n3, g->stream);
@@ -1076,11 +1303,12 @@ mhd_status_t tune_slab32(mhd_grid_s* g, int nc) {
         cudaMemsetAsync(g->x32, 0, sizeof(float) * n3, g->stream);
         enqueue_iteration(g, g->stream, 1, nc);
         cudaEventRecord(e0, g->stream);
-        for (int it = 0; it < 3; it++) enqueue_iteration(g, g->stream, 1, nc);
+        for (int it = 0; it < 4; it++) enqueue_iteration(g, g->stream, 1, nc);
         cudaEventRecord(e1, g->stream);
         if (cudaEventSynchronize(e1) != cudaSuccess) break;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
+        ms *= 0.75f;   // per 3 iterations, as the tiled candidates below
         if (ms < best_ms) {
             best_ms = ms;
             best = cand;
@@ -1109,7 +1337,7 @@ mhd_status_t tune_slab32(mhd_grid_s* g, int nc) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (best == 0) return set_error(g, MHD_ERR_CUDA, "FP32 CG kernels: no launchable variant");
-    g->slab32 = best;  // -1: split kernels, -2: p update folded into the stencil, > 0: tiled slab
+    g->slab32 = best;  // -1 split, -2 folded, -3/-4 recompute pair, <= -100 bulk-staged pair, > 0 tiled slab
     return check_cuda(g, "tune slab");
 }
 }  // namespace
@@ -1225,6 +1453,8 @@ mhd_status_t solve(mhd_grid_s* g, const double* alpha_dev, int nc, const double*
         st = run_iterations(g, pc2 ? 4 : 1, nc);
         if (st != MHD_OK) return st;
         k_inner_end<<<1, 1, 0, g->stream>>>(g->sc, saved);
+        if (g->h_sc->done == 6)
+            return set_error(g, MHD_ERR_TIMEOUT, "pcg (mixed): a bounded wait for a bulk copy gave up");
         if (g->h_sc->done == 3) break;
         k_correct<<<blocks2, kThreads, 0, g->stream>>>(d, nc, x, g->x32, g->p32, g->t64.s, g->sc);
         if ((st = check_cuda(g, "correction")) != MHD_OK) return st;

@@ -1,6 +1,9 @@
 """The FP32 inner-iteration variants of mixed-precision PCG, each forced in turn (MHD_FORCE_SLAB is
 read when a grid tunes its FP32 kernels): -1 the split kernels (p update, stencil, update), -2 the p
-update folded into the stencil with p double-buffered, 16 the plane-marching pair. Each must reach
+update folded into the stencil with p double-buffered, -3 and -4 the recompute pair (no q stored,
+x updated every second iteration; -4 with the r update walking the grid backwards), -132 and -116
+the same pair as plane-marching kernels whose rows are staged by bulk asynchronous copies (work
+units of 32 or 16 planes), 16 the plane-marching pair. Each must reach
 the FP64 tolerance on the true residual and agree with the oracle's FP64 solution (Sec. 2.2 PCG;
 mixed precision is the FP32-inner / FP64-refinement reading of the solver)."""
 import numpy as np
@@ -22,7 +25,7 @@ def _system(d, seed):
     return og, b
 
 
-@pytest.mark.parametrize("variant", ["-1", "-2", "16"])
+@pytest.mark.parametrize("variant", ["-1", "-2", "-3", "-4", "-5", "-132", "-116", "16"])
 @pytest.mark.parametrize("restart,inner", [(0, 0.1), (1, 1e-5)])
 def test_mixed_variant_matches_fp64_oracle(monkeypatch, variant, restart, inner):
     # np = 256 (float4 groups, plane-marching tiles possible); nt = 18 leaves a ragged row tile
@@ -44,10 +47,11 @@ def test_mixed_variant_matches_fp64_oracle(monkeypatch, variant, restart, inner)
         assert rel_l2(to_np(x), ref) < 1e-6, (variant, nc)
 
 
-def test_fused_variant_float2_groups_and_nonzero_start(monkeypatch):
+@pytest.mark.parametrize("variant", ["-2", "-3", "-4"])
+def test_fused_variant_float2_groups_and_nonzero_start(monkeypatch, variant):
     # np = 250: not a multiple of 4, so the FP32 kernels work on float2 groups; x0 != 0
     d = I.GridDesc(12, 14, 250, 1.0, 6.0, 1.04)
-    monkeypatch.setenv("MHD_FORCE_SLAB", "-2")
+    monkeypatch.setenv("MHD_FORCE_SLAB", variant)
     g = grid(d)
     og, b = _system(d, 32)
     rng = np.random.default_rng(33)
@@ -102,3 +106,57 @@ def test_mixed_pc2_variant_matches_fp64_oracle(monkeypatch, variant, d):
             res = b[:nc] - og.apply_M(alpha, to_np(x))
             assert np.linalg.norm(res) <= 1e-9 * np.linalg.norm(b[:nc]) * 1.0000001
             assert rel_l2(to_np(x), xr[:nc]) < 1e-6, (variant, restart, nc)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 8])
+def test_recompute_pair_pending_x_update(monkeypatch, k):
+    # the recompute pair adds alpha p to x two iterations at a time; an inner solve cut after an
+    # odd or an even number of iterations must hand the pending update to the FP64 correction.
+    # One outer pass with k inner iterations, against the fused variant (same arithmetic up to the
+    # reduction order of the dot products): a lost alpha_k p_k would move x by O(1)
+    d = I.GridDesc(12, 10, 128, 1.0, 5.0, 1.06)
+    og, b = _system(d, 36)
+    out = {}
+    for variant in ("-2", "-3", "-4", "-132"):
+        monkeypatch.setenv("MHD_FORCE_SLAB", variant)
+        g = grid(d)
+        x = torch.zeros(b.shape, dtype=torch.float64, device="cuda")
+        prm = P.make_params(tol=1e-14, inner_tol=1e-12, precision=P.PREC_MIXED, max_outer=1, max_iter=k)
+        st, it, ou, rr = P.pcg_solve(g, 3.0, to_dev(b), x, prm)
+        assert st == P.MHD_ERR_NOCONV and it == k and ou == 1, (variant, st, it, ou)
+        out[variant] = to_np(x)
+    for variant in ("-3", "-4", "-132"):
+        assert rel_l2(out[variant], out["-2"]) < 1e-6, (variant, k, rel_l2(out[variant], out["-2"]))
+
+
+def test_recompute_pair_and_fused_take_the_same_iterations(monkeypatch):
+    d = I.GridDesc(24, 20, 128, 1.0, 10.0, 1.05)
+    og, b = _system(d, 34)
+    out = {}
+    for variant in ("-2", "-3", "-4", "-132"):
+        monkeypatch.setenv("MHD_FORCE_SLAB", variant)
+        g = grid(d)
+        x = torch.zeros(b.shape, dtype=torch.float64, device="cuda")
+        prm = P.make_params(tol=1e-9, inner_tol=0.1, precision=P.PREC_MIXED, max_outer=60, max_iter=5000)
+        st, it, ou, rr = P.pcg_solve(g, 3.0, to_dev(b), x, prm)
+        assert st == P.MHD_OK and rr <= 1e-9
+        out[variant] = (it, ou, to_np(x))
+    for variant in ("-3", "-4", "-132"):
+        assert abs(out[variant][0] - out["-2"][0]) <= 1 and abs(out[variant][1] - out["-2"][1]) <= 1
+        assert rel_l2(out[variant][2], out["-2"][2]) < 1e-6
+
+
+def test_bulk_pair_ragged_rows_and_small_slabs(monkeypatch):
+    # nt = 7 leaves a partial row tile (TJ = 4), nr = 9 with 16-plane units a single slab, np = 384;
+    # two components too (the units of the third are skipped)
+    d = I.GridDesc(9, 7, 384, 1.0, 4.0, 1.05)
+    og, b = _system(d, 37)
+    monkeypatch.setenv("MHD_FORCE_SLAB", "-116")
+    g = grid(d)
+    for nc in (3, 2, 1):
+        xr, _, _, _ = og.pcg(2.0, b[:nc], tol=1e-13)
+        x = torch.zeros((nc,) + b.shape[1:], dtype=torch.float64, device="cuda")
+        prm = P.make_params(tol=1e-9, inner_tol=0.1, precision=P.PREC_MIXED, max_outer=60, max_iter=5000)
+        st, it, ou, rr = P.pcg_solve(g, 2.0, to_dev(b[:nc]), x, prm)
+        assert st == P.MHD_OK and rr <= 1e-9, (nc, st, rr)
+        assert rel_l2(to_np(x), xr) < 1e-6, nc
