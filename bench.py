@@ -12,8 +12,10 @@ needed between steps. Kernel durations come from CUDA events recorded on the gri
 around each launch inside the timed region.
 
 With N > 1 (torchrun) every rank runs an independent replica of the workload on its own GPU;
-the step has no data-path exchange between replicas. --impl reference times the CPU oracle
-(plain C, one thread) on a bounded sample of the same workload and prints the same JSON line.
+the step has no data-path exchange between replicas. --impl reference times the CPU oracle (its
+OpenMP timing build on every host core, and one thread beside it) on a bounded sample of the same
+workload, scaled by the oracle's own PCG iteration count, with whole oracle steps measured at
+32x32x64 and 128x128x256 as anchors, and prints the same JSON line.
 """
 from __future__ import annotations
 
@@ -143,15 +145,21 @@ def gen_state(name, grid=None):
 
 
 # ----------------------------------------------------------------------------------------------
-# reference arm and CPU baseline: the plain C oracle, one thread, bounded samples
+# reference arm and CPU baseline: the C oracle (its OpenMP timing build) on the host's cores
 # ----------------------------------------------------------------------------------------------
-def oracle_sample(w, st, iters_per_step, pcg_iters=2):
+def host_cores():
+    return os.cpu_count() or 1
+
+
+def oracle_sample(w, st, iters_per_step, pcg_iters=3, threads=0):
     """Time the oracle's explicit passes once and `pcg_iters` PCG iterations on the step's SI
-    system, and scale to one step with `iters_per_step` PCG iterations. Returns (ms, sample)."""
+    system with `threads` threads of its OpenMP timing build (0: every host core), and scale to one
+    step with `iters_per_step` PCG iterations. Returns (ms, sample text, threads used, parts)."""
     import numpy as np
     import oracle as O
+    used = O.set_threads(threads if threads > 0 else host_cores())
     d = w["desc"]
-    g = O.Grid.from_desc(d)
+    g = O.Grid.from_desc(d, omp=True)
     v = np.stack([st["vr"], st["vt"], st["vp"]])
     t0 = time.perf_counter()
     c = g.coeffs(v, st["br"], st["bt"], st["bp"], nu=w["nu"], cfl=w["cfl"])
@@ -167,11 +175,28 @@ def oracle_sample(w, st, iters_per_step, pcg_iters=2):
     t5 = time.perf_counter()
     per_iter = (t5 - t4) / pcg_iters
     setup = (t4 - t3) - per_iter  # residual, diagonal and one iteration
+    parts = dict(coeffs_ms=1e3 * (t1 - t0), force_ms=1e3 * (t2 - t1), induction_ms=1e3 * (t3 - t2),
+                 solve_setup_ms=1e3 * setup, pcg_iteration_ms=1e3 * per_iter)
     ms = 1e3 * ((t1 - t0) + 2 * (t2 - t1) + (t3 - t2) + 3 * setup + iters_per_step * per_iter)
-    sample = (f"oracle at {d.nr}x{d.nt}x{d.np}: one coefficient, force and induction pass and "
-              f"{pcg_iters + 2} PCG iterations timed ({t5 - t0:.1f} s), scaled to one step of "
-              f"{iters_per_step} PCG iterations (2 force passes, 3 solve set-ups)")
-    return ms, sample
+    sample = (f"oracle (OpenMP timing build, {used} threads) at {d.nr}x{d.nt}x{d.np}: one coefficient, force "
+              f"and induction pass and {pcg_iters + 2} PCG iterations timed ({t5 - t0:.1f} s), scaled to one "
+              f"step of {iters_per_step} PCG iterations (2 force passes, 3 solve set-ups)")
+    return ms, sample, used, parts
+
+
+def oracle_full_step(name, grid, threads=0):
+    """One whole oracle step (OpenMP timing build): (ms, PCG iterations, threads, its sampled model)."""
+    import oracle as O
+    w, st = gen_state(name, grid)
+    used = O.set_threads(threads if threads > 0 else host_cores())
+    g = O.Grid.from_desc(w["desc"], omp=True)
+    t0 = time.perf_counter()
+    _, info = g.step(st, nu=w["nu"], eta=w["eta"], cfl=w["cfl"], tol=w["tol"])
+    ms = 1e3 * (time.perf_counter() - t0)
+    iters = int(sum(info["iters"]))
+    model, _, _, _ = oracle_sample(w, st, iters, pcg_iters=3, threads=threads)
+    return dict(ms=round(ms, 1), pcg_iters=iters, threads=used, sampled_model_ms=round(model, 1),
+                model_over_measured=round(model / ms, 3))
 
 
 def oracle_iteration_counts(name):
@@ -185,6 +210,15 @@ def oracle_iteration_counts(name):
     return int(sum(rec["info"]["iters"]))
 
 
+def cpu_baseline_iters(args, fallback):
+    """PCG iterations per step by which both oracle figures are scaled, and where the number
+    comes from."""
+    rec = oracle_iteration_counts(args.workload) if args.grid is None else None
+    if rec is not None:
+        return rec, f"the oracle's own first step at this size (tests/golden/{args.workload}_oracle_step1.json)"
+    return int(fallback), "no oracle record for this grid: the count given"
+
+
 def run_reference(args):
     ws, rank, local = dist_env()
     if ws > 1:
@@ -195,20 +229,34 @@ def run_reference(args):
             dist.destroy_process_group()
             return
     w, st = gen_state(args.workload, args.grid)
-    iters = oracle_iteration_counts(args.workload) or args.ref_iters
+    d = w["desc"]
+    iters, iters_src = cpu_baseline_iters(args, args.ref_iters)
     vals = []
     sample = ""
+    parts = {}
+    used = 1
     for s in range(args.warmup + args.steps):
-        ms, sample = oracle_sample(w, st, iters, pcg_iters=1)
+        ms, sample, used, parts = oracle_sample(w, st, iters, pcg_iters=3)
         if s >= args.warmup:
             vals.append(ms)
     value = sum(vals) / len(vals)
+    one, _, _, _ = oracle_sample(w, st, iters, pcg_iters=2, threads=1)
+    anchors = {}
+    if not args.no_anchors:
+        anchors["32x32x64"] = oracle_full_step("parity_32x32x64", None)
+        anchors["128x128x256"] = oracle_full_step(args.workload, "128x128x256")
+    cpu = dict(value=round(value, 3), unit="ms/step", cores=used, kind="oracle", sample=sample,
+               single_thread_value=round(one, 1), iters_per_step=iters, iters_source=iters_src,
+               parts_ms={k: round(v, 2) for k, v in parts.items()},
+               measured_full_steps=anchors,
+               note="extrapolated from the timed sample by the iteration count; measured_full_steps are whole "
+                    "oracle steps on smaller grids with the same sampled model beside them")
     line = dict(impl="reference", metric=METRIC, value=round(value, 3), unit="ms/step", n_gpus=args.gpus,
                 steps=args.steps, warmup=args.warmup, ms_per_step=round(value, 3), higher_is_better=False,
                 scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
-                config=dict(workload=args.workload, grid="256x256x512", precision="fp64",
+                config=dict(workload=args.workload, grid=f"{d.nr}x{d.nt}x{d.np}", precision="fp64",
                             l2="inputs larger than L2"),
-                cpu_baseline=dict(value=round(value, 3), unit="ms/step", cores=1, kind="oracle", sample=sample),
+                cpu_baseline=cpu,
                 e2e=dict(value=round(value, 3), unit="ms/step", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
     if ws > 1:
@@ -298,11 +346,15 @@ def run_ours(args):
         return float(t.item())
 
     hbm, peak_src = peaks()
-    # ---- FP64 (headline)
+    # ---- FP64 (headline): K steps as a user runs them (CUDA graphs of PCG iterations, no per-launch
+    # events), then a short profiled run of the same workload for the per-kernel times
     snap = {}
-    ms64, infos64, prof64, clk64, ds64 = run(P.PREC_FP64, args.steps, args.warmup, True, snapshot=snap)
+    ms64, infos64u, _, clk64, ds64 = run(P.PREC_FP64, args.steps, args.warmup, False, snapshot=snap)
     ms64 = maxr(ms64)
-    it64 = sum(sum(i["iters"]) for i in infos64) / len(infos64)
+    it64 = sum(sum(i["iters"]) for i in infos64u) / len(infos64u)
+    psteps = max(1, min(args.steps, args.profile_steps))
+    ms64p, infos64, prof64, clk64p, ds64p = run(P.PREC_FP64, psteps, 1, True)
+    ms64p = maxr(ms64p)
     spmv_ms, spmv_n = prof64["spmv64"]
     pcg64_ms = sum(prof64[k][0] for k in ("pupdate64", "spmv64", "update64"))
     pcg64_n = prof64["spmv64"][1]
@@ -378,14 +430,14 @@ def run_ours(args):
 
     # ---- viscosity by RKL2 super time-stepping (the SI solves unchanged)
     def sts_entry(precision, inner_tol=0.1, restart=0):
-        mss, infoss, profs, clks, dss = run(precision, args.steps, args.warmup, True, inner_tol, restart, sts=1)
+        mss, infoss, profs, clks, dss = run(precision, psteps, 1, True, inner_tol, restart, sts=1)
         mss = maxr(mss)
         stages = sum(i["iters"][2] for i in infoss)
         st_ms, st_n = profs["sts"]
         per_stage = st_ms / max(stages, 1)
         tflops = STS_FLOPS_PER_CELL * N / (per_stage * 1e-3) / 1e12
         gbs = STS_BYTES_PER_CELL * N / (per_stage * 1e-3) / 1e9
-        err = {k: float(torch.linalg.norm(dss[k] - ds64[k]) / torch.linalg.norm(ds64[k])) for k in ds64}
+        err = {k: float(torch.linalg.norm(dss[k] - ds64p[k]) / torch.linalg.norm(ds64p[k])) for k in ds64p}
         return dict(si_precision=("fp64" if precision == P.PREC_FP64 else "mixed, reliable updates, inner_tol "
                                   f"{inner_tol}"),
                     ms_per_step=round(mss, 3), speedup_vs_fp64=round(ms64 / mss, 3),
@@ -402,7 +454,7 @@ def run_ours(args):
     # ---- FP64 with the single-reduction (Chronopoulos-Gear) PCG form
     pcg_cg = None
     if not args.no_cg:
-        msc, infosc, profc, clkc, dsc = run(P.PREC_FP64, args.steps, args.warmup, True, variant=1)
+        msc, infosc, profc, clkc, dsc = run(P.PREC_FP64, psteps, 1, True, variant=1)
         msc = maxr(msc)
         itc = sum(sum(i["iters"]) for i in infosc) / len(infosc)
         c_ms = profc["spmv64"][0] + profc["update64"][0]
@@ -411,15 +463,15 @@ def run_ours(args):
                       ms_per_iteration=round(c_ms / max(sum(sum(i["iters"]) for i in infosc), 1), 4),
                       ms_per_iteration_hestenes_stiefel=round(pcg64_ms / it64_total, 4),
                       kernels_per_iteration=2,
-                      rel_l2_vs_fp64_after_steps={k: float(torch.linalg.norm(dsc[k] - ds64[k]) /
-                                                           torch.linalg.norm(ds64[k])) for k in ds64},
+                      rel_l2_vs_fp64_after_steps={k: float(torch.linalg.norm(dsc[k] - ds64p[k]) /
+                                                           torch.linalg.norm(ds64p[k])) for k in ds64p},
                       clocks=clkc, kernel_ms={k: round(v[0], 3) for k, v in profc.items() if v[1]})
 
     # ---- PC2: block-Jacobi ILU(0) on phi lines (FP64), alone and with RKL2 viscosity
     # mixed PC2 runs reliable updates at inner tol 1e-3: a PC2 iteration is cheap against an FP64
     # correction, so fewer corrections win (the refinement study's PC2 rows: 1e-3 fastest)
     def pc2_entry(sts_flag, precision=P.PREC_FP64):
-        msp, infosp, profp, clkp, dsp = run(precision, args.steps, args.warmup, True, inner_tol=1e-3, restart=0,
+        msp, infosp, profp, clkp, dsp = run(precision, psteps, 1, True, inner_tol=1e-3, restart=0,
                                             sts=sts_flag, pc=1)
         msp = maxr(msp)
         if precision == P.PREC_MIXED:
@@ -431,8 +483,8 @@ def run_ours(args):
                         max_relres=max(max(i["relres"]) for i in infosp),
                         kernel_ms_per_iteration={k: round(profp[k][0] / n_it, 4)
                                                  for k in ("pupdate32", "spmv32", "pspmv32", "pc2") if profp[k][1]},
-                        rel_l2_vs_fp64_after_steps={k: float(torch.linalg.norm(dsp[k] - ds64[k]) /
-                                                             torch.linalg.norm(ds64[k])) for k in ds64},
+                        rel_l2_vs_fp64_after_steps={k: float(torch.linalg.norm(dsp[k] - ds64p[k]) /
+                                                             torch.linalg.norm(ds64p[k])) for k in ds64p},
                         clocks=clkp, kernel_ms={k: round(v[0], 3) for k, v in profp.items() if v[1]})
         # per iteration: summed kernel time over the CG iterations actually run (launches that return
         # at once after convergence last a few microseconds and are not iterations)
@@ -446,8 +498,8 @@ def run_ours(args):
                     ms_per_iteration=round(sum(per_it.values()), 4), ms_per_iteration_pc1=round(pcg64_ms / it64_total, 4),
                     kernel_ms_per_iteration=per_it,
                     line_kernel_gbs=round(PC2_LINE_BYTES_PER_CELL * N / (line_ms * 1e-3) / 1e9, 1),
-                    rel_l2_vs_fp64_after_steps={k: float(torch.linalg.norm(dsp[k] - ds64[k]) /
-                                                         torch.linalg.norm(ds64[k])) for k in ds64},
+                    rel_l2_vs_fp64_after_steps={k: float(torch.linalg.norm(dsp[k] - ds64p[k]) /
+                                                         torch.linalg.norm(ds64p[k])) for k in ds64p},
                     clocks=clkp, kernel_ms={k: round(v[0], 3) for k, v in profp.items() if v[1]})
 
     pc2 = pc2_sts = pc2_mixed = None
@@ -461,8 +513,8 @@ def run_ours(args):
     # ---- resistivity eta = RES_ETA: explicit (eta J in E) against the implicit face solve, PC2 solves
     res_entry = None
     if not args.no_res:
-        mse, infose, profe, clke, dse = run(P.PREC_FP64, args.steps, args.warmup, True, pc=1, eta=RES_ETA, res=0)
-        msi, infosi, profi, clki, dsi = run(P.PREC_FP64, args.steps, args.warmup, True, pc=1, eta=RES_ETA, res=1)
+        mse, infose, profe, clke, dse = run(P.PREC_FP64, psteps, 1, True, pc=1, eta=RES_ETA, res=0)
+        msi, infosi, profi, clki, dsi = run(P.PREC_FP64, psteps, 1, True, pc=1, eta=RES_ETA, res=1)
         mse, msi = maxr(mse), maxr(msi)
         n_res = max(sum(i["iters_res"] for i in infosi), 1)
         res_entry = dict(eta=RES_ETA, cell_solves="FP64 PC2",
@@ -488,7 +540,7 @@ def run_ours(args):
         out = {k: torch.empty_like(v, device="cpu").pin_memory() for k, v in snap.items()}
         f = P.make_fields(ds["br"], ds["bt"], ds["bp"], ds["vr"], ds["vt"], ds["vp"])
         prm = P.make_params(nu=w["nu"], eta=w["eta"], cfl=w["cfl"], tol=w["tol"])
-        ke = max(1, min(args.steps, 2))
+        ke = max(1, args.steps)
         h2d = sum(t.numel() * 8 for t in snap.values())
         barrier()
         ev = lambda: torch.cuda.Event(enable_timing=True)
@@ -523,9 +575,14 @@ def run_ours(args):
     # ---- CPU baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        iters = int(round(it64))
-        ms_cpu, sample = oracle_sample(w, st0, iters, pcg_iters=2)
-        cpu = dict(value=round(ms_cpu, 1), unit="ms/step", cores=1, kind="oracle", sample=sample)
+        iters, iters_src = cpu_baseline_iters(args, it64)
+        ms_cpu, sample, used, parts = oracle_sample(w, st0, iters, pcg_iters=3)
+        one, _, _, _ = oracle_sample(w, st0, iters, pcg_iters=2, threads=1)
+        cpu = dict(value=round(ms_cpu, 1), unit="ms/step", cores=used, kind="oracle", sample=sample,
+                   single_thread_value=round(one, 1), iters_per_step=iters, iters_source=iters_src,
+                   parts_ms={k: round(v, 2) for k, v in parts.items()},
+                   note="the same sample and iteration count as the reference arm (bench.py --impl reference), "
+                        "which also prints measured whole oracle steps at 32x32x64 and 128x128x256")
     launches = sum(v[1] for v in prof64.values())
     if rank == 0:
         line = dict(metric=METRIC, value=round(ms64, 3), unit="ms/step", n_gpus=ws, steps=args.steps,
@@ -535,7 +592,14 @@ def run_ours(args):
                                 parallelism=("replicas" if ws > 1 else "single"),
                                 l2="inputs larger than L2 (no flush)",
                                 pcg_iters_per_step=it64,
-                                dt=[i["dt"] for i in infos64]),
+                                dt=[i["dt"] for i in infos64u]),
+                    profiled=dict(steps=psteps, ms_per_step=round(ms64p, 3),
+                                  pcg_iters_per_step=sum(sum(i["iters"]) for i in infos64) / len(infos64),
+                                  clocks=clk64p,
+                                  note="the same workload from the same initial state with CUDA events around "
+                                       "every launch (PCG kernels launched directly instead of from graphs); "
+                                       "kernel_ms, pcg_gbs and roofline come from this run; value is the "
+                                       "unprofiled run"),
                     pcg_gbs=dict(fp64=round(pcg64_gbs, 1), fp64_frac_of_hbm=round(pcg64_gbs / hbm, 4),
                                  peak_gbs=hbm, peak_source=peak_src, kernels=kernels64),
                     roofline=roof, mixed=mixed, mixed_reliable=mixed_reliable, sts=sts, sts_mixed_reliable=sts_mixed, pcg_single_reduction=pcg_cg,
@@ -882,6 +946,12 @@ def main():
     ap.add_argument("--all-entries", action="store_true",
                     help="with N > 1 ranks, also time the mixed, RKL2, single-reduction, PC2 and resistivity entries")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=3,
+                    help="steps (after one warm-up) of the profiled FP64 run beside the unprofiled headline; "
+                         "the RKL2, single-reduction, PC2 and resistivity entries run as many and compare "
+                         "with it")
+    ap.add_argument("--no-anchors", action="store_true",
+                    help="reference arm: skip the measured whole oracle steps at 32x32x64 and 128x128x256")
     ap.add_argument("--ref-iters", type=int, default=1000,
                     help="PCG iterations per step assumed by the reference arm if no oracle record exists")
     args = ap.parse_args()

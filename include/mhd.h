@@ -23,10 +23,11 @@
  *      bp [nr][nt][np]    phi faces at phi_k
  *      vr, vt, vp [nr][nt][np] cell centres; "stacked" vectors hold ncomp such blocks back
  *      to back ([ncomp][nr][nt][np]).
- *  - A grid owns its metric tables and all workspace. It allocates in mhd_grid_create, in the
- *    first mhd_adjoint_step call on it (adjoint workspace) and in the first pcg_solve_batched
- *    call for a batch of grids (batch plan); mhd_step, pcg_solve and the other calls allocate
- *    nothing.
+ *  - A grid owns its metric tables and all workspace. It allocates in mhd_grid_create, and
+ *    features that need more allocate on first use: PC2 and implicit resistivity (their
+ *    workspaces), mhd_adjoint_step (its workspace), pcg_solve_batched (the plan of a batch), and
+ *    every PCG form (the CUDA graph of its iterations). mhd_grid_reserve and pcg_batch_reserve do
+ *    those allocations up front.
  *  - All work is enqueued on the grid's CUDA stream. Calls that return scalars (step info,
  *    iteration counts) synchronise that stream once at their end; the others return after
  *    enqueueing.
@@ -252,6 +253,34 @@ mhd_status_t mhd_adjoint_step(mhd_grid_t grid, const mhd_params_t* params,
  * default stream). Errors: MHD_ERR_ARG (null pointer, bad or too large grid), MHD_ERR_CUDA. */
 mhd_status_t mhd_force_noalloc(const mhd_grid_desc_t* desc, const mhd_fields_t* fields, double dt,
                                double* b, void* cuda_stream);
+
+/* Workspace reservation (not part of the method; the paper has no counterpart). Some features
+ * allocate on their first use: the PC2 factorisation, the implicit-resistivity face vectors, the
+ * adjoint workspace, and the CUDA graphs of the PCG iterations (instantiating a graph can take
+ * device memory), after the per-grid kernel choice that those graphs record. mhd_grid_reserve does
+ * all of that now for the features named, so that afterwards mhd_step, pcg_solve and
+ * mhd_adjoint_step on 3-component systems with those features allocate no device memory on this
+ * grid (a code that captures them in its own CUDA graph, or that budgets device memory up front,
+ * needs that). The PCG vectors' contents are overwritten (the timed trial iterations of the kernel
+ * choice); fields are not touched. Synchronises the grid's stream. Errors: MHD_ERR_ARG (unknown
+ * feature bit), MHD_ERR_OOM, MHD_ERR_CUDA. */
+enum {
+    MHD_RESERVE_PC1 = 1,           /* FP64 point-Jacobi PCG: FP64 kernel choice, iteration graph */
+    MHD_RESERVE_MIXED = 2,         /* mixed precision: FP32 kernel choice (timed), iteration graph */
+    MHD_RESERVE_CG = 4,            /* single-reduction PCG (pcg_variant = 1): iteration graph */
+    MHD_RESERVE_PC2 = 8,           /* preconditioner = 1: workspace, FP64 (and with MIXED FP32) graphs */
+    MHD_RESERVE_RESISTIVITY = 16,  /* resistivity_implicit = 1: face workspace and iteration graph */
+    MHD_RESERVE_ADJOINT = 32,      /* mhd_adjoint_step workspace */
+    MHD_RESERVE_ALL = 63
+};
+mhd_status_t mhd_grid_reserve(mhd_grid_t grid, int features);
+
+/* The same for a batch of pcg_solve_batched: builds (and times) the plan of exactly this batch
+ * (the grids and the b and x pointers, as a later call passes them) and instantiates its CUDA graph
+ * for these params; a later pcg_solve_batched with the same batch and the same tol and max_iter
+ * allocates nothing. Solves nothing; x is not written. Errors as pcg_solve_batched. */
+mhd_status_t pcg_batch_reserve(int n, const mhd_grid_t* grids, const double* alpha, const double* const* b,
+                               double* const* x, const mhd_params_t* params);
 
 /* Diagnostics (not part of the method): device time of the library's kernels, measured with
  * CUDA events recorded on the grid's stream immediately before and after each launch, summed

@@ -15,8 +15,10 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mhd_oracle.c")
 _SO = os.path.join(_HERE, "_build", "libmhd_oracle.so")
+_SO_OMP = os.path.join(_HERE, "_build", "libmhd_oracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 OK, ERR_ARG, ERR_NOCONV = 0, 1, 3
 
@@ -33,6 +35,19 @@ def build(force: bool = False) -> str:
     return _SO
 
 
+def build_omp(force: bool = False) -> str:
+    """The timing build: the same source with -fopenmp (the benchmark's CPU baseline on all host
+    cores). The default build above stays plain sequential C."""
+    os.makedirs(os.path.dirname(_SO_OMP), exist_ok=True)
+    if force or not os.path.exists(_SO_OMP) or os.path.getmtime(_SO_OMP) < max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "mhd_oracle.h"))):
+        tmp = _SO_OMP + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
+                               "-D_DEFAULT_SOURCE", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO_OMP)
+    return _SO_OMP
+
+
 def lib():
     global _lib
     with _lock:
@@ -42,11 +57,28 @@ def lib():
     return _lib
 
 
+def lib_omp():
+    global _lib_omp
+    with _lock:
+        if _lib_omp is None:
+            _lib_omp = C.CDLL(build_omp())
+            _declare(_lib_omp)
+    return _lib_omp
+
+
+def set_threads(n: int = 0, omp: bool = True) -> int:
+    """Threads of the timing build (n > 0 sets them); returns the count in use (1: plain build)."""
+    L = lib_omp() if omp else lib()
+    return int(L.og_set_threads(int(n)))
+
+
 _dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 
 
 def _declare(L):
     vp, i, d = C.c_void_p, C.c_int, C.c_double
+    L.og_set_threads.restype = i
+    L.og_set_threads.argtypes = [i]
     L.og_create.restype = vp
     L.og_create.argtypes = [i, i, i, d, d, d]
     L.og_destroy.argtypes = [vp]
@@ -126,8 +158,8 @@ def dot(a, b):
 class Grid:
     """Oracle grid: nr x nt x np cells, r in [r0, r1] with geometric stretch."""
 
-    def __init__(self, nr, nt, np_, r0, r1, stretch):
-        self.L = lib()
+    def __init__(self, nr, nt, np_, r0, r1, stretch, omp=False):
+        self.L = lib_omp() if omp else lib()
         self.h = self.L.og_create(nr, nt, np_, r0, r1, stretch)
         if not self.h:
             raise ValueError("bad grid")
@@ -136,8 +168,8 @@ class Grid:
         self.r0, self.r1, self.stretch = r0, r1, stretch
 
     @classmethod
-    def from_desc(cls, d):
-        return cls(d.nr, d.nt, d.np, d.r0, d.r1, d.stretch)
+    def from_desc(cls, d, omp=False):
+        return cls(d.nr, d.nt, d.np, d.r0, d.r1, d.stretch, omp=omp)
 
     def __del__(self):
         h = getattr(self, "h", None)

@@ -3,12 +3,21 @@
  * only tests, the smoke check and the benchmark's CPU baseline use it. See mhd_oracle.h for
  * layouts. Each function cites the passage of the paper it restates; where the paper is silent
  * the comment states the reading taken.
+ *
+ * The default build is plain sequential C. The `omp` pragmas below only take effect in the
+ * separate timing build (compiled with -fopenmp, used by the benchmark's CPU baseline on all host
+ * cores): they split loops whose iterations are independent, and the inner product then sums
+ * fixed chunks and combines them in chunk order, so its value does not depend on the thread
+ * count.
  */
 #include "mhd_oracle.h"
 
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 struct og_grid {
     int nr, nt, np;
@@ -41,6 +50,17 @@ static void res_weights(const og_grid* g, double* w);
  * Grid (reading R2: geometric radial stretch, uniform theta in [0,pi], periodic phi; exact
  * finite-volume geometry of spherical cells).
  * ------------------------------------------------------------------------------------------- */
+/* threads of the timing build (n > 0 sets them); 1 in the plain build */
+int og_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 og_grid* og_create(int nr, int nt, int np, double r0, double r1, double stretch) {
     if (nr < 2 || nt < 2 || np < 1 || !(r1 > r0) || !(r0 > 0) || !(stretch > 0)) return NULL;
     og_grid* g = (og_grid*)calloc(1, sizeof(og_grid));
@@ -133,6 +153,7 @@ static void apply_op(const og_grid* g, double alpha, int with_d, int with_dirich
     for (int c = 0; c < ncomp; c++) {
         const double* u = p + c * g->N;
         double* o = q + c * g->N;
+#pragma omp parallel for schedule(static)
         for (int i = 0; i < nr; i++)
             for (int j = 0; j < nt; j++)
                 for (int k = 0; k < np; k++) {
@@ -181,9 +202,9 @@ void og_diag(const og_grid* g, double alpha, double* d) {
  * error-free TwoSum, and the collected errors are added at the end. The result is as accurate as a
  * sum taken in twice the working precision and then rounded, whatever the length, so the PCG
  * scalars alpha and beta carry no summation-order error of this side's own. */
-static double dot(long long n, const double* a, const double* b) {
+static void dot2_range(const double* a, const double* b, long long lo, long long hi, double* sum, double* err) {
     double s = 0.0, c = 0.0;
-    for (long long i = 0; i < n; i++) {
+    for (long long i = lo; i < hi; i++) {
         double p = a[i] * b[i];
         double pe = fma(a[i], b[i], -p);
         double t = s + p;
@@ -191,7 +212,35 @@ static double dot(long long n, const double* a, const double* b) {
         c += ((s - (t - z)) + (p - z)) + pe;
         s = t;
     }
+    *sum = s;
+    *err = c;
+}
+
+static double dot(long long n, const double* a, const double* b) {
+#ifdef _OPENMP
+    /* timing build: 256 fixed chunks, each by Dot2, then the chunk sums by TwoSum in order */
+    enum { NCH = 256 };
+    double cs[NCH], ce[NCH];
+    long long len = (n + NCH - 1) / NCH;
+#pragma omp parallel for schedule(static)
+    for (int ch = 0; ch < NCH; ch++) {
+        long long lo = ch * len, hi = lo + len < n ? lo + len : n;
+        if (lo > n) lo = n;
+        dot2_range(a, b, lo, hi, &cs[ch], &ce[ch]);
+    }
+    double s = 0.0, c = 0.0;
+    for (int ch = 0; ch < NCH; ch++) {
+        double t = s + cs[ch];
+        double z = t - s;
+        c += ((s - (t - z)) + (cs[ch] - z)) + ce[ch];
+        s = t;
+    }
     return s + c;
+#else
+    double s, c;
+    dot2_range(a, b, 0, n, &s, &c);
+    return s + c;
+#endif
 }
 
 double og_dot(long long n, const double* a, const double* b) { return dot(n, a, b); }
@@ -213,8 +262,11 @@ int og_pcg(const og_grid* g, double alpha, int ncomp, const double* b, double* x
     double* q = (double*)malloc(sizeof(double) * n);
     og_diag(g, alpha, d);
     og_apply_M(g, alpha, ncomp, x, q);
+#pragma omp parallel for schedule(static)
     for (long long e = 0; e < n; e++) r[e] = b[e] - q[e];
+#pragma omp parallel for schedule(static)
     for (long long e = 0; e < n; e++) z[e] = r[e] / d[(e % N) / np];
+#pragma omp parallel for schedule(static)
     for (long long e = 0; e < n; e++) p[e] = z[e];
     double rz = dot(n, r, z);
     double rn = sqrt(dot(n, r, r));
@@ -231,14 +283,18 @@ int og_pcg(const og_grid* g, double alpha, int ncomp, const double* b, double* x
         double pq = dot(n, p, q);
         if (!(pq > 0.0)) { status = OG_ERR_NOCONV; break; }
         double a = rz / pq;
+#pragma omp parallel for schedule(static)
         for (long long e = 0; e < n; e++) x[e] += a * p[e];
+#pragma omp parallel for schedule(static)
         for (long long e = 0; e < n; e++) r[e] -= a * q[e];
         k++;
         rn = sqrt(dot(n, r, r));
+#pragma omp parallel for schedule(static)
         for (long long e = 0; e < n; e++) z[e] = r[e] / d[(e % N) / np];
         double rz_new = dot(n, r, z);
         double beta = rz_new / rz;
         rz = rz_new;
+#pragma omp parallel for schedule(static)
         for (long long e = 0; e < n; e++) p[e] = z[e] + beta * p[e];
     }
     *iters = k;
@@ -272,7 +328,9 @@ int og_pcg_cg(const og_grid* g, double alpha, int ncomp, const double* b, double
     double* sv = (double*)calloc(n, sizeof(double));
     og_diag(g, alpha, d);
     og_apply_M(g, alpha, ncomp, x, w);
+#pragma omp parallel for schedule(static)
     for (long long e = 0; e < n; e++) r[e] = b[e] - w[e];
+#pragma omp parallel for schedule(static)
     for (long long e = 0; e < n; e++) u[e] = r[e] / d[(e % N) / np];
     og_apply_M(g, alpha, ncomp, u, w);
     double gam = dot(n, r, u), del = dot(n, w, u);
@@ -297,11 +355,16 @@ int og_pcg_cg(const og_grid* g, double alpha, int ncomp, const double* b, double
         }
         if (!(den > 0.0)) { status = OG_ERR_NOCONV; break; }
         a = gam / den;
+#pragma omp parallel for schedule(static)
         for (long long e = 0; e < n; e++) p[e] = u[e] + beta * p[e];
+#pragma omp parallel for schedule(static)
         for (long long e = 0; e < n; e++) sv[e] = w[e] + beta * sv[e];
+#pragma omp parallel for schedule(static)
         for (long long e = 0; e < n; e++) x[e] += a * p[e];
+#pragma omp parallel for schedule(static)
         for (long long e = 0; e < n; e++) r[e] -= a * sv[e];
         k++;
+#pragma omp parallel for schedule(static)
         for (long long e = 0; e < n; e++) u[e] = r[e] / d[(e % N) / np];
         og_apply_M(g, alpha, ncomp, u, w);
         gam_old = gam;
@@ -379,6 +442,7 @@ void og_current_edges(const og_grid* g, const double* br, const double* bt, cons
     int nr = g->nr, nt = g->nt, np = g->np;
     double dth = g->dth, dph = g->dph;
     /* radial edges: (i, j, k), j = 0..nt, at (theta_j, phi_k), dual face at rc_i */
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < nr; i++) {
         double rc = g->rc[i];
         double circ_n = 0.0, circ_s = 0.0;
@@ -405,6 +469,7 @@ void og_current_edges(const og_grid* g, const double* br, const double* bt, cons
     }
     /* theta edges (i, j, k), i = 0..nr, at (r_i, phi_k); dual face at theta_c_j spanning
      * r_lo..r_hi (cell centres on either side, mirrored ghosts at the boundaries) */
+#pragma omp parallel for schedule(static)
     for (int i = 0; i <= nr; i++) {
         double rlo = (i > 0) ? g->rc[i - 1] : 2.0 * g->r0 - g->rc[0];
         double rhi = (i < nr) ? g->rc[i] : 2.0 * g->r[nr] - g->rc[nr - 1];
@@ -422,6 +487,7 @@ void og_current_edges(const og_grid* g, const double* br, const double* bt, cons
         }
     }
     /* phi edges (i, j, k), i = 0..nr, j = 0..nt, at (r_i, theta_j); zero on the polar axis */
+#pragma omp parallel for schedule(static)
     for (int i = 0; i <= nr; i++) {
         double rlo = (i > 0) ? g->rc[i - 1] : 2.0 * g->r0 - g->rc[0];
         double rhi = (i < nr) ? g->rc[i] : 2.0 * g->r[nr] - g->rc[nr - 1];
@@ -522,6 +588,7 @@ void og_force(const og_grid* g, const double* v, const double* br, const double*
     const double* vr = v;
     const double* vt = v + N;
     const double* vp = v + 2 * N;
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < g->nr; i++)
         for (int j = 0; j < nt; j++)
             for (int k = 0; k < g->np; k++) {
@@ -568,6 +635,7 @@ void og_efield_edges(const og_grid* g, const double* vbar, const double* br, con
         jc = (double*)malloc(sizeof(double) * 3 * N);
         og_current_centre(g, br, bt, bp, jc);
     }
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < nr; i++)
         for (int j = 0; j < nt; j++)
             for (int k = 0; k < np; k++) {
@@ -591,6 +659,7 @@ void og_efield_edges(const og_grid* g, const double* vbar, const double* br, con
     const double* Et = ec + N;
     const double* Ep = ec + 2 * N;
     /* radial edges */
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < nr; i++) {
         double sn = 0.0, ss = 0.0;
         for (int k = 0; k < np; k++) { sn += Er[IDX(g, i, 0, k)]; ss += Er[IDX(g, i, nt - 1, k)]; }
@@ -603,6 +672,7 @@ void og_efield_edges(const og_grid* g, const double* vbar, const double* br, con
             }
     }
     /* theta edges */
+#pragma omp parallel for schedule(static)
     for (int i = 0; i <= nr; i++)
         for (int j = 0; j < nt; j++)
             for (int k = 0; k < np; k++) {
@@ -615,6 +685,7 @@ void og_efield_edges(const og_grid* g, const double* vbar, const double* br, con
                 et[IDX(g, i, j, k)] = val;
             }
     /* phi edges */
+#pragma omp parallel for schedule(static)
     for (int i = 0; i <= nr; i++)
         for (int j = 0; j <= nt; j++)
             for (int k = 0; k < np; k++) {
@@ -639,6 +710,7 @@ void og_ct(const og_grid* g, const double* er, const double* et, const double* e
     int nr = g->nr, nt = g->nt, np = g->np;
     double dth = g->dth, dph = g->dph;
     /* radial faces (i, j, k), i = 0..nr */
+#pragma omp parallel for schedule(static)
     for (int i = 0; i <= nr; i++) {
         double ri = g->r[i];
         double lt = ri * dth;
@@ -653,6 +725,7 @@ void og_ct(const og_grid* g, const double* er, const double* et, const double* e
         }
     }
     /* theta faces (i, j, k), interior j */
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < nr; i++) {
         double ri = g->r[i], ro = g->r[i + 1];
         double lr = ro - ri;
@@ -667,6 +740,7 @@ void og_ct(const og_grid* g, const double* er, const double* et, const double* e
         }
     }
     /* phi faces (i, j, k) */
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < nr; i++) {
         double ri = g->r[i], ro = g->r[i + 1];
         double lr = ro - ri;
@@ -711,6 +785,7 @@ int og_coeffs(const og_grid* g, double nu, double cfl, double dt_fixed, double d
     long long N = g->N;
     int nt = g->nt;
     double mkv = 0.0, mka = 0.0, mk2 = 0.0;
+#pragma omp parallel for schedule(static) reduction(max : mkv, mka, mk2)
     for (int i = 0; i < g->nr; i++)
         for (int j = 0; j < nt; j++) {
             double kt2 = g->kt2[i * nt + j];
@@ -789,7 +864,9 @@ static int step_impl(const og_grid* g, int opts, double nu, double eta, double c
     og_force(g, v, br, bt, bp, dt, b0);
     s = pcg(g, asi, 3, b0, dlt, tol, max_iter, 0, &it[0], &rr[0]);
     if (s != OG_OK) status = s;
+#pragma omp parallel for schedule(static)
     for (long long e2 = 0; e2 < n3; e2++) vp[e2] = v[e2] + dlt[e2];
+#pragma omp parallel for schedule(static)
     for (long long e2 = 0; e2 < n3; e2++) vb[e2] = 0.5 * (v[e2] + vp[e2]);
     if (opts & OG_OPT_RES_IMPLICIT) {
         /* ideal CT update, then the resistive solve on the faces */
@@ -802,11 +879,14 @@ static int step_impl(const og_grid* g, int opts, double nu, double eta, double c
         og_ct(g, e.jr, e.jt, e.jp, dt, br, bt, bp);
     }
     og_force(g, vp, br, bt, bp, dt, b1);
+#pragma omp parallel for schedule(static)
     for (long long e2 = 0; e2 < n3; e2++) b1[e2] = 0.5 * (b0[e2] + b1[e2]);
     s = pcg(g, asi, 3, b1, dlt, tol, max_iter, 0, &it[1], &rr[1]);
     if (s != OG_OK) status = s;
+#pragma omp parallel for schedule(static)
     for (long long e2 = 0; e2 < n3; e2++) v[e2] = v[e2] + dlt[e2];          /* v** */
     for (int c = 0; c < 3; c++)
+#pragma omp parallel for schedule(static)
         for (long long q = 0; q < N; q++) {
             long long ij = q / np;
             b0[c * N + q] = g->rho[ij] * g->vol[ij] * v[c * N + q];
@@ -1558,8 +1638,11 @@ int og_res_pcg(const og_grid* g, double dte, const double* b, double* x, double 
     double* q = (double*)malloc(sizeof(double) * n);
     og_res_diag(g, dte, d);
     og_res_apply(g, dte, x, q);
+#pragma omp parallel for schedule(static)
     for (long long e = 0; e < n; e++) r[e] = b[e] - q[e];
+#pragma omp parallel for schedule(static)
     for (long long e = 0; e < n; e++) z[e] = r[e] / d[e];
+#pragma omp parallel for schedule(static)
     for (long long e = 0; e < n; e++) p[e] = z[e];
     double rz = dot(n, r, z);
     double rn = sqrt(dot(n, r, r));
@@ -1575,14 +1658,18 @@ int og_res_pcg(const og_grid* g, double dte, const double* b, double* x, double 
         double pq = dot(n, p, q);
         if (!(pq > 0.0)) { status = OG_ERR_NOCONV; break; }
         double a = rz / pq;
+#pragma omp parallel for schedule(static)
         for (long long e = 0; e < n; e++) x[e] += a * p[e];
+#pragma omp parallel for schedule(static)
         for (long long e = 0; e < n; e++) r[e] -= a * q[e];
         k++;
         rn = sqrt(dot(n, r, r));
+#pragma omp parallel for schedule(static)
         for (long long e = 0; e < n; e++) z[e] = r[e] / d[e];
         double rz_new = dot(n, r, z);
         double beta = rz_new / rz;
         rz = rz_new;
+#pragma omp parallel for schedule(static)
         for (long long e = 0; e < n; e++) p[e] = z[e] + beta * p[e];
     }
     *iters = k;
@@ -1719,8 +1806,10 @@ int og_pcg_pc2(const og_grid* g, double alpha, int blocks, int ncomp, const doub
     int status = OG_OK;
     if (og_ilu0(g, alpha, blocks, dt) != 0) status = OG_ERR_NOCONV;
     og_apply_M(g, alpha, ncomp, x, q);
+#pragma omp parallel for schedule(static)
     for (long long e = 0; e < n; e++) r[e] = b[e] - q[e];
     og_ilu0_apply(g, alpha, blocks, dt, ncomp, r, z);
+#pragma omp parallel for schedule(static)
     for (long long e = 0; e < n; e++) p[e] = z[e];
     double rz = dot(n, r, z);
     double rn = sqrt(dot(n, r, r));
@@ -1736,7 +1825,9 @@ int og_pcg_pc2(const og_grid* g, double alpha, int blocks, int ncomp, const doub
         double pq = dot(n, p, q);
         if (!(pq > 0.0)) { status = OG_ERR_NOCONV; break; }
         double a = rz / pq;
+#pragma omp parallel for schedule(static)
         for (long long e = 0; e < n; e++) x[e] += a * p[e];
+#pragma omp parallel for schedule(static)
         for (long long e = 0; e < n; e++) r[e] -= a * q[e];
         k++;
         rn = sqrt(dot(n, r, r));
@@ -1744,6 +1835,7 @@ int og_pcg_pc2(const og_grid* g, double alpha, int blocks, int ncomp, const doub
         double rz_new = dot(n, r, z);
         double beta = rz_new / rz;
         rz = rz_new;
+#pragma omp parallel for schedule(static)
         for (long long e = 0; e < n; e++) p[e] = z[e] + beta * p[e];
     }
     *iters = k;

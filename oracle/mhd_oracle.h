@@ -42,6 +42,9 @@ void og_apply_K_neumann(const og_grid* g, int ncomp, const double* p, double* q)
 /* diagonal of M_alpha per (i,j) row, nr*nt entries */
 void og_diag(const og_grid* g, double alpha, double* d);
 
+/* threads of the OpenMP timing build (n > 0 sets them); the plain build returns 1 */
+int og_set_threads(int n);
+
 /* the inner product every PCG form of the oracle uses (compensated, reading P12) */
 double og_dot(long long n, const double* a, const double* b);
 

@@ -8,7 +8,7 @@ takes ownership of them.
 The functions keep the C names:
     mhd_grid_create, mhd_grid_destroy, mhd_grid_sizes, mhd_step_coeffs, mhd_step,
     mhd_apply_operator, mhd_force, mhd_induction, pcg_solve, pcg_solve_batched,
-    mhd_adjoint_step, mhd_last_error
+    mhd_adjoint_step, mhd_grid_reserve, pcg_batch_reserve, mhd_last_error
 """
 from __future__ import annotations
 
@@ -23,12 +23,14 @@ MHD_OK, MHD_ERR_ARG, MHD_ERR_CUDA, MHD_ERR_NOCONV, MHD_ERR_NONFINITE, MHD_ERR_TI
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_NOCONV", 4: "ERR_NONFINITE",
                 5: "ERR_TIMEOUT", 6: "ERR_OOM"}
 PREC_FP64, PREC_MIXED = 0, 1
+(RESERVE_PC1, RESERVE_MIXED, RESERVE_CG, RESERVE_PC2, RESERVE_RESISTIVITY, RESERVE_ADJOINT,
+ RESERVE_ALL) = 1, 2, 4, 8, 16, 32, 63
 
 # C ABI symbols declared in include/mhd.h
 SYMBOLS = ["mhd_grid_create", "mhd_grid_destroy", "mhd_grid_sizes", "mhd_step_coeffs", "mhd_step",
            "mhd_apply_operator", "mhd_force", "mhd_induction", "pcg_solve", "pcg_solve_batched",
-           "mhd_adjoint_step", "mhd_force_noalloc", "mhd_profile_enable", "mhd_profile_read",
-           "mhd_last_error"]
+           "mhd_adjoint_step", "mhd_force_noalloc", "mhd_grid_reserve", "pcg_batch_reserve",
+           "mhd_profile_enable", "mhd_profile_read", "mhd_last_error"]
 
 KERNELS = ["pupdate64", "spmv64", "update64", "pupdate32", "spmv32", "update32", "outer_res", "force",
            "induction", "coeffs", "sts", "res", "pc2", "pspmv32", "pfold32", "rupd32"]
@@ -100,6 +102,9 @@ def lib():
             L.mhd_adjoint_step.argtypes = [vp, C.POINTER(Params), C.POINTER(Fields), d,
                                            C.POINTER(Fields), C.POINTER(Fields)]
             L.mhd_force_noalloc.argtypes = [C.POINTER(GridDesc), C.POINTER(Fields), d, vp, vp]
+            L.mhd_grid_reserve.argtypes = [vp, i]
+            L.pcg_batch_reserve.argtypes = [i, C.POINTER(vp), C.POINTER(C.c_double), C.POINTER(vp), C.POINTER(vp),
+                                            C.POINTER(Params)]
             L.mhd_profile_enable.argtypes = [vp, i]
             L.mhd_profile_read.argtypes = [vp, i, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
             L.mhd_last_error.argtypes = [vp]
@@ -253,6 +258,21 @@ def mhd_adjoint_step(grid: Grid, params: Params, state_n: Fields, dt: float, adj
                                 C.byref(adj_n))
     _check(st, grid, soft=(MHD_OK, MHD_ERR_NOCONV, MHD_ERR_NONFINITE))
     return st
+
+
+def mhd_grid_reserve(grid: Grid, features: int = RESERVE_ALL):
+    """Allocate now what the named features would allocate on first use (see include/mhd.h)."""
+    _check(lib().mhd_grid_reserve(grid.handle, int(features)), grid)
+
+
+def pcg_batch_reserve(grids, alphas, bs, xs, params: Params):
+    """Build the plan and graph of this batch for pcg_solve_batched (solves nothing)."""
+    n = len(grids)
+    hs = (C.c_void_p * n)(*[g.handle.value if hasattr(g.handle, "value") else g.handle for g in grids])
+    al = (C.c_double * n)(*[float(a) for a in alphas])
+    bp = (C.c_void_p * n)(*[_ptr(b, "b").value for b in bs])
+    xp = (C.c_void_p * n)(*[_ptr(x, "x").value for x in xs])
+    _check(lib().pcg_batch_reserve(n, hs, al, bp, xp, C.byref(params)), None)
 
 
 def mhd_profile_enable(grid: Grid, enable: bool = True):

@@ -576,6 +576,22 @@ void adjoint_free(mhd_grid_s* g) {
 }
 }  // namespace mhd
 
+namespace mhd {
+// the adjoint's workspace: B^{n+1} and its cotangent (faces), and 8 stacked cell vectors
+mhd_status_t adjoint_reserve(mhd_grid_s* g) {
+    if (g->adj_mem) return MHD_OK;
+    const Dims d = g->d;
+    const long long nbr = (long long)(d.nr + 1) * d.nt * d.np, nbt = (long long)d.nr * (d.nt + 1) * d.np;
+    const long long total = 2 * (nbr + nbt + d.N) + 8 * 3 * d.N + 64;
+    if (cudaMalloc(&g->adj_mem, sizeof(double) * total) != cudaSuccess) {
+        cudaGetLastError();
+        g->adj_mem = nullptr;
+        return set_error(g, MHD_ERR_OOM, "mhd_adjoint_step: workspace allocation failed");
+    }
+    return MHD_OK;
+}
+}  // namespace mhd
+
 extern "C" mhd_status_t mhd_adjoint_step(mhd_grid_t g, const mhd_params_t* p, const mhd_fields_t* s0, double dt,
                                          const mhd_fields_t* a1, mhd_fields_t* a0) {
     if (!g) return MHD_ERR_ARG;
@@ -591,14 +607,9 @@ extern "C" mhd_status_t mhd_adjoint_step(mhd_grid_t g, const mhd_params_t* p, co
     const Dims d = g->d;
     const long long N = d.N, n3 = 3 * N;
     const long long nbr = (long long)(d.nr + 1) * d.nt * d.np, nbt = (long long)d.nr * (d.nt + 1) * d.np, nbp = N;
-    // workspace, allocated on the first adjoint call of this grid
-    const long long total = 2 * (nbr + nbt + nbp) + 8 * n3 + 64;
-    if (!g->adj_mem) {
-        if (cudaMalloc(&g->adj_mem, sizeof(double) * total) != cudaSuccess) {
-            cudaGetLastError();
-            return set_error(g, MHD_ERR_OOM, "mhd_adjoint_step: workspace allocation failed");
-        }
-    }
+    // workspace, allocated on the first adjoint call of this grid (or by mhd_grid_reserve)
+    mhd_status_t sa = adjoint_reserve(g);
+    if (sa != MHD_OK) return sa;
     AdjWork w;
     double* m = static_cast<double*>(g->adj_mem);
     auto take = [&](long long n) {

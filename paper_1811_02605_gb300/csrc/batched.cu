@@ -545,9 +545,10 @@ void batched_forget(mhd_grid_s* g) {
 }
 }  // namespace mhd
 
-extern "C" mhd_status_t pcg_solve_batched(int n, const mhd_grid_t* grids, const double* alpha,
-                                          const double* const* b, double* const* x,
-                                          const mhd_params_t* params, int* iters, double* relres) {
+namespace {
+// the plan of a batch (built and timed on first use) and its graph for these params
+mhd_status_t prepare(int n, const mhd_grid_t* grids, const double* alpha, const double* const* b, double* const* x,
+                     const mhd_params_t* params, Plan** out) {
     if (n < 1 || n > kMaxSys || !grids || !alpha || !b || !x || !params)
         return fail(MHD_ERR_ARG, "pcg_solve_batched: need 1 <= n <= 256 and non-null arrays");
     if (params->precision != MHD_PREC_FP64 || !(params->tol > 0.0) || params->max_iter < 0)
@@ -559,7 +560,6 @@ extern "C" mhd_status_t pcg_solve_batched(int n, const mhd_grid_t* grids, const 
         for (int t = 0; t < s; t++)
             if (grids[t] == grids[s]) return fail(MHD_ERR_ARG, "pcg_solve_batched: a grid appears twice");
     }
-    std::lock_guard<std::mutex> lk(g_mu);
     std::vector<const void*> key;
     for (int s = 0; s < n; s++) {
         key.push_back(grids[s]);
@@ -622,6 +622,20 @@ extern "C" mhd_status_t pcg_solve_batched(int n, const mhd_grid_t* grids, const 
         mhd_status_t stt = capture(P, true, P.max_iter, &P.graph);
         if (stt != MHD_OK) return stt;
     }
+    *out = &P;
+    return MHD_OK;
+}
+}  // namespace
+
+extern "C" mhd_status_t pcg_solve_batched(int n, const mhd_grid_t* grids, const double* alpha,
+                                          const double* const* b, double* const* x,
+                                          const mhd_params_t* params, int* iters, double* relres) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    Plan* pp = nullptr;
+    mhd_status_t sp = prepare(n, grids, alpha, b, x, params, &pp);
+    if (sp != MHD_OK) return sp;
+    Plan& P = *pp;
+    cudaStream_t st = grids[0]->stream;
     if (cudaGraphLaunch(P.graph, st) != cudaSuccess) return fail(MHD_ERR_CUDA, "pcg_solve_batched: graph launch");
     BarrierState hb;
     if (cudaMemcpyAsync(&hb, P.d_bar, sizeof(hb), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -640,4 +654,11 @@ extern "C" mhd_status_t pcg_solve_batched(int n, const mhd_grid_t* grids, const 
     if (worst == MHD_ERR_NOCONV) return fail(worst, "pcg_solve_batched: a system missed the tolerance");
     if (worst == MHD_ERR_NONFINITE) return fail(worst, "pcg_solve_batched: non-finite value");
     return MHD_OK;
+}
+
+extern "C" mhd_status_t pcg_batch_reserve(int n, const mhd_grid_t* grids, const double* alpha,
+                                          const double* const* b, double* const* x, const mhd_params_t* params) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    Plan* pp = nullptr;
+    return prepare(n, grids, alpha, b, x, params, &pp);
 }

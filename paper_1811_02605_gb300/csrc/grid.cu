@@ -353,6 +353,17 @@ extern "C" mhd_status_t mhd_grid_create(const mhd_grid_desc_t* desc, void* cuda_
     return MHD_OK;
 }
 
+extern "C" mhd_status_t mhd_grid_reserve(mhd_grid_t g, int features) {
+    if (!g) return MHD_ERR_ARG;
+    if (features & ~MHD_RESERVE_ALL) return set_error(g, MHD_ERR_ARG, "mhd_grid_reserve: unknown feature bit");
+    mhd_status_t st = solver_reserve(g, features);
+    if (st != MHD_OK) return st;
+    if ((features & MHD_RESERVE_RESISTIVITY) && (st = res_reserve(g)) != MHD_OK) return st;
+    if ((features & MHD_RESERVE_ADJOINT) && (st = adjoint_reserve(g)) != MHD_OK) return st;
+    if (cudaStreamSynchronize(g->stream) != cudaSuccess) return check_cuda(g, "mhd_grid_reserve");
+    return MHD_OK;
+}
+
 extern "C" mhd_status_t mhd_grid_destroy(mhd_grid_t g) {
     if (!g) return MHD_OK;
     cudaStreamSynchronize(g->stream);

@@ -363,6 +363,11 @@ mhd_status_t solve(mhd_grid_s* g, const double* alpha_dev, int nc, const double*
                    double* relres);
 
 mhd_status_t set_error(mhd_grid_s* g, mhd_status_t st, const std::string& msg);
+// allocations ahead of first use (mhd_grid_reserve)
+mhd_status_t res_reserve(mhd_grid_s* g);
+mhd_status_t pc2_reserve(mhd_grid_s* g);
+mhd_status_t adjoint_reserve(mhd_grid_s* g);
+mhd_status_t solver_reserve(mhd_grid_s* g, int features);
 void batched_forget(mhd_grid_s* g);   // batched.cu: drop cached plans that use g
 void adjoint_free(mhd_grid_s* g);     // adjoint.cu: release the adjoint workspace
 

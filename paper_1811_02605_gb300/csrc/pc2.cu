@@ -433,4 +433,10 @@ void pc2_enqueue_line(mhd_grid_s* g, cudaStream_t st, int nc, bool fp32) {
     else launch_line<double, kIter>(g, st, nc);
 }
 
+// PC2 workspace, allocated ahead of the first PC2 solve
+mhd_status_t pc2_reserve(mhd_grid_s* g) {
+    Pc2Work* w = nullptr;
+    return pc2_workspace(g, &w);
+}
+
 }  // namespace mhd

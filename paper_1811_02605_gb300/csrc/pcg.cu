@@ -1385,6 +1385,41 @@ mhd_status_t tune_slab64(mhd_grid_s* g) {
 }
 }  // namespace
 
+namespace {
+__global__ void k_set_unit(double* a) { *a = 1.0; }
+}  // namespace
+
+// kernel choices and CUDA graphs of 3-component solves, ahead of the first solve (mhd_grid_reserve);
+// the tables are built for alpha = 1 so the timed trial iterations run on finite coefficients
+mhd_status_t solver_reserve(mhd_grid_s* g, int features) {
+    k_set_unit<<<1, 1, 0, g->stream>>>(&g->ss->alpha_user);
+    build_tables(g, &g->ss->alpha_user, true);
+    mhd_status_t st = check_cuda(g, "reserve: tables");
+    if (st != MHD_OK) return st;
+    cudaGraphExec_t ge = nullptr;
+    if (features & MHD_RESERVE_PC1) {
+        if (g->slab64 == 0 && (st = tune_slab64(g)) != MHD_OK) return st;
+        if ((st = iteration_graph(g, 0, 3, &ge)) != MHD_OK) return st;
+    }
+    if (features & MHD_RESERVE_MIXED) {
+        if (g->slab32 == 0 && (st = tune_slab32(g, 3)) != MHD_OK) return st;
+        if ((st = iteration_graph(g, 1, 3, &ge)) != MHD_OK) return st;
+    }
+    if (features & MHD_RESERVE_CG) {
+        if ((st = iteration_graph(g, 2, 3, &ge)) != MHD_OK) return st;
+    }
+    if (features & MHD_RESERVE_PC2) {
+        if ((st = pc2_reserve(g)) != MHD_OK) return st;
+        if ((st = iteration_graph(g, 3, 3, &ge)) != MHD_OK) return st;
+        if (features & MHD_RESERVE_MIXED) {
+            if (g->pc2_fused32 == 0) g->pc2_fused32 = (forced_slab() == -1) ? -1 : 1;
+            if ((st = iteration_graph(g, 4, 3, &ge)) != MHD_OK) return st;
+        }
+    }
+    if (cudaStreamSynchronize(g->stream) != cudaSuccess) return check_cuda(g, "reserve: sync");
+    return MHD_OK;
+}
+
 mhd_status_t solve(mhd_grid_s* g, const double* alpha_dev, int nc, const double* b, double* x,
                    const double* x0, const mhd_params_t* prm, int* iters, int* outer, double* relres) {
     const Dims d = g->d;

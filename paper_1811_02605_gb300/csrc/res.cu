@@ -637,4 +637,12 @@ mhd_status_t res_solve(mhd_grid_s* g, const double* dt_dev, double eta, double* 
     return set_error(g, MHD_ERR_NOCONV, "resistive pcg: no convergence within max_iter");
 }
 
+// workspace and iteration graph of the implicit resistive solve, allocated ahead of the first step
+mhd_status_t res_reserve(mhd_grid_s* g) {
+    ResWork* w = nullptr;
+    mhd_status_t st = res_workspace(g, &w);
+    if (st != MHD_OK) return st;
+    return res_graph(g, w);
+}
+
 }  // namespace mhd

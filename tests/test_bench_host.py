@@ -44,3 +44,25 @@ def test_roofline_constants():
     # x, r, p read and written once: 6 passes of a 3-component vector
     assert bench.PCG_BYTES_PER_CELL == {"fp64": 144, "fp32": 72}
     assert bench.PC2_LINE_BYTES_PER_CELL == 7 * 3 * 8 + 8
+
+
+def test_reference_arm_line_on_host_cores():
+    # the reference arm runs the oracle's OpenMP timing build on every host core, names the grid it
+    # ran and the source of its iteration count, and times one thread beside it
+    import json
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--grid", "12x12x24",
+                          "--steps", "1", "--warmup", "0", "--no-anchors", "--ref-iters", "50"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["config"]["grid"] == "12x12x24"
+    cpu = line["cpu_baseline"]
+    assert cpu["cores"] == (os.cpu_count() or 1) and cpu["iters_per_step"] == 50
+    assert cpu["single_thread_value"] > 0 and line["value"] > 0
+    assert "count given" in cpu["iters_source"]
+
+
+def test_full_oracle_step_anchor_has_its_model_beside_it():
+    a = bench.oracle_full_step("parity_32x32x64", "16x16x32", threads=2)
+    assert a["threads"] == 2 and a["pcg_iters"] > 0 and a["ms"] > 0 and a["sampled_model_ms"] > 0

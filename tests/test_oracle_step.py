@@ -95,3 +95,18 @@ def test_step_with_single_reduction_pcg_agrees_within_solver_tolerance():
         assert abs(ia["iters"][q] - ib["iters"][q]) <= 1
     for k in ("vr", "vt", "vp", "br", "bt", "bp"):
         assert np.linalg.norm(a[k] - b[k]) <= 1e-8 * np.linalg.norm(a[k]), k
+
+
+def test_openmp_timing_build_matches_plain_build():
+    # the benchmark times the oracle built with -fopenmp on all host cores; it must compute the
+    # same step as the plain build (dot products in fixed chunks: agreement to rounding)
+    w, st = I.workload("parity_32x32x64")
+    d = w["desc"]
+    n = O.set_threads(4)
+    assert n == 4
+    a, ia = O.Grid.from_desc(d).step(st, nu=w["nu"], cfl=w["cfl"], tol=w["tol"])
+    b, ib = O.Grid.from_desc(d, omp=True).step(st, nu=w["nu"], cfl=w["cfl"], tol=w["tol"])
+    assert ia["iters"] == ib["iters"] and ia["dt"] == ib["dt"]
+    for k in a:
+        assert np.linalg.norm(a[k] - b[k]) <= 1e-12 * np.linalg.norm(a[k]), k
+    assert O.set_threads(0, omp=False) == 1
