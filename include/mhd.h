@@ -254,6 +254,33 @@ mhd_status_t mhd_adjoint_step(mhd_grid_t grid, const mhd_params_t* params,
 mhd_status_t mhd_force_noalloc(const mhd_grid_desc_t* desc, const mhd_fields_t* fields, double dt,
                                double* b, void* cuda_stream);
 
+/* Domain decomposition in r (Sec. 4.2: the code runs one MPI rank per GPU, each rank owning a part
+ * of the mesh; a PCG iteration exchanges the boundary values its operator application needs and
+ * sums the few scalars of its inner products over the ranks with an allreduce). A slab grid holds
+ * the radial rows [i0, i1) of the grid `desc` describes (at least 2 rows), with the
+ * global metric and operator tables of those rows; its vectors are [ncomp][i1-i0][nt][np]. The
+ * calls of a whole grid (mhd_step, pcg_solve, mhd_apply_operator, ...) refuse a slab grid; the
+ * distributed point-Jacobi PCG of paper_1811_02605_gb300/dist.py drives these three calls and does
+ * the exchange and the sums. */
+mhd_status_t mhd_grid_create_slab(const mhd_grid_desc_t* desc, int i0, int i1, void* cuda_stream, mhd_grid_t* out);
+
+/* q = M_alpha p on the slab's rows (Sec. 4.1 operator; same arithmetic and order as the whole
+ * grid's operator, so the rows are bit-identical to it). p_lo / p_hi: the neighbours' boundary
+ * planes, global rows i0-1 and i1 ([ncomp][nt][np] device arrays); NULL exactly where the slab
+ * touches r0 or r1 (MHD_ERR_ARG otherwise). *pq (nullable, host): the slab's share of <p, q>
+ * (synchronises the stream when given). */
+mhd_status_t mhd_slab_apply(mhd_grid_t slab, double alpha, int ncomp, const double* p, const double* p_lo,
+                            const double* p_hi, double* q, double* pq);
+
+/* One iteration's vector updates of point-Jacobi PCG (Sec. 2.2, PC1) on the slab: x += a p (skipped
+ * when x is NULL), r -= a q, z = r / diag(M_alpha); dots (host) = the slab's shares of <r, z> and
+ * <r, r>. Synchronises the stream. */
+mhd_status_t mhd_slab_update(mhd_grid_t slab, double alpha, int ncomp, double a, double* x, const double* p,
+                             double* r, const double* q, double* z, double dots[2]);
+
+/* p = z + beta p (p = z when beta = 0, whatever p held). */
+mhd_status_t mhd_slab_pupdate(mhd_grid_t slab, int ncomp, double beta, const double* z, double* p);
+
 /* Workspace reservation (not part of the method; the paper has no counterpart). Some features
  * allocate on their first use: the PC2 factorisation, the implicit-resistivity face vectors, the
  * adjoint workspace, and the CUDA graphs of the PCG iterations (instantiating a graph can take

@@ -30,6 +30,7 @@ PREC_FP64, PREC_MIXED = 0, 1
 SYMBOLS = ["mhd_grid_create", "mhd_grid_destroy", "mhd_grid_sizes", "mhd_step_coeffs", "mhd_step",
            "mhd_apply_operator", "mhd_force", "mhd_induction", "pcg_solve", "pcg_solve_batched",
            "mhd_adjoint_step", "mhd_force_noalloc", "mhd_grid_reserve", "pcg_batch_reserve",
+           "mhd_grid_create_slab", "mhd_slab_apply", "mhd_slab_update", "mhd_slab_pupdate",
            "mhd_profile_enable", "mhd_profile_read", "mhd_last_error"]
 
 KERNELS = ["pupdate64", "spmv64", "update64", "pupdate32", "spmv32", "update32", "outer_res", "force",
@@ -103,6 +104,10 @@ def lib():
                                            C.POINTER(Fields), C.POINTER(Fields)]
             L.mhd_force_noalloc.argtypes = [C.POINTER(GridDesc), C.POINTER(Fields), d, vp, vp]
             L.mhd_grid_reserve.argtypes = [vp, i]
+            L.mhd_grid_create_slab.argtypes = [C.POINTER(GridDesc), i, i, vp, C.POINTER(vp)]
+            L.mhd_slab_apply.argtypes = [vp, d, i, vp, vp, vp, vp, C.POINTER(C.c_double)]
+            L.mhd_slab_update.argtypes = [vp, d, i, d, vp, vp, vp, vp, vp, C.POINTER(C.c_double)]
+            L.mhd_slab_pupdate.argtypes = [vp, i, d, vp, vp]
             L.pcg_batch_reserve.argtypes = [i, C.POINTER(vp), C.POINTER(C.c_double), C.POINTER(vp), C.POINTER(vp),
                                             C.POINTER(Params)]
             L.mhd_profile_enable.argtypes = [vp, i]
@@ -188,6 +193,47 @@ def mhd_grid_create(nr, nt, np_, r0, r1, stretch, stream=None) -> Grid:
     h = C.c_void_p()
     _check(lib().mhd_grid_create(C.byref(d), C.c_void_p(s), C.byref(h)))
     return Grid(h, d)
+
+
+def mhd_grid_create_slab(nr, nt, np_, r0, r1, stretch, i0, i1, stream=None) -> Grid:
+    """Radial rows [i0, i1) of the grid (nr, nt, np_, r0, r1, stretch); see include/mhd.h. The
+    returned Grid's desc is the slab's own (nr = i1 - i0)."""
+    import torch
+    if stream is None:
+        s = torch.cuda.current_stream().cuda_stream
+    elif hasattr(stream, "cuda_stream"):
+        s = stream.cuda_stream
+    else:
+        s = int(stream)
+    d = GridDesc(nr, nt, np_, r0, r1, stretch)
+    h = C.c_void_p()
+    _check(lib().mhd_grid_create_slab(C.byref(d), int(i0), int(i1), C.c_void_p(s), C.byref(h)))
+    return Grid(h, GridDesc(i1 - i0, nt, np_, r0, r1, stretch))
+
+
+def mhd_slab_apply(grid: Grid, alpha: float, p, p_lo, p_hi, q) -> float:
+    """q = M_alpha p on the slab (ghost planes p_lo, p_hi or None); returns the slab's <p, q>."""
+    nc = p.numel() // (grid.desc.nr * grid.desc.nt * grid.desc.np)
+    pq = C.c_double(0)
+    _check(lib().mhd_slab_apply(grid.handle, float(alpha), nc, _ptr(p, "p"),
+                                None if p_lo is None else _ptr(p_lo, "p_lo"),
+                                None if p_hi is None else _ptr(p_hi, "p_hi"), _ptr(q, "q"), C.byref(pq)), grid)
+    return pq.value
+
+
+def mhd_slab_update(grid: Grid, alpha: float, a: float, x, p, r, q, z):
+    """x += a p (x may be None), r -= a q, z = r / diag; returns the slab's (<r, z>, <r, r>)."""
+    nc = r.numel() // (grid.desc.nr * grid.desc.nt * grid.desc.np)
+    dots = (C.c_double * 2)()
+    _check(lib().mhd_slab_update(grid.handle, float(alpha), nc, float(a), None if x is None else _ptr(x, "x"),
+                                 None if p is None else _ptr(p, "p"), _ptr(r, "r"), _ptr(q, "q"), _ptr(z, "z"),
+                                 dots), grid)
+    return dots[0], dots[1]
+
+
+def mhd_slab_pupdate(grid: Grid, beta: float, z, p):
+    nc = z.numel() // (grid.desc.nr * grid.desc.nt * grid.desc.np)
+    _check(lib().mhd_slab_pupdate(grid.handle, nc, float(beta), _ptr(z, "z"), _ptr(p, "p")), grid)
 
 
 def mhd_grid_destroy(grid: Grid):

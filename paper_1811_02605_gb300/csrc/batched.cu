@@ -557,6 +557,7 @@ mhd_status_t prepare(int n, const mhd_grid_t* grids, const double* alpha, const 
         if (!grids[s] || !b[s] || !x[s] || !(alpha[s] >= 0.0))
             return fail(MHD_ERR_ARG, "pcg_solve_batched: null grid/vector or negative alpha");
         if ((const double*)x[s] == b[s]) return fail(MHD_ERR_ARG, "pcg_solve_batched: x aliases b");
+        if (grids[s]->slab_nr_global > 0) return fail(MHD_ERR_ARG, "pcg_solve_batched: a slab grid");
         for (int t = 0; t < s; t++)
             if (grids[t] == grids[s]) return fail(MHD_ERR_ARG, "pcg_solve_batched: a grid appears twice");
     }

@@ -207,17 +207,61 @@ bool dalloc(T** p, size_t n, std::vector<void*>& owned) {
     return true;
 }
 
+// rows [i0, i1) of the global grid's tables (the whole grid when i0 = 0, i1 = nr)
+HostGeo slice_geo(const HostGeo& a, int nr_global, int nt, int i0, int i1) {
+    if (i0 == 0 && i1 == nr_global) return a;
+    HostGeo h;
+    const size_t t = (size_t)nt, t1 = (size_t)nt + 1;
+    h.r.assign(a.r.begin() + i0, a.r.begin() + i1 + 1);
+    h.rc.assign(a.rc.begin() + i0, a.rc.begin() + i1);
+    h.rho.assign(a.rho.begin() + i0, a.rho.begin() + i1);
+    h.sn = a.sn;
+    h.cn = a.cn;
+    h.sc = a.sc;
+    h.cc = a.cc;
+    h.rhoV.assign(a.rhoV.begin() + i0 * t, a.rhoV.begin() + i1 * t);
+    h.kt2.assign(a.kt2.begin() + i0 * t, a.kt2.begin() + i1 * t);
+    h.wr.assign(a.wr.begin() + i0 * t, a.wr.begin() + (i1 + 1) * t);
+    h.wt.assign(a.wt.begin() + i0 * t1, a.wt.begin() + i1 * t1);
+    h.wp.assign(a.wp.begin() + i0 * t, a.wp.begin() + i1 * t);
+    h.max_kt2 = a.max_kt2;
+    return h;
+}
+
+mhd_status_t create_grid(const mhd_grid_desc_t* desc, int i0, int i1, void* cuda_stream, mhd_grid_t* out);
+
 }  // namespace
 
-extern "C" mhd_status_t mhd_grid_create(const mhd_grid_desc_t* desc, void* cuda_stream,
-                                        mhd_grid_t* out) {
+extern "C" mhd_status_t mhd_grid_create(const mhd_grid_desc_t* desc, void* cuda_stream, mhd_grid_t* out) {
     if (!desc || !out) return set_error(nullptr, MHD_ERR_ARG, "mhd_grid_create: null argument");
+    return create_grid(desc, 0, desc->nr, cuda_stream, out);
+}
+
+extern "C" mhd_status_t mhd_grid_create_slab(const mhd_grid_desc_t* desc, int i0, int i1, void* cuda_stream,
+                                             mhd_grid_t* out) {
+    if (!desc || !out) return set_error(nullptr, MHD_ERR_ARG, "mhd_grid_create_slab: null argument");
+    if (i0 < 0 || i1 > desc->nr || i1 - i0 < 2)
+        return set_error(nullptr, MHD_ERR_ARG, "mhd_grid_create_slab: need 0 <= i0, i1 <= nr, i1 - i0 >= 2");
+    return create_grid(desc, i0, i1, cuda_stream, out);
+}
+
+namespace {
+mhd_status_t create_grid(const mhd_grid_desc_t* desc, int i0, int i1, void* cuda_stream, mhd_grid_t* out) {
     *out = nullptr;
-    const mhd_grid_desc_t d = *desc;
-    if (d.nr < 2 || d.nt < 2 || d.np < 2 || (d.np % 2) != 0)
+    const mhd_grid_desc_t dg = *desc;
+    if (dg.nr < 2 || dg.nt < 2 || dg.np < 2 || (dg.np % 2) != 0)
         return set_error(nullptr, MHD_ERR_ARG, "mhd_grid_create: need nr>=2, nt>=2, np even >= 2");
-    if (!(d.r0 > 0) || !(d.r1 > d.r0) || !(d.stretch > 0))
+    if (!(dg.r0 > 0) || !(dg.r1 > dg.r0) || !(dg.stretch > 0))
         return set_error(nullptr, MHD_ERR_ARG, "mhd_grid_create: need 0 < r0 < r1, stretch > 0");
+    const bool slab = !(i0 == 0 && i1 == dg.nr);
+    // a slab is described by its own rows: nr = i1 - i0, r0 and r1 its first and last radial nodes
+    const HostGeo hg = make_geo(dg);
+    mhd_grid_desc_t d = dg;
+    if (slab) {
+        d.nr = i1 - i0;
+        d.r0 = hg.r[i0];
+        d.r1 = hg.r[i1];
+    }
     const long long N = (long long)d.nr * d.nt * d.np;
     // every flat index the kernels split (three face or edge families together) stays below 2^31
     if (N > (1LL << 30) || 3LL * (d.nr + 1) * (d.nt + 1) * d.np >= (1LL << 31))
@@ -235,7 +279,7 @@ extern "C" mhd_status_t mhd_grid_create(const mhd_grid_desc_t* desc, void* cuda_
     g->graph_batch = 16;
     std::memset(g->iter_graph, 0, sizeof(g->iter_graph));
 
-    HostGeo h = make_geo(d);
+    HostGeo h = slice_geo(hg, dg.nr, d.nt, i0, i1);
     HostEx hx = make_ex(h, d);
     g->max_kt2 = h.max_kt2;
     std::vector<void*> owned;
@@ -271,7 +315,10 @@ extern "C" mhd_status_t mhd_grid_create(const mhd_grid_desc_t* desc, void* cuda_
          dalloc(&g->ep, (size_t)(nr + 1) * (nt + 1) * d.np, owned) && dalloc(&g->ec, n3, owned) &&
          dalloc(&g->ring, 2 * (size_t)nr, owned) && dalloc(&g->sts_tab, 8 * (size_t)nr * nt, owned);
     double* pcs = nullptr;
-    ok = ok && dalloc(&pcs, 2 * (size_t)d.np, owned) && dalloc(&g->bharm, 8 * (size_t)nr, owned);
+    ok = ok && dalloc(&pcs, 2 * (size_t)d.np, owned) && dalloc(&g->bharm, 8 * (size_t)nr, owned) &&
+         dalloc(&g->slab_out, 8 + 2 * (size_t)nt, owned);
+    g->slab_i0 = slab ? i0 : 0;
+    g->slab_nr_global = slab ? dg.nr : 0;
     ok = ok && dalloc(&g->partials, (size_t)kMaxBlocks * kPartialsPerBlock + 16, owned) &&
          dalloc(&g->sc, 1, owned) && dalloc(&g->ss, 1, owned);
     if (!ok) {
@@ -353,8 +400,11 @@ extern "C" mhd_status_t mhd_grid_create(const mhd_grid_desc_t* desc, void* cuda_
     return MHD_OK;
 }
 
+}  // namespace
+
 extern "C" mhd_status_t mhd_grid_reserve(mhd_grid_t g, int features) {
     if (!g) return MHD_ERR_ARG;
+    if (g->slab_nr_global > 0) return set_error(g, MHD_ERR_ARG, "mhd_grid_reserve: not available on a slab grid");
     if (features & ~MHD_RESERVE_ALL) return set_error(g, MHD_ERR_ARG, "mhd_grid_reserve: unknown feature bit");
     mhd_status_t st = solver_reserve(g, features);
     if (st != MHD_OK) return st;

@@ -251,6 +251,9 @@ struct mhd_grid_s {
     double *er, *et, *ep;   // edge arrays (E or J)
     double *ec;             // cell-centred E (3N)
     double *ring;           // [2*nr] polar ring sums
+    int slab_i0;            // slab grids (mhd_grid_create_slab): first global row; slab_nr_global is
+    int slab_nr_global;     // the global row count (0 for an ordinary grid)
+    double *slab_out;       // [8 + 2*nt] slab calls: reduction results, interface couplings
     double *bharm;          // [8*nr] first-harmonic sums of the rings next to the poles: [0, 4 nr) of
                             // the B_theta faces (north rows, then south; cos and sin per row), [4 nr,
                             // 8 nr) scratch of the adjoint's transpose

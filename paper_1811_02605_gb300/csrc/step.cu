@@ -43,6 +43,13 @@ bool fields_ok(const mhd_fields_t* f, bool need_v) {
     return true;
 }
 
+// the calls of a whole grid are refused on a slab of one (its edge rows couple to ghost planes)
+mhd_status_t whole_grid(mhd_grid_s* g, const char* what) {
+    if (g->slab_nr_global > 0)
+        return set_error(g, MHD_ERR_ARG, std::string(what) + ": not available on a slab grid (mhd_slab_* calls)");
+    return MHD_OK;
+}
+
 mhd_status_t read_step_scalars(mhd_grid_s* g) {
     if (cudaMemcpyAsync(g->h_ss, g->ss, sizeof(StepScalars), cudaMemcpyDeviceToHost, g->stream) != cudaSuccess)
         return check_cuda(g, "read step scalars");
@@ -55,6 +62,7 @@ mhd_status_t read_step_scalars(mhd_grid_s* g) {
 extern "C" mhd_status_t mhd_step_coeffs(mhd_grid_t g, const mhd_params_t* p, const mhd_fields_t* f,
                                         mhd_step_info_t* info) {
     if (!g) return MHD_ERR_ARG;
+    if (whole_grid(g, "mhd_step_coeffs") != MHD_OK) return MHD_ERR_ARG;
     mhd_status_t st = check_params(g, p);
     if (st != MHD_OK) return st;
     if (!fields_ok(f, true)) return set_error(g, MHD_ERR_ARG, "mhd_step_coeffs: null field pointer");
@@ -75,6 +83,7 @@ extern "C" mhd_status_t mhd_step_coeffs(mhd_grid_t g, const mhd_params_t* p, con
 
 extern "C" mhd_status_t mhd_step(mhd_grid_t g, const mhd_params_t* p, mhd_fields_t* f, mhd_step_info_t* info) {
     if (!g) return MHD_ERR_ARG;
+    if (whole_grid(g, "mhd_step") != MHD_OK) return MHD_ERR_ARG;
     mhd_status_t st = check_params(g, p);
     if (st != MHD_OK) return st;
     if (!fields_ok(f, true)) return set_error(g, MHD_ERR_ARG, "mhd_step: null field pointer");
@@ -161,6 +170,7 @@ extern "C" mhd_status_t mhd_step(mhd_grid_t g, const mhd_params_t* p, mhd_fields
 
 extern "C" mhd_status_t mhd_apply_operator(mhd_grid_t g, double alpha, int ncomp, const double* p, double* q) {
     if (!g) return MHD_ERR_ARG;
+    if (whole_grid(g, "mhd_apply_operator") != MHD_OK) return MHD_ERR_ARG;
     if (ncomp < 1 || ncomp > 3 || !p || !q || p == q)
         return set_error(g, MHD_ERR_ARG, "mhd_apply_operator: need 1 <= ncomp <= 3, distinct non-null p, q");
     if (!(alpha >= 0.0)) return set_error(g, MHD_ERR_ARG, "mhd_apply_operator: alpha must be >= 0");
@@ -171,6 +181,7 @@ extern "C" mhd_status_t mhd_apply_operator(mhd_grid_t g, double alpha, int ncomp
 
 extern "C" mhd_status_t mhd_force(mhd_grid_t g, const mhd_fields_t* f, double dt, double* b) {
     if (!g) return MHD_ERR_ARG;
+    if (whole_grid(g, "mhd_force") != MHD_OK) return MHD_ERR_ARG;
     if (!fields_ok(f, true) || !b) return set_error(g, MHD_ERR_ARG, "mhd_force: null pointer");
     force(g, f->vr, f->vt, f->vp, nullptr, 0.0, f->br, f->bt, f->bp, nullptr, dt, nullptr, b);
     return check_cuda(g, "mhd_force");
@@ -178,6 +189,7 @@ extern "C" mhd_status_t mhd_force(mhd_grid_t g, const mhd_fields_t* f, double dt
 
 extern "C" mhd_status_t mhd_induction(mhd_grid_t g, const double* vbar, double eta, double dt, mhd_fields_t* f) {
     if (!g) return MHD_ERR_ARG;
+    if (whole_grid(g, "mhd_induction") != MHD_OK) return MHD_ERR_ARG;
     if (!fields_ok(f, false) || !vbar) return set_error(g, MHD_ERR_ARG, "mhd_induction: null pointer");
     const long long N = g->d.N;
     induction(g, vbar, vbar + N, vbar + 2 * N, nullptr, 0.0, eta, nullptr, dt, f->br, f->bt, f->bp);
@@ -187,6 +199,7 @@ extern "C" mhd_status_t mhd_induction(mhd_grid_t g, const double* vbar, double e
 extern "C" mhd_status_t pcg_solve(mhd_grid_t g, double alpha, int ncomp, const double* b, double* x,
                                   const mhd_params_t* p, int* iters, int* outer, double* relres) {
     if (!g) return MHD_ERR_ARG;
+    if (whole_grid(g, "pcg_solve") != MHD_OK) return MHD_ERR_ARG;
     mhd_status_t st = check_params(g, p);
     if (st != MHD_OK) return st;
     if (ncomp < 1 || ncomp > 3 || !b || !x || (const double*)x == b)
