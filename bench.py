@@ -865,9 +865,11 @@ def run_accuracy_study(args):
                 else:
                     errs[s] = {k: float(torch.linalg.norm(ds[k] - ref[s][k]) / torch.linalg.norm(ref[s][k]))
                                for k in ds}
+        diag = P.mhd_diagnostics(g, f)   # Sec. 3.1: the paper compares such integrals between solver forms
         rows.append(dict(variant=name, ms_per_step=round(ms / args.acc_steps, 3),
                          pcg_iters_per_step=round(iters / args.acc_steps, 2), max_final_relres=worst,
-                         rel_l2_vs_fp64_pc1={str(s): e for s, e in errs.items()}))
+                         rel_l2_vs_fp64_pc1={str(s): e for s, e in errs.items()},
+                         diagnostics_after_steps=diag))
         del ds, f
     print(json.dumps(dict(accuracy_study=f"{d.nr}x{d.nt}x{d.np}", workload=args.workload,
                           steps=args.acc_steps, reference="FP64 point-Jacobi PCG on the GPU (the same "

@@ -254,6 +254,14 @@ mhd_status_t mhd_adjoint_step(mhd_grid_t grid, const mhd_params_t* params,
 mhd_status_t mhd_force_noalloc(const mhd_grid_desc_t* desc, const mhd_fields_t* fields, double dt,
                                double* b, void* cuda_stream);
 
+/* Field diagnostics (Sec. 3.1 validates its runs by the integrated magnetic and kinetic energies
+ * and by |J x B| and |J . B|): out[0] = magnetic energy 1/2 sum_c |B_c|^2 V_c, out[1] = kinetic
+ * energy 1/2 sum_c rho_c |v_c|^2 V_c, out[2] = sum_c |J_c x B_c| V_c, out[3] = sum_c |J_c . B_c| V_c,
+ * out[4] = max_c |div_h B|, the net outward flux of a cell over its volume (0 to rounding while B
+ * evolves by constrained transport). B_c and J_c are the cell-centred fields of the momentum force.
+ * FP64 device reductions; synchronises the grid's stream. */
+mhd_status_t mhd_diagnostics(mhd_grid_t grid, const mhd_fields_t* fields, double out[5]);
+
 /* Domain decomposition in r (Sec. 4.2: the code runs one MPI rank per GPU, each rank owning a part
  * of the mesh; a PCG iteration exchanges the boundary values its operator application needs and
  * sums the few scalars of its inner products over the ranks with an allreduce). A slab grid holds

@@ -102,6 +102,7 @@ def _declare(L):
     L.og_efield_edges.argtypes = [vp, _dp, _dp, _dp, _dp, d, _dp, _dp, _dp]
     L.og_ct.argtypes = [vp, _dp, _dp, _dp, d, _dp, _dp, _dp]
     L.og_divb.argtypes = [vp, _dp, _dp, _dp, _dp]
+    L.og_diagnostics.argtypes = [vp, _dp, _dp, _dp, _dp, _dp]
     L.og_step.restype = i
     L.og_step.argtypes = [vp, d, d, d, d, d, d, d, i, _dp, _dp, _dp, _dp, _dp]
     L.og_step_cg.restype = i
@@ -373,6 +374,17 @@ def _adjoint(self, state, lam, dt, asi, nu=1e-3, eta=0.0, cfl=0.4, tol=1e-13, ma
 
 
 Grid.adjoint_step = _adjoint
+
+
+def _diagnostics(self, state):
+    """dict: magnetic and kinetic energy, int |J x B| dV, int |J . B| dV, max |div_h B|."""
+    v = np.ascontiguousarray(np.stack([state["vr"], state["vt"], state["vp"]]), dtype=np.float64)
+    o = np.empty(5)
+    self.L.og_diagnostics(self.h, v, _c(state["br"]), _c(state["bt"]), _c(state["bp"]), o)
+    return dict(magnetic_energy=o[0], kinetic_energy=o[1], int_jxb=o[2], int_jdotb=o[3], max_divb=o[4])
+
+
+Grid.diagnostics = _diagnostics
 
 
 def _rkl2_stages(self, nu, dt):

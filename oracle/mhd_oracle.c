@@ -773,6 +773,46 @@ void og_divb(const og_grid* g, const double* br, const double* bt, const double*
 }
 
 /* ---------------------------------------------------------------------------------------------
+ * Field diagnostics (Sec. 3.1 validates runs by the integrated energies and by |J x B| and
+ * |J . B|): out[0] = magnetic energy 1/2 sum_c |B_c|^2 V_c, out[1] = kinetic energy
+ * 1/2 sum_c rho_c |v_c|^2 V_c, out[2] = sum_c |J_c x B_c| V_c, out[3] = sum_c |J_c . B_c| V_c,
+ * out[4] = max_c |div_h B|_c, the net outward flux of the cell over its volume. B_c and J_c are
+ * the cell-centred fields of the momentum force.
+ * ------------------------------------------------------------------------------------------- */
+void og_diagnostics(const og_grid* g, const double* v, const double* br, const double* bt, const double* bp,
+                    double* out) {
+    long long N = g->N;
+    int nt = g->nt;
+    edges3 e = edges_alloc(g);
+    og_current_edges(g, br, bt, bp, e.jr, e.jt, e.jp);
+    double* div = (double*)malloc(sizeof(double) * N);
+    og_divb(g, br, bt, bp, div);
+    double em = 0.0, ek = 0.0, jxb = 0.0, jdb = 0.0, dmax = 0.0;
+    for (int i = 0; i < g->nr; i++)
+        for (int j = 0; j < nt; j++)
+            for (int k = 0; k < g->np; k++) {
+                long long c = IDX(g, i, j, k);
+                double V = g->vol[i * nt + j], rho = g->rho[i * nt + j];
+                double B[3], J[3];
+                bcentre_at(g, br, bt, bp, i, j, k, B);
+                current_centre_from_edges(g, e.jr, e.jt, e.jp, i, j, k, J);
+                double u0 = v[c], u1 = v[N + c], u2 = v[2 * N + c];
+                double x0 = J[1] * B[2] - J[2] * B[1];
+                double x1 = J[2] * B[0] - J[0] * B[2];
+                double x2 = J[0] * B[1] - J[1] * B[0];
+                em += 0.5 * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]) * V;
+                ek += 0.5 * rho * (u0 * u0 + u1 * u1 + u2 * u2) * V;
+                jxb += sqrt(x0 * x0 + x1 * x1 + x2 * x2) * V;
+                jdb += fabs(J[0] * B[0] + J[1] * B[1] + J[2] * B[2]) * V;
+                double dv = fabs(div[c]) / V;
+                if (dv > dmax) dmax = dv;
+            }
+    out[0] = em; out[1] = ek; out[2] = jxb; out[3] = jdb; out[4] = dmax;
+    free(div);
+    edges_free(e);
+}
+
+/* ---------------------------------------------------------------------------------------------
  * Step coefficients (Sec. 2.1: S = (dt^2 k~^2)^-1 (C_w^2/(1-C_f)^2 - 1), k~^2 the upper limit
  * of the combined inverse grid spacing). Reading R3: dt = cfl / max_c k~_c |v_c| (clipped to
  * dt_max, or fixed); C_f = dt max k~|v|, C_w = dt max k~ |B_c| / sqrt(rho_c);

@@ -45,6 +45,11 @@ void og_diag(const og_grid* g, double alpha, double* d);
 /* threads of the OpenMP timing build (n > 0 sets them); the plain build returns 1 */
 int og_set_threads(int n);
 
+/* field diagnostics (Sec. 3.1): out[5] = magnetic energy, kinetic energy, sum |J x B| V,
+ * sum |J . B| V, max |div_h B| (flux over volume); v stacked [3][N] */
+void og_diagnostics(const og_grid* g, const double* v, const double* br, const double* bt, const double* bp,
+                    double* out);
+
 /* the inner product every PCG form of the oracle uses (compensated, reading P12) */
 double og_dot(long long n, const double* a, const double* b);
 

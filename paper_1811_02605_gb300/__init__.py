@@ -30,7 +30,7 @@ PREC_FP64, PREC_MIXED = 0, 1
 SYMBOLS = ["mhd_grid_create", "mhd_grid_destroy", "mhd_grid_sizes", "mhd_step_coeffs", "mhd_step",
            "mhd_apply_operator", "mhd_force", "mhd_induction", "pcg_solve", "pcg_solve_batched",
            "mhd_adjoint_step", "mhd_force_noalloc", "mhd_grid_reserve", "pcg_batch_reserve",
-           "mhd_grid_create_slab", "mhd_slab_apply", "mhd_slab_update", "mhd_slab_pupdate",
+           "mhd_grid_create_slab", "mhd_slab_apply", "mhd_slab_update", "mhd_slab_pupdate", "mhd_diagnostics",
            "mhd_profile_enable", "mhd_profile_read", "mhd_last_error"]
 
 KERNELS = ["pupdate64", "spmv64", "update64", "pupdate32", "spmv32", "update32", "outer_res", "force",
@@ -104,6 +104,7 @@ def lib():
                                            C.POINTER(Fields), C.POINTER(Fields)]
             L.mhd_force_noalloc.argtypes = [C.POINTER(GridDesc), C.POINTER(Fields), d, vp, vp]
             L.mhd_grid_reserve.argtypes = [vp, i]
+            L.mhd_diagnostics.argtypes = [vp, C.POINTER(Fields), C.POINTER(C.c_double)]
             L.mhd_grid_create_slab.argtypes = [C.POINTER(GridDesc), i, i, vp, C.POINTER(vp)]
             L.mhd_slab_apply.argtypes = [vp, d, i, vp, vp, vp, vp, C.POINTER(C.c_double)]
             L.mhd_slab_update.argtypes = [vp, d, i, d, vp, vp, vp, vp, vp, C.POINTER(C.c_double)]
@@ -304,6 +305,13 @@ def mhd_adjoint_step(grid: Grid, params: Params, state_n: Fields, dt: float, adj
                                 C.byref(adj_n))
     _check(st, grid, soft=(MHD_OK, MHD_ERR_NOCONV, MHD_ERR_NONFINITE))
     return st
+
+
+def mhd_diagnostics(grid: Grid, fields: Fields) -> dict:
+    """Magnetic and kinetic energy, int |J x B| dV, int |J . B| dV, max |div_h B| (include/mhd.h)."""
+    o = (C.c_double * 5)()
+    _check(lib().mhd_diagnostics(grid.handle, C.byref(fields), o), grid)
+    return dict(magnetic_energy=o[0], kinetic_energy=o[1], int_jxb=o[2], int_jdotb=o[3], max_divb=o[4])
 
 
 def mhd_grid_reserve(grid: Grid, features: int = RESERVE_ALL):

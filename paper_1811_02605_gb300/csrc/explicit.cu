@@ -547,6 +547,83 @@ void ct_apply(mhd_grid_s* g, const double* dt_dev, double* br, double* bt, doubl
 }
 
 // ------------------------------------------------------------------------------------------
+// field diagnostics (Sec. 3.1 validates runs by integrated energies and by |J x B| and |J . B|):
+// out[0..3] = magnetic energy, kinetic energy, sum |J_c x B_c| V_c, sum |J_c . B_c| V_c; out[4] =
+// max |div_h B| (net outward flux over the cell volume). B_c and J_c as in the momentum force.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ double cell_volume(const Geo& G, int i, int j) {
+    const double ri = G.r[i], ro = G.r[i + 1];
+    return (ro * ro * ro - ri * ri * ri) / 3.0 * (G.cn[j] - G.cn[j + 1]) * G.dph;
+}
+
+__global__ void __launch_bounds__(kThreads) k_diag_sums(Dims d, Geo G, Vel v, const double* __restrict__ bh,
+                                                        const double* __restrict__ br, const double* __restrict__ bt,
+                                                        const double* __restrict__ bp, const double* __restrict__ jr,
+                                                        const double* __restrict__ jt, const double* __restrict__ jp,
+                                                        unsigned int* count, double* __restrict__ partials,
+                                                        double* __restrict__ out) {
+    double em = 0.0, ek = 0.0, jxb = 0.0, jdb = 0.0;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < d.N;
+         c += (long long)gridDim.x * blockDim.x) {
+        int k;
+        unsigned int ij;
+        split_np(d, c, k, ij);
+        const int j = (int)(ij % d.nt), i = (int)(ij / d.nt);
+        double u[3], B[3], J[3];
+        v.at(c, u);
+        bcentre(d, G, bh, br, bt, bp, i, j, k, B);
+        jcentre(d, jr, jt, jp, i, j, k, J);
+        const double V = cell_volume(G, i, j);
+        const double x0 = J[1] * B[2] - J[2] * B[1], x1 = J[2] * B[0] - J[0] * B[2], x2 = J[0] * B[1] - J[1] * B[0];
+        em += 0.5 * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]) * V;
+        ek += 0.5 * G.rho[i] * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) * V;
+        jxb += sqrt(x0 * x0 + x1 * x1 + x2 * x2) * V;
+        jdb += fabs(J[0] * B[0] + J[1] * B[1] + J[2] * B[2]) * V;
+    }
+    double val[4] = {em, ek, jxb, jdb}, o[4];
+    if (reduce_last<4>(val, partials, count, o) && threadIdx.x == 0)
+        for (int q = 0; q < 4; q++) out[q] = o[q];
+}
+
+__global__ void __launch_bounds__(kThreads) k_diag_divmax(Dims d, Geo G, const double* __restrict__ br,
+                                                          const double* __restrict__ bt,
+                                                          const double* __restrict__ bp, unsigned int* count,
+                                                          double* __restrict__ partials, double* __restrict__ out) {
+    double m = 0.0;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < d.N;
+         c += (long long)gridDim.x * blockDim.x) {
+        int k;
+        unsigned int ij;
+        split_np(d, c, k, ij);
+        const int j = (int)(ij % d.nt), i = (int)(ij / d.nt);
+        const double ri = G.r[i], ro = G.r[i + 1];
+        const double ring = 0.5 * (ro * ro - ri * ri);
+        const double band = G.cn[j] - G.cn[j + 1];
+        const double ari = ri * ri * band * G.dph, aro = ro * ro * band * G.dph;
+        const double atj = G.sn[j] * ring * G.dph, atj1 = G.sn[j + 1] * ring * G.dph;
+        const double ap = ring * G.dth;
+        const double flux = br[ix(d, i + 1, j, k)] * aro - br[ix(d, i, j, k)] * ari + bt[ixt(d, i, j + 1, k)] * atj1 -
+                            bt[ixt(d, i, j, k)] * atj + bp[ix(d, i, j, kp1(d, k))] * ap - bp[ix(d, i, j, k)] * ap;
+        m = fmax(m, fabs(flux) / cell_volume(G, i, j));
+    }
+    double val[1] = {m}, o[1];
+    if (reduce_last<1, OpMax>(val, partials, count, o) && threadIdx.x == 0) out[0] = o[0];
+}
+
+// out (device, 5 doubles): the diagnostics of the fields; enqueued on the grid's stream
+void diagnostics(mhd_grid_s* g, const double* vr, const double* vt, const double* vp, const double* br,
+                 const double* bt, const double* bp, double* out) {
+    const Dims d = g->d;
+    current_edges(g, br, bt, bp);
+    bt_harmonics(g, bt);
+    Vel v{vr, vt, vp, nullptr, 0.0, d.N};
+    const int blocks = grid_blocks(g, d.N, 8);
+    k_diag_sums<<<blocks, kThreads, 0, g->stream>>>(d, g->geo, v, g->bharm, br, bt, bp, g->er, g->et, g->ep,
+                                                    &g->ss->count, g->partials, out);
+    k_diag_divmax<<<blocks, kThreads, 0, g->stream>>>(d, g->geo, br, bt, bp, &g->ss->count, g->partials, out + 4);
+}
+
+// ------------------------------------------------------------------------------------------
 // v** = v + dlt (in place) and b = rho V v**
 // ------------------------------------------------------------------------------------------
 __global__ void k_vstar(Dims d, Geo G, double* __restrict__ vr, double* __restrict__ vt, double* __restrict__ vp,

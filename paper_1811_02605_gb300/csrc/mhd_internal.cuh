@@ -334,6 +334,8 @@ void induction(mhd_grid_s* g, const double* vr, const double* vt, const double* 
                const double* dlt, double dfac, double eta, const double* dt_dev, double dt_host,
                double* br, double* bt, double* bp);
 void vstar_rhs(mhd_grid_s* g, double* vr, double* vt, double* vp, const double* dlt, double* b);
+void diagnostics(mhd_grid_s* g, const double* vr, const double* vt, const double* vp, const double* br,
+                 const double* bt, const double* bp, double* out);
 int sts_stages(const mhd_grid_s* g, double nu, double dt);
 mhd_status_t res_solve(mhd_grid_s* g, const double* dt_dev, double eta, double* br, double* bt, double* bp,
                        const mhd_params_t* p, int* iters, double* relres);

@@ -208,3 +208,15 @@ extern "C" mhd_status_t pcg_solve(mhd_grid_t g, double alpha, int ncomp, const d
     k_set_alpha<<<1, 1, 0, g->stream>>>(g->ss, alpha);
     return solve(g, &g->ss->alpha_user, ncomp, b, x, x, p, iters, outer, relres);
 }
+
+extern "C" mhd_status_t mhd_diagnostics(mhd_grid_t g, const mhd_fields_t* f, double out[5]) {
+    if (!g) return MHD_ERR_ARG;
+    if (whole_grid(g, "mhd_diagnostics") != MHD_OK) return MHD_ERR_ARG;
+    if (!fields_ok(f, true) || !out) return set_error(g, MHD_ERR_ARG, "mhd_diagnostics: null pointer");
+    diagnostics(g, f->vr, f->vt, f->vp, f->br, f->bt, f->bp, g->slab_out);
+    if (cudaMemcpyAsync(g->h_alpha, g->slab_out, 5 * sizeof(double), cudaMemcpyDeviceToHost, g->stream) != cudaSuccess ||
+        cudaStreamSynchronize(g->stream) != cudaSuccess)
+        return check_cuda(g, "mhd_diagnostics");
+    for (int q = 0; q < 5; q++) out[q] = g->h_alpha[q];
+    return MHD_OK;
+}
