@@ -537,8 +537,23 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         ds = dev_state()
-        out = {k: torch.empty_like(v, device="cpu").pin_memory() for k, v in snap.items()}
+        # the caller's host buffers: page-locked, allocated here (as a user of the library would own
+        # them), holding the state at the start of the timed region
+        host = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in snap.items()}
+        for k in host:
+            host[k].copy_(snap[k])
+        out = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in snap.items()}
         f = P.make_fields(ds["br"], ds["bt"], ds["bp"], ds["vr"], ds["vt"], ds["vp"])
+        # copy bandwidth of one buffer before the timed region (a check on the host memory, reported)
+        torch.cuda.synchronize()
+        pa, pb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            ds["vp"].copy_(host["vp"], non_blocking=True)
+            pa.record(stream)
+            ds["vp"].copy_(host["vp"], non_blocking=True)
+            pb.record(stream)
+        stream.synchronize()
+        probe_gbs = host["vp"].numel() * 8 / (pa.elapsed_time(pb) * 1e6)
         prm = P.make_params(nu=w["nu"], eta=w["eta"], cfl=w["cfl"], tol=w["tol"])
         ke = max(1, args.steps)
         h2d = sum(t.numel() * 8 for t in snap.values())
@@ -552,7 +567,7 @@ def run_ours(args):
             a.record(stream)
             with torch.cuda.stream(stream):
                 for k in ds:
-                    ds[k].copy_(snap[k], non_blocking=True)
+                    ds[k].copy_(host[k], non_blocking=True)
             b_.record(stream)
             st_e, info_e = P.mhd_step(g, prm, f)
             c_.record(stream)
@@ -568,6 +583,7 @@ def run_ours(args):
         barrier()
         e2e = dict(value=round(maxr(e0.elapsed_time(e1) / ke), 3), unit="ms/step", h2d_bytes_per_step=h2d,
                    d2h_bytes_per_step=h2d, **{k: round(v, 3) for k, v in parts.items()},
+                   h2d_probe_gbs=round(probe_gbs, 1),
                    pcg_iters_per_step=sum(info_e["iters"]),
                    note="each step starts from the state at the start of the timed region (host copy); "
                         "step_ms is that step alone, so it differs from the timed steps' mean by the "

@@ -52,6 +52,8 @@ int prof_begin(mhd_grid_s* g, cudaStream_t st, int kernel) {
     if (!g->prof) return -1;
     if (g->prof_nslot >= mhd_grid_s::kProfSlots) {
         cudaStreamSynchronize(st);
+        if (g->side && st != g->side) cudaStreamSynchronize(g->side);   // slots recorded on the side stream
+        if (st != g->stream) cudaStreamSynchronize(g->stream);
         prof_flush(g);
     }
     const int s = g->prof_nslot++;
@@ -278,6 +280,10 @@ mhd_status_t create_grid(const mhd_grid_desc_t* desc, int i0, int i1, void* cuda
     cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
     g->graph_batch = 16;
     std::memset(g->iter_graph, 0, sizeof(g->iter_graph));
+    if (cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking) != cudaSuccess) g->side = nullptr;
+    for (int q = 0; q < 4; q++)
+        if (cudaEventCreateWithFlags(&g->side_ev[q], cudaEventDisableTiming) != cudaSuccess) g->side_ev[q] = nullptr;
+    cudaGetLastError();
 
     HostGeo h = slice_geo(hg, dg.nr, d.nt, i0, i1);
     HostEx hx = make_ex(h, d);
@@ -323,6 +329,9 @@ mhd_status_t create_grid(const mhd_grid_desc_t* desc, int i0, int i1, void* cuda
          dalloc(&g->sc, 1, owned) && dalloc(&g->ss, 1, owned);
     if (!ok) {
         for (void* m : owned) cudaFree(m);
+        if (g->side) cudaStreamDestroy(g->side);
+        for (auto& e : g->side_ev)
+            if (e) cudaEventDestroy(e);
         cudaGetLastError();
         delete g;
         return set_error(nullptr, MHD_ERR_OOM, "mhd_grid_create: device allocation failed");
@@ -331,6 +340,9 @@ mhd_status_t create_grid(const mhd_grid_desc_t* desc, int i0, int i1, void* cuda
         cudaMallocHost(&g->h_ss, sizeof(StepScalars)) != cudaSuccess ||
         cudaMallocHost(&g->h_alpha, 8 * sizeof(double)) != cudaSuccess) {
         for (void* m : owned) cudaFree(m);
+        if (g->side) cudaStreamDestroy(g->side);
+        for (auto& e : g->side_ev)
+            if (e) cudaEventDestroy(e);
         cudaGetLastError();
         delete g;
         return set_error(nullptr, MHD_ERR_OOM, "mhd_grid_create: pinned host allocation failed");
@@ -434,6 +446,9 @@ extern "C" mhd_status_t mhd_grid_destroy(mhd_grid_t g) {
     if (g->h_alpha) cudaFreeHost(g->h_alpha);
     if (g->prof_ev[0])
         for (auto& e : g->prof_ev) cudaEventDestroy(e);
+    if (g->side) cudaStreamDestroy(g->side);
+    for (auto& e : g->side_ev)
+        if (e) cudaEventDestroy(e);
     cudaGetLastError();
     delete g;
     return MHD_OK;

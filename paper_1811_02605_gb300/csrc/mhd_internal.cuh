@@ -37,6 +37,7 @@ struct PcgScalars {
     int par;         // FP32 tiled path: which of the two p buffers holds the current p
     double dte;      // implicit resistivity: dt eta of the current solve
     double ax;       // alpha of the last CG iteration whose alpha p~ has not yet been added to x~
+    double pqc[3];   // per-component shares of <p~, q~> (FP64 iteration with the components overlapped)
 };
 
 // Device-resident scalars of one step.
@@ -231,6 +232,8 @@ struct mhd_grid_s {
     mhd::Dims d;
     mhd_grid_desc_t desc;
     cudaStream_t stream;
+    cudaStream_t side;      // second stream of the FP64 iteration that overlaps the components
+    cudaEvent_t side_ev[4]; // its fork / join events (no timing)
     int device;
     int num_sms;
     // host copies of the metric tables
@@ -275,7 +278,8 @@ struct mhd_grid_s {
                             // p update folded into the stencil (-2), recompute pair (-3, -4 with the
                             // r update walking backwards), bulk-staged pair with units of L planes
                             // (-100 - L); 0: not tuned
-    int slab64;             // same for the FP64 fused p-update + stencil kernel
+    int slab64;             // same for the FP64 fused p-update + stencil kernel; -2: the split kernels
+                            // with each component's p update overlapping the previous one's stencil
     int pc2_fused32;        // FP32 PC2 iteration: p update folded into the stencil (1) or split (-1); 0: unset
     double visc_lambda_unit; // Gershgorin bound on the spectral radius of D^-1 K (nu = 1)
     std::string last_error;

@@ -259,6 +259,47 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 4) k_spmv_dot(D
     }
 }
 
+// A2 for one component c of the FP64 iteration whose components overlap: q_c = A~ p_c and the
+// component's share of <p, q> into sc->pqc[c] (the last component's last CTA also clears the
+// deferred x update: every component's p update has applied it by then)
+template <int V>
+__global__ void __launch_bounds__(kThreads, 3) k_spmv_dotc(Dims d, int c, int last, const double* __restrict__ p,
+                                                           double* __restrict__ q, OpTab<double> t, PcgScalars* sc,
+                                                           double* __restrict__ partials) {
+    if (sc->done) return;
+    const int nt = d.nt;
+    const unsigned int G = (unsigned int)(d.N / V);
+    double acc = 0.0;
+    const double* pc = p + c * d.N;
+    for (unsigned int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+        const Cell cl = decompose<V>(d, g);
+        const double cr_lo = t.ar[cl.i * nt + cl.j], cr_hi = t.ar[(cl.i + 1) * nt + cl.j];
+        const double ct_lo = t.at[cl.i * (nt + 1) + cl.j], ct_hi = t.at[cl.i * (nt + 1) + cl.j + 1];
+        const double cp = t.ap[cl.ij];
+        double v[V], o[V];
+        scaled_stencil<double, V>(d, cl, pc, cr_lo, cr_hi, ct_lo, ct_hi, cp, v, o);
+        stv<double, V>(q + c * d.N + cl.base, o);
+#pragma unroll
+        for (int e = 0; e < V; e++) acc = fma(v[e], o[e], acc);
+    }
+    double val[1] = {acc}, out[1];
+    if (reduce_last<1>(val, partials, &sc->count, out) && threadIdx.x == 0) {
+        sc->pqc[c] = out[0];
+        if (last) sc->ax = 0.0;
+    }
+}
+
+// <p, q> from the component shares, alpha = rho / <p, q> (one thread)
+__global__ void k_alpha_from_parts(PcgScalars* sc, int nc) {
+    if (sc->done) return;
+    double pq = 0.0;
+    for (int c = 0; c < nc; c++) pq += sc->pqc[c];
+    sc->pq = pq;
+    if (!finite(pq)) sc->done = 3;
+    else if (!(pq > 0.0)) sc->done = 4;
+    else sc->alpha = sc->rho / pq;
+}
+
 // A1+A2 for the FP32 inner iteration in one pass: p~ = r~ + beta p~_old is formed at the cell and,
 // from r~ and p~_old, at each of its six neighbours (the same fma as the p update kernel, so every
 // value equals the one its own thread stores); the cell's p~ goes to the other half of the p double
@@ -982,6 +1023,36 @@ void enqueue_split(mhd_grid_s* g, cudaStream_t st, T* x, T* r, T* p, T* q, const
     prof_end(g, st, s);
 }
 
+// FP64 iteration with the components overlapped: the stencil couples no components, so the HBM-bound
+// p update of component c+1 (side stream) runs while the FP64-bound stencil of component c runs
+// (grid stream); the stencils run at 3 CTAs per SM to leave the p update room on every SM. The
+// stencils stay in order on one stream (they share the reduction buffers); the update follows.
+template <int NC>
+void enqueue_split64_ov(mhd_grid_s* g, cudaStream_t st) {
+    const Dims d = g->d;
+    const int bp = grid_blocks(g, d.N / 2, kPerSmIter);
+    const int bs = grid_blocks(g, d.N / 2, 3);
+    cudaStream_t sd = g->side;
+    cudaEventRecord(g->side_ev[0], st);   // fork: the side stream follows everything before
+    cudaStreamWaitEvent(sd, g->side_ev[0], 0);
+    for (int c = 0; c < NC; c++) {
+        int s = prof_begin(g, sd, MHD_KERNEL_PUPDATE64);
+        k_pupdate<double, 2, 1, true><<<bp, kThreads, 0, sd>>>(d, g->r64 + c * d.N, g->p64 + c * d.N,
+                                                               g->x64 + c * d.N, g->sc);
+        prof_end(g, sd, s);
+        cudaEventRecord(g->side_ev[1 + c], sd);
+        cudaStreamWaitEvent(st, g->side_ev[1 + c], 0);   // the last wait also joins the side stream
+        s = prof_begin(g, st, MHD_KERNEL_SPMV64);
+        k_spmv_dotc<2><<<bs, kThreads, 0, st>>>(d, c, c == NC - 1 ? 1 : 0, g->p64, g->q64, g->t64, g->sc, g->partials);
+        prof_end(g, st, s);
+    }
+    k_alpha_from_parts<<<1, 1, 0, st>>>(g->sc, NC);
+    const int s = prof_begin(g, st, MHD_KERNEL_UPDATE64);
+    k_update<double, 2, NC, false, true><<<bp, kThreads, 0, st>>>(d, g->x64, g->p64, g->r64, g->q64, g->tu.dg, g->sc,
+                                                                  g->partials);
+    prof_end(g, st, s);
+}
+
 // FP32 inner iteration with the p update folded into the stencil (p~ double-buffered)
 template <int V, int NC>
 void enqueue_fused32(mhd_grid_s* g, cudaStream_t st) {
@@ -1124,6 +1195,10 @@ void enqueue_iteration(mhd_grid_s* g, cudaStream_t st, int prec, int nc) {
         if (nc == 3) enqueue_cg<3>(g, st, blocks);
         else if (nc == 2) enqueue_cg<2>(g, st, blocks);
         else enqueue_cg<1>(g, st, blocks);
+    } else if (prec == 0 && g->slab64 == -2 && g->side) {
+        if (nc == 3) enqueue_split64_ov<3>(g, st);
+        else if (nc == 2) enqueue_split64_ov<2>(g, st);
+        else enqueue_split64_ov<1>(g, st);
     } else if (prec == 0 && nc == 3 && tiled32_ok(g) && g->slab64 > 0) {
         // fused p update + stencil (p double-buffered), then the update reading the new p
         const int blocks = grid_blocks(g, d.N / 2, kPerSmIter);
@@ -1346,9 +1421,9 @@ namespace {
 // FP64: time the split iteration against the fused tiled kernel A at each slab length (alpha =
 // beta = 0 on positive finite vectors) and keep the fastest
 mhd_status_t tune_slab64(mhd_grid_s* g) {
-    if (!tiled32_ok(g) || g->slab64 != 0) return MHD_OK;
+    if (g->slab64 != 0) return MHD_OK;
     if (const int f = forced_slab()) {
-        g->slab64 = (f > 0 && tiled32_blocks(g, f) <= kMaxBlocks) ? f : -1;
+        g->slab64 = (f > 0 && tiled32_ok(g) && tiled32_blocks(g, f) <= kMaxBlocks) ? f : (f == -64 ? -2 : -1);
         return MHD_OK;
     }
     cudaEvent_t e0, e1;
@@ -1360,8 +1435,10 @@ mhd_status_t tune_slab64(mhd_grid_s* g) {
     cudaMemsetAsync(g->p64, 0x3F, sizeof(double) * 2 * n3, g->stream);
     int best = 0;
     float best_ms = 1e30f;
-    for (int slab : {-1, 8, 16, 32, 64}) {
-        if (slab > 0 && (tiled32_blocks(g, slab) > kMaxBlocks || (slab > 2 * g->d.nr && best != 0))) continue;
+    for (int slab : {-1, -2, 8, 16, 32, 64}) {
+        if (slab == -2 && !g->side) continue;
+        if (slab > 0 && (!tiled32_ok(g) || tiled32_blocks(g, slab) > kMaxBlocks || (slab > 2 * g->d.nr && best != 0)))
+            continue;
         g->slab64 = slab;
         k_tune_reset<<<1, 1, 0, g->stream>>>(g->sc);
         enqueue_iteration(g, g->stream, 0, 3);
