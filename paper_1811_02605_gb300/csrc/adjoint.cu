@@ -595,6 +595,7 @@ mhd_status_t adjoint_reserve(mhd_grid_s* g) {
 extern "C" mhd_status_t mhd_adjoint_step(mhd_grid_t g, const mhd_params_t* p, const mhd_fields_t* s0, double dt,
                                          const mhd_fields_t* a1, mhd_fields_t* a0) {
     if (!g) return MHD_ERR_ARG;
+    NvtxRange range("mhd_adjoint_step");
     if (g->slab_nr_global > 0) return set_error(g, MHD_ERR_ARG, "mhd_adjoint_step: not available on a slab grid");
     if (!p || !s0 || !a1 || !a0 || !(dt > 0.0)) return set_error(g, MHD_ERR_ARG, "mhd_adjoint_step: bad argument");
     if (p->precision != MHD_PREC_FP64 || !(p->tol > 0.0) || (p->viscosity_sts != 0 && p->viscosity_sts != 1) ||

@@ -632,6 +632,7 @@ extern "C" mhd_status_t pcg_solve_batched(int n, const mhd_grid_t* grids, const 
                                           const double* const* b, double* const* x,
                                           const mhd_params_t* params, int* iters, double* relres) {
     std::lock_guard<std::mutex> lk(g_mu);
+    NvtxRange range("pcg_solve_batched");
     Plan* pp = nullptr;
     mhd_status_t sp = prepare(n, grids, alpha, b, x, params, &pp);
     if (sp != MHD_OK) return sp;

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 #include <string>
@@ -384,6 +385,33 @@ void adjoint_free(mhd_grid_s* g);     // adjoint.cu: release the adjoint workspa
 int prof_begin(mhd_grid_s* g, cudaStream_t st, int kernel);
 void prof_end(mhd_grid_s* g, cudaStream_t st, int slot);
 void prof_flush(mhd_grid_s* g);   // after a stream sync: fold finished slots into the totals
+
+// NVTX ranges on the host timeline of a profiler (a function-pointer test when none is attached):
+// one named range per entry point, and `next` closes the current phase and opens the next one
+class NvtxRange {
+  public:
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+class NvtxPhase {
+  public:
+    NvtxPhase() = default;
+    void next(const char* name) {
+        if (open_) nvtxRangePop();
+        nvtxRangePushA(name);
+        open_ = true;
+    }
+    ~NvtxPhase() {
+        if (open_) nvtxRangePop();
+    }
+    NvtxPhase(const NvtxPhase&) = delete;
+    NvtxPhase& operator=(const NvtxPhase&) = delete;
+
+  private:
+    bool open_ = false;
+};
 mhd_status_t check_cuda(mhd_grid_s* g, const char* where);
 
 }  // namespace mhd

@@ -89,7 +89,10 @@ extern "C" mhd_status_t mhd_step(mhd_grid_t g, const mhd_params_t* p, mhd_fields
     if (!fields_ok(f, true)) return set_error(g, MHD_ERR_ARG, "mhd_step: null field pointer");
     const Dims d = g->d;
     const size_t bytes3 = sizeof(double) * 3 * (size_t)d.N;
+    NvtxRange range("mhd_step");
+    NvtxPhase phase;
     // 1. coefficients from (v^n, B^n)
+    phase.next("coefficients");
     int pc = prof_begin(g, g->stream, MHD_KERNEL_COEFFS);
     if ((st = coeffs(g, p, f->vr, f->vt, f->vp, f->br, f->bt, f->bp)) != MHD_OK) return st;
     prof_end(g, g->stream, pc);
@@ -100,6 +103,7 @@ extern "C" mhd_status_t mhd_step(mhd_grid_t g, const mhd_params_t* p, mhd_fields
     double rr[3] = {0, 0, 0};
     mhd_status_t worst = MHD_OK;
     // 2. predictor: M_SI d_p = rho V dt F(v^n, B^n), x0 = 0
+    phase.next("predictor");
     int ps = prof_begin(g, g->stream, MHD_KERNEL_FORCE);
     force(g, f->vr, f->vt, f->vp, nullptr, 0.0, f->br, f->bt, f->bp, dt_dev, 0.0, nullptr, g->b0);
     prof_end(g, g->stream, ps);
@@ -108,6 +112,7 @@ extern "C" mhd_status_t mhd_step(mhd_grid_t g, const mhd_params_t* p, mhd_fields
     if (st == MHD_ERR_CUDA) return st;
     if (st != MHD_OK && worst == MHD_OK) worst = st;
     // 3. B^{n+1} = B^n - dt curl_h E(v^n + d_p / 2, B^n)
+    phase.next("induction");
     int it_res = 0;
     double rr_res = 0.0;
     ps = prof_begin(g, g->stream, MHD_KERNEL_INDUCTION);
@@ -123,6 +128,7 @@ extern "C" mhd_status_t mhd_step(mhd_grid_t g, const mhd_params_t* p, mhd_fields
         if (st != MHD_OK && worst == MHD_OK) worst = st;
     }
     // 4. corrector: M_SI d_c = (b0 + rho V dt F(v^n + d_p, B^{n+1})) / 2, x0 = d_p
+    phase.next("corrector");
     ps = prof_begin(g, g->stream, MHD_KERNEL_FORCE);
     force(g, f->vr, f->vt, f->vp, g->dlt, 1.0, f->br, f->bt, f->bp, dt_dev, 0.0, g->b0, g->b1);
     prof_end(g, g->stream, ps);
@@ -130,6 +136,7 @@ extern "C" mhd_status_t mhd_step(mhd_grid_t g, const mhd_params_t* p, mhd_fields
     if (st == MHD_ERR_CUDA) return st;
     if (st != MHD_OK && worst == MHD_OK) worst = st;
     // 5. viscosity: M_nu v^{n+1} = rho V v**, x0 = v**  (v** is formed in the stacked buffer)
+    phase.next("viscosity");
     cudaMemcpyAsync(g->b1, f->vr, bytes3 / 3, cudaMemcpyDeviceToDevice, g->stream);
     cudaMemcpyAsync(g->b1 + d.N, f->vt, bytes3 / 3, cudaMemcpyDeviceToDevice, g->stream);
     cudaMemcpyAsync(g->b1 + 2 * d.N, f->vp, bytes3 / 3, cudaMemcpyDeviceToDevice, g->stream);
@@ -205,6 +212,7 @@ extern "C" mhd_status_t pcg_solve(mhd_grid_t g, double alpha, int ncomp, const d
     if (ncomp < 1 || ncomp > 3 || !b || !x || (const double*)x == b)
         return set_error(g, MHD_ERR_ARG, "pcg_solve: need 1 <= ncomp <= 3 and distinct non-null b, x");
     if (!(alpha >= 0.0)) return set_error(g, MHD_ERR_ARG, "pcg_solve: alpha must be >= 0");
+    NvtxRange range("pcg_solve");
     k_set_alpha<<<1, 1, 0, g->stream>>>(g->ss, alpha);
     return solve(g, &g->ss->alpha_user, ncomp, b, x, x, p, iters, outer, relres);
 }
