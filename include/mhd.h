@@ -123,6 +123,9 @@ enum { MHD_PREC_FP64 = 0, MHD_PREC_MIXED = 1 };
  * by timing on its first mixed solve; results agree to the order of one dot product's reduction.
  * Diagnostics only: the environment variable MHD_FORCE_SLAB skips the timing (-1 split, -2
  * folded, -3 recompute pair, -4 recompute pair with the second kernel walking the grid backwards,
+ * -5 recompute pair at 6 CTAs per SM, -6 / -7 the -3 / -4 pair with L2 prefetches of the next component,
+ * -64, -65, -66 the FP64 iteration with its components overlapped on two streams (the p updates
+ * launched for 4, 2 or 1 CTAs per SM),
  * n > 0 tiles of n planes). */
 typedef struct {
     double nu, eta, cfl, dt_fixed, dt_max, alpha_si_fixed;

@@ -230,13 +230,13 @@ HostGeo slice_geo(const HostGeo& a, int nr_global, int nt, int i0, int i1) {
     return h;
 }
 
-mhd_status_t create_grid(const mhd_grid_desc_t* desc, int i0, int i1, void* cuda_stream, mhd_grid_t* out);
+mhd_status_t create_grid(const mhd_grid_desc_t* desc, int i0, int i1, bool as_slab, void* cuda_stream, mhd_grid_t* out);
 
 }  // namespace
 
 extern "C" mhd_status_t mhd_grid_create(const mhd_grid_desc_t* desc, void* cuda_stream, mhd_grid_t* out) {
     if (!desc || !out) return set_error(nullptr, MHD_ERR_ARG, "mhd_grid_create: null argument");
-    return create_grid(desc, 0, desc->nr, cuda_stream, out);
+    return create_grid(desc, 0, desc->nr, false, cuda_stream, out);
 }
 
 extern "C" mhd_status_t mhd_grid_create_slab(const mhd_grid_desc_t* desc, int i0, int i1, void* cuda_stream,
@@ -244,18 +244,20 @@ extern "C" mhd_status_t mhd_grid_create_slab(const mhd_grid_desc_t* desc, int i0
     if (!desc || !out) return set_error(nullptr, MHD_ERR_ARG, "mhd_grid_create_slab: null argument");
     if (i0 < 0 || i1 > desc->nr || i1 - i0 < 2)
         return set_error(nullptr, MHD_ERR_ARG, "mhd_grid_create_slab: need 0 <= i0, i1 <= nr, i1 - i0 >= 2");
-    return create_grid(desc, i0, i1, cuda_stream, out);
+    return create_grid(desc, i0, i1, true, cuda_stream, out);
 }
 
 namespace {
-mhd_status_t create_grid(const mhd_grid_desc_t* desc, int i0, int i1, void* cuda_stream, mhd_grid_t* out) {
+mhd_status_t create_grid(const mhd_grid_desc_t* desc, int i0, int i1, bool as_slab, void* cuda_stream,
+                         mhd_grid_t* out) {
     *out = nullptr;
     const mhd_grid_desc_t dg = *desc;
     if (dg.nr < 2 || dg.nt < 2 || dg.np < 2 || (dg.np % 2) != 0)
         return set_error(nullptr, MHD_ERR_ARG, "mhd_grid_create: need nr>=2, nt>=2, np even >= 2");
     if (!(dg.r0 > 0) || !(dg.r1 > dg.r0) || !(dg.stretch > 0))
         return set_error(nullptr, MHD_ERR_ARG, "mhd_grid_create: need 0 < r0 < r1, stretch > 0");
-    const bool slab = !(i0 == 0 && i1 == dg.nr);
+    // a slab grid, even one holding every row (a decomposition over one rank), takes the slab calls
+    const bool slab = as_slab;
     // a slab is described by its own rows: nr = i1 - i0, r0 and r1 its first and last radial nodes
     const HostGeo hg = make_geo(dg);
     mhd_grid_desc_t d = dg;
