@@ -123,9 +123,8 @@ enum { MHD_PREC_FP64 = 0, MHD_PREC_MIXED = 1 };
  * by timing on its first mixed solve; results agree to the order of one dot product's reduction.
  * Diagnostics only: the environment variable MHD_FORCE_SLAB skips the timing (-1 split, -2
  * folded, -3 recompute pair, -4 recompute pair with the second kernel walking the grid backwards,
- * -5 recompute pair at 6 CTAs per SM, -6 / -7 the -3 / -4 pair with L2 prefetches of the next component,
- * -64, -65, -66 the FP64 iteration with its components overlapped on two streams (the p updates
- * launched for 4, 2 or 1 CTAs per SM),
+ * -5 recompute pair at 6 CTAs per SM, -64 the FP64 iteration with its components overlapped on two
+ * streams,
  * n > 0 tiles of n planes). */
 typedef struct {
     double nu, eta, cfl, dt_fixed, dt_max, alpha_si_fixed;
@@ -339,6 +338,11 @@ mhd_status_t mhd_profile_enable(mhd_grid_t grid, int enable);
 /* Total milliseconds and launch count of one kernel id since profiling was enabled.
  * Synchronises the grid's stream. */
 mhd_status_t mhd_profile_read(mhd_grid_t grid, int kernel, double* total_ms, long long* launches);
+/* The kernel forms the grid's autotuner chose, in the codes of MHD_FORCE_SLAB: *fp64_form for the
+ * FP64 iteration (-1 split, -2 components overlapped, n > 0 tiles of n planes) and *fp32_form for
+ * the FP32 inner iteration (-1 split, -2 folded, -3/-4/-5 recompute pair, <= -100 bulk-staged pair,
+ * n > 0 tiles); 0 where that precision has not been tuned yet. Either pointer may be NULL. */
+mhd_status_t mhd_grid_kernel_forms(mhd_grid_t grid, int* fp64_form, int* fp32_form);
 
 /* Text of the last error on this grid ("" if none); NULL grid gives the last create error. */
 const char* mhd_last_error(mhd_grid_t grid);

@@ -31,7 +31,7 @@ SYMBOLS = ["mhd_grid_create", "mhd_grid_destroy", "mhd_grid_sizes", "mhd_step_co
            "mhd_apply_operator", "mhd_force", "mhd_induction", "pcg_solve", "pcg_solve_batched",
            "mhd_adjoint_step", "mhd_force_noalloc", "mhd_grid_reserve", "pcg_batch_reserve",
            "mhd_grid_create_slab", "mhd_slab_apply", "mhd_slab_update", "mhd_slab_pupdate", "mhd_diagnostics",
-           "mhd_profile_enable", "mhd_profile_read", "mhd_last_error"]
+           "mhd_profile_enable", "mhd_profile_read", "mhd_grid_kernel_forms", "mhd_last_error"]
 
 KERNELS = ["pupdate64", "spmv64", "update64", "pupdate32", "spmv32", "update32", "outer_res", "force",
            "induction", "coeffs", "sts", "res", "pc2", "pspmv32", "pfold32", "rupd32"]
@@ -113,6 +113,7 @@ def lib():
                                             C.POINTER(Params)]
             L.mhd_profile_enable.argtypes = [vp, i]
             L.mhd_profile_read.argtypes = [vp, i, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
+            L.mhd_grid_kernel_forms.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
             L.mhd_last_error.argtypes = [vp]
             L.mhd_last_error.restype = C.c_char_p
             for name in SYMBOLS:
@@ -341,6 +342,13 @@ def mhd_profile_read(grid: Grid) -> dict:
         _check(lib().mhd_profile_read(grid.handle, k, C.byref(ms), C.byref(n)), grid)
         out[name] = (ms.value, n.value)
     return out
+
+
+def mhd_grid_kernel_forms(grid: Grid) -> tuple[int, int]:
+    """(fp64_form, fp32_form): the autotuner's choices in the codes of MHD_FORCE_SLAB (0: not tuned)."""
+    a, b = C.c_int(0), C.c_int(0)
+    _check(lib().mhd_grid_kernel_forms(grid.handle, C.byref(a), C.byref(b)), grid)
+    return a.value, b.value
 
 
 def mhd_force_noalloc(desc: GridDesc, fields: Fields, dt: float, b, stream=None):

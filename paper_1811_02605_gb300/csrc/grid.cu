@@ -491,6 +491,13 @@ extern "C" mhd_status_t mhd_profile_read(mhd_grid_t g, int kernel, double* total
     return MHD_OK;
 }
 
+extern "C" mhd_status_t mhd_grid_kernel_forms(mhd_grid_t g, int* fp64_form, int* fp32_form) {
+    if (!g) return MHD_ERR_ARG;
+    if (fp64_form) *fp64_form = g->slab64;
+    if (fp32_form) *fp32_form = g->slab32;
+    return MHD_OK;
+}
+
 extern "C" const char* mhd_last_error(mhd_grid_t g) {
     if (g) return g->last_error.c_str();
     std::lock_guard<std::mutex> lk(g_err_mu);

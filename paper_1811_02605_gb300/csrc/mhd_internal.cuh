@@ -279,9 +279,8 @@ struct mhd_grid_s {
                             // p update folded into the stencil (-2), recompute pair (-3, -4 with the
                             // r update walking backwards), bulk-staged pair with units of L planes
                             // (-100 - L); 0: not tuned
-    int slab64;             // same for the FP64 fused p-update + stencil kernel; -2, -3, -4: the split
-                            // kernels with each component's p update (4, 2 or 1 CTAs per SM) overlapping
-                            // the previous component's stencil
+    int slab64;             // same for the FP64 fused p-update + stencil kernel; -2: the split kernels
+                            // with each component's p update overlapping the previous component's stencil
     int pc2_fused32;        // FP32 PC2 iteration: p update folded into the stencil (1) or split (-1); 0: unset
     double visc_lambda_unit; // Gershgorin bound on the spectral radius of D^-1 K (nu = 1)
     std::string last_error;

@@ -423,12 +423,7 @@ struct Nbr {
     }
 };
 
-// L2 prefetch of the line holding addr (a hint: no register is written, nothing waits on it)
-__device__ __forceinline__ void prefetch_l2(const void* addr) {
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(addr));
-}
-
-template <int V, int NC, int MINB, bool PF = false>
+template <int V, int NC, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB) k_pfold32(Dims d, const float* __restrict__ r,
                                                             float* __restrict__ pbuf, OpTab<float> t,
                                                             PcgScalars* sc, double* __restrict__ partials) {
@@ -453,18 +448,6 @@ __global__ void __launch_bounds__(kThreads, MINB) k_pfold32(Dims d, const float*
         for (int k = 0; k < NC; k++) {
             const float* rk = r + k * d.N;
             const float* pk = pold + k * d.N;
-            if constexpr (PF) {
-                // the centre lines of the next component (or of the next cell's first one) start
-                // their way from DRAM while this component's loads and arithmetic run
-                const unsigned int gs = gridDim.x * blockDim.x;
-                if (k + 1 < NC) {
-                    prefetch_l2(rk + d.N + c.base);
-                    prefetch_l2(pk + d.N + c.base);
-                } else if (g + gs < G) {
-                    prefetch_l2(r + (long long)(g + gs) * V);
-                    prefetch_l2(pold + (long long)(g + gs) * V);
-                }
-            }
             float rv[V], pv[V], v[V], o[V], a0[V], a1[V], b0[V], b1[V], c0[V], c1[V], e0[V], e1[V];
             ldv<float, V>(rk + c.base, rv);
             ldv<float, V>(pk + c.base, pv);
@@ -507,7 +490,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_pfold32(Dims d, const float*
     }
 }
 
-template <int V, int NC, bool REV, int MINB, bool PF = false>
+template <int V, int NC, bool REV, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB) k_rupd32(Dims d, float* __restrict__ x, float* __restrict__ r,
                                                            const float* __restrict__ pbuf, OpTab<float> t,
                                                            const double* __restrict__ dg, PcgScalars* sc,
@@ -538,25 +521,6 @@ __global__ void __launch_bounds__(kThreads, MINB) k_rupd32(Dims d, float* __rest
 #pragma unroll 1
         for (int k = 0; k < NC; k++) {
             const float* pk = p + k * d.N;
-            if constexpr (PF) {
-                const unsigned int gs = gridDim.x * blockDim.x;
-                if (k + 1 < NC) {
-                    prefetch_l2(pk + d.N + c.base);
-                    prefetch_l2(r + (k + 1) * d.N + c.base);
-                    if (pair) {
-                        prefetch_l2(x + (k + 1) * d.N + c.base);
-                        prefetch_l2(pprev + (k + 1) * d.N + c.base);
-                    }
-                } else if (g0 + gs < G) {
-                    const long long nb0 = (long long)(REV ? G - 1u - (g0 + gs) : g0 + gs) * V;
-                    prefetch_l2(p + nb0);
-                    prefetch_l2(r + nb0);
-                    if (pair) {
-                        prefetch_l2(x + nb0);
-                        prefetch_l2(pprev + nb0);
-                    }
-                }
-            }
             float v[V], o[V], rv[V], a[V], b[V], cc[V], e4[V];
             ldv<float, V>(pk + c.base, v);
             const float ukm = pk[row + km], ukp = pk[row + kp];
@@ -1106,39 +1070,38 @@ void enqueue_fused32(mhd_grid_s* g, cudaStream_t st) {
 
 // FP32 inner iteration by the recompute pair (no q~ stored; x~ updated every second iteration); MINB:
 // CTAs per SM the kernels are compiled for (registers per thread 65536 / (256 MINB))
-template <int V, int NC, int MINB, bool PF>
+template <int V, int NC, int MINB>
 void enqueue_recompute32(mhd_grid_s* g, cudaStream_t st, bool rev) {
     const Dims d = g->d;
     int s = prof_begin(g, st, MHD_KERNEL_PFOLD32);
-    k_pfold32<V, NC, MINB, PF><<<grid_blocks(g, d.N / V, resident_per_sm<k_pfold32<V, NC, MINB, PF>>()), kThreads, 0,
-                                 st>>>(d, g->r32, g->p32, g->t32, g->sc, g->partials);
+    k_pfold32<V, NC, MINB><<<grid_blocks(g, d.N / V, resident_per_sm<k_pfold32<V, NC, MINB>>()), kThreads, 0, st>>>(
+        d, g->r32, g->p32, g->t32, g->sc, g->partials);
     prof_end(g, st, s);
     s = prof_begin(g, st, MHD_KERNEL_RUPD32);
     if (rev)
-        k_rupd32<V, NC, true, MINB, PF><<<grid_blocks(g, d.N / V, resident_per_sm<k_rupd32<V, NC, true, MINB, PF>>()),
-                                          kThreads, 0, st>>>(d, g->x32, g->r32, g->p32, g->t32, g->tu.dg, g->sc,
-                                                             g->partials);
+        k_rupd32<V, NC, true, MINB><<<grid_blocks(g, d.N / V, resident_per_sm<k_rupd32<V, NC, true, MINB>>()), kThreads,
+                                      0, st>>>(d, g->x32, g->r32, g->p32, g->t32, g->tu.dg, g->sc, g->partials);
     else
-        k_rupd32<V, NC, false, MINB, PF><<<grid_blocks(g, d.N / V, resident_per_sm<k_rupd32<V, NC, false, MINB, PF>>()),
-                                           kThreads, 0, st>>>(d, g->x32, g->r32, g->p32, g->t32, g->tu.dg, g->sc,
-                                                              g->partials);
+        k_rupd32<V, NC, false, MINB><<<grid_blocks(g, d.N / V, resident_per_sm<k_rupd32<V, NC, false, MINB>>()),
+                                       kThreads, 0, st>>>(d, g->x32, g->r32, g->p32, g->t32, g->tu.dg, g->sc,
+                                                          g->partials);
     prof_end(g, st, s);
 }
 
-template <int V, int MINB, bool PF>
+template <int V, int MINB>
 void enqueue_recompute32_nc(mhd_grid_s* g, cudaStream_t st, int nc, bool rev) {
-    if (nc == 3) enqueue_recompute32<V, 3, MINB, PF>(g, st, rev);
-    else if (nc == 2) enqueue_recompute32<V, 2, MINB, PF>(g, st, rev);
-    else enqueue_recompute32<V, 1, MINB, PF>(g, st, rev);
+    if (nc == 3) enqueue_recompute32<V, 3, MINB>(g, st, rev);
+    else if (nc == 2) enqueue_recompute32<V, 2, MINB>(g, st, rev);
+    else enqueue_recompute32<V, 1, MINB>(g, st, rev);
 }
 
-// -3 / -4: 4 CTAs per SM (64 registers); -5: 6 CTAs per SM (40 registers), forwards; -6 / -7: -3 / -4
-// with L2 prefetches of the next component's centre lines
+// -3 / -4: 4 CTAs per SM (64 registers); -5: 6 CTAs per SM (40 registers), forwards. (L2 prefetches
+// of the next component's centre lines were measured slower: 0.421 against 0.279 ms for the first
+// kernel at 256x256x512.)
 template <int V>
 void enqueue_recompute32_var(mhd_grid_s* g, cudaStream_t st, int nc) {
-    if (g->slab32 == -5) enqueue_recompute32_nc<V, 6, false>(g, st, nc, false);
-    else if (g->slab32 == -6 || g->slab32 == -7) enqueue_recompute32_nc<V, 4, true>(g, st, nc, g->slab32 == -7);
-    else enqueue_recompute32_nc<V, 4, false>(g, st, nc, g->slab32 == -4);
+    if (g->slab32 == -5) enqueue_recompute32_nc<V, 6>(g, st, nc, false);
+    else enqueue_recompute32_nc<V, 4>(g, st, nc, g->slab32 == -4);
 }
 
 template <int V>
@@ -1234,12 +1197,12 @@ void enqueue_iteration(mhd_grid_s* g, cudaStream_t st, int prec, int nc) {
         if (nc == 3) enqueue_cg<3>(g, st, blocks);
         else if (nc == 2) enqueue_cg<2>(g, st, blocks);
         else enqueue_cg<1>(g, st, blocks);
-    } else if (prec == 0 && g->slab64 <= -2 && g->slab64 >= -4 && g->side) {
-        // components overlapped; -2, -3, -4: the p updates launched for 4, 2 or 1 CTAs per SM
-        const int pps = (g->slab64 == -2) ? 4 : (g->slab64 == -3 ? 2 : 1);
-        if (nc == 3) enqueue_split64_ov<3>(g, st, pps);
-        else if (nc == 2) enqueue_split64_ov<2>(g, st, pps);
-        else enqueue_split64_ov<1>(g, st, pps);
+    } else if (prec == 0 && g->slab64 == -2 && g->side) {
+        // components overlapped (p updates launched for 4 CTAs per SM; 2 and 1 were measured
+        // slower, 2.355 and 2.603 against 2.182 ms per iteration at 256x256x512)
+        if (nc == 3) enqueue_split64_ov<3>(g, st, kPerSmIter);
+        else if (nc == 2) enqueue_split64_ov<2>(g, st, kPerSmIter);
+        else enqueue_split64_ov<1>(g, st, kPerSmIter);
     } else if (prec == 0 && nc == 3 && tiled32_ok(g) && g->slab64 > 0) {
         // fused p update + stencil (p double-buffered), then the update reading the new p
         const int blocks = grid_blocks(g, d.N / 2, kPerSmIter);
@@ -1254,7 +1217,7 @@ void enqueue_iteration(mhd_grid_s* g, cudaStream_t st, int prec, int nc) {
     } else if (g->slab32 <= -100) {
         // plane-marching pair with bulk-copy staging, when the autotuner measured it fastest
         enqueue_bulk32(g, st, nc, -100 - g->slab32);
-    } else if (g->slab32 <= -3 && g->slab32 >= -7) {
+    } else if (g->slab32 <= -3 && g->slab32 >= -5) {
         // recompute pair, when the autotuner measured it fastest (-4: the r update walks backwards,
         // -5: compiled for 6 CTAs per SM)
         if (use_v4(g)) enqueue_recompute32_var<4>(g, st, nc);
@@ -1391,7 +1354,7 @@ int forced_slab() {
 mhd_status_t tune_slab32(mhd_grid_s* g, int nc) {
     if (g->slab32 != 0) return MHD_OK;
     if (const int f = forced_slab()) {
-        if (f <= -2 && f >= -7) g->slab32 = f;
+        if (f <= -2 && f >= -5) g->slab32 = f;
         else if (f <= -100) g->slab32 = (bulk32_ok(g) && f < -100) ? f : -1;
         else g->slab32 = (f > 0 && tiled32_ok(g) && tiled32_blocks(g, f) <= kMaxBlocks) ? f : -1;
         return MHD_OK;
@@ -1407,11 +1370,10 @@ mhd_status_t tune_slab32(mhd_grid_s* g, int nc) {
     const size_t n3 = 3 * (size_t)g->d.N;
     // candidates -1: the split kernels (p update, stencil, update); -2: the p update folded into
     // the stencil, then the update; -3, -4, -5: the recompute pair (no q~ stored), forwards, with
-    // the r update walking backwards, or at 6 CTAs per SM; -6, -7: -3, -4 with L2 prefetches of
-    // the next component; -132, -164: the same pair as plane-marching kernels staged by bulk
-    // copies (units of 32 or 64 planes). Four iterations each after one untimed: an even count,
-    // so each is timed with its x updates.
-    for (int cand : {-1, -2, -3, -4, -5, -6, -7, -132, -164}) {
+    // the r update walking backwards, or at 6 CTAs per SM; -132, -164: the same pair as
+    // plane-marching kernels staged by bulk copies (units of 32 or 64 planes). Four iterations
+    // each after one untimed: an even count, so each is timed with its x updates.
+    for (int cand : {-1, -2, -3, -4, -5, -132, -164}) {
         if (cand <= -100 && !bulk32_ok(g)) continue;
         k_tune_reset<<<1, 1, 0, g->stream>>>(g->sc);
         g->slab32 = cand;
@@ -1465,9 +1427,7 @@ namespace {
 mhd_status_t tune_slab64(mhd_grid_s* g) {
     if (g->slab64 != 0) return MHD_OK;
     if (const int f = forced_slab()) {
-        g->slab64 = (f > 0 && tiled32_ok(g) && tiled32_blocks(g, f) <= kMaxBlocks) ? f
-                    : (f <= -64 && f >= -66) ? -2 - (-64 - f)
-                                             : -1;
+        g->slab64 = (f > 0 && tiled32_ok(g) && tiled32_blocks(g, f) <= kMaxBlocks) ? f : (f == -64 ? -2 : -1);
         return MHD_OK;
     }
     cudaEvent_t e0, e1;
@@ -1479,8 +1439,8 @@ mhd_status_t tune_slab64(mhd_grid_s* g) {
     cudaMemsetAsync(g->p64, 0x3F, sizeof(double) * 2 * n3, g->stream);
     int best = 0;
     float best_ms = 1e30f;
-    for (int slab : {-1, -2, -3, -4, 8, 16, 32, 64}) {
-        if (slab < -1 && !g->side) continue;
+    for (int slab : {-1, -2, 8, 16, 32, 64}) {
+        if (slab == -2 && !g->side) continue;
         if (slab > 0 && (!tiled32_ok(g) || tiled32_blocks(g, slab) > kMaxBlocks || (slab > 2 * g->d.nr && best != 0)))
             continue;
         g->slab64 = slab;
