@@ -427,21 +427,23 @@ def run_ours(args):
     def mixed_entry(inner_tol, restart):
         msm, infosm, profm, clkm, dsm = run(P.PREC_MIXED, args.steps, args.warmup, True, inner_tol, restart)
         msm = maxr(msm)
-        pcg32_ms = sum(profm[k][0] for k in ("pupdate32", "spmv32", "update32", "pspmv32", "pfold32", "rupd32"))
+        pcg32_ms = sum(profm[k][0] for k in ("pupdate32", "spmv32", "update32", "pspmv32", "pfold32", "rupd32",
+                                              "cgr32", "cgu32"))
         pcg32_n = max(sum(sum(i["iters"]) for i in infosm), 1)   # inner CG iterations actually run
         pcg32_gbs = PCG_BYTES_PER_CELL["fp32"] * N * pcg32_n / (pcg32_ms * 1e-3) / 1e9
         fused = profm["pspmv32"][1] > 0
-        recompute = profm["pfold32"][1] > 0
+        recompute = profm["pfold32"][1] > 0 or profm["cgr32"][1] > 0
         tiled = not fused and not recompute and profm["pupdate32"][1] == 0
         # per-kernel DRAM passes of a 3-component FP32 vector (4 B x 3 per cell per pass)
         # split form: the p update also adds the previous alpha p to x (r, p, x in; p, x out) and the
         # update kernel reads r, q and writes r; fused form: r, p, x in, p, x, q out, then the update;
         # recompute pair: r, p_old in, p out; then p, r in, r out, and every second iteration x,
-        # p_prev in, x out (4.5 on average)
+        # p_prev in, x out (4.5 on average); single-reduction pair: r in; then r, p_old in, p, r out,
+        # and every second iteration x in and out (5 on average)
         kb = {"spmv32": 3 if tiled else 2, "update32": 5 if tiled else 3, "pupdate32": 5, "pspmv32": 6,
-              "pfold32": 3, "rupd32": 4.5}
+              "pfold32": 3, "rupd32": 4.5, "cgr32": 1, "cgu32": 5}
         kernels = {}
-        for k in ("pupdate32", "spmv32", "pspmv32", "update32", "pfold32", "rupd32"):
+        for k in ("pupdate32", "spmv32", "pspmv32", "update32", "pfold32", "rupd32", "cgr32", "cgu32"):
             ms_k, n_k = profm[k]
             if n_k:
                 avg = ms_k / pcg32_n   # one launch per inner iteration that ran

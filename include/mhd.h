@@ -123,7 +123,7 @@ enum { MHD_PREC_FP64 = 0, MHD_PREC_MIXED = 1 };
  * by timing on its first mixed solve; results agree to the order of one dot product's reduction.
  * Diagnostics only: the environment variable MHD_FORCE_SLAB skips the timing (-1 split, -2
  * folded, -3 recompute pair, -4 recompute pair with the second kernel walking the grid backwards,
- * -5 recompute pair at 6 CTAs per SM, -64 the FP64 iteration with its components overlapped on two
+ * -5 recompute pair at 6 CTAs per SM, -6 single-reduction pair, -64 the FP64 iteration with its components overlapped on two
  * streams,
  * n > 0 tiles of n planes). */
 typedef struct {
@@ -332,7 +332,9 @@ enum {
     MHD_KERNEL_PSPMV32 = 13, /* FP32 p update folded into the stencil */
     MHD_KERNEL_PFOLD32 = 14, /* FP32 p update folded into <p, A p>, no q stored */
     MHD_KERNEL_RUPD32 = 15,  /* FP32 r update with A p recomputed, x every second iteration */
-    MHD_KERNEL_COUNT = 16
+    MHD_KERNEL_CGR32 = 16,   /* FP32 single-reduction pair: <r, r>, <r, A r> and the scalars */
+    MHD_KERNEL_CGU32 = 17,   /* FP32 single-reduction pair: p, A p, r and x updates */
+    MHD_KERNEL_COUNT = 18
 };
 mhd_status_t mhd_profile_enable(mhd_grid_t grid, int enable);
 /* Total milliseconds and launch count of one kernel id since profiling was enabled.

@@ -34,7 +34,7 @@ SYMBOLS = ["mhd_grid_create", "mhd_grid_destroy", "mhd_grid_sizes", "mhd_step_co
            "mhd_profile_enable", "mhd_profile_read", "mhd_grid_kernel_forms", "mhd_last_error"]
 
 KERNELS = ["pupdate64", "spmv64", "update64", "pupdate32", "spmv32", "update32", "outer_res", "force",
-           "induction", "coeffs", "sts", "res", "pc2", "pspmv32", "pfold32", "rupd32"]
+           "induction", "coeffs", "sts", "res", "pc2", "pspmv32", "pfold32", "rupd32", "cgr32", "cgu32"]
 
 
 class GridDesc(C.Structure):

@@ -639,6 +639,176 @@ __global__ void __launch_bounds__(kThreads) k_update(Dims d, T* __restrict__ x,
 }
 
 // ------------------------------------------------------------------------------------------
+// FP32 single-reduction pair (Chronopoulos-Gear scalars, nothing but p, r and x stored)
+// ------------------------------------------------------------------------------------------
+// The Chronopoulos-Gear recurrence needs one reduction per iteration: from gamma = <r~, r~> and
+// delta = <r~, A~ r~> of the current residual, beta = gamma / gamma_prev and
+// alpha = gamma / (delta - beta gamma / alpha_prev), the denominator being <p~, A~ p~> of the
+// Hestenes-Stiefel form in exact arithmetic. Instead of carrying s = A~ p~ as a stored
+// recurrence, the update kernel forms p~ = r~ + beta p~_old at the cell and its six neighbours
+// and applies A~ there, so an iteration moves r~ in (residual kernel), r~ and p~_old in, p~ and
+// r~ out (update kernel) and x~ in and out every second iteration: 6 vector passes, the
+// algorithmic minimum. r~ is double-buffered with the q~ workspace (the update reads r~ at its
+// neighbours while it writes the new r~), on the same parity as p~.
+//
+// R (k_cgr32): w = A~ r~ at the cell; gamma, delta and sum dg r~^2. Its last CTA first books the
+// update kernel that ran before it (parity flip, deferred alpha p~, iteration count), then takes
+// the stop test and forms beta and alpha for the next update (after a residual replacement,
+// iter = 0, beta is the one the replacement chose).
+template <int V, int NC>
+__global__ void __launch_bounds__(kThreads, 4) k_cgr32(Dims d, const float* __restrict__ ra,
+                                                       const float* __restrict__ rb, OpTab<float> t,
+                                                       const double* __restrict__ dg, PcgScalars* sc,
+                                                       double* __restrict__ partials) {
+    if (sc->done) return;
+    const float* __restrict__ r = (sc->pend ? 1 - sc->par : sc->par) ? rb : ra;
+    const int nt = d.nt;
+    const unsigned int G = (unsigned int)(d.N / V);
+    Acc<float> a_g, a_d;
+    double a_rr = 0.0;
+    for (unsigned int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+        const Cell c = decompose<V>(d, g);
+        const Nbr<V> nb(d, c);
+        const float cr_lo = t.ar[c.i * nt + c.j], cr_hi = t.ar[(c.i + 1) * nt + c.j];
+        const float ct_lo = t.at[c.i * (nt + 1) + c.j], ct_hi = t.at[c.i * (nt + 1) + c.j + 1];
+        const float cp = t.ap[c.ij];
+        const long long row = c.base - c.k0;
+        const int km = (c.k0 == 0) ? d.np - 1 : c.k0 - 1;
+        const int kp = (c.k0 + V == d.np) ? 0 : c.k0 + V;
+        float rs[V];
+        zerov<float, V>(rs);
+#pragma unroll 1
+        for (int k = 0; k < NC; k++) {
+            const float* rk = r + k * d.N;
+            float v[V], o[V], a[V], b[V], cc[V], e4[V];
+            ldv<float, V>(rk + c.base, v);
+            const float ukm = rk[row + km], ukp = rk[row + kp];
+            ldv<float, V>(rk + c.base + nb.im, a);
+            ldv<float, V>(rk + c.base + nb.ip, b);
+            ldv<float, V>(rk + c.base + nb.jm, cc);
+            ldv<float, V>(rk + c.base + nb.jp, e4);
+#pragma unroll
+            for (int e = 0; e < V; e++) {
+                const float left = (e == 0) ? ukm : v[e - 1];
+                const float right = (e == V - 1) ? ukp : v[e + 1];
+                o[e] = fmaf(-cp, left + right, v[e]);
+                o[e] = fmaf(-cr_lo, a[e], o[e]);
+                o[e] = fmaf(-cr_hi, b[e], o[e]);
+                o[e] = fmaf(-ct_lo, cc[e], o[e]);
+                o[e] = fmaf(-ct_hi, e4[e], o[e]);
+                rs[e] = fmaf(v[e], v[e], rs[e]);
+                a_d.fma_add(v[e], o[e]);
+            }
+        }
+        float cell = rs[0];
+#pragma unroll
+        for (int e = 1; e < V; e++) cell += rs[e];
+        a_g.add(cell);
+        a_rr = fma(dg[c.ij], (double)cell, a_rr);
+    }
+    double val[3] = {a_g.get(), a_d.get(), a_rr}, out[3];
+    if (reduce_last<3>(val, partials, &sc->count, out) && threadIdx.x == 0) {
+        if (sc->pend) {   // the update kernel since the last residual kernel
+            sc->par = 1 - sc->par;
+            sc->ax = (sc->ax != 0.0) ? 0.0 : sc->alpha;
+            sc->iter += 1;
+            sc->total_iter += 1;
+            sc->pend = 0;
+        }
+        const double gam = out[0], del = out[1], rr = out[2];
+        const double beta = (sc->iter == 0) ? sc->beta : gam / sc->rho;
+        sc->rho_prev = sc->rho;
+        sc->rho = gam;
+        sc->rr = rr;
+        if (!finite(gam) || !finite(del) || !finite(rr)) sc->done = 3;
+        else if (sqrt(rr) <= sc->tol * sqrt(sc->bb)) sc->done = 1;
+        else if (sc->iter >= sc->max_iter) sc->done = 2;
+        else {
+            const double den = (beta == 0.0) ? del : del - beta * gam / sc->alpha;
+            if (!finite(den)) sc->done = 3;
+            else if (!(den > 0.0)) sc->done = 4;
+            else {
+                sc->beta = beta;
+                sc->pq = den;
+                sc->alpha = gam / den;
+                sc->pend = 1;
+            }
+        }
+    }
+}
+
+// U (k_cgu32): p~ = r~ + beta p~_old at the cell and its neighbours, q~ = A~ p~ at the cell,
+// r~ -= alpha q~ into the other r~ half, p~ into the other p~ half; x~ += alpha p~ + ax p~_old every
+// second iteration (p~_old is at hand: the pending update is always the previous p~). No
+// reduction: the next residual kernel books this one.
+template <int V, int NC>
+__global__ void __launch_bounds__(kThreads, 4) k_cgu32(Dims d, float* __restrict__ x, float* __restrict__ ra,
+                                                       float* __restrict__ rb, float* __restrict__ pbuf,
+                                                       OpTab<float> t, const PcgScalars* sc) {
+    if (sc->done || !sc->pend) return;
+    const int par = sc->par;
+    const float* __restrict__ r = par ? rb : ra;
+    float* __restrict__ rn = par ? ra : rb;
+    const float* __restrict__ pold = pbuf + (long long)par * 3 * d.N;
+    float* __restrict__ pnew = pbuf + (long long)(1 - par) * 3 * d.N;
+    const float beta = (float)sc->beta, al = (float)sc->alpha, axp = (float)sc->ax;
+    const bool pair = (sc->ax != 0.0);
+    const int nt = d.nt;
+    const unsigned int G = (unsigned int)(d.N / V);
+    for (unsigned int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+        const Cell c = decompose<V>(d, g);
+        const Nbr<V> nb(d, c);
+        const float cr_lo = t.ar[c.i * nt + c.j], cr_hi = t.ar[(c.i + 1) * nt + c.j];
+        const float ct_lo = t.at[c.i * (nt + 1) + c.j], ct_hi = t.at[c.i * (nt + 1) + c.j + 1];
+        const float cp = t.ap[c.ij];
+        const long long row = c.base - c.k0;
+        const int km = (c.k0 == 0) ? d.np - 1 : c.k0 - 1;
+        const int kp = (c.k0 + V == d.np) ? 0 : c.k0 + V;
+#pragma unroll 1
+        for (int k = 0; k < NC; k++) {
+            const float* rk = r + k * d.N;
+            const float* pk = pold + k * d.N;
+            float rv[V], pv[V], v[V], o[V], a0[V], a1[V], b0[V], b1[V], c0[V], c1[V], e0[V], e1[V];
+            ldv<float, V>(rk + c.base, rv);
+            ldv<float, V>(pk + c.base, pv);
+            const float rkm = rk[row + km], pkm = pk[row + km], rkp = rk[row + kp], pkp = pk[row + kp];
+            ldv<float, V>(rk + c.base + nb.im, a0);
+            ldv<float, V>(pk + c.base + nb.im, a1);
+            ldv<float, V>(rk + c.base + nb.ip, b0);
+            ldv<float, V>(pk + c.base + nb.ip, b1);
+            ldv<float, V>(rk + c.base + nb.jm, c0);
+            ldv<float, V>(pk + c.base + nb.jm, c1);
+            ldv<float, V>(rk + c.base + nb.jp, e0);
+            ldv<float, V>(pk + c.base + nb.jp, e1);
+#pragma unroll
+            for (int e = 0; e < V; e++) v[e] = fmaf(beta, pv[e], rv[e]);
+            stv<float, V>(pnew + k * d.N + c.base, v);
+            const float ukm = fmaf(beta, pkm, rkm);
+            const float ukp = fmaf(beta, pkp, rkp);
+#pragma unroll
+            for (int e = 0; e < V; e++) {
+                const float left = (e == 0) ? ukm : v[e - 1];
+                const float right = (e == V - 1) ? ukp : v[e + 1];
+                o[e] = fmaf(-cp, left + right, v[e]);
+                o[e] = fmaf(-cr_lo, fmaf(beta, a1[e], a0[e]), o[e]);
+                o[e] = fmaf(-cr_hi, fmaf(beta, b1[e], b0[e]), o[e]);
+                o[e] = fmaf(-ct_lo, fmaf(beta, c1[e], c0[e]), o[e]);
+                o[e] = fmaf(-ct_hi, fmaf(beta, e1[e], e0[e]), o[e]);
+                rv[e] = fmaf(-al, o[e], rv[e]);
+            }
+            stv<float, V>(rn + k * d.N + c.base, rv);
+            if (pair) {
+                float xv[V];
+                ldv<float, V>(x + k * d.N + c.base, xv);
+#pragma unroll
+                for (int e = 0; e < V; e++) xv[e] = fmaf(al, v[e], fmaf(axp, pv[e], xv[e]));
+                stv<float, V>(x + k * d.N + c.base, xv);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // single-reduction (Chronopoulos-Gear) form, FP64: s = A~ p is carried by its own recurrence,
 // so one stencil pass w = A~ r yields every inner product of an iteration
 // ------------------------------------------------------------------------------------------
@@ -847,7 +1017,8 @@ __global__ void k_finish64(Dims d, int nc, const double* __restrict__ xs, const 
 // replacement): beta = <r~_true, r~_true> / rho of the previous iteration.
 template <int V>
 __global__ void __launch_bounds__(kThreads) k_outer_res(Dims d, int nc, const double* __restrict__ b,
-                                                        const double* __restrict__ x, float* __restrict__ r32,
+                                                        const double* __restrict__ x, float* __restrict__ r32a,
+                                                        float* __restrict__ r32b,
                                                         float* __restrict__ p32, float* __restrict__ x32,
                                                         OpTab<double> t, OpTab64u tu, PcgScalars* sc,
                                                         double* __restrict__ partials, int first, int restart,
@@ -855,6 +1026,8 @@ __global__ void __launch_bounds__(kThreads) k_outer_res(Dims d, int nc, const do
     const int nt = d.nt;
     const unsigned int G = (unsigned int)(d.N / 2);
     const long long plane = (long long)nt * d.np;
+    // r~ goes to the half of a double-buffered r~ (r32b non-null) on the parity of p~
+    float* __restrict__ r32 = (r32b && !first && sc->par) ? r32b : r32a;
     double a_rout = 0.0, a_bb = 0.0, a_rho = 0.0, a_rin = 0.0;
     for (unsigned int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
         const Cell c = decompose<2>(d, g);
@@ -1104,6 +1277,26 @@ void enqueue_recompute32_var(mhd_grid_s* g, cudaStream_t st, int nc) {
     else enqueue_recompute32_nc<V, 4>(g, st, nc, g->slab32 == -4);
 }
 
+template <int V, int NC>
+void enqueue_cgpair32(mhd_grid_s* g, cudaStream_t st) {
+    const Dims d = g->d;
+    int s = prof_begin(g, st, MHD_KERNEL_CGR32);
+    k_cgr32<V, NC><<<grid_blocks(g, d.N / V, resident_per_sm<k_cgr32<V, NC>>()), kThreads, 0, st>>>(
+        d, g->r32, g->q32, g->t32, g->tu.dg, g->sc, g->partials);
+    prof_end(g, st, s);
+    s = prof_begin(g, st, MHD_KERNEL_CGU32);
+    k_cgu32<V, NC><<<grid_blocks(g, d.N / V, resident_per_sm<k_cgu32<V, NC>>()), kThreads, 0, st>>>(
+        d, g->x32, g->r32, g->q32, g->p32, g->t32, g->sc);
+    prof_end(g, st, s);
+}
+
+template <int V>
+void enqueue_cgpair32_nc(mhd_grid_s* g, cudaStream_t st, int nc) {
+    if (nc == 3) enqueue_cgpair32<V, 3>(g, st);
+    else if (nc == 2) enqueue_cgpair32<V, 2>(g, st);
+    else enqueue_cgpair32<V, 1>(g, st);
+}
+
 template <int V>
 void enqueue_fused32_nc(mhd_grid_s* g, cudaStream_t st, int nc) {
     if (nc == 3) enqueue_fused32<V, 3>(g, st);
@@ -1217,6 +1410,10 @@ void enqueue_iteration(mhd_grid_s* g, cudaStream_t st, int prec, int nc) {
     } else if (g->slab32 <= -100) {
         // plane-marching pair with bulk-copy staging, when the autotuner measured it fastest
         enqueue_bulk32(g, st, nc, -100 - g->slab32);
+    } else if (g->slab32 == -6) {
+        // single-reduction pair (residual kernel, then the update), when measured fastest
+        if (use_v4(g)) enqueue_cgpair32_nc<4>(g, st, nc);
+        else enqueue_cgpair32_nc<2>(g, st, nc);
     } else if (g->slab32 <= -3 && g->slab32 >= -5) {
         // recompute pair, when the autotuner measured it fastest (-4: the r update walks backwards,
         // -5: compiled for 6 CTAs per SM)
@@ -1308,6 +1505,7 @@ __global__ void k_setup(PcgScalars* sc, double tol, double inner_tol, int max_it
     sc->rho_prev = 0.0;
     sc->par = 0;
     sc->ax = 0.0;
+    sc->pend = 0;
     sc->count = 0u;
 }
 
@@ -1338,6 +1536,7 @@ __global__ void k_tune_reset(PcgScalars* sc) {
     sc->max_iter = 1 << 30;
     sc->par = 0;
     sc->ax = 0.0;
+    sc->pend = 0;
     sc->count = 0u;
 }
 
@@ -1354,7 +1553,7 @@ int forced_slab() {
 mhd_status_t tune_slab32(mhd_grid_s* g, int nc) {
     if (g->slab32 != 0) return MHD_OK;
     if (const int f = forced_slab()) {
-        if (f <= -2 && f >= -5) g->slab32 = f;
+        if (f <= -2 && f >= -6) g->slab32 = f;
         else if (f <= -100) g->slab32 = (bulk32_ok(g) && f < -100) ? f : -1;
         else g->slab32 = (f > 0 && tiled32_ok(g) && tiled32_blocks(g, f) <= kMaxBlocks) ? f : -1;
         return MHD_OK;
@@ -1370,10 +1569,11 @@ mhd_status_t tune_slab32(mhd_grid_s* g, int nc) {
     const size_t n3 = 3 * (size_t)g->d.N;
     // candidates -1: the split kernels (p update, stencil, update); -2: the p update folded into
     // the stencil, then the update; -3, -4, -5: the recompute pair (no q~ stored), forwards, with
-    // the r update walking backwards, or at 6 CTAs per SM; -132, -164: the same pair as
-    // plane-marching kernels staged by bulk copies (units of 32 or 64 planes). Four iterations
-    // each after one untimed: an even count, so each is timed with its x updates.
-    for (int cand : {-1, -2, -3, -4, -5, -132, -164}) {
+    // the r update walking backwards, or at 6 CTAs per SM; -6: the single-reduction pair; -132,
+    // -164: the recompute pair as plane-marching kernels staged by bulk copies (units of 32 or 64
+    // planes). Four iterations each after one untimed: an even count, so each is timed with its
+    // x updates.
+    for (int cand : {-1, -2, -3, -4, -5, -6, -132, -164}) {
         if (cand <= -100 && !bulk32_ok(g)) continue;
         k_tune_reset<<<1, 1, 0, g->stream>>>(g->sc);
         g->slab32 = cand;
@@ -1556,8 +1756,8 @@ mhd_status_t solve(mhd_grid_s* g, const double* alpha_dev, int nc, const double*
         const int ps = prof_begin(g, g->stream, MHD_KERNEL_OUTER_RES);
         const int restart = (o == 0 || prm->mixed_restart) ? 1 : 0;
         k_outer_res<2><<<grid_blocks(g, d.N / 2, resident_per_sm<k_outer_res<2>>()), kThreads, 0, g->stream>>>(
-            d, nc, b, x, g->r32, g->p32, g->x32, g->t64, g->tu, g->sc, g->partials, o == 0 ? 1 : 0, restart,
-            pc2 ? 1 : 0);
+            d, nc, b, x, g->r32, (!pc2 && g->slab32 == -6) ? g->q32 : nullptr, g->p32, g->x32, g->t64, g->tu, g->sc,
+            g->partials, o == 0 ? 1 : 0, restart, pc2 ? 1 : 0);
         if (pc2) pc2_reliable32(g, nc, restart);
         prof_end(g, g->stream, ps);
         mhd_status_t st = check_cuda(g, "outer residual");
