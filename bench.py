@@ -977,6 +977,67 @@ def run_profile_case(args):
     print(json.dumps(dict(profile_case=f"{d.nr}x{d.nt}x{d.np}", alpha_si=c["alpha_si"], **out)), flush=True)
 
 
+def run_iteration_forms(args):
+    """Time each kernel form of the FP64 and FP32 CG iterations on the workload's first SI system:
+    every form forced in turn (MHD_FORCE_SLAB) on its own grid. FP64: a fixed-count solve
+    (--form-iters iterations, tol 1e-30); FP32: the mixed solve to tol 1e-9 with reliable updates at
+    inner tol 0.1. Each once unprofiled (CUDA events around the solve) and once with per-kernel
+    events. One JSON line per form."""
+    import torch
+    from paper_1811_02605_gb300 import build as B
+    B.build()
+    import paper_1811_02605_gb300 as P
+    w, st0 = gen_state(args.workload, args.grid)
+    d = w["desc"]
+    N = d.nr * d.nt * d.np
+    hbm, _ = peaks()
+    ds = {k: torch.from_numpy(v).cuda() for k, v in st0.items()}
+    del st0
+    legs = [("fp64", c) for c in args.forms64.split(",") if c] + [("fp32", c) for c in args.forms32.split(",") if c]
+    for prec, code in legs:
+        os.environ["MHD_FORCE_SLAB"] = code
+        g = P.mhd_grid_create(d.nr, d.nt, d.np, d.r0, d.r1, d.stretch)
+        f = P.make_fields(ds["br"], ds["bt"], ds["bp"], ds["vr"], ds["vt"], ds["vp"])
+        c = P.mhd_step_coeffs(g, P.make_params(nu=w["nu"], cfl=w["cfl"]), f)
+        b = torch.empty((3, d.nr, d.nt, d.np), dtype=torch.float64, device="cuda")
+        P.mhd_force(g, f, c["dt"], b)
+        if prec == "fp64":
+            prm = P.make_params(tol=1e-30, max_iter=args.form_iters)
+        else:
+            prm = P.make_params(tol=1e-9, inner_tol=0.1, precision=P.PREC_MIXED, max_outer=200, max_iter=20000)
+        x = torch.zeros_like(b)
+        P.pcg_solve(g, c["alpha_si"], b, x, prm)   # the autotuner's set-up and a warm-up
+        row = dict(precision=prec, form=code, forms_chosen=P.mhd_grid_kernel_forms(g))
+        for prof in (False, True):
+            x.zero_()
+            torch.cuda.synchronize()
+            P.mhd_profile_enable(g, prof)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st, it, ou, rr = P.pcg_solve(g, c["alpha_si"], b, x, prm)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            if prof:
+                pr = {k: v for k, v in P.mhd_profile_read(g).items() if v[1]}
+                row["kernel_ms_per_iteration"] = {k: round(v[0] / it, 4) for k, v in pr.items()}
+                P.mhd_profile_enable(g, False)
+            else:
+                row.update(iters=it, outer=ou, relres=rr, ms=round(ms, 3), ms_per_iteration=round(ms / it, 4))
+        if prec == "fp32":
+            inner = sum(v for k, v in row["kernel_ms_per_iteration"].items() if k.endswith("32"))
+            row["inner_kernels_ms_per_iteration"] = round(inner, 4)
+            row["inner_frac_of_hbm"] = round(PCG_BYTES_PER_CELL["fp32"] * N / (inner * 1e-3) / 1e9 / hbm, 4)
+            row["solve_frac_of_hbm"] = round(PCG_BYTES_PER_CELL["fp32"] * N / (row["ms_per_iteration"] * 1e-3)
+                                             / 1e9 / hbm, 4)
+        else:
+            row["fp64_pipe_frac"] = round(FP64_INSTR_PER_CELL_ITER * N / (row["ms_per_iteration"] * 1e-3)
+                                          / FP64_INSTR_PEAK, 4)
+        del g
+        print(json.dumps(row), flush=True)
+    os.environ.pop("MHD_FORCE_SLAB", None)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -990,6 +1051,11 @@ def main():
     ap.add_argument("--profile-iters", type=int, default=6)
     ap.add_argument("--profile-legs", default="fp64,mixed",
                     help="--profile-case pieces: fp64, mixed, pc2, pc2mixed (capped solves), sts, res (capped steps)")
+    ap.add_argument("--iteration-forms", action="store_true",
+                    help="time every kernel form of the FP64 and FP32 CG iterations on the first SI system and exit")
+    ap.add_argument("--forms64", default="-1,-64")
+    ap.add_argument("--forms32", default="-1,-2,-3,-4,-6")
+    ap.add_argument("--form-iters", type=int, default=300)
     ap.add_argument("--batched", action="store_true", help="time the 64-system batched solve and exit")
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--adjoint", action="store_true", help="time and check the adjoint workload and exit")
@@ -1021,6 +1087,8 @@ def main():
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args)
+    elif args.iteration_forms:
+        run_iteration_forms(args)
     elif args.batched:
         run_batched(args)
     elif args.adjoint:
