@@ -655,11 +655,40 @@ __global__ void __launch_bounds__(kThreads) k_update(Dims d, T* __restrict__ x,
 // update kernel that ran before it (parity flip, deferred alpha p~, iteration count), then takes
 // the stop test and forms beta and alpha for the next update (after a residual replacement,
 // iter = 0, beta is the one the replacement chose).
-template <int V, int NC>
-__global__ void __launch_bounds__(kThreads, 4) k_cgr32(Dims d, const float* __restrict__ ra,
-                                                       const float* __restrict__ rb, OpTab<float> t,
-                                                       const double* __restrict__ dg, PcgScalars* sc,
-                                                       double* __restrict__ partials) {
+// one component of R at one cell group: r~ at the cell and its neighbours, A~ r~, the partial sums
+template <int V>
+__device__ __forceinline__ void cgr_component(const Dims& d, const Cell& c, const Nbr<V>& nb, const float* rk,
+                                              long long row, int km, int kp, float cr_lo, float cr_hi,
+                                              float ct_lo, float ct_hi, float cp, float (&rs)[V],
+                                              Acc<float>& a_d) {
+    float v[V], o[V], a[V], b[V], cc[V], e4[V];
+    ldv<float, V>(rk + c.base, v);
+    const float ukm = rk[row + km], ukp = rk[row + kp];
+    ldv<float, V>(rk + c.base + nb.im, a);
+    ldv<float, V>(rk + c.base + nb.ip, b);
+    ldv<float, V>(rk + c.base + nb.jm, cc);
+    ldv<float, V>(rk + c.base + nb.jp, e4);
+#pragma unroll
+    for (int e = 0; e < V; e++) {
+        const float left = (e == 0) ? ukm : v[e - 1];
+        const float right = (e == V - 1) ? ukp : v[e + 1];
+        o[e] = fmaf(-cp, left + right, v[e]);
+        o[e] = fmaf(-cr_lo, a[e], o[e]);
+        o[e] = fmaf(-cr_hi, b[e], o[e]);
+        o[e] = fmaf(-ct_lo, cc[e], o[e]);
+        o[e] = fmaf(-ct_hi, e4[e], o[e]);
+        rs[e] = fmaf(v[e], v[e], rs[e]);
+        a_d.fma_add(v[e], o[e]);
+    }
+}
+
+// UNR: the component loop unrolled (every component's loads can be in flight at once, at fewer
+// CTAs per SM: MINB)
+template <int V, int NC, int MINB, bool UNR>
+__global__ void __launch_bounds__(kThreads, MINB) k_cgr32(Dims d, const float* __restrict__ ra,
+                                                          const float* __restrict__ rb, OpTab<float> t,
+                                                          const double* __restrict__ dg, PcgScalars* sc,
+                                                          double* __restrict__ partials) {
     if (sc->done) return;
     const float* __restrict__ r = (sc->pend ? 1 - sc->par : sc->par) ? rb : ra;
     const int nt = d.nt;
@@ -677,28 +706,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_cgr32(Dims d, const float* __re
         const int kp = (c.k0 + V == d.np) ? 0 : c.k0 + V;
         float rs[V];
         zerov<float, V>(rs);
-#pragma unroll 1
-        for (int k = 0; k < NC; k++) {
-            const float* rk = r + k * d.N;
-            float v[V], o[V], a[V], b[V], cc[V], e4[V];
-            ldv<float, V>(rk + c.base, v);
-            const float ukm = rk[row + km], ukp = rk[row + kp];
-            ldv<float, V>(rk + c.base + nb.im, a);
-            ldv<float, V>(rk + c.base + nb.ip, b);
-            ldv<float, V>(rk + c.base + nb.jm, cc);
-            ldv<float, V>(rk + c.base + nb.jp, e4);
+        if constexpr (UNR) {
 #pragma unroll
-            for (int e = 0; e < V; e++) {
-                const float left = (e == 0) ? ukm : v[e - 1];
-                const float right = (e == V - 1) ? ukp : v[e + 1];
-                o[e] = fmaf(-cp, left + right, v[e]);
-                o[e] = fmaf(-cr_lo, a[e], o[e]);
-                o[e] = fmaf(-cr_hi, b[e], o[e]);
-                o[e] = fmaf(-ct_lo, cc[e], o[e]);
-                o[e] = fmaf(-ct_hi, e4[e], o[e]);
-                rs[e] = fmaf(v[e], v[e], rs[e]);
-                a_d.fma_add(v[e], o[e]);
-            }
+            for (int k = 0; k < NC; k++)
+                cgr_component<V>(d, c, nb, r + k * d.N, row, km, kp, cr_lo, cr_hi, ct_lo, ct_hi, cp, rs, a_d);
+        } else {
+#pragma unroll 1
+            for (int k = 0; k < NC; k++)
+                cgr_component<V>(d, c, nb, r + k * d.N, row, km, kp, cr_lo, cr_hi, ct_lo, ct_hi, cp, rs, a_d);
         }
         float cell = rs[0];
 #pragma unroll
@@ -1281,8 +1296,12 @@ template <int V, int NC>
 void enqueue_cgpair32(mhd_grid_s* g, cudaStream_t st) {
     const Dims d = g->d;
     int s = prof_begin(g, st, MHD_KERNEL_CGR32);
-    k_cgr32<V, NC><<<grid_blocks(g, d.N / V, resident_per_sm<k_cgr32<V, NC>>()), kThreads, 0, st>>>(
-        d, g->r32, g->q32, g->t32, g->tu.dg, g->sc, g->partials);
+    if (g->slab32 == -7)   // residual kernel with the component loop unrolled, 3 CTAs per SM
+        k_cgr32<V, NC, 3, true><<<grid_blocks(g, d.N / V, resident_per_sm<k_cgr32<V, NC, 3, true>>()), kThreads, 0,
+                                  st>>>(d, g->r32, g->q32, g->t32, g->tu.dg, g->sc, g->partials);
+    else
+        k_cgr32<V, NC, 4, false><<<grid_blocks(g, d.N / V, resident_per_sm<k_cgr32<V, NC, 4, false>>()), kThreads, 0,
+                                   st>>>(d, g->r32, g->q32, g->t32, g->tu.dg, g->sc, g->partials);
     prof_end(g, st, s);
     s = prof_begin(g, st, MHD_KERNEL_CGU32);
     k_cgu32<V, NC><<<grid_blocks(g, d.N / V, resident_per_sm<k_cgu32<V, NC>>()), kThreads, 0, st>>>(
@@ -1410,7 +1429,7 @@ void enqueue_iteration(mhd_grid_s* g, cudaStream_t st, int prec, int nc) {
     } else if (g->slab32 <= -100) {
         // plane-marching pair with bulk-copy staging, when the autotuner measured it fastest
         enqueue_bulk32(g, st, nc, -100 - g->slab32);
-    } else if (g->slab32 == -6) {
+    } else if (g->slab32 == -6 || g->slab32 == -7) {
         // single-reduction pair (residual kernel, then the update), when measured fastest
         if (use_v4(g)) enqueue_cgpair32_nc<4>(g, st, nc);
         else enqueue_cgpair32_nc<2>(g, st, nc);
@@ -1553,7 +1572,7 @@ int forced_slab() {
 mhd_status_t tune_slab32(mhd_grid_s* g, int nc) {
     if (g->slab32 != 0) return MHD_OK;
     if (const int f = forced_slab()) {
-        if (f <= -2 && f >= -6) g->slab32 = f;
+        if (f <= -2 && f >= -7) g->slab32 = f;
         else if (f <= -100) g->slab32 = (bulk32_ok(g) && f < -100) ? f : -1;
         else g->slab32 = (f > 0 && tiled32_ok(g) && tiled32_blocks(g, f) <= kMaxBlocks) ? f : -1;
         return MHD_OK;
@@ -1569,11 +1588,12 @@ mhd_status_t tune_slab32(mhd_grid_s* g, int nc) {
     const size_t n3 = 3 * (size_t)g->d.N;
     // candidates -1: the split kernels (p update, stencil, update); -2: the p update folded into
     // the stencil, then the update; -3, -4, -5: the recompute pair (no q~ stored), forwards, with
-    // the r update walking backwards, or at 6 CTAs per SM; -6: the single-reduction pair; -132,
+    // the r update walking backwards, or at 6 CTAs per SM; -6, -7: the single-reduction pair (-7:
+    // its residual kernel with the component loop unrolled); -132,
     // -164: the recompute pair as plane-marching kernels staged by bulk copies (units of 32 or 64
     // planes). Four iterations each after one untimed: an even count, so each is timed with its
     // x updates.
-    for (int cand : {-1, -2, -3, -4, -5, -6, -132, -164}) {
+    for (int cand : {-1, -2, -3, -4, -5, -6, -7, -132, -164}) {
         if (cand <= -100 && !bulk32_ok(g)) continue;
         k_tune_reset<<<1, 1, 0, g->stream>>>(g->sc);
         g->slab32 = cand;
@@ -1756,7 +1776,7 @@ mhd_status_t solve(mhd_grid_s* g, const double* alpha_dev, int nc, const double*
         const int ps = prof_begin(g, g->stream, MHD_KERNEL_OUTER_RES);
         const int restart = (o == 0 || prm->mixed_restart) ? 1 : 0;
         k_outer_res<2><<<grid_blocks(g, d.N / 2, resident_per_sm<k_outer_res<2>>()), kThreads, 0, g->stream>>>(
-            d, nc, b, x, g->r32, (!pc2 && g->slab32 == -6) ? g->q32 : nullptr, g->p32, g->x32, g->t64, g->tu, g->sc,
+            d, nc, b, x, g->r32, (!pc2 && (g->slab32 == -6 || g->slab32 == -7)) ? g->q32 : nullptr, g->p32, g->x32, g->t64, g->tu, g->sc,
             g->partials, o == 0 ? 1 : 0, restart, pc2 ? 1 : 0);
         if (pc2) pc2_reliable32(g, nc, restart);
         prof_end(g, g->stream, ps);
