@@ -124,7 +124,7 @@ enum { MHD_PREC_FP64 = 0, MHD_PREC_MIXED = 1 };
  * Diagnostics only: the environment variable MHD_FORCE_SLAB skips the timing (-1 split, -2
  * folded, -3 recompute pair, -4 recompute pair with the second kernel walking the grid backwards,
  * -5 recompute pair at 6 CTAs per SM, -6 / -7 single-reduction pair (-7: its residual kernel
- * unrolled over the components), -64 the FP64 iteration with its components overlapped on two
+ * unrolled over the components, both kernels at 3 CTAs per SM), -64 the FP64 iteration with its components overlapped on two
  * streams,
  * n > 0 tiles of n planes). */
 typedef struct {

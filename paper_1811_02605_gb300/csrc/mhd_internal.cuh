@@ -39,7 +39,7 @@ struct PcgScalars {
     double dte;      // implicit resistivity: dt eta of the current solve
     double ax;       // alpha of the last CG iteration whose alpha p~ has not yet been added to x~
     double pqc[3];   // per-component shares of <p~, q~> (FP64 iteration with the components overlapped)
-    int pend;        // FP32 single-reduction pair: an update kernel ran since the last residual kernel
+    double wp;       // FP32 single-reduction pair: <r~, A~ p~_old> summed by the update kernel
 };
 
 // Device-resident scalars of one step.

@@ -639,28 +639,32 @@ __global__ void __launch_bounds__(kThreads) k_update(Dims d, T* __restrict__ x,
 }
 
 // ------------------------------------------------------------------------------------------
-// FP32 single-reduction pair (Chronopoulos-Gear scalars, nothing but p, r and x stored)
+// FP32 single-reduction pair (one reduction per iteration; nothing but p, r and x stored)
 // ------------------------------------------------------------------------------------------
-// The Chronopoulos-Gear recurrence needs one reduction per iteration: from gamma = <r~, r~> and
-// delta = <r~, A~ r~> of the current residual, beta = gamma / gamma_prev and
-// alpha = gamma / (delta - beta gamma / alpha_prev), the denominator being <p~, A~ p~> of the
-// Hestenes-Stiefel form in exact arithmetic. Instead of carrying s = A~ p~ as a stored
-// recurrence, the update kernel forms p~ = r~ + beta p~_old at the cell and its six neighbours
-// and applies A~ there, so an iteration moves r~ in (residual kernel), r~ and p~_old in, p~ and
-// r~ out (update kernel) and x~ in and out every second iteration: 6 vector passes, the
-// algorithmic minimum. r~ is double-buffered with the q~ workspace (the update reads r~ at its
-// neighbours while it writes the new r~), on the same parity as p~.
+// With p~ = r~ + beta p~_old, <p~, A~ p~> = delta + 2 beta <r~, A~ p~_old> + beta^2 <p~_old, A~ p~_old>,
+// delta = <r~, A~ r~>. The update kernel that formed r~ = r~_old - alpha A~ p~_old also sums
+// <r~, A~ p~_old> (A~ p~_old is at hand there), and <p~_old, A~ p~_old> is the previous iteration's
+// denominator, so one reduction per iteration (gamma = <r~, r~>, delta, sum dg r~^2 in the
+// residual kernel) gives alpha = gamma / <p~, A~ p~> and beta = gamma / gamma_prev: the
+// Hestenes-Stiefel scalars, without relying on the orthogonality that the Chronopoulos-Gear form
+// takes for <r~, A~ p~_old> (the FP64 residual replacement of the mixed solve breaks it; that
+// form, tried first, stagnated after the first replacement at inner tolerance 1e-5). After a
+// replacement (iter = 0 with the recurrence kept), the residual kernel sums <A~ r~, p~_old> itself
+// from one extra read of p~_old.
+// The update kernel forms p~ at the cell and its six neighbours and applies A~ there, so an
+// iteration moves r~ in (residual kernel), r~ and p~_old in, p~ and r~ out (update kernel) and x~
+// in and out every second iteration: 6 vector passes, the algorithmic minimum. r~ is
+// double-buffered with the q~ workspace (the update reads r~ at its neighbours while it writes the
+// new r~), on the parity of p~.
 //
-// R (k_cgr32): w = A~ r~ at the cell; gamma, delta and sum dg r~^2. Its last CTA first books the
-// update kernel that ran before it (parity flip, deferred alpha p~, iteration count), then takes
-// the stop test and forms beta and alpha for the next update (after a residual replacement,
-// iter = 0, beta is the one the replacement chose).
+// R (k_cgr32): A~ r~ at the cell; gamma, delta, sum dg r~^2 (and <A~ r~, p~_old> after a
+// replacement). Its last CTA takes the stop test and forms beta and alpha for the update.
 // one component of R at one cell group: r~ at the cell and its neighbours, A~ r~, the partial sums
-template <int V>
+template <int V, bool WP>
 __device__ __forceinline__ void cgr_component(const Dims& d, const Cell& c, const Nbr<V>& nb, const float* rk,
                                               long long row, int km, int kp, float cr_lo, float cr_hi,
                                               float ct_lo, float ct_hi, float cp, float (&rs)[V],
-                                              Acc<float>& a_d) {
+                                              Acc<float>& a_d, const float* pk, Acc<float>& a_w) {
     float v[V], o[V], a[V], b[V], cc[V], e4[V];
     ldv<float, V>(rk + c.base, v);
     const float ukm = rk[row + km], ukp = rk[row + kp];
@@ -680,20 +684,31 @@ __device__ __forceinline__ void cgr_component(const Dims& d, const Cell& c, cons
         rs[e] = fmaf(v[e], v[e], rs[e]);
         a_d.fma_add(v[e], o[e]);
     }
+    if constexpr (WP) {
+        float pv[V];
+        ldv<float, V>(pk + c.base, pv);
+#pragma unroll
+        for (int e = 0; e < V; e++) a_w.fma_add(o[e], pv[e]);
+    }
 }
 
 // UNR: the component loop unrolled (every component's loads can be in flight at once, at fewer
 // CTAs per SM: MINB)
 template <int V, int NC, int MINB, bool UNR>
 __global__ void __launch_bounds__(kThreads, MINB) k_cgr32(Dims d, const float* __restrict__ ra,
-                                                          const float* __restrict__ rb, OpTab<float> t,
+                                                          const float* __restrict__ rb,
+                                                          const float* __restrict__ pbuf, OpTab<float> t,
                                                           const double* __restrict__ dg, PcgScalars* sc,
                                                           double* __restrict__ partials) {
     if (sc->done) return;
-    const float* __restrict__ r = (sc->pend ? 1 - sc->par : sc->par) ? rb : ra;
+    const int par = sc->par;
+    const float* __restrict__ r = par ? rb : ra;
+    // first iteration after a residual replacement that keeps the recurrence: <A~ r~, p~_old> here
+    const bool repl = (sc->iter == 0 && sc->beta != 0.0);
+    const float* __restrict__ pold = pbuf + (long long)par * 3 * d.N;
     const int nt = d.nt;
     const unsigned int G = (unsigned int)(d.N / V);
-    Acc<float> a_g, a_d;
+    Acc<float> a_g, a_d, a_w;
     double a_rr = 0.0;
     for (unsigned int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
         const Cell c = decompose<V>(d, g);
@@ -706,14 +721,21 @@ __global__ void __launch_bounds__(kThreads, MINB) k_cgr32(Dims d, const float* _
         const int kp = (c.k0 + V == d.np) ? 0 : c.k0 + V;
         float rs[V];
         zerov<float, V>(rs);
-        if constexpr (UNR) {
+        if (repl) {
+#pragma unroll 1
+            for (int k = 0; k < NC; k++)
+                cgr_component<V, true>(d, c, nb, r + k * d.N, row, km, kp, cr_lo, cr_hi, ct_lo, ct_hi, cp, rs, a_d,
+                                       pold + k * d.N, a_w);
+        } else if constexpr (UNR) {
 #pragma unroll
             for (int k = 0; k < NC; k++)
-                cgr_component<V>(d, c, nb, r + k * d.N, row, km, kp, cr_lo, cr_hi, ct_lo, ct_hi, cp, rs, a_d);
+                cgr_component<V, false>(d, c, nb, r + k * d.N, row, km, kp, cr_lo, cr_hi, ct_lo, ct_hi, cp, rs, a_d,
+                                        nullptr, a_w);
         } else {
 #pragma unroll 1
             for (int k = 0; k < NC; k++)
-                cgr_component<V>(d, c, nb, r + k * d.N, row, km, kp, cr_lo, cr_hi, ct_lo, ct_hi, cp, rs, a_d);
+                cgr_component<V, false>(d, c, nb, r + k * d.N, row, km, kp, cr_lo, cr_hi, ct_lo, ct_hi, cp, rs, a_d,
+                                        nullptr, a_w);
         }
         float cell = rs[0];
 #pragma unroll
@@ -721,17 +743,11 @@ __global__ void __launch_bounds__(kThreads, MINB) k_cgr32(Dims d, const float* _
         a_g.add(cell);
         a_rr = fma(dg[c.ij], (double)cell, a_rr);
     }
-    double val[3] = {a_g.get(), a_d.get(), a_rr}, out[3];
-    if (reduce_last<3>(val, partials, &sc->count, out) && threadIdx.x == 0) {
-        if (sc->pend) {   // the update kernel since the last residual kernel
-            sc->par = 1 - sc->par;
-            sc->ax = (sc->ax != 0.0) ? 0.0 : sc->alpha;
-            sc->iter += 1;
-            sc->total_iter += 1;
-            sc->pend = 0;
-        }
+    double val[4] = {a_g.get(), a_d.get(), a_rr, a_w.get()}, out[4];
+    if (reduce_last<4>(val, partials, &sc->count, out) && threadIdx.x == 0) {
         const double gam = out[0], del = out[1], rr = out[2];
         const double beta = (sc->iter == 0) ? sc->beta : gam / sc->rho;
+        const double wp = repl ? out[3] : sc->wp;   // <r~, A~ p~_old>
         sc->rho_prev = sc->rho;
         sc->rho = gam;
         sc->rr = rr;
@@ -739,28 +755,28 @@ __global__ void __launch_bounds__(kThreads, MINB) k_cgr32(Dims d, const float* _
         else if (sqrt(rr) <= sc->tol * sqrt(sc->bb)) sc->done = 1;
         else if (sc->iter >= sc->max_iter) sc->done = 2;
         else {
-            const double den = (beta == 0.0) ? del : del - beta * gam / sc->alpha;
+            const double den = (beta == 0.0) ? del : del + beta * (2.0 * wp + beta * sc->pq);
             if (!finite(den)) sc->done = 3;
             else if (!(den > 0.0)) sc->done = 4;
             else {
                 sc->beta = beta;
                 sc->pq = den;
                 sc->alpha = gam / den;
-                sc->pend = 1;
             }
         }
     }
 }
 
 // U (k_cgu32): p~ = r~ + beta p~_old at the cell and its neighbours, q~ = A~ p~ at the cell,
-// r~ -= alpha q~ into the other r~ half, p~ into the other p~ half; x~ += alpha p~ + ax p~_old every
-// second iteration (p~_old is at hand: the pending update is always the previous p~). No
-// reduction: the next residual kernel books this one.
-template <int V, int NC>
-__global__ void __launch_bounds__(kThreads, 4) k_cgu32(Dims d, float* __restrict__ x, float* __restrict__ ra,
+// r~ -= alpha q~ into the other r~ half, p~ into the other p~ half, <r~_new, q~> for the next
+// denominator; x~ += alpha p~ + ax p~_old every second iteration (p~_old is at hand: the pending
+// update is always the previous p~). Last CTA: parity flip, deferred alpha, iteration count.
+template <int V, int NC, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_cgu32(Dims d, float* __restrict__ x, float* __restrict__ ra,
                                                        float* __restrict__ rb, float* __restrict__ pbuf,
-                                                       OpTab<float> t, const PcgScalars* sc) {
-    if (sc->done || !sc->pend) return;
+                                                       OpTab<float> t, PcgScalars* sc,
+                                                       double* __restrict__ partials) {
+    if (sc->done) return;
     const int par = sc->par;
     const float* __restrict__ r = par ? rb : ra;
     float* __restrict__ rn = par ? ra : rb;
@@ -770,6 +786,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_cgu32(Dims d, float* __restrict
     const bool pair = (sc->ax != 0.0);
     const int nt = d.nt;
     const unsigned int G = (unsigned int)(d.N / V);
+    Acc<float> a_rq;
     for (unsigned int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
         const Cell c = decompose<V>(d, g);
         const Nbr<V> nb(d, c);
@@ -810,6 +827,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_cgu32(Dims d, float* __restrict
                 o[e] = fmaf(-ct_lo, fmaf(beta, c1[e], c0[e]), o[e]);
                 o[e] = fmaf(-ct_hi, fmaf(beta, e1[e], e0[e]), o[e]);
                 rv[e] = fmaf(-al, o[e], rv[e]);
+                a_rq.fma_add(rv[e], o[e]);
             }
             stv<float, V>(rn + k * d.N + c.base, rv);
             if (pair) {
@@ -820,6 +838,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_cgu32(Dims d, float* __restrict
                 stv<float, V>(x + k * d.N + c.base, xv);
             }
         }
+    }
+    double val[1] = {a_rq.get()}, out[1];
+    if (reduce_last<1>(val, partials, &sc->count, out) && threadIdx.x == 0) {
+        sc->wp = out[0];
+        sc->par = 1 - par;
+        sc->ax = pair ? 0.0 : sc->alpha;   // pending: alpha p~, p~ in the new current half
+        sc->iter += 1;
+        sc->total_iter += 1;
     }
 }
 
@@ -1298,14 +1324,18 @@ void enqueue_cgpair32(mhd_grid_s* g, cudaStream_t st) {
     int s = prof_begin(g, st, MHD_KERNEL_CGR32);
     if (g->slab32 == -7)   // residual kernel with the component loop unrolled, 3 CTAs per SM
         k_cgr32<V, NC, 3, true><<<grid_blocks(g, d.N / V, resident_per_sm<k_cgr32<V, NC, 3, true>>()), kThreads, 0,
-                                  st>>>(d, g->r32, g->q32, g->t32, g->tu.dg, g->sc, g->partials);
+                                  st>>>(d, g->r32, g->q32, g->p32, g->t32, g->tu.dg, g->sc, g->partials);
     else
         k_cgr32<V, NC, 4, false><<<grid_blocks(g, d.N / V, resident_per_sm<k_cgr32<V, NC, 4, false>>()), kThreads, 0,
-                                   st>>>(d, g->r32, g->q32, g->t32, g->tu.dg, g->sc, g->partials);
+                                   st>>>(d, g->r32, g->q32, g->p32, g->t32, g->tu.dg, g->sc, g->partials);
     prof_end(g, st, s);
     s = prof_begin(g, st, MHD_KERNEL_CGU32);
-    k_cgu32<V, NC><<<grid_blocks(g, d.N / V, resident_per_sm<k_cgu32<V, NC>>()), kThreads, 0, st>>>(
-        d, g->x32, g->r32, g->q32, g->p32, g->t32, g->sc);
+    if (g->slab32 == -7)   // and the update kernel at 3 CTAs per SM (no spills)
+        k_cgu32<V, NC, 3><<<grid_blocks(g, d.N / V, resident_per_sm<k_cgu32<V, NC, 3>>()), kThreads, 0, st>>>(
+            d, g->x32, g->r32, g->q32, g->p32, g->t32, g->sc, g->partials);
+    else
+        k_cgu32<V, NC, 4><<<grid_blocks(g, d.N / V, resident_per_sm<k_cgu32<V, NC, 4>>()), kThreads, 0, st>>>(
+            d, g->x32, g->r32, g->q32, g->p32, g->t32, g->sc, g->partials);
     prof_end(g, st, s);
 }
 
@@ -1524,7 +1554,6 @@ __global__ void k_setup(PcgScalars* sc, double tol, double inner_tol, int max_it
     sc->rho_prev = 0.0;
     sc->par = 0;
     sc->ax = 0.0;
-    sc->pend = 0;
     sc->count = 0u;
 }
 
@@ -1555,7 +1584,6 @@ __global__ void k_tune_reset(PcgScalars* sc) {
     sc->max_iter = 1 << 30;
     sc->par = 0;
     sc->ax = 0.0;
-    sc->pend = 0;
     sc->count = 0u;
 }
 
