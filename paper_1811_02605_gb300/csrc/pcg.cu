@@ -649,22 +649,21 @@ __global__ void __launch_bounds__(kThreads) k_update(Dims d, T* __restrict__ x,
 // Hestenes-Stiefel scalars, without relying on the orthogonality that the Chronopoulos-Gear form
 // takes for <r~, A~ p~_old> (the FP64 residual replacement of the mixed solve breaks it; that
 // form, tried first, stagnated after the first replacement at inner tolerance 1e-5). After a
-// replacement (iter = 0 with the recurrence kept), the residual kernel sums <A~ r~, p~_old> itself
-// from one extra read of p~_old.
+// replacement the FP64 residual kernel sums <r~, A~ p~_old> for the replaced residual itself.
 // The update kernel forms p~ at the cell and its six neighbours and applies A~ there, so an
 // iteration moves r~ in (residual kernel), r~ and p~_old in, p~ and r~ out (update kernel) and x~
 // in and out every second iteration: 6 vector passes, the algorithmic minimum. r~ is
 // double-buffered with the q~ workspace (the update reads r~ at its neighbours while it writes the
 // new r~), on the parity of p~.
 //
-// R (k_cgr32): A~ r~ at the cell; gamma, delta, sum dg r~^2 (and <A~ r~, p~_old> after a
-// replacement). Its last CTA takes the stop test and forms beta and alpha for the update.
+// R (k_cgr32): A~ r~ at the cell; gamma, delta, sum dg r~^2. Its last CTA takes the stop test
+// and forms beta and alpha for the update.
 // one component of R at one cell group: r~ at the cell and its neighbours, A~ r~, the partial sums
-template <int V, bool WP>
+template <int V>
 __device__ __forceinline__ void cgr_component(const Dims& d, const Cell& c, const Nbr<V>& nb, const float* rk,
                                               long long row, int km, int kp, float cr_lo, float cr_hi,
                                               float ct_lo, float ct_hi, float cp, float (&rs)[V],
-                                              Acc<float>& a_d, const float* pk, Acc<float>& a_w) {
+                                              Acc<float>& a_d) {
     float v[V], o[V], a[V], b[V], cc[V], e4[V];
     ldv<float, V>(rk + c.base, v);
     const float ukm = rk[row + km], ukp = rk[row + kp];
@@ -684,31 +683,20 @@ __device__ __forceinline__ void cgr_component(const Dims& d, const Cell& c, cons
         rs[e] = fmaf(v[e], v[e], rs[e]);
         a_d.fma_add(v[e], o[e]);
     }
-    if constexpr (WP) {
-        float pv[V];
-        ldv<float, V>(pk + c.base, pv);
-#pragma unroll
-        for (int e = 0; e < V; e++) a_w.fma_add(o[e], pv[e]);
-    }
 }
 
 // UNR: the component loop unrolled (every component's loads can be in flight at once, at fewer
 // CTAs per SM: MINB)
 template <int V, int NC, int MINB, bool UNR>
 __global__ void __launch_bounds__(kThreads, MINB) k_cgr32(Dims d, const float* __restrict__ ra,
-                                                          const float* __restrict__ rb,
-                                                          const float* __restrict__ pbuf, OpTab<float> t,
+                                                          const float* __restrict__ rb, OpTab<float> t,
                                                           const double* __restrict__ dg, PcgScalars* sc,
                                                           double* __restrict__ partials) {
     if (sc->done) return;
-    const int par = sc->par;
-    const float* __restrict__ r = par ? rb : ra;
-    // first iteration after a residual replacement that keeps the recurrence: <A~ r~, p~_old> here
-    const bool repl = (sc->iter == 0 && sc->beta != 0.0);
-    const float* __restrict__ pold = pbuf + (long long)par * 3 * d.N;
+    const float* __restrict__ r = sc->par ? rb : ra;
     const int nt = d.nt;
     const unsigned int G = (unsigned int)(d.N / V);
-    Acc<float> a_g, a_d, a_w;
+    Acc<float> a_g, a_d;
     double a_rr = 0.0;
     for (unsigned int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
         const Cell c = decompose<V>(d, g);
@@ -721,21 +709,14 @@ __global__ void __launch_bounds__(kThreads, MINB) k_cgr32(Dims d, const float* _
         const int kp = (c.k0 + V == d.np) ? 0 : c.k0 + V;
         float rs[V];
         zerov<float, V>(rs);
-        if (repl) {
-#pragma unroll 1
-            for (int k = 0; k < NC; k++)
-                cgr_component<V, true>(d, c, nb, r + k * d.N, row, km, kp, cr_lo, cr_hi, ct_lo, ct_hi, cp, rs, a_d,
-                                       pold + k * d.N, a_w);
-        } else if constexpr (UNR) {
+        if constexpr (UNR) {
 #pragma unroll
             for (int k = 0; k < NC; k++)
-                cgr_component<V, false>(d, c, nb, r + k * d.N, row, km, kp, cr_lo, cr_hi, ct_lo, ct_hi, cp, rs, a_d,
-                                        nullptr, a_w);
+                cgr_component<V>(d, c, nb, r + k * d.N, row, km, kp, cr_lo, cr_hi, ct_lo, ct_hi, cp, rs, a_d);
         } else {
 #pragma unroll 1
             for (int k = 0; k < NC; k++)
-                cgr_component<V, false>(d, c, nb, r + k * d.N, row, km, kp, cr_lo, cr_hi, ct_lo, ct_hi, cp, rs, a_d,
-                                        nullptr, a_w);
+                cgr_component<V>(d, c, nb, r + k * d.N, row, km, kp, cr_lo, cr_hi, ct_lo, ct_hi, cp, rs, a_d);
         }
         float cell = rs[0];
 #pragma unroll
@@ -743,11 +724,11 @@ __global__ void __launch_bounds__(kThreads, MINB) k_cgr32(Dims d, const float* _
         a_g.add(cell);
         a_rr = fma(dg[c.ij], (double)cell, a_rr);
     }
-    double val[4] = {a_g.get(), a_d.get(), a_rr, a_w.get()}, out[4];
-    if (reduce_last<4>(val, partials, &sc->count, out) && threadIdx.x == 0) {
+    double val[3] = {a_g.get(), a_d.get(), a_rr}, out[3];
+    if (reduce_last<3>(val, partials, &sc->count, out) && threadIdx.x == 0) {
         const double gam = out[0], del = out[1], rr = out[2];
         const double beta = (sc->iter == 0) ? sc->beta : gam / sc->rho;
-        const double wp = repl ? out[3] : sc->wp;   // <r~, A~ p~_old>
+        const double wp = sc->wp;   // <r~, A~ p~_old>, from the update kernel or the replacement
         sc->rho_prev = sc->rho;
         sc->rho = gam;
         sc->rr = rr;
@@ -786,7 +767,9 @@ __global__ void __launch_bounds__(kThreads, MINB) k_cgu32(Dims d, float* __restr
     const bool pair = (sc->ax != 0.0);
     const int nt = d.nt;
     const unsigned int G = (unsigned int)(d.N / V);
-    Acc<float> a_rq;
+    // the cross term: plain FP32 per thread (one register; a compensated sum spilled here), FP64
+    // across threads
+    float a_rq = 0.f;
     for (unsigned int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
         const Cell c = decompose<V>(d, g);
         const Nbr<V> nb(d, c);
@@ -827,7 +810,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_cgu32(Dims d, float* __restr
                 o[e] = fmaf(-ct_lo, fmaf(beta, c1[e], c0[e]), o[e]);
                 o[e] = fmaf(-ct_hi, fmaf(beta, e1[e], e0[e]), o[e]);
                 rv[e] = fmaf(-al, o[e], rv[e]);
-                a_rq.fma_add(rv[e], o[e]);
+                a_rq = fmaf(rv[e], o[e], a_rq);
             }
             stv<float, V>(rn + k * d.N + c.base, rv);
             if (pair) {
@@ -839,7 +822,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_cgu32(Dims d, float* __restr
             }
         }
     }
-    double val[1] = {a_rq.get()}, out[1];
+    double val[1] = {(double)a_rq}, out[1];
     if (reduce_last<1>(val, partials, &sc->count, out) && threadIdx.x == 0) {
         sc->wp = out[0];
         sc->par = 1 - par;
@@ -1063,9 +1046,14 @@ __global__ void __launch_bounds__(kThreads) k_outer_res(Dims d, int nc, const do
                                                         float* __restrict__ p32, float* __restrict__ x32,
                                                         OpTab<double> t, OpTab64u tu, PcgScalars* sc,
                                                         double* __restrict__ partials, int first, int restart,
-                                                        int pc2) {
+                                                        int pc2, OpTab<float> t32) {
     const int nt = d.nt;
     const unsigned int G = (unsigned int)(d.N / 2);
+    // single-reduction FP32 pair (r32b non-null): <r~, A~ p~_old> of the replaced residual, in FP32
+    // as its update kernel would have formed it, for the denominator of the next iteration
+    const bool want_wp = (r32b != nullptr) && !first;
+    const float* __restrict__ pold = p32 + (long long)(first ? 0 : sc->par) * 3 * d.N;
+    double a_wp = 0.0;
     const long long plane = (long long)nt * d.np;
     // r~ goes to the half of a double-buffered r~ (r32b non-null) on the parity of p~
     float* __restrict__ r32 = (r32b && !first && sc->par) ? r32b : r32a;
@@ -1103,14 +1091,40 @@ __global__ void __launch_bounds__(kThreads) k_outer_res(Dims d, int nc, const do
                 cell_in = fma(rd, rd, cell_in);
             }
             *reinterpret_cast<float2*>(r32 + k * d.N + c.base) = make_float2(rs[0], rs[1]);
+            if (want_wp) {
+                const float* pk = pold + k * d.N;
+                const float2 pc = *reinterpret_cast<const float2*>(pk + c.base);
+                const float pm = pk[row + km], pp = pk[row + kp];
+                const long long im = (c.i > 0) ? -plane : 0, ip = (c.i < d.nr - 1) ? plane : 0;
+                const long long jm = (c.j > 0) ? -(long long)d.np : 0, jp = (c.j < nt - 1) ? (long long)d.np : 0;
+                const float2 a = *reinterpret_cast<const float2*>(pk + c.base + im);
+                const float2 bq = *reinterpret_cast<const float2*>(pk + c.base + ip);
+                const float2 cq = *reinterpret_cast<const float2*>(pk + c.base + jm);
+                const float2 eq = *reinterpret_cast<const float2*>(pk + c.base + jp);
+                const float cr_lo = t32.ar[c.i * nt + c.j], cr_hi = t32.ar[(c.i + 1) * nt + c.j];
+                const float ct_lo = t32.at[c.i * (nt + 1) + c.j], ct_hi = t32.at[c.i * (nt + 1) + c.j + 1];
+                const float cp = t32.ap[c.ij];
+                float o0 = fmaf(-cp, pm + pc.y, pc.x), o1 = fmaf(-cp, pc.x + pp, pc.y);
+                o0 = fmaf(-cr_lo, a.x, o0);
+                o1 = fmaf(-cr_lo, a.y, o1);
+                o0 = fmaf(-cr_hi, bq.x, o0);
+                o1 = fmaf(-cr_hi, bq.y, o1);
+                o0 = fmaf(-ct_lo, cq.x, o0);
+                o1 = fmaf(-ct_lo, cq.y, o1);
+                o0 = fmaf(-ct_hi, eq.x, o0);
+                o1 = fmaf(-ct_hi, eq.y, o1);
+                a_wp = fma((double)rs[0], (double)o0, a_wp);
+                a_wp = fma((double)rs[1], (double)o1, a_wp);
+            }
             *reinterpret_cast<float2*>(x32 + k * d.N + c.base) = make_float2(0.f, 0.f);
             // first pass: p~32 = r~32 so no value left from an earlier solve can reach 0 * p
             if (first) *reinterpret_cast<float2*>(p32 + k * d.N + c.base) = make_float2(rs[0], rs[1]);
         }
         a_rin = fma(dg, cell_in, a_rin);
     }
-    double val[4] = {a_rout, a_bb, a_rho, a_rin}, out[4];
+    double val[4] = {a_rout, first ? a_bb : a_wp, a_rho, a_rin}, out[4];
     if (reduce_last<4>(val, partials, &sc->count, out) && threadIdx.x == 0) {
+        if (want_wp) sc->wp = out[1];
         if (first) {
             sc->bb = out[1];
             sc->par = 0;
@@ -1322,12 +1336,12 @@ template <int V, int NC>
 void enqueue_cgpair32(mhd_grid_s* g, cudaStream_t st) {
     const Dims d = g->d;
     int s = prof_begin(g, st, MHD_KERNEL_CGR32);
-    if (g->slab32 == -7)   // residual kernel with the component loop unrolled, 3 CTAs per SM
+    if (g->slab32 == -7 || g->slab32 == -8)   // residual kernel unrolled over the components, 3 CTAs/SM
         k_cgr32<V, NC, 3, true><<<grid_blocks(g, d.N / V, resident_per_sm<k_cgr32<V, NC, 3, true>>()), kThreads, 0,
-                                  st>>>(d, g->r32, g->q32, g->p32, g->t32, g->tu.dg, g->sc, g->partials);
+                                  st>>>(d, g->r32, g->q32, g->t32, g->tu.dg, g->sc, g->partials);
     else
         k_cgr32<V, NC, 4, false><<<grid_blocks(g, d.N / V, resident_per_sm<k_cgr32<V, NC, 4, false>>()), kThreads, 0,
-                                   st>>>(d, g->r32, g->q32, g->p32, g->t32, g->tu.dg, g->sc, g->partials);
+                                   st>>>(d, g->r32, g->q32, g->t32, g->tu.dg, g->sc, g->partials);
     prof_end(g, st, s);
     s = prof_begin(g, st, MHD_KERNEL_CGU32);
     if (g->slab32 == -7)   // and the update kernel at 3 CTAs per SM (no spills)
@@ -1459,7 +1473,7 @@ void enqueue_iteration(mhd_grid_s* g, cudaStream_t st, int prec, int nc) {
     } else if (g->slab32 <= -100) {
         // plane-marching pair with bulk-copy staging, when the autotuner measured it fastest
         enqueue_bulk32(g, st, nc, -100 - g->slab32);
-    } else if (g->slab32 == -6 || g->slab32 == -7) {
+    } else if (g->slab32 <= -6 && g->slab32 >= -8) {
         // single-reduction pair (residual kernel, then the update), when measured fastest
         if (use_v4(g)) enqueue_cgpair32_nc<4>(g, st, nc);
         else enqueue_cgpair32_nc<2>(g, st, nc);
@@ -1600,7 +1614,7 @@ int forced_slab() {
 mhd_status_t tune_slab32(mhd_grid_s* g, int nc) {
     if (g->slab32 != 0) return MHD_OK;
     if (const int f = forced_slab()) {
-        if (f <= -2 && f >= -7) g->slab32 = f;
+        if (f <= -2 && f >= -8) g->slab32 = f;
         else if (f <= -100) g->slab32 = (bulk32_ok(g) && f < -100) ? f : -1;
         else g->slab32 = (f > 0 && tiled32_ok(g) && tiled32_blocks(g, f) <= kMaxBlocks) ? f : -1;
         return MHD_OK;
@@ -1616,12 +1630,13 @@ mhd_status_t tune_slab32(mhd_grid_s* g, int nc) {
     const size_t n3 = 3 * (size_t)g->d.N;
     // candidates -1: the split kernels (p update, stencil, update); -2: the p update folded into
     // the stencil, then the update; -3, -4, -5: the recompute pair (no q~ stored), forwards, with
-    // the r update walking backwards, or at 6 CTAs per SM; -6, -7: the single-reduction pair (-7:
-    // its residual kernel with the component loop unrolled); -132,
+    // the r update walking backwards, or at 6 CTAs per SM; -6, -7, -8: the single-reduction pair
+    // (-7: its residual kernel unrolled over the components and both kernels at 3 CTAs per SM; -8:
+    // the unrolled residual kernel with the update kernel at 4); -132,
     // -164: the recompute pair as plane-marching kernels staged by bulk copies (units of 32 or 64
     // planes). Four iterations each after one untimed: an even count, so each is timed with its
     // x updates.
-    for (int cand : {-1, -2, -3, -4, -5, -6, -7, -132, -164}) {
+    for (int cand : {-1, -2, -3, -4, -5, -6, -7, -8, -132, -164}) {
         if (cand <= -100 && !bulk32_ok(g)) continue;
         k_tune_reset<<<1, 1, 0, g->stream>>>(g->sc);
         g->slab32 = cand;
@@ -1804,8 +1819,8 @@ mhd_status_t solve(mhd_grid_s* g, const double* alpha_dev, int nc, const double*
         const int ps = prof_begin(g, g->stream, MHD_KERNEL_OUTER_RES);
         const int restart = (o == 0 || prm->mixed_restart) ? 1 : 0;
         k_outer_res<2><<<grid_blocks(g, d.N / 2, resident_per_sm<k_outer_res<2>>()), kThreads, 0, g->stream>>>(
-            d, nc, b, x, g->r32, (!pc2 && (g->slab32 == -6 || g->slab32 == -7)) ? g->q32 : nullptr, g->p32, g->x32, g->t64, g->tu, g->sc,
-            g->partials, o == 0 ? 1 : 0, restart, pc2 ? 1 : 0);
+            d, nc, b, x, g->r32, (!pc2 && g->slab32 <= -6 && g->slab32 >= -8) ? g->q32 : nullptr, g->p32, g->x32, g->t64, g->tu, g->sc,
+            g->partials, o == 0 ? 1 : 0, restart, pc2 ? 1 : 0, g->t32);
         if (pc2) pc2_reliable32(g, nc, restart);
         prof_end(g, g->stream, ps);
         mhd_status_t st = check_cuda(g, "outer residual");

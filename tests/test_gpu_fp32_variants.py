@@ -28,7 +28,7 @@ def _system(d, seed):
     return og, b
 
 
-@pytest.mark.parametrize("variant", ["-1", "-2", "-3", "-4", "-5", "-6", "-7", "-132", "-116", "16"])
+@pytest.mark.parametrize("variant", ["-1", "-2", "-3", "-4", "-5", "-6", "-7", "-8", "-132", "-116", "16"])
 @pytest.mark.parametrize("restart,inner", [(0, 0.1), (1, 1e-5)])
 def test_mixed_variant_matches_fp64_oracle(monkeypatch, variant, restart, inner):
     # np = 256 (float4 groups, plane-marching tiles possible); nt = 18 leaves a ragged row tile
