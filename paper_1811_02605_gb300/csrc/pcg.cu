@@ -659,11 +659,11 @@ __global__ void __launch_bounds__(kThreads) k_update(Dims d, T* __restrict__ x,
 // R (k_cgr32): A~ r~ at the cell; gamma, delta, sum dg r~^2. Its last CTA takes the stop test
 // and forms beta and alpha for the update.
 // one component of R at one cell group: r~ at the cell and its neighbours, A~ r~, the partial sums
-template <int V>
+template <int V, bool XO>
 __device__ __forceinline__ void cgr_component(const Dims& d, const Cell& c, const Nbr<V>& nb, const float* rk,
                                               long long row, int km, int kp, float cr_lo, float cr_hi,
                                               float ct_lo, float ct_hi, float cp, float (&rs)[V],
-                                              Acc<float>& a_d) {
+                                              Acc<float>& a_d, const float* rko, Acc<float>& a_x) {
     float v[V], o[V], a[V], b[V], cc[V], e4[V];
     ldv<float, V>(rk + c.base, v);
     const float ukm = rk[row + km], ukp = rk[row + kp];
@@ -683,20 +683,36 @@ __device__ __forceinline__ void cgr_component(const Dims& d, const Cell& c, cons
         rs[e] = fmaf(v[e], v[e], rs[e]);
         a_d.fma_add(v[e], o[e]);
     }
+    if constexpr (XO) {
+        if (rko) {
+            float ro[V];
+            ldv<float, V>(rko + c.base, ro);
+#pragma unroll
+            for (int e = 0; e < V; e++) a_x.fma_add(v[e], ro[e]);
+        }
+    }
 }
 
 // UNR: the component loop unrolled (every component's loads can be in flight at once, at fewer
 // CTAs per SM: MINB)
-template <int V, int NC, int MINB, bool UNR>
+// XO: the cross term <r~, A~ p~_old> = (<r~, r~_old> - <r~, r~>) / alpha_old from the previous
+// residual, still in the other r~ half (one more read here instead of a sum in the update kernel,
+// which then needs no reduction and books nothing: this kernel books it, through sc->pend)
+template <int V, int NC, int MINB, bool UNR, bool XO>
 __global__ void __launch_bounds__(kThreads, MINB) k_cgr32(Dims d, const float* __restrict__ ra,
                                                           const float* __restrict__ rb, OpTab<float> t,
                                                           const double* __restrict__ dg, PcgScalars* sc,
                                                           double* __restrict__ partials) {
     if (sc->done) return;
-    const float* __restrict__ r = sc->par ? rb : ra;
+    const int pend = XO ? sc->pend : 0;
+    const int cur = pend ? 1 - sc->par : sc->par;
+    const float* __restrict__ r = cur ? rb : ra;
+    // r~_old is the previous recursive residual except right after a residual replacement
+    const bool xo = XO && pend;
+    const float* __restrict__ rold = xo ? (cur ? ra : rb) : nullptr;
     const int nt = d.nt;
     const unsigned int G = (unsigned int)(d.N / V);
-    Acc<float> a_g, a_d;
+    Acc<float> a_g, a_d, a_x;
     double a_rr = 0.0;
     for (unsigned int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
         const Cell c = decompose<V>(d, g);
@@ -712,11 +728,13 @@ __global__ void __launch_bounds__(kThreads, MINB) k_cgr32(Dims d, const float* _
         if constexpr (UNR) {
 #pragma unroll
             for (int k = 0; k < NC; k++)
-                cgr_component<V>(d, c, nb, r + k * d.N, row, km, kp, cr_lo, cr_hi, ct_lo, ct_hi, cp, rs, a_d);
+                cgr_component<V, XO>(d, c, nb, r + k * d.N, row, km, kp, cr_lo, cr_hi, ct_lo, ct_hi, cp, rs, a_d,
+                                     rold ? rold + k * d.N : nullptr, a_x);
         } else {
 #pragma unroll 1
             for (int k = 0; k < NC; k++)
-                cgr_component<V>(d, c, nb, r + k * d.N, row, km, kp, cr_lo, cr_hi, ct_lo, ct_hi, cp, rs, a_d);
+                cgr_component<V, XO>(d, c, nb, r + k * d.N, row, km, kp, cr_lo, cr_hi, ct_lo, ct_hi, cp, rs, a_d,
+                                     rold ? rold + k * d.N : nullptr, a_x);
         }
         float cell = rs[0];
 #pragma unroll
@@ -724,11 +742,22 @@ __global__ void __launch_bounds__(kThreads, MINB) k_cgr32(Dims d, const float* _
         a_g.add(cell);
         a_rr = fma(dg[c.ij], (double)cell, a_rr);
     }
-    double val[3] = {a_g.get(), a_d.get(), a_rr}, out[3];
-    if (reduce_last<3>(val, partials, &sc->count, out) && threadIdx.x == 0) {
+    double val[4] = {a_g.get(), a_d.get(), a_rr, a_x.get()}, out[4];
+    if (reduce_last<XO ? 4 : 3>(*reinterpret_cast<double(*)[XO ? 4 : 3]>(val), partials, &sc->count,
+                                *reinterpret_cast<double(*)[XO ? 4 : 3]>(out)) &&
+        threadIdx.x == 0) {
+        if (XO && pend) {   // book the update kernel that ran since the last residual kernel
+            sc->par = 1 - sc->par;
+            sc->ax = (sc->ax != 0.0) ? 0.0 : sc->alpha;
+            sc->iter += 1;
+            sc->total_iter += 1;
+            sc->pend = 0;
+        }
         const double gam = out[0], del = out[1], rr = out[2];
         const double beta = (sc->iter == 0) ? sc->beta : gam / sc->rho;
-        const double wp = sc->wp;   // <r~, A~ p~_old>, from the update kernel or the replacement
+        // <r~, A~ p~_old>: from r~_old (alpha is still alpha_old here), or from the update kernel, or
+        // from the replacement
+        const double wp = xo ? (out[3] - gam) / sc->alpha : sc->wp;
         sc->rho_prev = sc->rho;
         sc->rho = gam;
         sc->rr = rr;
@@ -743,6 +772,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_cgr32(Dims d, const float* _
                 sc->beta = beta;
                 sc->pq = den;
                 sc->alpha = gam / den;
+                if (XO) sc->pend = 1;
             }
         }
     }
@@ -752,12 +782,13 @@ __global__ void __launch_bounds__(kThreads, MINB) k_cgr32(Dims d, const float* _
 // r~ -= alpha q~ into the other r~ half, p~ into the other p~ half, <r~_new, q~> for the next
 // denominator; x~ += alpha p~ + ax p~_old every second iteration (p~_old is at hand: the pending
 // update is always the previous p~). Last CTA: parity flip, deferred alpha, iteration count.
-template <int V, int NC, int MINB>
+// RED = false: no cross-term sum and no booking (the next residual kernel reads r~_old and books)
+template <int V, int NC, int MINB, bool RED>
 __global__ void __launch_bounds__(kThreads, MINB) k_cgu32(Dims d, float* __restrict__ x, float* __restrict__ ra,
                                                        float* __restrict__ rb, float* __restrict__ pbuf,
                                                        OpTab<float> t, PcgScalars* sc,
                                                        double* __restrict__ partials) {
-    if (sc->done) return;
+    if (sc->done || (!RED && !sc->pend)) return;
     const int par = sc->par;
     const float* __restrict__ r = par ? rb : ra;
     float* __restrict__ rn = par ? ra : rb;
@@ -810,7 +841,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_cgu32(Dims d, float* __restr
                 o[e] = fmaf(-ct_lo, fmaf(beta, c1[e], c0[e]), o[e]);
                 o[e] = fmaf(-ct_hi, fmaf(beta, e1[e], e0[e]), o[e]);
                 rv[e] = fmaf(-al, o[e], rv[e]);
-                a_rq = fmaf(rv[e], o[e], a_rq);
+                if constexpr (RED) a_rq = fmaf(rv[e], o[e], a_rq);
             }
             stv<float, V>(rn + k * d.N + c.base, rv);
             if (pair) {
@@ -822,6 +853,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_cgu32(Dims d, float* __restr
             }
         }
     }
+    if constexpr (!RED) return;
     double val[1] = {(double)a_rq}, out[1];
     if (reduce_last<1>(val, partials, &sc->count, out) && threadIdx.x == 0) {
         sc->wp = out[0];
@@ -1332,25 +1364,31 @@ void enqueue_recompute32_var(mhd_grid_s* g, cudaStream_t st, int nc) {
     else enqueue_recompute32_nc<V, 4>(g, st, nc, g->slab32 == -4);
 }
 
-template <int V, int NC>
-void enqueue_cgpair32(mhd_grid_s* g, cudaStream_t st) {
+template <int V, int NC, int MINB_R, bool UNR, bool XO, int MINB_U, bool RED>
+void enqueue_cgpair32_k(mhd_grid_s* g, cudaStream_t st) {
     const Dims d = g->d;
     int s = prof_begin(g, st, MHD_KERNEL_CGR32);
-    if (g->slab32 == -7 || g->slab32 == -8)   // residual kernel unrolled over the components, 3 CTAs/SM
-        k_cgr32<V, NC, 3, true><<<grid_blocks(g, d.N / V, resident_per_sm<k_cgr32<V, NC, 3, true>>()), kThreads, 0,
-                                  st>>>(d, g->r32, g->q32, g->t32, g->tu.dg, g->sc, g->partials);
-    else
-        k_cgr32<V, NC, 4, false><<<grid_blocks(g, d.N / V, resident_per_sm<k_cgr32<V, NC, 4, false>>()), kThreads, 0,
-                                   st>>>(d, g->r32, g->q32, g->t32, g->tu.dg, g->sc, g->partials);
+    k_cgr32<V, NC, MINB_R, UNR, XO>
+        <<<grid_blocks(g, d.N / V, resident_per_sm<k_cgr32<V, NC, MINB_R, UNR, XO>>()), kThreads, 0, st>>>(
+            d, g->r32, g->q32, g->t32, g->tu.dg, g->sc, g->partials);
     prof_end(g, st, s);
     s = prof_begin(g, st, MHD_KERNEL_CGU32);
-    if (g->slab32 == -7)   // and the update kernel at 3 CTAs per SM (no spills)
-        k_cgu32<V, NC, 3><<<grid_blocks(g, d.N / V, resident_per_sm<k_cgu32<V, NC, 3>>()), kThreads, 0, st>>>(
-            d, g->x32, g->r32, g->q32, g->p32, g->t32, g->sc, g->partials);
-    else
-        k_cgu32<V, NC, 4><<<grid_blocks(g, d.N / V, resident_per_sm<k_cgu32<V, NC, 4>>()), kThreads, 0, st>>>(
-            d, g->x32, g->r32, g->q32, g->p32, g->t32, g->sc, g->partials);
+    k_cgu32<V, NC, MINB_U, RED><<<grid_blocks(g, d.N / V, resident_per_sm<k_cgu32<V, NC, MINB_U, RED>>()), kThreads,
+                                  0, st>>>(d, g->x32, g->r32, g->q32, g->p32, g->t32, g->sc, g->partials);
     prof_end(g, st, s);
+}
+
+// -6: both kernels at 4 CTAs per SM; -7: the residual kernel unrolled over the components, both at 3;
+// -8: unrolled residual kernel at 3, update kernel at 4; -9: unrolled residual kernel reading r~_old
+// for the cross term, update kernel at 4 without a reduction
+template <int V, int NC>
+void enqueue_cgpair32(mhd_grid_s* g, cudaStream_t st) {
+    switch (g->slab32) {
+        case -7: enqueue_cgpair32_k<V, NC, 3, true, false, 3, true>(g, st); break;
+        case -8: enqueue_cgpair32_k<V, NC, 3, true, false, 4, true>(g, st); break;
+        case -9: enqueue_cgpair32_k<V, NC, 3, true, true, 4, false>(g, st); break;
+        default: enqueue_cgpair32_k<V, NC, 4, false, false, 4, true>(g, st); break;
+    }
 }
 
 template <int V>
@@ -1473,7 +1511,7 @@ void enqueue_iteration(mhd_grid_s* g, cudaStream_t st, int prec, int nc) {
     } else if (g->slab32 <= -100) {
         // plane-marching pair with bulk-copy staging, when the autotuner measured it fastest
         enqueue_bulk32(g, st, nc, -100 - g->slab32);
-    } else if (g->slab32 <= -6 && g->slab32 >= -8) {
+    } else if (g->slab32 <= -6 && g->slab32 >= -9) {
         // single-reduction pair (residual kernel, then the update), when measured fastest
         if (use_v4(g)) enqueue_cgpair32_nc<4>(g, st, nc);
         else enqueue_cgpair32_nc<2>(g, st, nc);
@@ -1568,6 +1606,7 @@ __global__ void k_setup(PcgScalars* sc, double tol, double inner_tol, int max_it
     sc->rho_prev = 0.0;
     sc->par = 0;
     sc->ax = 0.0;
+    sc->pend = 0;
     sc->count = 0u;
 }
 
@@ -1598,6 +1637,7 @@ __global__ void k_tune_reset(PcgScalars* sc) {
     sc->max_iter = 1 << 30;
     sc->par = 0;
     sc->ax = 0.0;
+    sc->pend = 0;
     sc->count = 0u;
 }
 
@@ -1614,7 +1654,7 @@ int forced_slab() {
 mhd_status_t tune_slab32(mhd_grid_s* g, int nc) {
     if (g->slab32 != 0) return MHD_OK;
     if (const int f = forced_slab()) {
-        if (f <= -2 && f >= -8) g->slab32 = f;
+        if (f <= -2 && f >= -9) g->slab32 = f;
         else if (f <= -100) g->slab32 = (bulk32_ok(g) && f < -100) ? f : -1;
         else g->slab32 = (f > 0 && tiled32_ok(g) && tiled32_blocks(g, f) <= kMaxBlocks) ? f : -1;
         return MHD_OK;
@@ -1632,11 +1672,12 @@ mhd_status_t tune_slab32(mhd_grid_s* g, int nc) {
     // the stencil, then the update; -3, -4, -5: the recompute pair (no q~ stored), forwards, with
     // the r update walking backwards, or at 6 CTAs per SM; -6, -7, -8: the single-reduction pair
     // (-7: its residual kernel unrolled over the components and both kernels at 3 CTAs per SM; -8:
-    // the unrolled residual kernel with the update kernel at 4); -132,
+    // the unrolled residual kernel with the update kernel at 4; -9: the cross term from r~_old in
+    // the residual kernel, the update kernel without a reduction); -132,
     // -164: the recompute pair as plane-marching kernels staged by bulk copies (units of 32 or 64
     // planes). Four iterations each after one untimed: an even count, so each is timed with its
     // x updates.
-    for (int cand : {-1, -2, -3, -4, -5, -6, -7, -8, -132, -164}) {
+    for (int cand : {-1, -2, -3, -4, -5, -6, -7, -8, -9, -132, -164}) {
         if (cand <= -100 && !bulk32_ok(g)) continue;
         k_tune_reset<<<1, 1, 0, g->stream>>>(g->sc);
         g->slab32 = cand;
@@ -1819,7 +1860,7 @@ mhd_status_t solve(mhd_grid_s* g, const double* alpha_dev, int nc, const double*
         const int ps = prof_begin(g, g->stream, MHD_KERNEL_OUTER_RES);
         const int restart = (o == 0 || prm->mixed_restart) ? 1 : 0;
         k_outer_res<2><<<grid_blocks(g, d.N / 2, resident_per_sm<k_outer_res<2>>()), kThreads, 0, g->stream>>>(
-            d, nc, b, x, g->r32, (!pc2 && g->slab32 <= -6 && g->slab32 >= -8) ? g->q32 : nullptr, g->p32, g->x32, g->t64, g->tu, g->sc,
+            d, nc, b, x, g->r32, (!pc2 && g->slab32 <= -6 && g->slab32 >= -9) ? g->q32 : nullptr, g->p32, g->x32, g->t64, g->tu, g->sc,
             g->partials, o == 0 ? 1 : 0, restart, pc2 ? 1 : 0, g->t32);
         if (pc2) pc2_reliable32(g, nc, restart);
         prof_end(g, g->stream, ps);
