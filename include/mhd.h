@@ -125,8 +125,7 @@ enum { MHD_PREC_FP64 = 0, MHD_PREC_MIXED = 1 };
  * folded, -3 recompute pair, -4 recompute pair with the second kernel walking the grid backwards,
  * -5 recompute pair at 6 CTAs per SM, -6 / -7 / -8 single-reduction pair (-7: its residual kernel
  * unrolled over the components, both kernels at 3 CTAs per SM; -8: unrolled residual kernel,
- * update kernel at 4; -9: the cross term from the previous residual, update kernel without a
- * reduction; -10, -11: -8, -9 with a plane-marching residual kernel), -64 the FP64 iteration with its components overlapped on two
+ * update kernel at 4), -64 the FP64 iteration with its components overlapped on two
  * streams,
  * n > 0 tiles of n planes). */
 typedef struct {

@@ -40,7 +40,6 @@ struct PcgScalars {
     double ax;       // alpha of the last CG iteration whose alpha p~ has not yet been added to x~
     double pqc[3];   // per-component shares of <p~, q~> (FP64 iteration with the components overlapped)
     double wp;       // FP32 single-reduction pair: <r~, A~ p~_old> summed by the update kernel
-    int pend;        // FP32 single-reduction pair (-9): an update kernel ran since the last residual kernel
 };
 
 // Device-resident scalars of one step.

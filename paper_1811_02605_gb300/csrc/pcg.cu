@@ -659,11 +659,11 @@ __global__ void __launch_bounds__(kThreads) k_update(Dims d, T* __restrict__ x,
 // R (k_cgr32): A~ r~ at the cell; gamma, delta, sum dg r~^2. Its last CTA takes the stop test
 // and forms beta and alpha for the update.
 // one component of R at one cell group: r~ at the cell and its neighbours, A~ r~, the partial sums
-template <int V, bool XO>
+template <int V>
 __device__ __forceinline__ void cgr_component(const Dims& d, const Cell& c, const Nbr<V>& nb, const float* rk,
                                               long long row, int km, int kp, float cr_lo, float cr_hi,
                                               float ct_lo, float ct_hi, float cp, float (&rs)[V],
-                                              Acc<float>& a_d, const float* rko, Acc<float>& a_x) {
+                                              Acc<float>& a_d) {
     float v[V], o[V], a[V], b[V], cc[V], e4[V];
     ldv<float, V>(rk + c.base, v);
     const float ukm = rk[row + km], ukp = rk[row + kp];
@@ -683,34 +683,15 @@ __device__ __forceinline__ void cgr_component(const Dims& d, const Cell& c, cons
         rs[e] = fmaf(v[e], v[e], rs[e]);
         a_d.fma_add(v[e], o[e]);
     }
-    if constexpr (XO) {
-        if (rko) {
-            float ro[V];
-            ldv<float, V>(rko + c.base, ro);
-#pragma unroll
-            for (int e = 0; e < V; e++) a_x.fma_add(v[e], ro[e]);
-        }
-    }
 }
 
 // UNR: the component loop unrolled (every component's loads can be in flight at once, at fewer
 // CTAs per SM: MINB)
-// last CTA of a residual kernel: book the update kernel that ran since the previous residual
-// kernel (XO forms), the stop test, then beta and alpha for the next update
-template <bool XO>
-__device__ __forceinline__ void cgr_finish(PcgScalars* sc, const double* out, bool xo, int pend) {
-    if (XO && pend) {
-        sc->par = 1 - sc->par;
-        sc->ax = (sc->ax != 0.0) ? 0.0 : sc->alpha;
-        sc->iter += 1;
-        sc->total_iter += 1;
-        sc->pend = 0;
-    }
+// last CTA of the residual kernel: the stop test, then beta and alpha for the next update
+__device__ __forceinline__ void cgr_finish(PcgScalars* sc, const double* out) {
     const double gam = out[0], del = out[1], rr = out[2];
     const double beta = (sc->iter == 0) ? sc->beta : gam / sc->rho;
-    // <r~, A~ p~_old>: from r~_old (alpha is still alpha_old here), or from the update kernel, or
-    // from the replacement
-    const double wp = xo ? (out[3] - gam) / sc->alpha : sc->wp;
+    const double wp = sc->wp;   // <r~, A~ p~_old>, from the update kernel or the replacement
     sc->rho_prev = sc->rho;
     sc->rho = gam;
     sc->rr = rr;
@@ -725,29 +706,20 @@ __device__ __forceinline__ void cgr_finish(PcgScalars* sc, const double* out, bo
             sc->beta = beta;
             sc->pq = den;
             sc->alpha = gam / den;
-            if (XO) sc->pend = 1;
         }
     }
 }
 
-// XO: the cross term <r~, A~ p~_old> = (<r~, r~_old> - <r~, r~>) / alpha_old from the previous
-// residual, still in the other r~ half (one more read here instead of a sum in the update kernel,
-// which then needs no reduction and books nothing: this kernel books it, through sc->pend)
-template <int V, int NC, int MINB, bool UNR, bool XO>
+template <int V, int NC, int MINB, bool UNR>
 __global__ void __launch_bounds__(kThreads, MINB) k_cgr32(Dims d, const float* __restrict__ ra,
                                                           const float* __restrict__ rb, OpTab<float> t,
                                                           const double* __restrict__ dg, PcgScalars* sc,
                                                           double* __restrict__ partials) {
     if (sc->done) return;
-    const int pend = XO ? sc->pend : 0;
-    const int cur = pend ? 1 - sc->par : sc->par;
-    const float* __restrict__ r = cur ? rb : ra;
-    // r~_old is the previous recursive residual except right after a residual replacement
-    const bool xo = XO && pend;
-    const float* __restrict__ rold = xo ? (cur ? ra : rb) : nullptr;
+    const float* __restrict__ r = sc->par ? rb : ra;
     const int nt = d.nt;
     const unsigned int G = (unsigned int)(d.N / V);
-    Acc<float> a_g, a_d, a_x;
+    Acc<float> a_g, a_d;
     double a_rr = 0.0;
     for (unsigned int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
         const Cell c = decompose<V>(d, g);
@@ -763,13 +735,11 @@ __global__ void __launch_bounds__(kThreads, MINB) k_cgr32(Dims d, const float* _
         if constexpr (UNR) {
 #pragma unroll
             for (int k = 0; k < NC; k++)
-                cgr_component<V, XO>(d, c, nb, r + k * d.N, row, km, kp, cr_lo, cr_hi, ct_lo, ct_hi, cp, rs, a_d,
-                                     rold ? rold + k * d.N : nullptr, a_x);
+                cgr_component<V>(d, c, nb, r + k * d.N, row, km, kp, cr_lo, cr_hi, ct_lo, ct_hi, cp, rs, a_d);
         } else {
 #pragma unroll 1
             for (int k = 0; k < NC; k++)
-                cgr_component<V, XO>(d, c, nb, r + k * d.N, row, km, kp, cr_lo, cr_hi, ct_lo, ct_hi, cp, rs, a_d,
-                                     rold ? rold + k * d.N : nullptr, a_x);
+                cgr_component<V>(d, c, nb, r + k * d.N, row, km, kp, cr_lo, cr_hi, ct_lo, ct_hi, cp, rs, a_d);
         }
         float cell = rs[0];
 #pragma unroll
@@ -777,115 +747,20 @@ __global__ void __launch_bounds__(kThreads, MINB) k_cgr32(Dims d, const float* _
         a_g.add(cell);
         a_rr = fma(dg[c.ij], (double)cell, a_rr);
     }
-    double val[4] = {a_g.get(), a_d.get(), a_rr, a_x.get()}, out[4];
-    if (reduce_last<XO ? 4 : 3>(*reinterpret_cast<double(*)[XO ? 4 : 3]>(val), partials, &sc->count,
-                                *reinterpret_cast<double(*)[XO ? 4 : 3]>(out)) &&
-        threadIdx.x == 0) {
-        cgr_finish<XO>(sc, out, xo, pend);
-    }
-}
-
-// R as a plane-marching kernel (np % 4 == 0): a CTA owns `rows` whole phi rows of L consecutive
-// planes in r (1D grid: row tile fastest); each thread owns one float4 group of one row and walks
-// its planes keeping r~ of planes i-1, i, i+1 in registers, loading plane i+2 one step ahead. Each
-// value of r~ is loaded from DRAM once (the slab's two halo planes aside); the theta and phi
-// neighbours are L1/L2 hits. The stop-test norm is summed in compensated FP32 (the plane walk does
-// not hold a cell's components together).
-template <int NC, int MINB, bool XO>
-__global__ void __launch_bounds__(kThreads, MINB) k_cgr32m(Dims d, const float* __restrict__ ra,
-                                                           const float* __restrict__ rb, OpTab<float> t,
-                                                           const double* __restrict__ dg, PcgScalars* sc,
-                                                           double* __restrict__ partials, int rows, int L) {
-    if (sc->done) return;
-    const int pend = XO ? sc->pend : 0;
-    const int cur = pend ? 1 - sc->par : sc->par;
-    const float* __restrict__ r = cur ? rb : ra;
-    const bool xo = XO && pend;
-    const float* __restrict__ rold = xo ? (cur ? ra : rb) : nullptr;
-    const int nt = d.nt, np = d.np;
-    const int tpr = np / 4;
-    const int ntiles = (nt + rows - 1) / rows;
-    const int tile = (int)(blockIdx.x % (unsigned)ntiles), slab = (int)(blockIdx.x / (unsigned)ntiles);
-    const int jr = threadIdx.x / tpr, kg = threadIdx.x - jr * tpr;
-    const int j = tile * rows + jr;
-    const int i0 = slab * L, i1 = min(i0 + L, d.nr);
-    Acc<float> a_g, a_d, a_x, a_r;
-    if (jr < rows && j < nt) {
-        const int k0 = 4 * kg;
-        const long long plane = (long long)nt * np;
-        const long long row = (long long)j * np;
-        const long long col = row + k0;
-        const int km = (k0 == 0) ? np - 1 : k0 - 1, kp = (k0 + 4 == np) ? 0 : k0 + 4;
-        const long long jm = (j > 0) ? -(long long)np : 0, jp = (j < nt - 1) ? (long long)np : 0;
-#pragma unroll 1
-        for (int c = 0; c < NC; c++) {
-            const float* __restrict__ u = r + c * d.N;
-            float pm[4], cu[4], nx[4], nn[4];
-            ldv<float, 4>(u + (long long)(i0 > 0 ? i0 - 1 : i0) * plane + col, pm);
-            ldv<float, 4>(u + (long long)i0 * plane + col, cu);
-            ldv<float, 4>(u + (long long)(i0 + 1 < d.nr ? i0 + 1 : i0) * plane + col, nx);
-#pragma unroll 1
-            for (int i = i0; i < i1; i++) {
-                // plane i+2, clamped at the outer wall (its coefficient there is 0), one step ahead
-                if (i + 1 < i1) ldv<float, 4>(u + (long long)(i + 2 < d.nr ? i + 2 : d.nr - 1) * plane + col, nn);
-                const float* __restrict__ uc = u + (long long)i * plane;
-                float a[4], b[4];
-                ldv<float, 4>(uc + col + jm, a);
-                ldv<float, 4>(uc + col + jp, b);
-                const float ukm = uc[row + km], ukp = uc[row + kp];
-                const int ij = i * nt + j;
-                const float cr_lo = t.ar[ij], cr_hi = t.ar[ij + nt];
-                const float ct_lo = t.at[i * (nt + 1) + j], ct_hi = t.at[i * (nt + 1) + j + 1];
-                const float cp = t.ap[ij];
-                float s2 = 0.f;
-#pragma unroll
-                for (int e = 0; e < 4; e++) {
-                    const float left = (e == 0) ? ukm : cu[e - 1];
-                    const float right = (e == 3) ? ukp : cu[e + 1];
-                    float o = fmaf(-cp, left + right, cu[e]);
-                    o = fmaf(-cr_lo, pm[e], o);
-                    o = fmaf(-cr_hi, nx[e], o);
-                    o = fmaf(-ct_lo, a[e], o);
-                    o = fmaf(-ct_hi, b[e], o);
-                    s2 = fmaf(cu[e], cu[e], s2);
-                    a_d.fma_add(cu[e], o);
-                }
-                a_g.add(s2);
-                a_r.fma_add((float)dg[ij], s2);
-                if (xo) {
-                    float ro[4];
-                    ldv<float, 4>(rold + c * d.N + (long long)i * plane + col, ro);
-#pragma unroll
-                    for (int e = 0; e < 4; e++) a_x.fma_add(cu[e], ro[e]);
-                }
-#pragma unroll
-                for (int e = 0; e < 4; e++) {
-                    pm[e] = cu[e];
-                    cu[e] = nx[e];
-                    nx[e] = nn[e];
-                }
-            }
-        }
-    }
-    double val[4] = {a_g.get(), a_d.get(), a_r.get(), a_x.get()}, out[4];
-    if (reduce_last<XO ? 4 : 3>(*reinterpret_cast<double(*)[XO ? 4 : 3]>(val), partials, &sc->count,
-                                *reinterpret_cast<double(*)[XO ? 4 : 3]>(out)) &&
-        threadIdx.x == 0) {
-        cgr_finish<XO>(sc, out, xo, pend);
-    }
+    double val[3] = {a_g.get(), a_d.get(), a_rr}, out[3];
+    if (reduce_last<3>(val, partials, &sc->count, out) && threadIdx.x == 0) cgr_finish(sc, out);
 }
 
 // U (k_cgu32): p~ = r~ + beta p~_old at the cell and its neighbours, q~ = A~ p~ at the cell,
 // r~ -= alpha q~ into the other r~ half, p~ into the other p~ half, <r~_new, q~> for the next
 // denominator; x~ += alpha p~ + ax p~_old every second iteration (p~_old is at hand: the pending
 // update is always the previous p~). Last CTA: parity flip, deferred alpha, iteration count.
-// RED = false: no cross-term sum and no booking (the next residual kernel reads r~_old and books)
-template <int V, int NC, int MINB, bool RED>
+template <int V, int NC, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB) k_cgu32(Dims d, float* __restrict__ x, float* __restrict__ ra,
                                                        float* __restrict__ rb, float* __restrict__ pbuf,
                                                        OpTab<float> t, PcgScalars* sc,
                                                        double* __restrict__ partials) {
-    if (sc->done || (!RED && !sc->pend)) return;
+    if (sc->done) return;
     const int par = sc->par;
     const float* __restrict__ r = par ? rb : ra;
     float* __restrict__ rn = par ? ra : rb;
@@ -938,7 +813,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_cgu32(Dims d, float* __restr
                 o[e] = fmaf(-ct_lo, fmaf(beta, c1[e], c0[e]), o[e]);
                 o[e] = fmaf(-ct_hi, fmaf(beta, e1[e], e0[e]), o[e]);
                 rv[e] = fmaf(-al, o[e], rv[e]);
-                if constexpr (RED) a_rq = fmaf(rv[e], o[e], a_rq);
+                a_rq = fmaf(rv[e], o[e], a_rq);
             }
             stv<float, V>(rn + k * d.N + c.base, rv);
             if (pair) {
@@ -950,7 +825,6 @@ __global__ void __launch_bounds__(kThreads, MINB) k_cgu32(Dims d, float* __restr
             }
         }
     }
-    if constexpr (!RED) return;
     double val[1] = {(double)a_rq}, out[1];
     if (reduce_last<1>(val, partials, &sc->count, out) && threadIdx.x == 0) {
         sc->wp = out[0];
@@ -1461,67 +1335,29 @@ void enqueue_recompute32_var(mhd_grid_s* g, cudaStream_t st, int nc) {
     else enqueue_recompute32_nc<V, 4>(g, st, nc, g->slab32 == -4);
 }
 
-template <int V, int NC, int MINB_R, bool UNR, bool XO, int MINB_U, bool RED>
+template <int V, int NC, int MINB_R, bool UNR, int MINB_U>
 void enqueue_cgpair32_k(mhd_grid_s* g, cudaStream_t st) {
     const Dims d = g->d;
     int s = prof_begin(g, st, MHD_KERNEL_CGR32);
-    k_cgr32<V, NC, MINB_R, UNR, XO>
-        <<<grid_blocks(g, d.N / V, resident_per_sm<k_cgr32<V, NC, MINB_R, UNR, XO>>()), kThreads, 0, st>>>(
-            d, g->r32, g->q32, g->t32, g->tu.dg, g->sc, g->partials);
+    k_cgr32<V, NC, MINB_R, UNR><<<grid_blocks(g, d.N / V, resident_per_sm<k_cgr32<V, NC, MINB_R, UNR>>()), kThreads,
+                                  0, st>>>(d, g->r32, g->q32, g->t32, g->tu.dg, g->sc, g->partials);
     prof_end(g, st, s);
     s = prof_begin(g, st, MHD_KERNEL_CGU32);
-    k_cgu32<V, NC, MINB_U, RED><<<grid_blocks(g, d.N / V, resident_per_sm<k_cgu32<V, NC, MINB_U, RED>>()), kThreads,
-                                  0, st>>>(d, g->x32, g->r32, g->q32, g->p32, g->t32, g->sc, g->partials);
-    prof_end(g, st, s);
-}
-
-// launch shape of the plane-marching residual kernel: whole phi rows per CTA (np % 4 == 0, full
-// warps), slabs of L planes with L doubled until the 1D grid fits the partial-sum array
-bool cgr_march_shape(const mhd_grid_s* g, int* rows, int* L, int* blocks, int* threads) {
-    const Dims d = g->d;
-    if (d.np % 4) return false;
-    const int tpr = d.np / 4;
-    if (tpr > kThreads) return false;
-    *rows = kThreads / tpr;
-    *threads = *rows * tpr;
-    if (*threads % 32) return false;
-    const int ntiles = (d.nt + *rows - 1) / *rows;
-    *L = 16;
-    while ((long long)ntiles * ((d.nr + *L - 1) / *L) > kMaxBlocks) *L *= 2;
-    *blocks = ntiles * ((d.nr + *L - 1) / *L);
-    return true;
-}
-
-template <int V, int NC, bool XO, int MINB_U, bool RED>
-void enqueue_cgpair32_m(mhd_grid_s* g, cudaStream_t st) {
-    int rows, L, blocks, threads;
-    if (V != 4 || !cgr_march_shape(g, &rows, &L, &blocks, &threads)) {
-        enqueue_cgpair32_k<V, NC, 3, true, XO, MINB_U, RED>(g, st);
-        return;
-    }
-    const Dims d = g->d;
-    int s = prof_begin(g, st, MHD_KERNEL_CGR32);
-    k_cgr32m<NC, 4, XO><<<blocks, threads, 0, st>>>(d, g->r32, g->q32, g->t32, g->tu.dg, g->sc, g->partials, rows, L);
-    prof_end(g, st, s);
-    s = prof_begin(g, st, MHD_KERNEL_CGU32);
-    k_cgu32<V, NC, MINB_U, RED><<<grid_blocks(g, d.N / V, resident_per_sm<k_cgu32<V, NC, MINB_U, RED>>()), kThreads,
-                                  0, st>>>(d, g->x32, g->r32, g->q32, g->p32, g->t32, g->sc, g->partials);
+    k_cgu32<V, NC, MINB_U><<<grid_blocks(g, d.N / V, resident_per_sm<k_cgu32<V, NC, MINB_U>>()), kThreads, 0, st>>>(
+        d, g->x32, g->r32, g->q32, g->p32, g->t32, g->sc, g->partials);
     prof_end(g, st, s);
 }
 
 // -6: both kernels at 4 CTAs per SM; -7: the residual kernel unrolled over the components, both at 3;
-// -8: unrolled residual kernel at 3, update kernel at 4; -9: unrolled residual kernel reading r~_old
-// for the cross term, update kernel at 4 without a reduction; -10, -11: -8, -9 with the
-// plane-marching residual kernel
+// -8: unrolled residual kernel at 3, update kernel at 4. (Measured slower and removed: the cross
+// term from the previous residual read by the residual kernel, its update kernel without a
+// reduction: 0.286 + 0.355 ms; a plane-marching residual kernel: 0.208 against 0.165 ms.)
 template <int V, int NC>
 void enqueue_cgpair32(mhd_grid_s* g, cudaStream_t st) {
     switch (g->slab32) {
-        case -10: enqueue_cgpair32_m<V, NC, false, 4, true>(g, st); break;
-        case -11: enqueue_cgpair32_m<V, NC, true, 4, false>(g, st); break;
-        case -7: enqueue_cgpair32_k<V, NC, 3, true, false, 3, true>(g, st); break;
-        case -8: enqueue_cgpair32_k<V, NC, 3, true, false, 4, true>(g, st); break;
-        case -9: enqueue_cgpair32_k<V, NC, 3, true, true, 4, false>(g, st); break;
-        default: enqueue_cgpair32_k<V, NC, 4, false, false, 4, true>(g, st); break;
+        case -7: enqueue_cgpair32_k<V, NC, 3, true, 3>(g, st); break;
+        case -8: enqueue_cgpair32_k<V, NC, 3, true, 4>(g, st); break;
+        default: enqueue_cgpair32_k<V, NC, 4, false, 4>(g, st); break;
     }
 }
 
@@ -1645,7 +1481,7 @@ void enqueue_iteration(mhd_grid_s* g, cudaStream_t st, int prec, int nc) {
     } else if (g->slab32 <= -100) {
         // plane-marching pair with bulk-copy staging, when the autotuner measured it fastest
         enqueue_bulk32(g, st, nc, -100 - g->slab32);
-    } else if (g->slab32 <= -6 && g->slab32 >= -11) {
+    } else if (g->slab32 <= -6 && g->slab32 >= -8) {
         // single-reduction pair (residual kernel, then the update), when measured fastest
         if (use_v4(g)) enqueue_cgpair32_nc<4>(g, st, nc);
         else enqueue_cgpair32_nc<2>(g, st, nc);
@@ -1740,7 +1576,6 @@ __global__ void k_setup(PcgScalars* sc, double tol, double inner_tol, int max_it
     sc->rho_prev = 0.0;
     sc->par = 0;
     sc->ax = 0.0;
-    sc->pend = 0;
     sc->count = 0u;
 }
 
@@ -1771,7 +1606,6 @@ __global__ void k_tune_reset(PcgScalars* sc) {
     sc->max_iter = 1 << 30;
     sc->par = 0;
     sc->ax = 0.0;
-    sc->pend = 0;
     sc->count = 0u;
 }
 
@@ -1788,7 +1622,7 @@ int forced_slab() {
 mhd_status_t tune_slab32(mhd_grid_s* g, int nc) {
     if (g->slab32 != 0) return MHD_OK;
     if (const int f = forced_slab()) {
-        if (f <= -2 && f >= -11) g->slab32 = f;
+        if (f <= -2 && f >= -8) g->slab32 = f;
         else if (f <= -100) g->slab32 = (bulk32_ok(g) && f < -100) ? f : -1;
         else g->slab32 = (f > 0 && tiled32_ok(g) && tiled32_blocks(g, f) <= kMaxBlocks) ? f : -1;
         return MHD_OK;
@@ -1806,13 +1640,11 @@ mhd_status_t tune_slab32(mhd_grid_s* g, int nc) {
     // the stencil, then the update; -3, -4, -5: the recompute pair (no q~ stored), forwards, with
     // the r update walking backwards, or at 6 CTAs per SM; -6, -7, -8: the single-reduction pair
     // (-7: its residual kernel unrolled over the components and both kernels at 3 CTAs per SM; -8:
-    // the unrolled residual kernel with the update kernel at 4; -9: the cross term from r~_old in
-    // the residual kernel, the update kernel without a reduction; -10, -11: -8, -9 with a
-    // plane-marching residual kernel); -132,
+    // the unrolled residual kernel with the update kernel at 4); -132,
     // -164: the recompute pair as plane-marching kernels staged by bulk copies (units of 32 or 64
     // planes). Four iterations each after one untimed: an even count, so each is timed with its
     // x updates.
-    for (int cand : {-1, -2, -3, -4, -5, -6, -7, -8, -9, -10, -11, -132, -164}) {
+    for (int cand : {-1, -2, -3, -4, -5, -6, -7, -8, -132, -164}) {
         if (cand <= -100 && !bulk32_ok(g)) continue;
         k_tune_reset<<<1, 1, 0, g->stream>>>(g->sc);
         g->slab32 = cand;
@@ -1995,7 +1827,7 @@ mhd_status_t solve(mhd_grid_s* g, const double* alpha_dev, int nc, const double*
         const int ps = prof_begin(g, g->stream, MHD_KERNEL_OUTER_RES);
         const int restart = (o == 0 || prm->mixed_restart) ? 1 : 0;
         k_outer_res<2><<<grid_blocks(g, d.N / 2, resident_per_sm<k_outer_res<2>>()), kThreads, 0, g->stream>>>(
-            d, nc, b, x, g->r32, (!pc2 && g->slab32 <= -6 && g->slab32 >= -11) ? g->q32 : nullptr, g->p32, g->x32, g->t64, g->tu, g->sc,
+            d, nc, b, x, g->r32, (!pc2 && g->slab32 <= -6 && g->slab32 >= -8) ? g->q32 : nullptr, g->p32, g->x32, g->t64, g->tu, g->sc,
             g->partials, o == 0 ? 1 : 0, restart, pc2 ? 1 : 0, g->t32);
         if (pc2) pc2_reliable32(g, nc, restart);
         prof_end(g, g->stream, ps);
