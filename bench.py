@@ -459,6 +459,9 @@ def run_ours(args):
                     pcg_gbs=round(pcg32_gbs, 1), pcg_frac_of_hbm=round(pcg32_gbs / hbm, 4),
                     kernels=kernels, fp32_kernels=("plane-marching pair (A: p update + stencil, B: stencil + "
                                                    "update)" if tiled else
+                                                   "single-reduction pair (residual kernel: gamma, delta, "
+                                                   "stop norm; update kernel: p, A p, r, x every second "
+                                                   "iteration)" if profm["cgr32"][1] > 0 else
                                                    "recompute pair (p update folded into <p, Ap>; r update "
                                                    "with Ap recomputed, x every second iteration)" if recompute
                                                    else
