@@ -125,7 +125,7 @@ enum { MHD_PREC_FP64 = 0, MHD_PREC_MIXED = 1 };
  * folded, -3 recompute pair, -4 recompute pair with the second kernel walking the grid backwards,
  * -5 recompute pair at 6 CTAs per SM, -6 / -7 / -8 single-reduction pair (-7: its residual kernel
  * unrolled over the components, both kernels at 3 CTAs per SM; -8: unrolled residual kernel,
- * update kernel at 4; -9: the pair split by component and pipelined over two streams), -64 the FP64 iteration with its components overlapped on two
+ * update kernel at 4), -64 the FP64 iteration with its components overlapped on two
  * streams,
  * n > 0 tiles of n planes). */
 typedef struct {

@@ -327,8 +327,7 @@ mhd_status_t create_grid(const mhd_grid_desc_t* desc, int i0, int i1, bool as_sl
          dalloc(&g->slab_out, 8 + 2 * (size_t)nt, owned);
     g->slab_i0 = slab ? i0 : 0;
     g->slab_nr_global = slab ? dg.nr : 0;
-    // two partial-sum areas (the second for kernels on the second stream), 16 spare doubles between
-    ok = ok && dalloc(&g->partials, 2 * (size_t)kMaxBlocks * kPartialsPerBlock + 16, owned) &&
+    ok = ok && dalloc(&g->partials, (size_t)kMaxBlocks * kPartialsPerBlock + 16, owned) &&
          dalloc(&g->sc, 1, owned) && dalloc(&g->ss, 1, owned);
     if (!ok) {
         for (void* m : owned) cudaFree(m);

@@ -40,10 +40,6 @@ struct PcgScalars {
     double ax;       // alpha of the last CG iteration whose alpha p~ has not yet been added to x~
     double pqc[3];   // per-component shares of <p~, q~> (FP64 iteration with the components overlapped)
     double wp;       // FP32 single-reduction pair: <r~, A~ p~_old> summed by the update kernel
-    double cg3[3][3];  // pipelined pair: per-component gamma, delta, stop norm of the residual kernels
-    double wpc[3];   // pipelined pair: per-component cross terms of the update kernels
-    int pend;        // pipelined pair: update kernels ran since the last scalar kernel
-    unsigned int count2;  // last-block ticket of kernels on the grid's second stream
 };
 
 // Device-resident scalars of one step.

@@ -835,157 +835,6 @@ __global__ void __launch_bounds__(kThreads, MINB) k_cgu32(Dims d, float* __restr
     }
 }
 
-// Pipelined form of the pair (-9): the kernels split by component, so that the residual kernel of
-// component c for the next iteration (second stream) runs beside the update kernel of component
-// c+1 (grid stream): two latency-bound kernels on the SMs at once. Per-component sums go to
-// sc->cg3 / sc->wpc; a one-thread kernel combines them, books the update kernels of the previous
-// iteration and forms the scalars. The residual kernels of the first iteration after a residual
-// replacement run before the inner loop (the prologue in the mixed solve).
-template <int V, int MINB>
-__global__ void __launch_bounds__(kThreads, MINB) k_cgr32c(Dims d, int c, const float* __restrict__ ra,
-                                                           const float* __restrict__ rb, OpTab<float> t,
-                                                           const double* __restrict__ dg, PcgScalars* sc,
-                                                           double* __restrict__ partials, unsigned int* count) {
-    if (sc->done) return;
-    const float* __restrict__ r = ((sc->pend ? 1 - sc->par : sc->par) ? rb : ra) + (long long)c * d.N;
-    const int nt = d.nt;
-    const unsigned int G = (unsigned int)(d.N / V);
-    Acc<float> a_g, a_d;
-    double a_rr = 0.0;
-    for (unsigned int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
-        const Cell cl = decompose<V>(d, g);
-        const Nbr<V> nb(d, cl);
-        const float cr_lo = t.ar[cl.i * nt + cl.j], cr_hi = t.ar[(cl.i + 1) * nt + cl.j];
-        const float ct_lo = t.at[cl.i * (nt + 1) + cl.j], ct_hi = t.at[cl.i * (nt + 1) + cl.j + 1];
-        const float cp = t.ap[cl.ij];
-        const long long row = cl.base - cl.k0;
-        const int km = (cl.k0 == 0) ? d.np - 1 : cl.k0 - 1;
-        const int kp = (cl.k0 + V == d.np) ? 0 : cl.k0 + V;
-        float rs[V];
-        zerov<float, V>(rs);
-        cgr_component<V>(d, cl, nb, r, row, km, kp, cr_lo, cr_hi, ct_lo, ct_hi, cp, rs, a_d);
-        float cell = rs[0];
-#pragma unroll
-        for (int e = 1; e < V; e++) cell += rs[e];
-        a_g.add(cell);
-        a_rr = fma(dg[cl.ij], (double)cell, a_rr);
-    }
-    double val[3] = {a_g.get(), a_d.get(), a_rr}, out[3];
-    if (reduce_last<3>(val, partials, count, out) && threadIdx.x == 0) {
-        sc->cg3[c][0] = out[0];
-        sc->cg3[c][1] = out[1];
-        sc->cg3[c][2] = out[2];
-    }
-}
-
-template <int V, int MINB>
-__global__ void __launch_bounds__(kThreads, MINB) k_cgu32c(Dims d, int c, float* __restrict__ x,
-                                                           float* __restrict__ ra, float* __restrict__ rb,
-                                                           float* __restrict__ pbuf, OpTab<float> t, PcgScalars* sc,
-                                                           double* __restrict__ partials) {
-    if (sc->done || !sc->pend) return;
-    const int par = sc->par;
-    const long long co = (long long)c * d.N;
-    const float* __restrict__ rk = (par ? rb : ra) + co;
-    float* __restrict__ rn = (par ? ra : rb) + co;
-    const float* __restrict__ pk = pbuf + (long long)par * 3 * d.N + co;
-    float* __restrict__ pnew = pbuf + (long long)(1 - par) * 3 * d.N + co;
-    float* __restrict__ xk = x + co;
-    const float beta = (float)sc->beta, al = (float)sc->alpha, axp = (float)sc->ax;
-    const bool pair = (sc->ax != 0.0);
-    const int nt = d.nt;
-    const unsigned int G = (unsigned int)(d.N / V);
-    float a_rq = 0.f;
-    for (unsigned int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
-        const Cell cl = decompose<V>(d, g);
-        const Nbr<V> nb(d, cl);
-        const float cr_lo = t.ar[cl.i * nt + cl.j], cr_hi = t.ar[(cl.i + 1) * nt + cl.j];
-        const float ct_lo = t.at[cl.i * (nt + 1) + cl.j], ct_hi = t.at[cl.i * (nt + 1) + cl.j + 1];
-        const float cp = t.ap[cl.ij];
-        const long long row = cl.base - cl.k0;
-        const int km = (cl.k0 == 0) ? d.np - 1 : cl.k0 - 1;
-        const int kp = (cl.k0 + V == d.np) ? 0 : cl.k0 + V;
-        float rv[V], pv[V], v[V], o[V], a0[V], a1[V], b0[V], b1[V], c0[V], c1[V], e0[V], e1[V];
-        ldv<float, V>(rk + cl.base, rv);
-        ldv<float, V>(pk + cl.base, pv);
-        const float rkm = rk[row + km], pkm = pk[row + km], rkp = rk[row + kp], pkp = pk[row + kp];
-        ldv<float, V>(rk + cl.base + nb.im, a0);
-        ldv<float, V>(pk + cl.base + nb.im, a1);
-        ldv<float, V>(rk + cl.base + nb.ip, b0);
-        ldv<float, V>(pk + cl.base + nb.ip, b1);
-        ldv<float, V>(rk + cl.base + nb.jm, c0);
-        ldv<float, V>(pk + cl.base + nb.jm, c1);
-        ldv<float, V>(rk + cl.base + nb.jp, e0);
-        ldv<float, V>(pk + cl.base + nb.jp, e1);
-#pragma unroll
-        for (int e = 0; e < V; e++) v[e] = fmaf(beta, pv[e], rv[e]);
-        stv<float, V>(pnew + cl.base, v);
-        const float ukm = fmaf(beta, pkm, rkm);
-        const float ukp = fmaf(beta, pkp, rkp);
-#pragma unroll
-        for (int e = 0; e < V; e++) {
-            const float left = (e == 0) ? ukm : v[e - 1];
-            const float right = (e == V - 1) ? ukp : v[e + 1];
-            o[e] = fmaf(-cp, left + right, v[e]);
-            o[e] = fmaf(-cr_lo, fmaf(beta, a1[e], a0[e]), o[e]);
-            o[e] = fmaf(-cr_hi, fmaf(beta, b1[e], b0[e]), o[e]);
-            o[e] = fmaf(-ct_lo, fmaf(beta, c1[e], c0[e]), o[e]);
-            o[e] = fmaf(-ct_hi, fmaf(beta, e1[e], e0[e]), o[e]);
-            rv[e] = fmaf(-al, o[e], rv[e]);
-            a_rq = fmaf(rv[e], o[e], a_rq);
-        }
-        stv<float, V>(rn + cl.base, rv);
-        if (pair) {
-            float xv[V];
-            ldv<float, V>(xk + cl.base, xv);
-#pragma unroll
-            for (int e = 0; e < V; e++) xv[e] = fmaf(al, v[e], fmaf(axp, pv[e], xv[e]));
-            stv<float, V>(xk + cl.base, xv);
-        }
-    }
-    double val[1] = {(double)a_rq}, out[1];
-    if (reduce_last<1>(val, partials, &sc->count, out) && threadIdx.x == 0) sc->wpc[c] = out[0];
-}
-
-// the scalars of the pipelined pair (one thread): book the update kernels of the previous
-// iteration, combine the components' sums, stop test, beta and alpha
-__global__ void k_cg_scalars(PcgScalars* sc, int nc) {
-    if (sc->done) return;
-    if (sc->pend) {
-        sc->par = 1 - sc->par;
-        sc->ax = (sc->ax != 0.0) ? 0.0 : sc->alpha;
-        sc->iter += 1;
-        sc->total_iter += 1;
-        sc->pend = 0;
-    }
-    double gam = 0.0, del = 0.0, rr = 0.0, wps = 0.0;
-    for (int c = 0; c < nc; c++) {
-        gam += sc->cg3[c][0];
-        del += sc->cg3[c][1];
-        rr += sc->cg3[c][2];
-        wps += sc->wpc[c];
-    }
-    const double beta = (sc->iter == 0) ? sc->beta : gam / sc->rho;
-    const double wp = (sc->iter == 0) ? sc->wp : wps;   // after a replacement: the residual kernel's
-    sc->rho_prev = sc->rho;
-    sc->rho = gam;
-    sc->rr = rr;
-    if (!finite(gam) || !finite(del) || !finite(rr)) sc->done = 3;
-    else if (sqrt(rr) <= sc->tol * sqrt(sc->bb)) sc->done = 1;
-    else if (sc->iter >= sc->max_iter) sc->done = 2;
-    else {
-        const double den = (beta == 0.0) ? del : del + beta * (2.0 * wp + beta * sc->pq);
-        if (!finite(den)) sc->done = 3;
-        else if (!(den > 0.0)) sc->done = 4;
-        else {
-            sc->beta = beta;
-            sc->pq = den;
-            sc->alpha = gam / den;
-            sc->pend = 1;
-        }
-    }
-}
-
 // ------------------------------------------------------------------------------------------
 // single-reduction (Chronopoulos-Gear) form, FP64: s = A~ p is carried by its own recurrence,
 // so one stencil pass w = A~ r yields every inner product of an iteration
@@ -1512,57 +1361,6 @@ void enqueue_cgpair32(mhd_grid_s* g, cudaStream_t st) {
     }
 }
 
-// pipelined pair (-9): residual kernel of one component, on stream st with its own partial sums
-template <int V>
-void enqueue_cgr32c(mhd_grid_s* g, cudaStream_t st, int c, int per_sm, bool second) {
-    const Dims d = g->d;
-    double* partials = second ? g->partials + (size_t)kMaxBlocks * kPartialsPerBlock + 16 : g->partials;
-    unsigned int* count = second ? &g->sc->count2 : &g->sc->count;
-    const int s = prof_begin(g, st, MHD_KERNEL_CGR32);
-    k_cgr32c<V, 3><<<grid_blocks(g, d.N / V, per_sm), kThreads, 0, st>>>(d, c, g->r32, g->q32, g->t32, g->tu.dg,
-                                                                         g->sc, partials, count);
-    prof_end(g, st, s);
-}
-
-// the residual kernels of the current r~ (after a residual replacement, ahead of the inner loop)
-template <int V>
-void enqueue_cgpipe_prologue(mhd_grid_s* g, cudaStream_t st, int nc) {
-    for (int c = 0; c < nc; c++) enqueue_cgr32c<V>(g, st, c, 3, false);
-}
-
-// one iteration: scalars; the update kernel of each component (grid stream), the next iteration's
-// residual kernel of component c on the second stream beside the update of c+1; the last
-// component's residual kernel on the grid stream; the second stream joins at the end
-template <int V>
-void enqueue_cgpipe(mhd_grid_s* g, cudaStream_t st, int nc) {
-    const Dims d = g->d;
-    cudaStream_t sd = g->side;
-    k_cg_scalars<<<1, 1, 0, st>>>(g->sc, nc);
-    for (int c = 0; c < nc; c++) {
-        const int s = prof_begin(g, st, MHD_KERNEL_CGU32);
-        // alone for the first component, beside a residual kernel (1 CTA per SM) for the others
-        k_cgu32c<V, 3><<<grid_blocks(g, d.N / V, c == 0 ? 3 : 2), kThreads, 0, st>>>(
-            d, c, g->x32, g->r32, g->q32, g->p32, g->t32, g->sc, g->partials);
-        prof_end(g, st, s);
-        if (c < nc - 1) {
-            cudaEventRecord(g->side_ev[c], st);
-            cudaStreamWaitEvent(sd, g->side_ev[c], 0);
-            enqueue_cgr32c<V>(g, sd, c, 1, true);
-        } else {
-            enqueue_cgr32c<V>(g, st, c, 3, false);
-        }
-    }
-    if (nc > 1) {
-        cudaEventRecord(g->side_ev[3], sd);
-        cudaStreamWaitEvent(st, g->side_ev[3], 0);
-    }
-}
-
-void cgpipe_prologue(mhd_grid_s* g, cudaStream_t st, int nc) {
-    if (use_v4(g)) enqueue_cgpipe_prologue<4>(g, st, nc);
-    else enqueue_cgpipe_prologue<2>(g, st, nc);
-}
-
 template <int V>
 void enqueue_cgpair32_nc(mhd_grid_s* g, cudaStream_t st, int nc) {
     if (nc == 3) enqueue_cgpair32<V, 3>(g, st);
@@ -1683,10 +1481,6 @@ void enqueue_iteration(mhd_grid_s* g, cudaStream_t st, int prec, int nc) {
     } else if (g->slab32 <= -100) {
         // plane-marching pair with bulk-copy staging, when the autotuner measured it fastest
         enqueue_bulk32(g, st, nc, -100 - g->slab32);
-    } else if (g->slab32 == -9 && g->side) {
-        // pipelined single-reduction pair, when measured fastest
-        if (use_v4(g)) enqueue_cgpipe<4>(g, st, nc);
-        else enqueue_cgpipe<2>(g, st, nc);
     } else if (g->slab32 <= -6 && g->slab32 >= -8) {
         // single-reduction pair (residual kernel, then the update), when measured fastest
         if (use_v4(g)) enqueue_cgpair32_nc<4>(g, st, nc);
@@ -1782,9 +1576,7 @@ __global__ void k_setup(PcgScalars* sc, double tol, double inner_tol, int max_it
     sc->rho_prev = 0.0;
     sc->par = 0;
     sc->ax = 0.0;
-    sc->pend = 0;
     sc->count = 0u;
-    sc->count2 = 0u;
 }
 
 // mixed: the inner stop test reuses k_update's sqrt(rr) <= tol*sqrt(bb) by swapping in
@@ -1814,9 +1606,7 @@ __global__ void k_tune_reset(PcgScalars* sc) {
     sc->max_iter = 1 << 30;
     sc->par = 0;
     sc->ax = 0.0;
-    sc->pend = 0;
     sc->count = 0u;
-    sc->count2 = 0u;
 }
 
 // choose the r-slab length of the tiled FP32 kernels by timing a few iterations of each
@@ -1832,7 +1622,7 @@ int forced_slab() {
 mhd_status_t tune_slab32(mhd_grid_s* g, int nc) {
     if (g->slab32 != 0) return MHD_OK;
     if (const int f = forced_slab()) {
-        if (f <= -2 && f >= -9) g->slab32 = (f == -9 && !g->side) ? -7 : f;
+        if (f <= -2 && f >= -8) g->slab32 = f;
         else if (f <= -100) g->slab32 = (bulk32_ok(g) && f < -100) ? f : -1;
         else g->slab32 = (f > 0 && tiled32_ok(g) && tiled32_blocks(g, f) <= kMaxBlocks) ? f : -1;
         return MHD_OK;
@@ -1850,20 +1640,17 @@ mhd_status_t tune_slab32(mhd_grid_s* g, int nc) {
     // the stencil, then the update; -3, -4, -5: the recompute pair (no q~ stored), forwards, with
     // the r update walking backwards, or at 6 CTAs per SM; -6, -7, -8: the single-reduction pair
     // (-7: its residual kernel unrolled over the components and both kernels at 3 CTAs per SM; -8:
-    // the unrolled residual kernel with the update kernel at 4; -9: the pair split by component and
-    // pipelined over two streams); -132,
+    // the unrolled residual kernel with the update kernel at 4); -132,
     // -164: the recompute pair as plane-marching kernels staged by bulk copies (units of 32 or 64
     // planes). Four iterations each after one untimed: an even count, so each is timed with its
     // x updates.
-    for (int cand : {-1, -2, -3, -4, -5, -6, -7, -8, -9, -132, -164}) {
+    for (int cand : {-1, -2, -3, -4, -5, -6, -7, -8, -132, -164}) {
         if (cand <= -100 && !bulk32_ok(g)) continue;
-        if (cand == -9 && !g->side) continue;
         k_tune_reset<<<1, 1, 0, g->stream>>>(g->sc);
         g->slab32 = cand;
         cudaMemsetAsync(g->r32, 0x3F, sizeof(float) * n3, g->stream);
         cudaMemsetAsync(g->p32, 0x3F, sizeof(float) * 2 * n3, g->stream);
         cudaMemsetAsync(g->x32, 0, sizeof(float) * n3, g->stream);
-        if (cand == -9) cgpipe_prologue(g, g->stream, nc);
         enqueue_iteration(g, g->stream, 1, nc);
         cudaEventRecord(e0, g->stream);
         for (int it = 0; it < 4; it++) enqueue_iteration(g, g->stream, 1, nc);
@@ -2040,7 +1827,7 @@ mhd_status_t solve(mhd_grid_s* g, const double* alpha_dev, int nc, const double*
         const int ps = prof_begin(g, g->stream, MHD_KERNEL_OUTER_RES);
         const int restart = (o == 0 || prm->mixed_restart) ? 1 : 0;
         k_outer_res<2><<<grid_blocks(g, d.N / 2, resident_per_sm<k_outer_res<2>>()), kThreads, 0, g->stream>>>(
-            d, nc, b, x, g->r32, (!pc2 && g->slab32 <= -6 && g->slab32 >= -9) ? g->q32 : nullptr, g->p32, g->x32, g->t64, g->tu, g->sc,
+            d, nc, b, x, g->r32, (!pc2 && g->slab32 <= -6 && g->slab32 >= -8) ? g->q32 : nullptr, g->p32, g->x32, g->t64, g->tu, g->sc,
             g->partials, o == 0 ? 1 : 0, restart, pc2 ? 1 : 0, g->t32);
         if (pc2) pc2_reliable32(g, nc, restart);
         prof_end(g, g->stream, ps);
@@ -2050,7 +1837,6 @@ mhd_status_t solve(mhd_grid_s* g, const double* alpha_dev, int nc, const double*
         outer_done = g->h_sc->outer_done;
         if (outer_done || o == prm->max_outer) break;
         k_inner_begin<<<1, 1, 0, g->stream>>>(g->sc, saved);
-        if (!pc2 && g->slab32 == -9 && g->side) cgpipe_prologue(g, g->stream, nc);
         st = run_iterations(g, pc2 ? 4 : 1, nc);
         if (st != MHD_OK) return st;
         k_inner_end<<<1, 1, 0, g->stream>>>(g->sc, saved);
