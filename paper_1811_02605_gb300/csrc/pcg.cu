@@ -663,7 +663,7 @@ template <int V>
 __device__ __forceinline__ void cgr_component(const Dims& d, const Cell& c, const Nbr<V>& nb, const float* rk,
                                               long long row, int km, int kp, float cr_lo, float cr_hi,
                                               float ct_lo, float ct_hi, float cp, float (&rs)[V],
-                                              Acc<float>& a_d) {
+                                              float& dsum) {
     float v[V], o[V], a[V], b[V], cc[V], e4[V];
     ldv<float, V>(rk + c.base, v);
     const float ukm = rk[row + km], ukp = rk[row + kp];
@@ -681,7 +681,7 @@ __device__ __forceinline__ void cgr_component(const Dims& d, const Cell& c, cons
         o[e] = fmaf(-ct_lo, cc[e], o[e]);
         o[e] = fmaf(-ct_hi, e4[e], o[e]);
         rs[e] = fmaf(v[e], v[e], rs[e]);
-        a_d.fma_add(v[e], o[e]);
+        dsum = fmaf(v[e], o[e], dsum);
     }
 }
 
@@ -732,15 +732,19 @@ __global__ void __launch_bounds__(kThreads, MINB) k_cgr32(Dims d, const float* _
         const int kp = (c.k0 + V == d.np) ? 0 : c.k0 + V;
         float rs[V];
         zerov<float, V>(rs);
+        // <r~, A~ r~> of the cell group in plain FP32 (at most 12 terms), then into the compensated
+        // per-thread sum once per group: a compensated add per term doubled the kernel's instructions
+        float dsum = 0.f;
         if constexpr (UNR) {
 #pragma unroll
             for (int k = 0; k < NC; k++)
-                cgr_component<V>(d, c, nb, r + k * d.N, row, km, kp, cr_lo, cr_hi, ct_lo, ct_hi, cp, rs, a_d);
+                cgr_component<V>(d, c, nb, r + k * d.N, row, km, kp, cr_lo, cr_hi, ct_lo, ct_hi, cp, rs, dsum);
         } else {
 #pragma unroll 1
             for (int k = 0; k < NC; k++)
-                cgr_component<V>(d, c, nb, r + k * d.N, row, km, kp, cr_lo, cr_hi, ct_lo, ct_hi, cp, rs, a_d);
+                cgr_component<V>(d, c, nb, r + k * d.N, row, km, kp, cr_lo, cr_hi, ct_lo, ct_hi, cp, rs, dsum);
         }
+        a_d.add(dsum);
         float cell = rs[0];
 #pragma unroll
         for (int e = 1; e < V; e++) cell += rs[e];
