@@ -119,15 +119,15 @@ enum { MHD_PREC_FP64 = 0, MHD_PREC_MIXED = 1 };
  *            factorisation and 3N floats for z of the FP32 iteration. pcg_solve_batched ignores it.
  *
  * Kernel variants of the FP32 inner iteration (split p update and stencil, the two folded into
- * one kernel, the recompute pair that stores no A p, or plane-marching tiles) are chosen per grid
- * by timing on its first mixed solve; results agree to the order of one dot product's reduction.
- * Diagnostics only: the environment variable MHD_FORCE_SLAB skips the timing (-1 split, -2
- * folded, -3 recompute pair, -4 recompute pair with the second kernel walking the grid backwards,
- * -5 recompute pair at 6 CTAs per SM, -6 / -7 / -8 single-reduction pair (-7: its residual kernel
- * unrolled over the components, both kernels at 3 CTAs per SM; -8: unrolled residual kernel,
- * update kernel at 4), -64 the FP64 iteration with its components overlapped on two
- * streams,
- * n > 0 tiles of n planes). */
+ * one kernel, the recompute pair that stores no A p, the single-reduction pair, or plane-marching
+ * tiles) and of the FP64 iteration (split, components overlapped on two streams, tiles) are chosen
+ * per grid by timing on its first solve of each precision (or in mhd_grid_reserve); results agree
+ * to the order of the dot products' reductions. Diagnostics only: the environment variable
+ * MHD_FORCE_SLAB skips the timing (-1 split, -2 folded, -3 recompute pair, -4 recompute pair with
+ * the second kernel walking the grid backwards, -5 recompute pair at 6 CTAs per SM, -6 / -7 / -8
+ * single-reduction pair (-7: its residual kernel unrolled over the components, both kernels at 3
+ * CTAs per SM; -8: unrolled residual kernel, update kernel at 4), -64 the FP64 iteration with its
+ * components overlapped, n > 0 tiles of n planes). */
 typedef struct {
     double nu, eta, cfl, dt_fixed, dt_max, alpha_si_fixed;
     double tol, inner_tol;
@@ -344,8 +344,9 @@ mhd_status_t mhd_profile_enable(mhd_grid_t grid, int enable);
 mhd_status_t mhd_profile_read(mhd_grid_t grid, int kernel, double* total_ms, long long* launches);
 /* The kernel forms the grid's autotuner chose, in the codes of MHD_FORCE_SLAB: *fp64_form for the
  * FP64 iteration (-1 split, -2 components overlapped, n > 0 tiles of n planes) and *fp32_form for
- * the FP32 inner iteration (-1 split, -2 folded, -3/-4/-5 recompute pair, <= -100 bulk-staged pair,
- * n > 0 tiles); 0 where that precision has not been tuned yet. Either pointer may be NULL. */
+ * the FP32 inner iteration (-1 split, -2 folded, -3/-4/-5 recompute pair, -6/-7/-8 single-reduction
+ * pair, <= -100 bulk-staged pair, n > 0 tiles); 0 where that precision has not been tuned yet.
+ * Either pointer may be NULL. */
 mhd_status_t mhd_grid_kernel_forms(mhd_grid_t grid, int* fp64_form, int* fp32_form);
 
 /* Text of the last error on this grid ("" if none); NULL grid gives the last create error. */
