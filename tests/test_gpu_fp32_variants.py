@@ -44,6 +44,8 @@ def test_mixed_variant_matches_fp64_oracle(monkeypatch, variant, restart, inner)
         x = torch.zeros((nc,) + b.shape[1:], dtype=torch.float64, device="cuda")
         st, it, ou, rr = P.pcg_solve(g, alpha, to_dev(b[:nc]), x, prm)
         assert st == P.MHD_OK and rr <= 1e-9, (variant, nc, st, rr)
+        # the forced form is the one that ran (no FP64 solve on this grid: that form is untuned)
+        assert P.mhd_grid_kernel_forms(g) == (0, int(variant)), (variant, P.mhd_grid_kernel_forms(g))
         res = b[:nc] - og.apply_M(alpha, to_np(x))
         assert np.linalg.norm(res) <= 1e-9 * np.linalg.norm(b[:nc]) * 1.0000001
         ref = xr if nc == 3 else og.pcg(alpha, b[:nc], tol=1e-13)[0]
