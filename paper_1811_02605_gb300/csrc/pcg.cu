@@ -658,6 +658,7 @@ __global__ void __launch_bounds__(kThreads) k_update(Dims d, T* __restrict__ x,
 //
 // R (k_cgr32): A~ r~ at the cell; gamma, delta, sum dg r~^2. Its last CTA takes the stop test
 // and forms beta and alpha for the update.
+
 // one component of R at one cell group: r~ at the cell and its neighbours, A~ r~, the partial sums
 template <int V>
 __device__ __forceinline__ void cgr_component(const Dims& d, const Cell& c, const Nbr<V>& nb, const float* rk,
