@@ -1061,7 +1061,7 @@ def main():
     ap.add_argument("--iteration-forms", action="store_true",
                     help="time every kernel form of the FP64 and FP32 CG iterations on the first SI system and exit")
     ap.add_argument("--forms64", default="-1,-64")
-    ap.add_argument("--forms32", default="-1,-2,-3,-4,-6,-7,-8,-9")
+    ap.add_argument("--forms32", default="-1,-2,-3,-4,-6,-7,-8")
     ap.add_argument("--form-iters", type=int, default=300)
     ap.add_argument("--batched", action="store_true", help="time the 64-system batched solve and exit")
     ap.add_argument("--batch", type=int, default=64)

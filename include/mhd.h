@@ -126,8 +126,7 @@ enum { MHD_PREC_FP64 = 0, MHD_PREC_MIXED = 1 };
  * MHD_FORCE_SLAB skips the timing (-1 split, -2 folded, -3 recompute pair, -4 recompute pair with
  * the second kernel walking the grid backwards, -5 recompute pair at 6 CTAs per SM, -6 / -7 / -8
  * single-reduction pair (-7: its residual kernel unrolled over the components, both kernels at 3
- * CTAs per SM; -8: unrolled residual kernel, update kernel at 4; -9: the residual kernel's own
- * values staged by asynchronous copies), -64 the FP64 iteration with its
+ * CTAs per SM; -8: unrolled residual kernel, update kernel at 4), -64 the FP64 iteration with its
  * components overlapped, n > 0 tiles of n planes). */
 typedef struct {
     double nu, eta, cfl, dt_fixed, dt_max, alpha_si_fixed;

@@ -756,92 +756,6 @@ __global__ void __launch_bounds__(kThreads, MINB) k_cgr32(Dims d, const float* _
     if (reduce_last<3>(val, partials, &sc->count, out) && threadIdx.x == 0) cgr_finish(sc, out);
 }
 
-// R with the cell's own r~ staged by asynchronous copies (V = 4): each thread copies the
-// centre float4 of every component for its next grid-stride group into its own shared-memory slot
-// (cp.async, 16 bytes, no register held while in flight) before it works on the current group, so
-// the DRAM reads of two groups are in flight at once. Only the copying thread reads its slots, so
-// cp.async.wait_group alone orders them (no block barrier). The neighbours are L1/L2 hits, loaded
-// as before.
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned int sa = static_cast<unsigned int>(__cvta_generic_to_shared(smem));
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-
-template <int NC, int MINB>
-__global__ void __launch_bounds__(kThreads, MINB) k_cgr32a(Dims d, const float* __restrict__ ra,
-                                                           const float* __restrict__ rb, OpTab<float> t,
-                                                           const double* __restrict__ dg, PcgScalars* sc,
-                                                           double* __restrict__ partials) {
-    __shared__ float4 stage[2][NC][kThreads];
-    if (sc->done) return;
-    const float* __restrict__ r = sc->par ? rb : ra;
-    const int nt = d.nt;
-    const unsigned int G = (unsigned int)(d.N / 4);
-    const unsigned int gs = gridDim.x * blockDim.x;
-    Acc<float> a_g, a_d;
-    double a_rr = 0.0;
-    unsigned int g = blockIdx.x * blockDim.x + threadIdx.x;
-    int sg = 0;
-    if (g < G) {
-#pragma unroll
-        for (int k = 0; k < NC; k++) cp_async16(&stage[0][k][threadIdx.x], r + k * d.N + (long long)g * 4);
-    }
-    cp_async_commit();
-    for (; g < G; g += gs) {
-        const unsigned int gn = g + gs;
-        if (gn < G) {
-#pragma unroll
-            for (int k = 0; k < NC; k++)
-                cp_async16(&stage[sg ^ 1][k][threadIdx.x], r + k * d.N + (long long)gn * 4);
-        }
-        cp_async_commit();
-        const Cell c = decompose<4>(d, g);
-        const Nbr<4> nb(d, c);
-        const float cr_lo = t.ar[c.i * nt + c.j], cr_hi = t.ar[(c.i + 1) * nt + c.j];
-        const float ct_lo = t.at[c.i * (nt + 1) + c.j], ct_hi = t.at[c.i * (nt + 1) + c.j + 1];
-        const float cp = t.ap[c.ij];
-        const long long row = c.base - c.k0;
-        const int km = (c.k0 == 0) ? d.np - 1 : c.k0 - 1;
-        const int kp = (c.k0 + 4 == d.np) ? 0 : c.k0 + 4;
-        float rs[4] = {0.f, 0.f, 0.f, 0.f};
-        float dsum = 0.f;
-#pragma unroll
-        for (int k = 0; k < NC; k++) {
-            const float* rk = r + k * d.N;
-            float a[4], b[4], cc[4], e4[4];
-            const float ukm = rk[row + km], ukp = rk[row + kp];
-            ldv<float, 4>(rk + c.base + nb.im, a);
-            ldv<float, 4>(rk + c.base + nb.ip, b);
-            ldv<float, 4>(rk + c.base + nb.jm, cc);
-            ldv<float, 4>(rk + c.base + nb.jp, e4);
-            if (k == 0) cp_async_wait1();   // this group's own values have landed
-            const float4 cv = stage[sg][k][threadIdx.x];
-            const float v[4] = {cv.x, cv.y, cv.z, cv.w};
-#pragma unroll
-            for (int e = 0; e < 4; e++) {
-                const float left = (e == 0) ? ukm : v[e - 1];
-                const float right = (e == 3) ? ukp : v[e + 1];
-                float o = fmaf(-cp, left + right, v[e]);
-                o = fmaf(-cr_lo, a[e], o);
-                o = fmaf(-cr_hi, b[e], o);
-                o = fmaf(-ct_lo, cc[e], o);
-                o = fmaf(-ct_hi, e4[e], o);
-                rs[e] = fmaf(v[e], v[e], rs[e]);
-                dsum = fmaf(v[e], o, dsum);
-            }
-        }
-        a_d.add(dsum);
-        const float cell = (rs[0] + rs[1]) + (rs[2] + rs[3]);
-        a_g.add(cell);
-        a_rr = fma(dg[c.ij], (double)cell, a_rr);
-        sg ^= 1;
-    }
-    double val[3] = {a_g.get(), a_d.get(), a_rr}, out[3];
-    if (reduce_last<3>(val, partials, &sc->count, out) && threadIdx.x == 0) cgr_finish(sc, out);
-}
-
 // U (k_cgu32): p~ = r~ + beta p~_old at the cell and its neighbours, q~ = A~ p~ at the cell,
 // r~ -= alpha q~ into the other r~ half, p~ into the other p~ half, <r~_new, q~> for the next
 // denominator; x~ += alpha p~ + ax p~_old every second iteration (p~_old is at hand: the pending
@@ -1439,25 +1353,6 @@ void enqueue_cgpair32_k(mhd_grid_s* g, cudaStream_t st) {
     prof_end(g, st, s);
 }
 
-// -9: the residual kernel with the cell's own r~ staged by asynchronous copies (V = 4), the update
-// kernel at 3 CTAs per SM
-template <int V, int NC>
-void enqueue_cgpair32_a(mhd_grid_s* g, cudaStream_t st) {
-    if (V != 4) {
-        enqueue_cgpair32_k<V, NC, 3, true, 3>(g, st);
-        return;
-    }
-    const Dims d = g->d;
-    int s = prof_begin(g, st, MHD_KERNEL_CGR32);
-    k_cgr32a<NC, 3><<<grid_blocks(g, d.N / 4, resident_per_sm<k_cgr32a<NC, 3>>()), kThreads, 0, st>>>(
-        d, g->r32, g->q32, g->t32, g->tu.dg, g->sc, g->partials);
-    prof_end(g, st, s);
-    s = prof_begin(g, st, MHD_KERNEL_CGU32);
-    k_cgu32<V, NC, 3><<<grid_blocks(g, d.N / V, resident_per_sm<k_cgu32<V, NC, 3>>()), kThreads, 0, st>>>(
-        d, g->x32, g->r32, g->q32, g->p32, g->t32, g->sc, g->partials);
-    prof_end(g, st, s);
-}
-
 // -6: both kernels at 4 CTAs per SM; -7: the residual kernel unrolled over the components, both at 3;
 // -8: unrolled residual kernel at 3, update kernel at 4. (Measured slower and removed: the cross
 // term from the previous residual read by the residual kernel, its update kernel without a
@@ -1467,7 +1362,6 @@ void enqueue_cgpair32(mhd_grid_s* g, cudaStream_t st) {
     switch (g->slab32) {
         case -7: enqueue_cgpair32_k<V, NC, 3, true, 3>(g, st); break;
         case -8: enqueue_cgpair32_k<V, NC, 3, true, 4>(g, st); break;
-        case -9: enqueue_cgpair32_a<V, NC>(g, st); break;
         default: enqueue_cgpair32_k<V, NC, 4, false, 4>(g, st); break;
     }
 }
@@ -1592,7 +1486,7 @@ void enqueue_iteration(mhd_grid_s* g, cudaStream_t st, int prec, int nc) {
     } else if (g->slab32 <= -100) {
         // plane-marching pair with bulk-copy staging, when the autotuner measured it fastest
         enqueue_bulk32(g, st, nc, -100 - g->slab32);
-    } else if (g->slab32 <= -6 && g->slab32 >= -9) {
+    } else if (g->slab32 <= -6 && g->slab32 >= -8) {
         // single-reduction pair (residual kernel, then the update), when measured fastest
         if (use_v4(g)) enqueue_cgpair32_nc<4>(g, st, nc);
         else enqueue_cgpair32_nc<2>(g, st, nc);
@@ -1733,7 +1627,7 @@ int forced_slab() {
 mhd_status_t tune_slab32(mhd_grid_s* g, int nc) {
     if (g->slab32 != 0) return MHD_OK;
     if (const int f = forced_slab()) {
-        if (f <= -2 && f >= -9) g->slab32 = f;
+        if (f <= -2 && f >= -8) g->slab32 = f;
         else if (f <= -100) g->slab32 = (bulk32_ok(g) && f < -100) ? f : -1;
         else g->slab32 = (f > 0 && tiled32_ok(g) && tiled32_blocks(g, f) <= kMaxBlocks) ? f : -1;
         return MHD_OK;
@@ -1751,12 +1645,11 @@ mhd_status_t tune_slab32(mhd_grid_s* g, int nc) {
     // the stencil, then the update; -3, -4, -5: the recompute pair (no q~ stored), forwards, with
     // the r update walking backwards, or at 6 CTAs per SM; -6, -7, -8: the single-reduction pair
     // (-7: its residual kernel unrolled over the components and both kernels at 3 CTAs per SM; -8:
-    // the unrolled residual kernel with the update kernel at 4; -9: the residual kernel with its
-    // own r~ staged by asynchronous copies); -132,
+    // the unrolled residual kernel with the update kernel at 4); -132,
     // -164: the recompute pair as plane-marching kernels staged by bulk copies (units of 32 or 64
     // planes). Four iterations each after one untimed: an even count, so each is timed with its
     // x updates.
-    for (int cand : {-1, -2, -3, -4, -5, -6, -7, -8, -9, -132, -164}) {
+    for (int cand : {-1, -2, -3, -4, -5, -6, -7, -8, -132, -164}) {
         if (cand <= -100 && !bulk32_ok(g)) continue;
         k_tune_reset<<<1, 1, 0, g->stream>>>(g->sc);
         g->slab32 = cand;
@@ -1939,7 +1832,7 @@ mhd_status_t solve(mhd_grid_s* g, const double* alpha_dev, int nc, const double*
         const int ps = prof_begin(g, g->stream, MHD_KERNEL_OUTER_RES);
         const int restart = (o == 0 || prm->mixed_restart) ? 1 : 0;
         k_outer_res<2><<<grid_blocks(g, d.N / 2, resident_per_sm<k_outer_res<2>>()), kThreads, 0, g->stream>>>(
-            d, nc, b, x, g->r32, (!pc2 && g->slab32 <= -6 && g->slab32 >= -9) ? g->q32 : nullptr, g->p32, g->x32, g->t64, g->tu, g->sc,
+            d, nc, b, x, g->r32, (!pc2 && g->slab32 <= -6 && g->slab32 >= -8) ? g->q32 : nullptr, g->p32, g->x32, g->t64, g->tu, g->sc,
             g->partials, o == 0 ? 1 : 0, restart, pc2 ? 1 : 0, g->t32);
         if (pc2) pc2_reliable32(g, nc, restart);
         prof_end(g, g->stream, ps);
